@@ -1,0 +1,526 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, an invariant, a textbook special case or brute force on tiny inputs.
+Citations name the section / equation of Mikkonen et al. (scattering graph
+method) that the checked function implements.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_16037_gb300 import scenes
+
+
+def hg(g, mu):
+    return (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * mu) ** 1.5)
+
+
+def sun_vec(sza, saa):
+    t, p = math.radians(sza), math.radians(saa)
+    return -np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)])
+
+
+def view_vec(vza, vaa):
+    t, p = math.radians(vza), math.radians(vaa)
+    return np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)])
+
+
+# --------------------------------------------------------------------------
+# Directions and stencil (Sec. 2 coupling graph restricted to a voxel stencil)
+
+@pytest.mark.parametrize("R,n,up,hor,down,ng,nmem", [(1, 26, 9, 8, 9, 9, 9), (2, 98, 41, 16, 41, 49, 50)])
+def test_direction_counts(R, n, up, hor, down, ng, nmem):
+    sc = scenes.make_layered(6, 6, 4, [0.1] * 4, [0.5], R=R, M=512)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    d = r["dirs"]
+    assert r["n_dirs"] == n
+    assert (d[:, 2] > 0).sum() == up and (d[:, 2] == 0).sum() == hor and (d[:, 2] < 0).sum() == down
+    assert r["n_gdirs"] == ng and r["gdir_nmem"].sum() == nmem
+    # the stencil offsets k*u cover the Chebyshev ball exactly once
+    offs = set()
+    for u, km in zip(d, r["kmax"]):
+        for k in range(1, km + 1):
+            o = tuple(int(v) for v in k * u)
+            assert o not in offs
+            offs.add(o)
+    assert len(offs) == (2 * R + 1) ** 3 - 1
+
+
+# --------------------------------------------------------------------------
+# P1: voxel traversal (Beer-Lambert optical depth, Eq. radiance_effectuality)
+
+def brute_tau(mu_e, n, P, V, tend, lphys):
+    """Exact rational traversal: all plane crossings, midpoint cell of each piece."""
+    nz, ny, nx = n
+    ts = {Fraction(0), Fraction(tend)}
+    for a in range(3):
+        if V[a] == 0:
+            continue
+        lo, hi = sorted([P[a], P[a] + V[a] * tend])
+        for b in range(math.floor(lo), math.ceil(hi) + 1):
+            t = (Fraction(b) - P[a]) / V[a]
+            if 0 < t < tend:
+                ts.add(t)
+    ts = sorted(ts)
+    tau = Fraction(0)
+    for t0, t1 in zip(ts[:-1], ts[1:]):
+        tm = (t0 + t1) / 2
+        c = [math.floor(P[a] + V[a] * tm) for a in range(3)]
+        cell = (c[2] * ny + c[1] % ny) * nx + c[0] % nx
+        tau += Fraction(mu_e[cell]) * (t1 - t0)
+    return float(tau) * lphys
+
+
+def test_p1_dda_brute_force():
+    rng = np.random.default_rng(1)
+    nx, ny, nz = 3, 4, 5
+    sc = scenes.make_layered(nx, ny, nz, [0.1] * nz, [0.5])
+    mu_e = rng.lognormal(0, 1, nx * ny * nz)
+    worst = 0.0
+    for trial in range(300):
+        # dyadic rationals: exact in FP64 and in Fractions
+        P = [Fraction(int(rng.integers(0, 64 * nx)), 64), Fraction(int(rng.integers(0, 64 * ny)), 64),
+             Fraction(int(rng.integers(1, 64 * nz - 1)), 64)]
+        if trial % 3 == 0:  # lattice-like: centres and integer directions (corner ties)
+            P = [Fraction(int(rng.integers(0, nx))) + Fraction(1, 2), Fraction(int(rng.integers(0, ny))) + Fraction(1, 2),
+                 Fraction(int(rng.integers(0, nz))) + Fraction(1, 2)]
+            V = [Fraction(int(v)) for v in rng.integers(-2, 3, 3)]
+        else:
+            V = [Fraction(int(v), 8) for v in rng.integers(-24, 25, 3)]
+        if V[2] == 0 and V[0] == 0 and V[1] == 0:
+            continue
+        # stay inside the slab vertically
+        if V[2] > 0:
+            tmax = (nz - P[2]) / V[2]
+        elif V[2] < 0:
+            tmax = P[2] / -V[2]
+        else:
+            tmax = Fraction(7)
+        tend = min(tmax, Fraction(int(rng.integers(1, 40)), 8))
+        lphys = 0.37
+        ref = brute_tau(mu_e, (nz, ny, nx), P, V, tend, lphys)
+        got = O.tau_segment(sc, mu_e, [float(p) for p in P], [float(v) for v in V], float(tend), lphys)
+        if ref > 0:
+            worst = max(worst, abs(got - ref) / ref)
+        else:
+            assert got == 0.0
+    assert worst < 1e-14
+
+
+def test_p1_dda_homogeneous_length():
+    rng = np.random.default_rng(2)
+    nx, ny, nz = 5, 4, 6
+    sc = scenes.make_layered(nx, ny, nz, [0.1] * nz, [0.5], h=(0.07, 0.05, 0.11))
+    mu_e = np.full(nx * ny * nz, 0.731)
+    for _ in range(200):
+        P = rng.uniform([0, 0, 0.01], [nx, ny, nz - 0.01])
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        V = d / np.array([sc.hx, sc.hy, sc.hz])  # cell units per km
+        tmax = (nz - P[2]) / V[2] if V[2] > 0 else P[2] / -V[2]
+        L = min(tmax, rng.uniform(0.01, 3.0))
+        tau = O.tau_segment(sc, mu_e, P, V, L, 1.0)
+        assert abs(tau - 0.731 * L) <= 1e-14 * 0.731 * L
+
+
+# --------------------------------------------------------------------------
+# P2: Beer-Lambert slab closed form (no scattering, Lambertian ground)
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_p2_beer_lambert_slab(R):
+    nz = 7
+    me = [0.3, 0.1, 0.25, 0.6, 0.05, 0.2, 0.4]
+    for A in (0.3, 0.0):
+        sc = scenes.make_layered(6, 5, nz, me, [0.0], albedo=A, R=R, sza=40.0, saa=33.0, vza=25.0, vaa=250.0,
+                                 h=(0.08, 0.1, 0.12), M=1024)
+        r = O.run(sc)
+        tau = sum(me) * sc.hz
+        mu0, muv = math.cos(math.radians(40.0)), math.cos(math.radians(25.0))
+        L = A * mu0 / math.pi * math.exp(-tau / mu0) * math.exp(-tau / muv)
+        if A > 0:
+            np.testing.assert_allclose(r["rad"], L, rtol=1e-14, atol=0)
+            np.testing.assert_allclose(r["refl"], math.pi * L / mu0, rtol=1e-14)
+        else:
+            assert np.all(r["rad"] == 0.0)
+
+
+# --------------------------------------------------------------------------
+# P3: discrete single-scattering closed form (homogeneous periodic slab)
+
+def l_ss_discrete(omega, g, sza, vza, mu_e, hz, nz, cosang):
+    mu0, muv = math.cos(math.radians(sza)), math.cos(math.radians(vza))
+    dt = mu_e * hz
+    a = 1 / mu0 + 1 / muv
+    return (omega * mu0 * hg(g, cosang) * (1 - math.exp(-dt / mu0)) * (1 - math.exp(-dt / muv)) / dt
+            * (1 - math.exp(-nz * dt * a)) / (1 - math.exp(-dt * a)))
+
+
+@pytest.mark.parametrize("R,sza,saa,vza,vaa", [(1, 30, 0, 0, 0), (2, 55, 40, 35, 300), (2, 10, 180, 50, 90)])
+def test_p3_single_scatter_closed_form(R, sza, saa, vza, vaa):
+    nz, mu_e, om, g = 9, 0.8, 0.7, 0.6
+    sc = scenes.make_layered(6, 6, nz, [mu_e] * nz, [om], g=(g,), albedo=0.0, R=R, sza=sza, saa=saa,
+                             vza=vza, vaa=vaa, h=(0.1, 0.12, 0.07), M=1024)
+    r = O.run(sc, flags=O.SINGLE_SCATTER)
+    ca = float(sun_vec(sza, saa) @ view_vec(vza, vaa))
+    ref = l_ss_discrete(om, g, sza, vza, mu_e, sc.hz, nz, ca)
+    np.testing.assert_allclose(r["rad"], ref, rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# P4: single-scattering limits
+
+def test_p4_ms_vanishes_linearly_in_omega():
+    nz = 6
+    rel = []
+    oms = [4e-3, 2e-3, 1e-3]
+    for om in oms:
+        sc = scenes.make_layered(6, 6, nz, [0.5] * nz, [om], g=(0.5,), albedo=0.0, R=1, sza=35, vza=20,
+                                 saa=0, vaa=90, M=1024)
+        full = O.run(sc)["rad"].mean()
+        ss = O.run(sc, flags=O.SINGLE_SCATTER)["rad"].mean()
+        rel.append((full - ss) / ss)
+    slope = np.polyfit(np.log(oms), np.log(rel), 1)[0]
+    assert abs(slope - 1.0) < 0.05
+
+
+def test_p4_single_scatter_continuum_limit():
+    sza, vza, g, om, tau = 40.0, 20.0, 0.5, 0.8, 0.9
+    mu0, muv = math.cos(math.radians(sza)), math.cos(math.radians(vza))
+    ca = float(sun_vec(sza, 0) @ view_vec(vza, 0))
+    cont = om * hg(g, ca) * mu0 / (mu0 + muv) * (1 - math.exp(-tau * (1 / mu0 + 1 / muv)))
+    errs, hs = [], []
+    for nz in (4, 8, 16):
+        hz = 1.0 / nz
+        sc = scenes.make_layered(4, 4, nz, [tau] * nz, [om], g=(g,), albedo=0.0, R=1, sza=sza, vza=vza,
+                                 h=(0.25, 0.25, hz), M=512)
+        L = O.run(sc, flags=O.SINGLE_SCATTER)["rad"].mean()
+        errs.append(abs(L - cont))
+        hs.append(hz)
+    order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert abs(order - 2.0) < 0.1
+
+
+# --------------------------------------------------------------------------
+# P5: energy conservation at omega = 1 with a black surface
+
+@pytest.mark.parametrize("R,sza,saa", [(1, 35.0, 10.0), (2, 62.0, 130.0)])
+def test_p5_energy_conservation(R, sza, saa):
+    nx, ny, nz = 6, 5, 7
+    rng = np.random.default_rng(5)
+    me = rng.uniform(0.1, 2.0, nz)
+    sc = scenes.make_layered(nx, ny, nz, me, [1.0], g=(0.6,), albedo=0.0, R=R, sza=sza, saa=saa,
+                             vza=10, h=(0.1, 0.08, 0.12), M=2048)
+    r = O.run(sc, gmres_tol=1e-15)
+    na = r["n_atm"]
+    mu0 = math.cos(math.radians(sza))
+    incident = nx * ny * mu0 * sc.hx * sc.hy
+    escape = float(r["e1"] @ r["esc_sun"] + r["x"] @ r["esc_iso"])
+    direct_ground = float(mu0 * sc.hx * sc.hy * r["tsun"][na:].sum())
+    row, col = r["slot_row"], r["slot_col"]
+    gnd = row >= na
+    deposited_ground = float((r["slot_depsun"][gnd] * r["e1"][col[gnd]]).sum()
+                             + (r["slot_dep"][gnd] * r["x"][col[gnd]]).sum())
+    total = escape + direct_ground + deposited_ground
+    assert abs(total - incident) <= 1e-12 * incident
+
+
+# --------------------------------------------------------------------------
+# P6: horizontal translation invariance / equivariance (periodic x, y)
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_p6_translation_invariance(R):
+    nz = 6
+    rng = np.random.default_rng(6)
+    sc = scenes.make_layered(6, 6, nz, rng.uniform(0.2, 1.5, nz), rng.uniform(0.5, 0.95, nz), g=(0.7,),
+                             albedo=0.25, R=R, sza=50, saa=20, vza=30, vaa=200, M=2048)
+    r = O.run(sc)
+    L = r["rad"]
+    assert (L.max() - L.min()) <= 1e-13 * L.mean()
+    x = r["x"][: r["n_atm"]].reshape(nz, 6, 6)
+    spread = (x.max(axis=(1, 2)) - x.min(axis=(1, 2))) / x.mean(axis=(1, 2))
+    assert spread.max() <= 1e-13
+
+
+def test_p6_shift_equivariance():
+    sc = scenes.make_random(6, 5, 4, seed=3, S=2, R=2, M=1024)
+    r0 = O.run(sc)
+    sh = sc.copy()
+    sh.mu_a = np.roll(sc.mu_a, (2, 1), axis=(2, 1))
+    sh.mu_s = np.roll(sc.mu_s, (2, 1), axis=(3, 2))
+    r1 = O.run(sh)
+    np.testing.assert_allclose(r1["rad"], np.roll(r0["rad"], (1, 2), axis=(0, 1)), rtol=1e-12)
+
+
+def test_p9_mirror_single_scatter():
+    # y-mirror with sun and sensor in the x-z plane: the single-scattered and
+    # surface-reflected image mirrors exactly (the Fibonacci lattice is not
+    # mirror symmetric, so orders >= 2 are excluded)
+    sc = scenes.make_random(6, 6, 4, seed=9, S=2, R=2, M=1024, saa=0.0, vaa=0.0, vza=30.0, sza=50.0)
+    r0 = O.run(sc, flags=O.SINGLE_SCATTER)
+    mi = sc.copy()
+    mi.mu_a = sc.mu_a[:, ::-1, :].copy()
+    mi.mu_s = sc.mu_s[:, :, ::-1, :].copy()
+    r1 = O.run(mi, flags=O.SINGLE_SCATTER)
+    np.testing.assert_allclose(r1["rad"], r0["rad"][::-1, :], rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# P7: the solve of Eq. flux_system against a dense direct solve; the series
+# of Eq. fs_sum increases monotonically to the same x
+
+@pytest.mark.parametrize("maker", [
+    lambda: scenes.make_plain(),
+    lambda: scenes.make_random(4, 4, 4, seed=1, R=1, M=512),
+    lambda: scenes.make_random(5, 5, 4, seed=2, R=2, M=512),
+])
+def test_p7_dense_solve_and_series(maker):
+    sc = maker()
+    r = O.run(sc)
+    K = O.dense(r)
+    n = K.shape[0]
+    x = np.linalg.solve(np.eye(n) - K, r["s"])
+    np.testing.assert_allclose(r["x"], x, rtol=1e-12, atol=1e-12 * np.abs(x).max())
+    part = r["s"].copy()
+    term = r["s"].copy()
+    for _ in range(60):
+        term = K @ term
+        nxt = part + term
+        assert np.all(nxt >= part)
+        part = nxt
+    assert np.abs(part - x).max() <= 1e-6 * np.abs(x).max()
+    assert max(abs(np.linalg.eigvals(K))) < 1.0
+
+
+# --------------------------------------------------------------------------
+# P8: every unit of power leaving a node is deposited or escapes
+
+@pytest.mark.parametrize("maker", [
+    lambda: scenes.make_plain(),
+    lambda: scenes.make_random(5, 6, 5, seed=4, R=2, M=1024),
+    lambda: scenes.make_random(5, 5, 2, seed=5, R=2, M=1024),   # thinner than the stencil
+])
+def test_p8_column_identity(maker):
+    sc = maker()
+    r = O.run(sc, flags=O.NO_SOLVE)
+    nn = r["n_nodes"]
+    for dep, esc in (("slot_dep", "esc_iso"), ("slot_depsun", "esc_sun")):
+        tot = np.zeros(nn)
+        np.add.at(tot, r["slot_col"], r[dep])
+        np.testing.assert_allclose(tot + r[esc], 1.0, atol=1e-14)
+    # sum_u q c = 1 expressed through the normalisers: z = sum qC / sum q
+    assert np.all(r["z_iso"] > 0)
+
+
+# --------------------------------------------------------------------------
+# Chain deposits in a homogeneous medium: closed forms of the three cases
+
+def test_chain_cases_closed_form():
+    nx, ny, nz, me = 6, 6, 5, 0.9
+    sc = scenes.make_layered(nx, ny, nz, [me] * nz, [0.5], albedo=0.3, R=1, h=(0.1, 0.1, 0.1), M=2048,
+                             coupling=0)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    dirs = [tuple(d) for d in r["dirs"]]
+    q = r["q_iso"]
+    na = r["n_atm"]
+    row, col, dr, k, dep = r["slot_row"], r["slot_col"], r["slot_dir"], r["slot_k"], r["slot_dep"]
+
+    def node(ix, iy, iz):
+        return (iz * ny + iy % ny) * nx + ix % nx
+
+    def slots(j, u):
+        m = (col == j) & (dr == u)
+        return {(int(a), int(b)): float(v) for a, b, v in zip(row[m], k[m], dep[m])}
+
+    h = 0.1
+    # (c) diagonal down from the bottom layer: the ground is hit at a corner
+    u = dirs.index((1, 1, -1))
+    j = node(2, 3, 0)
+    L = h * math.sqrt(3)
+    s = slots(j, u)
+    Th = math.exp(-me * L / 2)
+    assert abs(s[(j, O.K_SELF)] - q[u] * (1 - Th)) < 1e-15
+    cols = [na + (3 + dy) * nx + (2 + dx) for dx in (0, 1) for dy in (0, 1)]
+    for c in cols:
+        assert abs(s[(c, O.K_GROUND)] - q[u] * Th / 4) < 1e-15
+    # (b) up from the top layer: self-deposit and escape
+    u = dirs.index((0, 1, 1))
+    j = node(1, 1, nz - 1)
+    L = h * math.sqrt(2)
+    s = slots(j, u)
+    assert abs(s[(j, O.K_SELF)] - q[u] * (1 - math.exp(-me * L / 2))) < 1e-15
+    # (a) up from an interior voxel: p1 gets its segment plus the extinction
+    # beyond the stencil up to the TOA; horizontal: p1 takes everything
+    u = dirs.index((1, 0, 1))
+    j = node(0, 0, 1)
+    L = h * math.sqrt(2)
+    s = slots(j, u)
+    p1 = node(1, 0, 2)
+    dist_top = (nz - 2.5) * L  # from the centre of layer 2 to the TOA along u
+    expect = (1 - math.exp(-me * L)) + math.exp(-me * L) * (1 - math.exp(-me * dist_top))
+    assert abs(s[(p1, 1)] - q[u] * expect) < 1e-15
+    u = dirs.index((-1, 0, 0))
+    s = slots(j, u)
+    assert abs(s[(node(-1, 0, 1), 1)] - q[u]) < 1e-15
+
+
+def test_coupling_weight_eq_scatt_coup():
+    """Eq. scatt_coup through the assembled matrix: with uniform extinction,
+    the horizontal chains of one source deposit everything at their first
+    node, so deposit ratios of opposite / perpendicular neighbours equal the
+    coupling ratio sqrt(mu_s(n) mu_s(j)) / |r_n - r_j|."""
+    nx, ny, nz = 6, 6, 3
+    rng = np.random.default_rng(8)
+    me = 1.2
+    mus = rng.uniform(0.1, 1.1, (nz, ny, nx))
+    sc = scenes.Scene(nx, ny, nz, 0.07, 0.11, 0.1, mu_a=me - mus, mu_s=mus[None], g=np.array([0.3]),
+                      albedo=0.2, R=1, M=4096)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    dirs = [tuple(d) for d in r["dirs"]]
+    q = r["q_iso"]
+    row, col, dr, dep = r["slot_row"], r["slot_col"], r["slot_dir"], r["slot_dep"]
+    j = (1 * ny + 2) * nx + 3
+    flat = mus.ravel()
+
+    def d_of(u):
+        m = (col == j) & (dr == dirs.index(u))
+        assert m.sum() == 1
+        return float(dep[m][0]), int(row[m][0])
+
+    (dp, np_), (dm, nm) = d_of((1, 0, 0)), d_of((-1, 0, 0))
+    (dyp, nyp) = d_of((0, 1, 0))
+    qp, qm, qy = q[dirs.index((1, 0, 0))], q[dirs.index((-1, 0, 0))], q[dirs.index((0, 1, 0))]
+    np.testing.assert_allclose((dp / qp) / (dm / qm), math.sqrt(flat[np_] / flat[nm]), rtol=1e-13)
+    np.testing.assert_allclose((dp / qp) / (dyp / qy), math.sqrt(flat[np_] / flat[nyp]) * 0.11 / 0.07, rtol=1e-13)
+    # invariance: scaling every mu_s by a constant at fixed extinction leaves
+    # the routing weights unchanged
+    sc2 = sc.copy()
+    sc2.mu_s = 0.5 * sc.mu_s
+    sc2.mu_a = me - sc2.mu_s[0]
+    r2 = O.run(sc2, flags=O.NO_SOLVE)
+    np.testing.assert_allclose(r2["slot_dep"], r["slot_dep"], rtol=1e-13, atol=1e-17)
+    # no coupling: every direction keeps its quadrature weight
+    sc3 = sc.replace(coupling=0)
+    r3 = O.run(sc3, flags=O.NO_SOLVE)
+    assert np.all(r3["z_iso"] == 1.0)
+
+
+# --------------------------------------------------------------------------
+# P10: quadrature of Eq. F_term_phase on the Fibonacci lattice
+
+def test_p10_quadrature_sums_and_hg_normalisation():
+    for R in (1, 2):
+        sc = scenes.make_random(5, 5, 3, seed=1, S=2, R=R, M=8192)
+        r = O.run(sc, flags=O.NO_SOLVE)
+        assert abs(r["q_iso"].sum() - 1) < 1e-14
+        assert abs(r["q_lamb"].sum() - 1) < 1e-14
+        np.testing.assert_allclose(r["q_sun"].sum(axis=1), 1.0, atol=1e-14)
+    pts = O.fibonacci(8192)
+    np.testing.assert_allclose(np.linalg.norm(pts, axis=1), 1.0, atol=1e-15)
+    assert abs(pts.mean(axis=0)).max() < 1e-3
+    for g in (0.0, 0.3, 0.65, 0.85):
+        for s0 in (np.array([0, 0, -1.0]), sun_vec(63, 27)):
+            val = np.array([hg(g, mu) for mu in pts @ s0]).sum() * 4 * math.pi / 8192
+            assert abs(val - 1) < 1e-3
+
+
+def test_p10_cells_converge_to_spherical_voronoi():
+    sv_mod = pytest.importorskip("scipy.spatial")
+    for R, h in ((1, (0.1, 0.1, 0.1)), (2, (0.05, 0.05, 0.1))):
+        sc = scenes.make_layered(5, 5, 3, [0.1] * 3, [0.5], R=R, h=h, M=8192)
+        r8 = O.run(sc, flags=O.NO_SOLVE)
+        u = r8["dirs"] * np.array(h)
+        u = u / np.linalg.norm(u, axis=1, keepdims=True)
+        sv = sv_mod.SphericalVoronoi(u, radius=1.0)
+        area = sv.calculate_areas() / (4 * math.pi)
+        e8 = np.abs(r8["q_iso"] - area).max()
+        rb = O.run(sc.replace(M=262144), flags=O.NO_SOLVE)
+        eb = np.abs(rb["q_iso"] - area).max()
+        assert eb < 2.5e-4 and eb < e8
+
+
+# --------------------------------------------------------------------------
+# Emission toward the instrument (final radiance sum of Sec. 2)
+
+def test_isotropic_emission_identity():
+    """With isotropic phase functions every in-edge is weighted by 1/(4 pi):
+    E_i = (e1_i + x_i) / (4 pi), because the in-edge deposits of a receiver
+    sum to x_i = s_i + (K x)_i."""
+    sc = scenes.make_random(5, 6, 4, seed=11, S=2, R=2, M=1024)
+    sc.g = np.zeros(2)
+    r = O.run(sc)
+    na = r["n_atm"]
+    np.testing.assert_allclose(r["emis"], (r["e1"][:na] + r["x"][:na]) / (4 * math.pi), rtol=1e-12,
+                               atol=1e-15 * r["emis"].max())
+
+
+def _pos(sc, n):
+    na = sc.n_atm
+    if n >= na:
+        c = n - na
+        return np.array([(c % sc.nx + 0.5) * sc.hx, (c // sc.nx + 0.5) * sc.hy, 0.0])
+    iz, rem = divmod(n, sc.nx * sc.ny)
+    iy, ix = divmod(rem, sc.nx)
+    return np.array([(ix + 0.5) * sc.hx, (iy + 0.5) * sc.hy, (iz + 0.5) * sc.hz])
+
+
+def test_emission_directions_from_node_geometry():
+    """E_i recomputed from the slot list with each in-edge's travel direction
+    taken from the node positions (source -> receiver, nearest periodic image)
+    rather than from the direction tables."""
+    sc = scenes.make_random(6, 6, 4, seed=12, S=2, R=2, M=1024, vza=40.0, vaa=70.0)
+    r = O.run(sc)
+    v = view_vec(sc.vza, sc.vaa)
+    s0 = sun_vec(sc.sza, sc.saa)
+    Lx, Ly = sc.nx * sc.hx, sc.ny * sc.hy
+    mus = sc.mu_s.reshape(sc.n_species, -1)
+    tot = mus.sum(0)
+    dirs = r["dirs"]
+    rows = np.random.default_rng(0).choice(r["n_atm"], 25, replace=False)
+    for i in rows:
+        w = mus[:, i] / tot[i] if tot[i] > 0 else np.full(sc.n_species, 1 / sc.n_species)
+        theta = lambda mu: sum(w[s] * hg(sc.g[s], mu) for s in range(sc.n_species))
+        E = r["e1"][i] * theta(float(s0 @ v))
+        m = np.nonzero(r["slot_row"] == i)[0]
+        for e in m:
+            j, k = r["slot_col"][e], r["slot_k"][e]
+            if k == O.K_SELF:
+                u = dirs[r["slot_dir"][e]] * np.array([sc.hx, sc.hy, sc.hz])
+            else:
+                u = _pos(sc, i) - _pos(sc, j)
+                u[0] -= Lx * round(u[0] / Lx)
+                u[1] -= Ly * round(u[1] / Ly)
+            u = u / np.linalg.norm(u)
+            E += theta(float(u @ v)) * (r["slot_valsun"][e] * r["e1"][j] + r["slot_val"][e] * r["x"][j])
+        assert abs(E - r["emis"][i]) <= 1e-12 * abs(E)
+
+
+def test_ground_hit_columns_brute_force():
+    """Every chain that reaches the ground deposits on the column(s) that a
+    dense exact walk of its ray meets at z = 0, split equally on ties."""
+    sc = scenes.make_random(7, 6, 3, seed=13, S=1, R=2, M=512)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    na = r["n_atm"]
+    dirs = r["dirs"]
+    m = r["slot_k"] == O.K_GROUND
+    groups = {}
+    for row, col, d, val in zip(r["slot_row"][m], r["slot_col"][m], r["slot_dir"][m], r["slot_dep"][m]):
+        groups.setdefault((int(col), int(d)), []).append((int(row) - na, float(val)))
+    assert groups
+    for (j, d), hits in groups.items():
+        u = [Fraction(int(c)) for c in dirs[d]]
+        iz, rem = divmod(j, sc.nx * sc.ny)
+        iy, ix = divmod(rem, sc.nx)
+        P = [Fraction(ix) + Fraction(1, 2), Fraction(iy) + Fraction(1, 2), Fraction(iz) + Fraction(1, 2)]
+        t = P[2] / -u[2]
+        hx, hy = P[0] + t * u[0], P[1] + t * u[1]
+        xs = [hx - 1, hx] if hx.denominator == 1 else [math.floor(hx)]
+        ys = [hy - 1, hy] if hy.denominator == 1 else [math.floor(hy)]
+        expect = sorted((int(y) % sc.ny) * sc.nx + int(x) % sc.nx for x in xs for y in ys)
+        got = sorted(c for c, _ in hits)
+        assert got == expect
+        vals = [v for _, v in hits]
+        assert max(vals) - min(vals) <= 1e-15 * max(vals)
