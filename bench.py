@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the scattering-graph voxel path on GB300.
+
+A step is one whole scene: set the medium, assemble K and s, solve
+(I - K) x = s to a relative FP64 residual of 1e-10 (FP32 SpMV, FP64
+refinement), render the 64x64 detector.  The workload is the plume scene of
+64x64x32 voxels with the 124-neighbour stencil (16.8M edges).  The graph
+structure (per shape) is built once before timing.
+
+Default: 1 GPU, 20 timed steps after 3 warm-up steps; L2 is flushed (256 MB
+write) between timed steps, outside the timed interval.  Under torchrun each
+rank runs an independent replica (weak scaling; the path has no exchange).
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "scenes/s and edges/s at 64²×32 (rel err ≤1e-4 vs FP64), %HBM roofline; p50/p99 served"
+WORKLOAD = "plume 64x64x32 voxels (50x50x100 m), R=2 stencil (124 neighbours), 2 species + gas, SZA 60 VZA 30, " \
+           "64x64 detector; FP32 assembly+SpMV, FP64 refinement to rel. residual 1e-10"
+RTOL = 1e-10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--solver", type=int, default=0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
+    summary's source hash matches the kernel source as it is now."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2503_16037_gb300", "csrc", "kernels_solve.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == sha:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, bus_id=None):
+        self.lines = []
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["--id=" + self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(sc, full=True):
+    """The FP64 oracle as it stands, on all host cores, on one scene."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.run(sc, threads=cores)
+    t = time.perf_counter() - t0
+    return r, t, cores
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    if rank != 0:
+        return
+    from paper_2503_16037_gb300 import scenes
+    from oracle import oracle
+    oracle.build()
+    # bounded sample: a quarter of the plume's columns (32x32x32, same physics);
+    # oracle work is proportional to the column count, so the rate is scaled by 1/4
+    sample = scenes.make_plume(nx=32, ny=32, nz=32)
+    frac = (32 * 32) / (64 * 64)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.run(sample, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(sample, threads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = frac * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "scenes/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "32x32x32 plume per step (1/4 of the columns), rate scaled x1/4"},
+        "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": cores, "kind": "oracle",
+                         "sample": "32x32x32 plume per step, FP64 C oracle with OpenMP on all host cores"},
+        "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+    else:
+        torch.cuda.set_device(0)
+    from paper_2503_16037_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2503_16037_gb300 import scenes
+    from paper_2503_16037_gb300 import tursca as T
+
+    sc = scenes.make_plume()
+    stream = torch.cuda.current_stream()
+    rn = T.Runner(sc, T.FP32_REFINE, stream=stream)
+    st = rn.stats
+    mu_a, mu_s = rn.fields("cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step():
+        rn.set_medium(mu_a, mu_s)
+        rn.assemble()
+        rn.solve(rtol=RTOL, solver=args.solver)
+        rn.render()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(torch.cuda.current_device()).pci_bus_id
+    except Exception:
+        bus = None
+    clk = Clocks(bus)
+    clk.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    T.tursca_profile_enable(rn.handle, True)
+    l0 = rn.launches()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    iters = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+        iters.append((rn.info.iters, rn.info.refinements, rn.info.rho_est, rn.info.rel_resid64))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = rn.launches() - l0
+    prof = T.tursca_profile_read(rn.handle)
+    T.tursca_profile_enable(rn.handle, False)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside
+    mu_a_h = mu_a.cpu().pin_memory()
+    mu_s_h = mu_s.cpu().pin_memory()
+    rad_h = torch.empty((sc.npy, sc.npx), dtype=torch.float32).pin_memory()
+    refl_h = torch.empty((sc.npy, sc.npx), dtype=torch.float32).pin_memory()
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T.tursca_set_medium(rn.handle, mu_a_h, mu_s_h, list(sc.g), sc.albedo)
+        T.tursca_assemble_flux(rn.handle, rn.geom)
+        T.tursca_solve_with(rn.handle, args.solver, RTOL, 5000)
+        T.tursca_render_radiance(rn.handle, rad_h, refl_h)  # synchronises
+        if k >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * args.steps / e2e_total
+    h2d = mu_a_h.numel() * 4 + mu_s_h.numel() * 4
+    d2h = rad_h.numel() * 4 + refl_h.numel() * 4
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (FP32 SpMV of the inner iterations)
+    peak, peak_kind = peaks()
+    n_sp, ms_sp = prof.get("spmv", (0, 0.0))
+    kernels = {}
+    tot_prof = sum(v[1] for v in prof.values())
+    for name, (n, ms) in prof.items():
+        if n:
+            kernels[name] = {"launches": n, "avg_us": 1000.0 * ms / n, "share_of_step": ms / total_ms * world}
+    spmv_bytes = st.nnz * 8 + st.n_nodes * 16  # val + col per slot; row_ptr, b, y, x per row
+    roof = None
+    if n_sp:
+        avg_s = ms_sp / n_sp / 1000.0
+        ach = spmv_bytes / avg_s / 1e9
+        roof = {"kernel": "k_spmv (FP32 CSR SpMV, y = b + K x)", "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
+                "traffic": traffic_record("k_spmv"), "algorithmic_bytes_per_launch": spmv_bytes,
+                "avg_launch_us": avg_s * 1e6}
+    # ---- accuracy of this run against the FP64 oracle (also the CPU baseline)
+    cpu = None
+    parity = None
+    if not args.no_cpu_baseline:
+        r, t, cores = cpu_baseline(sc)
+        got = rn.rad.float().cpu().numpy().astype(np.float64)
+        err = np.abs(got - r["rad"]) / np.abs(r["rad"])
+        parity = {"max_rel_err_vs_fp64_oracle": float(err.max()), "mean_rel_err": float(err.mean()),
+                  "tolerance": 1e-4, "pixels": int(err.size)}
+        cpu = {"value": 1.0 / t, "unit": "scenes/s", "cores": cores, "kind": "oracle",
+               "sample": "1 full plume scene 64x64x32 (all stages, FP64 C oracle, OpenMP)", "seconds": t}
+    it = iters[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "scenes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nnz_edges": st.nnz_edges, "nnz_stored": st.nnz, "nodes": st.n_nodes,
+                   "l2": "flushed between timed steps (256 MB write, outside the timed interval)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "edges_per_s": value * st.nnz_edges,
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "scenes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "parity": parity,
+        "solve": {"iters": it[0], "refinements": it[1], "rho_est": it[2], "rel_resid64": it[3]},
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

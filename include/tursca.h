@@ -1,0 +1,237 @@
+/*
+ * tursca.h -- C ABI of the GB300 scattering-graph radiative-transfer library
+ * (libtursca_gb.so).
+ *
+ * The library computes the data-parallel hot path of the scattering graph
+ * method (Mikkonen et al., "Scattering graph method for 3D radiative
+ * transfer", Sec. 2 and Sec. 3) on a graph whose nodes are the voxels of a
+ * regular 3D grid plus one Lambertian ground node per column:
+ *
+ *   1. assemble the flux matrix K (rows = receivers) whose entries are a
+ *      Beer-Lambert transmittance of the edge (Eq. radiance_effectuality and
+ *      the exponential of Eq. Fab) x a phase-function quadrature weight p'
+ *      (Eq. F_term_phase, Fibonacci lattice of Sec. 3) x the normalised
+ *      scattering coupling C(r, r') (Eq. scatt_coup), and the direct solar
+ *      source s (S_a, Sec. 2);
+ *   2. solve (I - K) x = s (Eq. flux_system, equivalently the series of
+ *      Eq. fs_sum);
+ *   3. sum the node radiances into detector pixels along the lines of sight
+ *      (final radiance sum of Sec. 2, step 5 of the algorithm in Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - Functions return tursca_status; no C++ exception crosses the ABI.
+ *   - Array arguments are caller-owned and borrowed for the duration of the
+ *     call; the library copies what it keeps.  They may be device pointers or
+ *     host pointers (pageable or pinned): copies use cudaMemcpyDefault.
+ *   - The element type of field and output arrays follows
+ *     tursca_grid_desc.precision: double for TURSCA_FP64, float for
+ *     TURSCA_FP32_REFINE.
+ *   - Grid arrays are C order (z, y, x), x fastest.  Lengths in km,
+ *     coefficients in km^-1, angles in degrees.
+ *   - Work is enqueued on the stream given at creation.  Argument errors are
+ *     returned synchronously; asynchronous CUDA errors and invalid field
+ *     values found on the device are returned by the next call that
+ *     synchronises (tursca_solve, tursca_render_radiance, tursca_get).
+ *   - Calls out of order (e.g. solve before assemble_flux) return
+ *     TURSCA_E_STATE.
+ *   - A scene is not thread safe; distinct scenes may be used from distinct
+ *     threads.
+ */
+#ifndef TURSCA_H
+#define TURSCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tursca_scene tursca_scene; /* opaque; owns its device state */
+
+typedef enum {
+    TURSCA_OK = 0,
+    TURSCA_E_INVALID = 1,       /* bad argument or invalid field value */
+    TURSCA_E_NOMEM = 2,         /* device or host allocation failed */
+    TURSCA_E_CUDA = 3,          /* CUDA runtime error (see tursca_last_error) */
+    TURSCA_E_NOT_CONVERGED = 4, /* solver stopped at max_iter above rtol */
+    TURSCA_E_TIMEOUT = 5,       /* a bounded device wait gave up */
+    TURSCA_E_STATE = 6,         /* call out of order */
+    TURSCA_E_UNSUPPORTED = 7    /* entry point declared but not available */
+} tursca_status;
+
+enum { TURSCA_FP64 = 0, TURSCA_FP32_REFINE = 1 };
+enum { TURSCA_COUPLING_NONE = 0, TURSCA_COUPLING_WEIGHT = 1 };
+enum { TURSCA_SOLVER_AUTO = 0, TURSCA_SOLVER_NEUMANN = 1, TURSCA_SOLVER_GMRES = 2 };
+
+/* Grid and method parameters (fixed for the life of a scene).
+ *   nx, ny >= 2 R + 1 (x and y are periodic), nz >= R.
+ *   stencil_radius R in {1, 2}: each voxel couples to the voxel centres
+ *     j + k u, u a primitive integer vector with |u|_inf <= R,
+ *     k = 1..floor(R / |u|_inf) (26 neighbours for R = 1, 124 for R = 2);
+ *     the ground node of a column couples to the voxels (dx, dy, dz - 1/2)
+ *     away, |dx|, |dy| <= R, 1 <= dz <= R.
+ *   fib_points M (>= 64): points of the Fibonacci lattice used for the
+ *     quadrature of Eq. F_term_phase (Sec. 3).
+ *   n_species S in 1..4: scattering species, each with a Henyey-Greenstein
+ *     phase function.
+ *   coupling_mode: TURSCA_COUPLING_WEIGHT applies Eq. scatt_coup as a
+ *     normalised routing weight; TURSCA_COUPLING_NONE uses weight 1.
+ *   precision: TURSCA_FP64 (all FP64) or TURSCA_FP32_REFINE (FP32 edge march
+ *     and SpMV, FP64 residual and refinement update). */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+    int n_species;
+    int stencil_radius;
+    int fib_points;
+    int coupling_mode;
+    int precision;
+} tursca_grid_desc;
+
+/* Illumination and viewing geometry (Sec. 2: far-field source, instrument).
+ *   sza < 90, vza < 90; f0 the solar irradiance normal to the beam.
+ *   The sun's beam travels along -(sin sza cos saa, sin sza sin saa, cos sza);
+ *   the instrument sees the scene along +(sin vza cos vaa, sin vza sin vaa,
+ *   cos vza).  Pixel (a, b) of the npx x npy detector looks at the ground
+ *   point ((a + 1/2) nx hx / npx, (b + 1/2) ny hy / npy, 0). */
+typedef struct {
+    double sza, saa, vza, vaa, f0;
+    int npx, npy;
+} tursca_geometry;
+
+typedef struct {
+    int iters;          /* matrix-vector products with K in the solve */
+    int refinements;    /* outer FP64 residual evaluations */
+    double rel_resid64; /* ||s - (I - K) x|| / ||s|| evaluated in FP64 */
+    double rho_est;     /* estimate of the spectral radius of K */
+    int solver;         /* TURSCA_SOLVER_* actually used */
+} tursca_solve_info;
+
+/* Counts of the graph for a grid (host only; no GPU needed). */
+typedef struct {
+    int n_atm, n_ground, n_nodes;
+    int n_dirs, n_up_dirs, n_gdirs, n_gmembers;
+    long long nnz;        /* stored slots including row padding */
+    long long nnz_edges;  /* slots that carry a graph edge (no padding) */
+    int n_classes;        /* distinct slot classes (translation-invariant) */
+    int max_row;          /* longest row (slots) */
+} tursca_graph_stats;
+
+/* Internal arrays that tursca_get can copy out (for tests and tools). */
+typedef enum {
+    TURSCA_F_ROW_PTR = 0,  /* int32 [n_nodes + 1] */
+    TURSCA_F_COL = 1,      /* int32 [nnz] source node of each slot */
+    TURSCA_F_VAL = 2,      /* real  [nnz] K value of each slot */
+    TURSCA_F_SLOT_DIR = 3, /* int16 [nnz] direction: atmospheric 0..n_dirs-1, ground n_dirs + g, -1 padding */
+    TURSCA_F_SLOT_K = 4,   /* int8  [nnz] chain index; 0 self, 7 ground hit, -1 padding */
+    TURSCA_F_TSUN = 5,     /* real  [n_nodes] sun transmittance (top-face centre / ground point) */
+    TURSCA_F_E1 = 6,       /* real  [n_nodes] first-order scattered (reflected) power */
+    TURSCA_F_S = 7,        /* real  [n_nodes] s = K^sun e1 */
+    TURSCA_F_X = 8,        /* double [n_nodes] solution of (I - K) x = s */
+    TURSCA_F_EMIS = 9,     /* real  [n_atm] emission toward the instrument E_i */
+    TURSCA_F_GSUN = 10,    /* real  [n_atm] second-order part of E_i */
+    TURSCA_F_Q_ISO = 11,   /* double [n_dirs] */
+    TURSCA_F_Q_LAMB = 12,  /* double [n_gdirs] */
+    TURSCA_F_Q_SUN = 13,   /* real  [n_species][n_dirs] */
+    TURSCA_F_DIRS = 14     /* int32 [n_dirs][3] lattice directions, in the library's order */
+} tursca_field;
+
+/* Create a scene for grid *desc whose work runs on cuda_stream (a
+ * cudaStream_t; NULL = the legacy default stream).  Allocates nothing on the
+ * device until build_graph.  Errors: TURSCA_E_INVALID on a bad descriptor. */
+tursca_status tursca_scene_create(const tursca_grid_desc *desc, void *cuda_stream, tursca_scene **out);
+
+/* Free every resource of the scene (synchronises its stream).  NULL is a no-op. */
+tursca_status tursca_scene_destroy(tursca_scene *scene);
+
+/* Set the optical fields (Sec. 2: mu_a, mu_s, Theta).
+ *   mu_abs [nz][ny][nx] absorption coefficient, >= 0;
+ *   mu_sca [n_species][nz][ny][nx] scattering coefficient per species, >= 0;
+ *   g [n_species] host array of HG asymmetry parameters, |g| < 1;
+ *   albedo: Lambertian surface albedo in [0, 1].
+ * The fields are copied; negative or non-finite values are reported as
+ * TURSCA_E_INVALID by the next synchronising call. */
+tursca_status tursca_set_medium(tursca_scene *scene, const void *mu_abs, const void *mu_sca, const double *g,
+                                double albedo);
+
+/* Build the graph for the scene's grid: direction sets, Fibonacci partition
+ * (Sec. 3), translation-invariant tap tables of every edge segment, and the
+ * CSR structure of K (rows = receivers).  Cached: a second call is a no-op. */
+tursca_status tursca_build_graph(tursca_scene *scene);
+
+/* Assemble K, the direct source e1 and s = K^sun e1 for the current medium
+ * and geometry (Eqs. Fab, F_term_phase, scatt_coup; S_a of Sec. 2).
+ * Requires build_graph and set_medium. */
+tursca_status tursca_assemble_flux(tursca_scene *scene, const tursca_geometry *geom);
+
+/* Solve (I - K) x = s (Eq. flux_system) to ||s - (I - K) x|| <= rtol ||s||
+ * evaluated in FP64, with at most max_iter products with K.  FP32_REFINE
+ * scenes run FP32 inner iterations and FP64 residual refinement; FP64 scenes
+ * run FP64 GMRES.  Synchronises.  info may be NULL. */
+tursca_status tursca_solve(tursca_scene *scene, double rtol, int max_iter, tursca_solve_info *info);
+
+/* Same as tursca_solve with an explicit solver choice (TURSCA_SOLVER_*). */
+tursca_status tursca_solve_with(tursca_scene *scene, int solver, double rtol, int max_iter,
+                                tursca_solve_info *info);
+
+/* Emission toward the instrument and detector radiance (final radiance sum of
+ * Sec. 2, integrated over voxel segments): radiance [npy][npx] in units of
+ * f0 per steradian; reflectance [npy][npx] = pi L / (cos(sza) f0), may be
+ * NULL.  Requires solve.  Synchronises before returning. */
+tursca_status tursca_render_radiance(tursca_scene *scene, void *radiance, void *reflectance);
+
+/* Gradient of J with respect to mu_abs given dJ/dL [npy][npx] (adjoint of the
+ * path).  Declared for the interface; this version returns
+ * TURSCA_E_UNSUPPORTED without touching its arguments. */
+tursca_status tursca_adjoint(tursca_scene *scene, const void *dJ_dL, void *dJ_dmu_abs);
+
+/* Copy an internal array out (device -> dst, host or device pointer) after the
+ * stage that produces it; bytes must equal the array size.  Synchronises. */
+tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, size_t bytes);
+
+/* Number of kernel launches the scene has issued since creation. */
+long long tursca_launch_count(const tursca_scene *scene);
+
+/* Per-kernel device time measured with CUDA events recorded on the scene's
+ * stream around each launch of the hot kernels (profiling only). */
+typedef struct {
+    char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render" */
+    long long launches; /* launches since the last read */
+    double total_ms;    /* summed event time of those launches */
+} tursca_kernel_stat;
+
+/* Turn event timing on (1) or off (0).  While on, every launch of a profiled
+ * kernel is bracketed by two events; the pool grows as needed. */
+tursca_status tursca_profile_enable(tursca_scene *scene, int on);
+
+/* Synchronise, fill out[0..n) with the per-kernel totals since the last read
+ * (or enable), reset them, and set *n_out to the number of entries. */
+tursca_status tursca_profile_read(tursca_scene *scene, tursca_kernel_stat *out, int n, int *n_out);
+
+/* Host-only (no GPU): graph counts for a grid descriptor. */
+tursca_status tursca_graph_info(const tursca_grid_desc *desc, tursca_graph_stats *out);
+
+/* Host-only (no GPU): the CSR structure for a grid descriptor, into caller
+ * host arrays sized by tursca_graph_info: row_ptr [n_nodes + 1], col [nnz],
+ * dir [nnz], k [nnz] (same meaning as the TURSCA_F_* fields). */
+tursca_status tursca_graph_structure(const tursca_grid_desc *desc, int32_t *row_ptr, int32_t *col, int16_t *dir,
+                                     int8_t *k);
+
+/* Host-only (no GPU): the Fibonacci-partition quadrature weights of the grid's
+ * direction sets: q_iso [n_dirs] (cell fraction), q_lamb [n_gdirs]
+ * (cosine-weighted fraction of the upper hemisphere). */
+tursca_status tursca_quadrature(const tursca_grid_desc *desc, double *q_iso, double *q_lamb);
+
+/* Static description of a status code. */
+const char *tursca_status_string(tursca_status status);
+
+/* Last error message recorded on the scene (or the last global error when
+ * scene is NULL), NUL-terminated into buf[n]. */
+tursca_status tursca_last_error(const tursca_scene *scene, char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TURSCA_H */

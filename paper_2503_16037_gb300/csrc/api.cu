@@ -1,0 +1,984 @@
+// C ABI of libtursca_gb (declared in include/tursca.h): scene lifecycle,
+// uploads, stage orchestration and the solver control loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "graph.h"
+#include "kern.h"
+#include "tursca.h"
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+struct tursca_scene {
+    tursca_grid_desc d{};
+    cudaStream_t st = nullptr;
+    std::string err;
+    long long launches = 0;
+    size_t es = 4;  // element size of the compute type
+
+    tg::Graph G;
+    bool built = false;
+    tg::ViewTables VT;
+    bool view_ok = false;
+    tursca_geometry geom{};
+    bool medium = false, assembled = false, solved = false;
+    double g[tk::MAX_SPECIES] = {0, 0, 0, 0};
+    double albedo = 0.0;
+
+    std::vector<void *> allocs;      // graph-lifetime allocations
+    std::vector<void *> view_allocs; // geometry-lifetime allocations
+
+    // graph
+    int32_t *row_ptr = nullptr, *col = nullptr;
+    uint16_t *code = nullptr;
+    tk::DClass *cls = nullptr;
+    tk::DTap *taps = nullptr;
+    float *tlf = nullptr;
+    double *tld = nullptr;
+    int4 *dirs = nullptr, *gmem1 = nullptr;
+    double *dir_len = nullptr, *q_iso = nullptr, *q_lamb = nullptr, *gdist1 = nullptr;
+    int *up_dirs = nullptr, *top_off = nullptr, *top_n = nullptr, *lat_off = nullptr, *lat_n = nullptr,
+        *gtop_off = nullptr, *gtop_n = nullptr;
+    double *lattice = nullptr, *dirhat = nullptr;
+    int *cell_start = nullptr;
+    // view
+    tk::DTap *sun_taps = nullptr, *los_taps = nullptr;
+    float *sun_lf = nullptr, *los_lf = nullptr;
+    double *sun_ld = nullptr, *los_ld = nullptr;
+    int *sun_off = nullptr, *sun_n = nullptr, *los_off = nullptr, *los_n = nullptr, *pix_cx = nullptr,
+        *pix_cy = nullptr, *pix_cls = nullptr;
+    void *rad = nullptr, *refl = nullptr;
+    // fields (compute type)
+    void *mu_a = nullptr, *mu_s = nullptr, *mu_e = nullptr, *mu_st = nullptr, *tsun = nullptr, *e1 = nullptr,
+         *tinf = nullptr, *tinfg = nullptr, *zc_iso = nullptr, *zc_sun = nullptr, *q_sun = nullptr, *hgv = nullptr,
+         *hg0v = nullptr, *val = nullptr, *s = nullptr, *gsun = nullptr, *emis = nullptr;
+    unsigned long long *musmax = nullptr;
+    int *status = nullptr;
+    bool fields_alloc = false;
+    // solver
+    double *x64 = nullptr, *r64 = nullptr, *part = nullptr, *dred = nullptr, *hred = nullptr;
+    void *b = nullptr, *d0 = nullptr, *d1 = nullptr, *V = nullptr, *w = nullptr;
+    int gm_m = 0;
+    // event timing of the hot kernels
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;   // pairs
+    std::vector<int> ev_cat;
+    size_t ev_used = 0;
+};
+
+namespace {
+const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render"};
+constexpr int kNProf = 5;
+enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4 };
+
+// returns the index of the pair, or -1 when profiling is off
+int prof_begin(tursca_scene *sc, int cat) {
+    if (!sc->prof) return -1;
+    if (sc->ev_used * 2 + 2 > sc->ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            sc->ev.push_back(e);
+        }
+        sc->ev_cat.resize(sc->ev.size() / 2);
+    }
+    size_t i = sc->ev_used++;
+    sc->ev_cat[i] = cat;
+    cudaEventRecord(sc->ev[2 * i], sc->st);
+    return (int)i;
+}
+void prof_end(tursca_scene *sc, int i) {
+    if (i >= 0) cudaEventRecord(sc->ev[2 * i + 1], sc->st);
+}
+}  // namespace
+
+namespace {
+
+tursca_status fail(tursca_scene *sc, tursca_status code, const std::string &msg) {
+    if (sc) sc->err = msg;
+    g_last_error = msg;
+    return code;
+}
+
+tursca_status cuda_fail(tursca_scene *sc, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(sc, e == cudaErrorMemoryAllocation ? TURSCA_E_NOMEM : TURSCA_E_CUDA, m);
+}
+
+#define CK(expr, where)                                   \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return cuda_fail(sc, _e, where); \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(std::vector<void *> &list, P *&p, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    list.push_back(q);
+    p = reinterpret_cast<P *>(q);
+    return cudaSuccess;
+}
+
+template <typename P>
+cudaError_t upload(tursca_scene *sc, std::vector<void *> &list, P *&p, const void *src, size_t bytes) {
+    cudaError_t e = dalloc(list, p, bytes);
+    if (e != cudaSuccess) return e;
+    if (bytes) e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, sc->st);
+    return e;
+}
+
+void free_list(std::vector<void *> &list) {
+    for (void *p : list) cudaFree(p);
+    list.clear();
+}
+
+tk::GridC grid_c(const tursca_scene *sc) {
+    const tg::Graph &G = sc->G;
+    tk::GridC g;
+    g.nx = sc->d.nx;
+    g.ny = sc->d.ny;
+    g.nz = sc->d.nz;
+    g.nxy = g.nx * g.ny;
+    g.n_atm = g.nxy * g.nz;
+    g.n_ground = g.nxy;
+    g.n_nodes = g.n_atm + g.n_ground;
+    g.S = sc->d.n_species;
+    g.nd = (int)G.dirs.size();
+    g.ngd = (int)G.gdirs.size();
+    g.nup = (int)G.up_dirs.size();
+    g.R = sc->d.stencil_radius;
+    g.hx = sc->d.hx;
+    g.hy = sc->d.hy;
+    g.hz = sc->d.hz;
+    return g;
+}
+
+tk::GraphP graph_p(const tursca_scene *sc) {
+    tk::GraphP p;
+    p.row_ptr = sc->row_ptr;
+    p.col = sc->col;
+    p.code = sc->code;
+    p.cls = sc->cls;
+    p.taps = sc->taps;
+    p.tap_len_f = sc->tlf;
+    p.tap_len_d = sc->tld;
+    p.dirs = sc->dirs;
+    p.dir_len = sc->dir_len;
+    p.q_iso = sc->q_iso;
+    p.q_lamb = sc->q_lamb;
+    p.gmem1 = sc->gmem1;
+    p.gdist1 = sc->gdist1;
+    p.up_dirs = sc->up_dirs;
+    p.top_off = sc->top_off;
+    p.top_n = sc->top_n;
+    p.lat_off = sc->lat_off;
+    p.lat_n = sc->lat_n;
+    p.gtop_off = sc->gtop_off;
+    p.gtop_n = sc->gtop_n;
+    return p;
+}
+
+template <typename T>
+tk::FieldP<T> field_p(const tursca_scene *sc) {
+    tk::FieldP<T> f;
+    f.mu_a = (const T *)sc->mu_a;
+    f.mu_s = (const T *)sc->mu_s;
+    f.mu_e = (T *)sc->mu_e;
+    f.mu_st = (T *)sc->mu_st;
+    f.tsun = (T *)sc->tsun;
+    f.e1 = (T *)sc->e1;
+    f.tinf = (T *)sc->tinf;
+    f.tinfg = (T *)sc->tinfg;
+    f.zc_iso = (T *)sc->zc_iso;
+    f.zc_sun = (T *)sc->zc_sun;
+    f.q_sun = (T *)sc->q_sun;
+    f.hgv = (T *)sc->hgv;
+    f.hg0v = (T *)sc->hg0v;
+    f.val = (T *)sc->val;
+    f.s = (T *)sc->s;
+    f.gsun = (T *)sc->gsun;
+    f.mus_max_bits = sc->musmax;
+    f.status = sc->status;
+    return f;
+}
+
+tk::ViewC view_c(const tursca_scene *sc) {
+    tk::ViewC v;
+    for (int a = 0; a < 3; ++a) {
+        v.s0[a] = sc->VT.s0[a];
+        v.v[a] = sc->VT.v[a];
+    }
+    v.mu0 = sc->VT.mu0;
+    v.f0 = sc->geom.f0;
+    v.albedo = sc->albedo;
+    for (int s = 0; s < tk::MAX_SPECIES; ++s) v.g[s] = sc->g[s];
+    v.coupling = sc->d.coupling_mode;
+    return v;
+}
+
+tk::ViewP view_p(const tursca_scene *sc) {
+    tk::ViewP p;
+    p.sun_taps = sc->sun_taps;
+    p.sun_len_f = sc->sun_lf;
+    p.sun_len_d = sc->sun_ld;
+    p.sun_off = sc->sun_off;
+    p.sun_n = sc->sun_n;
+    p.los_taps = sc->los_taps;
+    p.los_len_f = sc->los_lf;
+    p.los_len_d = sc->los_ld;
+    p.los_off = sc->los_off;
+    p.los_n = sc->los_n;
+    p.pix_cx = sc->pix_cx;
+    p.pix_cy = sc->pix_cy;
+    p.pix_cls = sc->pix_cls;
+    p.lattice = sc->lattice;
+    p.cell_start = sc->cell_start;
+    p.dirhat = sc->dirhat;
+    p.npx = sc->geom.npx;
+    p.npy = sc->geom.npy;
+    return p;
+}
+
+void split_taps(const std::vector<tg::Tap> &t, std::vector<tk::DTap> &off, std::vector<float> &lf,
+                std::vector<double> &ld) {
+    off.resize(t.size());
+    lf.resize(t.size());
+    ld.resize(t.size());
+    for (size_t i = 0; i < t.size(); ++i) {
+        off[i] = tk::DTap{(int16_t)t[i].dx, (int16_t)t[i].dy, (int16_t)t[i].dz, 0};
+        lf[i] = (float)t[i].len;
+        ld[i] = t[i].len;
+    }
+}
+
+std::string check_desc(const tursca_grid_desc *d) {
+    if (!d) return "null descriptor";
+    if (d->n_species < 1 || d->n_species > tk::MAX_SPECIES) return "n_species must be in 1..4";
+    if (d->precision != TURSCA_FP64 && d->precision != TURSCA_FP32_REFINE) return "unknown precision";
+    if (d->coupling_mode != TURSCA_COUPLING_NONE && d->coupling_mode != TURSCA_COUPLING_WEIGHT)
+        return "unknown coupling_mode";
+    if (d->stencil_radius < 1 || d->stencil_radius > 2) return "stencil_radius must be 1 or 2";
+    if (d->nx < 2 * d->stencil_radius + 1 || d->ny < 2 * d->stencil_radius + 1)
+        return "nx and ny must be at least 2 * stencil_radius + 1";
+    if (d->nz < d->stencil_radius) return "nz must be at least stencil_radius";
+    if (!(d->hx > 0 && d->hy > 0 && d->hz > 0) || !std::isfinite(d->hx) || !std::isfinite(d->hy) ||
+        !std::isfinite(d->hz))
+        return "cell sizes must be positive and finite";
+    if (d->fib_points < 64 || d->fib_points > (1 << 24)) return "fib_points must be in [64, 2^24]";
+    if ((long long)d->nx * d->ny * (d->nz + 1) > 200000000LL) return "grid too large";
+    return std::string();
+}
+
+tursca_status ensure_fields(tursca_scene *sc) {
+    if (sc->fields_alloc) return TURSCA_OK;
+    const size_t es = sc->es;
+    const size_t na = (size_t)sc->d.nx * sc->d.ny * sc->d.nz;
+    const size_t nn = na + (size_t)sc->d.nx * sc->d.ny;
+    CK(dalloc(sc->allocs, sc->mu_a, na * es), "alloc mu_a");
+    CK(dalloc(sc->allocs, sc->mu_s, na * es * sc->d.n_species), "alloc mu_s");
+    CK(dalloc(sc->allocs, sc->mu_e, na * es), "alloc mu_e");
+    CK(dalloc(sc->allocs, sc->mu_st, na * es), "alloc mu_st");
+    CK(dalloc(sc->allocs, sc->tsun, nn * es), "alloc tsun");
+    CK(dalloc(sc->allocs, sc->e1, nn * es), "alloc e1");
+    CK(dalloc(sc->allocs, sc->zc_iso, nn * es), "alloc zc");
+    CK(dalloc(sc->allocs, sc->zc_sun, nn * es), "alloc zc");
+    CK(dalloc(sc->allocs, sc->s, nn * es), "alloc s");
+    CK(dalloc(sc->allocs, sc->gsun, na * es), "alloc gsun");
+    CK(dalloc(sc->allocs, sc->emis, na * es), "alloc emis");
+    CK(dalloc(sc->allocs, sc->musmax, sizeof(unsigned long long)), "alloc musmax");
+    CK(dalloc(sc->allocs, sc->status, sizeof(int)), "alloc status");
+    CK(cudaMemsetAsync(sc->status, 0, sizeof(int), sc->st), "memset status");
+    CK(dalloc(sc->allocs, sc->x64, nn * sizeof(double)), "alloc x");
+    CK(dalloc(sc->allocs, sc->r64, nn * sizeof(double)), "alloc r");
+    CK(dalloc(sc->allocs, sc->part, 64 * 1024 * sizeof(double)), "alloc part");
+    CK(dalloc(sc->allocs, sc->dred, 256 * sizeof(double)), "alloc red");
+    CK(dalloc(sc->allocs, sc->b, nn * es), "alloc b");
+    CK(dalloc(sc->allocs, sc->d0, nn * es), "alloc d0");
+    CK(dalloc(sc->allocs, sc->d1, nn * es), "alloc d1");
+    CK(dalloc(sc->allocs, sc->w, nn * es), "alloc w");
+    if (!sc->hred) {
+        cudaError_t e = cudaMallocHost((void **)&sc->hred, 256 * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(sc, e, "alloc pinned");
+    }
+    sc->fields_alloc = true;
+    return TURSCA_OK;
+}
+
+tursca_status sync_check(tursca_scene *sc, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sc->st);
+    if (e != cudaSuccess) return cuda_fail(sc, e, where);
+    if (sc->status) {
+        int stv = 0;
+        e = cudaMemcpy(&stv, sc->status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(sc, e, where);
+        if (stv & tk::STATUS_BAD_FIELD)
+            return fail(sc, TURSCA_E_INVALID, "field values must be finite and non-negative");
+        if (stv & tk::STATUS_TIMEOUT) return fail(sc, TURSCA_E_TIMEOUT, "a bounded device wait gave up");
+    }
+    return TURSCA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solver
+
+struct SolveState {
+    int iters = 0, refinements = 0, solver = 0;
+    double rel = 1.0, rho = 0.0;
+};
+
+template <typename T>
+tursca_status read_red(tursca_scene *sc, int n) {
+    CK(cudaMemcpyAsync(sc->hred, sc->dred, n * sizeof(double), cudaMemcpyDeviceToHost, sc->st), "d2h");
+    CK(cudaStreamSynchronize(sc->st), "sync");
+    return TURSCA_OK;
+}
+
+// Neumann (source) iteration on (I - K) d = b: d <- b + K d, n sweeps after d = b.
+template <typename T>
+T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, int n, SolveState &ss) {
+    T *cur = (T *)sc->d0, *nxt = (T *)sc->d1;
+    cudaMemcpyAsync(cur, b, (size_t)g.n_nodes * sizeof(T), cudaMemcpyDeviceToDevice, sc->st);  // checked at the next sync
+    for (int it = 0; it < n; ++it) {
+        int pi = prof_begin(sc, P_SPMV);
+        tk::launch_spmv<T>(sc->st, g, gp, (const T *)sc->val, cur, b, nxt);
+        prof_end(sc, pi);
+        std::swap(cur, nxt);
+    }
+    sc->launches += n;
+    ss.iters += n;
+    return cur;
+}
+
+// Restarted GMRES(m) on (I - K) d = b to ||b - (I - K) d|| <= tol ||b||; d must
+// not alias b.  Classical Gram-Schmidt with one re-orthogonalisation pass.
+template <typename T>
+tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, T *d, double tol,
+                    int maxit, SolveState &ss) {
+    const int n = g.n_nodes, m = sc->gm_m;
+    const size_t ld = (size_t)n;
+    T *V = (T *)sc->V, *w = (T *)sc->w, *r = (T *)sc->d1;
+    const int nb = tk::dot_blocks(n);
+    CK(cudaMemsetAsync(d, 0, (size_t)n * sizeof(T), sc->st), "memset");
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    tk::launch_sumsq<T>(sc->st, n, b, sc->part, nb, sc->dred);
+    sc->launches += 2;
+    tursca_status rs = read_red<T>(sc, 1);
+    if (rs) return rs;
+    const double bn = std::sqrt(sc->hred[0]);
+    if (bn == 0.0) return TURSCA_OK;
+    int total = 0;
+    const T *rc = b;  // residual of the current cycle
+    double beta = bn;
+    for (int cycle = 0; cycle < 1000; ++cycle) {
+        tk::launch_scale<T>(sc->st, n, rc, 1.0 / beta, V);
+        sc->launches++;
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int k = 0;
+        bool done = false;
+        for (k = 0; k < m; ++k) {
+            T *vk = V + (size_t)k * ld, *vn = V + (size_t)(k + 1) * ld;
+            int pi = prof_begin(sc, P_SPMV);
+            tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, vk, w);
+            prof_end(sc, pi);
+            tk::launch_dots<T, T>(sc->st, n, V, ld, k + 1, w, sc->part, nb, sc->dred);
+            tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);
+            tk::launch_dots<T, T>(sc->st, n, V, ld, k + 1, w, sc->part, nb, sc->dred + 64);
+            tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred + 64);
+            tk::launch_sumsq<T>(sc->st, n, w, sc->part, nb, sc->dred + 128);
+            sc->launches += 10;
+            ss.iters++;
+            total++;
+            CK(cudaMemcpyAsync(sc->hred, sc->dred, 129 * sizeof(double), cudaMemcpyDeviceToHost, sc->st), "d2h");
+            CK(cudaStreamSynchronize(sc->st), "sync");
+            for (int i = 0; i <= k; ++i) H[(size_t)i * m + k] = sc->hred[i] + sc->hred[64 + i];
+            double hn = std::sqrt(std::max(0.0, sc->hred[128]));
+            H[(size_t)(k + 1) * m + k] = hn;
+            if (hn > 0.0) {
+                tk::launch_scale<T>(sc->st, n, w, 1.0 / hn, vn);
+                sc->launches++;
+            }
+            for (int i = 0; i < k; ++i) {
+                double a = H[(size_t)i * m + k], c = H[(size_t)(i + 1) * m + k];
+                H[(size_t)i * m + k] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + k] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)k * m + k], c = H[(size_t)(k + 1) * m + k];
+            double den = std::sqrt(a * a + c * c);
+            cs[k] = den > 0 ? a / den : 1.0;
+            sn[k] = den > 0 ? c / den : 0.0;
+            H[(size_t)k * m + k] = den;
+            H[(size_t)(k + 1) * m + k] = 0.0;
+            gv[k + 1] = -sn[k] * gv[k];
+            gv[k] = cs[k] * gv[k];
+            if (std::fabs(gv[k + 1]) <= tol * bn || hn == 0.0 || total >= maxit) {
+                ++k;
+                done = true;
+                break;
+            }
+        }
+        if (k > m) k = m;
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = gv[i];
+            for (int j = i + 1; j < k; ++j) acc -= H[(size_t)i * m + j] * y[j];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? acc / H[(size_t)i * m + i] : 0.0;
+        }
+        CK(cudaMemcpyAsync(sc->dred + 192, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, sc->st), "h2d");
+        tk::launch_combine<T>(sc->st, n, d, V, ld, k, sc->dred + 192);
+        sc->launches++;
+        // true residual r = b - (I - K) d
+        tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, d, w);
+        tk::launch_axpby<T>(sc->st, n, 1.0, b, -1.0, w, r);
+        tk::launch_sumsq<T>(sc->st, n, r, sc->part, nb, sc->dred);
+        sc->launches += 4;
+        ss.iters++;
+        rs = read_red<T>(sc, 1);
+        if (rs) return rs;
+        double nb_ = std::sqrt(sc->hred[0]);
+        if (nb_ <= tol * bn * 1.0000001 || total >= maxit || nb_ == 0.0) break;
+        if (!(nb_ < 0.5 * beta)) break;  // the cycle stagnated (rounding floor)
+        beta = nb_;
+        rc = r;
+        (void)done;
+    }
+    return TURSCA_OK;
+}
+
+template <typename T>
+tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+    const tk::GridC g = grid_c(sc);
+    const tk::GraphP gp = graph_p(sc);
+    const int n = g.n_nodes;
+    const int nbr = tk::resid_blocks(g);
+    const int nb = tk::dot_blocks(n);
+    SolveState ss;
+    const bool fp64 = sc->d.precision == TURSCA_FP64;
+    if (solver == TURSCA_SOLVER_AUTO) solver = fp64 ? TURSCA_SOLVER_GMRES : 0;
+    if (solver == TURSCA_SOLVER_GMRES || solver == 0) {
+        int m = fp64 ? 40 : 30;
+        if (!sc->V || sc->gm_m != m) {
+            T *V;
+            CK(dalloc(sc->allocs, V, (size_t)(m + 1) * n * sizeof(T)), "alloc gmres basis");
+            sc->V = V;
+            sc->gm_m = m;
+        }
+    }
+    // x = 0, r = s, ||s||
+    CK(cudaMemsetAsync(sc->x64, 0, (size_t)n * sizeof(double), sc->st), "memset x");
+    tk::launch_convert<T, double>(sc->st, n, (const T *)sc->s, sc->r64);
+    tk::launch_sumsq<double>(sc->st, n, sc->r64, sc->part, nb, sc->dred);
+    sc->launches += 3;
+    tursca_status rs = read_red<T>(sc, 1);
+    if (rs) return rs;
+    const double sn = std::sqrt(sc->hred[0]);
+    double rel = sn > 0 ? 1.0 : 0.0;
+    double prev_rel = 1.0;
+    int used_inner = 0;  // inner sweeps of the last Neumann step
+    int mode = solver;   // 0: adaptive (Neumann first), 1: Neumann, 2: GMRES
+    int inner_n = 8;
+    while (rel > rtol) {
+        if (ss.iters >= max_iter) break;
+        int budget = max_iter - ss.iters;
+        // b = r in the compute type
+        T *bb = (T *)sc->b;
+        tk::launch_convert<double, T>(sc->st, n, sc->r64, bb);
+        sc->launches++;
+        const T *dd = nullptr;
+        bool use_gmres = (mode == TURSCA_SOLVER_GMRES) || (mode == 0 && ss.rho > 0.85);
+        if (use_gmres) {
+            double tol = fp64 ? std::max(0.3 * rtol / rel, 1e-15) : std::max(0.3 * rtol / rel, 2e-6);
+            tursca_status e = gmres<T>(sc, g, gp, bb, (T *)sc->d0, tol, budget, ss);
+            if (e) return e;
+            dd = (const T *)sc->d0;
+            ss.solver = TURSCA_SOLVER_GMRES;
+            used_inner = 0;
+        } else {
+            int nn = std::min(inner_n, std::max(1, budget));
+            dd = neumann<T>(sc, g, gp, bb, nn, ss);
+            used_inner = nn;
+            ss.solver = TURSCA_SOLVER_NEUMANN;
+        }
+        tk::launch_axpy_to64<T>(sc->st, n, dd, sc->x64);
+        int pr = prof_begin(sc, P_RESID);
+        tk::launch_resid64<T>(sc->st, g, gp, (const T *)sc->val, (const T *)sc->s, sc->x64, sc->r64, sc->part, nbr);
+        prof_end(sc, pr);
+        tk::launch_finalize(sc->st, sc->part, nbr, sc->dred);
+        sc->launches += 3;
+        ss.refinements++;
+        ss.iters++;
+        rs = read_red<T>(sc, 1);
+        if (rs) return rs;
+        prev_rel = rel;
+        rel = sn > 0 ? std::sqrt(sc->hred[0]) / sn : 0.0;
+        if (used_inner > 0 && prev_rel > 0 && rel > 0) {
+            double f = rel / prev_rel;
+            // the inner Neumann error after n sweeps is rho^(n+1)
+            double rho = std::pow(std::min(f, 0.999999), 1.0 / (used_inner + 1));
+            if (ss.refinements == 1 || f > 1e-6) ss.rho = rho;
+            double target = fp64 ? std::max(rtol / rel * 0.3, 1e-15) : std::max(rtol / rel * 0.3, 1e-6);
+            int want = (int)std::ceil(std::log(target) / std::log(std::max(ss.rho, 1e-3))) - 1;
+            inner_n = std::max(2, std::min(want, 400));
+        }
+        if (!(rel <= prev_rel * 1.5) && ss.refinements > 3) break;  // stagnation
+    }
+    if (info) {
+        info->iters = ss.iters;
+        info->refinements = ss.refinements;
+        info->rel_resid64 = rel;
+        info->rho_est = ss.rho;
+        info->solver = ss.solver;
+    }
+    sc->solved = true;
+    if (rel > rtol) return fail(sc, TURSCA_E_NOT_CONVERGED, "solver stopped above rtol");
+    return TURSCA_OK;
+}
+
+template <typename T>
+tursca_status do_render(tursca_scene *sc, void *radiance, void *reflectance) {
+    const tk::GridC g = grid_c(sc);
+    const tk::GraphP gp = graph_p(sc);
+    tk::FieldP<T> f = field_p<T>(sc);
+    tk::ViewC vc = view_c(sc);
+    tk::ViewP vp = view_p(sc);
+    int pi = prof_begin(sc, P_RENDER);
+    tk::launch_emission<T>(sc->st, g, gp, f, vc, sc->x64, (T *)sc->emis);
+    tk::launch_pixels<T>(sc->st, g, f, vc, vp, (const T *)sc->emis, sc->x64, (T *)sc->rad, (T *)sc->refl);
+    prof_end(sc, pi);
+    sc->launches += 2;
+    size_t np = (size_t)sc->geom.npx * sc->geom.npy;
+    CK(cudaGetLastError(), "render launch");
+    if (radiance) CK(cudaMemcpyAsync(radiance, sc->rad, np * sizeof(T), cudaMemcpyDefault, sc->st), "copy radiance");
+    if (reflectance)
+        CK(cudaMemcpyAsync(reflectance, sc->refl, np * sizeof(T), cudaMemcpyDefault, sc->st), "copy reflectance");
+    return sync_check(sc, "render");
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+tursca_status tursca_scene_create(const tursca_grid_desc *desc, void *cuda_stream, tursca_scene **out) {
+    if (!out) return fail(nullptr, TURSCA_E_INVALID, "out is null");
+    *out = nullptr;
+    std::string m = check_desc(desc);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    tursca_scene *sc = new (std::nothrow) tursca_scene();
+    if (!sc) return fail(nullptr, TURSCA_E_NOMEM, "host allocation failed");
+    sc->d = *desc;
+    sc->st = (cudaStream_t)cuda_stream;
+    sc->es = desc->precision == TURSCA_FP64 ? 8 : 4;
+    *out = sc;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_scene_destroy(tursca_scene *sc) {
+    if (!sc) return TURSCA_OK;
+    cudaStreamSynchronize(sc->st);
+    free_list(sc->allocs);
+    free_list(sc->view_allocs);
+    if (sc->hred) cudaFreeHost(sc->hred);
+    for (cudaEvent_t e : sc->ev) cudaEventDestroy(e);
+    delete sc;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_set_medium(tursca_scene *sc, const void *mu_abs, const void *mu_sca, const double *g,
+                                double albedo) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!mu_abs || !mu_sca || !g) return fail(sc, TURSCA_E_INVALID, "null field pointer");
+    for (int s = 0; s < sc->d.n_species; ++s)
+        if (!(std::fabs(g[s]) < 1.0)) return fail(sc, TURSCA_E_INVALID, "HG asymmetry must satisfy |g| < 1");
+    if (!(albedo >= 0.0 && albedo <= 1.0)) return fail(sc, TURSCA_E_INVALID, "albedo must be in [0, 1]");
+    tursca_status e = ensure_fields(sc);
+    if (e) return e;
+    const size_t na = (size_t)sc->d.nx * sc->d.ny * sc->d.nz;
+    CK(cudaMemcpyAsync(sc->mu_a, mu_abs, na * sc->es, cudaMemcpyDefault, sc->st), "copy mu_abs");
+    CK(cudaMemcpyAsync(sc->mu_s, mu_sca, na * sc->es * sc->d.n_species, cudaMemcpyDefault, sc->st), "copy mu_sca");
+    CK(cudaMemsetAsync(sc->status, 0, sizeof(int), sc->st), "memset status");
+    for (int s = 0; s < tk::MAX_SPECIES; ++s) sc->g[s] = s < sc->d.n_species ? g[s] : 0.0;
+    sc->albedo = albedo;
+    sc->medium = true;
+    sc->assembled = sc->solved = false;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_build_graph(tursca_scene *sc) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (sc->built) return TURSCA_OK;
+    const tursca_grid_desc &d = sc->d;
+    std::string m = tg::build_graph(sc->G, d.nx, d.ny, d.nz, d.hx, d.hy, d.hz, d.stencil_radius, d.fib_points);
+    if (!m.empty()) return fail(sc, TURSCA_E_INVALID, m);
+    tursca_status e = ensure_fields(sc);
+    if (e) return e;
+    tg::Graph &G = sc->G;
+    // classes
+    std::vector<tk::DClass> dc(G.classes.size());
+    for (size_t i = 0; i < G.classes.size(); ++i) {
+        const tg::SlotClass &c = G.classes[i];
+        tk::DClass &o = dc[i];
+        std::memset(&o, 0, sizeof(o));
+        o.kind = (int16_t)c.kind;
+        o.dir = (int16_t)std::max(c.dir, 0);
+        o.hgdir = (int16_t)c.hgdir;
+        o.k = (int16_t)c.k;
+        o.bkind = (int16_t)c.bkind;
+        o.up_idx = (int16_t)std::max(c.up_idx, 0);
+        o.gdir = (int16_t)std::max(c.gdir, 0);
+        o.c_one = (int16_t)c.c_one;
+        o.pre_off = c.pre_off;
+        o.seg_off = c.seg_off;
+        o.hit_off = c.hit_off;
+        o.pre_n = (int16_t)c.pre_n;
+        o.seg_n = (int16_t)c.seg_n;
+        o.hit_n = (int16_t)c.hit_n;
+        o.n1_ground = (int16_t)c.n1_ground;
+        o.n1_dx = (int16_t)c.n1_dx;
+        o.n1_dy = (int16_t)c.n1_dy;
+        o.n1_dz = (int16_t)c.n1_dz;
+        o.dist1_inv = c.dist1 > 0 ? 1.0 / c.dist1 : 0.0;
+        o.split = c.split;
+    }
+    CK(upload(sc, sc->allocs, sc->cls, dc.data(), dc.size() * sizeof(tk::DClass)), "upload classes");
+    std::vector<tk::DTap> to;
+    std::vector<float> lf;
+    std::vector<double> ld;
+    split_taps(G.taps, to, lf, ld);
+    CK(upload(sc, sc->allocs, sc->taps, to.data(), to.size() * sizeof(tk::DTap)), "upload taps");
+    CK(upload(sc, sc->allocs, sc->tlf, lf.data(), lf.size() * sizeof(float)), "upload taps");
+    CK(upload(sc, sc->allocs, sc->tld, ld.data(), ld.size() * sizeof(double)), "upload taps");
+    const int nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size();
+    std::vector<int4> dirs(nd);
+    for (int u = 0; u < nd; ++u) dirs[u] = make_int4(G.dirs[u][0], G.dirs[u][1], G.dirs[u][2], G.kmax[u]);
+    CK(upload(sc, sc->allocs, sc->dirs, dirs.data(), nd * sizeof(int4)), "upload dirs");
+    CK(upload(sc, sc->allocs, sc->dir_len, G.len.data(), nd * sizeof(double)), "upload len");
+    CK(upload(sc, sc->allocs, sc->q_iso, G.q_iso.data(), nd * sizeof(double)), "upload q");
+    CK(upload(sc, sc->allocs, sc->q_lamb, G.q_lamb.data(), ngd * sizeof(double)), "upload q");
+    std::vector<int4> gm(ngd);
+    std::vector<double> gd1(ngd);
+    for (int k = 0; k < ngd; ++k) {
+        const auto &m0 = G.gdirs[k].mem[0];
+        gm[k] = make_int4(m0[0], m0[1], m0[2], 0);
+        double a = m0[0] * G.hx, b = m0[1] * G.hy, c = (m0[2] - 0.5) * G.hz;
+        gd1[k] = std::sqrt(a * a + b * b + c * c);
+    }
+    CK(upload(sc, sc->allocs, sc->gmem1, gm.data(), ngd * sizeof(int4)), "upload gmem");
+    CK(upload(sc, sc->allocs, sc->gdist1, gd1.data(), ngd * sizeof(double)), "upload gdist");
+    CK(upload(sc, sc->allocs, sc->up_dirs, G.up_dirs.data(), G.up_dirs.size() * sizeof(int)), "upload up");
+    CK(upload(sc, sc->allocs, sc->top_off, G.top_off.data(), G.top_off.size() * sizeof(int)), "upload top");
+    CK(upload(sc, sc->allocs, sc->top_n, G.top_n.data(), G.top_n.size() * sizeof(int)), "upload top");
+    CK(upload(sc, sc->allocs, sc->lat_off, G.lat_off.data(), nd * sizeof(int)), "upload lat");
+    CK(upload(sc, sc->allocs, sc->lat_n, G.lat_n.data(), nd * sizeof(int)), "upload lat");
+    CK(upload(sc, sc->allocs, sc->gtop_off, G.gtop_off.data(), ngd * sizeof(int)), "upload gtop");
+    CK(upload(sc, sc->allocs, sc->gtop_n, G.gtop_n.data(), ngd * sizeof(int)), "upload gtop");
+    std::vector<double> lat((size_t)3 * G.M);
+    for (int i = 0; i < G.M; ++i)
+        for (int a = 0; a < 3; ++a) lat[(size_t)3 * i + a] = G.lattice[G.cell_order[i]][a];
+    CK(upload(sc, sc->allocs, sc->lattice, lat.data(), lat.size() * sizeof(double)), "upload lattice");
+    CK(upload(sc, sc->allocs, sc->cell_start, G.cell_start.data(), G.cell_start.size() * sizeof(int)), "upload cells");
+    std::vector<double> dh((size_t)3 * (nd + ngd));
+    for (int u = 0; u < nd; ++u)
+        for (int a = 0; a < 3; ++a) dh[3 * u + a] = G.uhat[u][a];
+    for (int k = 0; k < ngd; ++k)
+        for (int a = 0; a < 3; ++a) dh[3 * (nd + k) + a] = G.gdirs[k].uhat[a];
+    CK(upload(sc, sc->allocs, sc->dirhat, dh.data(), dh.size() * sizeof(double)), "upload dirhat");
+    // CSR structure from the templates
+    std::vector<int4> tm(G.tmpl.size());
+    for (size_t i = 0; i < G.tmpl.size(); ++i)
+        tm[i] = make_int4(G.tmpl[i].cls, G.tmpl[i].sdx, G.tmpl[i].sdy, G.tmpl[i].sz);
+    int *tstart, *tlen;
+    int4 *tmd;
+    std::vector<void *> tmp;
+    CK(upload(sc, tmp, tstart, G.tmpl_start.data(), G.tmpl_start.size() * sizeof(int)), "upload tmpl");
+    CK(upload(sc, tmp, tlen, G.tmpl_len.data(), G.tmpl_len.size() * sizeof(int)), "upload tmpl");
+    CK(upload(sc, tmp, tmd, tm.data(), tm.size() * sizeof(int4)), "upload tmpl");
+    const size_t nn = (size_t)G.n_nodes;
+    CK(dalloc(sc->allocs, sc->row_ptr, (nn + 1) * sizeof(int32_t)), "alloc row_ptr");
+    CK(dalloc(sc->allocs, sc->col, (size_t)G.nnz * sizeof(int32_t)), "alloc col");
+    CK(dalloc(sc->allocs, sc->code, (size_t)G.nnz * sizeof(uint16_t)), "alloc code");
+    CK(dalloc(sc->allocs, sc->val, (size_t)G.nnz * sc->es), "alloc val");
+    const size_t es = sc->es;
+    CK(dalloc(sc->allocs, sc->tinf, (size_t)G.up_dirs.size() * G.n_atm * es), "alloc tinf");
+    CK(dalloc(sc->allocs, sc->tinfg, (size_t)ngd * G.n_ground * es), "alloc tinfg");
+    CK(dalloc(sc->allocs, sc->q_sun, (size_t)sc->d.n_species * nd * es), "alloc qsun");
+    CK(dalloc(sc->allocs, sc->hgv, (size_t)sc->d.n_species * (nd + ngd) * es), "alloc hgv");
+    CK(dalloc(sc->allocs, sc->hg0v, (size_t)sc->d.n_species * es), "alloc hg0v");
+    tk::GridC gc = grid_c(sc);
+    tk::launch_expand(sc->st, gc, tstart, tmd, tlen, sc->row_ptr, sc->col, sc->code);
+    sc->launches++;
+    cudaError_t ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(sc->st);
+    free_list(tmp);
+    if (ce != cudaSuccess) return cuda_fail(sc, ce, "build_graph");
+    sc->built = true;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!geom) return fail(sc, TURSCA_E_INVALID, "geometry is null");
+    if (!sc->built) return fail(sc, TURSCA_E_STATE, "build_graph has not been called");
+    if (!sc->medium) return fail(sc, TURSCA_E_STATE, "set_medium has not been called");
+    if (!(geom->f0 > 0.0) || !std::isfinite(geom->f0)) return fail(sc, TURSCA_E_INVALID, "f0 must be positive");
+    bool same = sc->view_ok && geom->sza == sc->geom.sza && geom->saa == sc->geom.saa && geom->vza == sc->geom.vza &&
+                geom->vaa == sc->geom.vaa && geom->npx == sc->geom.npx && geom->npy == sc->geom.npy;
+    if (!same) {
+        tg::ViewTables VT;
+        std::string m = tg::build_view(sc->G, VT, geom->sza, geom->saa, geom->vza, geom->vaa, geom->npx, geom->npy);
+        if (!m.empty()) return fail(sc, TURSCA_E_INVALID, m);
+        for (const auto &t : VT.sun_taps)
+            if (std::abs(t.dx) > 32000 || std::abs(t.dy) > 32000) return fail(sc, TURSCA_E_INVALID, "ray too oblique");
+        for (const auto &t : VT.los_taps)
+            if (std::abs(t.dx) > 32000 || std::abs(t.dy) > 32000) return fail(sc, TURSCA_E_INVALID, "ray too oblique");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        free_list(sc->view_allocs);
+        sc->VT = VT;
+        std::vector<tk::DTap> to;
+        std::vector<float> lf;
+        std::vector<double> ld;
+        split_taps(VT.sun_taps, to, lf, ld);
+        CK(upload(sc, sc->view_allocs, sc->sun_taps, to.data(), to.size() * sizeof(tk::DTap)), "upload sun");
+        CK(upload(sc, sc->view_allocs, sc->sun_lf, lf.data(), lf.size() * sizeof(float)), "upload sun");
+        CK(upload(sc, sc->view_allocs, sc->sun_ld, ld.data(), ld.size() * sizeof(double)), "upload sun");
+        CK(upload(sc, sc->view_allocs, sc->sun_off, VT.sun_off.data(), VT.sun_off.size() * sizeof(int)), "upload sun");
+        CK(upload(sc, sc->view_allocs, sc->sun_n, VT.sun_n.data(), VT.sun_n.size() * sizeof(int)), "upload sun");
+        split_taps(VT.los_taps, to, lf, ld);
+        CK(upload(sc, sc->view_allocs, sc->los_taps, to.data(), to.size() * sizeof(tk::DTap)), "upload los");
+        CK(upload(sc, sc->view_allocs, sc->los_lf, lf.data(), lf.size() * sizeof(float)), "upload los");
+        CK(upload(sc, sc->view_allocs, sc->los_ld, ld.data(), ld.size() * sizeof(double)), "upload los");
+        CK(upload(sc, sc->view_allocs, sc->los_off, VT.los_off.data(), VT.los_off.size() * sizeof(int)), "upload los");
+        CK(upload(sc, sc->view_allocs, sc->los_n, VT.los_n.data(), VT.los_n.size() * sizeof(int)), "upload los");
+        CK(upload(sc, sc->view_allocs, sc->pix_cx, VT.pix_cx.data(), VT.pix_cx.size() * sizeof(int)), "upload pix");
+        CK(upload(sc, sc->view_allocs, sc->pix_cy, VT.pix_cy.data(), VT.pix_cy.size() * sizeof(int)), "upload pix");
+        CK(upload(sc, sc->view_allocs, sc->pix_cls, VT.pix_cls.data(), VT.pix_cls.size() * sizeof(int)), "upload pix");
+        size_t np = (size_t)geom->npx * geom->npy;
+        CK(dalloc(sc->view_allocs, sc->rad, np * sc->es), "alloc rad");
+        CK(dalloc(sc->view_allocs, sc->refl, np * sc->es), "alloc refl");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        sc->view_ok = true;
+    }
+    sc->geom = *geom;
+    const tk::GridC g = grid_c(sc);
+    const tk::GraphP gp = graph_p(sc);
+    const tk::ViewC vc = view_c(sc);
+    const tk::ViewP vp = view_p(sc);
+    int p0 = prof_begin(sc, P_PRE);
+    if (sc->d.precision == TURSCA_FP64)
+        tk::launch_assemble_pre<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, &sc->launches);
+    else
+        tk::launch_assemble_pre<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, &sc->launches);
+    prof_end(sc, p0);
+    int p1 = prof_begin(sc, P_ROWS);
+    if (sc->d.precision == TURSCA_FP64)
+        tk::launch_assemble_rows<double>(sc->st, g, gp, field_p<double>(sc), vc, &sc->launches);
+    else
+        tk::launch_assemble_rows<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
+    prof_end(sc, p1);
+    CK(cudaGetLastError(), "assemble launch");
+    sc->assembled = true;
+    sc->solved = false;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!sc->assembled) return fail(sc, TURSCA_E_STATE, "assemble_flux has not been called");
+    if (!(rtol > 0.0) || max_iter < 1) return fail(sc, TURSCA_E_INVALID, "rtol must be > 0 and max_iter >= 1");
+    if (solver < 0 || solver > 2) return fail(sc, TURSCA_E_INVALID, "unknown solver");
+    tursca_status e = sync_check(sc, "assemble");
+    if (e) return e;
+    if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info);
+    return do_solve<float>(sc, solver, rtol, max_iter, info);
+}
+
+tursca_status tursca_solve(tursca_scene *sc, double rtol, int max_iter, tursca_solve_info *info) {
+    return tursca_solve_with(sc, TURSCA_SOLVER_AUTO, rtol, max_iter, info);
+}
+
+tursca_status tursca_render_radiance(tursca_scene *sc, void *radiance, void *reflectance) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!sc->solved) return fail(sc, TURSCA_E_STATE, "solve has not been called");
+    if (sc->d.precision == TURSCA_FP64) return do_render<double>(sc, radiance, reflectance);
+    return do_render<float>(sc, radiance, reflectance);
+}
+
+tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) {
+    (void)dJ_dL;
+    (void)dJ_dmu_abs;
+    return fail(sc, TURSCA_E_UNSUPPORTED, "the adjoint is not available in this version");
+}
+
+tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t bytes) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!dst) return fail(sc, TURSCA_E_INVALID, "dst is null");
+    if (!sc->built) return fail(sc, TURSCA_E_STATE, "build_graph has not been called");
+    const tg::Graph &G = sc->G;
+    const size_t es = sc->es, nn = (size_t)G.n_nodes, na = (size_t)G.n_atm, nnz = (size_t)G.nnz;
+    const void *src = nullptr;
+    size_t need = 0;
+    bool host = false;
+    std::vector<int16_t> tmp16;
+    std::vector<int32_t> tmp32;
+    void *dtmp = nullptr;
+    switch (which) {
+        case TURSCA_F_ROW_PTR: src = sc->row_ptr; need = (nn + 1) * 4; break;
+        case TURSCA_F_COL: src = sc->col; need = nnz * 4; break;
+        case TURSCA_F_VAL: src = sc->val; need = nnz * es; break;
+        case TURSCA_F_SLOT_DIR:
+        case TURSCA_F_SLOT_K: {
+            need = which == TURSCA_F_SLOT_DIR ? nnz * 2 : nnz;
+            if (bytes != need) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
+            CK(cudaMalloc(&dtmp, nnz * 3), "alloc");
+            int16_t *dd = (int16_t *)dtmp;
+            int8_t *kk = (int8_t *)((char *)dtmp + nnz * 2);
+            tk::launch_slot_info(sc->st, (long long)nnz, sc->code, sc->cls, dd, kk, (int)G.dirs.size());
+            sc->launches++;
+            cudaError_t e = cudaMemcpyAsync(dst, which == TURSCA_F_SLOT_DIR ? (void *)dd : (void *)kk, need,
+                                            cudaMemcpyDefault, sc->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(sc->st);
+            cudaFree(dtmp);
+            if (e != cudaSuccess) return cuda_fail(sc, e, "get slot info");
+            return TURSCA_OK;
+        }
+        case TURSCA_F_TSUN: src = sc->tsun; need = nn * es; break;
+        case TURSCA_F_E1: src = sc->e1; need = nn * es; break;
+        case TURSCA_F_S: src = sc->s; need = nn * es; break;
+        case TURSCA_F_X: src = sc->x64; need = nn * 8; break;
+        case TURSCA_F_EMIS: src = sc->emis; need = na * es; break;
+        case TURSCA_F_GSUN: src = sc->gsun; need = na * es; break;
+        case TURSCA_F_Q_ISO: src = G.q_iso.data(); need = G.q_iso.size() * 8; host = true; break;
+        case TURSCA_F_Q_LAMB: src = G.q_lamb.data(); need = G.q_lamb.size() * 8; host = true; break;
+        case TURSCA_F_Q_SUN: src = sc->q_sun; need = (size_t)sc->d.n_species * G.dirs.size() * es; break;
+        case TURSCA_F_DIRS:
+            tmp32.resize(G.dirs.size() * 3);
+            for (size_t u = 0; u < G.dirs.size(); ++u)
+                for (int a = 0; a < 3; ++a) tmp32[3 * u + a] = G.dirs[u][a];
+            src = tmp32.data();
+            need = tmp32.size() * 4;
+            host = true;
+            break;
+        default: return fail(sc, TURSCA_E_INVALID, "unknown field");
+    }
+    if (bytes != need) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
+    if (host) {
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        CK(cudaMemcpy(dst, src, need, cudaMemcpyDefault), "get");
+        return TURSCA_OK;
+    }
+    CK(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, sc->st), "get");
+    return sync_check(sc, "get");
+}
+
+long long tursca_launch_count(const tursca_scene *sc) { return sc ? sc->launches : 0; }
+
+tursca_status tursca_profile_enable(tursca_scene *sc, int on) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    CK(cudaStreamSynchronize(sc->st), "sync");
+    sc->prof = on != 0;
+    sc->ev_used = 0;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int n, int *n_out) {
+    if (!sc || !out || n < 0) return fail(sc, TURSCA_E_INVALID, "bad arguments");
+    CK(cudaStreamSynchronize(sc->st), "sync");
+    double ms[kNProf] = {0, 0, 0, 0, 0};
+    long long cnt[kNProf] = {0, 0, 0, 0, 0};
+    for (size_t i = 0; i < sc->ev_used; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, sc->ev[2 * i], sc->ev[2 * i + 1]), "event time");
+        ms[sc->ev_cat[i]] += t;
+        cnt[sc->ev_cat[i]]++;
+    }
+    sc->ev_used = 0;
+    int m = std::min(n, kNProf);
+    for (int c = 0; c < m; ++c) {
+        std::snprintf(out[c].name, sizeof(out[c].name), "%s", kProfNames[c]);
+        out[c].launches = cnt[c];
+        out[c].total_ms = ms[c];
+    }
+    if (n_out) *n_out = m;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_graph_info(const tursca_grid_desc *desc, tursca_graph_stats *out) {
+    if (!out) return fail(nullptr, TURSCA_E_INVALID, "out is null");
+    std::string m = check_desc(desc);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    tg::Graph G;
+    m = tg::build_graph(G, desc->nx, desc->ny, desc->nz, desc->hx, desc->hy, desc->hz, desc->stencil_radius,
+                        desc->fib_points);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    out->n_atm = G.n_atm;
+    out->n_ground = G.n_ground;
+    out->n_nodes = G.n_nodes;
+    out->n_dirs = (int)G.dirs.size();
+    out->n_up_dirs = (int)G.up_dirs.size();
+    out->n_gdirs = (int)G.gdirs.size();
+    out->n_gmembers = G.n_gmembers;
+    out->nnz = G.nnz;
+    out->nnz_edges = G.nnz_edges;
+    out->n_classes = (int)G.classes.size();
+    out->max_row = G.max_row;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_graph_structure(const tursca_grid_desc *desc, int32_t *row_ptr, int32_t *col, int16_t *dir,
+                                     int8_t *k) {
+    std::string m = check_desc(desc);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    tg::Graph G;
+    m = tg::build_graph(G, desc->nx, desc->ny, desc->nz, desc->hx, desc->hy, desc->hz, desc->stencil_radius,
+                        desc->fib_points);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    tg::expand_csr(G, row_ptr, col, dir, k);
+    return TURSCA_OK;
+}
+
+tursca_status tursca_quadrature(const tursca_grid_desc *desc, double *q_iso, double *q_lamb) {
+    std::string m = check_desc(desc);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    tg::Graph G;
+    m = tg::build_graph(G, desc->nx, desc->ny, desc->nz, desc->hx, desc->hy, desc->hz, desc->stencil_radius,
+                        desc->fib_points);
+    if (!m.empty()) return fail(nullptr, TURSCA_E_INVALID, m);
+    if (q_iso) std::memcpy(q_iso, G.q_iso.data(), G.q_iso.size() * sizeof(double));
+    if (q_lamb) std::memcpy(q_lamb, G.q_lamb.data(), G.q_lamb.size() * sizeof(double));
+    return TURSCA_OK;
+}
+
+const char *tursca_status_string(tursca_status s) {
+    switch (s) {
+        case TURSCA_OK: return "ok";
+        case TURSCA_E_INVALID: return "invalid argument";
+        case TURSCA_E_NOMEM: return "out of memory";
+        case TURSCA_E_CUDA: return "CUDA error";
+        case TURSCA_E_NOT_CONVERGED: return "solver did not converge";
+        case TURSCA_E_TIMEOUT: return "device wait timed out";
+        case TURSCA_E_STATE: return "call out of order";
+        case TURSCA_E_UNSUPPORTED: return "not available";
+    }
+    return "unknown status";
+}
+
+tursca_status tursca_last_error(const tursca_scene *sc, char *buf, size_t n) {
+    if (!buf || n == 0) return TURSCA_E_INVALID;
+    const std::string &m = sc ? sc->err : g_last_error;
+    std::snprintf(buf, n, "%s", m.c_str());
+    return TURSCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,141 @@
+// Host-side graph description of the voxel scattering graph: direction sets,
+// Fibonacci-lattice partition, tap tables of every edge segment, and the
+// per-layer row templates from which the CSR structure of K is expanded.
+//
+// Everything here depends only on the grid (shape, spacing, stencil radius,
+// lattice size) or on the illumination / viewing geometry, never on the
+// optical fields, so it is built once and cached.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace tg {
+
+// Slot kinds: what kind of graph edge a stored entry of K is.
+enum SlotKind : int {
+    SK_CHAIN = 0,  // atmospheric source j deposits on chain node j + k u
+    SK_SELF = 1,   // atmospheric source deposits on itself (chain left the domain before p1)
+    SK_GROUND = 2, // atmospheric source's chain hits the ground: deposit on a ground column
+    SK_GCHAIN = 3, // ground source deposits on a voxel of its chain
+    SK_PAD = 4     // row padding (value 0)
+};
+
+// What lies beyond a terminal chain node.
+enum BeyondKind : int {
+    B_NONE = 0,  // not terminal
+    B_ALL = 1,   // terminal, nothing beyond (horizontal or downward, stencil ended)
+    B_TINF = 2,  // terminal, upward: optical depth to the TOA from the receiver (table)
+    B_HIT = 3,   // terminal, the chain reaches the ground: optical depth to the hit point (taps)
+    B_TINFG = 4  // terminal node of a ground chain: optical depth to the TOA (table per ground source)
+};
+
+struct Tap {
+    int dx, dy, dz;  // cell offset relative to the segment's base cell
+    double len;      // physical length (km)
+};
+
+struct SlotClass {
+    int kind = 0, dir = 0, hgdir = 0, k = 0, bkind = B_NONE;
+    int pre_off = 0, pre_n = 0;  // taps of the chain segments before the receiver
+    int seg_off = 0, seg_n = 0;  // taps of the segment ending at the receiver
+    int hit_off = 0, hit_n = 0;  // taps from the last chain node to the ground hit
+    int n1_dx = 0, n1_dy = 0, n1_dz = 0, n1_ground = 0;  // first receiver of the chain
+    double dist1 = 0.0;          // distance to the first receiver (km)
+    double split = 1.0;          // share of a ground hit that falls on this column
+    int c_one = 0;               // direction has no receiver other than the source: coupling 1
+    int up_idx = -1;             // upward-direction index for B_TINF
+    int gdir = -1;               // ground direction index for ground sources
+};
+
+// One entry of a row template: the source of a slot relative to the receiver.
+struct TSlot {
+    int cls;
+    int sdx, sdy;  // source column offset (periodic)
+    int sz;        // absolute source layer, -1 for a ground source
+};
+
+struct GroundDir {
+    std::vector<std::array<int, 3>> mem;  // (dx, dy, dzc): voxel (c + dx, c + dy, dzc - 1)
+    std::array<double, 3> uhat;
+};
+
+struct Graph {
+    // grid
+    int nx = 0, ny = 0, nz = 0, R = 1, M = 0;
+    double hx = 0, hy = 0, hz = 0;
+    int n_atm = 0, n_ground = 0, n_nodes = 0;
+
+    // atmospheric directions (order: dz, dy, dx ascending from -R)
+    std::vector<std::array<int, 3>> dirs;
+    std::vector<int> kmax;
+    std::vector<std::array<double, 3>> uhat;
+    std::vector<double> len;
+    std::vector<int> up_of_dir;  // -1 if not upward
+    std::vector<int> up_dirs;    // atmospheric index of each upward direction
+
+    // ground directions (collinear members form one chain)
+    std::vector<GroundDir> gdirs;
+    int n_gmembers = 0;
+
+    // Fibonacci partition
+    std::vector<std::array<double, 3>> lattice;  // M unit vectors
+    std::vector<int> cell;                       // atmospheric cell of each lattice point
+    std::vector<int> cell_order, cell_start;     // lattice points sorted by cell
+    std::vector<double> q_iso, q_lamb;
+
+    // taps and classes
+    std::vector<Tap> taps;
+    std::vector<SlotClass> classes;
+    int pad_class = -1;
+
+    // tau_inf sweep: partial taps from the centre of a top layer to the TOA,
+    // per upward direction and start layer offset o (layer nz - 1 - o)
+    std::vector<int> top_off, top_n;  // [n_up * R]
+    // lattice taps of each direction (segment from a centre to the next)
+    std::vector<int> lat_off, lat_n;  // [n_dirs]
+    // ground chains: taps from the terminal member to the TOA, per ground direction
+    std::vector<int> gtop_off, gtop_n;
+
+    // row templates: layers 0..nz-1, then the ground (index nz)
+    std::vector<int> tmpl_start;  // [nz + 2]
+    std::vector<TSlot> tmpl;
+    std::vector<int> tmpl_len;    // padded row length per template
+    long long nnz = 0, nnz_edges = 0;
+    int max_row = 0;
+};
+
+// Build the grid-only part.  Returns an empty string on success, else a message.
+std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, double hz, int R, int M);
+
+// Expand the templates into a CSR structure on the host.
+void expand_csr(const Graph &G, int32_t *row_ptr, int32_t *col, int16_t *dir, int8_t *k);
+
+// Illumination / viewing geometry tables.
+struct ViewTables {
+    // sun: tables per start height Zs = 0..nz (0: ground point, z + 1: top face of layer z)
+    std::vector<int> sun_off, sun_n;
+    std::vector<Tap> sun_taps;
+    // line of sight: per pixel class, taps from the TOA down to the ground point,
+    // relative to the pixel's ground column; per pixel (cx, cy, class)
+    std::vector<int> los_off, los_n;
+    std::vector<Tap> los_taps;
+    std::vector<int> pix_cx, pix_cy, pix_cls;
+    std::array<double, 3> s0, v;  // sun propagation direction, direction to the instrument
+    double mu0 = 1.0;
+};
+
+std::string build_view(const Graph &G, ViewTables &V, double sza, double saa, double vza, double vaa, int npx,
+                       int npy);
+
+// Straight-path traversal: pieces of P + t V, t in [0, tend], by cell; cells are
+// absolute (unwrapped) cell coordinates minus (bx, by, bz).  The path must stay
+// within layers [0, nz): a piece outside them is dropped if it is a rounding
+// sliver at an end point (length below 1e-9 of the path) and is an error
+// otherwise (returns false).
+bool trace(const double P[3], const double V[3], double tend, double lphys, int bx, int by, int bz, int nz,
+           std::vector<Tap> &out);
+
+}  // namespace tg

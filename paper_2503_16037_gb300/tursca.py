@@ -1,0 +1,313 @@
+"""Python binding of libtursca_gb (C ABI in include/tursca.h).
+
+The functions below carry the C names and only marshal arguments; every step
+of the path runs in the library's CUDA kernels.  There is no fallback: if the
+shared library is missing or fails to load, every call raises.
+
+``Runner`` strings the stages together for one scene on torch device memory
+and the current torch CUDA stream (torch supplies memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtursca_gb.so")
+
+FP64, FP32_REFINE = 0, 1
+COUPLING_NONE, COUPLING_WEIGHT = 0, 1
+SOLVER_AUTO, SOLVER_NEUMANN, SOLVER_GMRES = 0, 1, 2
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_STATE, E_UNSUPPORTED = range(8)
+
+F_ROW_PTR, F_COL, F_VAL, F_SLOT_DIR, F_SLOT_K, F_TSUN, F_E1, F_S, F_X, F_EMIS, F_GSUN, F_Q_ISO, F_Q_LAMB, \
+    F_Q_SUN, F_DIRS = range(15)
+
+
+class TurscaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (status %d)" % (msg, status))
+        self.status = status
+
+
+class tursca_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double),
+                ("n_species", C.c_int), ("stencil_radius", C.c_int), ("fib_points", C.c_int),
+                ("coupling_mode", C.c_int), ("precision", C.c_int)]
+
+
+class tursca_geometry(C.Structure):
+    _fields_ = [("sza", C.c_double), ("saa", C.c_double), ("vza", C.c_double), ("vaa", C.c_double),
+                ("f0", C.c_double), ("npx", C.c_int), ("npy", C.c_int)]
+
+
+class tursca_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("rel_resid64", C.c_double),
+                ("rho_est", C.c_double), ("solver", C.c_int)]
+
+
+class tursca_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double)]
+
+
+class tursca_graph_stats(C.Structure):
+    _fields_ = [("n_atm", C.c_int), ("n_ground", C.c_int), ("n_nodes", C.c_int),
+                ("n_dirs", C.c_int), ("n_up_dirs", C.c_int), ("n_gdirs", C.c_int), ("n_gmembers", C.c_int),
+                ("nnz", C.c_longlong), ("nnz_edges", C.c_longlong), ("n_classes", C.c_int), ("max_row", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = C.c_void_p
+
+
+def lib() -> C.CDLL:
+    """Load libtursca_gb.so (built by ``build.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtursca_gb.so is not built (run paper_2503_16037_gb300.build.build())")
+        L = C.CDLL(LIB_PATH)
+        st = C.c_int
+        sig = {
+            "tursca_scene_create": (st, [C.POINTER(tursca_grid_desc), _vp, C.POINTER(_vp)]),
+            "tursca_scene_destroy": (st, [_vp]),
+            "tursca_set_medium": (st, [_vp, _vp, _vp, C.POINTER(C.c_double), C.c_double]),
+            "tursca_build_graph": (st, [_vp]),
+            "tursca_assemble_flux": (st, [_vp, C.POINTER(tursca_geometry)]),
+            "tursca_solve": (st, [_vp, C.c_double, C.c_int, C.POINTER(tursca_solve_info)]),
+            "tursca_solve_with": (st, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(tursca_solve_info)]),
+            "tursca_render_radiance": (st, [_vp, _vp, _vp]),
+            "tursca_adjoint": (st, [_vp, _vp, _vp]),
+            "tursca_get": (st, [_vp, C.c_int, _vp, C.c_size_t]),
+            "tursca_launch_count": (C.c_longlong, [_vp]),
+            "tursca_graph_info": (st, [C.POINTER(tursca_grid_desc), C.POINTER(tursca_graph_stats)]),
+            "tursca_graph_structure": (st, [C.POINTER(tursca_grid_desc), _vp, _vp, _vp, _vp]),
+            "tursca_quadrature": (st, [C.POINTER(tursca_grid_desc), _vp, _vp]),
+            "tursca_profile_enable": (st, [_vp, C.c_int]),
+            "tursca_profile_read": (st, [_vp, C.POINTER(tursca_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
+            "tursca_status_string": (C.c_char_p, [C.c_int]),
+            "tursca_last_error": (st, [_vp, C.c_char_p, C.c_size_t]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def _err(scene, status: int):
+    buf = C.create_string_buffer(512)
+    lib().tursca_last_error(scene, buf, 512)
+    return TurscaError(status, buf.value.decode() or lib().tursca_status_string(status).decode())
+
+
+def _check(scene, status: int):
+    if status != OK:
+        raise _err(scene, status)
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a)
+
+
+# ---- same-name wrappers ----------------------------------------------------
+
+def tursca_scene_create(desc: tursca_grid_desc, cuda_stream: int = 0):
+    out = _vp()
+    _check(None, lib().tursca_scene_create(C.byref(desc), cuda_stream or None, C.byref(out)))
+    return out
+
+
+def tursca_scene_destroy(scene):
+    _check(None, lib().tursca_scene_destroy(scene))
+
+
+def tursca_set_medium(scene, mu_abs, mu_sca, g, albedo: float):
+    gg = (C.c_double * len(g))(*[float(v) for v in g])
+    _check(scene, lib().tursca_set_medium(scene, _ptr(mu_abs), _ptr(mu_sca), gg, float(albedo)))
+
+
+def tursca_build_graph(scene):
+    _check(scene, lib().tursca_build_graph(scene))
+
+
+def tursca_assemble_flux(scene, geom: tursca_geometry):
+    _check(scene, lib().tursca_assemble_flux(scene, C.byref(geom)))
+
+
+def tursca_solve(scene, rtol: float, max_iter: int) -> tursca_solve_info:
+    info = tursca_solve_info()
+    _check(scene, lib().tursca_solve(scene, float(rtol), int(max_iter), C.byref(info)))
+    return info
+
+
+def tursca_solve_with(scene, solver: int, rtol: float, max_iter: int) -> tursca_solve_info:
+    info = tursca_solve_info()
+    _check(scene, lib().tursca_solve_with(scene, int(solver), float(rtol), int(max_iter), C.byref(info)))
+    return info
+
+
+def tursca_render_radiance(scene, radiance, reflectance=None):
+    _check(scene, lib().tursca_render_radiance(scene, _ptr(radiance), _ptr(reflectance)))
+
+
+def tursca_adjoint(scene, dJ_dL, dJ_dmu_abs):
+    _check(scene, lib().tursca_adjoint(scene, _ptr(dJ_dL), _ptr(dJ_dmu_abs)))
+
+
+def tursca_get(scene, which: int, dst, nbytes: int):
+    _check(scene, lib().tursca_get(scene, int(which), _ptr(dst), int(nbytes)))
+
+
+def tursca_launch_count(scene) -> int:
+    return int(lib().tursca_launch_count(scene))
+
+
+def tursca_profile_enable(scene, on: bool):
+    _check(scene, lib().tursca_profile_enable(scene, 1 if on else 0))
+
+
+def tursca_profile_read(scene) -> dict:
+    arr = (tursca_kernel_stat * 8)()
+    n = C.c_int(0)
+    _check(scene, lib().tursca_profile_read(scene, arr, 8, C.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def tursca_graph_info(desc: tursca_grid_desc) -> tursca_graph_stats:
+    out = tursca_graph_stats()
+    _check(None, lib().tursca_graph_info(C.byref(desc), C.byref(out)))
+    return out
+
+
+def tursca_graph_structure(desc: tursca_grid_desc):
+    st = tursca_graph_info(desc)
+    row_ptr = np.zeros(st.n_nodes + 1, np.int32)
+    col = np.zeros(st.nnz, np.int32)
+    dr = np.zeros(st.nnz, np.int16)
+    k = np.zeros(st.nnz, np.int8)
+    _check(None, lib().tursca_graph_structure(C.byref(desc), row_ptr.ctypes.data, col.ctypes.data, dr.ctypes.data,
+                                              k.ctypes.data))
+    return row_ptr, col, dr, k
+
+
+def tursca_quadrature(desc: tursca_grid_desc):
+    st = tursca_graph_info(desc)
+    qi = np.zeros(st.n_dirs)
+    ql = np.zeros(st.n_gdirs)
+    _check(None, lib().tursca_quadrature(C.byref(desc), qi.ctypes.data, ql.ctypes.data))
+    return qi, ql
+
+
+def tursca_status_string(status: int) -> str:
+    return lib().tursca_status_string(int(status)).decode()
+
+
+# ---- helpers ----------------------------------------------------------------
+
+def grid_desc(sc, precision: Optional[int] = None) -> tursca_grid_desc:
+    """Descriptor for a ``scenes.Scene``."""
+    d = tursca_grid_desc()
+    d.nx, d.ny, d.nz = sc.nx, sc.ny, sc.nz
+    d.hx, d.hy, d.hz = sc.hx, sc.hy, sc.hz
+    d.n_species = sc.n_species
+    d.stencil_radius = sc.R
+    d.fib_points = sc.M
+    d.coupling_mode = sc.coupling
+    d.precision = sc.precision if precision is None else precision
+    return d
+
+
+def geometry(sc) -> tursca_geometry:
+    g = tursca_geometry()
+    g.sza, g.saa, g.vza, g.vaa, g.f0 = sc.sza, sc.saa, sc.vza, sc.vaa, sc.f0
+    g.npx, g.npy = sc.npx, sc.npy
+    return g
+
+
+class Runner:
+    """One scene on the current CUDA device and torch stream.
+
+    Fields are torch tensors (device or host); results are torch tensors on
+    the device.  ``run()`` executes set_medium -> assemble -> solve -> render.
+    """
+
+    def __init__(self, sc, precision: Optional[int] = None, stream=None):
+        import torch
+        self.torch = torch
+        self.sc = sc
+        self.desc = grid_desc(sc, precision)
+        self.dtype = torch.float64 if self.desc.precision == FP64 else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = tursca_scene_create(self.desc, self.stream.cuda_stream)
+        self.stats = tursca_graph_info(self.desc)
+        self.geom = geometry(sc)
+        tursca_build_graph(self.handle)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.rad = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)
+        self.refl = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)
+        self.info = None
+
+    def fields(self, device="cuda"):
+        t = self.torch
+        mu_a = t.as_tensor(np.ascontiguousarray(self.sc.mu_a), dtype=self.dtype).to(device)
+        mu_s = t.as_tensor(np.ascontiguousarray(self.sc.mu_s), dtype=self.dtype).to(device)
+        return mu_a.contiguous(), mu_s.contiguous()
+
+    def set_medium(self, mu_a, mu_s):
+        tursca_set_medium(self.handle, mu_a, mu_s, list(self.sc.g), self.sc.albedo)
+
+    def assemble(self):
+        tursca_assemble_flux(self.handle, self.geom)
+
+    def solve(self, rtol=1e-10, max_iter=5000, solver=SOLVER_AUTO):
+        self.info = tursca_solve_with(self.handle, solver, rtol, max_iter)
+        return self.info
+
+    def render(self, rad=None, refl=None):
+        rad = self.rad if rad is None else rad
+        refl = self.refl if refl is None else refl
+        tursca_render_radiance(self.handle, rad, refl)
+        return rad, refl
+
+    def run(self, mu_a, mu_s, rtol=1e-10, max_iter=5000, solver=SOLVER_AUTO):
+        self.set_medium(mu_a, mu_s)
+        self.assemble()
+        self.solve(rtol, max_iter, solver)
+        return self.render()
+
+    def get(self, which: int, n: int, dtype):
+        t = self.torch
+        out = t.empty(n, dtype=dtype)
+        tursca_get(self.handle, which, out.data_ptr(), out.numel() * out.element_size())
+        return out.numpy()
+
+    def launches(self) -> int:
+        return tursca_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            tursca_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
