@@ -223,6 +223,33 @@ tursca_status tursca_graph_structure(const tursca_grid_desc *desc, int32_t *row_
  * (cosine-weighted fraction of the upper hemisphere). */
 tursca_status tursca_quadrature(const tursca_grid_desc *desc, double *q_iso, double *q_lamb);
 
+/* Allocation-free solve of (I - K) x = s for callers that may not allocate
+ * device memory when they solve: programs whose device memory is owned by
+ * their own allocator and fixed at start-up, or latency-critical loops where
+ * cudaMalloc / cudaFree (which can synchronise the whole device) are not
+ * allowed.  The paper has no counterpart; it is a deployment variant of the
+ * refined solve that tursca_solve_with(..., TURSCA_SOLVER_NEUMANN, ...) runs.
+ *
+ * Computes, on cuda_stream, x = 0 then `refinements` times: sweeps of
+ * d <- r + K d starting from d = r (FP32), x += d, r = s - (I - K) x (FP64).
+ *   row_ptr [n_nodes + 1], col [nnz] (entries in [0, n_nodes)), val [nnz]:
+ *     K in CSR, rows = receivers, any layout (e.g. TURSCA_F_ROW_PTR,
+ *     TURSCA_F_COL, TURSCA_F_VAL of an FP32 scene); s [n_nodes] float;
+ *     x [n_nodes] double (output); resid2: optional device double receiving
+ *     ||r||^2 of the last refinement.  All are caller-owned device pointers.
+ *   1 <= n_nodes <= 1048576, 0 <= sweeps <= 100000, 1 <= refinements <= 1000;
+ *     larger sizes or null pointers return TURSCA_E_INVALID before any work.
+ * Its work vectors live in one fixed device array of about 12 MiB that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * each device looks up that array's address (with that device current); make
+ * that first call before any stream capture.  Every call shares the array and
+ * finds the previous call's contents in it, so calls whose work overlaps on
+ * the GPU (different streams, or different host threads) race with each other.
+ * The call allocates nothing and returns without synchronising. */
+tursca_status tursca_csr_solve_noalloc(const int32_t *row_ptr, const int32_t *col, const float *val, int n_nodes,
+                                       const float *s, double *x, int sweeps, int refinements, double *resid2,
+                                       void *cuda_stream);
+
 /* Static description of a status code. */
 const char *tursca_status_string(tursca_status status);
 

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtursca_gb.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "api.cu"]
+SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["graph.h", "kern.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
             "tursca_quadrature": (st, [C.POINTER(tursca_grid_desc), _vp, _vp]),
             "tursca_profile_enable": (st, [_vp, C.c_int]),
             "tursca_profile_read": (st, [_vp, C.POINTER(tursca_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
+            "tursca_csr_solve_noalloc": (st, [_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp]),
             "tursca_status_string": (C.c_char_p, [C.c_int]),
             "tursca_last_error": (st, [_vp, C.c_char_p, C.c_size_t]),
         }
@@ -213,6 +214,13 @@ def tursca_quadrature(desc: tursca_grid_desc):
     ql = np.zeros(st.n_gdirs)
     _check(None, lib().tursca_quadrature(C.byref(desc), qi.ctypes.data, ql.ctypes.data))
     return qi, ql
+
+
+def tursca_csr_solve_noalloc(row_ptr, col, val, n_nodes: int, s, x, sweeps: int, refinements: int, resid2=None,
+                             cuda_stream: int = 0):
+    """Allocation-free refined solve on caller device arrays (see tursca.h)."""
+    _check(None, lib().tursca_csr_solve_noalloc(_ptr(row_ptr), _ptr(col), _ptr(val), int(n_nodes), _ptr(s), _ptr(x),
+                                                int(sweeps), int(refinements), _ptr(resid2), cuda_stream or None))
 
 
 def tursca_status_string(status: int) -> str:
