@@ -62,7 +62,7 @@ typedef enum {
 
 enum { TURSCA_FP64 = 0, TURSCA_FP32_REFINE = 1 };
 enum { TURSCA_COUPLING_NONE = 0, TURSCA_COUPLING_WEIGHT = 1 };
-enum { TURSCA_SOLVER_AUTO = 0, TURSCA_SOLVER_NEUMANN = 1, TURSCA_SOLVER_GMRES = 2 };
+enum { TURSCA_SOLVER_AUTO = 0, TURSCA_SOLVER_NEUMANN = 1, TURSCA_SOLVER_GMRES = 2, TURSCA_SOLVER_CHEBYSHEV = 3 };
 
 /* Grid and method parameters (fixed for the life of a scene).
  *   nx, ny >= 2 R + 1 (x and y are periodic), nz >= R.
@@ -166,9 +166,13 @@ tursca_status tursca_build_graph(tursca_scene *scene);
 tursca_status tursca_assemble_flux(tursca_scene *scene, const tursca_geometry *geom);
 
 /* Solve (I - K) x = s (Eq. flux_system) to ||s - (I - K) x|| <= rtol ||s||
- * evaluated in FP64, with at most max_iter products with K.  FP32_REFINE
- * scenes run FP32 inner iterations and FP64 residual refinement; FP64 scenes
- * run FP64 GMRES.  Synchronises.  info may be NULL. */
+ * evaluated in FP64, with at most max_iter products with K.  The outer loop
+ * is FP64 residual refinement; each refinement solves for the correction
+ * with inner iterations in the scene's precision: FP32_REFINE scenes first run
+ * a few Neumann sweeps (the series of Eq. fs_sum) that also estimate the
+ * largest eigenvalue of K, then Chebyshev iterations on the interval that
+ * estimate implies (GMRES when it is within 0.01 of 1); FP64 scenes run
+ * GMRES.  Synchronises once per refinement.  info may be NULL. */
 tursca_status tursca_solve(tursca_scene *scene, double rtol, int max_iter, tursca_solve_info *info);
 
 /* Same as tursca_solve with an explicit solver choice (TURSCA_SOLVER_*). */
@@ -189,6 +193,14 @@ tursca_status tursca_adjoint(tursca_scene *scene, const void *dJ_dL, void *dJ_dm
 /* Copy an internal array out (device -> dst, host or device pointer) after the
  * stage that produces it; bytes must equal the array size.  Synchronises. */
 tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, size_t bytes);
+
+/* Scene options (tursca_set_option).
+ *   TURSCA_OPT_RESIDUAL_FP64: 0 (default) evaluates the refinement residual of
+ *     FP32_REFINE scenes in FP32-pair arithmetic (exact products by FMA and
+ *     compensated sums, about 48 significant bits; FP64 arithmetic runs at a
+ *     small fraction of the FP32 rate on GB300); 1 uses FP64 arithmetic. */
+enum { TURSCA_OPT_RESIDUAL_FP64 = 1 };
+tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 
 /* Number of kernel launches the scene has issued since creation. */
 long long tursca_launch_count(const tursca_scene *scene);

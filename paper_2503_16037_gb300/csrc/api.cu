@@ -37,18 +37,22 @@ struct tursca_scene {
     std::vector<void *> view_allocs; // geometry-lifetime allocations
 
     // graph
-    int32_t *row_ptr = nullptr, *col = nullptr;
-    uint16_t *code = nullptr;
+    int *tstart = nullptr;
+    int4 *tmpl = nullptr;
+    long long *voff = nullptr;
     tk::DClass *cls = nullptr;
+    tk::PClass *pcls = nullptr;
     tk::DTap *taps = nullptr;
     float *tlf = nullptr;
     double *tld = nullptr;
     int4 *dirs = nullptr, *gmem1 = nullptr;
     double *dir_len = nullptr, *q_iso = nullptr, *q_lamb = nullptr, *gdist1 = nullptr;
+    float *dir_len_f = nullptr, *q_iso_f = nullptr, *q_lamb_f = nullptr, *gdist1_f = nullptr;
     int *up_dirs = nullptr, *top_off = nullptr, *top_n = nullptr, *lat_off = nullptr, *lat_n = nullptr,
         *gtop_off = nullptr, *gtop_n = nullptr;
     double *lattice = nullptr, *dirhat = nullptr;
     int *cell_start = nullptr;
+    int *canon_dirs = nullptr, *up_canon = nullptr;
     // view
     tk::DTap *sun_taps = nullptr, *los_taps = nullptr;
     float *sun_lf = nullptr, *los_lf = nullptr;
@@ -58,15 +62,18 @@ struct tursca_scene {
     void *rad = nullptr, *refl = nullptr;
     // fields (compute type)
     void *mu_a = nullptr, *mu_s = nullptr, *mu_e = nullptr, *mu_st = nullptr, *tsun = nullptr, *e1 = nullptr,
-         *tinf = nullptr, *tinfg = nullptr, *zc_iso = nullptr, *zc_sun = nullptr, *q_sun = nullptr, *hgv = nullptr,
+         *tinf = nullptr, *tinfg = nullptr, *zc_iso = nullptr, *zc_sun = nullptr, *tseg = nullptr, *rt = nullptr, *wsp = nullptr, *q_sun = nullptr, *hgv = nullptr,
          *hg0v = nullptr, *val = nullptr, *s = nullptr, *gsun = nullptr, *emis = nullptr;
     unsigned long long *musmax = nullptr;
     int *status = nullptr;
+    double *cellsum = nullptr;
     bool fields_alloc = false;
     // solver
     double *x64 = nullptr, *r64 = nullptr, *part = nullptr, *dred = nullptr, *hred = nullptr;
     void *b = nullptr, *d0 = nullptr, *d1 = nullptr, *V = nullptr, *w = nullptr;
+    float *xh = nullptr, *xl = nullptr;  // double-single split of x
     int gm_m = 0;
+    int resid_fp64 = 0;  // 1: evaluate the refinement residual with FP64 arithmetic
     // event timing of the hot kernels
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // pairs
@@ -157,6 +164,7 @@ tk::GridC grid_c(const tursca_scene *sc) {
     g.ngd = (int)G.gdirs.size();
     g.nup = (int)G.up_dirs.size();
     g.R = sc->d.stencil_radius;
+    g.nc = (int)G.canon_dirs.size();
     g.hx = sc->d.hx;
     g.hy = sc->d.hy;
     g.hz = sc->d.hz;
@@ -165,10 +173,11 @@ tk::GridC grid_c(const tursca_scene *sc) {
 
 tk::GraphP graph_p(const tursca_scene *sc) {
     tk::GraphP p;
-    p.row_ptr = sc->row_ptr;
-    p.col = sc->col;
-    p.code = sc->code;
+    p.tstart = sc->tstart;
+    p.tmpl = sc->tmpl;
+    p.voff = sc->voff;
     p.cls = sc->cls;
+    p.pcls = sc->pcls;
     p.taps = sc->taps;
     p.tap_len_f = sc->tlf;
     p.tap_len_d = sc->tld;
@@ -176,6 +185,10 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.dir_len = sc->dir_len;
     p.q_iso = sc->q_iso;
     p.q_lamb = sc->q_lamb;
+    p.q_iso_f = sc->q_iso_f;
+    p.q_lamb_f = sc->q_lamb_f;
+    p.dir_len_f = sc->dir_len_f;
+    p.gdist1_f = sc->gdist1_f;
     p.gmem1 = sc->gmem1;
     p.gdist1 = sc->gdist1;
     p.up_dirs = sc->up_dirs;
@@ -185,6 +198,8 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.lat_n = sc->lat_n;
     p.gtop_off = sc->gtop_off;
     p.gtop_n = sc->gtop_n;
+    p.canon_dirs = sc->canon_dirs;
+    p.up_canon = sc->up_canon;
     return p;
 }
 
@@ -199,8 +214,11 @@ tk::FieldP<T> field_p(const tursca_scene *sc) {
     f.e1 = (T *)sc->e1;
     f.tinf = (T *)sc->tinf;
     f.tinfg = (T *)sc->tinfg;
-    f.zc_iso = (T *)sc->zc_iso;
-    f.zc_sun = (T *)sc->zc_sun;
+    f.a_iso = (T *)sc->zc_iso;
+    f.a_sun = (T *)sc->zc_sun;
+    f.tseg = (T *)sc->tseg;
+    f.rt = (T *)sc->rt;
+    f.wsp = (T *)sc->wsp;
     f.q_sun = (T *)sc->q_sun;
     f.hgv = (T *)sc->hgv;
     f.hg0v = (T *)sc->hg0v;
@@ -209,6 +227,7 @@ tk::FieldP<T> field_p(const tursca_scene *sc) {
     f.gsun = (T *)sc->gsun;
     f.mus_max_bits = sc->musmax;
     f.status = sc->status;
+    f.cellsum = sc->cellsum;
     return f;
 }
 
@@ -300,12 +319,16 @@ tursca_status ensure_fields(tursca_scene *sc) {
     CK(cudaMemsetAsync(sc->status, 0, sizeof(int), sc->st), "memset status");
     CK(dalloc(sc->allocs, sc->x64, nn * sizeof(double)), "alloc x");
     CK(dalloc(sc->allocs, sc->r64, nn * sizeof(double)), "alloc r");
-    CK(dalloc(sc->allocs, sc->part, 64 * 1024 * sizeof(double)), "alloc part");
+    // block partial sums: the residual writes one per 32 rows, the power sweeps two
+    // columns of one per 32 rows, the dot products up to 64 x 296
+    CK(dalloc(sc->allocs, sc->part, std::max<size_t>(64 * 1024, nn / 16 + 64) * sizeof(double)), "alloc part");
     CK(dalloc(sc->allocs, sc->dred, 256 * sizeof(double)), "alloc red");
     CK(dalloc(sc->allocs, sc->b, nn * es), "alloc b");
     CK(dalloc(sc->allocs, sc->d0, nn * es), "alloc d0");
     CK(dalloc(sc->allocs, sc->d1, nn * es), "alloc d1");
     CK(dalloc(sc->allocs, sc->w, nn * es), "alloc w");
+    CK(dalloc(sc->allocs, sc->xh, nn * sizeof(float)), "alloc xh");
+    CK(dalloc(sc->allocs, sc->xl, nn * sizeof(float)), "alloc xl");
     if (!sc->hred) {
         cudaError_t e = cudaMallocHost((void **)&sc->hred, 256 * sizeof(double));
         if (e != cudaSuccess) return cuda_fail(sc, e, "alloc pinned");
@@ -455,6 +478,21 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
     return TURSCA_OK;
 }
 
+// Chebyshev iteration parameters for A = I - K with the eigenvalues of K taken
+// in [lo, hi] (real, hi < 1): A's eigenvalues lie in [1 - hi, 1 - lo].
+struct ChebPlan {
+    double theta, delta, sigma, rate;
+};
+ChebPlan cheb_plan(double lo, double hi) {
+    ChebPlan c;
+    double alpha = 1.0 - hi, beta = 1.0 - lo;
+    c.theta = 0.5 * (alpha + beta);
+    c.delta = 0.5 * (beta - alpha);
+    c.sigma = c.theta / c.delta;
+    c.rate = 1.0 / (c.sigma + std::sqrt(c.sigma * c.sigma - 1.0));  // asymptotic error factor per step
+    return c;
+}
+
 template <typename T>
 tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
     const tk::GridC g = grid_c(sc);
@@ -462,10 +500,11 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     const int n = g.n_nodes;
     const int nbr = tk::resid_blocks(g);
     const int nb = tk::dot_blocks(n);
+    const int nsw = tk::sweep_blocks(g);
     SolveState ss;
     const bool fp64 = sc->d.precision == TURSCA_FP64;
-    if (solver == TURSCA_SOLVER_AUTO) solver = fp64 ? TURSCA_SOLVER_GMRES : 0;
-    if (solver == TURSCA_SOLVER_GMRES || solver == 0) {
+    if (solver == TURSCA_SOLVER_AUTO) solver = fp64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
+    auto ensure_basis = [&]() -> tursca_status {
         int m = fp64 ? 40 : 30;
         if (!sc->V || sc->gm_m != m) {
             T *V;
@@ -473,7 +512,11 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             sc->V = V;
             sc->gm_m = m;
         }
-    }
+        return TURSCA_OK;
+    };
+    // residual arithmetic: FP32 pairs on FP32 scenes (FP64 runs at a small
+    // fraction of the FP32 rate on this GPU), FP64 on FP64 scenes or on request
+    const bool ds = !fp64 && !sc->resid_fp64 && tk::resid_ds_ok(g);
     // x = 0, r = s, ||s||
     CK(cudaMemsetAsync(sc->x64, 0, (size_t)n * sizeof(double), sc->st), "memset x");
     tk::launch_convert<T, double>(sc->st, n, (const T *)sc->s, sc->r64);
@@ -483,54 +526,147 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     if (rs) return rs;
     const double sn = std::sqrt(sc->hred[0]);
     double rel = sn > 0 ? 1.0 : 0.0;
-    double prev_rel = 1.0;
-    int used_inner = 0;  // inner sweeps of the last Neumann step
-    int mode = solver;   // 0: adaptive (Neumann first), 1: Neumann, 2: GMRES
-    int inner_n = 8;
-    while (rel > rtol) {
-        if (ss.iters >= max_iter) break;
-        int budget = max_iter - ss.iters;
-        // b = r in the compute type
+    double rho = -1.0;      // estimate of the largest eigenvalue of K (-1: none yet)
+    double widen = 0.0;     // extra margin after a refinement that under-delivered
+    int inner_n = 8;        // Neumann sweeps (explicit Neumann solver)
+    int stalls = 0;
+    bool use_gmres = false;       // Chebyshev under-delivered: GMRES from now on
+    const double floor32 = 3e-7;  // relative accuracy the FP32 inner iterations can reach
+    while (rel > rtol && ss.iters < max_iter) {
+        const int budget = max_iter - ss.iters;
         T *bb = (T *)sc->b;
         tk::launch_convert<double, T>(sc->st, n, sc->r64, bb);
         sc->launches++;
+        // reduction asked of this refinement: all that is left if one
+        // refinement can reach it, else an equal share over the fewest
+        // refinements the FP32 floor allows
+        const double need = rtol / rel;
+        double target;
+        if (fp64 || need >= 10.0 * floor32) {
+            target = std::max(0.3 * need, fp64 ? 1e-15 : floor32);
+        } else {
+            int m = (int)std::ceil(std::log(need) / std::log(10.0 * floor32));
+            target = 0.3 * std::max(std::pow(need, 1.0 / m), 10.0 * floor32);
+        }
         const T *dd = nullptr;
-        bool use_gmres = (mode == TURSCA_SOLVER_GMRES) || (mode == 0 && ss.rho > 0.85);
-        if (use_gmres) {
+        int kind = solver;
+        bool power = false;
+        double predicted = 1.0;
+        if (solver == TURSCA_SOLVER_CHEBYSHEV) {
+            // Chebyshev on a real interval needs a clear gap below 1: near 1 the
+            // (small) imaginary parts of the spectrum in the middle of the
+            // interval are amplified, so GMRES takes over there
+            if (rho < 0.0)
+                power = true;
+            else if (rho + widen >= 0.85 || use_gmres)
+                kind = TURSCA_SOLVER_GMRES;
+        }
+        if (power) {
+            // Neumann sweeps d <- r + K d from d = r; the norms of successive
+            // differences (K^k r) give the power estimate of the largest eigenvalue
+            const int n1 = std::max(2, std::min(6, budget - 1));
+            T *cur = (T *)sc->d0, *nxt = (T *)sc->d1;
+            CK(cudaMemcpyAsync(cur, bb, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, sc->st), "copy");
+            for (int it = 0; it < n1; ++it) {
+                int pi = prof_begin(sc, P_SPMV);
+                tk::launch_sweep_pow<T>(sc->st, g, gp, (const T *)sc->val, cur, bb, nxt, sc->part + (it & 1) * nsw);
+                prof_end(sc, pi);
+                std::swap(cur, nxt);
+            }
+            tk::launch_finalize2(sc->st, sc->part, nsw, sc->dred + 2);
+            sc->launches += n1 + 1;
+            ss.iters += n1;
+            dd = cur;
+            ss.solver = TURSCA_SOLVER_NEUMANN;
+            // columns: last sweep (n1 - 1) & 1, the one before (n1 - 2) & 1
+            inner_n = n1;
+        } else if (kind == TURSCA_SOLVER_CHEBYSHEV) {
+            const double hi = std::min(0.9995, 1.02 * (rho + widen) + 0.005);
+            const ChebPlan cp = cheb_plan(-0.5 * hi, hi);
+            // K is not normal: the error contracts more slowly than the
+            // interval bound says (measured ~ rate^0.65 per step on the plume)
+            const double eff = std::pow(cp.rate, 0.65);
+            int nc = (int)std::ceil(std::log(target / 2.0) / std::log(eff));
+            nc = std::max(1, std::min(nc, budget - 1));
+            predicted = 2.0 * std::pow(eff, nc);
+            T *r = bb, *d = (T *)sc->w, *p0 = (T *)sc->d0, *p1 = (T *)sc->d1;
+            CK(cudaMemsetAsync(d, 0, (size_t)n * sizeof(T), sc->st), "memset");
+            tk::launch_scale<T>(sc->st, n, r, 1.0 / cp.theta, p0);
+            sc->launches++;
+            double rk = 1.0 / cp.sigma;
+            for (int k = 0; k < nc; ++k) {
+                double rk1 = 1.0 / (2.0 * cp.sigma - rk);
+                int pi = prof_begin(sc, P_SPMV);
+                tk::launch_cheb<T>(sc->st, g, gp, (const T *)sc->val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta);
+                prof_end(sc, pi);
+                std::swap(p0, p1);
+                rk = rk1;
+            }
+            sc->launches += nc;
+            ss.iters += nc;
+            dd = d;
+            ss.solver = TURSCA_SOLVER_CHEBYSHEV;
+        } else if (kind == TURSCA_SOLVER_GMRES) {
+            tursca_status e = ensure_basis();
+            if (e) return e;
             double tol = fp64 ? std::max(0.3 * rtol / rel, 1e-15) : std::max(0.3 * rtol / rel, 2e-6);
-            tursca_status e = gmres<T>(sc, g, gp, bb, (T *)sc->d0, tol, budget, ss);
+            e = gmres<T>(sc, g, gp, bb, (T *)sc->d0, tol, budget, ss);
             if (e) return e;
             dd = (const T *)sc->d0;
             ss.solver = TURSCA_SOLVER_GMRES;
-            used_inner = 0;
-        } else {
-            int nn = std::min(inner_n, std::max(1, budget));
+        } else {  // Neumann
+            int nn = std::min(inner_n, std::max(1, budget - 1));
             dd = neumann<T>(sc, g, gp, bb, nn, ss);
-            used_inner = nn;
+            inner_n = nn;
             ss.solver = TURSCA_SOLVER_NEUMANN;
         }
-        tk::launch_axpy_to64<T>(sc->st, n, dd, sc->x64);
+        tk::launch_update_x<T>(sc->st, n, dd, sc->x64, ds ? sc->xh : nullptr, ds ? sc->xl : nullptr);
         int pr = prof_begin(sc, P_RESID);
-        tk::launch_resid64<T>(sc->st, g, gp, (const T *)sc->val, (const T *)sc->s, sc->x64, sc->r64, sc->part, nbr);
+        if (ds)
+            tk::launch_resid_ds(sc->st, g, gp, (const float *)sc->val, (const float *)sc->s, sc->x64, sc->xh, sc->xl,
+                                sc->r64, sc->part, nbr);
+        else
+            tk::launch_resid64<T>(sc->st, g, gp, (const T *)sc->val, (const T *)sc->s, sc->x64, sc->r64, sc->part,
+                                  nbr);
         prof_end(sc, pr);
         tk::launch_finalize(sc->st, sc->part, nbr, sc->dred);
         sc->launches += 3;
         ss.refinements++;
         ss.iters++;
-        rs = read_red<T>(sc, 1);
+        rs = read_red<T>(sc, 4);
         if (rs) return rs;
-        prev_rel = rel;
+        const double prev = rel;
         rel = sn > 0 ? std::sqrt(sc->hred[0]) / sn : 0.0;
-        if (used_inner > 0 && prev_rel > 0 && rel > 0) {
-            double f = rel / prev_rel;
-            // the inner Neumann error after n sweeps is rho^(n+1)
-            double rho = std::pow(std::min(f, 0.999999), 1.0 / (used_inner + 1));
-            if (ss.refinements == 1 || f > 1e-6) ss.rho = rho;
-            double target = fp64 ? std::max(rtol / rel * 0.3, 1e-15) : std::max(rtol / rel * 0.3, 1e-6);
-            int want = (int)std::ceil(std::log(target) / std::log(std::max(ss.rho, 1e-3))) - 1;
-            inner_n = std::max(2, std::min(want, 400));
+        const double f = prev > 0 ? rel / prev : 0.0;
+        if (power) {
+            const int n1 = inner_n;
+            double last = sc->hred[2 + ((n1 - 1) & 1)], before = sc->hred[2 + ((n1 - 2) & 1)];
+            double est = before > 0 ? std::sqrt(last / before) : 0.0;
+            // the series' own reduction bounds the estimate from below
+            double avg = (f > 0 && f < 1) ? std::pow(f, 1.0 / (n1 + 1)) : 0.0;
+            rho = std::min(0.9999, std::max(est, avg));
+            ss.rho = rho;
+        } else if (kind == TURSCA_SOLVER_CHEBYSHEV) {
+            if (f > std::max(30.0 * predicted, 3.0 * floor32) && rel > rtol) {
+                // the interval missed part of the spectrum: widen it once toward 1,
+                // or hand over to GMRES
+                if (f > 0.5 || widen > 0.0 || rho + 0.5 * (1.0 - rho) > 0.95)
+                    use_gmres = true;
+                else
+                    widen += 0.5 * (1.0 - (rho + widen));
+                ++stalls;
+            }
+        } else if (kind == TURSCA_SOLVER_NEUMANN && solver == TURSCA_SOLVER_NEUMANN) {
+            if (prev > 0 && rel > 0 && f < 1.0) {
+                double rr = std::pow(std::min(f, 0.999999), 1.0 / (inner_n + 1));
+                if (ss.refinements == 1 || f > 1e-6) ss.rho = rr;
+                double tg = fp64 ? std::max(rtol / rel * 0.3, 1e-15) : std::max(rtol / rel * 0.3, 1e-6);
+                int want = (int)std::ceil(std::log(tg) / std::log(std::max(ss.rho, 1e-3))) - 1;
+                inner_n = std::max(2, std::min(want, 400));
+            }
         }
-        if (!(rel <= prev_rel * 1.5) && ss.refinements > 3) break;  // stagnation
+        if (!(rel <= prev * 1.5) && ss.refinements > 3) break;  // diverging
+        if (stalls > 6) break;
     }
     if (info) {
         info->iters = ss.iters;
@@ -651,8 +787,47 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
         o.n1_dz = (int16_t)c.n1_dz;
         o.dist1_inv = c.dist1 > 0 ? 1.0 / c.dist1 : 0.0;
         o.split = c.split;
+        o.pre_tab = (int16_t)c.pre_tab;
+        o.pre_dx = (int16_t)c.pre_dx;
+        o.pre_dy = (int16_t)c.pre_dy;
+        o.pre_dz = (int16_t)c.pre_dz;
+        o.seg_tab = (int16_t)c.seg_tab;
+        o.seg_dx = (int16_t)c.seg_dx;
+        o.seg_dy = (int16_t)c.seg_dy;
+        o.seg_dz = (int16_t)c.seg_dz;
+        o.dist1_inv_f = (float)o.dist1_inv;
+        o.split_f = (float)o.split;
     }
     CK(upload(sc, sc->allocs, sc->cls, dc.data(), dc.size() * sizeof(tk::DClass)), "upload classes");
+    {
+        std::vector<tk::PClass> pc(G.classes.size());
+        auto b8 = [](int v) { return (unsigned)(v & 0xff); };
+        for (size_t i = 0; i < G.classes.size(); ++i) {
+            const tg::SlotClass &c = G.classes[i];
+            const tk::DClass &o = dc[i];
+            tk::PClass &q = pc[i];
+            float dinv = (float)o.dist1_inv, spl = (float)o.split;
+            int dbits, sbits;
+            std::memcpy(&dbits, &dinv, 4);
+            std::memcpy(&sbits, &spl, 4);
+            q.w0 = make_int4((int)(c.kind | (c.bkind << 8) | (c.c_one << 16) | (c.n1_ground << 24)),
+                             (int)((unsigned)std::max(c.dir, 0) | ((unsigned)c.hgdir << 16)),
+                             (int)((unsigned)std::max(c.up_idx, 0) | ((unsigned)std::max(c.gdir, 0) << 16)), dbits);
+            q.w1 = make_int4((int)(b8(c.seg_tab + 1) | (b8(c.seg_dx) << 8) | (b8(c.seg_dy) << 16) | (b8(c.seg_dz) << 24)),
+                             (int)(b8(c.pre_tab + 1) | (b8(c.pre_dx) << 8) | (b8(c.pre_dy) << 16) | (b8(c.pre_dz) << 24)),
+                             (int)(b8(c.n1_dx) | (b8(c.n1_dy) << 8) | (b8(c.n1_dz) << 16)), sbits);
+            q.w2 = make_int4(c.pre_off, c.seg_off, c.hit_off, (int)(c.pre_n | (c.seg_n << 8) | (c.hit_n << 16)));
+            double dd = o.dist1_inv, ss = o.split;
+            long long di, si;
+            std::memcpy(&di, &dd, 8);
+            std::memcpy(&si, &ss, 8);
+            q.w3 = make_int4((int)(di & 0xffffffff), (int)(di >> 32), (int)(si & 0xffffffff), (int)(si >> 32));
+            if (c.pre_n > 255 || c.seg_n > 255 || c.hit_n > 255 || c.hgdir > 65535)
+                return fail(sc, TURSCA_E_INVALID, "internal error: class does not fit its packed form");
+        }
+        CK(upload(sc, sc->allocs, sc->pcls, pc.data(), pc.size() * sizeof(tk::PClass)), "upload classes");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+    }
     std::vector<tk::DTap> to;
     std::vector<float> lf;
     std::vector<double> ld;
@@ -677,6 +852,15 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     }
     CK(upload(sc, sc->allocs, sc->gmem1, gm.data(), ngd * sizeof(int4)), "upload gmem");
     CK(upload(sc, sc->allocs, sc->gdist1, gd1.data(), ngd * sizeof(double)), "upload gdist");
+    {
+        std::vector<float> a(G.len.begin(), G.len.end()), b(G.q_iso.begin(), G.q_iso.end()),
+            c(G.q_lamb.begin(), G.q_lamb.end()), d(gd1.begin(), gd1.end());
+        CK(upload(sc, sc->allocs, sc->dir_len_f, a.data(), a.size() * sizeof(float)), "upload f");
+        CK(upload(sc, sc->allocs, sc->q_iso_f, b.data(), b.size() * sizeof(float)), "upload f");
+        CK(upload(sc, sc->allocs, sc->q_lamb_f, c.data(), c.size() * sizeof(float)), "upload f");
+        CK(upload(sc, sc->allocs, sc->gdist1_f, d.data(), d.size() * sizeof(float)), "upload f");
+        CK(cudaStreamSynchronize(sc->st), "sync");  // the host vectors die here
+    }
     CK(upload(sc, sc->allocs, sc->up_dirs, G.up_dirs.data(), G.up_dirs.size() * sizeof(int)), "upload up");
     CK(upload(sc, sc->allocs, sc->top_off, G.top_off.data(), G.top_off.size() * sizeof(int)), "upload top");
     CK(upload(sc, sc->allocs, sc->top_n, G.top_n.data(), G.top_n.size() * sizeof(int)), "upload top");
@@ -695,33 +879,32 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     for (int k = 0; k < ngd; ++k)
         for (int a = 0; a < 3; ++a) dh[3 * (nd + k) + a] = G.gdirs[k].uhat[a];
     CK(upload(sc, sc->allocs, sc->dirhat, dh.data(), dh.size() * sizeof(double)), "upload dirhat");
-    // CSR structure from the templates
+    // row templates (the CSR structure of K, one template per layer)
     std::vector<int4> tm(G.tmpl.size());
-    for (size_t i = 0; i < G.tmpl.size(); ++i)
-        tm[i] = make_int4(G.tmpl[i].cls, G.tmpl[i].sdx, G.tmpl[i].sdy, G.tmpl[i].sz);
-    int *tstart, *tlen;
-    int4 *tmd;
-    std::vector<void *> tmp;
-    CK(upload(sc, tmp, tstart, G.tmpl_start.data(), G.tmpl_start.size() * sizeof(int)), "upload tmpl");
-    CK(upload(sc, tmp, tlen, G.tmpl_len.data(), G.tmpl_len.size() * sizeof(int)), "upload tmpl");
-    CK(upload(sc, tmp, tmd, tm.data(), tm.size() * sizeof(int4)), "upload tmpl");
-    const size_t nn = (size_t)G.n_nodes;
-    CK(dalloc(sc->allocs, sc->row_ptr, (nn + 1) * sizeof(int32_t)), "alloc row_ptr");
-    CK(dalloc(sc->allocs, sc->col, (size_t)G.nnz * sizeof(int32_t)), "alloc col");
-    CK(dalloc(sc->allocs, sc->code, (size_t)G.nnz * sizeof(uint16_t)), "alloc code");
-    CK(dalloc(sc->allocs, sc->val, (size_t)G.nnz * sc->es), "alloc val");
+    for (size_t i = 0; i < G.tmpl.size(); ++i) {
+        const tg::TSlot &t = G.tmpl[i];
+        tm[i] = make_int4(t.cls, t.flat, (int)((unsigned)(t.sdx & 0xffff) | ((unsigned)(t.sdy & 0xffff) << 16)),
+                          t.sz);
+    }
+    CK(upload(sc, sc->allocs, sc->tstart, G.tmpl_start.data(), G.tmpl_start.size() * sizeof(int)), "upload tmpl");
+    CK(upload(sc, sc->allocs, sc->tmpl, tm.data(), tm.size() * sizeof(int4)), "upload tmpl");
+    CK(upload(sc, sc->allocs, sc->voff, G.voff.data(), G.voff.size() * sizeof(long long)), "upload tmpl");
+    CK(dalloc(sc->allocs, sc->val, (size_t)G.nval * sc->es), "alloc val");
     const size_t es = sc->es;
     CK(dalloc(sc->allocs, sc->tinf, (size_t)G.up_dirs.size() * G.n_atm * es), "alloc tinf");
     CK(dalloc(sc->allocs, sc->tinfg, (size_t)ngd * G.n_ground * es), "alloc tinfg");
     CK(dalloc(sc->allocs, sc->q_sun, (size_t)sc->d.n_species * nd * es), "alloc qsun");
     CK(dalloc(sc->allocs, sc->hgv, (size_t)sc->d.n_species * (nd + ngd) * es), "alloc hgv");
     CK(dalloc(sc->allocs, sc->hg0v, (size_t)sc->d.n_species * es), "alloc hg0v");
-    tk::GridC gc = grid_c(sc);
-    tk::launch_expand(sc->st, gc, tstart, tmd, tlen, sc->row_ptr, sc->col, sc->code);
-    sc->launches++;
-    cudaError_t ce = cudaGetLastError();
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(sc->st);
-    free_list(tmp);
+    CK(dalloc(sc->allocs, sc->cellsum, (size_t)sc->d.n_species * nd * sizeof(double)), "alloc cellsum");
+    CK(upload(sc, sc->allocs, sc->canon_dirs, G.canon_dirs.data(), G.canon_dirs.size() * sizeof(int)), "upload canon");
+    std::vector<int> upc(G.up_dirs.size());
+    for (size_t i = 0; i < upc.size(); ++i) upc[i] = G.canon_of_dir[G.up_dirs[i]];
+    CK(upload(sc, sc->allocs, sc->up_canon, upc.data(), upc.size() * sizeof(int)), "upload canon");
+    CK(dalloc(sc->allocs, sc->tseg, G.canon_dirs.size() * (size_t)G.n_atm * es), "alloc tseg");
+    CK(dalloc(sc->allocs, sc->rt, (size_t)G.n_atm * es), "alloc rt");
+    CK(dalloc(sc->allocs, sc->wsp, (size_t)sc->d.n_species * G.n_atm * es), "alloc wsp");
+    cudaError_t ce = cudaStreamSynchronize(sc->st);
     if (ce != cudaSuccess) return cuda_fail(sc, ce, "build_graph");
     sc->built = true;
     return TURSCA_OK;
@@ -797,7 +980,7 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!sc->assembled) return fail(sc, TURSCA_E_STATE, "assemble_flux has not been called");
     if (!(rtol > 0.0) || max_iter < 1) return fail(sc, TURSCA_E_INVALID, "rtol must be > 0 and max_iter >= 1");
-    if (solver < 0 || solver > 2) return fail(sc, TURSCA_E_INVALID, "unknown solver");
+    if (solver < 0 || solver > 3) return fail(sc, TURSCA_E_INVALID, "unknown solver");
     tursca_status e = sync_check(sc, "assemble");
     if (e) return e;
     if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info);
@@ -830,27 +1013,41 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
     const void *src = nullptr;
     size_t need = 0;
     bool host = false;
-    std::vector<int16_t> tmp16;
     std::vector<int32_t> tmp32;
     void *dtmp = nullptr;
     switch (which) {
-        case TURSCA_F_ROW_PTR: src = sc->row_ptr; need = (nn + 1) * 4; break;
-        case TURSCA_F_COL: src = sc->col; need = nnz * 4; break;
-        case TURSCA_F_VAL: src = sc->val; need = nnz * es; break;
+        case TURSCA_F_ROW_PTR:
+        case TURSCA_F_COL:
+        case TURSCA_F_VAL:
         case TURSCA_F_SLOT_DIR:
         case TURSCA_F_SLOT_K: {
-            need = which == TURSCA_F_SLOT_DIR ? nnz * 2 : nnz;
+            // CSR view of the slot-major matrix, produced on demand
+            need = which == TURSCA_F_ROW_PTR ? (nn + 1) * 4
+                   : which == TURSCA_F_COL   ? nnz * 4
+                   : which == TURSCA_F_VAL   ? nnz * es
+                   : which == TURSCA_F_SLOT_DIR ? nnz * 2
+                                                : nnz;
             if (bytes != need) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
-            CK(cudaMalloc(&dtmp, nnz * 3), "alloc");
-            int16_t *dd = (int16_t *)dtmp;
-            int8_t *kk = (int8_t *)((char *)dtmp + nnz * 2);
-            tk::launch_slot_info(sc->st, (long long)nnz, sc->code, sc->cls, dd, kk, (int)G.dirs.size());
+            if (which == TURSCA_F_VAL && !sc->assembled) return fail(sc, TURSCA_E_STATE, "K is not assembled");
+            CK(cudaMalloc(&dtmp, need), "alloc");
+            const tk::GridC gc = grid_c(sc);
+            const tk::GraphP gp = graph_p(sc);
+            int32_t *rp = which == TURSCA_F_ROW_PTR ? (int32_t *)dtmp : nullptr;
+            int32_t *cc = which == TURSCA_F_COL ? (int32_t *)dtmp : nullptr;
+            int16_t *dd = which == TURSCA_F_SLOT_DIR ? (int16_t *)dtmp : nullptr;
+            int8_t *kk = which == TURSCA_F_SLOT_K ? (int8_t *)dtmp : nullptr;
+            if (sc->d.precision == TURSCA_FP64)
+                tk::launch_export_csr<double>(sc->st, gc, gp, (const double *)sc->val, rp, cc,
+                                              which == TURSCA_F_VAL ? (double *)dtmp : nullptr, dd, kk);
+            else
+                tk::launch_export_csr<float>(sc->st, gc, gp, (const float *)sc->val, rp, cc,
+                                             which == TURSCA_F_VAL ? (float *)dtmp : nullptr, dd, kk);
             sc->launches++;
-            cudaError_t e = cudaMemcpyAsync(dst, which == TURSCA_F_SLOT_DIR ? (void *)dd : (void *)kk, need,
-                                            cudaMemcpyDefault, sc->st);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dtmp, need, cudaMemcpyDefault, sc->st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(sc->st);
             cudaFree(dtmp);
-            if (e != cudaSuccess) return cuda_fail(sc, e, "get slot info");
+            if (e != cudaSuccess) return cuda_fail(sc, e, "get csr");
             return TURSCA_OK;
         }
         case TURSCA_F_TSUN: src = sc->tsun; need = nn * es; break;
@@ -883,6 +1080,16 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
 }
 
 long long tursca_launch_count(const tursca_scene *sc) { return sc ? sc->launches : 0; }
+
+tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    switch (option) {
+        case TURSCA_OPT_RESIDUAL_FP64:
+            sc->resid_fp64 = value != 0.0;
+            return TURSCA_OK;
+        default: return fail(sc, TURSCA_E_INVALID, "unknown option");
+    }
+}
 
 tursca_status tursca_profile_enable(tursca_scene *sc, int on) {
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");

@@ -128,6 +128,31 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
                 }
             }
     const int nd = (int)G.dirs.size();
+    {
+        auto canonical = [](const std::array<int, 3> &u) {
+            return u[2] > 0 || (u[2] == 0 && (u[1] > 0 || (u[1] == 0 && u[0] > 0)));
+        };
+        for (int u = 0; u < nd; ++u)
+            if (canonical(G.dirs[u])) G.canon_dirs.push_back(u);
+        G.canon_of_dir.assign(nd, -1);
+        for (int u = 0; u < nd; ++u)
+            for (int c = 0; c < (int)G.canon_dirs.size(); ++c) {
+                const auto &v = G.dirs[G.canon_dirs[c]];
+                const auto &w = G.dirs[u];
+                if ((v[0] == w[0] && v[1] == w[1] && v[2] == w[2]) || (v[0] == -w[0] && v[1] == -w[1] && v[2] == -w[2]))
+                    G.canon_of_dir[u] = c;
+            }
+    }
+    // segment s (1-based) of the chain along u, from p_{s-1} to p_s, as a table
+    // entry: canonical direction and its start node relative to the source
+    auto seg_entry = [&](int u, int s, int &tab, int &dx, int &dy, int &dz) {
+        tab = G.canon_of_dir[u];
+        bool canon = G.canon_dirs[tab] == u;
+        int b = canon ? s - 1 : s;
+        dx = b * G.dirs[u][0];
+        dy = b * G.dirs[u][1];
+        dz = b * G.dirs[u][2];
+    };
 
     // ---- ground directions: (dx, dy, dzc - 1/2); collinear members share a chain
     {
@@ -320,10 +345,12 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
                 std::vector<Tap> pre, seg, h;
                 for (int s = 0; s < k - 1; ++s) shifted(u, s, pre);
                 shifted(u, k - 1, seg);
+                if (k == 2) seg_entry(u, 1, c.pre_tab, c.pre_dx, c.pre_dy, c.pre_dz);
+                seg_entry(u, k, c.seg_tab, c.seg_dx, c.seg_dy, c.seg_dz);
                 if (bk == B_HIT) h = hit;
                 std::vector<long> key = {SK_CHAIN, u, k, bk, bk == B_HIT ? sz : -1, 0, 0};
                 int id = get_class(c, key, pre, seg, h);
-                rows[sz + k * uz].push_back(TSlot{id, -k * ux, -k * uy, sz});
+                rows[sz + k * uz].push_back(TSlot{id, -k * ux, -k * uy, sz, 0});
             }
             if (m == 0) {
                 SlotClass c;
@@ -344,7 +371,7 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
                 }
                 std::vector<long> key = {SK_SELF, u, 0, c.bkind, cs == 'c' ? sz : -1, 0, 0};
                 int id = get_class(c, key, none, none, h);
-                rows[sz].push_back(TSlot{id, 0, 0, sz});
+                rows[sz].push_back(TSlot{id, 0, 0, sz, 0});
             }
             if (cs == 'c') {
                 // ground column(s) containing the hit point; exact edge / corner hits split equally
@@ -380,9 +407,10 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
                             c.n1_ground = 1;
                             c.dist1 = thit * G.len[u];
                         }
+                        if (m == 1) seg_entry(u, 1, c.pre_tab, c.pre_dx, c.pre_dy, c.pre_dz);
                         std::vector<long> key = {SK_GROUND, u, m, B_HIT, sz, cx, cy};
                         int id = get_class(c, key, pre, none, hit);
-                        rows[nz].push_back(TSlot{id, -cx, -cy, sz});
+                        rows[nz].push_back(TSlot{id, -cx, -cy, sz, 0});
                     }
             }
         }
@@ -433,23 +461,16 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
             for (int s = 0; s < k - 1; ++s) pre.insert(pre.end(), segs[s].begin(), segs[s].end());
             std::vector<long> key = {SK_GCHAIN, g, k, c.bkind, -1, 0, 0};
             int id = get_class(c, key, pre, segs[k - 1], none);
-            rows[mem[k - 1][2] - 1].push_back(TSlot{id, -mem[k - 1][0], -mem[k - 1][1], -1});
+            rows[mem[k - 1][2] - 1].push_back(TSlot{id, -mem[k - 1][0], -mem[k - 1][1], -1, 0});
         }
-    }
-
-    // padding class
-    {
-        SlotClass c;
-        c.kind = SK_PAD;
-        c.dir = -1;
-        c.hgdir = 0;
-        std::vector<Tap> none;
-        G.pad_class = get_class(c, {SK_PAD, 0, 0, 0, 0, 0, 0}, none, none, none);
     }
 
     // ---- templates: fixed order (ground sources last; then by source layer, row, column)
     G.tmpl_start.assign(nz + 2, 0);
     G.tmpl_len.assign(nz + 1, 0);
+    G.voff.assign(nz + 2, 0);
+    const long long nxy = (long long)nx * ny;
+    const long long nxy_pad = (nxy + kGroup - 1) / kGroup * kGroup;
     for (int z = 0; z <= nz; ++z) {
         auto &r = rows[z];
         std::stable_sort(r.begin(), r.end(), [](const TSlot &a, const TSlot &b) {
@@ -460,15 +481,20 @@ std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, 
             if (a.sdx != b.sdx) return a.sdx < b.sdx;
             return a.cls < b.cls;
         });
-        G.nnz_edges += (long long)r.size() * nx * ny;
-        while (r.size() % 4 != 0) r.push_back(TSlot{G.pad_class, 0, 0, z < nz ? z : -1});
+        for (auto &t : r) {
+            long long src_base = t.sz >= 0 ? (long long)t.sz * nxy : (long long)G.n_atm;
+            t.flat = (int)(src_base - (long long)z * nxy + (long long)t.sdy * nx + t.sdx);
+        }
         G.tmpl_len[z] = (int)r.size();
         G.max_row = std::max(G.max_row, (int)r.size());
         G.tmpl_start[z + 1] = G.tmpl_start[z] + (int)r.size();
         G.tmpl.insert(G.tmpl.end(), r.begin(), r.end());
-        G.nnz += (long long)r.size() * nx * ny;
+        G.voff[z + 1] = G.voff[z] + (long long)r.size() * nxy_pad;
+        G.nnz += (long long)r.size() * nxy;
     }
-    if (G.nnz >= (1LL << 31)) return "graph has more than 2^31 slots";
+    G.nnz_edges = G.nnz;
+    G.nval = G.voff[nz + 1];
+    if (G.nval >= (1LL << 31)) return "graph has more than 2^31 slots";
     if (!ok_) return "internal error: a traced segment left the domain";
     return std::string();
 }
@@ -494,8 +520,8 @@ void expand_csr(const Graph &G, int32_t *row_ptr, int32_t *col, int16_t *dir, in
             int src = s.sz >= 0 ? (s.sz * ny + sy) * nx + sx : G.n_atm + sy * nx + sx;
             const SlotClass &c = G.classes[s.cls];
             if (col) col[e] = src;
-            if (dir) dir[e] = (int16_t)(c.kind == SK_PAD ? -1 : c.hgdir);
-            if (k) k[e] = (int8_t)(c.kind == SK_PAD ? -1 : c.kind == SK_SELF ? 0 : c.kind == SK_GROUND ? 7 : c.k);
+            if (dir) dir[e] = (int16_t)c.hgdir;
+            if (k) k[e] = (int8_t)(c.kind == SK_SELF ? 0 : c.kind == SK_GROUND ? 7 : c.k);
         }
     }
     if (row_ptr) row_ptr[G.n_nodes] = (int32_t)e;

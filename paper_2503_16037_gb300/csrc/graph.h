@@ -14,13 +14,14 @@
 
 namespace tg {
 
+constexpr int kGroup = 128;  // rows per storage group of the value array
+
 // Slot kinds: what kind of graph edge a stored entry of K is.
 enum SlotKind : int {
     SK_CHAIN = 0,  // atmospheric source j deposits on chain node j + k u
     SK_SELF = 1,   // atmospheric source deposits on itself (chain left the domain before p1)
     SK_GROUND = 2, // atmospheric source's chain hits the ground: deposit on a ground column
-    SK_GCHAIN = 3, // ground source deposits on a voxel of its chain
-    SK_PAD = 4     // row padding (value 0)
+    SK_GCHAIN = 3  // ground source deposits on a voxel of its chain
 };
 
 // What lies beyond a terminal chain node.
@@ -48,6 +49,11 @@ struct SlotClass {
     int c_one = 0;               // direction has no receiver other than the source: coupling 1
     int up_idx = -1;             // upward-direction index for B_TINF
     int gdir = -1;               // ground direction index for ground sources
+    // full lattice segments are read from the per-node segment table:
+    // table index of the segment direction (-1: use the taps) and the node,
+    // relative to the source, from which that canonical direction starts
+    int pre_tab = -1, pre_dx = 0, pre_dy = 0, pre_dz = 0;
+    int seg_tab = -1, seg_dx = 0, seg_dy = 0, seg_dz = 0;
 };
 
 // One entry of a row template: the source of a slot relative to the receiver.
@@ -55,6 +61,7 @@ struct TSlot {
     int cls;
     int sdx, sdy;  // source column offset (periodic)
     int sz;        // absolute source layer, -1 for a ground source
+    int flat;      // source node - receiver node when no periodic wrap occurs
 };
 
 struct GroundDir {
@@ -75,6 +82,10 @@ struct Graph {
     std::vector<double> len;
     std::vector<int> up_of_dir;  // -1 if not upward
     std::vector<int> up_dirs;    // atmospheric index of each upward direction
+    // canonical half of the directions (u_z > 0, or u_z = 0 and (u_y > 0 or
+    // u_y = 0 and u_x > 0)): one per pair {u, -u}; segment table rows
+    std::vector<int> canon_of_dir;  // index of u or -u in canon_dirs
+    std::vector<int> canon_dirs;    // atmospheric index of each canonical direction
 
     // ground directions (collinear members form one chain)
     std::vector<GroundDir> gdirs;
@@ -89,7 +100,6 @@ struct Graph {
     // taps and classes
     std::vector<Tap> taps;
     std::vector<SlotClass> classes;
-    int pad_class = -1;
 
     // tau_inf sweep: partial taps from the centre of a top layer to the TOA,
     // per upward direction and start layer offset o (layer nz - 1 - o)
@@ -99,11 +109,16 @@ struct Graph {
     // ground chains: taps from the terminal member to the TOA, per ground direction
     std::vector<int> gtop_off, gtop_n;
 
-    // row templates: layers 0..nz-1, then the ground (index nz)
+    // row templates: layers 0..nz-1, then the ground (index nz).  Every row of
+    // a template has the same slots in the same order.  Values are stored per
+    // group of kGroup rows of a layer, slot-major inside the group:
+    // val[voff[z] + ((r / kGroup) * nt + t) * kGroup + r % kGroup]
+    // (r = row - z * nxy, nt = template length); layers are padded to whole groups.
     std::vector<int> tmpl_start;  // [nz + 2]
     std::vector<TSlot> tmpl;
-    std::vector<int> tmpl_len;    // padded row length per template
-    long long nnz = 0, nnz_edges = 0;
+    std::vector<int> tmpl_len;    // row length per template
+    std::vector<long long> voff;  // [nz + 2] first value of each template
+    long long nnz = 0, nnz_edges = 0, nval = 0;  // nval: stored values including group padding
     int max_row = 0;
 };
 

@@ -17,7 +17,23 @@ struct __align__(16) DClass {
     int16_t n1_dx, n1_dy, n1_dz, pad1;
     double dist1_inv;
     double split;
+    int16_t pre_tab, pre_dx, pre_dy, pre_dz;  // segment table lookups (tab < 0: taps)
+    int16_t seg_tab, seg_dx, seg_dy, seg_dz;
+    float dist1_inv_f, split_f;               // FP32 copies for the FP32 kernels
+    float pad2, pad3;
 };
+
+// Packed form of a slot class for the edge kernel (four 16-byte words):
+//   w0 = {kind | bkind << 8 | c_one << 16 | n1_ground << 24, dir | hgdir << 16,
+//         up_idx | gdir << 16, float bits of 1 / dist1}
+//   w1 = {seg_tab + 1 | seg_dx << 8 | seg_dy << 16 | seg_dz << 24 (signed bytes),
+//         the same for pre, n1_dx | n1_dy << 8 | n1_dz << 16, float bits of split}
+//   w2 = {pre_off, seg_off, hit_off, pre_n | seg_n << 8 | hit_n << 16}
+//   w3 = {double 1 / dist1, double split} (FP64 kernels)
+struct __align__(16) PClass {
+    int4 w0, w1, w2, w3;
+};
+__host__ __device__ __forceinline__ int sbyte(int v, int sh) { return (int)(signed char)((v >> sh) & 0xff); }
 
 // Tap offsets (cell offsets relative to the segment base); lengths are in
 // separate float / double arrays.
@@ -28,16 +44,22 @@ struct __align__(8) DTap {
 // Grid constants shared by most kernels.
 struct GridC {
     int nx, ny, nz, nxy, n_atm, n_ground, n_nodes;
-    int S, nd, ngd, nup, R;
+    int S, nd, ngd, nup, R, nc;  // nc: canonical directions (segment table rows)
     double hx, hy, hz;
 };
 
-// Pointers of the graph (per shape).
+// Row templates: every receiver row of layer z (z = nz: the ground) has the
+// slots tmpl[tstart[z] .. tstart[z+1]); the value of slot t of row r of the
+// layer is val[val_base(voff[z], nt, r) + t * kGroup].  A template entry is
+// (class, flat, sdx | sdy << 16, sz): source node = row + flat, corrected by
+// +-nx when x + sdx leaves [0, nx) and by +-nx*ny when y + sdy leaves
+// [0, ny); sz is the absolute source layer (-1: a ground source).
 struct GraphP {
-    const int32_t *row_ptr;
-    const int32_t *col;
-    const uint16_t *code;
+    const int *tstart;        // [nz + 2]
+    const int4 *tmpl;         // (class, flat, sdx, sdy)
+    const long long *voff;    // [nz + 2]
     const DClass *cls;
+    const PClass *pcls;
     const DTap *taps;
     const float *tap_len_f;
     const double *tap_len_d;
@@ -45,12 +67,18 @@ struct GraphP {
     const double *dir_len;    // physical length of u
     const double *q_iso;      // [nd]
     const double *q_lamb;     // [ngd]
+    const float *q_iso_f;     // FP32 copies of the per-direction constants
+    const float *q_lamb_f;
+    const float *dir_len_f;
+    const float *gdist1_f;
     const int4 *gmem1;        // first member (dx, dy, dzc) of each ground chain
     const double *gdist1;     // distance from the ground point to the first member
     const int *up_dirs;       // atmospheric index of each upward direction
     const int *top_off, *top_n;    // [nup * R]
     const int *lat_off, *lat_n;    // [nd]
     const int *gtop_off, *gtop_n;  // [ngd]
+    const int *canon_dirs;         // [nc] atmospheric index of each canonical direction
+    const int *up_canon;           // [nup] canonical index of each upward direction
 };
 
 // Per-scene optical fields and assembled quantities (element type T).
@@ -64,12 +92,16 @@ struct FieldP {
     T *e1;           // [n_nodes]
     T *tinf;         // [nup][n_atm]
     T *tinfg;        // [ngd][n_ground]
-    T *zc_iso;       // [n_nodes]
-    T *zc_sun;       // [n_nodes]
+    T *a_iso;        // [n_nodes] coupling factor zc * sqrt(mu_s) of each source (0: weight 1)
+    T *a_sun;        // [n_nodes]
+    T *tseg;         // [nc][n_atm] optical depth of the lattice segment from a node along a canonical direction
+    T *rt;           // [n_atm] sqrt of the total scattering coefficient
+    T *wsp;          // [S][n_atm] species fractions of the scattering coefficient
     T *q_sun;        // [S][nd]
     T *hgv;          // [S][nd + ngd]
     T *hg0v;         // [S]
-    T *val;          // [nnz]
+    T *val;          // [nnz] slot-major per template
+    double *cellsum; // [S][nd] HG sums per Fibonacci cell
     T *s;            // [n_nodes]
     T *gsun;         // [n_atm]
     unsigned long long *mus_max_bits;  // max of mu_s (bits of a non-negative double)
@@ -100,9 +132,50 @@ struct ViewP {
 
 enum { STATUS_BAD_FIELD = 1, STATUS_TIMEOUT = 2 };
 
+// per-direction and per-class constants in the compute type, without
+// FP64 -> FP32 conversions in FP32 kernels
+template <typename T>
+struct Cst;
+template <>
+struct Cst<float> {
+    __device__ static __forceinline__ float q_iso(const GraphP &p, int u) { return p.q_iso_f[u]; }
+    __device__ static __forceinline__ float q_lamb(const GraphP &p, int u) { return p.q_lamb_f[u]; }
+    __device__ static __forceinline__ float dir_len(const GraphP &p, int u) { return p.dir_len_f[u]; }
+    __device__ static __forceinline__ float gdist1(const GraphP &p, int u) { return p.gdist1_f[u]; }
+    __device__ static __forceinline__ float dinv(const DClass &c) { return c.dist1_inv_f; }
+    __device__ static __forceinline__ float split(const DClass &c) { return c.split_f; }
+};
+template <>
+struct Cst<double> {
+    __device__ static __forceinline__ double q_iso(const GraphP &p, int u) { return p.q_iso[u]; }
+    __device__ static __forceinline__ double q_lamb(const GraphP &p, int u) { return p.q_lamb[u]; }
+    __device__ static __forceinline__ double dir_len(const GraphP &p, int u) { return p.dir_len[u]; }
+    __device__ static __forceinline__ double gdist1(const GraphP &p, int u) { return p.gdist1[u]; }
+    __device__ static __forceinline__ double dinv(const DClass &c) { return c.dist1_inv; }
+    __device__ static __forceinline__ double split(const DClass &c) { return c.split; }
+};
+
+// Values: per group of kGroup rows of a layer, slot-major inside the group.
+constexpr int kGroup = 128;
+__host__ __device__ __forceinline__ long long val_base(long long voff_z, int nt, int r) {
+    return voff_z + (long long)(r / kGroup) * nt * kGroup + (r % kGroup);
+}
+
+// source node of template slot (sdx, sdy, flat) for the receiver at (x, y)
+__host__ __device__ __forceinline__ int tmpl_sdx(int4 t) { return (int)(short)(t.z & 0xffff); }
+__host__ __device__ __forceinline__ int tmpl_sdy(int4 t) { return (int)(short)((unsigned)t.z >> 16); }
+__host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x, int y, int4 t) {
+    int sx = x + tmpl_sdx(t), sy = y + tmpl_sdy(t);
+    int j = row + t.y;
+    j += sx < 0 ? g.nx : 0;
+    j -= sx >= g.nx ? g.nx : 0;
+    j += sy < 0 ? g.nxy : 0;
+    j -= sy >= g.ny ? g.nxy : 0;
+    return j;
+}
+
 // ---- assembly (kernels_asm.cu)
-void launch_expand(cudaStream_t st, const GridC &g, const int *tmpl_start, const int4 *tmpl, const int *tmpl_len,
-                   int32_t *row_ptr, int32_t *col, uint16_t *code);
+// CSR export of the slot-major matrix (row order = template order)
 // field preparation, quadrature tables, sun, tau_inf sweeps, coupling normalisers
 template <typename T>
 void launch_assemble_pre(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
@@ -112,9 +185,9 @@ template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                           long long *launches);
 
-// direction and chain index of every slot (from its class)
-void launch_slot_info(cudaStream_t st, long long nnz, const uint16_t *code, const DClass *cls, int16_t *dir,
-                      int8_t *k, int nd);
+template <typename T>
+void launch_export_csr(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, int32_t *row_ptr,
+                       int32_t *col, T *cval, int16_t *dir, int8_t *k);
 
 // ---- solve (kernels_solve.cu)
 // y = b + K x (b may be null); T-valued vectors, T accumulation
@@ -125,6 +198,13 @@ template <typename T>
 void launch_resid64(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *s, const double *x,
                     double *r, double *part, int nblk);
 int resid_blocks(const GridC &g);
+// the same residual with FP32-pair (double-single) arithmetic: x = xh + xl
+bool resid_ds_ok(const GridC &g);
+void launch_resid_ds(cudaStream_t st, const GridC &g, const GraphP &gp, const float *val, const float *s,
+                     const double *x, const float *xh, const float *xl, double *r, double *part, int nblk);
+// x += d and (xh, xl may be null) its double-single split
+template <typename T>
+void launch_update_x(cudaStream_t st, int n, const T *d, double *x, float *xh, float *xl);
 // deterministic reductions: out[k] = sum_i V[k*ldv + i] * y[i], k < ncol
 template <typename A, typename B>
 void launch_dots(cudaStream_t st, int n, const A *V, size_t ldv, int ncol, const B *y, double *part, int nblk,
@@ -134,6 +214,8 @@ void launch_sumsq(cudaStream_t st, int n, const T *x, double *part, int nblk, do
 int dot_blocks(int n);
 // finalize block partials part[nblk] (single column) into out[0]
 void launch_finalize(cudaStream_t st, const double *part, int nblk, double *out);
+// finalize two columns part[2][nblk] into out[0..1]
+void launch_finalize2(cudaStream_t st, const double *part, int nblk, double *out);
 // vector ops
 template <typename T, typename U>
 void launch_convert(cudaStream_t st, int n, const T *a, U *b);
@@ -145,6 +227,15 @@ template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h);  // w -= V h
 template <typename T>
 void launch_combine(cudaStream_t st, int n, T *x, const T *V, size_t ldv, int k, const double *y);  // x += V y
+// Neumann sweep y = b + K x that also writes per-block sums of (y - x)^2 to part[sweep_blocks]
+template <typename T>
+void launch_sweep_pow(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y,
+                      double *part);
+int sweep_blocks(const GridC &g);
+// Chebyshev step: q = K p; r <- r - p + q; d <- d + p; pn = c1 p + c2 r
+template <typename T>
+void launch_cheb(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *p, T *r, T *d, T *pn,
+                 double c1, double c2);
 template <typename T>
 void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const T *y, T *out);  // out = a x + b y
 template <typename T>

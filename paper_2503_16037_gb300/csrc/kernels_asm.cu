@@ -8,6 +8,12 @@
 //   external source     S_a                    Sec. 2 (far-field source)
 // The deposit of a chain on its nodes lumps the extinction beyond the
 // stencil on the terminal node; escape to the TOA leaves the graph.
+//
+// Layout: all receiver rows of one layer share a slot template, so the edge
+// kernel runs one thread per row and a warp walks the template in lockstep:
+// the slot class, its tap offsets and the chain kind are warp-uniform, the
+// extinction gathers of a tap are coalesced along x, and the values are
+// stored slot-major (val[voff + t * nxy + r]) with coalesced writes.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,7 +49,7 @@ __device__ __forceinline__ const float *tap_len<float>(const GraphP &gp) { retur
 template <>
 __device__ __forceinline__ const double *tap_len<double>(const GraphP &gp) { return gp.tap_len_d; }
 
-__device__ __forceinline__ int wrap_small(int a, int n) {  // |a| < 2n
+__device__ __forceinline__ int wrap_small(int a, int n) {  // -n <= a < 2n
     a = a < 0 ? a + n : a;
     return a >= n ? a - n : a;
 }
@@ -52,30 +58,36 @@ __device__ __forceinline__ int wrap_any(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-// optical depth of a tap list based at cell (bx, by, bz); offsets small (stencil)
+// optical depth of a stencil-sized tap list based at cell (bx, by, bz)
 template <typename T>
-__device__ __forceinline__ T tap_sum(const GridC &g, const GraphP &gp, const T *mu_e, int off, int n, int bx, int by,
-                                     int bz) {
+__device__ __forceinline__ T tap_sum(const GridC &g, const GraphP &gp, const T *__restrict__ mu_e, int off, int n,
+                                     int bx, int by, int bz) {
     const T *len = tap_len<T>(gp);
     T acc = T(0);
     for (int t = 0; t < n; ++t) {
         DTap tp = gp.taps[off + t];
         int x = wrap_small(bx + tp.dx, g.nx), y = wrap_small(by + tp.dy, g.ny), z = bz + tp.dz;
-        acc += len[off + t] * mu_e[(z * g.ny + y) * g.nx + x];
+        acc += len[off + t] * __ldg(mu_e + (z * g.ny + y) * g.nx + x);
     }
     return acc;
 }
 
-// same for long rays whose horizontal offsets may exceed the grid (any wrap)
+// optical depth of a long ray (taps ordered along the ray, so consecutive
+// offsets differ by at most one cell per axis): the column is wrapped once
+// and then followed incrementally
 template <typename T>
-__device__ __forceinline__ T tap_sum_far(const GridC &g, const GraphP &gp, const T *mu_e, int off, int n, int bx,
-                                         int by, int bz) {
-    const T *len = tap_len<T>(gp);
+__device__ __forceinline__ T ray_sum(const GridC &g, const DTap *__restrict__ taps, const T *__restrict__ len,
+                                     const T *__restrict__ mu_e, int off, int n, int bx, int by, int bz) {
     T acc = T(0);
+    if (n == 0) return acc;
+    DTap p = taps[off];
+    int x = wrap_any(bx + p.dx, g.nx), y = wrap_any(by + p.dy, g.ny);
     for (int t = 0; t < n; ++t) {
-        DTap tp = gp.taps[off + t];
-        int x = wrap_any(bx + tp.dx, g.nx), y = wrap_any(by + tp.dy, g.ny), z = bz + tp.dz;
-        acc += len[off + t] * mu_e[(z * g.ny + y) * g.nx + x];
+        DTap tp = taps[off + t];
+        x = wrap_small(x + (tp.dx - p.dx), g.nx);
+        y = wrap_small(y + (tp.dy - p.dy), g.ny);
+        p = tp;
+        acc += len[off + t] * __ldg(mu_e + ((bz + tp.dz) * g.ny + y) * g.nx + x);
     }
     return acc;
 }
@@ -87,66 +99,38 @@ __device__ __forceinline__ T hg(T g, T mu) {
 }
 
 // ---------------------------------------------------------------------------
-// CSR structure from the per-layer row templates (one warp per row)
+// CSR export (row order = template order): one thread per row
 
-__global__ void k_expand(GridC g, const int *tmpl_start, const int4 *tmpl, const int *tmpl_len, int32_t *row_ptr,
-                         int32_t *col, uint16_t *code) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= g.n_nodes) return;
-    int i = warp, z, x, y;
-    if (i < g.n_atm) {
-        z = i / g.nxy;
-        int r = i - z * g.nxy;
-        y = r / g.nx;
-        x = r - y * g.nx;
-    } else {
-        z = g.nz;
-        int r = i - g.n_atm;
-        y = r / g.nx;
-        x = r - y * g.nx;
-    }
-    // row start: all rows of earlier templates, then earlier rows of this layer
+template <typename T>
+__global__ void k_export_csr(GridC g, GraphP gp, const T *__restrict__ val, int32_t *row_ptr, int32_t *col,
+                             T *cval, int16_t *dir, int8_t *kk) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= g.n_nodes) return;
+    int z = row / g.nxy, r = row - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
+    // CSR offsets: all rows of earlier layers, then earlier rows of this layer
     long long e0 = 0;
-    for (int zz = 0; zz < z; ++zz) e0 += (long long)tmpl_len[zz] * g.nxy;
-    e0 += (long long)(i - (z < g.nz ? z * g.nxy : g.n_atm)) * tmpl_len[z];
-    if (lane == 0) {
-        row_ptr[i] = (int32_t)e0;
-        if (i == g.n_nodes - 1) row_ptr[g.n_nodes] = (int32_t)(e0 + tmpl_len[z]);
+    for (int zz = 0; zz < z; ++zz) e0 += (long long)(gp.tstart[zz + 1] - gp.tstart[zz]) * g.nxy;
+    e0 += (long long)r * nt;
+    const long long vb = val_base(gp.voff[z], nt, r);
+    if (row_ptr) {
+        row_ptr[row] = (int32_t)e0;
+        if (row == g.n_nodes - 1) row_ptr[g.n_nodes] = (int32_t)(e0 + nt);
     }
-    int t0 = tmpl_start[z], n = tmpl_start[z + 1] - t0;
-    for (int t = lane; t < n; t += 32) {
-        int4 s = tmpl[t0 + t];  // (cls, sdx, sdy, sz)
-        int sx = wrap_small(x + s.y, g.nx), sy = wrap_small(y + s.z, g.ny);
-        int src = s.w >= 0 ? (s.w * g.ny + sy) * g.nx + sx : g.n_atm + sy * g.nx + sx;
-        col[e0 + t] = src;
-        code[e0 + t] = (uint16_t)s.x;
+    for (int t = 0; t < nt; ++t) {
+        int4 te = gp.tmpl[t0 + t];
+        const DClass &c = gp.cls[te.x];
+        if (col) col[e0 + t] = slot_src(g, row, x, y, te);
+        if (cval) cval[e0 + t] = val[vb + (long long)t * kGroup];
+        if (dir) dir[e0 + t] = c.hgdir;
+        if (kk) kk[e0 + t] = (int8_t)(c.kind == 1 ? 0 : c.kind == 2 ? 7 : c.k);
     }
 }
 
-void launch_expand(cudaStream_t st, const GridC &g, const int *tmpl_start, const int4 *tmpl, const int *tmpl_len,
-                   int32_t *row_ptr, int32_t *col, uint16_t *code) {
-    int threads = 256;
-    long long blocks = ((long long)g.n_nodes * 32 + threads - 1) / threads;
-    k_expand<<<(unsigned)blocks, threads, 0, st>>>(g, tmpl_start, tmpl, tmpl_len, row_ptr, col, code);
-}
-
-__global__ void k_slot_info(long long nnz, const uint16_t *code, const DClass *cls, int16_t *dir, int8_t *k, int nd) {
-    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nnz) return;
-    const DClass &c = cls[code[e]];
-    if (c.kind == 4) {
-        dir[e] = -1;
-        k[e] = -1;
-    } else {
-        dir[e] = c.hgdir;
-        k[e] = (int8_t)(c.kind == 1 ? 0 : c.kind == 2 ? 7 : c.k);
-    }
-    (void)nd;
-}
-
-void launch_slot_info(cudaStream_t st, long long nnz, const uint16_t *code, const DClass *cls, int16_t *dir,
-                      int8_t *k, int nd) {
-    k_slot_info<<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(nnz, code, cls, dir, k, nd);
+template <typename T>
+void launch_export_csr(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, int32_t *row_ptr,
+                       int32_t *col, T *cval, int16_t *dir, int8_t *k) {
+    k_export_csr<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, val, row_ptr, col, cval, dir, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -172,6 +156,10 @@ __global__ void k_prep(GridC g, FieldP<T> f) {
         }
         f.mu_st[i] = s;
         f.mu_e[i] = a + s;
+        f.rt[i] = dsqrt<T>(s);
+        T inv = s > T(0) ? T(1) / s : T(0);
+        for (int sp = 0; sp < g.S; ++sp)
+            f.wsp[(size_t)sp * g.n_atm + i] = s > T(0) ? f.mu_s[(size_t)sp * g.n_atm + i] * inv : T(1) / (T)g.S;
         m = (double)s;
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -180,36 +168,43 @@ __global__ void k_prep(GridC g, FieldP<T> f) {
 }
 
 // ---------------------------------------------------------------------------
-// Quadrature tables of the scene geometry: q^sun per species and direction
-// (HG-weighted Fibonacci cell fractions, FP64 sums in a fixed order), and the
-// HG values toward the instrument for every travel direction.
-// One block per species.
+// Quadrature tables of the scene geometry.  q^sun of species s and direction
+// u is the HG-weighted fraction of the Fibonacci lattice in the cell of u;
+// the sums are FP64 in a fixed order (one block per (cell, species)).
 
 template <typename T>
-__global__ void k_tables(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
-    extern __shared__ double cellsum[];  // [nd]
-    int sp = blockIdx.x;
+__global__ void k_tables_cells(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
+    __shared__ double red[32];
+    int u = blockIdx.x, sp = blockIdx.y;
     double gg = vc.g[sp];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int u = warp; u < g.nd; u += nw) {
-        double acc = 0.0;
-        for (int m = vp.cell_start[u] + lane; m < vp.cell_start[u + 1]; m += 32) {
-            const double *s = vp.lattice + 3 * (size_t)m;
-            double mu = vc.s0[0] * s[0] + vc.s0[1] * s[1] + vc.s0[2] * s[2];
-            acc += hg<double>(gg, mu);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) cellsum[u] = acc;
+    double acc = 0.0;
+    for (int m = vp.cell_start[u] + threadIdx.x; m < vp.cell_start[u + 1]; m += blockDim.x) {
+        const double *s = vp.lattice + 3 * (size_t)m;
+        double mu = vc.s0[0] * s[0] + vc.s0[1] * s[1] + vc.s0[2] * s[2];
+        acc += hg<double>(gg, mu);
     }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    __shared__ double total;
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int u = 0; u < g.nd; ++u) t += cellsum[u];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        f.cellsum[sp * g.nd + u] = t;
+    }
+}
+
+template <typename T>
+__global__ void k_tables_norm(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
+    __shared__ double total;
+    int sp = blockIdx.x;
+    double gg = vc.g[sp];
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int u = 0; u < g.nd; ++u) t += f.cellsum[sp * g.nd + u];
         total = t;
     }
     __syncthreads();
-    for (int u = threadIdx.x; u < g.nd; u += blockDim.x) f.q_sun[sp * g.nd + u] = (T)(cellsum[u] / total);
+    for (int u = threadIdx.x; u < g.nd; u += blockDim.x) f.q_sun[sp * g.nd + u] = (T)(f.cellsum[sp * g.nd + u] / total);
     int ndir = g.nd + g.ngd;
     for (int d = threadIdx.x; d < ndir; d += blockDim.x) {
         const double *h = vp.dirhat + 3 * d;
@@ -232,30 +227,14 @@ template <typename T>
 __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_nodes) return;
-    int x, y, Zs;
-    if (i < g.n_atm) {
-        int z = i / g.nxy, r = i - z * g.nxy;
-        y = r / g.nx;
-        x = r - y * g.nx;
-        Zs = z + 1;
-    } else {
-        int r = i - g.n_atm;
-        y = r / g.nx;
-        x = r - y * g.nx;
-        Zs = 0;
-    }
-    const T *len = nullptr;
+    int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    int Zs = i < g.n_atm ? z + 1 : 0;
+    const T *len;
     if constexpr (sizeof(T) == 4)
         len = (const T *)vp.sun_len_f;
     else
         len = (const T *)vp.sun_len_d;
-    int off = vp.sun_off[Zs], n = vp.sun_n[Zs];
-    T tau = T(0);
-    for (int t = 0; t < n; ++t) {
-        DTap tp = vp.sun_taps[off + t];
-        int xx = wrap_any(x + tp.dx, g.nx), yy = wrap_any(y + tp.dy, g.ny);
-        tau += len[off + t] * f.mu_e[(tp.dz * g.ny + yy) * g.nx + xx];
-    }
+    T tau = ray_sum<T>(g, vp.sun_taps, len, f.mu_e, vp.sun_off[Zs], vp.sun_n[Zs], x, y, 0);
     T Ts = dexp<T>(-tau);
     f.tsun[i] = Ts;
     T base = (T)(vc.f0 * vc.mu0 * g.hx * g.hy);
@@ -269,11 +248,33 @@ __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
 }
 
 // ---------------------------------------------------------------------------
+// Optical depth of the lattice segment from every voxel centre a to a + u, for
+// each canonical direction u (one of each pair {u, -u}); a segment traversed
+// backwards (-u, from a + u) reads the same entry.  One thread per (u, a);
+// entries whose end lies above the TOA are not used and are set to 0.
+
+template <typename T>
+__global__ void k_segtau(GridC g, GraphP gp, FieldP<T> f) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)g.nc * g.n_atm) return;
+    int c = (int)(t / g.n_atm), a = (int)(t - (long long)c * g.n_atm);
+    int u = gp.canon_dirs[c];
+    int4 d = gp.dirs[u];
+    int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    T tau = T(0);
+    if (z + d.z < g.nz) tau = tap_sum<T>(g, gp, f.mu_e, gp.lat_off[u], gp.lat_n[u], x, y, z);
+    f.tseg[t] = tau;
+}
+
+template <typename T>
+__device__ __forceinline__ T seg_at(const GridC &g, const T *__restrict__ tseg, int tab, int x, int y, int z) {
+    return __ldg(tseg + (size_t)tab * g.n_atm + (z * g.ny + wrap_small(y, g.ny)) * g.nx + wrap_small(x, g.nx));
+}
+
 // Optical depth from each voxel centre to the TOA along each upward lattice
 // direction, by recursion down the lattice lines:
 //   tau_inf(j, u) = tau(j -> j + u) + tau_inf(j + u, u).
 // One thread per (upward direction, start layer offset, column).
-
 template <typename T>
 __global__ void k_tinf(GridC g, GraphP gp, FieldP<T> f) {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,11 +292,11 @@ __global__ void k_tinf(GridC g, GraphP gp, FieldP<T> f) {
     T tau = tap_sum<T>(g, gp, f.mu_e, gp.top_off[ui * g.R + o], gp.top_n[ui * g.R + o], x, y, zt);
     T *out = f.tinf + (size_t)ui * g.n_atm;
     out[(zt * g.ny + y) * g.nx + x] = tau;
-    int loff = gp.lat_off[u], ln = gp.lat_n[u];
+    const int tab = gp.up_canon[ui];
     for (int z = zt - d.z; z >= 0; z -= d.z) {
         x = wrap_small(x - d.x, g.nx);
         y = wrap_small(y - d.y, g.ny);
-        tau += tap_sum<T>(g, gp, f.mu_e, loff, ln, x, y, z);
+        tau += seg_at<T>(g, f.tseg, tab, x, y, z);
         out[(z * g.ny + y) * g.nx + x] = tau;
     }
 }
@@ -307,42 +308,44 @@ __global__ void k_tinfg(GridC g, GraphP gp, FieldP<T> f) {
     if (t >= g.ngd * g.nxy) return;
     int gd = t / g.nxy, c = t - gd * g.nxy;
     int y = c / g.nx, x = c - y * g.nx;
-    f.tinfg[t] = tap_sum_far<T>(g, gp, f.mu_e, gp.gtop_off[gd], gp.gtop_n[gd], x, y, 0);
+    f.tinfg[t] = ray_sum<T>(g, gp.taps, tap_len<T>(gp), f.mu_e, gp.gtop_off[gd], gp.gtop_n[gd], x, y, 0);
 }
 
 // ---------------------------------------------------------------------------
 // Coupling normalisers (Eq. scatt_coup as a routing weight): for each source
 //   zc = sum_{U_c} q / sum_{U_c} q C   (0 when the coupling is off or the
-// denominator vanishes), so that c_{j,u} = C_{j,u} zc and sum_u q c = 1.
-// U_c: directions whose chain has a receiver other than the source.
+// denominator vanishes), so that c_{j,u} = C_{j,u} zc and sum_u q c = 1,
+// with C_{j,u} = sqrt(mu_s(j)) sqrt(mu_s(n1)) / d.  U_c: directions whose
+// chain has a receiver other than the source.
 
 template <typename T>
 __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= g.n_nodes) return;
-    T mus_lamb = (T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits));
+    const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     T sq_i = 0, sqc_i = 0, sq_s = 0, sqc_s = 0;
+    int z = j / g.nxy, r = j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    T rt_src;
     if (j < g.n_atm) {
-        int z = j / g.nxy, r = j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
-        T mus = f.mu_st[j];
+        rt_src = f.rt[j];
         T w[MAX_SPECIES];
-        for (int sp = 0; sp < g.S; ++sp)
-            w[sp] = mus > T(0) ? f.mu_s[(size_t)sp * g.n_atm + j] / mus : T(1) / (T)g.S;
+        for (int sp = 0; sp < g.S; ++sp) w[sp] = f.wsp[(size_t)sp * g.n_atm + j];
+#pragma unroll 2
         for (int u = 0; u < g.nd; ++u) {
             int4 d = gp.dirs[u];
             int rz = z + d.z;
-            T mun, dist;
+            T rtn, dist;
             if (rz >= 0 && rz < g.nz) {
-                mun = f.mu_st[(rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx)];
-                dist = (T)gp.dir_len[u];
+                rtn = __ldg(f.rt + (rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx));
+                dist = Cst<T>::dir_len(gp, u);
             } else if (d.z < 0) {
-                mun = mus_lamb;
-                dist = (T)((z + 0.5) / (double)(-d.z) * gp.dir_len[u]);
+                rtn = rt_lamb;
+                dist = ((T)z + T(0.5)) / (T)(-d.z) * Cst<T>::dir_len(gp, u);
             } else {
                 continue;
             }
-            T C = dsqrt<T>(mus * mun) / dist;
-            T qi = (T)gp.q_iso[u];
+            T C = rt_src * rtn / dist;
+            T qi = Cst<T>::q_iso(gp, u);
             T qs = T(0);
             for (int sp = 0; sp < g.S; ++sp) qs += w[sp] * f.q_sun[sp * g.nd + u];
             sq_i += qi;
@@ -351,132 +354,149 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
             sqc_s += qs * C;
         }
     } else {
-        int c = j - g.n_atm, y = c / g.nx, x = c - y * g.nx;
+        rt_src = rt_lamb;
         for (int gd = 0; gd < g.ngd; ++gd) {
             int4 m = gp.gmem1[gd];
-            T mun = f.mu_st[((m.z - 1) * g.ny + wrap_small(y + m.y, g.ny)) * g.nx + wrap_small(x + m.x, g.nx)];
-            T C = dsqrt<T>(mus_lamb * mun) / (T)gp.gdist1[gd];
-            T q = (T)gp.q_lamb[gd];
+            T rtn = f.rt[((m.z - 1) * g.ny + wrap_small(y + m.y, g.ny)) * g.nx + wrap_small(x + m.x, g.nx)];
+            T C = rt_src * rtn / Cst<T>::gdist1(gp, gd);
+            T q = Cst<T>::q_lamb(gp, gd);
             sq_i += q;
             sqc_i += q * C;
         }
         sq_s = sq_i;
         sqc_s = sqc_i;
     }
-    f.zc_iso[j] = (vc.coupling && sqc_i > T(0)) ? sq_i / sqc_i : T(0);
-    f.zc_sun[j] = (vc.coupling && sqc_s > T(0)) ? sq_s / sqc_s : T(0);
+    // stored premultiplied by sqrt(mu_s) of the source: c = a sqrt(mu_s(n1)) / d
+    f.a_iso[j] = (vc.coupling && sqc_i > T(0)) ? sq_i / sqc_i * rt_src : T(0);
+    f.a_sun[j] = (vc.coupling && sqc_s > T(0)) ? sq_s / sqc_s * rt_src : T(0);
 }
 
 // ---------------------------------------------------------------------------
-// Fused edge march + edge weights: one warp per receiver row.  For every slot
-// the optical depths of the chain segments come from the translation-
-// invariant tap tables; the deposit fraction P, the quadrature weight q and
-// the coupling c of the source give
-//   K_ij = rho_i q_{j,u} c_{j,u} P          (stored, CSR order)
+// Fused edge march + edge weights: one thread per receiver row, the warp
+// walking the row template in lockstep.  For every slot the optical depths of
+// the chain segments come from the translation-invariant tap tables; the
+// deposit fraction P, the quadrature weight q and the coupling c of the
+// source give
+//   K_ij = rho_i q_{j,u} c_{j,u} P          (stored slot-major)
 //   s_i  = sum_slots rho_i q^sun c^sun P e1_j
 //   g_i  = sum_slots Theta_i(u . v) rho_i q^sun c^sun P e1_j   (atmospheric rows)
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_assemble(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= g.n_nodes) return;
-    const int e0 = gp.row_ptr[row], e1 = gp.row_ptr[row + 1];
+    const int z = row / g.nxy, r = row - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
+    T *vrow = f.val + val_base(gp.voff[z], nt, r);
     const T mus_lamb = (T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits));
     const int ndir = g.nd + g.ngd;
+    const bool ground_row = row >= g.n_atm;
     T rho, wr[MAX_SPECIES];
-    if (row < g.n_atm) {
+    if (!ground_row) {
         T me = f.mu_e[row], ms = f.mu_st[row];
         rho = me > T(0) ? ms / me : T(0);
-        for (int sp = 0; sp < g.S; ++sp)
-            wr[sp] = ms > T(0) ? f.mu_s[(size_t)sp * g.n_atm + row] / ms : T(1) / (T)g.S;
+        for (int sp = 0; sp < g.S; ++sp) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
     } else {
         rho = (T)vc.albedo;
         for (int sp = 0; sp < g.S; ++sp) wr[sp] = T(0);
     }
     T acc_s = T(0), acc_g = T(0);
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const int j = gp.col[e];
-        const DClass c = gp.cls[gp.code[e]];
-        if (c.kind == 4) {  // padding
-            f.val[e] = T(0);
-            continue;
-        }
-        int bx, by, bz;
-        if (j < g.n_atm) {
-            bz = j / g.nxy;
-            int r = j - bz * g.nxy;
-            by = r / g.nx;
-            bx = r - by * g.nx;
-        } else {
-            int r = j - g.n_atm;
-            by = r / g.nx;
-            bx = r - by * g.nx;
-            bz = 0;
-        }
-        T tpre = c.pre_n ? tap_sum<T>(g, gp, f.mu_e, c.pre_off, c.pre_n, bx, by, bz) : T(0);
-        T tseg = c.seg_n ? tap_sum<T>(g, gp, f.mu_e, c.seg_off, c.seg_n, bx, by, bz) : T(0);
-        T thit = c.hit_n ? tap_sum<T>(g, gp, f.mu_e, c.hit_off, c.hit_n, bx, by, bz) : T(0);
+    const T rt_lamb = dsqrt<T>(mus_lamb);
+    for (int t = 0; t < nt; ++t) {
+        const int4 te = __ldg(gp.tmpl + t0 + t);
+        const PClass *pc = gp.pcls + te.x;
+        const int4 w0 = __ldg(&pc->w0), w1 = __ldg(&pc->w1);
+        const int kind = w0.x & 0xff, bkind = (w0.x >> 8) & 0xff;
+        const bool c_one = (w0.x >> 16) & 0xff, n1_ground = (w0.x >> 24) & 0xff;
+        const int dir = w0.y & 0xffff, hgdir = (w0.y >> 16) & 0xffff;
+        const int up_idx = w0.z & 0xffff, gdir = (w0.z >> 16) & 0xffff;
+        const int sz = te.w;
+        const int bx = wrap_small(x + tmpl_sdx(te), g.nx), by = wrap_small(y + tmpl_sdy(te), g.ny);
+        const int bz = sz >= 0 ? sz : 0;
+        const int j = sz >= 0 ? (sz * g.ny + by) * g.nx + bx : g.n_atm + by * g.nx + bx;
+        // optical depths: full lattice segments from the table, partial ones from taps
+        T tpre = T(0), tseg = T(0), thit = T(0);
+        const int seg_tab = (w1.x & 0xff) - 1, pre_tab = (w1.y & 0xff) - 1;
+        int4 w2 = make_int4(0, 0, 0, 0);
+        const bool need_taps = seg_tab < 0 || pre_tab < 0;  // a segment given by taps, or none
+        if (need_taps) w2 = __ldg(&pc->w2);
+        if (pre_tab >= 0)
+            tpre = seg_at<T>(g, f.tseg, pre_tab, bx + sbyte(w1.y, 8), by + sbyte(w1.y, 16), bz + sbyte(w1.y, 24));
+        else if (w2.w & 0xff)
+            tpre = tap_sum<T>(g, gp, f.mu_e, w2.x, w2.w & 0xff, bx, by, bz);
+        if (seg_tab >= 0)
+            tseg = seg_at<T>(g, f.tseg, seg_tab, bx + sbyte(w1.x, 8), by + sbyte(w1.x, 16), bz + sbyte(w1.x, 24));
+        else if ((w2.w >> 8) & 0xff)
+            tseg = tap_sum<T>(g, gp, f.mu_e, w2.y, (w2.w >> 8) & 0xff, bx, by, bz);
+        if ((w2.w >> 16) & 0xff) thit = tap_sum<T>(g, gp, f.mu_e, w2.z, (w2.w >> 16) & 0xff, bx, by, bz);
         T P;
-        if (c.kind == 0 || c.kind == 3) {  // chain node (atmospheric or ground source)
-            T ep = dexp<T>(-tpre);
-            if (c.bkind == 0) {
+        if (kind == 0 || kind == 3) {  // chain node (atmospheric or ground source)
+            const bool has_pre = pre_tab >= 0 || (w2.w & 0xff);
+            const T ep = has_pre ? dexp<T>(-tpre) : T(1);
+            if (bkind == 0) {
                 P = ep * (-dexpm1<T>(-tseg));
-            } else if (c.bkind == 1) {
+            } else if (bkind == 1) {
                 P = ep;
             } else {
-                T tb = c.bkind == 2 ? f.tinf[(size_t)c.up_idx * g.n_atm + row]
-                                    : (c.bkind == 3 ? thit : f.tinfg[(size_t)c.gdir * g.nxy + (j - g.n_atm)]);
+                T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row]
+                                  : (bkind == 3 ? thit : f.tinfg[(size_t)gdir * g.nxy + (j - g.n_atm)]);
                 P = ep * (-dexpm1<T>(-(tseg + tb)));
             }
-        } else if (c.kind == 1) {  // self deposit
-            T tb = c.bkind == 2 ? f.tinf[(size_t)c.up_idx * g.n_atm + row] : thit;
+        } else if (kind == 1) {  // self deposit
+            T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row] : thit;
             P = -dexpm1<T>(-tb);
         } else {  // ground hit
-            P = (T)c.split * dexp<T>(-(tpre + thit));
-        }
-        T Wi, Ws;
-        if (j < g.n_atm) {
-            T mus = f.mu_st[j];
-            T qi = (T)gp.q_iso[c.dir], qs = T(0);
-            for (int sp = 0; sp < g.S; ++sp) {
-                T w = mus > T(0) ? f.mu_s[(size_t)sp * g.n_atm + j] / mus : T(1) / (T)g.S;
-                qs += w * f.q_sun[sp * g.nd + c.dir];
+            T split;
+            if constexpr (sizeof(T) == 4) {
+                split = __int_as_float(w1.w);
+            } else {
+                const int4 w3 = __ldg(&pc->w3);
+                split = __hiloint2double(w3.w, w3.z);
             }
+            P = split * dexp<T>(-(tpre + thit));
+        }
+        // quadrature weight x coupling of the source
+        T dinv;
+        if constexpr (sizeof(T) == 4) {
+            dinv = __int_as_float(w0.w);
+        } else {
+            const int4 w3 = __ldg(&pc->w3);
+            dinv = __hiloint2double(w3.y, w3.x);
+        }
+        const int n1dx = sbyte(w1.z, 0), n1dy = sbyte(w1.z, 8), n1dz = sbyte(w1.z, 16);
+        T Wi, Ws;
+        if (sz >= 0) {
+            T qi = Cst<T>::q_iso(gp, dir), qs = T(0);
+            for (int sp = 0; sp < g.S; ++sp) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * f.q_sun[sp * g.nd + dir];
             T ci = T(1), cs = T(1);
-            if (!c.c_one) {
-                T mun = c.n1_ground ? mus_lamb
-                                    : f.mu_st[((bz + c.n1_dz) * g.ny + wrap_small(by + c.n1_dy, g.ny)) * g.nx +
-                                              wrap_small(bx + c.n1_dx, g.nx)];
-                T C = dsqrt<T>(mus * mun) * (T)c.dist1_inv;
-                T zi = f.zc_iso[j], zs = f.zc_sun[j];
-                ci = zi > T(0) ? C * zi : T(1);
-                cs = zs > T(0) ? C * zs : T(1);
+            if (!c_one) {
+                T rtn = n1_ground ? rt_lamb
+                                  : __ldg(f.rt + ((bz + n1dz) * g.ny + wrap_small(by + n1dy, g.ny)) * g.nx +
+                                          wrap_small(bx + n1dx, g.nx));
+                T ai = __ldg(f.a_iso + j), as = __ldg(f.a_sun + j);
+                ci = ai > T(0) ? ai * rtn * dinv : T(1);
+                cs = as > T(0) ? as * rtn * dinv : T(1);
             }
             Wi = qi * ci;
             Ws = qs * cs;
         } else {
-            T mun = f.mu_st[(c.n1_dz * g.ny + wrap_small(by + c.n1_dy, g.ny)) * g.nx + wrap_small(bx + c.n1_dx, g.nx)];
-            T C = dsqrt<T>(mus_lamb * mun) * (T)c.dist1_inv;
-            T z = f.zc_iso[j];
-            T cc = z > T(0) ? C * z : T(1);
-            Wi = (T)gp.q_lamb[c.gdir] * cc;
+            T rtn = __ldg(f.rt + (n1dz * g.ny + wrap_small(by + n1dy, g.ny)) * g.nx + wrap_small(bx + n1dx, g.nx));
+            T a = __ldg(f.a_iso + j);
+            T cc = a > T(0) ? a * rtn * dinv : T(1);
+            Wi = Cst<T>::q_lamb(gp, gdir) * cc;
             Ws = Wi;
         }
-        f.val[e] = rho * Wi * P;
-        T sun = rho * Ws * P * f.e1[j];
+        vrow[(size_t)t * kGroup] = rho * Wi * P;
+        T sun = rho * Ws * P * __ldg(f.e1 + j);
         acc_s += sun;
-        T th = T(0);
-        for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + c.hgdir];
-        acc_g += th * sun;
+        if (!ground_row) {
+            T th = T(0);
+            for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + hgdir];
+            acc_g += th * sun;
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        acc_s += __shfl_xor_sync(0xffffffffu, acc_s, o);
-        acc_g += __shfl_xor_sync(0xffffffffu, acc_g, o);
-    }
-    if (lane == 0) {
-        f.s[row] = acc_s;
-        if (row < g.n_atm) f.gsun[row] = acc_g;
-    }
+    f.s[row] = acc_s;
+    if (!ground_row) f.gsun[row] = acc_g;
 }
 
 template <typename T>
@@ -485,21 +505,22 @@ void launch_assemble_pre(cudaStream_t st, const GridC &g, const GraphP &gp, cons
     const int th = 256;
     cudaMemsetAsync(f.mus_max_bits, 0, sizeof(unsigned long long), st);
     k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st>>>(g, f);
-    k_tables<T><<<g.S, 256, sizeof(double) * g.nd, st>>>(g, f, vc, vp);
-    k_sun<T><<<(g.n_nodes + th - 1) / th, th, 0, st>>>(g, f, vc, vp);
+    k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st>>>(g, f, vc, vp);
+    k_tables_norm<T><<<g.S, 128, 0, st>>>(g, f, vc, vp);
+    k_sun<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, f, vc, vp);
+    long long ns = (long long)g.nc * g.n_atm;
+    k_segtau<T><<<(unsigned)((ns + th - 1) / th), th, 0, st>>>(g, gp, f);
     long long nt = (long long)g.nup * g.R * g.nxy;
     k_tinf<T><<<(unsigned)((nt + th - 1) / th), th, 0, st>>>(g, gp, f);
-    k_tinfg<T><<<(g.ngd * g.nxy + th - 1) / th, th, 0, st>>>(g, gp, f);
-    k_znorm<T><<<(g.n_nodes + th - 1) / th, th, 0, st>>>(g, gp, f, vc);
-    if (launches) *launches += 6;
+    k_tinfg<T><<<(g.ngd * g.nxy + 127) / 128, 128, 0, st>>>(g, gp, f);
+    k_znorm<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
+    if (launches) *launches += 8;
 }
 
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                           long long *launches) {
-    const int th = 256;
-    long long nthr = (long long)g.n_nodes * 32;
-    k_assemble<T><<<(unsigned)((nthr + th - 1) / th), th, 0, st>>>(g, gp, f, vc);
+    k_assemble<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
     if (launches) *launches += 1;
 }
 
@@ -507,7 +528,9 @@ void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, con
     template void launch_assemble_pre<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
                                          const ViewC &, const ViewP &, long long *);                              \
     template void launch_assemble_rows<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,         \
-                                          const ViewC &, long long *);
+                                          const ViewC &, long long *);                                            \
+    template void launch_export_csr<T>(cudaStream_t, const GridC &, const GraphP &, const T *, int32_t *,         \
+                                       int32_t *, T *, int16_t *, int8_t *);
 INST(float)
 INST(double)
 #undef INST

@@ -34,29 +34,42 @@ __device__ __forceinline__ int rwrap(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-// one warp per atmospheric receiver row
+// Rows in groups of 32 (one per lane) shared by kEmSplit warps, each summing
+// every kEmSplit-th slot of the template; partials combined in a fixed order.
+constexpr int kEmSplit = 4;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_emission(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const double *x,
-                                                  T *emis) {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= g.n_atm) return;
+__global__ void __launch_bounds__(32 * kEmSplit) k_emission(GridC g, GraphP gp, FieldP<T> f, ViewC vc,
+                                                            const double *x, T *emis) {
+    __shared__ T sh[kEmSplit][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * 32 + lane;
+    const bool live = row < g.n_atm;
     const int ndir = g.nd + g.ngd;
-    T ms = f.mu_st[row];
-    T wr[MAX_SPECIES];
-    for (int sp = 0; sp < g.S; ++sp) wr[sp] = ms > T(0) ? f.mu_s[(size_t)sp * g.n_atm + row] / ms : T(1) / (T)g.S;
     T acc = T(0);
-    const int e0 = gp.row_ptr[row], e1 = gp.row_ptr[row + 1];
-    for (int e = e0 + lane; e < e1; e += 32) {
-        const DClass &c = gp.cls[gp.code[e]];
-        T th = T(0);
-        for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + c.hgdir];
-        acc += th * f.val[e] * (T)x[gp.col[e]];
+    T wr[MAX_SPECIES];
+    if (live) {
+        const int z = row / g.nxy, r = row - z * g.nxy, yy = r / g.nx, xx = r - yy * g.nx;
+        const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
+        const T *v = f.val + val_base(gp.voff[z], nt, r);
+        for (int sp = 0; sp < g.S; ++sp) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
+        for (int t = w; t < nt; t += kEmSplit) {
+            const int4 te = __ldg(gp.tmpl + t0 + t);
+            const int hgd = gp.cls[te.x].hgdir;
+            T th = T(0);
+            for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + hgd];
+            const int j = slot_src(g, row, xx, yy, te);
+            acc += th * v[(size_t)t * kGroup] * (T)x[j];
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
+    sh[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && live) {
+        T tot = T(0);
+        for (int k = 0; k < kEmSplit; ++k) tot += sh[k][lane];
         T th0 = T(0);
         for (int sp = 0; sp < g.S; ++sp) th0 += wr[sp] * f.hg0v[sp];
-        emis[row] = f.e1[row] * th0 + f.gsun[row] + acc;
+        emis[row] = f.e1[row] * th0 + f.gsun[row] + tot;
     }
 }
 
@@ -74,13 +87,23 @@ __global__ void k_pixels(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__re
     int off = vp.los_off[cl], n = vp.los_n[cl];
     const T inv_vol = (T)(1.0 / (g.hx * g.hy * g.hz));
     T tau = T(0), L = T(0);
-    for (int t = 0; t < n; ++t) {
-        DTap tp = vp.los_taps[off + t];
-        int idx = (tp.dz * g.ny + rwrap(cy + tp.dy, g.ny)) * g.nx + rwrap(cx + tp.dx, g.nx);
-        T me = f.mu_e[idx], ds = len[off + t];
-        T fr = me > T(0) ? -rexpm1<T>(-me * ds) / me : ds;
-        L += rexp<T>(-tau) * fr * emis[idx] * inv_vol;
-        tau += me * ds;
+    if (n > 0) {
+        // taps run along the ray: wrap the first column once, then follow it
+        DTap prev = vp.los_taps[off];
+        int xw = rwrap(cx + prev.dx, g.nx), yw = rwrap(cy + prev.dy, g.ny);
+        for (int t = 0; t < n; ++t) {
+            DTap tp = vp.los_taps[off + t];
+            xw += tp.dx - prev.dx;
+            xw = xw < 0 ? xw + g.nx : (xw >= g.nx ? xw - g.nx : xw);
+            yw += tp.dy - prev.dy;
+            yw = yw < 0 ? yw + g.ny : (yw >= g.ny ? yw - g.ny : yw);
+            prev = tp;
+            int idx = (tp.dz * g.ny + yw) * g.nx + xw;
+            T me = f.mu_e[idx], ds = len[off + t];
+            T fr = me > T(0) ? -rexpm1<T>(-me * ds) / me : ds;
+            L += rexp<T>(-tau) * fr * emis[idx] * inv_vol;
+            tau += me * ds;
+        }
     }
     int c = g.n_atm + cy * g.nx + cx;
     L += rexp<T>(-tau) * (f.e1[c] + (T)x[c]) * (T)(1.0 / (3.14159265358979323846 * g.hx * g.hy));
@@ -91,8 +114,7 @@ __global__ void k_pixels(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__re
 template <typename T>
 void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                      const double *x, T *emis) {
-    long long th = (long long)g.n_atm * 32;
-    k_emission<T><<<(unsigned)((th + 255) / 256), 256, 0, st>>>(g, gp, f, vc, x, emis);
+    k_emission<T><<<(g.n_atm + 31) / 32, 32 * kEmSplit, 0, st>>>(g, gp, f, vc, x, emis);
 }
 
 template <typename T>

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libtursca_gb.so")
 
 FP64, FP32_REFINE = 0, 1
 COUPLING_NONE, COUPLING_WEIGHT = 0, 1
-SOLVER_AUTO, SOLVER_NEUMANN, SOLVER_GMRES = 0, 1, 2
+SOLVER_AUTO, SOLVER_NEUMANN, SOLVER_GMRES, SOLVER_CHEBYSHEV = 0, 1, 2, 3
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_STATE, E_UNSUPPORTED = range(8)
 
@@ -93,6 +93,7 @@ def lib() -> C.CDLL:
             "tursca_graph_structure": (st, [C.POINTER(tursca_grid_desc), _vp, _vp, _vp, _vp]),
             "tursca_quadrature": (st, [C.POINTER(tursca_grid_desc), _vp, _vp]),
             "tursca_profile_enable": (st, [_vp, C.c_int]),
+            "tursca_set_option": (st, [_vp, C.c_int, C.c_double]),
             "tursca_profile_read": (st, [_vp, C.POINTER(tursca_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
             "tursca_csr_solve_noalloc": (st, [_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp]),
             "tursca_status_string": (C.c_char_p, [C.c_int]),
@@ -178,6 +179,13 @@ def tursca_get(scene, which: int, dst, nbytes: int):
 
 def tursca_launch_count(scene) -> int:
     return int(lib().tursca_launch_count(scene))
+
+
+OPT_RESIDUAL_FP64 = 1
+
+
+def tursca_set_option(scene, option: int, value: float):
+    _check(scene, lib().tursca_set_option(scene, int(option), float(value)))
 
 
 def tursca_profile_enable(scene, on: bool):
