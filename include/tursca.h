@@ -208,7 +208,7 @@ long long tursca_launch_count(const tursca_scene *scene);
 /* Per-kernel device time measured with CUDA events recorded on the scene's
  * stream around each launch of the hot kernels (profiling only). */
 typedef struct {
-    char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render" */
+    char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb" */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;

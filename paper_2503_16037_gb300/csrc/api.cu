@@ -82,9 +82,9 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render"};
-constexpr int kNProf = 5;
-enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4 };
+const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb"};
+constexpr int kNProf = 6;
+enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5 };
 
 // returns the index of the pair, or -1 when profiling is off
 int prof_begin(tursca_scene *sc, int cat) {
@@ -596,7 +596,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             double rk = 1.0 / cp.sigma;
             for (int k = 0; k < nc; ++k) {
                 double rk1 = 1.0 / (2.0 * cp.sigma - rk);
-                int pi = prof_begin(sc, P_SPMV);
+                int pi = prof_begin(sc, P_CHEB);
                 tk::launch_cheb<T>(sc->st, g, gp, (const T *)sc->val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta);
                 prof_end(sc, pi);
                 std::swap(p0, p1);
@@ -1102,8 +1102,8 @@ tursca_status tursca_profile_enable(tursca_scene *sc, int on) {
 tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int n, int *n_out) {
     if (!sc || !out || n < 0) return fail(sc, TURSCA_E_INVALID, "bad arguments");
     CK(cudaStreamSynchronize(sc->st), "sync");
-    double ms[kNProf] = {0, 0, 0, 0, 0};
-    long long cnt[kNProf] = {0, 0, 0, 0, 0};
+    double ms[kNProf] = {0, 0, 0, 0, 0, 0};
+    long long cnt[kNProf] = {0, 0, 0, 0, 0, 0};
     for (size_t i = 0; i < sc->ev_used; ++i) {
         float t = 0.f;
         CK(cudaEventElapsedTime(&t, sc->ev[2 * i], sc->ev[2 * i + 1]), "event time");
