@@ -59,9 +59,12 @@ def traffic_record(kernel: str):
     summary's source hash matches the kernel source as it is now."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_2503_16037_gb300", "csrc", "kernels_solve.cu")
+    csrc = os.path.join(ROOT, "paper_2503_16037_gb300", "csrc")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in ("kernels_solve.cu", "stage.cuh", "kern.h"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        sha = h.hexdigest()[:16]
         for line in open(path):
             parts = line.split()
             if len(parts) >= 3 and parts[0] == kernel and parts[1] == sha:
@@ -227,26 +230,40 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    T.tursca_profile_enable(rn.handle, True)
+    # per-kernel CUDA events are recorded on every PROF_EVERY-th timed step only:
+    # an event pair around each launch drains the stream between kernels
+    # (about 4 us per launch), which would slow every step if always on
+    PROF_EVERY = 8
     l0 = rn.launches()
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     iters = []
+    prof = {}
+    prof_steps = []
     for k in range(args.steps):
+        profiled = k % PROF_EVERY == 0
+        if profiled:
+            T.tursca_profile_enable(rn.handle, True)
         flush.zero_()
         ev0[k].record(stream)
         step()
         ev1[k].record(stream)
+        if profiled:
+            for name, (n, ms) in T.tursca_profile_read(rn.handle).items():
+                a = prof.setdefault(name, [0, 0.0])
+                a[0] += n
+                a[1] += ms
+            T.tursca_profile_enable(rn.handle, False)
+            prof_steps.append(k)
         iters.append((rn.info.iters, rn.info.refinements, rn.info.rho_est, rn.info.rel_resid64))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     launches = rn.launches() - l0
-    prof = T.tursca_profile_read(rn.handle)
-    T.tursca_profile_enable(rn.handle, False)
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = sum(step_ms)
+    prof_ms = sum(step_ms[k] for k in prof_steps)
     if dist:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -289,10 +306,9 @@ def main():
     peak, peak_kind = peaks()
     n_sp, ms_sp = prof.get("cheb", (0, 0.0))
     kernels = {}
-    tot_prof = sum(v[1] for v in prof.values())
     for name, (n, ms) in prof.items():
         if n:
-            kernels[name] = {"launches": n, "avg_us": 1000.0 * ms / n, "share_of_step": ms / total_ms * world}
+            kernels[name] = {"launches": n, "avg_us": 1000.0 * ms / n, "share_of_step": ms / prof_ms}
     # 4 B per stored value (columns are implicit), per row: p gathered (4),
     # r read + written (8), d read + written (8), new p written (4)
     spmv_bytes = st.nnz * 4 + st.n_nodes * 24
@@ -300,10 +316,11 @@ def main():
     if n_sp:
         avg_s = ms_sp / n_sp / 1000.0
         ach = spmv_bytes / avg_s / 1e9
-        roof = {"kernel": "k_cheb4 (FP32 Chebyshev step: q = K p over the CSR rows)", "bound": "hbm", "achieved": ach,
+        roof = {"kernel": "k_plain<W, float, OpCheb<float>> (FP32 Chebyshev step: q = K p over the rows of K, "
+                          "then r, d, p updated per row)", "bound": "hbm", "achieved": ach,
                 "peak": peak,
                 "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
-                "traffic": traffic_record("k_cheb4"), "algorithmic_bytes_per_launch": spmv_bytes,
+                "traffic": traffic_record("k_plain_OpCheb"), "algorithmic_bytes_per_launch": spmv_bytes,
                 "avg_launch_us": avg_s * 1e6}
     # ---- accuracy of this run against the FP64 oracle (also the CPU baseline)
     cpu = None
@@ -330,6 +347,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scenes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "kernel_timing": "CUDA events around each launch on the scene stream, on every %dth timed step (%d steps)"
+                         % (PROF_EVERY, len(prof_steps)),
         "clocks": clocks,
         "parity": parity,
         "solve": {"iters": it[0], "refinements": it[1], "rho_est": it[2], "rel_resid64": it[3]},

@@ -198,8 +198,23 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *   TURSCA_OPT_RESIDUAL_FP64: 0 (default) evaluates the refinement residual of
  *     FP32_REFINE scenes in FP32-pair arithmetic (exact products by FMA and
  *     compensated sums, about 48 significant bits; FP64 arithmetic runs at a
- *     small fraction of the FP32 rate on GB300); 1 uses FP64 arithmetic. */
-enum { TURSCA_OPT_RESIDUAL_FP64 = 1 };
+ *     small fraction of the FP32 rate on GB300); 1 uses FP64 arithmetic.
+ *   TURSCA_OPT_GROUP_WARPS: warps that share each group of 128 rows in the
+ *     sweep, Chebyshev, residual and emission passes: 4, 6, 8 or 16 (the
+ *     streamed passes take 4, 8 or 16), or 0 to let the library pick
+ *     (default: 4 for the solver passes and 6 for the emission pass, 16 for
+ *     the streamed passes).
+ *   TURSCA_OPT_STAGE_VALUES: 0 (default) runs one block per group of 128
+ *     rows that reads the matrix values directly; 1 runs the FP32 sweep,
+ *     Chebyshev, residual and emission passes as persistent kernels (one
+ *     block per SM, each streaming an equal share of the values) in which
+ *     one warp copies the values into a ring of shared-memory stages with
+ *     bulk asynchronous copies while the other warps compute.  Both sum the
+ *     same products in the same order for the same TURSCA_OPT_GROUP_WARPS.
+ *     A copy that does not land within about a second makes the solve
+ *     return TURSCA_E_TIMEOUT.
+ */
+enum { TURSCA_OPT_RESIDUAL_FP64 = 1, TURSCA_OPT_GROUP_WARPS = 2, TURSCA_OPT_STAGE_VALUES = 3 };
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 
 /* Number of kernel launches the scene has issued since creation. */

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libtursca_gb.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "api.cu", "noalloc.cu"]
-HEADERS = ["graph.h", "kern.h"]
+HEADERS = ["graph.h", "kern.h", "stage.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

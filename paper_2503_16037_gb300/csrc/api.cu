@@ -53,6 +53,10 @@ struct tursca_scene {
     double *lattice = nullptr, *dirhat = nullptr;
     int *cell_start = nullptr;
     int *canon_dirs = nullptr, *up_canon = nullptr;
+    int *tflat = nullptr;  // template offsets in the haloed layout
+    int *run_g[2] = {nullptr, nullptr};  // runs of the persistent streamed passes
+    long long *run_v[2] = {nullptr, nullptr};
+    int run_n[2] = {0, 0};
     // view
     tk::DTap *sun_taps = nullptr, *los_taps = nullptr;
     float *sun_lf = nullptr, *los_lf = nullptr;
@@ -74,6 +78,12 @@ struct tursca_scene {
     float *xh = nullptr, *xl = nullptr;  // double-single split of x
     int gm_m = 0;
     int resid_fp64 = 0;  // 1: evaluate the refinement residual with FP64 arithmetic
+    int stage_values = 0;  // 1: FP32 passes stream the values through shared memory (persistent kernels)
+    int wq = 8;          // warps per 128-row group of the row-group passes
+    bool wq_auto = true;  // wq chosen by the library (else set by the caller)
+    // auxiliary streams and events for the concurrent per-scene tables
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     // event timing of the hot kernels
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // pairs
@@ -165,6 +175,16 @@ tk::GridC grid_c(const tursca_scene *sc) {
     g.nup = (int)G.up_dirs.size();
     g.R = sc->d.stencil_radius;
     g.nc = (int)G.canon_dirs.size();
+    g.wq = sc->wq;
+    g.wq_em = sc->wq_auto ? (sc->stage_values && sc->d.precision != TURSCA_FP64 ? 16 : 6) : sc->wq;
+    g.gpl = (g.nxy + tk::kGroup - 1) / tk::kGroup;
+    g.ntmax = G.max_row;
+    g.H = sc->d.stencil_radius;
+    g.nxp = g.nx + 2 * g.H;
+    g.nyp = g.ny + 2 * g.H;
+    g.lp = g.nxp * g.nyp;
+    g.npad = (long long)(g.nz + 1) * g.lp;
+    g.stage = (sc->stage_values && sc->d.precision != TURSCA_FP64 && tk::stage_fits(G.max_row)) ? 1 : 0;
     g.hx = sc->d.hx;
     g.hy = sc->d.hy;
     g.hz = sc->d.hz;
@@ -200,6 +220,13 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.gtop_n = sc->gtop_n;
     p.canon_dirs = sc->canon_dirs;
     p.up_canon = sc->up_canon;
+    p.status = sc->status;
+    p.tflat = sc->tflat;
+    for (int k = 0; k < 2; ++k) {
+        p.run_g[k] = sc->run_g[k];
+        p.run_v[k] = sc->run_v[k];
+        p.run_n[k] = sc->run_n[k];
+    }
     return p;
 }
 
@@ -317,18 +344,25 @@ tursca_status ensure_fields(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->musmax, sizeof(unsigned long long)), "alloc musmax");
     CK(dalloc(sc->allocs, sc->status, sizeof(int)), "alloc status");
     CK(cudaMemsetAsync(sc->status, 0, sizeof(int), sc->st), "memset status");
-    CK(dalloc(sc->allocs, sc->x64, nn * sizeof(double)), "alloc x");
-    CK(dalloc(sc->allocs, sc->r64, nn * sizeof(double)), "alloc r");
-    // block partial sums: the residual writes one per 32 rows, the power sweeps two
-    // columns of one per 32 rows, the dot products up to 64 x 296
-    CK(dalloc(sc->allocs, sc->part, std::max<size_t>(64 * 1024, nn / 16 + 64) * sizeof(double)), "alloc part");
+    // solver vectors live in the haloed layout (border of stencil_radius)
+    const size_t H = (size_t)sc->d.stencil_radius;
+    const size_t np = (size_t)(sc->d.nz + 1) * (sc->d.nx + 2 * H) * (sc->d.ny + 2 * H);
+    CK(dalloc(sc->allocs, sc->x64, np * sizeof(double)), "alloc x");
+    CK(dalloc(sc->allocs, sc->r64, np * sizeof(double)), "alloc r");
+    // partial sums: the residual writes one per row block (4 per group of 128
+    // rows), the power sweeps two columns of those, the dot products up to 64 x 296
+    {
+        const size_t groups = (size_t)(sc->d.nz + 1) * (((size_t)sc->d.nx * sc->d.ny + tk::kGroup - 1) / tk::kGroup);
+        CK(dalloc(sc->allocs, sc->part, std::max<size_t>(64 * 1024, 8 * groups + 64) * sizeof(double)),
+           "alloc part");
+    }
     CK(dalloc(sc->allocs, sc->dred, 256 * sizeof(double)), "alloc red");
-    CK(dalloc(sc->allocs, sc->b, nn * es), "alloc b");
-    CK(dalloc(sc->allocs, sc->d0, nn * es), "alloc d0");
-    CK(dalloc(sc->allocs, sc->d1, nn * es), "alloc d1");
-    CK(dalloc(sc->allocs, sc->w, nn * es), "alloc w");
-    CK(dalloc(sc->allocs, sc->xh, nn * sizeof(float)), "alloc xh");
-    CK(dalloc(sc->allocs, sc->xl, nn * sizeof(float)), "alloc xl");
+    CK(dalloc(sc->allocs, sc->b, np * es), "alloc b");
+    CK(dalloc(sc->allocs, sc->d0, np * es), "alloc d0");
+    CK(dalloc(sc->allocs, sc->d1, np * es), "alloc d1");
+    CK(dalloc(sc->allocs, sc->w, np * es), "alloc w");
+    CK(dalloc(sc->allocs, sc->xh, np * sizeof(float)), "alloc xh");
+    CK(dalloc(sc->allocs, sc->xl, np * sizeof(float)), "alloc xl");
     if (!sc->hred) {
         cudaError_t e = cudaMallocHost((void **)&sc->hred, 256 * sizeof(double));
         if (e != cudaSuccess) return cuda_fail(sc, e, "alloc pinned");
@@ -363,7 +397,11 @@ struct SolveState {
 template <typename T>
 tursca_status read_red(tursca_scene *sc, int n) {
     CK(cudaMemcpyAsync(sc->hred, sc->dred, n * sizeof(double), cudaMemcpyDeviceToHost, sc->st), "d2h");
+    // the status word rides along: a bounded wait that gave up shows here
+    int *hst = (int *)(sc->hred + 255);
+    CK(cudaMemcpyAsync(hst, sc->status, sizeof(int), cudaMemcpyDeviceToHost, sc->st), "d2h");
     CK(cudaStreamSynchronize(sc->st), "sync");
+    if (*hst & tk::STATUS_TIMEOUT) return fail(sc, TURSCA_E_TIMEOUT, "a bounded device wait gave up");
     return TURSCA_OK;
 }
 
@@ -371,7 +409,7 @@ tursca_status read_red(tursca_scene *sc, int n) {
 template <typename T>
 T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, int n, SolveState &ss) {
     T *cur = (T *)sc->d0, *nxt = (T *)sc->d1;
-    cudaMemcpyAsync(cur, b, (size_t)g.n_nodes * sizeof(T), cudaMemcpyDeviceToDevice, sc->st);  // checked at the next sync
+    cudaMemcpyAsync(cur, b, (size_t)g.npad * sizeof(T), cudaMemcpyDeviceToDevice, sc->st);  // checked at the next sync
     for (int it = 0; it < n; ++it) {
         int pi = prof_begin(sc, P_SPMV);
         tk::launch_spmv<T>(sc->st, g, gp, (const T *)sc->val, cur, b, nxt);
@@ -388,13 +426,13 @@ T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *
 template <typename T>
 tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, T *d, double tol,
                     int maxit, SolveState &ss) {
-    const int n = g.n_nodes, m = sc->gm_m;
+    const int n = (int)g.npad, m = sc->gm_m;  // haloed vectors
     const size_t ld = (size_t)n;
     T *V = (T *)sc->V, *w = (T *)sc->w, *r = (T *)sc->d1;
-    const int nb = tk::dot_blocks(n);
+    const int nb = tk::dot_blocks(g);
     CK(cudaMemsetAsync(d, 0, (size_t)n * sizeof(T), sc->st), "memset");
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
-    tk::launch_sumsq<T>(sc->st, n, b, sc->part, nb, sc->dred);
+    tk::launch_sumsq<T>(sc->st, g, b, sc->part, nb, sc->dred);
     sc->launches += 2;
     tursca_status rs = read_red<T>(sc, 1);
     if (rs) return rs;
@@ -415,11 +453,11 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
             int pi = prof_begin(sc, P_SPMV);
             tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, vk, w);
             prof_end(sc, pi);
-            tk::launch_dots<T, T>(sc->st, n, V, ld, k + 1, w, sc->part, nb, sc->dred);
+            tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);
-            tk::launch_dots<T, T>(sc->st, n, V, ld, k + 1, w, sc->part, nb, sc->dred + 64);
+            tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred + 64);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred + 64);
-            tk::launch_sumsq<T>(sc->st, n, w, sc->part, nb, sc->dred + 128);
+            tk::launch_sumsq<T>(sc->st, g, w, sc->part, nb, sc->dred + 128);
             sc->launches += 10;
             ss.iters++;
             total++;
@@ -463,7 +501,7 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
         // true residual r = b - (I - K) d
         tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, d, w);
         tk::launch_axpby<T>(sc->st, n, 1.0, b, -1.0, w, r);
-        tk::launch_sumsq<T>(sc->st, n, r, sc->part, nb, sc->dred);
+        tk::launch_sumsq<T>(sc->st, g, r, sc->part, nb, sc->dred);
         sc->launches += 4;
         ss.iters++;
         rs = read_red<T>(sc, 1);
@@ -497,11 +535,12 @@ template <typename T>
 tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
     const tk::GridC g = grid_c(sc);
     const tk::GraphP gp = graph_p(sc);
-    const int n = g.n_nodes;
+    const int n = (int)g.npad;  // solver vectors are haloed
     const int nbr = tk::resid_blocks(g);
-    const int nb = tk::dot_blocks(n);
+    const int nb = tk::dot_blocks(g);
     const int nsw = tk::sweep_blocks(g);
     SolveState ss;
+    (void)nb;
     const bool fp64 = sc->d.precision == TURSCA_FP64;
     if (solver == TURSCA_SOLVER_AUTO) solver = fp64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
     auto ensure_basis = [&]() -> tursca_status {
@@ -519,13 +558,13 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     const bool ds = !fp64 && !sc->resid_fp64 && tk::resid_ds_ok(g);
     // x = 0, r = s, ||s||
     CK(cudaMemsetAsync(sc->x64, 0, (size_t)n * sizeof(double), sc->st), "memset x");
-    tk::launch_convert<T, double>(sc->st, n, (const T *)sc->s, sc->r64);
-    tk::launch_sumsq<double>(sc->st, n, sc->r64, sc->part, nb, sc->dred);
+    tk::launch_to_halo<T, double>(sc->st, g, (const T *)sc->s, sc->r64);
+    // ||s||^2 goes to dred[4] and is read with the first refinement's residual
+    tk::launch_sumsq<double>(sc->st, g, sc->r64, sc->part, nb, sc->dred + 4);
     sc->launches += 3;
-    tursca_status rs = read_red<T>(sc, 1);
-    if (rs) return rs;
-    const double sn = std::sqrt(sc->hred[0]);
-    double rel = sn > 0 ? 1.0 : 0.0;
+    tursca_status rs = TURSCA_OK;
+    double sn = -1.0;  // not read yet
+    double rel = 1.0;
     double rho = -1.0;      // estimate of the largest eigenvalue of K (-1: none yet)
     double widen = 0.0;     // extra margin after a refinement that under-delivered
     int inner_n = 8;        // Neumann sweeps (explicit Neumann solver)
@@ -609,6 +648,11 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
         } else if (kind == TURSCA_SOLVER_GMRES) {
             tursca_status e = ensure_basis();
             if (e) return e;
+            if (sn < 0.0) {  // GMRES reuses the reduction buffer: read ||s|| first
+                rs = read_red<T>(sc, 5);
+                if (rs) return rs;
+                sn = std::sqrt(sc->hred[4]);
+            }
             double tol = fp64 ? std::max(0.3 * rtol / rel, 1e-15) : std::max(0.3 * rtol / rel, 2e-6);
             e = gmres<T>(sc, g, gp, bb, (T *)sc->d0, tol, budget, ss);
             if (e) return e;
@@ -633,8 +677,9 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
         sc->launches += 3;
         ss.refinements++;
         ss.iters++;
-        rs = read_red<T>(sc, 4);
+        rs = read_red<T>(sc, 5);
         if (rs) return rs;
+        if (sn < 0.0) sn = std::sqrt(sc->hred[4]);
         const double prev = rel;
         rel = sn > 0 ? std::sqrt(sc->hred[0]) / sn : 0.0;
         const double f = prev > 0 ? rel / prev : 0.0;
@@ -688,7 +733,16 @@ tursca_status do_render(tursca_scene *sc, void *radiance, void *reflectance) {
     tk::ViewC vc = view_c(sc);
     tk::ViewP vp = view_p(sc);
     int pi = prof_begin(sc, P_RENDER);
-    tk::launch_emission<T>(sc->st, g, gp, f, vc, sc->x64, (T *)sc->emis);
+    // the solution in the compute type, gathered by the emission kernel
+    const T *xc;
+    if constexpr (sizeof(T) == 8) {
+        xc = (const T *)sc->x64;
+    } else {
+        tk::launch_convert<double, T>(sc->st, (int)g.npad, sc->x64, (T *)sc->w);
+        sc->launches++;
+        xc = (const T *)sc->w;
+    }
+    tk::launch_emission<T>(sc->st, g, gp, f, vc, xc, (T *)sc->emis);
     tk::launch_pixels<T>(sc->st, g, f, vc, vp, (const T *)sc->emis, sc->x64, (T *)sc->rad, (T *)sc->refl);
     prof_end(sc, pi);
     sc->launches += 2;
@@ -728,6 +782,10 @@ tursca_status tursca_scene_destroy(tursca_scene *sc) {
     free_list(sc->view_allocs);
     if (sc->hred) cudaFreeHost(sc->hred);
     for (cudaEvent_t e : sc->ev) cudaEventDestroy(e);
+    for (int i = 0; i < 3; ++i)
+        if (sc->aux[i]) cudaStreamDestroy(sc->aux[i]);
+    for (int i = 0; i < 5; ++i)
+        if (sc->fork[i]) cudaEventDestroy(sc->fork[i]);
     delete sc;
     return TURSCA_OK;
 }
@@ -888,6 +946,56 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     }
     CK(upload(sc, sc->allocs, sc->tstart, G.tmpl_start.data(), G.tmpl_start.size() * sizeof(int)), "upload tmpl");
     CK(upload(sc, sc->allocs, sc->tmpl, tm.data(), tm.size() * sizeof(int4)), "upload tmpl");
+    // the same templates as offsets in the solver's haloed layout (border R;
+    // every template's column offset is at most R)
+    {
+        const int H = sc->d.stencil_radius, nxp = sc->d.nx + 2 * H, lp = nxp * (sc->d.ny + 2 * H);
+        std::vector<int> tf(G.tmpl.size());
+        for (int z = 0; z <= sc->d.nz; ++z)
+            for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
+                const tg::TSlot &t = G.tmpl[i];
+                if (std::abs(t.sdx) > H || std::abs(t.sdy) > H)
+                    return fail(sc, TURSCA_E_INVALID, "internal error: template offset beyond the halo");
+                const int szl = t.sz >= 0 ? t.sz : sc->d.nz;
+                tf[i] = (szl - z) * lp + t.sdy * nxp + t.sdx;
+            }
+        CK(upload(sc, sc->allocs, sc->tflat, tf.data(), tf.size() * sizeof(int)), "upload tmpl");
+    }
+    // Runs of the persistent streamed passes: one per SM, each an equal share
+    // of the value stream cut at group boundaries (pass 0: all groups, pass
+    // 1: the atmospheric layers)
+    {
+        int dev = 0, nsm = 0;
+        CK(cudaGetDevice(&dev), "device");
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "device");
+        const long long nxy = (long long)sc->d.nx * sc->d.ny;
+        const int gpl = (int)((nxy + tk::kGroup - 1) / tk::kGroup);
+        auto gstart = [&](long long gi) -> long long {
+            const int z = (int)(gi / gpl), q = (int)(gi - (long long)z * gpl);
+            if (z > sc->d.nz) return G.voff[sc->d.nz + 1];
+            const long long nt = G.tmpl_start[z + 1] - G.tmpl_start[z];
+            return G.voff[z] + (long long)q * nt * tk::kGroup;
+        };
+        for (int k = 0; k < 2; ++k) {
+            const long long ng = (long long)(k == 0 ? sc->d.nz + 1 : sc->d.nz) * gpl;
+            const int nb = (int)std::max<long long>(1, std::min<long long>(ng, std::max(nsm, 1)));
+            const long long vtot = gstart(ng);
+            std::vector<int> rg(nb + 1);
+            std::vector<long long> rv(nb + 1);
+            long long gi = 0;
+            for (int b = 0; b <= nb; ++b) {
+                const long long target = vtot * b / nb;
+                while (gi < ng && gstart(gi) < target) ++gi;
+                rg[b] = (int)gi;
+                rv[b] = gstart(gi);
+            }
+            rg[nb] = (int)ng;
+            rv[nb] = vtot;
+            CK(upload(sc, sc->allocs, sc->run_g[k], rg.data(), rg.size() * sizeof(int)), "upload runs");
+            CK(upload(sc, sc->allocs, sc->run_v[k], rv.data(), rv.size() * sizeof(long long)), "upload runs");
+            sc->run_n[k] = nb;
+        }
+    }
     CK(upload(sc, sc->allocs, sc->voff, G.voff.data(), G.voff.size() * sizeof(long long)), "upload tmpl");
     CK(dalloc(sc->allocs, sc->val, (size_t)G.nval * sc->es), "alloc val");
     const size_t es = sc->es;
@@ -906,6 +1014,9 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->wsp, (size_t)sc->d.n_species * G.n_atm * es), "alloc wsp");
     cudaError_t ce = cudaStreamSynchronize(sc->st);
     if (ce != cudaSuccess) return cuda_fail(sc, ce, "build_graph");
+    if (sc->wq_auto) sc->wq = tk::choose_wq(grid_c(sc), sc->d.precision == TURSCA_FP64);
+    for (int i = 0; i < 3; ++i) CK(cudaStreamCreateWithFlags(&sc->aux[i], cudaStreamNonBlocking), "aux stream");
+    for (int i = 0; i < 5; ++i) CK(cudaEventCreateWithFlags(&sc->fork[i], cudaEventDisableTiming), "aux event");
     sc->built = true;
     return TURSCA_OK;
 }
@@ -959,10 +1070,11 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     const tk::ViewC vc = view_c(sc);
     const tk::ViewP vp = view_p(sc);
     int p0 = prof_begin(sc, P_PRE);
+    const cudaStream_t streams[4] = {sc->st, sc->aux[0], sc->aux[1], sc->aux[2]};
     if (sc->d.precision == TURSCA_FP64)
-        tk::launch_assemble_pre<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, &sc->launches);
+        tk::launch_assemble_pre<double>(streams, sc->fork, g, gp, field_p<double>(sc), vc, vp, &sc->launches);
     else
-        tk::launch_assemble_pre<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, &sc->launches);
+        tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, &sc->launches);
     prof_end(sc, p0);
     int p1 = prof_begin(sc, P_ROWS);
     if (sc->d.precision == TURSCA_FP64)
@@ -1053,7 +1165,14 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
         case TURSCA_F_TSUN: src = sc->tsun; need = nn * es; break;
         case TURSCA_F_E1: src = sc->e1; need = nn * es; break;
         case TURSCA_F_S: src = sc->s; need = nn * es; break;
-        case TURSCA_F_X: src = sc->x64; need = nn * 8; break;
+        case TURSCA_F_X:
+            // the solver keeps x haloed: gather the nodes into the residual
+            // buffer (scratch between solves) first
+            if (!sc->fields_alloc) return fail(sc, TURSCA_E_STATE, "set_medium has not been called");
+            tk::launch_from_halo<double>(sc->st, grid_c(sc), sc->x64, sc->r64);
+            src = sc->r64;
+            need = nn * 8;
+            break;
         case TURSCA_F_EMIS: src = sc->emis; need = na * es; break;
         case TURSCA_F_GSUN: src = sc->gsun; need = na * es; break;
         case TURSCA_F_Q_ISO: src = G.q_iso.data(); need = G.q_iso.size() * 8; host = true; break;
@@ -1086,6 +1205,25 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
     switch (option) {
         case TURSCA_OPT_RESIDUAL_FP64:
             sc->resid_fp64 = value != 0.0;
+            return TURSCA_OK;
+        case TURSCA_OPT_STAGE_VALUES:
+            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "stage values must be 0 or 1");
+            if (value == 1.0 && !sc->wq_auto && sc->wq == 6 && sc->d.precision != TURSCA_FP64)
+                return fail(sc, TURSCA_E_INVALID, "the streamed passes take 4, 8 or 16 group warps");
+            sc->stage_values = (int)value;
+            if (sc->built && sc->wq_auto) sc->wq = tk::choose_wq(grid_c(sc), sc->d.precision == TURSCA_FP64);
+            return TURSCA_OK;
+        case TURSCA_OPT_GROUP_WARPS:
+            if (value != 0.0 && value != 4.0 && value != 6.0 && value != 8.0 && value != 16.0)
+                return fail(sc, TURSCA_E_INVALID, "group warps must be 0 (automatic), 4, 6, 8 or 16");
+            if (value == 6.0 && sc->stage_values && sc->d.precision != TURSCA_FP64)
+                return fail(sc, TURSCA_E_INVALID, "the streamed passes take 4, 8 or 16 group warps");
+            sc->wq_auto = value == 0.0;
+            if (value == 0.0) {
+                if (sc->built) sc->wq = tk::choose_wq(grid_c(sc), sc->d.precision == TURSCA_FP64);
+            } else {
+                sc->wq = (int)value;
+            }
             return TURSCA_OK;
         default: return fail(sc, TURSCA_E_INVALID, "unknown option");
     }

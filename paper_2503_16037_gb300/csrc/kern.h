@@ -45,6 +45,18 @@ struct __align__(8) DTap {
 struct GridC {
     int nx, ny, nz, nxy, n_atm, n_ground, n_nodes;
     int S, nd, ngd, nup, R, nc;  // nc: canonical directions (segment table rows)
+    int wq;                      // warps per 128-row group in the solver passes (4, 6, 8 or 16)
+    int wq_em;                   // warps per group in the emission pass
+    int gpl;                     // groups of kGroup rows per layer: ceil(nxy / kGroup)
+    int ntmax;                   // largest row template (slots per row of a layer)
+    // Haloed layout of the solver's node vectors: layer z (z = nz: the ground)
+    // is a (ny + 2H) x (nx + 2H) plane, node (x, y, z) at
+    // z * lp + (y + H) * nxp + x + H, and the border of width H repeats the
+    // periodic partners, so a gather at a column offset of at most H needs no
+    // wrap.  H is the largest |sdx|, |sdy| of the row templates.
+    int H, nxp, nyp, lp;
+    long long npad;              // (nz + 1) * lp
+    int stage;                   // 1: FP32 sweeps stage each group's values in shared memory
     double hx, hy, hz;
 };
 
@@ -79,6 +91,15 @@ struct GraphP {
     const int *gtop_off, *gtop_n;  // [ngd]
     const int *canon_dirs;         // [nc] atmospheric index of each canonical direction
     const int *up_canon;           // [nup] canonical index of each upward direction
+    int *status;                   // scene status word (STATUS_* bits; bounded waits set STATUS_TIMEOUT)
+    const int *tflat;              // per template entry: source - receiver in the haloed layout
+    // Runs of the persistent streamed passes: block b of pass kind k (0: all
+    // (nz + 1) * gpl groups, 1: the nz * gpl atmospheric groups) handles the
+    // groups [run_g[k][b], run_g[k][b + 1]), whose values are
+    // [run_v[k][b], run_v[k][b + 1]); run_n[k] blocks.
+    const int *run_g[2];
+    const long long *run_v[2];
+    int run_n[2];
 };
 
 // Per-scene optical fields and assembled quantities (element type T).
@@ -164,6 +185,11 @@ __host__ __device__ __forceinline__ long long val_base(long long voff_z, int nt,
 // source node of template slot (sdx, sdy, flat) for the receiver at (x, y)
 __host__ __device__ __forceinline__ int tmpl_sdx(int4 t) { return (int)(short)(t.z & 0xffff); }
 __host__ __device__ __forceinline__ int tmpl_sdy(int4 t) { return (int)(short)((unsigned)t.z >> 16); }
+// haloed position of node (x, y, z)
+__host__ __device__ __forceinline__ long long halo_pos(const GridC &g, int x, int y, int z) {
+    return (long long)z * g.lp + (long long)(y + g.H) * g.nxp + x + g.H;
+}
+
 __host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x, int y, int4 t) {
     int sx = x + tmpl_sdx(t), sy = y + tmpl_sdy(t);
     int j = row + t.y;
@@ -177,9 +203,10 @@ __host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x,
 // ---- assembly (kernels_asm.cu)
 // CSR export of the slot-major matrix (row order = template order)
 // field preparation, quadrature tables, sun, tau_inf sweeps, coupling normalisers
+// st[0]: scene stream; st[1..3]: auxiliary streams; ev: five events (no timing)
 template <typename T>
-void launch_assemble_pre(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                         const ViewP &vp, long long *launches);
+void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], const GridC &g, const GraphP &gp,
+                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, long long *launches);
 // the fused edge march + edge weights over all receiver rows
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
@@ -198,20 +225,30 @@ template <typename T>
 void launch_resid64(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *s, const double *x,
                     double *r, double *part, int nblk);
 int resid_blocks(const GridC &g);
+// warps per 128-row group that fills the GPU's waves best for this grid
+int choose_wq(const GridC &g, bool fp64);
 // the same residual with FP32-pair (double-single) arithmetic: x = xh + xl
 bool resid_ds_ok(const GridC &g);
+// true when a group of 128 rows with ntmax template slots can be staged in shared memory (FP32)
+bool stage_fits(int ntmax);
 void launch_resid_ds(cudaStream_t st, const GridC &g, const GraphP &gp, const float *val, const float *s,
                      const double *x, const float *xh, const float *xl, double *r, double *part, int nblk);
 // x += d and (xh, xl may be null) its double-single split
 template <typename T>
 void launch_update_x(cudaStream_t st, int n, const T *d, double *x, float *xh, float *xl);
-// deterministic reductions: out[k] = sum_i V[k*ldv + i] * y[i], k < ncol
+// deterministic reductions over the nodes of haloed vectors (halo copies
+// skipped): out[k] = sum_nodes V[k*ldv + p] * y[p], k < ncol
 template <typename A, typename B>
-void launch_dots(cudaStream_t st, int n, const A *V, size_t ldv, int ncol, const B *y, double *part, int nblk,
-                 double *out);
+void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int ncol, const B *y, double *part,
+                 int nblk, double *out);
 template <typename T>
-void launch_sumsq(cudaStream_t st, int n, const T *x, double *part, int nblk, double *out);
-int dot_blocks(int n);
+void launch_sumsq(cudaStream_t st, const GridC &g, const T *x, double *part, int nblk, double *out);
+int dot_blocks(const GridC &g);
+// haloed dst <- node-ordered src; node-ordered dst <- haloed src
+template <typename T, typename U>
+void launch_to_halo(cudaStream_t st, const GridC &g, const T *src, U *dst);
+template <typename U>
+void launch_from_halo(cudaStream_t st, const GridC &g, const U *src, U *dst);
 // finalize block partials part[nblk] (single column) into out[0]
 void launch_finalize(cudaStream_t st, const double *part, int nblk, double *out);
 // finalize two columns part[2][nblk] into out[0..1]
@@ -242,9 +279,10 @@ template <typename T>
 void launch_imk(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, T *y);  // y = x - K x
 
 // ---- render (kernels_render.cu)
+// xc: the solution x in the compute type
 template <typename T>
 void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                     const double *x, T *emis);
+                     const T *xc, T *emis);
 template <typename T>
 void launch_pixels(cudaStream_t st, const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp,
                    const T *emis, const double *x, T *rad, T *refl);

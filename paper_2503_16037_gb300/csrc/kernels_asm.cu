@@ -42,6 +42,35 @@ __device__ __forceinline__ float dsqrt<float>(float a) { return sqrtf(a); }
 template <>
 __device__ __forceinline__ double dsqrt<double>(double a) { return sqrt(a); }
 
+// 1 - exp(-t) for t >= 0 in the edge kernel.  FP32: the Taylor series
+// t - t^2/2 + ... - t^8/8! below t = 1/4 (truncation below 2e-9 relative),
+// 1 - __expf(-t) above it (cancellation there is at most a factor 4.6);
+// FP64: expm1.
+template <typename T>
+__device__ __forceinline__ T one_minus_exp(T t);
+template <>
+__device__ __forceinline__ float one_minus_exp<float>(float t) {
+    if (t < 0.25f) {
+        float p = 1.f - t * (1.f / 8.f);
+        p = 1.f - t * (1.f / 7.f) * p;
+        p = 1.f - t * (1.f / 6.f) * p;
+        p = 1.f - t * (1.f / 5.f) * p;
+        p = 1.f - t * (1.f / 4.f) * p;
+        p = 1.f - t * (1.f / 3.f) * p;
+        p = 1.f - t * (1.f / 2.f) * p;
+        return t * p;
+    }
+    return 1.f - __expf(-t);
+}
+template <>
+__device__ __forceinline__ double one_minus_exp<double>(double t) { return -expm1(-t); }
+template <typename T>
+__device__ __forceinline__ T fast_exp_neg(T t);
+template <>
+__device__ __forceinline__ float fast_exp_neg<float>(float t) { return __expf(-t); }
+template <>
+__device__ __forceinline__ double fast_exp_neg<double>(double t) { return exp(-t); }
+
 template <typename T>
 __device__ __forceinline__ const T *tap_len(const GraphP &gp);
 template <>
@@ -82,6 +111,7 @@ __device__ __forceinline__ T ray_sum(const GridC &g, const DTap *__restrict__ ta
     if (n == 0) return acc;
     DTap p = taps[off];
     int x = wrap_any(bx + p.dx, g.nx), y = wrap_any(by + p.dy, g.ny);
+#pragma unroll 4
     for (int t = 0; t < n; ++t) {
         DTap tp = taps[off + t];
         x = wrap_small(x + (tp.dx - p.dx), g.nx);
@@ -144,7 +174,8 @@ __global__ void k_prep(GridC g, FieldP<T> f) {
         T a = f.mu_a[i];
         bool ok = isfinite((double)a) && a >= T(0);
         T s = T(0);
-        for (int sp = 0; sp < g.S; ++sp) {
+        #pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) {
             T v = f.mu_s[(size_t)sp * g.n_atm + i];
             ok = ok && isfinite((double)v) && v >= T(0);
             s += v;
@@ -158,7 +189,8 @@ __global__ void k_prep(GridC g, FieldP<T> f) {
         f.mu_e[i] = a + s;
         f.rt[i] = dsqrt<T>(s);
         T inv = s > T(0) ? T(1) / s : T(0);
-        for (int sp = 0; sp < g.S; ++sp)
+        #pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S)
             f.wsp[(size_t)sp * g.n_atm + i] = s > T(0) ? f.mu_s[(size_t)sp * g.n_atm + i] * inv : T(1) / (T)g.S;
         m = (double)s;
     }
@@ -176,7 +208,7 @@ template <typename T>
 __global__ void k_tables_cells(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
     __shared__ double red[32];
     int u = blockIdx.x, sp = blockIdx.y;
-    double gg = vc.g[sp];
+    double gg = sp == 0 ? vc.g[0] : sp == 1 ? vc.g[1] : sp == 2 ? vc.g[2] : vc.g[3];
     double acc = 0.0;
     for (int m = vp.cell_start[u] + threadIdx.x; m < vp.cell_start[u + 1]; m += blockDim.x) {
         const double *s = vp.lattice + 3 * (size_t)m;
@@ -197,7 +229,7 @@ template <typename T>
 __global__ void k_tables_norm(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
     __shared__ double total;
     int sp = blockIdx.x;
-    double gg = vc.g[sp];
+    double gg = sp == 0 ? vc.g[0] : sp == 1 ? vc.g[1] : sp == 2 ? vc.g[2] : vc.g[3];
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int u = 0; u < g.nd; ++u) t += f.cellsum[sp * g.nd + u];
@@ -255,9 +287,9 @@ __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
 
 template <typename T>
 __global__ void k_segtau(GridC g, GraphP gp, FieldP<T> f) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)g.nc * g.n_atm) return;
-    int c = (int)(t / g.n_atm), a = (int)(t - (long long)c * g.n_atm);
+    const int c = blockIdx.y, a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= g.n_atm) return;
+    const size_t t = (size_t)c * g.n_atm + a;
     int u = gp.canon_dirs[c];
     int4 d = gp.dirs[u];
     int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
@@ -277,12 +309,9 @@ __device__ __forceinline__ T seg_at(const GridC &g, const T *__restrict__ tseg, 
 // One thread per (upward direction, start layer offset, column).
 template <typename T>
 __global__ void k_tinf(GridC g, GraphP gp, FieldP<T> f) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long per = (long long)g.R * g.nxy;
-    if (t >= per * g.nup) return;
-    int ui = (int)(t / per);
-    int rem = (int)(t - (long long)ui * per);
-    int o = rem / g.nxy, c = rem - o * g.nxy;
+    const int ui = blockIdx.y, rem = blockIdx.x * blockDim.x + threadIdx.x;
+    if (rem >= g.R * g.nxy) return;
+    const int o = rem / g.nxy, c = rem - o * g.nxy;
     int u = gp.up_dirs[ui];
     int4 d = gp.dirs[u];
     if (o >= d.z) return;
@@ -329,7 +358,8 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
     if (j < g.n_atm) {
         rt_src = f.rt[j];
         T w[MAX_SPECIES];
-        for (int sp = 0; sp < g.S; ++sp) w[sp] = f.wsp[(size_t)sp * g.n_atm + j];
+        #pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) w[sp] = f.wsp[(size_t)sp * g.n_atm + j];
 #pragma unroll 2
         for (int u = 0; u < g.nd; ++u) {
             int4 d = gp.dirs[u];
@@ -347,7 +377,8 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
             T C = rt_src * rtn / dist;
             T qi = Cst<T>::q_iso(gp, u);
             T qs = T(0);
-            for (int sp = 0; sp < g.S; ++sp) qs += w[sp] * f.q_sun[sp * g.nd + u];
+            #pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) qs += w[sp] * f.q_sun[sp * g.nd + u];
             sq_i += qi;
             sqc_i += qi * C;
             sq_s += qs;
@@ -395,10 +426,12 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
     if (!ground_row) {
         T me = f.mu_e[row], ms = f.mu_st[row];
         rho = me > T(0) ? ms / me : T(0);
-        for (int sp = 0; sp < g.S; ++sp) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
+        #pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
     } else {
         rho = (T)vc.albedo;
-        for (int sp = 0; sp < g.S; ++sp) wr[sp] = T(0);
+        #pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) wr[sp] = T(0);
     }
     T acc_s = T(0), acc_g = T(0);
     const T rt_lamb = dsqrt<T>(mus_lamb);
@@ -432,19 +465,19 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
         T P;
         if (kind == 0 || kind == 3) {  // chain node (atmospheric or ground source)
             const bool has_pre = pre_tab >= 0 || (w2.w & 0xff);
-            const T ep = has_pre ? dexp<T>(-tpre) : T(1);
+            const T ep = has_pre ? fast_exp_neg<T>(tpre) : T(1);
             if (bkind == 0) {
-                P = ep * (-dexpm1<T>(-tseg));
+                P = ep * one_minus_exp<T>(tseg);
             } else if (bkind == 1) {
                 P = ep;
             } else {
                 T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row]
                                   : (bkind == 3 ? thit : f.tinfg[(size_t)gdir * g.nxy + (j - g.n_atm)]);
-                P = ep * (-dexpm1<T>(-(tseg + tb)));
+                P = ep * one_minus_exp<T>(tseg + tb);
             }
         } else if (kind == 1) {  // self deposit
             T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row] : thit;
-            P = -dexpm1<T>(-tb);
+            P = one_minus_exp<T>(tb);
         } else {  // ground hit
             T split;
             if constexpr (sizeof(T) == 4) {
@@ -453,7 +486,7 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
                 const int4 w3 = __ldg(&pc->w3);
                 split = __hiloint2double(w3.w, w3.z);
             }
-            P = split * dexp<T>(-(tpre + thit));
+            P = split * fast_exp_neg<T>(tpre + thit);
         }
         // quadrature weight x coupling of the source
         T dinv;
@@ -467,7 +500,8 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
         T Wi, Ws;
         if (sz >= 0) {
             T qi = Cst<T>::q_iso(gp, dir), qs = T(0);
-            for (int sp = 0; sp < g.S; ++sp) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * f.q_sun[sp * g.nd + dir];
+            #pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * f.q_sun[sp * g.nd + dir];
             T ci = T(1), cs = T(1);
             if (!c_one) {
                 T rtn = n1_ground ? rt_lamb
@@ -491,7 +525,8 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
         acc_s += sun;
         if (!ground_row) {
             T th = T(0);
-            for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + hgdir];
+            #pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) th += wr[sp] * f.hgv[sp * ndir + hgdir];
             acc_g += th * sun;
         }
     }
@@ -499,34 +534,231 @@ __global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> 
     if (!ground_row) f.gsun[row] = acc_g;
 }
 
+// Four consecutive rows per thread (nx divisible by 4): the slot's template
+// entry, class descriptor and table offsets are decoded once for the four
+// rows, their values are stored with one 16-byte store per slot.
 template <typename T>
-void launch_assemble_pre(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                         const ViewP &vp, long long *launches) {
+struct Store4;
+template <>
+struct Store4<float> {
+    __device__ static __forceinline__ void st(float *p, const float v[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Store4<double> {
+    __device__ static __forceinline__ void st(double *p, const double v[4]) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+};
+
+// kAsmSplit warps share each 128-row group (warp w takes slots t = w mod
+// kAsmSplit); the row sums s and g are combined in shared memory in a fixed order.
+constexpr int kAsmSplit = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kAsmSplit) k_assemble4(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
+    __shared__ T sh_s[kAsmSplit][4][32], sh_g[kAsmSplit][4][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = (blockIdx.x * 32 + lane) * 4;
+    const bool live = row0 < g.n_nodes;
+    T acc_s[4] = {T(0), T(0), T(0), T(0)}, acc_g[4] = {T(0), T(0), T(0), T(0)};
+    if (live) {
+    const int z = row0 / g.nxy, r0 = row0 - z * g.nxy, y = r0 / g.nx, x0 = r0 - y * g.nx;
+    const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
+    T *vrow = f.val + val_base(gp.voff[z], nt, r0);
+    const T mus_lamb = (T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits));
+    const T rt_lamb = dsqrt<T>(mus_lamb);
+    const int ndir = g.nd + g.ngd;
+    const bool ground_row = row0 >= g.n_atm;
+    T rho[4], wr[4][MAX_SPECIES];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!ground_row) {
+            const T me = f.mu_e[row0 + k], ms = f.mu_st[row0 + k];
+            rho[k] = me > T(0) ? ms / me : T(0);
+#pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp)
+                wr[k][sp] = sp < g.S ? f.wsp[(size_t)sp * g.n_atm + row0 + k] : T(0);
+        } else {
+            rho[k] = (T)vc.albedo;
+#pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp) wr[k][sp] = T(0);
+        }
+    }
+    for (int t = w; t < nt; t += kAsmSplit) {
+        const int4 te = __ldg(gp.tmpl + t0 + t);
+        const PClass *pc = gp.pcls + te.x;
+        const int4 w0 = __ldg(&pc->w0), w1 = __ldg(&pc->w1);
+        const int kind = w0.x & 0xff, bkind = (w0.x >> 8) & 0xff;
+        const bool c_one = (w0.x >> 16) & 0xff, n1_ground = (w0.x >> 24) & 0xff;
+        const int dir = w0.y & 0xffff, hgdir = (w0.y >> 16) & 0xffff;
+        const int up_idx = w0.z & 0xffff, gdir = (w0.z >> 16) & 0xffff;
+        const int sz = te.w;
+        const int bz = sz >= 0 ? sz : 0;
+        const int by = wrap_small(y + tmpl_sdy(te), g.ny);
+        const int bx0 = x0 + tmpl_sdx(te);  // unwrapped column of row0's source
+        const int seg_tab = (w1.x & 0xff) - 1, pre_tab = (w1.y & 0xff) - 1;
+        int4 w2 = make_int4(0, 0, 0, 0);
+        if (seg_tab < 0 || pre_tab < 0) w2 = __ldg(&pc->w2);
+        const int pre_n = w2.w & 0xff, seg_n = (w2.w >> 8) & 0xff, hit_n = (w2.w >> 16) & 0xff;
+        const bool has_pre = pre_tab >= 0 || pre_n;
+        T split = T(0), dinv;
+        if constexpr (sizeof(T) == 4) {
+            split = __int_as_float(w1.w);
+            dinv = __int_as_float(w0.w);
+        } else {
+            const int4 w3 = __ldg(&pc->w3);
+            dinv = __hiloint2double(w3.y, w3.x);
+            split = __hiloint2double(w3.w, w3.z);
+        }
+        const T qi = sz >= 0 ? Cst<T>::q_iso(gp, dir) : Cst<T>::q_lamb(gp, gdir);
+        T qsun_s[MAX_SPECIES];
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) qsun_s[sp] = (sz >= 0 && sp < g.S) ? f.q_sun[sp * g.nd + dir] : T(0);
+        T th[4] = {T(0), T(0), T(0), T(0)};
+        if (!ground_row) {
+#pragma unroll
+            for (int sp = 0; sp < MAX_SPECIES; ++sp)
+                if (sp < g.S) {
+                    const T h = f.hgv[sp * ndir + hgdir];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) th[k] += wr[k][sp] * h;
+                }
+        }
+        T out[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int bx = wrap_small(bx0 + k, g.nx);
+            const int j = sz >= 0 ? (sz * g.ny + by) * g.nx + bx : g.n_atm + by * g.nx + bx;
+            T tpre = T(0), tseg = T(0), thit = T(0);
+            if (pre_tab >= 0)
+                tpre = seg_at<T>(g, f.tseg, pre_tab, bx + sbyte(w1.y, 8), by + sbyte(w1.y, 16), bz + sbyte(w1.y, 24));
+            else if (pre_n)
+                tpre = tap_sum<T>(g, gp, f.mu_e, w2.x, pre_n, bx, by, bz);
+            if (seg_tab >= 0)
+                tseg = seg_at<T>(g, f.tseg, seg_tab, bx + sbyte(w1.x, 8), by + sbyte(w1.x, 16), bz + sbyte(w1.x, 24));
+            else if (seg_n)
+                tseg = tap_sum<T>(g, gp, f.mu_e, w2.y, seg_n, bx, by, bz);
+            if (hit_n) thit = tap_sum<T>(g, gp, f.mu_e, w2.z, hit_n, bx, by, bz);
+            T P;
+            if (kind == 0 || kind == 3) {
+                const T ep = has_pre ? fast_exp_neg<T>(tpre) : T(1);
+                if (bkind == 0) {
+                    P = ep * one_minus_exp<T>(tseg);
+                } else if (bkind == 1) {
+                    P = ep;
+                } else {
+                    const T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row0 + k]
+                                            : (bkind == 3 ? thit : f.tinfg[(size_t)gdir * g.nxy + (j - g.n_atm)]);
+                    P = ep * one_minus_exp<T>(tseg + tb);
+                }
+            } else if (kind == 1) {
+                const T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row0 + k] : thit;
+                P = one_minus_exp<T>(tb);
+            } else {
+                P = split * fast_exp_neg<T>(tpre + thit);
+            }
+            T Wi, Ws;
+            if (sz >= 0) {
+                T qs = T(0);
+#pragma unroll
+                for (int sp = 0; sp < MAX_SPECIES; ++sp)
+                    if (sp < g.S) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * qsun_s[sp];
+                T ci = T(1), cs = T(1);
+                if (!c_one) {
+                    const T rtn = n1_ground ? rt_lamb
+                                            : __ldg(f.rt + ((bz + sbyte(w1.z, 16)) * g.ny + wrap_small(by + sbyte(w1.z, 8), g.ny)) * g.nx +
+                                                    wrap_small(bx + sbyte(w1.z, 0), g.nx));
+                    const T ai = __ldg(f.a_iso + j), as = __ldg(f.a_sun + j);
+                    ci = ai > T(0) ? ai * rtn * dinv : T(1);
+                    cs = as > T(0) ? as * rtn * dinv : T(1);
+                }
+                Wi = qi * ci;
+                Ws = qs * cs;
+            } else {
+                const T rtn = __ldg(f.rt + (sbyte(w1.z, 16) * g.ny + wrap_small(by + sbyte(w1.z, 8), g.ny)) * g.nx +
+                                    wrap_small(bx + sbyte(w1.z, 0), g.nx));
+                const T a = __ldg(f.a_iso + j);
+                Wi = qi * (a > T(0) ? a * rtn * dinv : T(1));
+                Ws = Wi;
+            }
+            out[k] = rho[k] * Wi * P;
+            const T sun = rho[k] * Ws * P * __ldg(f.e1 + j);
+            acc_s[k] += sun;
+            acc_g[k] += th[k] * sun;
+        }
+        Store4<T>::st(vrow + (size_t)t * kGroup, out);
+    }
+    }  // live
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        sh_s[w][k][lane] = acc_s[k];
+        sh_g[w][k][lane] = acc_g[k];
+    }
+    __syncthreads();
+    if (w == 0 && live) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T a = T(0), b = T(0);
+#pragma unroll
+            for (int q = 0; q < kAsmSplit; ++q) {
+                a += sh_s[q][k][lane];
+                b += sh_g[q][k][lane];
+            }
+            f.s[row0 + k] = a;
+            if (row0 < g.n_atm) f.gsun[row0 + k] = b;
+        }
+    }
+}
+
+// Per-scene tables.  Dependencies: prep -> {sun, segtau -> tinf, tinfg, znorm};
+// tables -> znorm.  st[0] is the scene stream; st[1..3] are auxiliary streams
+// forked from it and joined back with events, so the independent tables run
+// concurrently.
+template <typename T>
+void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], const GridC &g, const GraphP &gp,
+                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, long long *launches) {
     const int th = 256;
-    cudaMemsetAsync(f.mus_max_bits, 0, sizeof(unsigned long long), st);
-    k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st>>>(g, f);
-    k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st>>>(g, f, vc, vp);
-    k_tables_norm<T><<<g.S, 128, 0, st>>>(g, f, vc, vp);
-    k_sun<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, f, vc, vp);
-    long long ns = (long long)g.nc * g.n_atm;
-    k_segtau<T><<<(unsigned)((ns + th - 1) / th), th, 0, st>>>(g, gp, f);
-    long long nt = (long long)g.nup * g.R * g.nxy;
-    k_tinf<T><<<(unsigned)((nt + th - 1) / th), th, 0, st>>>(g, gp, f);
-    k_tinfg<T><<<(g.ngd * g.nxy + 127) / 128, 128, 0, st>>>(g, gp, f);
-    k_znorm<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
+    // ev[0]: start (orders the aux streams after earlier work of the scene stream)
+    cudaEventRecord(ev[0], st[0]);
+    cudaStreamWaitEvent(st[1], ev[0], 0);
+    k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st[1]>>>(g, f, vc, vp);
+    k_tables_norm<T><<<g.S, 128, 0, st[1]>>>(g, f, vc, vp);
+    cudaEventRecord(ev[2], st[1]);
+    cudaMemsetAsync(f.mus_max_bits, 0, sizeof(unsigned long long), st[0]);
+    k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st[0]>>>(g, f);
+    cudaEventRecord(ev[1], st[0]);  // fields ready
+    cudaStreamWaitEvent(st[2], ev[1], 0);
+    k_segtau<T><<<dim3((g.n_atm + th - 1) / th, g.nc), th, 0, st[2]>>>(g, gp, f);
+    k_tinf<T><<<dim3((g.R * g.nxy + th - 1) / th, g.nup), th, 0, st[2]>>>(g, gp, f);
+    cudaEventRecord(ev[3], st[2]);
+    cudaStreamWaitEvent(st[3], ev[1], 0);
+    k_tinfg<T><<<(g.ngd * g.nxy + 127) / 128, 128, 0, st[3]>>>(g, gp, f);
+    k_sun<T><<<(g.n_nodes + 127) / 128, 128, 0, st[3]>>>(g, f, vc, vp);
+    cudaEventRecord(ev[4], st[3]);
+    cudaStreamWaitEvent(st[0], ev[2], 0);
+    k_znorm<T><<<(g.n_nodes + 127) / 128, 128, 0, st[0]>>>(g, gp, f, vc);
+    cudaStreamWaitEvent(st[0], ev[3], 0);
+    cudaStreamWaitEvent(st[0], ev[4], 0);
     if (launches) *launches += 8;
 }
 
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                           long long *launches) {
-    k_assemble<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
+    if (g.nx % 4 == 0)
+        k_assemble4<T><<<(g.n_nodes / 4 + 31) / 32, 32 * kAsmSplit, 0, st>>>(g, gp, f, vc);
+    else
+        k_assemble<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
     if (launches) *launches += 1;
 }
 
 #define INST(T)                                                                                                   \
-    template void launch_assemble_pre<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
-                                         const ViewC &, const ViewP &, long long *);                              \
+    template void launch_assemble_pre<T>(cudaStream_t const[4], cudaEvent_t const[5], const GridC &,              \
+                                         const GraphP &, const FieldP<T> &, const ViewC &, const ViewP &,         \
+                                         long long *);                                                            \
     template void launch_assemble_rows<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,         \
                                           const ViewC &, long long *);                                            \
     template void launch_export_csr<T>(cudaStream_t, const GridC &, const GraphP &, const T *, int32_t *,         \

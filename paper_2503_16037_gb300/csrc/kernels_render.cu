@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "kern.h"
+#include "stage.cuh"
 
 namespace tk {
 
@@ -34,98 +35,151 @@ __device__ __forceinline__ int rwrap(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Rows in groups of 32 (one per lane) shared by kEmSplit warps, each summing
-// every kEmSplit-th slot of the template; partials combined in a fixed order.
-constexpr int kEmSplit = 4;
-
+// E_i as one pass over the atmospheric rows of K (the same row-group drivers
+// as the solver's sweeps).  Theta_i(u . v) = sum_sp w_sp,i hg_sp(u . v) is
+// split by species: for each species the row accumulates
+// sum_slots hg_sp(slot direction) K_ij x_j, and the row's species weights
+// are applied once at the end.  x is gathered from a compute-type copy (xc)
+// of the FP64 solution, in the solver's haloed layout.
 template <typename T>
-__global__ void __launch_bounds__(32 * kEmSplit) k_emission(GridC g, GraphP gp, FieldP<T> f, ViewC vc,
-                                                            const double *x, T *emis) {
-    __shared__ T sh[kEmSplit][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 32 + lane;
-    const bool live = row < g.n_atm;
-    const int ndir = g.nd + g.ngd;
-    T acc = T(0);
-    T wr[MAX_SPECIES];
-    if (live) {
-        const int z = row / g.nxy, r = row - z * g.nxy, yy = r / g.nx, xx = r - yy * g.nx;
-        const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
-        const T *v = f.val + val_base(gp.voff[z], nt, r);
-        for (int sp = 0; sp < g.S; ++sp) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
-        for (int t = w; t < nt; t += kEmSplit) {
-            const int4 te = __ldg(gp.tmpl + t0 + t);
-            const int hgd = gp.cls[te.x].hgdir;
-            T th = T(0);
-            for (int sp = 0; sp < g.S; ++sp) th += wr[sp] * f.hgv[sp * ndir + hgd];
-            const int j = slot_src(g, row, xx, yy, te);
-            acc += th * v[(size_t)t * kGroup] * (T)x[j];
+struct OpEmission {
+    using A = T;
+    static constexpr int NA = 4 * MAX_SPECIES;
+    static constexpr bool kPart = false;
+    struct Slot {
+        T hv[MAX_SPECIES];
+    };
+    struct Pre {
+        T w[MAX_SPECIES];
+        T e1, gsun;
+    };
+    FieldP<T> f;
+    const T *xc;
+    T *emis;
+    int S, ndir, n_atm;
+    __device__ __forceinline__ Slot slot(const GraphP &gp, int t) const {
+        Slot si;
+        const int hgd = gp.cls[__ldg(&gp.tmpl[t].x)].hgdir;
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) si.hv[sp] = sp < S ? f.hgv[sp * ndir + hgd] : T(0);
+        return si;
+    }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, const Slot &si) const {
+        const T vx = v * __ldg(xc + j);
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp)
+            if (sp < S) a[sp * 4 + k] += vx * si.hv[sp];
+    }
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        Pre p;
+        const int i = G.row[k];
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) p.w[sp] = sp < S ? f.wsp[(size_t)sp * n_atm + i] : T(0);
+        p.e1 = f.e1[i];
+        p.gsun = f.gsun[i];
+        return p;
+    }
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) sum_word<W, A, NA>(sh, lane, sp * 4 + k, a);
+    }
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
+        T tot = T(0), th0 = T(0);
+#pragma unroll
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) {
+            if (sp >= S) continue;
+            tot += p.w[sp] * a[sp * 4 + k];
+            th0 += p.w[sp] * f.hg0v[sp];
         }
+        emis[G.row[k]] = p.e1 * th0 + p.gsun + tot;
+        return 0.0;
     }
-    sh[w][lane] = acc;
-    __syncthreads();
-    if (w == 0 && live) {
-        T tot = T(0);
-        for (int k = 0; k < kEmSplit; ++k) tot += sh[k][lane];
-        T th0 = T(0);
-        for (int sp = 0; sp < g.S; ++sp) th0 += wr[sp] * f.hg0v[sp];
-        emis[row] = f.e1[row] * th0 + f.gsun[row] + tot;
-    }
-}
+};
 
+// One warp per pixel.  The line of sight's taps are split into 32 contiguous
+// chunks; each lane sums its chunk's optical depth and its chunk's
+// contribution as seen from the chunk's top, an exclusive warp scan of the
+// chunk depths gives each chunk's attenuation from the TOA, and the warp sum
+// of the attenuated contributions is the radiance.
 template <typename T>
 __global__ void k_pixels(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__restrict__ emis,
                          const double *__restrict__ x, T *rad, T *refl) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (p >= vp.npx * vp.npy) return;
     const T *len;
     if constexpr (sizeof(T) == 4)
         len = (const T *)vp.los_len_f;
     else
         len = (const T *)vp.los_len_d;
-    int cx = vp.pix_cx[p], cy = vp.pix_cy[p], cl = vp.pix_cls[p];
-    int off = vp.los_off[cl], n = vp.los_n[cl];
+    const int cx = vp.pix_cx[p], cy = vp.pix_cy[p], cl = vp.pix_cls[p];
+    const int off = vp.los_off[cl], n = vp.los_n[cl];
     const T inv_vol = (T)(1.0 / (g.hx * g.hy * g.hz));
+    const int per = (n + 31) / 32;
+    const int t0 = min(n, lane * per), t1 = min(n, t0 + per);
     T tau = T(0), L = T(0);
-    if (n > 0) {
-        // taps run along the ray: wrap the first column once, then follow it
-        DTap prev = vp.los_taps[off];
+    if (t0 < t1) {
+        DTap prev = vp.los_taps[off + t0];
         int xw = rwrap(cx + prev.dx, g.nx), yw = rwrap(cy + prev.dy, g.ny);
-        for (int t = 0; t < n; ++t) {
+        for (int t = t0; t < t1; ++t) {
             DTap tp = vp.los_taps[off + t];
             xw += tp.dx - prev.dx;
             xw = xw < 0 ? xw + g.nx : (xw >= g.nx ? xw - g.nx : xw);
             yw += tp.dy - prev.dy;
             yw = yw < 0 ? yw + g.ny : (yw >= g.ny ? yw - g.ny : yw);
             prev = tp;
-            int idx = (tp.dz * g.ny + yw) * g.nx + xw;
-            T me = f.mu_e[idx], ds = len[off + t];
-            T fr = me > T(0) ? -rexpm1<T>(-me * ds) / me : ds;
+            const int idx = (tp.dz * g.ny + yw) * g.nx + xw;
+            const T me = f.mu_e[idx], ds = len[off + t];
+            const T fr = me > T(0) ? -rexpm1<T>(-me * ds) / me : ds;
             L += rexp<T>(-tau) * fr * emis[idx] * inv_vol;
             tau += me * ds;
         }
     }
-    int c = g.n_atm + cy * g.nx + cx;
-    L += rexp<T>(-tau) * (f.e1[c] + (T)x[c]) * (T)(1.0 / (3.14159265358979323846 * g.hx * g.hy));
-    rad[p] = L;
-    if (refl) refl[p] = L * (T)(3.14159265358979323846 / (vc.mu0 * vc.f0));
+    // exclusive scan of the chunk depths (fixed order)
+    T incl = tau;
+    for (int o = 1; o < 32; o <<= 1) {
+        T v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const T before = incl - tau;
+    T contrib = rexp<T>(-before) * L;
+    for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+    const T total = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) {
+        const int c = g.n_atm + cy * g.nx + cx;
+        T Lp = contrib + rexp<T>(-total) * (f.e1[c] + (T)x[halo_pos(g, cx, cy, g.nz)]) * (T)(1.0 / (3.14159265358979323846 * g.hx * g.hy));
+        rad[p] = Lp;
+        if (refl) refl[p] = Lp * (T)(3.14159265358979323846 / (vc.mu0 * vc.f0));
+    }
 }
 
 template <typename T>
 void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                     const double *x, T *emis) {
-    k_emission<T><<<(g.n_atm + 31) / 32, 32 * kEmSplit, 0, st>>>(g, gp, f, vc, x, emis);
+                     const T *xc, T *emis) {
+    (void)vc;
+    OpEmission<T> op;
+    op.f = f;
+    op.xc = xc;
+    op.emis = emis;
+    op.S = g.S;
+    op.ndir = g.nd + g.ngd;
+    op.n_atm = g.n_atm;
+    // atmospheric layers only: the ground emits nothing toward the instrument
+    GridC ge = g;
+    ge.wq = g.wq_em;
+    run_op(st, ge, gp, f.val, op, 1);
 }
+
 
 template <typename T>
 void launch_pixels(cudaStream_t st, const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp,
                    const T *emis, const double *x, T *rad, T *refl) {
-    int n = vp.npx * vp.npy;
-    k_pixels<T><<<(n + 127) / 128, 128, 0, st>>>(g, f, vc, vp, emis, x, rad, refl);
+    long long n = (long long)vp.npx * vp.npy * 32;
+    k_pixels<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, f, vc, vp, emis, x, rad, refl);
 }
 
 template void launch_emission<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
-                                     const ViewC &, const double *, float *);
+                                     const ViewC &, const float *, float *);
 template void launch_emission<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,
                                       const ViewC &, const double *, double *);
 template void launch_pixels<float>(cudaStream_t, const GridC &, const FieldP<float> &, const ViewC &, const ViewP &,

@@ -1,253 +1,165 @@
 // Solver kernels for (I - K) x = s (Eq. flux_system of Mikkonen et al.;
 // the Neumann / source iteration is the series of Eq. fs_sum).
 //
-// The SpMV walks rows of receivers (K in CSR order by row), one thread per
-// row; the column of each slot comes from the row template of the row's
-// layer instead of a stored index, so only the 4-byte values stream (and stay
-// resident in L2 across the sweeps of a solve).  Reductions are
-// deterministic: fixed grids, fixed per-block order, fixed-order trees.
+// The sweeps walk rows of receivers (K in CSR order by row) in groups of 128
+// rows; the column of each slot comes from the row template of the row's
+// layer instead of a stored index, so only the 4-byte values stream.
+// Reductions are deterministic: fixed grids, fixed per-block order,
+// fixed-order trees.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "kern.h"
+#include "stage.cuh"
 
 namespace tk {
 
-// Rows are processed in groups of 32 consecutive rows (one per lane) by
-// kSplit warps; warp w sums the slots t = w, w + kSplit, ... of its lane's
-// row.  The value loads of a warp are coalesced (a slot's values are
-// contiguous across the rows of a layer), the x gathers of consecutive rows
-// hit consecutive entries (apart from the periodic wrap), and the partial
-// sums are combined in shared memory in a fixed order.
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
-    }
-    return r;  // valid in thread 0
-}
+// ---- Row-group kernels.  One pass over K does one of the operations below
+// (an "Op"): it accumulates, for each row of a group, the products of the
+// row's values with the source values it gathers, and finishes the row
+// (combination of the warps' partial sums in a fixed order, the row update,
+// per-group partial sums of squares).  The plain driver runs one block of W
+// warps per group and reads the values directly; the pipelined driver
+// (k_pipe) streams them through shared memory.  Source values are gathered
+// from haloed vectors (the template offset is the only index arithmetic),
+// and every row result is stored with its halo copies.
 
-constexpr int kSplit = 4;
+// Op interface (both drivers): A / NA: accumulator type and words per lane;
+// kPart: the op writes per-row-block partial sums part[4 gi + k]; Pre: the
+// epilogue inputs of one row, loaded when a group starts (pre) so that their
+// latency hides behind the group's slots; slot / add: per-slot constants and
+// the accumulation of one value times one gathered source value;
+// combine_row: the words of row k summed over the W warps in a fixed order;
+// finish_row: the row update, returning the row's share of the partial sum.
 
-template <typename T, typename XT, typename AT>
-__device__ __forceinline__ AT row_part(const GridC &g, const GraphP &gp, const T *__restrict__ val,
-                                       const XT *__restrict__ x, int row, int w) {
-    const int z = row / g.nxy, r = row - z * g.nxy, yy = r / g.nx, xx = r - yy * g.nx;
-    const int t0 = __ldg(gp.tstart + z), nt = __ldg(gp.tstart + z + 1) - t0;
-    const T *v = val + val_base(__ldg(gp.voff + z), nt, r);
-    const size_t stride = (size_t)kGroup;
-    AT acc = AT(0);
-#pragma unroll 4
-    for (int t = w; t < nt; t += kSplit) {
-        const int4 te = __ldg(gp.tmpl + t0 + t);
-        const int j = slot_src(g, row, xx, yy, te);
-        acc += (AT)__ldg(v + (size_t)t * stride) * (AT)__ldg(x + j);
-    }
-    return acc;
-}
-
-// combine the kSplit partial sums of each row; valid in warp 0
-template <typename AT>
-__device__ __forceinline__ AT combine_parts(AT part) {
-    __shared__ AT sh[kSplit][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    sh[w][lane] = part;
-    __syncthreads();
-    AT tot = AT(0);
-    if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < kSplit; ++k) tot += sh[k][lane];
-    }
-    return tot;
-}
-
-// ---- four rows per thread (nx divisible by 4): rows row0 .. row0 + 3 share y
-// and the template, their values of a slot are one aligned 16-byte load, and
-// their sources are consecutive apart from the periodic wrap in x.
-constexpr int kQSplit = 8;
-
-template <typename T>
-struct Vec4T;
-template <>
-struct Vec4T<float> {
-    __device__ static __forceinline__ void load(const float *p, float &a, float &b, float &c, float &d) {
-        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-        a = v.x;
-        b = v.y;
-        c = v.z;
-        d = v.w;
-    }
-};
-template <>
-struct Vec4T<double> {
-    __device__ static __forceinline__ void load(const double *p, double &a, double &b, double &c, double &d) {
-        double2 v0 = __ldg(reinterpret_cast<const double2 *>(p)), v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
-        a = v0.x;
-        b = v0.y;
-        c = v1.x;
-        d = v1.y;
-    }
-};
-
-template <typename T, typename XT, typename AT>
-__device__ __forceinline__ void quad_part(const GridC &g, const GraphP &gp, const T *__restrict__ val,
-                                          const XT *__restrict__ x, int row0, int w, AT acc[4]) {
-    const int z = row0 / g.nxy, r0 = row0 - z * g.nxy, y = r0 / g.nx, x0 = r0 - y * g.nx;
-    const int t0 = __ldg(gp.tstart + z), nt = __ldg(gp.tstart + z + 1) - t0;
-    const T *v = val + val_base(__ldg(gp.voff + z), nt, r0);
-    const size_t stride = (size_t)kGroup;
-#pragma unroll 2
-    for (int t = w; t < nt; t += kQSplit) {
-        const int4 te = __ldg(gp.tmpl + t0 + t);
-        const int sy = y + tmpl_sdy(te), sx = x0 + tmpl_sdx(te);
-        const int jb = row0 + te.y + (sy < 0 ? g.nxy : 0) - (sy >= g.ny ? g.nxy : 0);
-        T v0, v1, v2, v3;
-        Vec4T<T>::load(v + (size_t)t * stride, v0, v1, v2, v3);
-        const int j0 = jb + (sx < 0 ? g.nx : 0) - (sx >= g.nx ? g.nx : 0);
-        const int j1 = jb + 1 + (sx + 1 < 0 ? g.nx : 0) - (sx + 1 >= g.nx ? g.nx : 0);
-        const int j2 = jb + 2 + (sx + 2 < 0 ? g.nx : 0) - (sx + 2 >= g.nx ? g.nx : 0);
-        const int j3 = jb + 3 + (sx + 3 < 0 ? g.nx : 0) - (sx + 3 >= g.nx ? g.nx : 0);
-        acc[0] += (AT)v0 * (AT)__ldg(x + j0);
-        acc[1] += (AT)v1 * (AT)__ldg(x + j1);
-        acc[2] += (AT)v2 * (AT)__ldg(x + j2);
-        acc[3] += (AT)v3 * (AT)__ldg(x + j3);
-    }
-}
-
-// combine kQSplit partials of four rows per lane; valid in warp 0
-template <typename AT>
-__device__ __forceinline__ void combine_quad(AT acc[4]) {
-    __shared__ AT sh[kQSplit][4][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) sh[w][k][lane] = acc[k];
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            AT t = AT(0);
-#pragma unroll
-            for (int q = 0; q < kQSplit; ++q) t += sh[q][k][lane];
-            acc[k] = t;
-        }
-    }
-}
-
+// MODE 0: y = b + K x (b may be null); MODE 1: y = x - K x
 template <typename T, int MODE>
-__global__ void __launch_bounds__(32 * kQSplit) k_spmv4(GridC g, GraphP gp, const T *__restrict__ val,
-                                                        const T *__restrict__ x, const T *__restrict__ b,
-                                                        T *__restrict__ y) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    if (live) quad_part<T, T, T>(g, gp, val, x, row0, w, acc);
-    combine_quad<T>(acc);
-    if (w == 0 && live) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (MODE == 0)
-                y[row0 + k] = (b ? b[row0 + k] : T(0)) + acc[k];
-            else
-                y[row0 + k] = x[row0 + k] - acc[k];
-        }
+struct OpSpmv {
+    using A = T;
+    static constexpr int NA = 4;
+    static constexpr bool kPart = false;
+    struct Pre {
+        T u;
+    };
+    const T *x, *b;
+    T *y;
+    __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        Pre p;
+        p.u = MODE == 0 ? (b ? b[G.rp[k]] : T(0)) : x[G.rp[k]];
+        return p;
     }
-}
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+        sum_word<W, A, NA>(sh, lane, k, a);
+    }
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
+        store_h(y, G, k, MODE == 0 ? p.u + a[k] : p.u - a[k]);
+        return 0.0;
+    }
+};
 
+// r = s - x + K x with FP64 x and FP64 accumulation; partial sums of r^2
 template <typename T>
-__global__ void __launch_bounds__(32 * kQSplit) k_resid64_4(GridC g, GraphP gp, const T *__restrict__ val,
-                                                            const T *__restrict__ s, const double *__restrict__ x,
-                                                            double *__restrict__ r, double *__restrict__ part) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (live) quad_part<T, double, double>(g, gp, val, x, row0, w, acc);
-    combine_quad<double>(acc);
-    double sq = 0.0;
-    if (w == 0 && live) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            double v = (double)s[row0 + k] - x[row0 + k] + acc[k];
-            r[row0 + k] = v;
-            sq += v * v;
-        }
+struct OpResid64 {
+    using A = double;
+    static constexpr int NA = 4;
+    static constexpr bool kPart = true;
+    struct Pre {
+        double s, x;
+    };
+    const T *s;
+    const double *x;
+    double *r, *part;
+    __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += (double)v * __ldg(x + j); }
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        Pre p;
+        p.s = (double)s[G.row[k]];
+        p.x = x[G.rp[k]];
+        return p;
     }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (lane == 0) red[w] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kQSplit; ++i) t += red[i];
-        part[blockIdx.x] = t;
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+        sum_word<W, A, NA>(sh, lane, k, a);
     }
-}
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
+        const double vv = p.s - p.x + a[k];
+        store_h(r, G, k, vv);
+        return vv * vv;
+    }
+};
 
-// Neumann sweep that also records ||y - x||^2 per block (the norm of K^k r
-// along the series, for the power estimate of the largest eigenvalue)
+// Neumann sweep y = b + K x with partial sums of (y - x)^2
 template <typename T>
-__global__ void __launch_bounds__(32 * kQSplit) k_sweep_pow4(GridC g, GraphP gp, const T *__restrict__ val,
-                                                             const T *__restrict__ x, const T *__restrict__ b,
-                                                             T *__restrict__ y, double *__restrict__ part) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    if (live) quad_part<T, T, T>(g, gp, val, x, row0, w, acc);
-    combine_quad<T>(acc);
-    double sq = 0.0;
-    if (w == 0 && live) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            T v = b[row0 + k] + acc[k];
-            double dd = (double)v - (double)x[row0 + k];
-            sq += dd * dd;
-            y[row0 + k] = v;
-        }
+struct OpSweepPow {
+    using A = T;
+    static constexpr int NA = 4;
+    static constexpr bool kPart = true;
+    struct Pre {
+        T b, x;
+    };
+    const T *x, *b;
+    T *y;
+    double *part;
+    __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        Pre p;
+        p.b = b[G.rp[k]];
+        p.x = x[G.rp[k]];
+        return p;
     }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (lane == 0) red[w] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kQSplit; ++i) t += red[i];
-        part[blockIdx.x] = t;
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+        sum_word<W, A, NA>(sh, lane, k, a);
     }
-}
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
+        const T vv = p.b + a[k];
+        const T dd = vv - p.x;
+        store_h(y, G, k, vv);
+        return (double)(dd * dd);
+    }
+};
 
 // One Chebyshev step on (I - K) d = r0 (three-term form):
 //   q = K p;  r <- r - p + q;  d <- d + p;  p' = c1 p + c2 r
 template <typename T>
-__global__ void __launch_bounds__(32 * kQSplit) k_cheb4(GridC g, GraphP gp, const T *__restrict__ val,
-                                                        const T *__restrict__ p, T *__restrict__ r,
-                                                        T *__restrict__ d, T *__restrict__ pn, T c1, T c2) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    if (live) quad_part<T, T, T>(g, gp, val, p, row0, w, acc);
-    combine_quad<T>(acc);
-    if (w == 0 && live) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = row0 + k;
-            const T pi = p[i];
-            const T rr = r[i] - pi + acc[k];
-            r[i] = rr;
-            d[i] += pi;
-            pn[i] = c1 * pi + c2 * rr;
-        }
+struct OpCheb {
+    using A = T;
+    static constexpr int NA = 4;
+    static constexpr bool kPart = false;
+    struct Pre {
+        T p, r, d;
+    };
+    const T *p;
+    T *r, *d, *pn;
+    T c1, c2;
+    __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(p + j); }
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        const int ip = G.rp[k];
+        Pre q;
+        q.p = p[ip];
+        q.r = r[ip];
+        q.d = d[ip];
+        return q;
     }
-}
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+        sum_word<W, A, NA>(sh, lane, k, a);
+    }
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &q) const {
+        const T rr = q.r - q.p + a[k];
+        store_h(r, G, k, rr);
+        store_h(d, G, k, q.d + q.p);
+        store_h(pn, G, k, c1 * q.p + c2 * rr);
+        return 0.0;
+    }
+};
 
 // ---- residual in double-single arithmetic (pairs of FP32 numbers).  x is
 // held as x_hi + x_lo (x_hi = fl32(x), x_lo = fl32(x - x_hi)); each product
@@ -266,65 +178,50 @@ __device__ __forceinline__ void ds_add_prod(float &hi, float &lo, float v, float
     lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(err, e), __fmul_rn(v, xl)));
 }
 
-__device__ __forceinline__ void quad_part_ds(const GridC &g, const GraphP &gp, const float *__restrict__ val,
-                                             const float *__restrict__ xh, const float *__restrict__ xl, int row0,
-                                             int w, double acc[4]) {
-    const int z = row0 / g.nxy, r0 = row0 - z * g.nxy, y = r0 / g.nx, x0 = r0 - y * g.nx;
-    const int t0 = __ldg(gp.tstart + z), nt = __ldg(gp.tstart + z + 1) - t0;
-    const float *v = val + val_base(__ldg(gp.voff + z), nt, r0);
-    float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, l0 = 0.f, l1 = 0.f, l2 = 0.f, l3 = 0.f;
-#pragma unroll 2
-    for (int t = w; t < nt; t += kQSplit) {
-        const int4 te = __ldg(gp.tmpl + t0 + t);
-        const int sy = y + tmpl_sdy(te), sx = x0 + tmpl_sdx(te);
-        const int jb = row0 + te.y + (sy < 0 ? g.nxy : 0) - (sy >= g.ny ? g.nxy : 0);
-        float v0, v1, v2, v3;
-        Vec4T<float>::load(v + (size_t)t * kGroup, v0, v1, v2, v3);
-        const int j0 = jb + (sx < 0 ? g.nx : 0) - (sx >= g.nx ? g.nx : 0);
-        const int j1 = jb + 1 + (sx + 1 < 0 ? g.nx : 0) - (sx + 1 >= g.nx ? g.nx : 0);
-        const int j2 = jb + 2 + (sx + 2 < 0 ? g.nx : 0) - (sx + 2 >= g.nx ? g.nx : 0);
-        const int j3 = jb + 3 + (sx + 3 < 0 ? g.nx : 0) - (sx + 3 >= g.nx ? g.nx : 0);
-        ds_add_prod(h0, l0, v0, __ldg(xh + j0), __ldg(xl + j0));
-        ds_add_prod(h1, l1, v1, __ldg(xh + j1), __ldg(xl + j1));
-        ds_add_prod(h2, l2, v2, __ldg(xh + j2), __ldg(xl + j2));
-        ds_add_prod(h3, l3, v3, __ldg(xh + j3), __ldg(xl + j3));
+// r = s - x + K x with K x summed in FP32 pairs (a[k]: high part, a[4 + k]: low part)
+struct OpResidDS {
+    using A = float;
+    static constexpr int NA = 8;
+    static constexpr bool kPart = true;
+    struct Pre {
+        double s, x;
+    };
+    const float *s;
+    const double *x;
+    const float *xh, *xl;
+    double *r, *part;
+    __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
+    __device__ __forceinline__ void add(A *a, int k, float v, int j, NoSlot) const {
+        ds_add_prod(a[k], a[4 + k], v, __ldg(xh + j), __ldg(xl + j));
     }
-    acc[0] = (double)h0 + (double)l0;
-    acc[1] = (double)h1 + (double)l1;
-    acc[2] = (double)h2 + (double)l2;
-    acc[3] = (double)h3 + (double)l3;
-}
-
-__global__ void __launch_bounds__(32 * kQSplit) k_resid_ds4(GridC g, GraphP gp, const float *__restrict__ val,
-                                                            const float *__restrict__ s, const double *__restrict__ x,
-                                                            const float *__restrict__ xh,
-                                                            const float *__restrict__ xl, double *__restrict__ r,
-                                                            double *__restrict__ part) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (live) quad_part_ds(g, gp, val, xh, xl, row0, w, acc);
-    combine_quad<double>(acc);
-    double sq = 0.0;
-    if (w == 0 && live) {
+    __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
+        Pre p;
+        p.s = (double)s[G.row[k]];
+        p.x = x[G.rp[k]];
+        return p;
+    }
+    // the W (hi, lo) partials of row k combined with FP32 two-sums
+    template <int W>
+    __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
+        float h = 0.f, l = 0.f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            double vv = (double)s[row0 + k] - x[row0 + k] + acc[k];
-            r[row0 + k] = vv;
-            sq += vv * vv;
+        for (int q = 0; q < W; ++q) {
+            const float pp = sh[q][k][lane];
+            const float ss = __fadd_rn(h, pp);
+            const float bb = __fsub_rn(ss, h);
+            l = __fadd_rn(l, __fadd_rn(__fadd_rn(__fsub_rn(h, __fsub_rn(ss, bb)), __fsub_rn(pp, bb)),
+                                       sh[q][k + 4][lane]));
+            h = ss;
         }
+        a[k] = h;
+        a[k + 4] = l;
     }
-    __shared__ double red[32];
-    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (lane == 0) red[w] = sq;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < kQSplit; ++i) t += red[i];
-        part[blockIdx.x] = t;
+    __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
+        const double vv = p.s - p.x + ((double)a[k] + (double)a[k + 4]);
+        store_h(r, G, k, vv);
+        return vv * vv;
     }
-}
+};
 
 // x += d, with the double-single split of the new x
 template <typename T>
@@ -341,128 +238,109 @@ __global__ void k_update_x(int n, const T *__restrict__ d, double *__restrict__ 
     }
 }
 
-static bool quad_ok(const GridC &g) { return g.nx % 4 == 0; }
+// partial sums of a sweep or residual pass: one per row block (4 per group)
+int sweep_blocks(const GridC &g) { return 4 * (g.nz + 1) * g.gpl; }
+int resid_blocks(const GridC &g) { return sweep_blocks(g); }
 
-// MODE 0: y = b + K x (b may be null); MODE 1: y = x - K x
-template <typename T, int MODE>
-__global__ void __launch_bounds__(32 * kSplit) k_spmv(GridC g, GraphP gp, const T *__restrict__ val,
-                                                      const T *__restrict__ x, const T *__restrict__ b,
-                                                      T *__restrict__ y) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 32 + lane;
-    const bool live = row < g.n_nodes;
-    T part = live ? row_part<T, T, T>(g, gp, val, x, row, w) : T(0);
-    T acc = combine_parts<T>(part);
-    if (w == 0 && live) {
-        if (MODE == 0)
-            y[row] = (b ? b[row] : T(0)) + acc;
+bool stage_fits(int ntmax) { return ntmax > 0; }
+
+// Warps per group (measured on GB300, plume 64 x 64 x 32): the streamed
+// passes run 16 consumer warps per SM; the plain solver passes are fastest
+// with 4 warps per group while all groups fit in one wave of resident
+// blocks, else with the count that fills the last wave best.
+template <typename T>
+int choose_wq_t(const GridC &g) {
+    if (sizeof(T) == 4 && g.stage) return 16;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0)
+        return 4;
+    const long long blocks = (long long)(g.nz + 1) * g.gpl;
+    int best = 4;
+    double best_eff = -1.0;
+    const int cand[3] = {4, 6, 8};
+    for (int i = 0; i < 3; ++i) {
+        int w = cand[i], bps = 0;
+        cudaError_t e;
+        if (w == 8)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_plain<8, T, OpCheb<T>>, 32 * 8, 0);
+        else if (w == 6)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_plain<6, T, OpCheb<T>>, 32 * 6, 0);
         else
-            y[row] = x[row] - acc;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_plain<4, T, OpCheb<T>>, 32 * 4, 0);
+        if (e != cudaSuccess || bps <= 0) continue;
+        const double waves = (double)blocks / ((double)sms * bps);
+        if (w == 4 && waves <= 1.0) {
+            best = 4;
+            break;
+        }
+        const double eff = waves / std::ceil(waves);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = w;
+        }
     }
+    cudaGetLastError();  // clear a failed occupancy query
+    return best;
+}
+
+int choose_wq(const GridC &g, bool fp64) { return fp64 ? choose_wq_t<double>(g) : choose_wq_t<float>(g); }
+
+template <typename T>
+void launch_spmv(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y) {
+    OpSpmv<T, 0> op;
+    op.x = x;
+    op.b = b;
+    op.y = y;
+    run_op(st, g, gp, val, op, 0);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kSplit) k_sweep_pow(GridC g, GraphP gp, const T *__restrict__ val,
-                                                           const T *__restrict__ x, const T *__restrict__ b,
-                                                           T *__restrict__ y, double *__restrict__ part) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 32 + lane;
-    const bool live = row < g.n_nodes;
-    T pr = live ? row_part<T, T, T>(g, gp, val, x, row, w) : T(0);
-    T acc = combine_parts<T>(pr);
-    double sq = 0.0;
-    if (w == 0 && live) {
-        T v = b[row] + acc;
-        double dd = (double)v - (double)x[row];
-        sq = dd * dd;
-        y[row] = v;
-    }
-    double bs = block_sum(sq);
-    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+void launch_imk(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, T *y) {
+    OpSpmv<T, 1> op;
+    op.x = x;
+    op.b = nullptr;
+    op.y = y;
+    run_op(st, g, gp, val, op, 0);
 }
-
-template <typename T>
-__global__ void __launch_bounds__(32 * kSplit) k_cheb(GridC g, GraphP gp, const T *__restrict__ val,
-                                                      const T *__restrict__ p, T *__restrict__ r, T *__restrict__ d,
-                                                      T *__restrict__ pn, T c1, T c2) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 32 + lane;
-    const bool live = row < g.n_nodes;
-    T pr = live ? row_part<T, T, T>(g, gp, val, p, row, w) : T(0);
-    T acc = combine_parts<T>(pr);
-    if (w == 0 && live) {
-        const T pi = p[row];
-        const T rr = r[row] - pi + acc;
-        r[row] = rr;
-        d[row] += pi;
-        pn[row] = c1 * pi + c2 * rr;
-    }
-}
-
-int sweep_blocks(const GridC &g) { return quad_ok(g) ? (g.n_nodes / 4 + 31) / 32 : (g.n_nodes + 31) / 32; }
 
 template <typename T>
 void launch_sweep_pow(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y,
                       double *part) {
-    if (quad_ok(g))
-        k_sweep_pow4<T><<<sweep_blocks(g), 32 * kQSplit, 0, st>>>(g, gp, val, x, b, y, part);
-    else
-        k_sweep_pow<T><<<sweep_blocks(g), 32 * kSplit, 0, st>>>(g, gp, val, x, b, y, part);
+    OpSweepPow<T> op;
+    op.x = x;
+    op.b = b;
+    op.y = y;
+    op.part = part;
+    run_op(st, g, gp, val, op, 0);
 }
 
 template <typename T>
 void launch_cheb(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *p, T *r, T *d, T *pn,
                  double c1, double c2) {
-    if (quad_ok(g))
-        k_cheb4<T><<<sweep_blocks(g), 32 * kQSplit, 0, st>>>(g, gp, val, p, r, d, pn, (T)c1, (T)c2);
-    else
-        k_cheb<T><<<sweep_blocks(g), 32 * kSplit, 0, st>>>(g, gp, val, p, r, d, pn, (T)c1, (T)c2);
+    OpCheb<T> op;
+    op.p = p;
+    op.r = r;
+    op.d = d;
+    op.pn = pn;
+    op.c1 = (T)c1;
+    op.c2 = (T)c2;
+    run_op(st, g, gp, val, op, 0);
 }
 
-template <typename T>
-void launch_spmv(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y) {
-    if (quad_ok(g))
-        k_spmv4<T, 0><<<(g.n_nodes / 4 + 31) / 32, 32 * kQSplit, 0, st>>>(g, gp, val, x, b, y);
-    else
-        k_spmv<T, 0><<<(g.n_nodes + 31) / 32, 32 * kSplit, 0, st>>>(g, gp, val, x, b, y);
-}
-
-template <typename T>
-void launch_imk(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, T *y) {
-    if (quad_ok(g))
-        k_spmv4<T, 1><<<(g.n_nodes / 4 + 31) / 32, 32 * kQSplit, 0, st>>>(g, gp, val, x, nullptr, y);
-    else
-        k_spmv<T, 1><<<(g.n_nodes + 31) / 32, 32 * kSplit, 0, st>>>(g, gp, val, x, nullptr, y);
-}
-
-
-// r = s - x + K x with FP64 x and FP64 accumulation; per-block sums of r^2
-template <typename T>
-__global__ void __launch_bounds__(32 * kSplit) k_resid64(GridC g, GraphP gp, const T *__restrict__ val,
-                                                         const T *__restrict__ s, const double *__restrict__ x,
-                                                         double *__restrict__ r, double *__restrict__ part) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 32 + lane;
-    const bool live = row < g.n_nodes;
-    double p = live ? row_part<T, double, double>(g, gp, val, x, row, w) : 0.0;
-    double acc = combine_parts<double>(p);
-    double sq = 0.0;
-    if (w == 0 && live) {
-        double v = (double)s[row] - x[row] + acc;
-        r[row] = v;
-        sq = v * v;
-    }
-    double b = block_sum(sq);
-    if (threadIdx.x == 0) part[blockIdx.x] = b;
-}
-
-int resid_blocks(const GridC &g) { return quad_ok(g) ? (g.n_nodes / 4 + 31) / 32 : (g.n_nodes + 31) / 32; }
-
-bool resid_ds_ok(const GridC &g) { return quad_ok(g); }
+bool resid_ds_ok(const GridC &g) { return true; }
 
 void launch_resid_ds(cudaStream_t st, const GridC &g, const GraphP &gp, const float *val, const float *s,
                      const double *x, const float *xh, const float *xl, double *r, double *part, int nblk) {
-    k_resid_ds4<<<nblk, 32 * kQSplit, 0, st>>>(g, gp, val, s, x, xh, xl, r, part);
+    (void)nblk;
+    OpResidDS op;
+    op.s = s;
+    op.x = x;
+    op.xh = xh;
+    op.xl = xl;
+    op.r = r;
+    op.part = part;
+    run_op(st, g, gp, val, op, 0);
 }
 
 template <typename T>
@@ -473,23 +351,49 @@ void launch_update_x(cudaStream_t st, int n, const T *d, double *x, float *xh, f
 template <typename T>
 void launch_resid64(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *s, const double *x,
                     double *r, double *part, int nblk) {
-    if (quad_ok(g))
-        k_resid64_4<T><<<nblk, 32 * kQSplit, 0, st>>>(g, gp, val, s, x, r, part);
-    else
-        k_resid64<T><<<nblk, 32 * kSplit, 0, st>>>(g, gp, val, s, x, r, part);
+    (void)nblk;
+    OpResid64<T> op;
+    op.s = s;
+    op.x = x;
+    op.r = r;
+    op.part = part;
+    run_op(st, g, gp, val, op, 0);
+}
+
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+    }
+    return r;  // valid in thread 0
 }
 
 // ---------------------------------------------------------------------------
 // Reductions
 
+// Dot products over the nodes of haloed vectors (each node once, halo
+// copies skipped): warp per line of nx nodes, lines strided over the grid.
 template <typename A, typename B>
-__global__ void k_dots(int n, const A *__restrict__ V, size_t ldv, int ncol, const B *__restrict__ y,
+__global__ void k_dots(GridC g, const A *__restrict__ V, size_t ldv, int ncol, const B *__restrict__ y,
                        double *__restrict__ part) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5), nw = gridDim.x * wpb;
+    const int nlines = (g.nz + 1) * g.ny;
     for (int k = 0; k < ncol; ++k) {
         const A *v = V + (size_t)k * ldv;
         double acc = 0.0;
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-            acc += (double)v[i] * (double)y[i];
+        for (int l = gw; l < nlines; l += nw) {
+            const int z = l / g.ny, yy = l - z * g.ny;
+            const long long base = halo_pos(g, 0, yy, z);
+            for (int x = lane; x < g.nx; x += 32) acc += (double)v[base + x] * (double)y[base + x];
+        }
         double b = block_sum(acc);
         if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = b;
     }
@@ -511,23 +415,60 @@ __global__ void k_finalize(const double *__restrict__ part, int nblk, int ncol, 
     (void)ncol;
 }
 
-int dot_blocks(int n) {
-    long long b = ((long long)n + 2047) / 2048;
+int dot_blocks(const GridC &g) {
+    long long b = ((long long)(g.nz + 1) * g.ny + 7) / 8;
     if (b > 296) b = 296;
     if (b < 1) b = 1;
     return (int)b;
 }
 
 template <typename A, typename B>
-void launch_dots(cudaStream_t st, int n, const A *V, size_t ldv, int ncol, const B *y, double *part, int nblk,
-                 double *out) {
-    k_dots<A, B><<<nblk, 256, 0, st>>>(n, V, ldv, ncol, y, part);
+void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int ncol, const B *y, double *part,
+                 int nblk, double *out) {
+    k_dots<A, B><<<nblk, 256, 0, st>>>(g, V, ldv, ncol, y, part);
     k_finalize<<<ncol, 256, 0, st>>>(part, nblk, ncol, out);
 }
 
 template <typename T>
-void launch_sumsq(cudaStream_t st, int n, const T *x, double *part, int nblk, double *out) {
-    launch_dots<T, T>(st, n, x, 0, 1, x, part, nblk, out);
+void launch_sumsq(cudaStream_t st, const GridC &g, const T *x, double *part, int nblk, double *out) {
+    launch_dots<T, T>(st, g, x, 0, 1, x, part, nblk, out);
+}
+
+// haloed dst <- node-ordered src (every halo copy written)
+template <typename T, typename U>
+__global__ void k_to_halo(GridC g, const T *__restrict__ src, U *__restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_nodes) return;
+    const int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    const long long p = halo_pos(g, x, y, z);
+    const int ax = x < g.H ? g.nx : (x >= g.nx - g.H ? -g.nx : 0);
+    const int ay = y < g.H ? g.ny * g.nxp : (y >= g.ny - g.H ? -g.ny * g.nxp : 0);
+    const U v = (U)src[i];
+    dst[p] = v;
+    if (ax) dst[p + ax] = v;
+    if (ay) {
+        dst[p + ay] = v;
+        if (ax) dst[p + ax + ay] = v;
+    }
+}
+
+// node-ordered dst <- haloed src
+template <typename U>
+__global__ void k_from_halo(GridC g, const U *__restrict__ src, U *__restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_nodes) return;
+    const int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    dst[i] = src[halo_pos(g, x, y, z)];
+}
+
+template <typename T, typename U>
+void launch_to_halo(cudaStream_t st, const GridC &g, const T *src, U *dst) {
+    k_to_halo<T, U><<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g, src, dst);
+}
+
+template <typename U>
+void launch_from_halo(cudaStream_t st, const GridC &g, const U *src, U *dst) {
+    k_from_halo<U><<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g, src, dst);
 }
 
 void launch_finalize2(cudaStream_t st, const double *part, int nblk, double *out) {
@@ -603,8 +544,11 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
     template void launch_imk<T>(cudaStream_t, const GridC &, const GraphP &, const T *, const T *, T *);             \
     template void launch_resid64<T>(cudaStream_t, const GridC &, const GraphP &, const T *, const T *,               \
                                     const double *, double *, double *, int);                                       \
-    template void launch_dots<T, T>(cudaStream_t, int, const T *, size_t, int, const T *, double *, int, double *); \
-    template void launch_sumsq<T>(cudaStream_t, int, const T *, double *, int, double *);                           \
+    template void launch_dots<T, T>(cudaStream_t, const GridC &, const T *, size_t, int, const T *, double *, int,  \
+                                    double *);                                                                      \
+    template void launch_sumsq<T>(cudaStream_t, const GridC &, const T *, double *, int, double *);                 \
+    template void launch_to_halo<T, double>(cudaStream_t, const GridC &, const T *, double *);                      \
+    template void launch_from_halo<T>(cudaStream_t, const GridC &, const T *, T *);                                 \
     template void launch_axpy_to64<T>(cudaStream_t, int, const T *, double *);                                      \
     template void launch_scale<T>(cudaStream_t, int, const T *, double, T *);                                       \
     template void launch_gmres_update<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);           \

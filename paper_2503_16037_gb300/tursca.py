@@ -182,6 +182,8 @@ def tursca_launch_count(scene) -> int:
 
 
 OPT_RESIDUAL_FP64 = 1
+OPT_GROUP_WARPS = 2
+OPT_STAGE_VALUES = 3
 
 
 def tursca_set_option(scene, option: int, value: float):
