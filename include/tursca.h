@@ -202,8 +202,7 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *   TURSCA_OPT_GROUP_WARPS: warps that share each group of 128 rows in the
  *     sweep, Chebyshev, residual and emission passes: 4, 6, 8 or 16 (the
  *     streamed passes take 4, 8 or 16), or 0 to let the library pick
- *     (default: 4 for the solver passes and 6 for the emission pass, 16 for
- *     the streamed passes).
+ *     (default: 6, 16 for the streamed passes).
  *   TURSCA_OPT_STAGE_VALUES: 0 (default) runs one block per group of 128
  *     rows that reads the matrix values directly; 1 runs the FP32 sweep,
  *     Chebyshev, residual and emission passes as persistent kernels (one

@@ -244,21 +244,22 @@ int resid_blocks(const GridC &g) { return sweep_blocks(g); }
 
 bool stage_fits(int ntmax) { return ntmax > 0; }
 
-// Warps per group (measured on GB300, plume 64 x 64 x 32): the streamed
-// passes run 16 consumer warps per SM; the plain solver passes are fastest
-// with 4 warps per group while all groups fit in one wave of resident
-// blocks, else with the count that fills the last wave best.
+// Warps per group (measured on GB300, plume 64 x 64 x 32, interleaved runs):
+// the streamed passes run 16 consumer warps per SM; the plain passes with
+// programmatic launches are fastest with 6 warps per group while all groups
+// fit in one wave of resident blocks, else with the count that fills the
+// last wave best.
 template <typename T>
 int choose_wq_t(const GridC &g) {
     if (sizeof(T) == 4 && g.stage) return 16;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                    cudaSuccess || sms <= 0)
-        return 4;
+        return 6;
     const long long blocks = (long long)(g.nz + 1) * g.gpl;
-    int best = 4;
+    int best = 6;
     double best_eff = -1.0;
-    const int cand[3] = {4, 6, 8};
+    const int cand[3] = {6, 8, 4};
     for (int i = 0; i < 3; ++i) {
         int w = cand[i], bps = 0;
         cudaError_t e;
@@ -270,8 +271,8 @@ int choose_wq_t(const GridC &g) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_plain<4, T, OpCheb<T>>, 32 * 4, 0);
         if (e != cudaSuccess || bps <= 0) continue;
         const double waves = (double)blocks / ((double)sms * bps);
-        if (w == 4 && waves <= 1.0) {
-            best = 4;
+        if (w == 6 && waves <= 1.0) {
+            best = 6;
             break;
         }
         const double eff = waves / std::ceil(waves);

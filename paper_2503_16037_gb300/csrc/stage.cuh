@@ -336,22 +336,65 @@ __device__ __forceinline__ double ld_stream(const double *p) {
 #endif
 }
 
+// Programmatic dependent launch: a pass may be launched while the previous
+// pass on the stream is still running.  Everything it reads before
+// pdl_wait() (graph structure, the values of K) was written by earlier,
+// completed work; pdl_wait() returns once the previous pass has completed
+// and its writes are visible (a hardware wait, no polling).  pdl_trigger()
+// lets the next pass launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+#ifndef TK_PDL_PEEL
+#define TK_PDL_PEEL 1
+#endif
+
 // The plain driver over groups [0, gridDim.x): block gi = group gi, W warps,
-// values read from global memory.
+// values read from global memory.  The values of each warp's first two slots
+// are requested before waiting for the previous pass.
 template <int W, typename T, class Op>
 __global__ void __launch_bounds__(32 * W) k_plain(GridC g, GraphP gp, const T *__restrict__ val, Op op) {
     using A = typename Op::A;
     constexpr int NA = Op::NA;
     __shared__ A sh[W][NA][32];
+    pdl_trigger();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
-    const typename Op::Pre pre = load_pre(op, G);
+    const T *v = val + G.vb + lane;
     A a[NA];
 #pragma unroll
     for (int m = 0; m < NA; ++m) a[m] = A(0);
-    const T *v = val + G.vb + lane;
+#if TK_PDL_PEEL
+    // the values of the warp's first two slots are requested before waiting
+    T v0[4], v1[4];
+    const int tA = w, tB = w + W;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v0[k] = tA < G.nt ? ld_stream(v + (size_t)tA * kGroup + 32 * k) : T(0);
+        v1[k] = tB < G.nt ? ld_stream(v + (size_t)tB * kGroup + 32 * k) : T(0);
+    }
+    pdl_wait();
+    const typename Op::Pre pre = load_pre(op, G);
+    if (tA < G.nt) {
+        const int fp = __ldg(gp.tflat + G.t0 + tA);
+        const auto si = op.slot(gp, G.t0 + tA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) op.add(a, k, v0[k], G.rp[k] + fp, si);
+    }
+    if (tB < G.nt) {
+        const int fp = __ldg(gp.tflat + G.t0 + tB);
+        const auto si = op.slot(gp, G.t0 + tB);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) op.add(a, k, v1[k], G.rp[k] + fp, si);
+    }
+    const int tfirst = w + 2 * W;
+#else
+    pdl_wait();
+    const typename Op::Pre pre = load_pre(op, G);
+    const int tfirst = w;
+#endif
 #pragma unroll kSweepUnroll
-    for (int t = w; t < G.nt; t += W) {
+    for (int t = tfirst; t < G.nt; t += W) {
         const int fp = __ldg(gp.tflat + G.t0 + t);
         const auto si = op.slot(gp, G.t0 + t);
         const T *vt = v + (size_t)t * kGroup;
@@ -378,6 +421,9 @@ static void run_pipe(cudaStream_t st, const GridC &g, const GraphP &gp, const fl
     k_pipe<W, Op><<<gp.run_n[kind], 32 * (W + 1), smem, st>>>(g, gp, val, op, kind);
 }
 
+#ifndef TK_PDL
+#define TK_PDL 1
+#endif
 #ifndef TK_PLAIN_CARVEOUT
 #define TK_PLAIN_CARVEOUT -1
 #endif
@@ -392,7 +438,18 @@ static void run_plain(cudaStream_t st, const GridC &g, const GraphP &gp, const T
         attr[dev] = true;
     }
 #endif
-    k_plain<W, T, Op><<<ngroups, 32 * W, 0, st>>>(g, gp, val, op);
+    // launched as a programmatic dependent of the previous work on the stream
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ngroups);
+    cfg.blockDim = dim3(32 * W);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = TK_PDL;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_plain<W, T, Op>, g, gp, val, op);
 }
 
 // Dispatch on the warp count and the driver: the pipeline for FP32 scenes
