@@ -41,7 +41,6 @@ struct tursca_scene {
     int4 *tmpl = nullptr;
     long long *voff = nullptr;
     tk::DClass *cls = nullptr;
-    tk::PClass *pcls = nullptr;
     tk::DTap *taps = nullptr;
     float *tlf = nullptr;
     double *tld = nullptr;
@@ -54,6 +53,9 @@ struct tursca_scene {
     int *cell_start = nullptr;
     int *canon_dirs = nullptr, *up_canon = nullptr;
     int *tflat = nullptr;  // template offsets in the haloed layout
+    tk::ASlot *aslot = nullptr;  // edge-kernel descriptors of the template entries
+    int *tap_h = nullptr, *dir_h = nullptr;  // haloed offsets of the taps and the directions
+    void *rt_h = nullptr, *wsp_h = nullptr, *mu_e_h = nullptr, *e1_h = nullptr;  // haloed copies
     int *run_g[2] = {nullptr, nullptr};  // runs of the persistent streamed passes
     long long *run_v[2] = {nullptr, nullptr};
     int run_n[2] = {0, 0};
@@ -197,7 +199,6 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.tmpl = sc->tmpl;
     p.voff = sc->voff;
     p.cls = sc->cls;
-    p.pcls = sc->pcls;
     p.taps = sc->taps;
     p.tap_len_f = sc->tlf;
     p.tap_len_d = sc->tld;
@@ -222,6 +223,9 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.up_canon = sc->up_canon;
     p.status = sc->status;
     p.tflat = sc->tflat;
+    p.aslot = sc->aslot;
+    p.tap_h = sc->tap_h;
+    p.dir_h = sc->dir_h;
     for (int k = 0; k < 2; ++k) {
         p.run_g[k] = sc->run_g[k];
         p.run_v[k] = sc->run_v[k];
@@ -246,6 +250,10 @@ tk::FieldP<T> field_p(const tursca_scene *sc) {
     f.tseg = (T *)sc->tseg;
     f.rt = (T *)sc->rt;
     f.wsp = (T *)sc->wsp;
+    f.rt_h = (T *)sc->rt_h;
+    f.wsp_h = (T *)sc->wsp_h;
+    f.mu_e_h = (T *)sc->mu_e_h;
+    f.e1_h = (T *)sc->e1_h;
     f.q_sun = (T *)sc->q_sun;
     f.hgv = (T *)sc->hgv;
     f.hg0v = (T *)sc->hg0v;
@@ -336,8 +344,18 @@ tursca_status ensure_fields(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->mu_st, na * es), "alloc mu_st");
     CK(dalloc(sc->allocs, sc->tsun, nn * es), "alloc tsun");
     CK(dalloc(sc->allocs, sc->e1, nn * es), "alloc e1");
-    CK(dalloc(sc->allocs, sc->zc_iso, nn * es), "alloc zc");
-    CK(dalloc(sc->allocs, sc->zc_sun, nn * es), "alloc zc");
+    {
+        // haloed arrays of the edge kernel (zeroed once: halo-free entries of
+        // the ground layer are never read but stay defined)
+        const size_t H = (size_t)sc->d.stencil_radius;
+        const size_t npd = (size_t)(sc->d.nz + 1) * (sc->d.nx + 2 * H) * (sc->d.ny + 2 * H);
+        void **hal[6] = {(void **)&sc->zc_iso, (void **)&sc->zc_sun, &sc->rt_h, &sc->mu_e_h, &sc->e1_h, &sc->wsp_h};
+        for (int k = 0; k < 6; ++k) {
+            const size_t bytes = npd * es * (k == 5 ? (size_t)sc->d.n_species : 1);
+            CK(dalloc(sc->allocs, *hal[k], bytes), "alloc haloed");
+            CK(cudaMemsetAsync(*hal[k], 0, bytes, sc->st), "memset haloed");
+        }
+    }
     CK(dalloc(sc->allocs, sc->s, nn * es), "alloc s");
     CK(dalloc(sc->allocs, sc->gsun, na * es), "alloc gsun");
     CK(dalloc(sc->allocs, sc->emis, na * es), "alloc emis");
@@ -857,35 +875,6 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
         o.split_f = (float)o.split;
     }
     CK(upload(sc, sc->allocs, sc->cls, dc.data(), dc.size() * sizeof(tk::DClass)), "upload classes");
-    {
-        std::vector<tk::PClass> pc(G.classes.size());
-        auto b8 = [](int v) { return (unsigned)(v & 0xff); };
-        for (size_t i = 0; i < G.classes.size(); ++i) {
-            const tg::SlotClass &c = G.classes[i];
-            const tk::DClass &o = dc[i];
-            tk::PClass &q = pc[i];
-            float dinv = (float)o.dist1_inv, spl = (float)o.split;
-            int dbits, sbits;
-            std::memcpy(&dbits, &dinv, 4);
-            std::memcpy(&sbits, &spl, 4);
-            q.w0 = make_int4((int)(c.kind | (c.bkind << 8) | (c.c_one << 16) | (c.n1_ground << 24)),
-                             (int)((unsigned)std::max(c.dir, 0) | ((unsigned)c.hgdir << 16)),
-                             (int)((unsigned)std::max(c.up_idx, 0) | ((unsigned)std::max(c.gdir, 0) << 16)), dbits);
-            q.w1 = make_int4((int)(b8(c.seg_tab + 1) | (b8(c.seg_dx) << 8) | (b8(c.seg_dy) << 16) | (b8(c.seg_dz) << 24)),
-                             (int)(b8(c.pre_tab + 1) | (b8(c.pre_dx) << 8) | (b8(c.pre_dy) << 16) | (b8(c.pre_dz) << 24)),
-                             (int)(b8(c.n1_dx) | (b8(c.n1_dy) << 8) | (b8(c.n1_dz) << 16)), sbits);
-            q.w2 = make_int4(c.pre_off, c.seg_off, c.hit_off, (int)(c.pre_n | (c.seg_n << 8) | (c.hit_n << 16)));
-            double dd = o.dist1_inv, ss = o.split;
-            long long di, si;
-            std::memcpy(&di, &dd, 8);
-            std::memcpy(&si, &ss, 8);
-            q.w3 = make_int4((int)(di & 0xffffffff), (int)(di >> 32), (int)(si & 0xffffffff), (int)(si >> 32));
-            if (c.pre_n > 255 || c.seg_n > 255 || c.hit_n > 255 || c.hgdir > 65535)
-                return fail(sc, TURSCA_E_INVALID, "internal error: class does not fit its packed form");
-        }
-        CK(upload(sc, sc->allocs, sc->pcls, pc.data(), pc.size() * sizeof(tk::PClass)), "upload classes");
-        CK(cudaStreamSynchronize(sc->st), "sync");
-    }
     std::vector<tk::DTap> to;
     std::vector<float> lf;
     std::vector<double> ld;
@@ -960,6 +949,42 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
                 tf[i] = (szl - z) * lp + t.sdy * nxp + t.sdx;
             }
         CK(upload(sc, sc->allocs, sc->tflat, tf.data(), tf.size() * sizeof(int)), "upload tmpl");
+        // edge-kernel descriptors (every lookup of a slot as one offset from
+        // the receiver's haloed position)
+        std::vector<tg::EdgeDesc> ed;
+        std::vector<int> th, dh;
+        const std::string err = tg::edge_descriptors(G, H, ed, th, dh);
+        if (!err.empty()) return fail(sc, TURSCA_E_INVALID, "internal error: " + err);
+        std::vector<tk::ASlot> as(ed.size());
+        for (size_t i = 0; i < ed.size(); ++i) {
+            const tg::EdgeDesc &e = ed[i];
+            tk::ASlot &d = as[i];
+            std::memset(&d, 0, sizeof(d));
+            d.src = e.src;
+            d.pre = e.pre;
+            d.seg = e.seg;
+            d.n1 = e.n1;
+            d.aux = e.aux;
+            d.tbase = e.tbase;
+            d.bits = e.bits;
+            d.dir = e.dir;
+            d.hgdir = e.hgdir;
+            d.taps = e.taps;
+            d.pre_off = e.pre_off;
+            d.seg_off = e.seg_off;
+            d.hit_off = e.hit_off;
+            d.q = (float)e.q;
+            d.qd = e.q;
+            d.dinv = (float)e.dinv;
+            d.dinvd = e.dinv;
+            d.split = (float)e.split;
+            d.splitd = e.split;
+        }
+        CK(upload(sc, sc->allocs, sc->aslot, as.data(), as.size() * sizeof(tk::ASlot)), "upload slots");
+        if (th.empty()) th.push_back(0);
+        CK(upload(sc, sc->allocs, sc->tap_h, th.data(), th.size() * sizeof(int)), "upload taps");
+        CK(upload(sc, sc->allocs, sc->dir_h, dh.data(), dh.size() * sizeof(int)), "upload dirs");
+        CK(cudaStreamSynchronize(sc->st), "sync");
     }
     // Runs of the persistent streamed passes: one per SM, each an equal share
     // of the value stream cut at group boundaries (pass 0: all groups, pass
@@ -1000,7 +1025,10 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->val, (size_t)G.nval * sc->es), "alloc val");
     const size_t es = sc->es;
     CK(dalloc(sc->allocs, sc->tinf, (size_t)G.up_dirs.size() * G.n_atm * es), "alloc tinf");
-    CK(dalloc(sc->allocs, sc->tinfg, (size_t)ngd * G.n_ground * es), "alloc tinfg");
+    const size_t Hh = (size_t)sc->d.stencil_radius;
+    const size_t lph = (sc->d.nx + 2 * Hh) * (sc->d.ny + 2 * Hh), nph = (size_t)(sc->d.nz + 1) * lph;
+    CK(dalloc(sc->allocs, sc->tinfg, (size_t)ngd * lph * es), "alloc tinfg");
+    CK(cudaMemsetAsync(sc->tinfg, 0, (size_t)ngd * lph * es, sc->st), "memset tinfg");
     CK(dalloc(sc->allocs, sc->q_sun, (size_t)sc->d.n_species * nd * es), "alloc qsun");
     CK(dalloc(sc->allocs, sc->hgv, (size_t)sc->d.n_species * (nd + ngd) * es), "alloc hgv");
     CK(dalloc(sc->allocs, sc->hg0v, (size_t)sc->d.n_species * es), "alloc hg0v");
@@ -1009,7 +1037,8 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     std::vector<int> upc(G.up_dirs.size());
     for (size_t i = 0; i < upc.size(); ++i) upc[i] = G.canon_of_dir[G.up_dirs[i]];
     CK(upload(sc, sc->allocs, sc->up_canon, upc.data(), upc.size() * sizeof(int)), "upload canon");
-    CK(dalloc(sc->allocs, sc->tseg, G.canon_dirs.size() * (size_t)G.n_atm * es), "alloc tseg");
+    CK(dalloc(sc->allocs, sc->tseg, G.canon_dirs.size() * nph * es), "alloc tseg");
+    CK(cudaMemsetAsync(sc->tseg, 0, G.canon_dirs.size() * nph * es, sc->st), "memset tseg");
     CK(dalloc(sc->allocs, sc->rt, (size_t)G.n_atm * es), "alloc rt");
     CK(dalloc(sc->allocs, sc->wsp, (size_t)sc->d.n_species * G.n_atm * es), "alloc wsp");
     cudaError_t ce = cudaStreamSynchronize(sc->st);

@@ -589,4 +589,68 @@ std::string build_view(const Graph &G, ViewTables &V, double sza, double saa, do
     return std::string();
 }
 
+std::string edge_descriptors(const Graph &G, int H, std::vector<EdgeDesc> &out, std::vector<int> &tap_h,
+                             std::vector<int> &dir_h) {
+    const int nz = G.nz, nxp = G.nx + 2 * H, lp = nxp * (G.ny + 2 * H);
+    const long long npad = (long long)(nz + 1) * lp;
+    auto inside = [&](int dx, int dy) { return std::abs(dx) <= H && std::abs(dy) <= H; };
+    out.assign(G.tmpl.size(), EdgeDesc());
+    for (int z = 0; z <= nz; ++z)
+        for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
+            const TSlot &t = G.tmpl[i];
+            const SlotClass &c = G.classes[t.cls];
+            EdgeDesc &d = out[i];
+            d = EdgeDesc();
+            const bool gsrc = t.sz < 0;
+            const int bz = gsrc ? 0 : t.sz;       // base layer of the source's segments and taps
+            const int szl = gsrc ? nz : t.sz;     // layer of the source node
+            auto rel = [&](int lz, int dx, int dy) { return (lz - z) * lp + (t.sdy + dy) * nxp + (t.sdx + dx); };
+            if (!inside(t.sdx, t.sdy)) return "template offset beyond the halo";
+            d.src = rel(szl, 0, 0);
+            d.pre = -1;
+            d.seg = -1;
+            if (c.pre_tab >= 0) {
+                if (!inside(t.sdx + c.pre_dx, t.sdy + c.pre_dy)) return "segment lookup beyond the halo";
+                d.pre = (int)(c.pre_tab * npad + rel(bz + c.pre_dz, c.pre_dx, c.pre_dy));
+            }
+            if (c.seg_tab >= 0) {
+                if (!inside(t.sdx + c.seg_dx, t.sdy + c.seg_dy)) return "segment lookup beyond the halo";
+                d.seg = (int)(c.seg_tab * npad + rel(bz + c.seg_dz, c.seg_dx, c.seg_dy));
+            }
+            // coupling neighbour: always for ground sources (absolute layer n1_dz),
+            // for atmospheric sources unless the coupling is 1 or n1 is the ground
+            if (gsrc || (!c.c_one && !c.n1_ground)) {
+                if (!inside(t.sdx + c.n1_dx, t.sdy + c.n1_dy)) return "coupling lookup beyond the halo";
+                d.n1 = rel(gsrc ? c.n1_dz : bz + c.n1_dz, c.n1_dx, c.n1_dy);
+            }
+            if (c.bkind == B_TINF) d.aux = std::max(c.up_idx, 0);
+            if (c.bkind == B_TINFG) d.aux = std::max(c.gdir, 0) * lp - z * lp + t.sdy * nxp + t.sdx;
+            d.tbase = rel(bz, 0, 0);
+            for (int q = 0; q < 3; ++q) {
+                const int off = q == 0 ? c.pre_off : q == 1 ? c.seg_off : c.hit_off;
+                const int n = q == 0 ? c.pre_n : q == 1 ? c.seg_n : c.hit_n;
+                for (int k = 0; k < n; ++k)
+                    if (!inside(t.sdx + G.taps[off + k].dx, t.sdy + G.taps[off + k].dy)) return "tap beyond the halo";
+            }
+            if (c.pre_n > 255 || c.seg_n > 255 || c.hit_n > 255) return "tap list too long";
+            const int has_pre = (c.pre_tab >= 0 || c.pre_n > 0) ? 1 : 0;
+            d.bits = c.kind | (c.bkind << 4) | (c.c_one << 8) | (c.n1_ground << 9) | (has_pre << 10) |
+                     ((gsrc ? 1 : 0) << 11);
+            d.dir = gsrc ? std::max(c.gdir, 0) : std::max(c.dir, 0);
+            d.hgdir = c.hgdir;
+            d.taps = c.pre_n | (c.seg_n << 8) | (c.hit_n << 16);
+            d.pre_off = c.pre_off;
+            d.seg_off = c.seg_off;
+            d.hit_off = c.hit_off;
+            d.q = gsrc ? G.q_lamb[std::max(c.gdir, 0)] : G.q_iso[std::max(c.dir, 0)];
+            d.dinv = c.dist1 > 0 ? 1.0 / c.dist1 : 0.0;
+            d.split = c.split;
+        }
+    tap_h.resize(G.taps.size());
+    for (size_t k = 0; k < G.taps.size(); ++k) tap_h[k] = G.taps[k].dz * lp + G.taps[k].dy * nxp + G.taps[k].dx;
+    dir_h.resize(G.dirs.size());
+    for (size_t u = 0; u < G.dirs.size(); ++u) dir_h[u] = G.dirs[u][2] * lp + G.dirs[u][1] * nxp + G.dirs[u][0];
+    return std::string();
+}
+
 }  // namespace tg

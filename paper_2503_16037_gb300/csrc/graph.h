@@ -125,6 +125,27 @@ struct Graph {
 // Build the grid-only part.  Returns an empty string on success, else a message.
 std::string build_graph(Graph &G, int nx, int ny, int nz, double hx, double hy, double hz, int R, int M);
 
+// One template entry as the edge kernel reads it: every lookup resolved to an
+// offset from the receiver's position in the haloed node layout (layer z of
+// (ny + 2H) x (nx + 2H), node (x, y, z) at z lp + (y + H)(nx + 2H) + x + H).
+//   src    source node;  pre / seg  segment-table index (table * npad + offset), -1: none
+//   n1     first chain member of the source (coupling);  tbase  tap base cell (the source cell)
+//   aux    upward direction index (B_TINF), or tinfg plane index - receiver position (B_TINFG)
+//   bits   kind | bkind << 4 | c_one << 8 | n1_ground << 9 | has_pre << 10 | ground source << 11
+//   dir    atmospheric direction, or the ground direction of a ground source
+//   taps   pre_n | seg_n << 8 | hit_n << 16 (lists at pre_off, seg_off, hit_off)
+//   q      quadrature weight (q_iso or q_lamb);  dinv  1 / distance to n1;  split  ground-hit share
+struct EdgeDesc {
+    int src, pre, seg, n1, aux, tbase, bits, dir, hgdir, taps, pre_off, seg_off, hit_off;
+    double q, dinv, split;
+};
+
+// Edge descriptors of every template entry for halo width H, the haloed
+// offset of every tap from its base cell, and of every direction.  Fails
+// (non-empty message) if a lookup lies more than H columns from its receiver.
+std::string edge_descriptors(const Graph &G, int H, std::vector<EdgeDesc> &out, std::vector<int> &tap_h,
+                             std::vector<int> &dir_h);
+
 // Expand the templates into a CSR structure on the host.
 void expand_csr(const Graph &G, int32_t *row_ptr, int32_t *col, int16_t *dir, int8_t *k);
 

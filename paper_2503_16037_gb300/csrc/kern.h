@@ -23,17 +23,28 @@ struct __align__(16) DClass {
     float pad2, pad3;
 };
 
-// Packed form of a slot class for the edge kernel (four 16-byte words):
-//   w0 = {kind | bkind << 8 | c_one << 16 | n1_ground << 24, dir | hgdir << 16,
-//         up_idx | gdir << 16, float bits of 1 / dist1}
-//   w1 = {seg_tab + 1 | seg_dx << 8 | seg_dy << 16 | seg_dz << 24 (signed bytes),
-//         the same for pre, n1_dx | n1_dy << 8 | n1_dz << 16, float bits of split}
-//   w2 = {pre_off, seg_off, hit_off, pre_n | seg_n << 8 | hit_n << 16}
-//   w3 = {double 1 / dist1, double split} (FP64 kernels)
-struct __align__(16) PClass {
-    int4 w0, w1, w2, w3;
+
+// One row-template entry as the edge kernel uses it: every lookup of the
+// slot resolved to one offset from the receiver's haloed position rp (so a
+// value needs no index arithmetic beyond an add per lookup).
+//   src    source node: rp + src
+//   pre    tseg index of the segments before the receiver: pre + rp (-1: none or taps)
+//   seg    tseg index of the segment ending at the receiver: seg + rp (-1: taps)
+//   n1     first chain member of the source (coupling): rt_h[rp + n1]
+//   aux    B_TINF: upward direction index; B_TINFG: tinfg index - rp
+//   tbase  tap base cell (the source cell): mu_e_h[rp + tbase + tap_h[k]]
+//   bits   kind | bkind << 4 | c_one << 8 | n1_ground << 9 | has_pre << 10 | ground source << 11
+//   dir    atmospheric direction (q columns), or the ground direction of a ground source
+//   taps   pre_n | seg_n << 8 | hit_n << 16, with the lists at pre_off, seg_off, hit_off
+//   q, dinv, split  quadrature weight (q_iso or q_lamb), 1 / distance to n1, ground-hit share
+struct __align__(16) ASlot {
+    int src, pre, seg, n1;
+    int aux, tbase, bits, dir;
+    int hgdir, taps, pre_off, seg_off;
+    int hit_off;
+    float q, dinv, split;
+    double qd, dinvd, splitd, pad;
 };
-__host__ __device__ __forceinline__ int sbyte(int v, int sh) { return (int)(signed char)((v >> sh) & 0xff); }
 
 // Tap offsets (cell offsets relative to the segment base); lengths are in
 // separate float / double arrays.
@@ -71,7 +82,6 @@ struct GraphP {
     const int4 *tmpl;         // (class, flat, sdx, sdy)
     const long long *voff;    // [nz + 2]
     const DClass *cls;
-    const PClass *pcls;
     const DTap *taps;
     const float *tap_len_f;
     const double *tap_len_d;
@@ -93,6 +103,9 @@ struct GraphP {
     const int *up_canon;           // [nup] canonical index of each upward direction
     int *status;                   // scene status word (STATUS_* bits; bounded waits set STATUS_TIMEOUT)
     const int *tflat;              // per template entry: source - receiver in the haloed layout
+    const ASlot *aslot;            // per template entry: the edge kernel's lookups
+    const int *tap_h;              // per tap: haloed offset from the tap's base cell
+    const int *dir_h;              // per atmospheric direction: haloed offset of u
     // Runs of the persistent streamed passes: block b of pass kind k (0: all
     // (nz + 1) * gpl groups, 1: the nz * gpl atmospheric groups) handles the
     // groups [run_g[k][b], run_g[k][b + 1]), whose values are
@@ -112,12 +125,17 @@ struct FieldP {
     T *tsun;         // [n_nodes]
     T *e1;           // [n_nodes]
     T *tinf;         // [nup][n_atm]
-    T *tinfg;        // [ngd][n_ground]
-    T *a_iso;        // [n_nodes] coupling factor zc * sqrt(mu_s) of each source (0: weight 1)
-    T *a_sun;        // [n_nodes]
-    T *tseg;         // [nc][n_atm] optical depth of the lattice segment from a node along a canonical direction
+    T *tinfg;        // [ngd][lp] haloed ground layer: optical depth from a ground chain's last member to the TOA
+    T *a_iso;        // [npad] haloed: coupling factor zc * sqrt(mu_s) of each source (0: weight 1)
+    T *a_sun;        // [npad] haloed
+    T *tseg;         // [nc][npad] haloed: optical depth of the lattice segment from a node along a canonical direction
     T *rt;           // [n_atm] sqrt of the total scattering coefficient
     T *wsp;          // [S][n_atm] species fractions of the scattering coefficient
+    // haloed copies read by the edge kernel at source-relative positions
+    T *rt_h;         // [npad]
+    T *wsp_h;        // [S][npad]
+    T *mu_e_h;       // [npad]
+    T *e1_h;         // [npad]
     T *q_sun;        // [S][nd]
     T *hgv;          // [S][nd + ngd]
     T *hg0v;         // [S]
@@ -188,6 +206,20 @@ __host__ __device__ __forceinline__ int tmpl_sdy(int4 t) { return (int)(short)((
 // haloed position of node (x, y, z)
 __host__ __device__ __forceinline__ long long halo_pos(const GridC &g, int x, int y, int z) {
     return (long long)z * g.lp + (long long)(y + g.H) * g.nxp + x + g.H;
+}
+
+// store v at node (x, y, z)'s haloed position and at each of its halo copies
+template <typename T>
+__device__ __forceinline__ void store_halo(T *a, const GridC &g, int x, int y, int z, T v) {
+    const long long p = halo_pos(g, x, y, z);
+    const int ax = x < g.H ? g.nx : (x >= g.nx - g.H ? -g.nx : 0);
+    const int ay = y < g.H ? g.ny * g.nxp : (y >= g.ny - g.H ? -g.ny * g.nxp : 0);
+    a[p] = v;
+    if (ax) a[p + ax] = v;
+    if (ay) {
+        a[p + ay] = v;
+        if (ax) a[p + ax + ay] = v;
+    }
 }
 
 __host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x, int y, int4 t) {

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "kern.h"
+#include "stage.cuh"
 
 namespace tk {
 
@@ -185,13 +186,20 @@ __global__ void k_prep(GridC g, FieldP<T> f) {
             s = T(0);
             a = T(0);
         }
+        const int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
         f.mu_st[i] = s;
         f.mu_e[i] = a + s;
-        f.rt[i] = dsqrt<T>(s);
+        store_halo(f.mu_e_h, g, x, y, z, a + s);
+        const T rs = dsqrt<T>(s);
+        f.rt[i] = rs;
+        store_halo(f.rt_h, g, x, y, z, rs);
         T inv = s > T(0) ? T(1) / s : T(0);
         #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S)
-            f.wsp[(size_t)sp * g.n_atm + i] = s > T(0) ? f.mu_s[(size_t)sp * g.n_atm + i] * inv : T(1) / (T)g.S;
+        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) {
+            const T wv = s > T(0) ? f.mu_s[(size_t)sp * g.n_atm + i] * inv : T(1) / (T)g.S;
+            f.wsp[(size_t)sp * g.n_atm + i] = wv;
+            store_halo(f.wsp_h + (size_t)sp * g.npad, g, x, y, z, wv);
+        }
         m = (double)s;
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -273,9 +281,13 @@ __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
     if (i < g.n_atm) {
         T me = f.mu_e[i];
         T om = me > T(0) ? f.mu_st[i] / me : T(0);
-        f.e1[i] = om * base * Ts * (-dexpm1<T>(-me * (T)(g.hz / vc.mu0)));
+        const T e = om * base * Ts * (-dexpm1<T>(-me * (T)(g.hz / vc.mu0)));
+        f.e1[i] = e;
+        store_halo(f.e1_h, g, x, y, z, e);
     } else {
-        f.e1[i] = (T)vc.albedo * base * Ts;
+        const T e = (T)vc.albedo * base * Ts;
+        f.e1[i] = e;
+        store_halo(f.e1_h, g, x, y, g.nz, e);
     }
 }
 
@@ -289,18 +301,18 @@ template <typename T>
 __global__ void k_segtau(GridC g, GraphP gp, FieldP<T> f) {
     const int c = blockIdx.y, a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= g.n_atm) return;
-    const size_t t = (size_t)c * g.n_atm + a;
     int u = gp.canon_dirs[c];
     int4 d = gp.dirs[u];
     int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
     T tau = T(0);
     if (z + d.z < g.nz) tau = tap_sum<T>(g, gp, f.mu_e, gp.lat_off[u], gp.lat_n[u], x, y, z);
-    f.tseg[t] = tau;
+    store_halo(f.tseg + (size_t)c * g.npad, g, x, y, z, tau);
 }
 
+// segment table entry of canonical direction tab at node (x, y, z), x and y in range
 template <typename T>
 __device__ __forceinline__ T seg_at(const GridC &g, const T *__restrict__ tseg, int tab, int x, int y, int z) {
-    return __ldg(tseg + (size_t)tab * g.n_atm + (z * g.ny + wrap_small(y, g.ny)) * g.nx + wrap_small(x, g.nx));
+    return __ldg(tseg + (size_t)tab * g.npad + halo_pos(g, x, y, z));
 }
 
 // Optical depth from each voxel centre to the TOA along each upward lattice
@@ -337,7 +349,9 @@ __global__ void k_tinfg(GridC g, GraphP gp, FieldP<T> f) {
     if (t >= g.ngd * g.nxy) return;
     int gd = t / g.nxy, c = t - gd * g.nxy;
     int y = c / g.nx, x = c - y * g.nx;
-    f.tinfg[t] = ray_sum<T>(g, gp.taps, tap_len<T>(gp), f.mu_e, gp.gtop_off[gd], gp.gtop_n[gd], x, y, 0);
+    // haloed plane of ground direction gd: layer index 0 of a (1 x lp) array
+    store_halo(f.tinfg + (size_t)gd * g.lp, g, x, y, 0,
+               ray_sum<T>(g, gp.taps, tap_len<T>(gp), f.mu_e, gp.gtop_off[gd], gp.gtop_n[gd], x, y, 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -398,317 +412,182 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
         sqc_s = sqc_i;
     }
     // stored premultiplied by sqrt(mu_s) of the source: c = a sqrt(mu_s(n1)) / d
-    f.a_iso[j] = (vc.coupling && sqc_i > T(0)) ? sq_i / sqc_i * rt_src : T(0);
-    f.a_sun[j] = (vc.coupling && sqc_s > T(0)) ? sq_s / sqc_s * rt_src : T(0);
+    const int zz = j < g.n_atm ? z : g.nz;
+    store_halo(f.a_iso, g, x, y, zz, (vc.coupling && sqc_i > T(0)) ? sq_i / sqc_i * rt_src : T(0));
+    store_halo(f.a_sun, g, x, y, zz, (vc.coupling && sqc_s > T(0)) ? sq_s / sqc_s * rt_src : T(0));
 }
 
 // ---------------------------------------------------------------------------
-// Fused edge march + edge weights: one thread per receiver row, the warp
-// walking the row template in lockstep.  For every slot the optical depths of
-// the chain segments come from the translation-invariant tap tables; the
-// deposit fraction P, the quadrature weight q and the coupling c of the
-// source give
-//   K_ij = rho_i q_{j,u} c_{j,u} P          (stored slot-major)
+// Fused edge march + edge weights, one block of kAsmW warps per group of 128
+// receiver rows (lane l owns rows l + 32k; warp w takes the slots t = w mod
+// kAsmW).  For every slot the optical depths of the chain segments come from
+// the per-node segment table (or, for partial segments, from tap lists over
+// the extinction), the deposit fraction P, the quadrature weight q and the
+// coupling c of the source give
+//   K_ij = rho_i q_{j,u} c_{j,u} P          (stored slot-major per group)
 //   s_i  = sum_slots rho_i q^sun c^sun P e1_j
 //   g_i  = sum_slots Theta_i(u . v) rho_i q^sun c^sun P e1_j   (atmospheric rows)
+// Every lookup is one add from the receiver's haloed position (the slot's
+// ASlot descriptor holds the offsets), so a warp's loads of one slot cover
+// contiguous lines.
+constexpr int kAsmW = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_assemble(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= g.n_nodes) return;
-    const int z = row / g.nxy, r = row - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
-    const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
-    T *vrow = f.val + val_base(gp.voff[z], nt, r);
-    const T mus_lamb = (T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits));
-    const int ndir = g.nd + g.ngd;
-    const bool ground_row = row >= g.n_atm;
-    T rho, wr[MAX_SPECIES];
-    if (!ground_row) {
-        T me = f.mu_e[row], ms = f.mu_st[row];
-        rho = me > T(0) ? ms / me : T(0);
-        #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) wr[sp] = f.wsp[(size_t)sp * g.n_atm + row];
-    } else {
-        rho = (T)vc.albedo;
-        #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) wr[sp] = T(0);
-    }
-    T acc_s = T(0), acc_g = T(0);
-    const T rt_lamb = dsqrt<T>(mus_lamb);
-    for (int t = 0; t < nt; ++t) {
-        const int4 te = __ldg(gp.tmpl + t0 + t);
-        const PClass *pc = gp.pcls + te.x;
-        const int4 w0 = __ldg(&pc->w0), w1 = __ldg(&pc->w1);
-        const int kind = w0.x & 0xff, bkind = (w0.x >> 8) & 0xff;
-        const bool c_one = (w0.x >> 16) & 0xff, n1_ground = (w0.x >> 24) & 0xff;
-        const int dir = w0.y & 0xffff, hgdir = (w0.y >> 16) & 0xffff;
-        const int up_idx = w0.z & 0xffff, gdir = (w0.z >> 16) & 0xffff;
-        const int sz = te.w;
-        const int bx = wrap_small(x + tmpl_sdx(te), g.nx), by = wrap_small(y + tmpl_sdy(te), g.ny);
-        const int bz = sz >= 0 ? sz : 0;
-        const int j = sz >= 0 ? (sz * g.ny + by) * g.nx + bx : g.n_atm + by * g.nx + bx;
-        // optical depths: full lattice segments from the table, partial ones from taps
-        T tpre = T(0), tseg = T(0), thit = T(0);
-        const int seg_tab = (w1.x & 0xff) - 1, pre_tab = (w1.y & 0xff) - 1;
-        int4 w2 = make_int4(0, 0, 0, 0);
-        const bool need_taps = seg_tab < 0 || pre_tab < 0;  // a segment given by taps, or none
-        if (need_taps) w2 = __ldg(&pc->w2);
-        if (pre_tab >= 0)
-            tpre = seg_at<T>(g, f.tseg, pre_tab, bx + sbyte(w1.y, 8), by + sbyte(w1.y, 16), bz + sbyte(w1.y, 24));
-        else if (w2.w & 0xff)
-            tpre = tap_sum<T>(g, gp, f.mu_e, w2.x, w2.w & 0xff, bx, by, bz);
-        if (seg_tab >= 0)
-            tseg = seg_at<T>(g, f.tseg, seg_tab, bx + sbyte(w1.x, 8), by + sbyte(w1.x, 16), bz + sbyte(w1.x, 24));
-        else if ((w2.w >> 8) & 0xff)
-            tseg = tap_sum<T>(g, gp, f.mu_e, w2.y, (w2.w >> 8) & 0xff, bx, by, bz);
-        if ((w2.w >> 16) & 0xff) thit = tap_sum<T>(g, gp, f.mu_e, w2.z, (w2.w >> 16) & 0xff, bx, by, bz);
-        T P;
-        if (kind == 0 || kind == 3) {  // chain node (atmospheric or ground source)
-            const bool has_pre = pre_tab >= 0 || (w2.w & 0xff);
-            const T ep = has_pre ? fast_exp_neg<T>(tpre) : T(1);
-            if (bkind == 0) {
-                P = ep * one_minus_exp<T>(tseg);
-            } else if (bkind == 1) {
-                P = ep;
-            } else {
-                T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row]
-                                  : (bkind == 3 ? thit : f.tinfg[(size_t)gdir * g.nxy + (j - g.n_atm)]);
-                P = ep * one_minus_exp<T>(tseg + tb);
-            }
-        } else if (kind == 1) {  // self deposit
-            T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row] : thit;
-            P = one_minus_exp<T>(tb);
-        } else {  // ground hit
-            T split;
-            if constexpr (sizeof(T) == 4) {
-                split = __int_as_float(w1.w);
-            } else {
-                const int4 w3 = __ldg(&pc->w3);
-                split = __hiloint2double(w3.w, w3.z);
-            }
-            P = split * fast_exp_neg<T>(tpre + thit);
-        }
-        // quadrature weight x coupling of the source
-        T dinv;
-        if constexpr (sizeof(T) == 4) {
-            dinv = __int_as_float(w0.w);
-        } else {
-            const int4 w3 = __ldg(&pc->w3);
-            dinv = __hiloint2double(w3.y, w3.x);
-        }
-        const int n1dx = sbyte(w1.z, 0), n1dy = sbyte(w1.z, 8), n1dz = sbyte(w1.z, 16);
-        T Wi, Ws;
-        if (sz >= 0) {
-            T qi = Cst<T>::q_iso(gp, dir), qs = T(0);
-            #pragma unroll
-            for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * f.q_sun[sp * g.nd + dir];
-            T ci = T(1), cs = T(1);
-            if (!c_one) {
-                T rtn = n1_ground ? rt_lamb
-                                  : __ldg(f.rt + ((bz + n1dz) * g.ny + wrap_small(by + n1dy, g.ny)) * g.nx +
-                                          wrap_small(bx + n1dx, g.nx));
-                T ai = __ldg(f.a_iso + j), as = __ldg(f.a_sun + j);
-                ci = ai > T(0) ? ai * rtn * dinv : T(1);
-                cs = as > T(0) ? as * rtn * dinv : T(1);
-            }
-            Wi = qi * ci;
-            Ws = qs * cs;
-        } else {
-            T rtn = __ldg(f.rt + (n1dz * g.ny + wrap_small(by + n1dy, g.ny)) * g.nx + wrap_small(bx + n1dx, g.nx));
-            T a = __ldg(f.a_iso + j);
-            T cc = a > T(0) ? a * rtn * dinv : T(1);
-            Wi = Cst<T>::q_lamb(gp, gdir) * cc;
-            Ws = Wi;
-        }
-        vrow[(size_t)t * kGroup] = rho * Wi * P;
-        T sun = rho * Ws * P * __ldg(f.e1 + j);
-        acc_s += sun;
-        if (!ground_row) {
-            T th = T(0);
-            #pragma unroll
-            for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) th += wr[sp] * f.hgv[sp * ndir + hgdir];
-            acc_g += th * sun;
-        }
-    }
-    f.s[row] = acc_s;
-    if (!ground_row) f.gsun[row] = acc_g;
+__device__ __forceinline__ T aslot_q(const ASlot &d) {
+    if constexpr (sizeof(T) == 4) return d.q;
+    else return d.qd;
+}
+template <typename T>
+__device__ __forceinline__ T aslot_dinv(const ASlot &d) {
+    if constexpr (sizeof(T) == 4) return d.dinv;
+    else return d.dinvd;
+}
+template <typename T>
+__device__ __forceinline__ T aslot_split(const ASlot &d) {
+    if constexpr (sizeof(T) == 4) return d.split;
+    else return d.splitd;
 }
 
-// Four consecutive rows per thread (nx divisible by 4): the slot's template
-// entry, class descriptor and table offsets are decoded once for the four
-// rows, their values are stored with one 16-byte store per slot.
+// optical depth of a tap list based at haloed position b
 template <typename T>
-struct Store4;
-template <>
-struct Store4<float> {
-    __device__ static __forceinline__ void st(float *p, const float v[4]) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-};
-template <>
-struct Store4<double> {
-    __device__ static __forceinline__ void st(double *p, const double v[4]) {
-        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
-    }
-};
+__device__ __forceinline__ T tap_sum_h(const GraphP &gp, const T *__restrict__ mu_e_h, int off, int n, int b) {
+    const T *len = tap_len<T>(gp);
+    T acc = T(0);
+    for (int t = 0; t < n; ++t) acc += len[off + t] * __ldg(mu_e_h + b + __ldg(gp.tap_h + off + t));
+    return acc;
+}
 
-// kAsmSplit warps share each 128-row group (warp w takes slots t = w mod
-// kAsmSplit); the row sums s and g are combined in shared memory in a fixed order.
-constexpr int kAsmSplit = 4;
-
-template <typename T>
-__global__ void __launch_bounds__(32 * kAsmSplit) k_assemble4(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
-    __shared__ T sh_s[kAsmSplit][4][32], sh_g[kAsmSplit][4][32];
+#ifndef TK_ASM_MINB
+#define TK_ASM_MINB 8
+#endif
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
+    __shared__ T sh[kAsmW][8][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row0 = (blockIdx.x * 32 + lane) * 4;
-    const bool live = row0 < g.n_nodes;
-    T acc_s[4] = {T(0), T(0), T(0), T(0)}, acc_g[4] = {T(0), T(0), T(0), T(0)};
-    if (live) {
-    const int z = row0 / g.nxy, r0 = row0 - z * g.nxy, y = r0 / g.nx, x0 = r0 - y * g.nx;
-    const int t0 = gp.tstart[z], nt = gp.tstart[z + 1] - t0;
-    T *vrow = f.val + val_base(gp.voff[z], nt, r0);
-    const T mus_lamb = (T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits));
-    const T rt_lamb = dsqrt<T>(mus_lamb);
+    const GroupRows G = group_rows(g, gp, blockIdx.x);
+    const bool ground_row = G.z == g.nz;
+    const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     const int ndir = g.nd + g.ngd;
-    const bool ground_row = row0 >= g.n_atm;
-    T rho[4], wr[4][MAX_SPECIES];
+    int rowc[4];
+    T rho[4], wr[4][S];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+        rowc[k] = G.row[k] >= 0 ? G.row[k] : G.z * g.nxy;  // rows past the layer's end read a valid node
         if (!ground_row) {
-            const T me = f.mu_e[row0 + k], ms = f.mu_st[row0 + k];
+            const T me = f.mu_e[rowc[k]], ms = f.mu_st[rowc[k]];
             rho[k] = me > T(0) ? ms / me : T(0);
 #pragma unroll
-            for (int sp = 0; sp < MAX_SPECIES; ++sp)
-                wr[k][sp] = sp < g.S ? f.wsp[(size_t)sp * g.n_atm + row0 + k] : T(0);
+            for (int sp = 0; sp < S; ++sp) wr[k][sp] = f.wsp[(size_t)sp * g.n_atm + rowc[k]];
         } else {
             rho[k] = (T)vc.albedo;
 #pragma unroll
-            for (int sp = 0; sp < MAX_SPECIES; ++sp) wr[k][sp] = T(0);
+            for (int sp = 0; sp < S; ++sp) wr[k][sp] = T(0);
         }
     }
-    for (int t = w; t < nt; t += kAsmSplit) {
-        const int4 te = __ldg(gp.tmpl + t0 + t);
-        const PClass *pc = gp.pcls + te.x;
-        const int4 w0 = __ldg(&pc->w0), w1 = __ldg(&pc->w1);
-        const int kind = w0.x & 0xff, bkind = (w0.x >> 8) & 0xff;
-        const bool c_one = (w0.x >> 16) & 0xff, n1_ground = (w0.x >> 24) & 0xff;
-        const int dir = w0.y & 0xffff, hgdir = (w0.y >> 16) & 0xffff;
-        const int up_idx = w0.z & 0xffff, gdir = (w0.z >> 16) & 0xffff;
-        const int sz = te.w;
-        const int bz = sz >= 0 ? sz : 0;
-        const int by = wrap_small(y + tmpl_sdy(te), g.ny);
-        const int bx0 = x0 + tmpl_sdx(te);  // unwrapped column of row0's source
-        const int seg_tab = (w1.x & 0xff) - 1, pre_tab = (w1.y & 0xff) - 1;
-        int4 w2 = make_int4(0, 0, 0, 0);
-        if (seg_tab < 0 || pre_tab < 0) w2 = __ldg(&pc->w2);
-        const int pre_n = w2.w & 0xff, seg_n = (w2.w >> 8) & 0xff, hit_n = (w2.w >> 16) & 0xff;
-        const bool has_pre = pre_tab >= 0 || pre_n;
-        T split = T(0), dinv;
-        if constexpr (sizeof(T) == 4) {
-            split = __int_as_float(w1.w);
-            dinv = __int_as_float(w0.w);
-        } else {
-            const int4 w3 = __ldg(&pc->w3);
-            dinv = __hiloint2double(w3.y, w3.x);
-            split = __hiloint2double(w3.w, w3.z);
-        }
-        const T qi = sz >= 0 ? Cst<T>::q_iso(gp, dir) : Cst<T>::q_lamb(gp, gdir);
-        T qsun_s[MAX_SPECIES];
+    T acc_s[4] = {T(0), T(0), T(0), T(0)}, acc_g[4] = {T(0), T(0), T(0), T(0)};
+    T *vout = f.val + G.vb + lane;
+    for (int t = w; t < G.nt; t += kAsmW) {
+        const ASlot &d = gp.aslot[G.t0 + t];
+        const int4 a0 = __ldg(reinterpret_cast<const int4 *>(&d));
+        const int4 a1 = __ldg(reinterpret_cast<const int4 *>(&d) + 1);
+        const int4 a2 = __ldg(reinterpret_cast<const int4 *>(&d) + 2);
+        const int src = a0.x, pre = a0.y, seg = a0.z, n1 = a0.w;
+        const int aux = a1.x, tbase = a1.y, bits = a1.z, dir = a1.w;
+        const int hgdir = a2.x, taps = a2.y, pre_off = a2.z, seg_off = a2.w;
+        const int kind = bits & 15, bkind = (bits >> 4) & 15;
+        const bool c_one = (bits >> 8) & 1, n1_ground = (bits >> 9) & 1, has_pre = (bits >> 10) & 1;
+        const bool gsrc = (bits >> 11) & 1;
+        const int pre_n = taps & 0xff, seg_n = (taps >> 8) & 0xff, hit_n = (taps >> 16) & 0xff;
+        const T q = aslot_q<T>(d), dinv = aslot_dinv<T>(d), split = aslot_split<T>(d);
+        const int hit_off = __ldg(&d.hit_off);
+        T qsun[S];
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) qsun_s[sp] = (sz >= 0 && sp < g.S) ? f.q_sun[sp * g.nd + dir] : T(0);
+        for (int sp = 0; sp < S; ++sp) qsun[sp] = !gsrc ? f.q_sun[sp * g.nd + dir] : T(0);
         T th[4] = {T(0), T(0), T(0), T(0)};
         if (!ground_row) {
 #pragma unroll
-            for (int sp = 0; sp < MAX_SPECIES; ++sp)
-                if (sp < g.S) {
-                    const T h = f.hgv[sp * ndir + hgdir];
+            for (int sp = 0; sp < S; ++sp) {
+                const T h = f.hgv[sp * ndir + hgdir];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) th[k] += wr[k][sp] * h;
-                }
+                for (int k = 0; k < 4; ++k) th[k] += wr[k][sp] * h;
+            }
         }
-        T out[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int bx = wrap_small(bx0 + k, g.nx);
-            const int j = sz >= 0 ? (sz * g.ny + by) * g.nx + bx : g.n_atm + by * g.nx + bx;
-            T tpre = T(0), tseg = T(0), thit = T(0);
-            if (pre_tab >= 0)
-                tpre = seg_at<T>(g, f.tseg, pre_tab, bx + sbyte(w1.y, 8), by + sbyte(w1.y, 16), bz + sbyte(w1.y, 24));
+            const int rp = G.rp[k];
+            const int j = rp + src;
+            T tpre = T(0), tsg = T(0), thit = T(0);
+            if (pre >= 0)
+                tpre = __ldg(f.tseg + pre + rp);
             else if (pre_n)
-                tpre = tap_sum<T>(g, gp, f.mu_e, w2.x, pre_n, bx, by, bz);
-            if (seg_tab >= 0)
-                tseg = seg_at<T>(g, f.tseg, seg_tab, bx + sbyte(w1.x, 8), by + sbyte(w1.x, 16), bz + sbyte(w1.x, 24));
+                tpre = tap_sum_h<T>(gp, f.mu_e_h, pre_off, pre_n, rp + tbase);
+            if (seg >= 0)
+                tsg = __ldg(f.tseg + seg + rp);
             else if (seg_n)
-                tseg = tap_sum<T>(g, gp, f.mu_e, w2.y, seg_n, bx, by, bz);
-            if (hit_n) thit = tap_sum<T>(g, gp, f.mu_e, w2.z, hit_n, bx, by, bz);
+                tsg = tap_sum_h<T>(gp, f.mu_e_h, seg_off, seg_n, rp + tbase);
+            if (hit_n) thit = tap_sum_h<T>(gp, f.mu_e_h, hit_off, hit_n, rp + tbase);
             T P;
-            if (kind == 0 || kind == 3) {
+            if (kind == 0 || kind == 3) {  // chain node (atmospheric or ground source)
                 const T ep = has_pre ? fast_exp_neg<T>(tpre) : T(1);
                 if (bkind == 0) {
-                    P = ep * one_minus_exp<T>(tseg);
+                    P = ep * one_minus_exp<T>(tsg);
                 } else if (bkind == 1) {
                     P = ep;
                 } else {
-                    const T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row0 + k]
-                                            : (bkind == 3 ? thit : f.tinfg[(size_t)gdir * g.nxy + (j - g.n_atm)]);
-                    P = ep * one_minus_exp<T>(tseg + tb);
+                    const T tb = bkind == 2 ? f.tinf[(size_t)aux * g.n_atm + rowc[k]]
+                                            : (bkind == 3 ? thit : __ldg(f.tinfg + aux + rp));
+                    P = ep * one_minus_exp<T>(tsg + tb);
                 }
-            } else if (kind == 1) {
-                const T tb = bkind == 2 ? f.tinf[(size_t)up_idx * g.n_atm + row0 + k] : thit;
+            } else if (kind == 1) {  // self deposit
+                const T tb = bkind == 2 ? f.tinf[(size_t)aux * g.n_atm + rowc[k]] : thit;
                 P = one_minus_exp<T>(tb);
-            } else {
+            } else {  // ground hit
                 P = split * fast_exp_neg<T>(tpre + thit);
             }
             T Wi, Ws;
-            if (sz >= 0) {
+            if (!gsrc) {
                 T qs = T(0);
 #pragma unroll
-                for (int sp = 0; sp < MAX_SPECIES; ++sp)
-                    if (sp < g.S) qs += __ldg(f.wsp + (size_t)sp * g.n_atm + j) * qsun_s[sp];
+                for (int sp = 0; sp < S; ++sp) qs += __ldg(f.wsp_h + (size_t)sp * g.npad + j) * qsun[sp];
                 T ci = T(1), cs = T(1);
                 if (!c_one) {
-                    const T rtn = n1_ground ? rt_lamb
-                                            : __ldg(f.rt + ((bz + sbyte(w1.z, 16)) * g.ny + wrap_small(by + sbyte(w1.z, 8), g.ny)) * g.nx +
-                                                    wrap_small(bx + sbyte(w1.z, 0), g.nx));
+                    const T rtn = n1_ground ? rt_lamb : __ldg(f.rt_h + rp + n1);
                     const T ai = __ldg(f.a_iso + j), as = __ldg(f.a_sun + j);
                     ci = ai > T(0) ? ai * rtn * dinv : T(1);
                     cs = as > T(0) ? as * rtn * dinv : T(1);
                 }
-                Wi = qi * ci;
+                Wi = q * ci;
                 Ws = qs * cs;
             } else {
-                const T rtn = __ldg(f.rt + (sbyte(w1.z, 16) * g.ny + wrap_small(by + sbyte(w1.z, 8), g.ny)) * g.nx +
-                                    wrap_small(bx + sbyte(w1.z, 0), g.nx));
+                const T rtn = __ldg(f.rt_h + rp + n1);
                 const T a = __ldg(f.a_iso + j);
-                Wi = qi * (a > T(0) ? a * rtn * dinv : T(1));
+                Wi = q * (a > T(0) ? a * rtn * dinv : T(1));
                 Ws = Wi;
             }
-            out[k] = rho[k] * Wi * P;
-            const T sun = rho[k] * Ws * P * __ldg(f.e1 + j);
+            vout[(size_t)t * kGroup + 32 * k] = rho[k] * Wi * P;
+            const T sun = rho[k] * Ws * P * __ldg(f.e1_h + j);
             acc_s[k] += sun;
             acc_g[k] += th[k] * sun;
         }
-        Store4<T>::st(vrow + (size_t)t * kGroup, out);
     }
-    }  // live
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        sh_s[w][k][lane] = acc_s[k];
-        sh_g[w][k][lane] = acc_g[k];
+        sh[w][k][lane] = acc_s[k];
+        sh[w][4 + k][lane] = acc_g[k];
     }
     __syncthreads();
-    if (w == 0 && live) {
+    if (w == 0) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+            if (G.row[k] < 0) continue;
             T a = T(0), b = T(0);
 #pragma unroll
-            for (int q = 0; q < kAsmSplit; ++q) {
-                a += sh_s[q][k][lane];
-                b += sh_g[q][k][lane];
+            for (int qq = 0; qq < kAsmW; ++qq) {
+                a += sh[qq][k][lane];
+                b += sh[qq][4 + k][lane];
             }
-            f.s[row0 + k] = a;
-            if (row0 < g.n_atm) f.gsun[row0 + k] = b;
+            f.s[G.row[k]] = a;
+            if (!ground_row) f.gsun[G.row[k]] = b;
         }
     }
 }
@@ -748,10 +627,13 @@ void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], cons
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                           long long *launches) {
-    if (g.nx % 4 == 0)
-        k_assemble4<T><<<(g.n_nodes / 4 + 31) / 32, 32 * kAsmSplit, 0, st>>>(g, gp, f, vc);
-    else
-        k_assemble<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, f, vc);
+    const int nb = (g.nz + 1) * g.gpl;
+    switch (g.S) {  // the species count as a compile-time constant
+        case 1: k_asm<T, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+        case 2: k_asm<T, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+        case 3: k_asm<T, 3><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+        default: k_asm<T, 4><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+    }
     if (launches) *launches += 1;
 }
 
