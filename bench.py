@@ -296,6 +296,28 @@ def main():
     h2d = mu_a_h.numel() * 4 + mu_s_h.numel() * 4
     d2h = rad_h.numel() * 4 + refl_h.numel() * 4
 
+    # ---- adjoint of the same scene (J = sum_p L_p^2, gradient w.r.t. every
+    # voxel's absorption), outside the timed region: time per gradient
+    adj = None
+    try:
+        rn.run(mu_a, mu_s, rtol=RTOL)
+        lbar = 2.0 * rn.rad
+        rn.adjoint(lbar)  # first call allocates the K^T copy
+        torch.cuda.synchronize()
+        ta = []
+        for _ in range(10):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grad = rn.adjoint(lbar)
+            ta.append(time.perf_counter() - t0)
+        adj = {"ms_per_gradient": 1000.0 * statistics.median(ta), "objective": "J = sum_p L_p^2",
+               "wrt": "absorption coefficient of every voxel (131,072)",
+               "timing": "host wall clock around tursca_adjoint (synchronising), median of 10, L2 flushed",
+               "grad_abs_max": float(grad.abs().max().item())}
+    except Exception as e:  # the bench line must still print
+        adj = {"error": str(e)[:200]}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -352,6 +374,7 @@ def main():
         "clocks": clocks,
         "parity": parity,
         "solve": {"iters": it[0], "refinements": it[1], "rho_est": it[2], "rel_resid64": it[3]},
+        "adjoint": adj,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
     print(json.dumps(line), flush=True)

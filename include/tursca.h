@@ -185,9 +185,24 @@ tursca_status tursca_solve_with(tursca_scene *scene, int solver, double rtol, in
  * NULL.  Requires solve.  Synchronises before returning. */
 tursca_status tursca_render_radiance(tursca_scene *scene, void *radiance, void *reflectance);
 
-/* Gradient of J with respect to mu_abs given dJ/dL [npy][npx] (adjoint of the
- * path).  Declared for the interface; this version returns
- * TURSCA_E_UNSUPPORTED without touching its arguments. */
+/* Gradient of a detector objective J with respect to the absorption
+ * coefficient of every voxel, by the adjoint of the whole path (reverse-mode
+ * differentiation written out by hand; the paper motivates the method with
+ * retrievals, Sec. 3 and the conclusions).  mu_abs enters only through the
+ * extinction mu_e = mu_abs + sum_s mu_sca,s, which enters the optical depths
+ * of every edge, the direct beam and the lines of sight (Eq.
+ * radiance_effectuality, Eq. Fab, the final radiance sum of Sec. 2) and the
+ * scattering ratio and e1 of every node.  The adjoint runs: pixels -> emission
+ * -> (I - K)^T lambda = x-bar (the transposed system of Eq. flux_system,
+ * solved like the forward one) -> reverse edge march (segment-table, tau_inf,
+ * tap and direct-beam adjoints) -> dJ/dmu_e.
+ *   dJ_dL       [npy][npx] dJ/dL_p, compute type, host or device; borrowed.
+ *   dJ_dmu_abs  [nz][ny][nx] output, compute type, host or device.
+ * Requires render_radiance since the last solve (TURSCA_E_STATE otherwise);
+ * uses the scene's resident state and does not change the forward results.
+ * The first call allocates a transposed copy of K (4 bytes per edge in FP32)
+ * and the adjoint accumulators.  Accumulations use atomic adds, so repeated
+ * calls agree to rounding, not bit for bit.  Synchronises before returning. */
 tursca_status tursca_adjoint(tursca_scene *scene, const void *dJ_dL, void *dJ_dmu_abs);
 
 /* Copy an internal array out (device -> dst, host or device pointer) after the

@@ -29,7 +29,16 @@ struct tursca_scene {
     tg::ViewTables VT;
     bool view_ok = false;
     tursca_geometry geom{};
-    bool medium = false, assembled = false, solved = false;
+    bool medium = false, assembled = false, solved = false, rendered = false;
+    // adjoint state (allocated on the first tursca_adjoint)
+    bool adj_ready = false;
+    int *tstartT = nullptr, *flatT = nullptr, *hgdirT = nullptr;
+    long long *voffT = nullptr;
+    int4 *infoT = nullptr;
+    void *valT = nullptr, *Lbar = nullptr;
+    double *lam64 = nullptr;
+    void *adj[10] = {nullptr};  // Ebar, Ebar_h, e1bar, e1bar_h, xbar, mubar, mubar_h, tsegbar, tinfbar, tinfgbar
+    size_t adj_bytes[10] = {0};
     double g[tk::MAX_SPECIES] = {0, 0, 0, 0};
     double albedo = 0.0;
 
@@ -425,12 +434,13 @@ tursca_status read_red(tursca_scene *sc, int n) {
 
 // Neumann (source) iteration on (I - K) d = b: d <- b + K d, n sweeps after d = b.
 template <typename T>
-T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, int n, SolveState &ss) {
+T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *val, const T *b, int n,
+          SolveState &ss) {
     T *cur = (T *)sc->d0, *nxt = (T *)sc->d1;
     cudaMemcpyAsync(cur, b, (size_t)g.npad * sizeof(T), cudaMemcpyDeviceToDevice, sc->st);  // checked at the next sync
     for (int it = 0; it < n; ++it) {
         int pi = prof_begin(sc, P_SPMV);
-        tk::launch_spmv<T>(sc->st, g, gp, (const T *)sc->val, cur, b, nxt);
+        tk::launch_spmv<T>(sc->st, g, gp, val, cur, b, nxt);
         prof_end(sc, pi);
         std::swap(cur, nxt);
     }
@@ -442,8 +452,8 @@ T *neumann(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *
 // Restarted GMRES(m) on (I - K) d = b to ||b - (I - K) d|| <= tol ||b||; d must
 // not alias b.  Classical Gram-Schmidt with one re-orthogonalisation pass.
 template <typename T>
-tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *b, T *d, double tol,
-                    int maxit, SolveState &ss) {
+tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, const T *val, const T *b, T *d,
+                    double tol, int maxit, SolveState &ss) {
     const int n = (int)g.npad, m = sc->gm_m;  // haloed vectors
     const size_t ld = (size_t)n;
     T *V = (T *)sc->V, *w = (T *)sc->w, *r = (T *)sc->d1;
@@ -469,7 +479,7 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
         for (k = 0; k < m; ++k) {
             T *vk = V + (size_t)k * ld, *vn = V + (size_t)(k + 1) * ld;
             int pi = prof_begin(sc, P_SPMV);
-            tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, vk, w);
+            tk::launch_imk<T>(sc->st, g, gp, val, vk, w);
             prof_end(sc, pi);
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);
@@ -517,7 +527,7 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
         tk::launch_combine<T>(sc->st, n, d, V, ld, k, sc->dred + 192);
         sc->launches++;
         // true residual r = b - (I - K) d
-        tk::launch_imk<T>(sc->st, g, gp, (const T *)sc->val, d, w);
+        tk::launch_imk<T>(sc->st, g, gp, val, d, w);
         tk::launch_axpby<T>(sc->st, n, 1.0, b, -1.0, w, r);
         tk::launch_sumsq<T>(sc->st, g, r, sc->part, nb, sc->dred);
         sc->launches += 4;
@@ -549,10 +559,34 @@ ChebPlan cheb_plan(double lo, double hi) {
     return c;
 }
 
+// What a solve works on: K (graph and values) or K^T (the transposed ones),
+// the source (node order) and the FP64 solution (haloed).
 template <typename T>
-tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
-    const tk::GridC g = grid_c(sc);
-    const tk::GraphP gp = graph_p(sc);
+struct SolveIO {
+    tk::GridC g;
+    tk::GraphP gp;
+    const T *val;
+    const T *s;
+    double *x;
+};
+
+template <typename T>
+SolveIO<T> forward_io(tursca_scene *sc) {
+    SolveIO<T> io;
+    io.g = grid_c(sc);
+    io.gp = graph_p(sc);
+    io.val = (const T *)sc->val;
+    io.s = (const T *)sc->s;
+    io.x = sc->x64;
+    return io;
+}
+
+template <typename T>
+tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info,
+                       const SolveIO<T> &io) {
+    const tk::GridC &g = io.g;
+    const tk::GraphP &gp = io.gp;
+    const T *val = io.val;
     const int n = (int)g.npad;  // solver vectors are haloed
     const int nbr = tk::resid_blocks(g);
     const int nb = tk::dot_blocks(g);
@@ -575,8 +609,8 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     // fraction of the FP32 rate on this GPU), FP64 on FP64 scenes or on request
     const bool ds = !fp64 && !sc->resid_fp64 && tk::resid_ds_ok(g);
     // x = 0, r = s, ||s||
-    CK(cudaMemsetAsync(sc->x64, 0, (size_t)n * sizeof(double), sc->st), "memset x");
-    tk::launch_to_halo<T, double>(sc->st, g, (const T *)sc->s, sc->r64);
+    CK(cudaMemsetAsync(io.x, 0, (size_t)n * sizeof(double), sc->st), "memset x");
+    tk::launch_to_halo<T, double>(sc->st, g, io.s, sc->r64);
     // ||s||^2 goes to dred[4] and is read with the first refinement's residual
     tk::launch_sumsq<double>(sc->st, g, sc->r64, sc->part, nb, sc->dred + 4);
     sc->launches += 3;
@@ -626,7 +660,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             CK(cudaMemcpyAsync(cur, bb, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, sc->st), "copy");
             for (int it = 0; it < n1; ++it) {
                 int pi = prof_begin(sc, P_SPMV);
-                tk::launch_sweep_pow<T>(sc->st, g, gp, (const T *)sc->val, cur, bb, nxt, sc->part + (it & 1) * nsw);
+                tk::launch_sweep_pow<T>(sc->st, g, gp, val, cur, bb, nxt, sc->part + (it & 1) * nsw);
                 prof_end(sc, pi);
                 std::swap(cur, nxt);
             }
@@ -654,7 +688,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             for (int k = 0; k < nc; ++k) {
                 double rk1 = 1.0 / (2.0 * cp.sigma - rk);
                 int pi = prof_begin(sc, P_CHEB);
-                tk::launch_cheb<T>(sc->st, g, gp, (const T *)sc->val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta);
+                tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta);
                 prof_end(sc, pi);
                 std::swap(p0, p1);
                 rk = rk1;
@@ -672,23 +706,23 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
                 sn = std::sqrt(sc->hred[4]);
             }
             double tol = fp64 ? std::max(0.3 * rtol / rel, 1e-15) : std::max(0.3 * rtol / rel, 2e-6);
-            e = gmres<T>(sc, g, gp, bb, (T *)sc->d0, tol, budget, ss);
+            e = gmres<T>(sc, g, gp, val, bb, (T *)sc->d0, tol, budget, ss);
             if (e) return e;
             dd = (const T *)sc->d0;
             ss.solver = TURSCA_SOLVER_GMRES;
         } else {  // Neumann
             int nn = std::min(inner_n, std::max(1, budget - 1));
-            dd = neumann<T>(sc, g, gp, bb, nn, ss);
+            dd = neumann<T>(sc, g, gp, val, bb, nn, ss);
             inner_n = nn;
             ss.solver = TURSCA_SOLVER_NEUMANN;
         }
-        tk::launch_update_x<T>(sc->st, n, dd, sc->x64, ds ? sc->xh : nullptr, ds ? sc->xl : nullptr);
+        tk::launch_update_x<T>(sc->st, n, dd, io.x, ds ? sc->xh : nullptr, ds ? sc->xl : nullptr);
         int pr = prof_begin(sc, P_RESID);
         if (ds)
-            tk::launch_resid_ds(sc->st, g, gp, (const float *)sc->val, (const float *)sc->s, sc->x64, sc->xh, sc->xl,
+            tk::launch_resid_ds(sc->st, g, gp, (const float *)val, (const float *)io.s, io.x, sc->xh, sc->xl,
                                 sc->r64, sc->part, nbr);
         else
-            tk::launch_resid64<T>(sc->st, g, gp, (const T *)sc->val, (const T *)sc->s, sc->x64, sc->r64, sc->part,
+            tk::launch_resid64<T>(sc->st, g, gp, val, io.s, io.x, sc->r64, sc->part,
                                   nbr);
         prof_end(sc, pr);
         tk::launch_finalize(sc->st, sc->part, nbr, sc->dred);
@@ -769,7 +803,100 @@ tursca_status do_render(tursca_scene *sc, void *radiance, void *reflectance) {
     if (radiance) CK(cudaMemcpyAsync(radiance, sc->rad, np * sizeof(T), cudaMemcpyDefault, sc->st), "copy radiance");
     if (reflectance)
         CK(cudaMemcpyAsync(reflectance, sc->refl, np * sizeof(T), cudaMemcpyDefault, sc->st), "copy reflectance");
-    return sync_check(sc, "render");
+    tursca_status rs = sync_check(sc, "render");
+    sc->rendered = rs == TURSCA_OK;
+    return rs;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+
+tursca_status ensure_adjoint(tursca_scene *sc) {
+    if (sc->adj_ready) return TURSCA_OK;
+    const tg::Graph &G = sc->G;
+    const tk::GridC g = grid_c(sc);
+    tg::Transposed Tt;
+    tg::transpose_templates(G, g.H, Tt);
+    const size_t ne = Tt.recv_layer.size();
+    std::vector<int4> info(ne);
+    std::vector<int> hg(ne);
+    for (size_t e = 0; e < ne; ++e) {
+        const int i = Tt.tmpl_index[e], zi = Tt.recv_layer[e];
+        const tg::TSlot &t = G.tmpl[i];
+        info[e] = make_int4(i - G.tmpl_start[zi], zi, t.sdx, t.sdy);
+        hg[e] = G.classes[t.cls].hgdir;
+    }
+    if (Tt.voff[g.nz + 1] != G.nval) return fail(sc, TURSCA_E_INVALID, "internal error: K^T size");
+    CK(upload(sc, sc->allocs, sc->tstartT, Tt.tstart.data(), Tt.tstart.size() * sizeof(int)), "upload K^T");
+    CK(upload(sc, sc->allocs, sc->voffT, Tt.voff.data(), Tt.voff.size() * sizeof(long long)), "upload K^T");
+    CK(upload(sc, sc->allocs, sc->infoT, info.data(), std::max<size_t>(1, ne) * sizeof(int4)), "upload K^T");
+    CK(upload(sc, sc->allocs, sc->flatT, Tt.flat_h.data(), std::max<size_t>(1, ne) * sizeof(int)), "upload K^T");
+    CK(upload(sc, sc->allocs, sc->hgdirT, hg.data(), std::max<size_t>(1, ne) * sizeof(int)), "upload K^T");
+    const size_t es = sc->es;
+    CK(dalloc(sc->allocs, sc->valT, (size_t)G.nval * es), "alloc K^T");
+    CK(dalloc(sc->allocs, sc->lam64, (size_t)g.npad * sizeof(double)), "alloc adjoint");
+    CK(dalloc(sc->allocs, sc->Lbar, (size_t)sc->geom.npx * sc->geom.npy * es), "alloc adjoint");
+    const size_t nn = (size_t)g.n_nodes, na = (size_t)g.n_atm, np = (size_t)g.npad;
+    const size_t sz[10] = {nn, np, nn, np, nn, na, np, (size_t)g.nc * np, (size_t)g.nup * na, (size_t)g.ngd * g.lp};
+    for (int k = 0; k < 10; ++k) {
+        sc->adj_bytes[k] = std::max<size_t>(1, sz[k]) * es;
+        CK(dalloc(sc->allocs, sc->adj[k], sc->adj_bytes[k]), "alloc adjoint");
+    }
+    CK(cudaStreamSynchronize(sc->st), "sync");
+    sc->adj_ready = true;
+    return TURSCA_OK;
+}
+
+template <typename T>
+tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) {
+    tk::GridC g = grid_c(sc);
+    const tk::GraphP gp = graph_p(sc);
+    tk::FieldP<T> f = field_p<T>(sc);
+    const tk::ViewC vc = view_c(sc);
+    const tk::ViewP vp = view_p(sc);
+    tk::TransP tp;
+    tp.tstart = sc->tstartT;
+    tp.voff = sc->voffT;
+    tp.info = sc->infoT;
+    tp.flat = sc->flatT;
+    tp.hgdir = sc->hgdirT;
+    tk::GraphP gpT = gp;  // K^T: the same kind of templates over source layers
+    gpT.tstart = sc->tstartT;
+    gpT.voff = sc->voffT;
+    gpT.tflat = sc->flatT;
+    tk::AdjP<T> ad;
+    T **slot[10] = {&ad.Ebar, &ad.Ebar_h, &ad.e1bar, &ad.e1bar_h, &ad.xbar,
+                    &ad.mubar, &ad.mubar_h, &ad.tsegbar, &ad.tinfbar, &ad.tinfgbar};
+    for (int k = 0; k < 10; ++k) {
+        *slot[k] = (T *)sc->adj[k];
+        CK(cudaMemsetAsync(sc->adj[k], 0, sc->adj_bytes[k], sc->st), "memset adjoint");
+    }
+    const size_t npix = (size_t)sc->geom.npx * sc->geom.npy;
+    CK(cudaMemcpyAsync(sc->Lbar, dJ_dL, npix * sizeof(T), cudaMemcpyDefault, sc->st), "copy dJ/dL");
+    // K^T first: the launches after it are plain ones until the row-group passes
+    tk::launch_transpose_vals<T>(sc->st, g, gp, tp, (const T *)sc->val, (T *)sc->valT);
+    tk::launch_pix_adj<T>(sc->st, g, f, vc, vp, (const T *)sc->emis, sc->x64, (const T *)sc->Lbar, ad);
+    tk::launch_to_halo<T, T>(sc->st, g, ad.Ebar, ad.Ebar_h);
+    tk::launch_emis_adj<T>(sc->st, g, gpT, tp, f, (const T *)sc->valT, ad);
+    sc->launches += 4;
+    // (I - K)^T lambda = x-bar
+    SolveIO<T> io;
+    g.stage = 0;
+    io.g = g;
+    io.gp = gpT;
+    io.val = (const T *)sc->valT;
+    io.s = ad.xbar;
+    io.x = sc->lam64;
+    tursca_solve_info info;
+    const double rtol = sc->d.precision == TURSCA_FP64 ? 1e-12 : 1e-9;
+    tursca_status rs = do_solve<T>(sc, TURSCA_SOLVER_AUTO, rtol, 5000, &info, io);
+    if (rs) return rs;
+    tk::launch_asm_adj<T>(sc->st, grid_c(sc), gp, f, vc, sc->x64, sc->lam64, ad);
+    tk::launch_tables_adj<T>(sc->st, grid_c(sc), gp, f, vc, vp, ad);
+    sc->launches += 6;
+    CK(cudaGetLastError(), "adjoint launch");
+    CK(cudaMemcpyAsync(dJ_dmu_abs, ad.mubar, (size_t)g.n_atm * sizeof(T), cudaMemcpyDefault, sc->st), "copy gradient");
+    return sync_check(sc, "adjoint");
 }
 
 }  // namespace
@@ -824,7 +951,7 @@ tursca_status tursca_set_medium(tursca_scene *sc, const void *mu_abs, const void
     for (int s = 0; s < tk::MAX_SPECIES; ++s) sc->g[s] = s < sc->d.n_species ? g[s] : 0.0;
     sc->albedo = albedo;
     sc->medium = true;
-    sc->assembled = sc->solved = false;
+    sc->assembled = sc->solved = sc->rendered = false;
     return TURSCA_OK;
 }
 
@@ -1113,7 +1240,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     prof_end(sc, p1);
     CK(cudaGetLastError(), "assemble launch");
     sc->assembled = true;
-    sc->solved = false;
+    sc->solved = sc->rendered = false;
     return TURSCA_OK;
 }
 
@@ -1121,11 +1248,12 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!sc->assembled) return fail(sc, TURSCA_E_STATE, "assemble_flux has not been called");
     if (!(rtol > 0.0) || max_iter < 1) return fail(sc, TURSCA_E_INVALID, "rtol must be > 0 and max_iter >= 1");
+    sc->rendered = false;
     if (solver < 0 || solver > 3) return fail(sc, TURSCA_E_INVALID, "unknown solver");
     tursca_status e = sync_check(sc, "assemble");
     if (e) return e;
-    if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info);
-    return do_solve<float>(sc, solver, rtol, max_iter, info);
+    if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc));
+    return do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
 }
 
 tursca_status tursca_solve(tursca_scene *sc, double rtol, int max_iter, tursca_solve_info *info) {
@@ -1140,9 +1268,13 @@ tursca_status tursca_render_radiance(tursca_scene *sc, void *radiance, void *ref
 }
 
 tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) {
-    (void)dJ_dL;
-    (void)dJ_dmu_abs;
-    return fail(sc, TURSCA_E_UNSUPPORTED, "the adjoint is not available in this version");
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
+    if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
+    tursca_status e = ensure_adjoint(sc);
+    if (e) return e;
+    if (sc->d.precision == TURSCA_FP64) return do_adjoint<double>(sc, dJ_dL, dJ_dmu_abs);
+    return do_adjoint<float>(sc, dJ_dL, dJ_dmu_abs);
 }
 
 tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t bytes) {

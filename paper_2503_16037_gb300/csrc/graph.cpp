@@ -653,4 +653,40 @@ std::string edge_descriptors(const Graph &G, int H, std::vector<EdgeDesc> &out, 
     return std::string();
 }
 
+void transpose_templates(const Graph &G, int H, Transposed &T) {
+    const int nz = G.nz, nxp = G.nx + 2 * H, lp = nxp * (G.ny + 2 * H);
+    const long long nxy = (long long)G.nx * G.ny, nxy_pad = (nxy + kGroup - 1) / kGroup * kGroup;
+    std::vector<std::vector<int>> per(nz + 1);  // template indices grouped by source layer
+    for (int z = 0; z <= nz; ++z)
+        for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
+            const int szl = G.tmpl[i].sz >= 0 ? G.tmpl[i].sz : nz;
+            per[szl].push_back(i);
+        }
+    T.tstart.assign(nz + 2, 0);
+    T.voff.assign(nz + 2, 0);
+    T.recv_layer.clear();
+    T.tmpl_index.clear();
+    T.flat_h.clear();
+    T.max_row = 0;
+    // receiver layer of a template index
+    std::vector<int> layer_of(G.tmpl.size());
+    for (int z = 0; z <= nz; ++z)
+        for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) layer_of[i] = z;
+    for (int zs = 0; zs <= nz; ++zs) {
+        for (int i : per[zs]) {
+            const TSlot &t = G.tmpl[i];
+            const int zi = layer_of[i];
+            T.recv_layer.push_back(zi);
+            T.tmpl_index.push_back(i);
+            // receiver - source = -(source - receiver)
+            T.flat_h.push_back(-((zs - zi) * lp + t.sdy * nxp + t.sdx));
+        }
+        const int n = (int)per[zs].size();
+        T.tstart[zs + 1] = T.tstart[zs] + n;
+        T.voff[zs + 1] = T.voff[zs] + (long long)n * nxy_pad;
+        T.max_row = std::max(T.max_row, n);
+    }
+    T.tstart[nz + 1] = (int)T.recv_layer.size();
+}
+
 }  // namespace tg

@@ -146,6 +146,22 @@ struct EdgeDesc {
 std::string edge_descriptors(const Graph &G, int H, std::vector<EdgeDesc> &out, std::vector<int> &tap_h,
                              std::vector<int> &dir_h);
 
+// Templates of K^T: for every source layer zs (zs = nz: the ground), the
+// template entries of all receiver layers whose source lies in layer zs, in
+// a fixed order (receiver layer, then template index).  Because K is
+// invariant under horizontal translation, K^T has the same per-layer form:
+// the column of entry e of source node j is the receiver j + flat_h[e]
+// (haloed offset), and K^T_je = K_{i, tmpl[e]}.
+struct Transposed {
+    std::vector<int> tstart;        // [nz + 2]
+    std::vector<int> recv_layer;    // receiver layer of each entry
+    std::vector<int> tmpl_index;    // index of the entry in G.tmpl
+    std::vector<int> flat_h;        // receiver - source in the haloed layout (width H)
+    std::vector<long long> voff;    // [nz + 2] values of K^T, groups of kGroup source rows, slot-major
+    int max_row = 0;
+};
+void transpose_templates(const Graph &G, int H, Transposed &T);
+
 // Expand the templates into a CSR structure on the host.
 void expand_csr(const Graph &G, int32_t *row_ptr, int32_t *col, int16_t *dir, int8_t *k);
 

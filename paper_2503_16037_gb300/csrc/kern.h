@@ -310,6 +310,48 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
 template <typename T>
 void launch_imk(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, T *y);  // y = x - K x
 
+// ---- adjoint (kernels_adjoint.cu)
+// Transposed templates of K (rows = sources), see tg::Transposed
+struct TransP {
+    const int *tstart;       // [nz + 2]
+    const long long *voff;   // [nz + 2]
+    const int4 *info;        // per entry: (template-local index in the receiver layer, receiver layer, sdx, sdy)
+    const int *flat;         // per entry: receiver - source in the haloed layout
+    const int *hgdir;        // per entry: scattering-direction index of the slot
+};
+
+// adjoint accumulators (compute type); the gradient is mubar
+template <typename T>
+struct AdjP {
+    T *Ebar;      // [n_atm] dJ/dE
+    T *Ebar_h;    // [npad]  the same, haloed
+    T *e1bar;     // [n_nodes] dJ/de1 (pixels)
+    T *e1bar_h;   // [npad]  dJ/de1 (slots), haloed accumulation
+    T *xbar;      // [n_nodes] dJ/dx
+    T *mubar;     // [n_atm] dJ/dmu_e = dJ/dmu_a
+    T *mubar_h;   // [npad]  tap contributions, haloed accumulation
+    T *tsegbar;   // [nc][npad]
+    T *tinfbar;   // [nup][n_atm]
+    T *tinfgbar;  // [ngd][lp]
+};
+
+template <typename T>
+void launch_transpose_vals(cudaStream_t st, const GridC &g, const GraphP &gp, const TransP &tp, const T *val,
+                           T *valT);
+template <typename T>
+void launch_pix_adj(cudaStream_t st, const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp,
+                    const T *emis, const double *x, const T *Lbar, const AdjP<T> &ad);
+// x-bar += (theta K)^T E-bar over the transposed templates
+template <typename T>
+void launch_emis_adj(cudaStream_t st, const GridC &g, const GraphP &gpT, const TransP &tp, const FieldP<T> &f,
+                     const T *valT, const AdjP<T> &ad);
+template <typename T>
+void launch_asm_adj(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                    const double *x64, const double *lam64, const AdjP<T> &ad);
+template <typename T>
+void launch_tables_adj(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                       const ViewP &vp, const AdjP<T> &ad);
+
 // ---- render (kernels_render.cu)
 // xc: the solution x in the compute type
 template <typename T>

@@ -563,6 +563,7 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
 INST(float)
 INST(double)
 #undef INST
+template void launch_to_halo<float, float>(cudaStream_t, const GridC &, const float *, float *);
 template void launch_convert<double, float>(cudaStream_t, int, const double *, float *);
 template void launch_convert<float, double>(cudaStream_t, int, const float *, double *);
 template void launch_convert<double, double>(cudaStream_t, int, const double *, double *);

@@ -310,6 +310,17 @@ class Runner:
         self.solve(rtol, max_iter, solver)
         return self.render()
 
+    def adjoint(self, dJ_dL):
+        """dJ/dmu_abs (per voxel, C order (z, y, x), compute type) for the
+        detector-radiance adjoint dJ/dL of the last render."""
+        t = self.torch
+        dl = t.as_tensor(dJ_dL, dtype=self.dtype, device=self.rad.device).contiguous()
+        if dl.numel() != self.rad.numel():
+            raise ValueError("dJ_dL must have one entry per detector pixel")
+        out = t.empty((self.sc.nz, self.sc.ny, self.sc.nx), dtype=self.dtype, device=self.rad.device)
+        tursca_adjoint(self.handle, dl, out)
+        return out
+
     def get(self, which: int, n: int, dtype):
         t = self.torch
         out = t.empty(n, dtype=dtype)
@@ -329,3 +340,38 @@ class Runner:
             self.close()
         except Exception:
             pass
+
+
+def _autograd():
+    import torch
+
+    class TurscaRender(torch.autograd.Function):
+        """Detector radiance of a scene as a differentiable function of the
+        per-voxel absorption coefficient: forward runs set_medium ->
+        assemble -> solve -> render on the Runner's scene, backward runs the
+        library's adjoint (K^T solve and reverse edge march)."""
+
+        @staticmethod
+        def forward(ctx, mu_a, runner, mu_s, rtol):
+            runner.run(mu_a.detach().contiguous(), mu_s, rtol=rtol)
+            ctx.runner = runner
+            return runner.rad.clone()
+
+        @staticmethod
+        def backward(ctx, grad_rad):
+            g = ctx.runner.adjoint(grad_rad.contiguous())
+            return g, None, None, None
+
+    return TurscaRender
+
+
+_TurscaRender = None
+
+
+def render(mu_a, runner, mu_s, rtol=1e-10):
+    """Differentiable detector radiance (see TurscaRender)."""
+    global _TurscaRender
+    if _TurscaRender is None:
+        _TurscaRender = _autograd()
+    return _TurscaRender.apply(mu_a, runner, mu_s, rtol)
+

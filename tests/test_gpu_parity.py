@@ -233,7 +233,7 @@ def test_out_of_order_and_invalid_fields():
     assert ei.value.status == T.E_INVALID
     with pytest.raises(T.TurscaError) as ei:
         T.tursca_adjoint(rn.handle, None, None)
-    assert ei.value.status == T.E_UNSUPPORTED
+    assert ei.value.status == T.E_INVALID
     # a valid medium afterwards works on the same scene
     mu_a, mu_s = rn.fields("cuda")
     rn.set_medium(mu_a, mu_s)
