@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--solver", type=int, default=0)
     return p.parse_args()
 
@@ -172,6 +173,103 @@ def run_reference(args, rank):
         "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+SERVE_SHAPES = [(16, 16, 16), (32, 32, 24), (48, 48, 32), (64, 64, 32), (96, 96, 32)]
+
+
+def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
+    """Continuous-batching serving of plume scenes of uneven sizes (uniform
+    over SERVE_SHAPES, SZA ~ U(20, 75) deg, FP32 + refinement to 1e-10):
+    the saturation rate with all requests queued at once, then an open-loop
+    run with Poisson arrivals at `load` x that rate (latency = completion -
+    arrival), then the plain FP64 path (one scene at a time, FP64 solve) on a
+    subset of the same requests."""
+    import threading
+    rng = np.random.default_rng(seed)
+    nvar = 8
+    pool = {sh: [scenes.make_plume(nx=sh[0], ny=sh[1], nz=sh[2], sza=float(rng.uniform(20.0, 75.0)))
+                 for _ in range(nvar)] for sh in SERVE_SHAPES}
+    fields = {(sh, k): (torch.as_tensor(sc.mu_a, dtype=torch.float32).pin_memory(),
+                        torch.as_tensor(sc.mu_s, dtype=torch.float32).pin_memory())
+              for sh, l in pool.items() for k, sc in enumerate(l)}
+    reqs = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], int(rng.integers(nvar))) for _ in range(n_requests)]
+    outs = [torch.empty((sh[1], sh[0]), dtype=torch.float32).pin_memory() for sh, _ in reqs]
+    srv = T.Server(40 << 30, workers)
+    for sh in SERVE_SHAPES:  # one warm request per shape builds its first slot
+        srv.wait(srv.submit(pool[sh][0], T.FP32_REFINE, 1e-10, fields=fields[(sh, 0)]))
+
+    def closed(sub):
+        t0 = time.perf_counter()
+        tk = [srv.submit(pool[sh][k], T.FP32_REFINE, 1e-10, fields=fields[(sh, k)], out=outs[j])
+              for j, (sh, k) in sub]
+        infos = [srv.wait(t)[1] for t in tk]
+        return len(sub) / (time.perf_counter() - t0), infos
+
+    sat, _ = closed(list(enumerate(reqs[:256])))
+    rate = load * sat
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    tickets = [None] * n_requests
+
+    def submitter():
+        t = time.perf_counter()
+        for j, (sh, k) in enumerate(reqs):
+            t += gaps[j]
+            while True:
+                d = t - time.perf_counter()
+                if d <= 0:
+                    break
+                time.sleep(min(d, 0.0005) if d > 0.0002 else 0)
+            tickets[j] = srv.submit(pool[sh][k], T.FP32_REFINE, 1e-10, fields=fields[(sh, k)], out=outs[j])
+
+    th = threading.Thread(target=submitter)
+    t0 = time.perf_counter()
+    th.start()
+    infos = []
+    for j in range(n_requests):
+        while tickets[j] is None:
+            time.sleep(0.0001)
+        infos.append(srv.wait(tickets[j])[1])
+    th.join()
+    wall = time.perf_counter() - t0
+    lat = np.array([i["end_ms"] - i["submit_ms"] for i in infos])
+    subm = np.array([i["submit_ms"] for i in infos])
+    st = srv.stats()
+    srv.close()
+    ok = all(i["status"] == 0 and i["rel_resid64"] <= 1e-10 for i in infos)
+    # the plain FP64 path: one scene per call sequence, nothing overlapped
+    base = []
+    rn_of = {}
+    for sh, k in reqs[:64]:
+        if sh not in rn_of:
+            rn_of[sh] = T.Runner(pool[sh][0], T.FP64)
+        rn = rn_of[sh]
+        rn.sc = pool[sh][k]
+        rn.geom = T.geometry(pool[sh][k])
+        a = torch.as_tensor(pool[sh][k].mu_a, dtype=torch.float64).pin_memory()
+        m = torch.as_tensor(pool[sh][k].mu_s, dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rn.run(a, m, rtol=1e-10)
+        rn.rad.cpu()
+        base.append(1000.0 * (time.perf_counter() - t1))
+    for rn in rn_of.values():
+        rn.close()
+    base = np.array(base)
+    return {
+        "workload": "1024 plume scenes, shapes uniform over 16^3, 32^2x24, 48^2x32, 64^2x32, 96^2x32 "
+                    "(R = 2), SZA ~ U(20, 75) deg, FP32 + FP64 refinement to 1e-10, host inputs (pinned)",
+        "workers": workers, "saturation_scenes_per_s": sat,
+        "arrivals": "Poisson at %.2f x saturation (%.0f /s requested, %.0f /s achieved)"
+                    % (load, rate, (n_requests - 1) / max(1e-9, (subm.max() - subm.min()) / 1000.0)),
+        "scenes_per_s": n_requests / wall, "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "all_converged": ok,
+        "slots_built": st["slots_built"], "peak_device_bytes": st["peak_bytes"], "evictions": st["evictions"],
+        "plain_fp64_one_scene_at_a_time": {
+            "requests": int(base.size), "scenes_per_s": 1000.0 / float(base.mean()),
+            "p50_ms": float(np.percentile(base, 50)), "p99_ms": float(np.percentile(base, 99)),
+            "note": "service time per scene with nothing overlapped (no queueing)"},
+    }
 
 
 def main():
@@ -318,6 +416,14 @@ def main():
     except Exception as e:  # the bench line must still print
         adj = {"error": str(e)[:200]}
 
+    # ---- serving (continuous batching over resident slots), rank 0 of one GPU
+    serve = None
+    if rank == 0 and not args.no_serving:
+        try:
+            serve = serving(T, scenes, torch, np)
+        except Exception as e:  # the bench line must still print
+            serve = {"error": str(e)[:200]}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -375,6 +481,7 @@ def main():
         "parity": parity,
         "solve": {"iters": it[0], "refinements": it[1], "rho_est": it[2], "rel_resid64": it[3]},
         "adjoint": adj,
+        "serving": serve,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
     print(json.dumps(line), flush=True)

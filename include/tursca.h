@@ -234,6 +234,9 @@ tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 /* Number of kernel launches the scene has issued since creation. */
 long long tursca_launch_count(const tursca_scene *scene);
 
+/* Device memory the scene holds (bytes of its own allocations). */
+size_t tursca_scene_device_bytes(const tursca_scene *scene);
+
 /* Per-kernel device time measured with CUDA events recorded on the scene's
  * stream around each launch of the hot kernels (profiling only). */
 typedef struct {
@@ -297,6 +300,62 @@ const char *tursca_status_string(tursca_status status);
 /* Last error message recorded on the scene (or the last global error when
  * scene is NULL), NUL-terminated into buf[n]. */
 tursca_status tursca_last_error(const tursca_scene *scene, char *buf, size_t n);
+
+/* ---- Serving (continuous batching of scene solves).  The paper solves one
+ * scene at a time (Sec. 3, step 4) and notes that the graph structure can be
+ * reused across runs that change only the optical properties (Fig.
+ * tursca-data); the server below is the deployment form of that: a pool of
+ * resident scenes ("slots", one per grid shape and precision in use, each on
+ * its own CUDA stream, keeping graph, tables and solver state between
+ * requests) and worker threads that run each request's
+ * set_medium -> assemble_flux -> solve -> render_radiance on a free slot.
+ * Requests that arrive while others run are admitted as soon as a worker and
+ * a slot are free; a request whose shape has no idle slot gets a new slot if
+ * the slot's device memory fits the budget (idle slots of other shapes are
+ * evicted, least recently used first, to make room) and otherwise waits.
+ * Work of concurrent requests overlaps on the device.  Every request runs
+ * the same deterministic kernels on its own scene, so its radiance does not
+ * depend on what else runs (tested bit for bit). */
+typedef struct tursca_server tursca_server;
+
+typedef struct {
+    double submit_ms;     /* times on the server's clock (ms since creation) */
+    double start_ms;      /* a worker began the request */
+    double end_ms;        /* the radiance was copied out */
+    int slot_reused;      /* 1: ran on a resident slot, 0: a new slot was built */
+    int iters;            /* solver products with K */
+    double rel_resid64;   /* final relative residual */
+    tursca_status status; /* the request's own status */
+} tursca_request_info;
+
+typedef struct {
+    size_t budget_bytes, used_bytes, peak_bytes;
+    int slots, busy_slots, pending, evictions, slots_built;
+} tursca_server_stats;
+
+/* hbm_budget_bytes: device memory the slots may hold together (>= the
+ * largest single slot); max_concurrent: worker threads (1..64), i.e. requests
+ * on the device at once.  Uses the current device. */
+tursca_status tursca_server_create(size_t hbm_budget_bytes, int max_concurrent, tursca_server **out);
+
+/* Queue one scene solve.  desc, geom: as for tursca_scene_create /
+ * tursca_assemble_flux (copied).  mu_abs, mu_sca, g, albedo: as for
+ * tursca_set_medium, host or device, borrowed until tursca_server_wait
+ * returns for this ticket.  radiance: caller output [npy][npx] in the scene
+ * precision, host or device.  rtol: as for tursca_solve.  Returns at once
+ * with a ticket; invalid descriptors return TURSCA_E_INVALID. */
+tursca_status tursca_server_submit(tursca_server *srv, const tursca_grid_desc *desc, const tursca_geometry *geom,
+                                   const void *mu_abs, const void *mu_sca, const double *g, double albedo,
+                                   double rtol, void *radiance, long long *ticket);
+
+/* Block until the request completes; info may be NULL.  Returns the
+ * request's status (the ticket is released). */
+tursca_status tursca_server_wait(tursca_server *srv, long long ticket, tursca_request_info *info);
+
+tursca_status tursca_server_stats_get(tursca_server *srv, tursca_server_stats *out);
+
+/* Waits for all queued requests, then frees every slot. */
+tursca_status tursca_server_destroy(tursca_server *srv);
 
 #ifdef __cplusplus
 }

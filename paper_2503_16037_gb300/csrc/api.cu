@@ -17,6 +17,19 @@ namespace {
 thread_local std::string g_last_error;
 }
 
+// device allocations owned by a scene, with their total size
+struct AllocList {
+    std::vector<void *> ptrs;
+    size_t bytes = 0;
+};
+
+// a device buffer reused across calls, grown only when a call needs more
+// (a geometry change then costs no device-wide synchronisation of cudaFree)
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
 struct tursca_scene {
     tursca_grid_desc d{};
     cudaStream_t st = nullptr;
@@ -42,8 +55,8 @@ struct tursca_scene {
     double g[tk::MAX_SPECIES] = {0, 0, 0, 0};
     double albedo = 0.0;
 
-    std::vector<void *> allocs;      // graph-lifetime allocations
-    std::vector<void *> view_allocs; // geometry-lifetime allocations
+    AllocList allocs;       // graph-lifetime allocations
+    DevBuf vbuf[16];        // geometry-dependent buffers (sun and line-of-sight taps, pixels)
 
     // graph
     int *tstart = nullptr;
@@ -148,26 +161,45 @@ tursca_status cuda_fail(tursca_scene *sc, cudaError_t e, const char *where) {
     } while (0)
 
 template <typename P>
-cudaError_t dalloc(std::vector<void *> &list, P *&p, size_t bytes) {
+cudaError_t dalloc(AllocList &list, P *&p, size_t bytes) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    const size_t b = bytes ? bytes : 16;
+    cudaError_t e = cudaMalloc(&q, b);
     if (e != cudaSuccess) return e;
-    list.push_back(q);
+    list.ptrs.push_back(q);
+    list.bytes += b;
     p = reinterpret_cast<P *>(q);
     return cudaSuccess;
 }
 
 template <typename P>
-cudaError_t upload(tursca_scene *sc, std::vector<void *> &list, P *&p, const void *src, size_t bytes) {
+cudaError_t upload(tursca_scene *sc, AllocList &list, P *&p, const void *src, size_t bytes) {
     cudaError_t e = dalloc(list, p, bytes);
     if (e != cudaSuccess) return e;
     if (bytes) e = cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, sc->st);
     return e;
 }
 
-void free_list(std::vector<void *> &list) {
-    for (void *p : list) cudaFree(p);
-    list.clear();
+void free_list(AllocList &list) {
+    for (void *p : list.ptrs) cudaFree(p);
+    list.ptrs.clear();
+    list.bytes = 0;
+}
+
+// copy bytes from host src into buffer b (grown if needed) on stream st
+template <typename P>
+cudaError_t put(DevBuf &b, P *&out, const void *src, size_t bytes, cudaStream_t st) {
+    const size_t need = bytes ? bytes : 16;
+    if (need > b.cap) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        cudaError_t e = cudaMalloc(&b.p, need);
+        if (e != cudaSuccess) return e;
+        b.cap = need;
+    }
+    out = reinterpret_cast<P *>(b.p);
+    return (bytes && src) ? cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
 }
 
 tk::GridC grid_c(const tursca_scene *sc) {
@@ -924,7 +956,8 @@ tursca_status tursca_scene_destroy(tursca_scene *sc) {
     if (!sc) return TURSCA_OK;
     cudaStreamSynchronize(sc->st);
     free_list(sc->allocs);
-    free_list(sc->view_allocs);
+    for (DevBuf &v : sc->vbuf)
+        if (v.p) cudaFree(v.p);
     if (sc->hred) cudaFreeHost(sc->hred);
     for (cudaEvent_t e : sc->ev) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i)
@@ -1193,30 +1226,31 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
             if (std::abs(t.dx) > 32000 || std::abs(t.dy) > 32000) return fail(sc, TURSCA_E_INVALID, "ray too oblique");
         for (const auto &t : VT.los_taps)
             if (std::abs(t.dx) > 32000 || std::abs(t.dy) > 32000) return fail(sc, TURSCA_E_INVALID, "ray too oblique");
-        CK(cudaStreamSynchronize(sc->st), "sync");
-        free_list(sc->view_allocs);
+        CK(cudaStreamSynchronize(sc->st), "sync");  // earlier work of the scene may read the buffers
         sc->VT = VT;
         std::vector<tk::DTap> to;
         std::vector<float> lf;
         std::vector<double> ld;
+        DevBuf *vb = sc->vbuf;
         split_taps(VT.sun_taps, to, lf, ld);
-        CK(upload(sc, sc->view_allocs, sc->sun_taps, to.data(), to.size() * sizeof(tk::DTap)), "upload sun");
-        CK(upload(sc, sc->view_allocs, sc->sun_lf, lf.data(), lf.size() * sizeof(float)), "upload sun");
-        CK(upload(sc, sc->view_allocs, sc->sun_ld, ld.data(), ld.size() * sizeof(double)), "upload sun");
-        CK(upload(sc, sc->view_allocs, sc->sun_off, VT.sun_off.data(), VT.sun_off.size() * sizeof(int)), "upload sun");
-        CK(upload(sc, sc->view_allocs, sc->sun_n, VT.sun_n.data(), VT.sun_n.size() * sizeof(int)), "upload sun");
+        CK(put(vb[0], sc->sun_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload sun");
+        CK(put(vb[1], sc->sun_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload sun");
+        CK(put(vb[2], sc->sun_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload sun");
+        CK(put(vb[3], sc->sun_off, VT.sun_off.data(), VT.sun_off.size() * sizeof(int), sc->st), "upload sun");
+        CK(put(vb[4], sc->sun_n, VT.sun_n.data(), VT.sun_n.size() * sizeof(int), sc->st), "upload sun");
+        // (pageable host memory: the copies are complete when put returns)
         split_taps(VT.los_taps, to, lf, ld);
-        CK(upload(sc, sc->view_allocs, sc->los_taps, to.data(), to.size() * sizeof(tk::DTap)), "upload los");
-        CK(upload(sc, sc->view_allocs, sc->los_lf, lf.data(), lf.size() * sizeof(float)), "upload los");
-        CK(upload(sc, sc->view_allocs, sc->los_ld, ld.data(), ld.size() * sizeof(double)), "upload los");
-        CK(upload(sc, sc->view_allocs, sc->los_off, VT.los_off.data(), VT.los_off.size() * sizeof(int)), "upload los");
-        CK(upload(sc, sc->view_allocs, sc->los_n, VT.los_n.data(), VT.los_n.size() * sizeof(int)), "upload los");
-        CK(upload(sc, sc->view_allocs, sc->pix_cx, VT.pix_cx.data(), VT.pix_cx.size() * sizeof(int)), "upload pix");
-        CK(upload(sc, sc->view_allocs, sc->pix_cy, VT.pix_cy.data(), VT.pix_cy.size() * sizeof(int)), "upload pix");
-        CK(upload(sc, sc->view_allocs, sc->pix_cls, VT.pix_cls.data(), VT.pix_cls.size() * sizeof(int)), "upload pix");
+        CK(put(vb[5], sc->los_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload los");
+        CK(put(vb[6], sc->los_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload los");
+        CK(put(vb[7], sc->los_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload los");
+        CK(put(vb[8], sc->los_off, VT.los_off.data(), VT.los_off.size() * sizeof(int), sc->st), "upload los");
+        CK(put(vb[9], sc->los_n, VT.los_n.data(), VT.los_n.size() * sizeof(int), sc->st), "upload los");
+        CK(put(vb[10], sc->pix_cx, VT.pix_cx.data(), VT.pix_cx.size() * sizeof(int), sc->st), "upload pix");
+        CK(put(vb[11], sc->pix_cy, VT.pix_cy.data(), VT.pix_cy.size() * sizeof(int), sc->st), "upload pix");
+        CK(put(vb[12], sc->pix_cls, VT.pix_cls.data(), VT.pix_cls.size() * sizeof(int), sc->st), "upload pix");
         size_t np = (size_t)geom->npx * geom->npy;
-        CK(dalloc(sc->view_allocs, sc->rad, np * sc->es), "alloc rad");
-        CK(dalloc(sc->view_allocs, sc->refl, np * sc->es), "alloc refl");
+        CK(put(vb[13], sc->rad, nullptr, np * sc->es, sc->st), "alloc rad");
+        CK(put(vb[14], sc->refl, nullptr, np * sc->es, sc->st), "alloc refl");
         CK(cudaStreamSynchronize(sc->st), "sync");
         sc->view_ok = true;
     }
@@ -1360,6 +1394,13 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
 }
 
 long long tursca_launch_count(const tursca_scene *sc) { return sc ? sc->launches : 0; }
+
+size_t tursca_scene_device_bytes(const tursca_scene *sc) {
+    if (!sc) return 0;
+    size_t b = sc->allocs.bytes;
+    for (const DevBuf &v : sc->vbuf) b += v.cap;
+    return b;
+}
 
 tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");

@@ -47,6 +47,17 @@ class tursca_geometry(C.Structure):
                 ("f0", C.c_double), ("npx", C.c_int), ("npy", C.c_int)]
 
 
+class tursca_request_info(C.Structure):
+    _fields_ = [("submit_ms", C.c_double), ("start_ms", C.c_double), ("end_ms", C.c_double),
+                ("slot_reused", C.c_int), ("iters", C.c_int), ("rel_resid64", C.c_double), ("status", C.c_int)]
+
+
+class tursca_server_stats(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("used_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
+                ("slots", C.c_int), ("busy_slots", C.c_int), ("pending", C.c_int), ("evictions", C.c_int),
+                ("slots_built", C.c_int)]
+
+
 class tursca_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("rel_resid64", C.c_double),
                 ("rho_est", C.c_double), ("solver", C.c_int)]
@@ -89,6 +100,14 @@ def lib() -> C.CDLL:
             "tursca_adjoint": (st, [_vp, _vp, _vp]),
             "tursca_get": (st, [_vp, C.c_int, _vp, C.c_size_t]),
             "tursca_launch_count": (C.c_longlong, [_vp]),
+            "tursca_scene_device_bytes": (C.c_size_t, [_vp]),
+            "tursca_server_create": (st, [C.c_size_t, C.c_int, C.POINTER(_vp)]),
+            "tursca_server_submit": (st, [_vp, C.POINTER(tursca_grid_desc), C.POINTER(tursca_geometry), _vp, _vp,
+                                          C.POINTER(C.c_double), C.c_double, C.c_double, _vp,
+                                          C.POINTER(C.c_longlong)]),
+            "tursca_server_wait": (st, [_vp, C.c_longlong, C.POINTER(tursca_request_info)]),
+            "tursca_server_stats_get": (st, [_vp, C.POINTER(tursca_server_stats)]),
+            "tursca_server_destroy": (st, [_vp]),
             "tursca_graph_info": (st, [C.POINTER(tursca_grid_desc), C.POINTER(tursca_graph_stats)]),
             "tursca_graph_structure": (st, [C.POINTER(tursca_grid_desc), _vp, _vp, _vp, _vp]),
             "tursca_quadrature": (st, [C.POINTER(tursca_grid_desc), _vp, _vp]),
@@ -374,4 +393,70 @@ def render(mu_a, runner, mu_s, rtol=1e-10):
     if _TurscaRender is None:
         _TurscaRender = _autograd()
     return _TurscaRender.apply(mu_a, runner, mu_s, rtol)
+
+
+class Server:
+    """Continuous-batching server of scene solves (the tursca_server_* calls):
+    requests are queued at once, run on resident slots by the library's
+    worker threads, and collected with wait().  Inputs are copied to pinned
+    host buffers at submit and kept alive until wait() returns."""
+
+    def __init__(self, budget_bytes: int, workers: int):
+        import torch
+        self.torch = torch
+        h = _vp()
+        st = lib().tursca_server_create(C.c_size_t(int(budget_bytes)), int(workers), C.byref(h))
+        if st != OK:
+            raise TurscaError(st, "tursca_server_create failed")
+        self.handle = h.value
+        self._live = {}
+
+    def submit(self, sc, precision: Optional[int] = None, rtol: float = 1e-10, fields=None, out=None) -> int:
+        """Queue scene ``sc``; fields = (mu_a, mu_s) tensors (host pinned or
+        device) or None to take them from ``sc``; out = radiance tensor or None."""
+        t = self.torch
+        desc = grid_desc(sc, precision)
+        dtype = t.float64 if desc.precision == FP64 else t.float32
+        if fields is None:
+            mu_a = t.as_tensor(np.ascontiguousarray(sc.mu_a), dtype=dtype).pin_memory()
+            mu_s = t.as_tensor(np.ascontiguousarray(sc.mu_s), dtype=dtype).pin_memory()
+        else:
+            mu_a, mu_s = fields
+        if out is None:
+            out = t.empty((sc.npy, sc.npx), dtype=dtype).pin_memory()
+        g = (C.c_double * len(sc.g))(*[float(v) for v in sc.g])
+        geom = geometry(sc)
+        tk = C.c_longlong()
+        st = lib().tursca_server_submit(self.handle, C.byref(desc), C.byref(geom), _ptr(mu_a), _ptr(mu_s), g,
+                                        float(sc.albedo), float(rtol), _ptr(out), C.byref(tk))
+        if st != OK:
+            raise TurscaError(st, "tursca_server_submit failed")
+        self._live[tk.value] = (mu_a, mu_s, out, g, desc, geom)
+        return tk.value
+
+    def wait(self, ticket: int):
+        info = tursca_request_info()
+        st = lib().tursca_server_wait(self.handle, C.c_longlong(ticket), C.byref(info))
+        keep = self._live.pop(ticket)
+        if st != OK:
+            raise TurscaError(st, "request %d failed" % ticket)
+        d = {k: getattr(info, k) for k, _ in tursca_request_info._fields_}
+        return keep[2], d
+
+    def stats(self) -> dict:
+        s = tursca_server_stats()
+        _check(None, lib().tursca_server_stats_get(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in tursca_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().tursca_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
