@@ -201,7 +201,7 @@ __global__ void k_segtau(GridC g, GraphP gp, FieldP<T> f) {
     int4 d = gp.dirs[u];
     int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
     T tau = T(0);
-    if (z + d.z < g.nz) tau = tap_sum<T>(g, gp, f.mu_e, gp.lat_off[u], gp.lat_n[u], x, y, z);
+    if (z + d.z < g.nz) tau = tap_sum_h<T>(gp, f.mu_e_h, gp.lat_off[u], gp.lat_n[u], (int)halo_pos(g, x, y, z));
     store_halo(f.tseg + (size_t)c * g.npad, g, x, y, z, tau);
 }
 
@@ -262,16 +262,17 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
     T rt_src;
     if (j < g.n_atm) {
         rt_src = f.rt[j];
+        const T *rt_j = f.rt_h + halo_pos(g, x, y, z);  // |u_x|, |u_y| <= R: no wrap
         T w[MAX_SPECIES];
         #pragma unroll
         for (int sp = 0; sp < MAX_SPECIES; ++sp) if (sp < g.S) w[sp] = f.wsp[(size_t)sp * g.n_atm + j];
-#pragma unroll 2
+#pragma unroll 4
         for (int u = 0; u < g.nd; ++u) {
             int4 d = gp.dirs[u];
             int rz = z + d.z;
             T rtn, dist;
             if (rz >= 0 && rz < g.nz) {
-                rtn = __ldg(f.rt + (rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx));
+                rtn = __ldg(rt_j + __ldg(gp.dir_h + u));
                 dist = Cst<T>::dir_len(gp, u);
             } else if (d.z < 0) {
                 rtn = rt_lamb;
