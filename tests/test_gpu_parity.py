@@ -256,3 +256,20 @@ def test_plume_full_size_bench_configuration():
     vg, vo = match_slots(rn, r)
     idx = np.random.default_rng(0).choice(len(vo), 200000, replace=False)
     assert rel_err(vg[idx], vo[idx], 1e-6 * vo.max()).max() < 2e-5
+
+
+def test_cloud_full_size_configuration():
+    """The broken-cloud configuration at full size (128 x 128 x 40, R = 2,
+    about 81M edges; omega 0.999, largest eigenvalue of K near 0.99, so the
+    solver hands over to GMRES), FP32 + FP64 refinement, every radiance
+    against the FP64 oracle."""
+    sc = scenes.make_cloud()
+    r = O.run(sc)
+    rn, rad, refl = run_gpu(sc, precision=T.FP32_REFINE, rtol=1e-10)
+    err = rel_err(rad, r["rad"])
+    print("cloud 128x128x40: max rel err %.3e  mean %.3e  iters %d refinements %d solver %d"
+          % (err.max(), err.mean(), rn.info.iters, rn.info.refinements, rn.info.solver))
+    assert rn.info.rel_resid64 <= 1e-10
+    assert err.max() < 1e-4
+    assert rel_err(refl, r["refl"]).max() < 1e-4
+
