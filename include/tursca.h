@@ -227,8 +227,28 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     same products in the same order for the same TURSCA_OPT_GROUP_WARPS.
  *     A copy that does not land within about a second makes the solve
  *     return TURSCA_E_TIMEOUT.
+ *   TURSCA_OPT_L2_RESIDENT: 0 (default); 1 keeps the values of K in the
+ *     persisting part of L2 while a solve runs (every pass of a solve streams
+ *     the same values).  Setting 1 raises this CUDA context's persisting-L2
+ *     set-aside to the device maximum for the rest of the process; each
+ *     solve sets an access-policy window over the values on the scene
+ *     stream, and on return removes it and resets every persisting line of
+ *     the context to normal (which also affects other scenes running
+ *     concurrently in the same context).  Pays only when the values fit in
+ *     the set-aside; results are bit-identical either way.
+ *   TURSCA_OPT_GATHER_TILE: 1 (default) lets the FP32 row-group passes that
+ *     gather from one vector (sweeps, Chebyshev steps, products with I - K)
+ *     copy each group's source rows into a shared-memory tile (at most
+ *     48 KB per block; larger groups gather from global memory); 0 always
+ *     gathers from global memory.  Results are bit-identical either way.
  */
-enum { TURSCA_OPT_RESIDUAL_FP64 = 1, TURSCA_OPT_GROUP_WARPS = 2, TURSCA_OPT_STAGE_VALUES = 3 };
+enum {
+    TURSCA_OPT_RESIDUAL_FP64 = 1,
+    TURSCA_OPT_GROUP_WARPS = 2,
+    TURSCA_OPT_STAGE_VALUES = 3,
+    TURSCA_OPT_L2_RESIDENT = 4,
+    TURSCA_OPT_GATHER_TILE = 5
+};
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 
 /* Number of kernel launches the scene has issued since creation. */

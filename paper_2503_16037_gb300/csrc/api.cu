@@ -75,6 +75,8 @@ struct tursca_scene {
     int *cell_start = nullptr;
     int *canon_dirs = nullptr, *up_canon = nullptr;
     int *tflat = nullptr;  // template offsets in the haloed layout
+    int *ttile = nullptr, *tlay = nullptr;  // gather-tile offsets and layers of the row-group passes
+    int tile_tl = 0;                        // floats per tile layer (0: no tiles)
     tk::ASlot *aslot = nullptr;  // edge-kernel descriptors of the template entries
     int *tap_h = nullptr, *dir_h = nullptr;  // haloed offsets of the taps and the directions
     void *rt_h = nullptr, *wsp_h = nullptr, *mu_e_h = nullptr, *e1_h = nullptr;  // haloed copies
@@ -103,6 +105,8 @@ struct tursca_scene {
     int gm_m = 0;
     int resid_fp64 = 0;  // 1: evaluate the refinement residual with FP64 arithmetic
     int stage_values = 0;  // 1: FP32 passes stream the values through shared memory (persistent kernels)
+    int l2_resident = 0;   // 1: the solves keep the values of K in the persisting part of L2
+    int gather_tile = 1;   // 1: FP32 passes gather from a shared-memory tile
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
     // auxiliary streams and events for the concurrent per-scene tables
@@ -228,6 +232,7 @@ tk::GridC grid_c(const tursca_scene *sc) {
     g.lp = g.nxp * g.nyp;
     g.npad = (long long)(g.nz + 1) * g.lp;
     g.stage = (sc->stage_values && sc->d.precision != TURSCA_FP64 && tk::stage_fits(G.max_row)) ? 1 : 0;
+    g.tl = sc->gather_tile ? sc->tile_tl : 0;
     g.hx = sc->d.hx;
     g.hy = sc->d.hy;
     g.hz = sc->d.hz;
@@ -264,6 +269,8 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.up_canon = sc->up_canon;
     p.status = sc->status;
     p.tflat = sc->tflat;
+    p.ttile = sc->ttile;
+    p.tlay = sc->tlay;
     p.aslot = sc->aslot;
     p.tap_h = sc->tap_h;
     p.dir_h = sc->dir_h;
@@ -613,9 +620,44 @@ SolveIO<T> forward_io(tursca_scene *sc) {
     return io;
 }
 
+// The values of K in the persisting part of L2 for the passes of one solve
+// (TURSCA_OPT_L2_RESIDENT): every pass of a solve streams the same values,
+// and a scene's values often fit in the 126 MB L2.  The window covers the
+// values (the fraction of it that the set-aside holds, by address); when the
+// solve ends the window is removed and the persisting lines return to normal
+// status, so later work finds an ordinary cache.
+struct L2Window {
+    cudaStream_t st = nullptr;
+    L2Window(tursca_scene *sc, const void *base, size_t bytes) {
+        if (!sc->l2_resident || !base || !bytes) return;
+        int dev = 0, maxw = 0;
+        size_t lim = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return;
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+        cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+        if (maxw <= 0 || lim == 0) return;
+        cudaStreamAttrValue a = {};
+        a.accessPolicyWindow.base_ptr = const_cast<void *>(base);
+        a.accessPolicyWindow.num_bytes = std::min(bytes, (size_t)maxw);
+        a.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)lim / (double)a.accessPolicyWindow.num_bytes);
+        a.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        a.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        if (cudaStreamSetAttribute(sc->st, cudaStreamAttributeAccessPolicyWindow, &a) == cudaSuccess) st = sc->st;
+    }
+    ~L2Window() {
+        if (!st) return;
+        cudaStreamAttrValue a = {};
+        a.accessPolicyWindow.num_bytes = 0;
+        cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &a);
+        cudaStreamSynchronize(st);
+        cudaCtxResetPersistingL2Cache();
+    }
+};
+
 template <typename T>
 tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info,
                        const SolveIO<T> &io) {
+    const L2Window l2w(sc, io.val, (size_t)sc->G.nval * sizeof(T));
     const tk::GridC &g = io.g;
     const tk::GraphP &gp = io.gp;
     const T *val = io.val;
@@ -896,6 +938,8 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
     gpT.tstart = sc->tstartT;
     gpT.voff = sc->voffT;
     gpT.tflat = sc->flatT;
+    gpT.ttile = nullptr;  // the K^T passes gather from global memory
+    gpT.tlay = nullptr;
     tk::AdjP<T> ad;
     T **slot[10] = {&ad.Ebar, &ad.Ebar_h, &ad.e1bar, &ad.e1bar_h, &ad.xbar,
                     &ad.mubar, &ad.mubar_h, &ad.tsegbar, &ad.tinfbar, &ad.tinfgbar};
@@ -914,6 +958,7 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
     // (I - K)^T lambda = x-bar
     SolveIO<T> io;
     g.stage = 0;
+    g.tl = 0;
     io.g = g;
     io.gp = gpT;
     io.val = (const T *)sc->valT;
@@ -1109,6 +1154,17 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
                 tf[i] = (szl - z) * lp + t.sdy * nxp + t.sdx;
             }
         CK(upload(sc, sc->allocs, sc->tflat, tf.data(), tf.size() * sizeof(int)), "upload tmpl");
+        // gather tiles of the FP32 row-group passes (none when a group's
+        // tile would exceed kTileMaxBytes)
+        static_assert(tg::kTileLayers == tk::kTileLayers, "tile layers");
+        tg::TileLayout tl;
+        sc->tile_tl = 0;
+        if (tg::tile_layout(G, H, tl).empty() &&
+            (size_t)tk::kTileLayers * tl.tl * sizeof(float) <= (size_t)tk::kTileMaxBytes) {
+            CK(upload(sc, sc->allocs, sc->ttile, tl.ttile.data(), tl.ttile.size() * sizeof(int)), "upload tiles");
+            CK(upload(sc, sc->allocs, sc->tlay, tl.layers.data(), tl.layers.size() * sizeof(int)), "upload tiles");
+            sc->tile_tl = tl.tl;
+        }
         // edge-kernel descriptors (every lookup of a slot as one offset from
         // the receiver's haloed position)
         std::vector<tg::EdgeDesc> ed;
@@ -1407,6 +1463,27 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
     switch (option) {
         case TURSCA_OPT_RESIDUAL_FP64:
             sc->resid_fp64 = value != 0.0;
+            return TURSCA_OK;
+        case TURSCA_OPT_L2_RESIDENT: {
+            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "L2 residency must be 0 or 1");
+            if (value == 1.0) {
+                // the set-aside of this context: as much of L2 as persisting lines may take
+                int dev = 0;
+                cudaDeviceProp prop;
+                CK(cudaGetDevice(&dev), "device");
+                CK(cudaGetDeviceProperties(&prop, dev), "device properties");
+                size_t lim = 0;
+                cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+                if (prop.persistingL2CacheMaxSize > 0 && lim < (size_t)prop.persistingL2CacheMaxSize)
+                    CK(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)prop.persistingL2CacheMaxSize),
+                       "persisting L2 limit");
+            }
+            sc->l2_resident = (int)value;
+            return TURSCA_OK;
+        }
+        case TURSCA_OPT_GATHER_TILE:
+            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "gather tile must be 0 or 1");
+            sc->gather_tile = (int)value;
             return TURSCA_OK;
         case TURSCA_OPT_STAGE_VALUES:
             if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "stage values must be 0 or 1");

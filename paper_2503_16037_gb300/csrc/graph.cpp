@@ -689,4 +689,36 @@ void transpose_templates(const Graph &G, int H, Transposed &T) {
     T.tstart[nz + 1] = (int)T.recv_layer.size();
 }
 
+std::string tile_layout(const Graph &G, int H, TileLayout &L) {
+    const int nx = G.nx, nz = G.nz, nxp = nx + 2 * H;
+    const long long nxy = (long long)nx * G.ny;
+    // rows spanned by a group of kGroup rows: at most ceil((kGroup - 1) / nx) + 1
+    int span = 0;
+    for (long long r0 = 0; r0 < nxy; r0 += kGroup) {
+        const long long r1 = std::min(r0 + kGroup - 1, nxy - 1);
+        span = std::max(span, (int)(r1 / nx - r0 / nx + 1));
+    }
+    L.tl = (span + 2 * H) * nxp;
+    L.layers.assign((size_t)(nz + 1) * kTileLayers, -1);
+    L.ttile.assign(G.tmpl.size(), 0);
+    for (int z = 0; z <= nz; ++z) {
+        int *lay = &L.layers[(size_t)z * kTileLayers];
+        int n = 0;
+        for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
+            const TSlot &t = G.tmpl[i];
+            const int szl = t.sz >= 0 ? t.sz : nz;
+            int ls = -1;
+            for (int k = 0; k < n; ++k)
+                if (lay[k] == szl) ls = k;
+            if (ls < 0) {
+                if (n == kTileLayers) return "a layer draws on more source layers than a tile holds";
+                ls = n;
+                lay[n++] = szl;
+            }
+            L.ttile[i] = ls * L.tl + t.sdy * nxp + t.sdx;
+        }
+    }
+    return std::string();
+}
+
 }  // namespace tg

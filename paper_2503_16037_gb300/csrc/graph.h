@@ -112,8 +112,10 @@ struct Graph {
     // row templates: layers 0..nz-1, then the ground (index nz).  Every row of
     // a template has the same slots in the same order.  Values are stored per
     // group of kGroup rows of a layer, slot-major inside the group:
-    // val[voff[z] + ((r / kGroup) * nt + t) * kGroup + r % kGroup]
-    // (r = row - z * nxy, nt = template length); layers are padded to whole groups.
+    // val[voff[z] + ((r / kGroup) * nt + t) * kGroup + pos(r % kGroup)], with
+    // pos(i) = 4 (i mod 32) + i / 32 (the four rows a lane of a 32-wide warp owns
+    // are adjacent) (r = row - z * nxy, nt = template length); layers are padded
+    // to whole groups.
     std::vector<int> tmpl_start;  // [nz + 2]
     std::vector<TSlot> tmpl;
     std::vector<int> tmpl_len;    // row length per template
@@ -145,6 +147,23 @@ struct EdgeDesc {
 // (non-empty message) if a lookup lies more than H columns from its receiver.
 std::string edge_descriptors(const Graph &G, int H, std::vector<EdgeDesc> &out, std::vector<int> &tap_h,
                              std::vector<int> &dir_h);
+
+// Shared-memory tiles of the gathered vector for the row-group passes.  The
+// sources of a group of 128 rows of layer z lie in at most kTileLayers
+// layers (the receiver's layer +- R and the ground) and in the group's rows
+// +- H; the tile holds, for each such layer, the rows y0 - H .. y1 + H of the
+// haloed layout (y0, y1: first and last row of the group), each layer at a
+// stride of tl floats.  A slot's source is then tile[ttile[t] + rl], with rl
+// = (y - y0 + H) (nx + 2H) + x + H the row's position inside one tile layer.
+constexpr int kTileLayers = 6;
+struct TileLayout {
+    std::vector<int> ttile;        // per template entry: layer slot * tl + sdy * (nx + 2H) + sdx
+    std::vector<int> layers;       // [(nz + 1) * kTileLayers] haloed source layer of each slot, -1: unused
+    int tl = 0;                    // floats per tile layer (the largest group span)
+};
+// Fails (non-empty message) if a layer's templates draw on more than
+// kTileLayers source layers.
+std::string tile_layout(const Graph &G, int H, TileLayout &L);
 
 // Templates of K^T: for every source layer zs (zs = nz: the ground), the
 // template entries of all receiver layers whose source lies in layer zs, in

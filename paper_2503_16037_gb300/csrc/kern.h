@@ -68,6 +68,7 @@ struct GridC {
     int H, nxp, nyp, lp;
     long long npad;              // (nz + 1) * lp
     int stage;                   // 1: FP32 sweeps stage each group's values in shared memory
+    int tl;                      // floats per layer of a group's gather tile (0: passes gather from global memory)
     double hx, hy, hz;
 };
 
@@ -106,6 +107,8 @@ struct GraphP {
     const ASlot *aslot;            // per template entry: the edge kernel's lookups
     const int *tap_h;              // per tap: haloed offset from the tap's base cell
     const int *dir_h;              // per atmospheric direction: haloed offset of u
+    const int *ttile;              // per template entry: the source's offset in a group's gather tile
+    const int *tlay;               // [(nz + 1) * kTileLayers] haloed layer copied into each tile layer (-1: none)
     // Runs of the persistent streamed passes: block b of pass kind k (0: all
     // (nz + 1) * gpl groups, 1: the nz * gpl atmospheric groups) handles the
     // groups [run_g[k][b], run_g[k][b + 1]), whose values are
@@ -194,10 +197,18 @@ struct Cst<double> {
     __device__ static __forceinline__ double split(const DClass &c) { return c.split; }
 };
 
-// Values: per group of kGroup rows of a layer, slot-major inside the group.
+// Values: per group of kGroup rows of a layer, slot-major inside the group;
+// inside one slot row of 128 values, row i of the group (lane i mod 32, row
+// block i / 32) sits at 4 (i mod 32) + i / 32, so the four rows a lane owns
+// are one aligned 16-byte (FP32) or 32-byte (FP64) quad.
 constexpr int kGroup = 128;
+__host__ __device__ __forceinline__ int val_lane_pos(int i) { return ((i & 31) << 2) | (i >> 5); }
+// source layers a group's gather tile holds (the receiver layer +- R and the ground)
+constexpr int kTileLayers = 6;
+// largest gather tile (bytes of shared memory per block)
+constexpr int kTileMaxBytes = 48 * 1024;
 __host__ __device__ __forceinline__ long long val_base(long long voff_z, int nt, int r) {
-    return voff_z + (long long)(r / kGroup) * nt * kGroup + (r % kGroup);
+    return voff_z + (long long)(r / kGroup) * nt * kGroup + val_lane_pos(r % kGroup);
 }
 
 // source node of template slot (sdx, sdy, flat) for the receiver at (x, y)

@@ -80,17 +80,18 @@ __global__ void k_transpose_vals(GridC g, GraphP gp, TransP tp, const T *__restr
         const int zi = inf.y;
         const int nt = __ldg(gp.tstart + zi + 1) - __ldg(gp.tstart + zi);
         const long long vz = __ldg(gp.voff + zi);
+        T v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int r = q * kGroup + lane + 32 * k;
-            T v = T(0);
+            v[k] = T(0);
             if (r < g.nxy) {
                 const int y = r / g.nx, x = r - y * g.nx;
                 const int ri = wrap_small(y - inf.w, g.ny) * g.nx + wrap_small(x - inf.z, g.nx);
-                v = val[vz + ((long long)(ri / kGroup) * nt + inf.x) * kGroup + ri % kGroup];
+                v[k] = val[val_base(vz, nt, ri) + (long long)inf.x * kGroup];
             }
-            valT[vbT + (long long)e * kGroup + lane + 32 * k] = v;
         }
+        st_quad(valT + vbT + (long long)e * kGroup + 4 * lane, v);
     }
 }
 

@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP
         }
     }
     T acc_s[4] = {T(0), T(0), T(0), T(0)}, acc_g[4] = {T(0), T(0), T(0), T(0)};
-    T *vout = f.val + G.vb + lane;
+    T *vout = f.val + G.vb + 4 * lane;
     for (int t = w; t < G.nt; t += kAsmW) {
         const ASlot &d = gp.aslot[G.t0 + t];
         const int4 a0 = __ldg(reinterpret_cast<const int4 *>(&d));
@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP
                 for (int k = 0; k < 4; ++k) th[k] += wr[k][sp] * h;
             }
         }
+        T kv[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int rp = G.rp[k];
@@ -431,11 +432,12 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP
                 Wi = q * (a > T(0) ? a * rtn * dinv : T(1));
                 Ws = Wi;
             }
-            vout[(size_t)t * kGroup + 32 * k] = rho[k] * Wi * P;
+            kv[k] = rho[k] * Wi * P;
             const T sun = rho[k] * Ws * P * __ldg(f.e1_h + j);
             acc_s[k] += sun;
             acc_g[k] += th[k] * sun;
         }
+        st_quad(vout + (size_t)t * kGroup, kv);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

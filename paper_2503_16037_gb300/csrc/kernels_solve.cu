@@ -45,6 +45,9 @@ struct OpSpmv {
     };
     const T *x, *b;
     T *y;
+    static constexpr bool kTile = sizeof(T) == 4;
+    __device__ __forceinline__ const T *gsrc() const { return x; }
+    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -105,6 +108,9 @@ struct OpSweepPow {
     const T *x, *b;
     T *y;
     double *part;
+    static constexpr bool kTile = sizeof(T) == 4;
+    __device__ __forceinline__ const T *gsrc() const { return x; }
+    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -138,6 +144,9 @@ struct OpCheb {
     const T *p;
     T *r, *d, *pn;
     T c1, c2;
+    static constexpr bool kTile = sizeof(T) == 4;
+    __device__ __forceinline__ const T *gsrc() const { return p; }
+    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(p + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {

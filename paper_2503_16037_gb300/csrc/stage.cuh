@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "kern.h"
 
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) k_pipe(GridC g, GraphP gp, co
         pipe_wait(smem_addr(&full[s]), (unsigned)((i / kPipeStages) & 1), &abort_flag, gp.status, true);
         const long long off = v0 + (long long)i * kPipeStageFloats;
         const int rows = (int)((v1 - off < kPipeStageFloats ? v1 - off : kPipeStageFloats) / kGroup);
-        const float *st = ring + (size_t)s * kPipeStageFloats + lane;
+        const float *st = ring + (size_t)s * kPipeStageFloats + 4 * lane;
         int u = 0;  // slot rows of this chunk consumed
         while (u < rows) {
             const int seg = min(rows - u, G.nt - t);  // rows of the current group in this chunk
@@ -283,9 +284,10 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) k_pipe(GridC g, GraphP gp, co
             for (; tt < t + seg; tt += W) {
                 const int fp = __ldg(gp.tflat + G.t0 + tt);
                 const auto si = op.slot(gp, G.t0 + tt);
-                const float *vt = st + (size_t)(u + tt - t) * kGroup;
+                const float4 vq = *reinterpret_cast<const float4 *>(st + (size_t)(u + tt - t) * kGroup);
+                const float vt[4] = {vq.x, vq.y, vq.z, vq.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) op.add(a, k, vt[32 * k], G.rp[k] + fp, si);
+                for (int k = 0; k < 4; ++k) op.add(a, k, vt[k], G.rp[k] + fp, si);
             }
             u += seg;
             t += seg;
@@ -306,9 +308,10 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) k_pipe(GridC g, GraphP gp, co
     }
 }
 
-// A value of the matrix stream (read once per pass).  Measured on GB300 the
-// plain read-only load is fastest; the L1 no-allocate and evict-first forms
-// (TK_STREAM_LOAD 1, 2) are kept for experiments.
+// The values of the four rows a lane owns in one slot row (adjacent, aligned:
+// 16 bytes in FP32, 32 bytes in FP64), read once per pass.  Measured on GB300
+// the plain read-only load is fastest; the L1 no-allocate and evict-first
+// forms (TK_STREAM_LOAD 1, 2) are kept for experiments.
 #ifndef TK_STREAM_LOAD
 #define TK_STREAM_LOAD 0
 #endif
@@ -317,23 +320,31 @@ __global__ void __launch_bounds__(32 * (W + 1), 1) k_pipe(GridC g, GraphP gp, co
 #elif TK_STREAM_LOAD == 2
 #define TK_STREAM_QUAL "ld.global.nc.L1::evict_first"
 #endif
-__device__ __forceinline__ float ld_stream(const float *p) {
+__device__ __forceinline__ void ld_quad(const float *p, float (&v)[4]) {
 #if TK_STREAM_LOAD == 0
-    return __ldg(p);
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
 #else
-    float v;
-    asm(TK_STREAM_QUAL ".f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
+    asm(TK_STREAM_QUAL ".v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "l"(p));
 #endif
 }
-__device__ __forceinline__ double ld_stream(const double *p) {
-#if TK_STREAM_LOAD == 0
-    return __ldg(p);
-#else
-    double v;
-    asm(TK_STREAM_QUAL ".f64 %0, [%1];" : "=d"(v) : "l"(p));
-    return v;
-#endif
+__device__ __forceinline__ void ld_quad(const double *p, double (&v)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+__device__ __forceinline__ void st_quad(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st_quad(double *p, const double (&v)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
 
 // Programmatic dependent launch: a pass may be launched while the previous
@@ -360,19 +371,16 @@ __global__ void __launch_bounds__(32 * W) k_plain(GridC g, GraphP gp, const T *_
     pdl_trigger();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
-    const T *v = val + G.vb + lane;
+    const T *v = val + G.vb + 4 * lane;
     A a[NA];
 #pragma unroll
     for (int m = 0; m < NA; ++m) a[m] = A(0);
 #if TK_PDL_PEEL
     // the values of the warp's first two slots are requested before waiting
-    T v0[4], v1[4];
+    T v0[4] = {T(0), T(0), T(0), T(0)}, v1[4] = {T(0), T(0), T(0), T(0)};
     const int tA = w, tB = w + W;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v0[k] = tA < G.nt ? ld_stream(v + (size_t)tA * kGroup + 32 * k) : T(0);
-        v1[k] = tB < G.nt ? ld_stream(v + (size_t)tB * kGroup + 32 * k) : T(0);
-    }
+    if (tA < G.nt) ld_quad(v + (size_t)tA * kGroup, v0);
+    if (tB < G.nt) ld_quad(v + (size_t)tB * kGroup, v1);
     pdl_wait();
     const typename Op::Pre pre = load_pre(op, G);
     if (tA < G.nt) {
@@ -397,9 +405,94 @@ __global__ void __launch_bounds__(32 * W) k_plain(GridC g, GraphP gp, const T *_
     for (int t = tfirst; t < G.nt; t += W) {
         const int fp = __ldg(gp.tflat + G.t0 + t);
         const auto si = op.slot(gp, G.t0 + t);
-        const T *vt = v + (size_t)t * kGroup;
+        T q[4];
+        ld_quad(v + (size_t)t * kGroup, q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add(a, k, ld_stream(vt + 32 * k), G.rp[k] + fp, si);
+        for (int k = 0; k < 4; ++k) op.add(a, k, q[k], G.rp[k] + fp, si);
+    }
+#pragma unroll
+    for (int m = 0; m < NA; ++m) sh[w][m][lane] = a[m];
+    __syncthreads();
+    finish_rows<W>(op, sh, G, pre, blockIdx.x);
+}
+
+// ops that gather from a single FP32 vector declare kTile = true, gsrc() (the
+// vector) and add_v (the accumulation of one value times one gathered value)
+template <class Op, class = void>
+struct tile_op {
+    static constexpr bool value = false;
+};
+template <class Op>
+struct tile_op<Op, std::void_t<decltype(Op::kTile)>> {
+    static constexpr bool value = Op::kTile;
+};
+
+// The plain driver with the gathered vector staged in shared memory (FP32
+// ops that gather from one vector).  The sources of a group lie in at most
+// kTileLayers layers and in the rows y0 - H .. y1 + H of the group's first
+// and last rows y0, y1; the block copies those rows of each source layer
+// (whole haloed rows, coalesced) into a tile of tl floats per layer once the
+// previous pass has completed, and every slot then gathers from the tile:
+// tile[ttile[t] + rl], with rl the row's position within one tile layer.
+// Products and their order are those of k_plain.
+template <int W, class Op>
+__global__ void __launch_bounds__(32 * W, 48 / W) k_tile(GridC g, GraphP gp, const float *__restrict__ val, Op op) {
+    using A = typename Op::A;
+    constexpr int NA = Op::NA;
+    __shared__ A sh[W][NA][32];
+    extern __shared__ float tile[];
+    pdl_trigger();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const GroupRows G = group_rows(g, gp, blockIdx.x);
+    const int r0 = (blockIdx.x - G.z * g.gpl) * kGroup;
+    const int y0 = r0 / g.nx;
+    const int y1 = min(r0 + kGroup - 1, g.nxy - 1) / g.nx;
+    const int tla = (y1 - y0 + 2 * g.H + 1) * g.nxp;  // floats copied per tile layer (<= tl)
+    int rl[4];
+    {
+        const int b = G.z * g.lp + y0 * g.nxp;
+        const int pad = g.H * g.nxp + (r0 - y0 * g.nx) + g.H;  // rows past the end read the group's first row
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rl[k] = G.row[k] >= 0 ? G.rp[k] - b : pad;
+    }
+    const float *v = val + G.vb + 4 * lane;
+    A a[NA];
+#pragma unroll
+    for (int m = 0; m < NA; ++m) a[m] = A(0);
+    float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tA = w, tB = w + W;
+    if (tA < G.nt) ld_quad(v + (size_t)tA * kGroup, v0);
+    if (tB < G.nt) ld_quad(v + (size_t)tB * kGroup, v1);
+    pdl_wait();
+    const typename Op::Pre pre = load_pre(op, G);
+    {
+        const float *src = op.gsrc() + (long long)y0 * g.nxp;
+        for (int ls = 0; ls < kTileLayers; ++ls) {
+            const int lay = __ldg(gp.tlay + G.z * kTileLayers + ls);
+            if (lay < 0) break;  // the used tile layers come first
+            const float *s = src + (long long)lay * g.lp;
+            float *d = tile + ls * g.tl;
+            for (int j = threadIdx.x; j < tla; j += 32 * W) d[j] = s[j];
+        }
+    }
+    __syncthreads();
+    if (tA < G.nt) {
+        const int tt = __ldg(gp.ttile + G.t0 + tA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) op.add_v(a, k, v0[k], tile[tt + rl[k]]);
+    }
+    if (tB < G.nt) {
+        const int tt = __ldg(gp.ttile + G.t0 + tB);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) op.add_v(a, k, v1[k], tile[tt + rl[k]]);
+    }
+#pragma unroll kSweepUnroll
+    for (int t = w + 2 * W; t < G.nt; t += W) {
+        const int tt = __ldg(gp.ttile + G.t0 + t);
+        float q[4];
+        ld_quad(v + (size_t)t * kGroup, q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) op.add_v(a, k, q[k], tile[tt + rl[k]]);
     }
 #pragma unroll
     for (int m = 0; m < NA; ++m) sh[w][m][lane] = a[m];
@@ -423,6 +516,9 @@ static void run_pipe(cudaStream_t st, const GridC &g, const GraphP &gp, const fl
 
 #ifndef TK_PDL
 #define TK_PDL 1
+#endif
+#ifndef TK_TILE
+#define TK_TILE 1
 #endif
 #ifndef TK_PLAIN_CARVEOUT
 #define TK_PLAIN_CARVEOUT -1
@@ -449,6 +545,15 @@ static void run_plain(cudaStream_t st, const GridC &g, const GraphP &gp, const T
     at[0].val.programmaticStreamSerializationAllowed = TK_PDL;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+#if TK_TILE
+    if constexpr (sizeof(T) == 4 && tile_op<Op>::value) {
+        if (g.tl > 0) {
+            cfg.dynamicSmemBytes = (size_t)kTileLayers * g.tl * sizeof(float);
+            cudaLaunchKernelEx(&cfg, k_tile<W, Op>, g, gp, val, op);
+            return;
+        }
+    }
+#endif
     cudaLaunchKernelEx(&cfg, k_plain<W, T, Op>, g, gp, val, op);
 }
 

@@ -203,6 +203,8 @@ def tursca_launch_count(scene) -> int:
 OPT_RESIDUAL_FP64 = 1
 OPT_GROUP_WARPS = 2
 OPT_STAGE_VALUES = 3
+OPT_L2_RESIDENT = 4
+OPT_GATHER_TILE = 5
 
 
 def tursca_set_option(scene, option: int, value: float):

@@ -196,6 +196,31 @@ def test_staged_values_identical(name):
                 ref = None
 
 
+@pytest.mark.parametrize("solver", [T.SOLVER_NEUMANN, T.SOLVER_GMRES, T.SOLVER_CHEBYSHEV])
+@pytest.mark.parametrize("name", ["random_R2_ragged", "random_R1_3species", "thin_nz_eq_R", "plume_small"])
+def test_gather_tile_and_l2_residency_identical(name, solver):
+    """Gathering the source vector from a shared-memory tile, and keeping the
+    values of K resident in L2, change where the passes read their operands,
+    not the products or their order: x and the radiance are bit-identical to
+    those of the passes that gather from global memory, for every solver."""
+    sc = SMALL[name]()
+    outs = []
+    for tile, l2 in ((0, 0), (1, 0), (1, 1), (0, 1)):
+        rn = T.Runner(sc, T.FP32_REFINE)
+        T.tursca_set_option(rn.handle, T.OPT_GATHER_TILE, tile)
+        T.tursca_set_option(rn.handle, T.OPT_L2_RESIDENT, l2)
+        mu_a, mu_s = rn.fields("cuda")
+        rad, _ = rn.run(mu_a, mu_s, rtol=1e-11, solver=solver)
+        torch.cuda.synchronize()
+        x = rn.get(T.F_X, rn.stats.n_nodes, torch.float64)
+        outs.append((x, rad.cpu().numpy(), rn.info.iters))
+        rn.close()
+    for got in outs[1:]:
+        assert got[2] == outs[0][2]
+        assert np.array_equal(got[0], outs[0][0])
+        assert np.array_equal(got[1], outs[0][1])
+
+
 def test_host_pointers_end_to_end():
     sc = SMALL["plume_small"]()
     r = O.run(sc)
