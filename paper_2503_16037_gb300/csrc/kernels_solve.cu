@@ -45,9 +45,9 @@ struct OpSpmv {
     };
     const T *x, *b;
     T *y;
-    static constexpr bool kTile = sizeof(T) == 4;
-    __device__ __forceinline__ const T *gsrc() const { return x; }
-    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
+    static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
+    __device__ __forceinline__ const T *gsrc(int) const { return x; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -108,9 +108,9 @@ struct OpSweepPow {
     const T *x, *b;
     T *y;
     double *part;
-    static constexpr bool kTile = sizeof(T) == 4;
-    __device__ __forceinline__ const T *gsrc() const { return x; }
-    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
+    static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
+    __device__ __forceinline__ const T *gsrc(int) const { return x; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -144,9 +144,9 @@ struct OpCheb {
     const T *p;
     T *r, *d, *pn;
     T c1, c2;
-    static constexpr bool kTile = sizeof(T) == 4;
-    __device__ __forceinline__ const T *gsrc() const { return p; }
-    __device__ __forceinline__ void add_v(A *a, int k, T v, T xv) const { a[k] += v * xv; }
+    static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
+    __device__ __forceinline__ const T *gsrc(int) const { return p; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(p + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -202,6 +202,11 @@ struct OpResidDS {
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, float v, int j, NoSlot) const {
         ds_add_prod(a[k], a[4 + k], v, __ldg(xh + j), __ldg(xl + j));
+    }
+    static constexpr int kTile = 2;
+    __device__ __forceinline__ const float *gsrc(int i) const { return i == 0 ? xh : xl; }
+    __device__ __forceinline__ void add_t(A *a, int k, float v, const float *s, int st) const {
+        ds_add_prod(a[k], a[4 + k], v, s[0], s[st]);
     }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
         Pre p;

@@ -416,15 +416,28 @@ __global__ void __launch_bounds__(32 * W) k_plain(GridC g, GraphP gp, const T *_
     finish_rows<W>(op, sh, G, pre, blockIdx.x);
 }
 
-// ops that gather from a single FP32 vector declare kTile = true, gsrc() (the
-// vector) and add_v (the accumulation of one value times one gathered value)
+// resident warps per SM the tiled driver's register budget is sized for, and
+// iterations of its slot loop kept in flight per warp (measured best on GB300:
+// 48 warps, 2 iterations)
+#ifndef TK_TILE_WARPS
+#define TK_TILE_WARPS 48
+#endif
+#ifndef TK_TILE_UNROLL
+#define TK_TILE_UNROLL 2
+#endif
+constexpr int kTileUnroll = TK_TILE_UNROLL;
+
+// Ops that gather from FP32 vectors only declare kTile = n (the number of
+// gathered vectors, 1 or 2), gsrc(i) (vector i) and add_t(a, k, v, s, st):
+// the accumulation of one value times the gathered values s[0], s[st], ...
+// (one tile per vector, st floats apart).
 template <class Op, class = void>
 struct tile_op {
-    static constexpr bool value = false;
+    static constexpr int value = 0;
 };
 template <class Op>
 struct tile_op<Op, std::void_t<decltype(Op::kTile)>> {
-    static constexpr bool value = Op::kTile;
+    static constexpr int value = Op::kTile;
 };
 
 // The plain driver with the gathered vector staged in shared memory (FP32
@@ -436,7 +449,7 @@ struct tile_op<Op, std::void_t<decltype(Op::kTile)>> {
 // tile[ttile[t] + rl], with rl the row's position within one tile layer.
 // Products and their order are those of k_plain.
 template <int W, class Op>
-__global__ void __launch_bounds__(32 * W, 48 / W) k_tile(GridC g, GraphP gp, const float *__restrict__ val, Op op) {
+__global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, GraphP gp, const float *__restrict__ val, Op op) {
     using A = typename Op::A;
     constexpr int NA = Op::NA;
     __shared__ A sh[W][NA][32];
@@ -465,13 +478,15 @@ __global__ void __launch_bounds__(32 * W, 48 / W) k_tile(GridC g, GraphP gp, con
     if (tB < G.nt) ld_quad(v + (size_t)tB * kGroup, v1);
     pdl_wait();
     const typename Op::Pre pre = load_pre(op, G);
-    {
-        const float *src = op.gsrc() + (long long)y0 * g.nxp;
+    const int ts = kTileLayers * g.tl;  // floats per vector's tile
+#pragma unroll
+    for (int iv = 0; iv < tile_op<Op>::value; ++iv) {
+        const float *src = op.gsrc(iv) + (long long)y0 * g.nxp;
         for (int ls = 0; ls < kTileLayers; ++ls) {
             const int lay = __ldg(gp.tlay + G.z * kTileLayers + ls);
             if (lay < 0) break;  // the used tile layers come first
             const float *s = src + (long long)lay * g.lp;
-            float *d = tile + ls * g.tl;
+            float *d = tile + iv * ts + ls * g.tl;
             for (int j = threadIdx.x; j < tla; j += 32 * W) d[j] = s[j];
         }
     }
@@ -479,20 +494,20 @@ __global__ void __launch_bounds__(32 * W, 48 / W) k_tile(GridC g, GraphP gp, con
     if (tA < G.nt) {
         const int tt = __ldg(gp.ttile + G.t0 + tA);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_v(a, k, v0[k], tile[tt + rl[k]]);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v0[k], tile + tt + rl[k], ts);
     }
     if (tB < G.nt) {
         const int tt = __ldg(gp.ttile + G.t0 + tB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_v(a, k, v1[k], tile[tt + rl[k]]);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v1[k], tile + tt + rl[k], ts);
     }
-#pragma unroll kSweepUnroll
+#pragma unroll kTileUnroll
     for (int t = w + 2 * W; t < G.nt; t += W) {
         const int tt = __ldg(gp.ttile + G.t0 + t);
         float q[4];
         ld_quad(v + (size_t)t * kGroup, q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_v(a, k, q[k], tile[tt + rl[k]]);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, q[k], tile + tt + rl[k], ts);
     }
 #pragma unroll
     for (int m = 0; m < NA; ++m) sh[w][m][lane] = a[m];
@@ -546,9 +561,10 @@ static void run_plain(cudaStream_t st, const GridC &g, const GraphP &gp, const T
     cfg.attrs = at;
     cfg.numAttrs = 1;
 #if TK_TILE
-    if constexpr (sizeof(T) == 4 && tile_op<Op>::value) {
-        if (g.tl > 0) {
-            cfg.dynamicSmemBytes = (size_t)kTileLayers * g.tl * sizeof(float);
+    if constexpr (sizeof(T) == 4 && tile_op<Op>::value > 0) {
+        const size_t tb = (size_t)tile_op<Op>::value * kTileLayers * g.tl * sizeof(float);
+        if (g.tl > 0 && tb <= (size_t)kTileMaxBytes) {
+            cfg.dynamicSmemBytes = tb;
             cudaLaunchKernelEx(&cfg, k_tile<W, Op>, g, gp, val, op);
             return;
         }
