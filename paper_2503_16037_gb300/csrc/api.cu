@@ -30,6 +30,13 @@ struct DevBuf {
     size_t cap = 0;
 };
 
+// one geometry-dependent device buffer per slot
+enum VSlot {
+    VB_SUN_TAPS, VB_SUN_LF, VB_SUN_LD, VB_SUN_OFF, VB_SUN_N, VB_SUN_RT,
+    VB_LOS_TAPS, VB_LOS_LF, VB_LOS_LD, VB_LOS_OFF, VB_LOS_N,
+    VB_PIX_CX, VB_PIX_CY, VB_PIX_CLS, VB_RAD, VB_REFL, VB_COUNT
+};
+
 struct tursca_scene {
     tursca_grid_desc d{};
     cudaStream_t st = nullptr;
@@ -56,7 +63,7 @@ struct tursca_scene {
     double albedo = 0.0;
 
     AllocList allocs;       // graph-lifetime allocations
-    DevBuf vbuf[16];        // geometry-dependent buffers (sun and line-of-sight taps, pixels)
+    DevBuf vbuf[VB_COUNT];  // geometry-dependent buffers (sun and line-of-sight taps, pixels, images)
 
     // graph
     int *tstart = nullptr;
@@ -75,8 +82,11 @@ struct tursca_scene {
     int *cell_start = nullptr;
     int *canon_dirs = nullptr, *up_canon = nullptr;
     int *tflat = nullptr;  // template offsets in the haloed layout
+    tk::RTap *rtaps = nullptr, *sun_rt = nullptr;  // taps of long rays, pre-wrapped (graph, sun)
     int *ttile = nullptr, *tlay = nullptr;  // gather-tile offsets and layers of the row-group passes
     int tile_tl = 0;                        // floats per tile layer (0: no tiles)
+    int *ttileT = nullptr, *tlayT = nullptr;  // the same for the K^T passes of the adjoint
+    int tile_tlT = 0;
     tk::ASlot *aslot = nullptr;  // edge-kernel descriptors of the template entries
     int *tap_h = nullptr, *dir_h = nullptr;  // haloed offsets of the taps and the directions
     void *rt_h = nullptr, *wsp_h = nullptr, *mu_e_h = nullptr, *e1_h = nullptr;  // haloed copies
@@ -265,6 +275,7 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.lat_n = sc->lat_n;
     p.gtop_off = sc->gtop_off;
     p.gtop_n = sc->gtop_n;
+    p.rtaps = sc->rtaps;
     p.canon_dirs = sc->canon_dirs;
     p.up_canon = sc->up_canon;
     p.status = sc->status;
@@ -331,6 +342,7 @@ tk::ViewC view_c(const tursca_scene *sc) {
 tk::ViewP view_p(const tursca_scene *sc) {
     tk::ViewP p;
     p.sun_taps = sc->sun_taps;
+    p.sun_rt = sc->sun_rt;
     p.sun_len_f = sc->sun_lf;
     p.sun_len_d = sc->sun_ld;
     p.sun_off = sc->sun_off;
@@ -361,6 +373,21 @@ void split_taps(const std::vector<tg::Tap> &t, std::vector<tk::DTap> &off, std::
         lf[i] = (float)t[i].len;
         ld[i] = t[i].len;
     }
+}
+
+// taps of long rays as RTaps for an nx x ny grid (false: a column offset or
+// a layer offset does not fit)
+bool ray_taps(const std::vector<tg::Tap> &t, int nx, int ny, std::vector<tk::RTap> &out) {
+    if (nx > 0xffff || ny > 0x7fff) return false;
+    const long long nxy = (long long)nx * ny;
+    out.resize(t.size());
+    for (size_t i = 0; i < t.size(); ++i) {
+        const int dx = ((t[i].dx % nx) + nx) % nx, dy = ((t[i].dy % ny) + ny) % ny;
+        const long long zo = (long long)t[i].dz * nxy;
+        if (zo < -(1LL << 31) || zo >= (1LL << 31)) return false;
+        out[i] = tk::RTap{dx | (dy << 16), (int)zo};
+    }
+    return true;
 }
 
 std::string check_desc(const tursca_grid_desc *d) {
@@ -906,6 +933,16 @@ tursca_status ensure_adjoint(tursca_scene *sc) {
     CK(upload(sc, sc->allocs, sc->infoT, info.data(), std::max<size_t>(1, ne) * sizeof(int4)), "upload K^T");
     CK(upload(sc, sc->allocs, sc->flatT, Tt.flat_h.data(), std::max<size_t>(1, ne) * sizeof(int)), "upload K^T");
     CK(upload(sc, sc->allocs, sc->hgdirT, hg.data(), std::max<size_t>(1, ne) * sizeof(int)), "upload K^T");
+    {
+        tg::TileLayout tl;
+        sc->tile_tlT = 0;
+        if (ne && tg::tile_layout(G, Tt, g.H, tl).empty() &&
+            (size_t)tk::kTileLayers * tl.tl * sizeof(float) <= (size_t)tk::kTileMaxBytes) {
+            CK(upload(sc, sc->allocs, sc->ttileT, tl.ttile.data(), tl.ttile.size() * sizeof(int)), "upload K^T tiles");
+            CK(upload(sc, sc->allocs, sc->tlayT, tl.layers.data(), tl.layers.size() * sizeof(int)), "upload K^T tiles");
+            sc->tile_tlT = tl.tl;
+        }
+    }
     const size_t es = sc->es;
     CK(dalloc(sc->allocs, sc->valT, (size_t)G.nval * es), "alloc K^T");
     CK(dalloc(sc->allocs, sc->lam64, (size_t)g.npad * sizeof(double)), "alloc adjoint");
@@ -938,8 +975,8 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
     gpT.tstart = sc->tstartT;
     gpT.voff = sc->voffT;
     gpT.tflat = sc->flatT;
-    gpT.ttile = nullptr;  // the K^T passes gather from global memory
-    gpT.tlay = nullptr;
+    gpT.ttile = sc->ttileT;  // gather tiles of the K^T templates
+    gpT.tlay = sc->tlayT;
     tk::AdjP<T> ad;
     T **slot[10] = {&ad.Ebar, &ad.Ebar_h, &ad.e1bar, &ad.e1bar_h, &ad.xbar,
                     &ad.mubar, &ad.mubar_h, &ad.tsegbar, &ad.tinfbar, &ad.tinfgbar};
@@ -958,7 +995,7 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
     // (I - K)^T lambda = x-bar
     SolveIO<T> io;
     g.stage = 0;
-    g.tl = 0;
+    g.tl = sc->gather_tile ? sc->tile_tlT : 0;
     io.g = g;
     io.gp = gpT;
     io.val = (const T *)sc->valT;
@@ -1087,6 +1124,12 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     CK(upload(sc, sc->allocs, sc->taps, to.data(), to.size() * sizeof(tk::DTap)), "upload taps");
     CK(upload(sc, sc->allocs, sc->tlf, lf.data(), lf.size() * sizeof(float)), "upload taps");
     CK(upload(sc, sc->allocs, sc->tld, ld.data(), ld.size() * sizeof(double)), "upload taps");
+    {
+        std::vector<tk::RTap> rt;
+        if (!ray_taps(G.taps, sc->d.nx, sc->d.ny, rt)) return fail(sc, TURSCA_E_INVALID, "grid too large for ray tables");
+        CK(upload(sc, sc->allocs, sc->rtaps, rt.data(), std::max<size_t>(1, rt.size()) * sizeof(tk::RTap)), "upload taps");
+        CK(cudaStreamSynchronize(sc->st), "sync");  // rt dies here
+    }
     const int nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size();
     std::vector<int4> dirs(nd);
     for (int u = 0; u < nd; ++u) dirs[u] = make_int4(G.dirs[u][0], G.dirs[u][1], G.dirs[u][2], G.kmax[u]);
@@ -1289,24 +1332,30 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         std::vector<double> ld;
         DevBuf *vb = sc->vbuf;
         split_taps(VT.sun_taps, to, lf, ld);
-        CK(put(vb[0], sc->sun_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload sun");
-        CK(put(vb[1], sc->sun_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload sun");
-        CK(put(vb[2], sc->sun_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload sun");
-        CK(put(vb[3], sc->sun_off, VT.sun_off.data(), VT.sun_off.size() * sizeof(int), sc->st), "upload sun");
-        CK(put(vb[4], sc->sun_n, VT.sun_n.data(), VT.sun_n.size() * sizeof(int), sc->st), "upload sun");
+        CK(put(vb[VB_SUN_TAPS], sc->sun_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload sun");
+        CK(put(vb[VB_SUN_LF], sc->sun_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload sun");
+        CK(put(vb[VB_SUN_LD], sc->sun_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload sun");
+        CK(put(vb[VB_SUN_OFF], sc->sun_off, VT.sun_off.data(), VT.sun_off.size() * sizeof(int), sc->st), "upload sun");
+        CK(put(vb[VB_SUN_N], sc->sun_n, VT.sun_n.data(), VT.sun_n.size() * sizeof(int), sc->st), "upload sun");
+        {
+            std::vector<tk::RTap> rt;
+            if (!ray_taps(VT.sun_taps, sc->d.nx, sc->d.ny, rt)) return fail(sc, TURSCA_E_INVALID, "grid too large for ray tables");
+            CK(put(vb[VB_SUN_RT], sc->sun_rt, rt.data(), std::max<size_t>(1, rt.size()) * sizeof(tk::RTap), sc->st), "upload sun");
+            CK(cudaStreamSynchronize(sc->st), "sync");  // rt dies here
+        }
         // (pageable host memory: the copies are complete when put returns)
         split_taps(VT.los_taps, to, lf, ld);
-        CK(put(vb[5], sc->los_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload los");
-        CK(put(vb[6], sc->los_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload los");
-        CK(put(vb[7], sc->los_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload los");
-        CK(put(vb[8], sc->los_off, VT.los_off.data(), VT.los_off.size() * sizeof(int), sc->st), "upload los");
-        CK(put(vb[9], sc->los_n, VT.los_n.data(), VT.los_n.size() * sizeof(int), sc->st), "upload los");
-        CK(put(vb[10], sc->pix_cx, VT.pix_cx.data(), VT.pix_cx.size() * sizeof(int), sc->st), "upload pix");
-        CK(put(vb[11], sc->pix_cy, VT.pix_cy.data(), VT.pix_cy.size() * sizeof(int), sc->st), "upload pix");
-        CK(put(vb[12], sc->pix_cls, VT.pix_cls.data(), VT.pix_cls.size() * sizeof(int), sc->st), "upload pix");
+        CK(put(vb[VB_LOS_TAPS], sc->los_taps, to.data(), to.size() * sizeof(tk::DTap), sc->st), "upload los");
+        CK(put(vb[VB_LOS_LF], sc->los_lf, lf.data(), lf.size() * sizeof(float), sc->st), "upload los");
+        CK(put(vb[VB_LOS_LD], sc->los_ld, ld.data(), ld.size() * sizeof(double), sc->st), "upload los");
+        CK(put(vb[VB_LOS_OFF], sc->los_off, VT.los_off.data(), VT.los_off.size() * sizeof(int), sc->st), "upload los");
+        CK(put(vb[VB_LOS_N], sc->los_n, VT.los_n.data(), VT.los_n.size() * sizeof(int), sc->st), "upload los");
+        CK(put(vb[VB_PIX_CX], sc->pix_cx, VT.pix_cx.data(), VT.pix_cx.size() * sizeof(int), sc->st), "upload pix");
+        CK(put(vb[VB_PIX_CY], sc->pix_cy, VT.pix_cy.data(), VT.pix_cy.size() * sizeof(int), sc->st), "upload pix");
+        CK(put(vb[VB_PIX_CLS], sc->pix_cls, VT.pix_cls.data(), VT.pix_cls.size() * sizeof(int), sc->st), "upload pix");
         size_t np = (size_t)geom->npx * geom->npy;
-        CK(put(vb[13], sc->rad, nullptr, np * sc->es, sc->st), "alloc rad");
-        CK(put(vb[14], sc->refl, nullptr, np * sc->es, sc->st), "alloc refl");
+        CK(put(vb[VB_RAD], sc->rad, nullptr, np * sc->es, sc->st), "alloc rad");
+        CK(put(vb[VB_REFL], sc->refl, nullptr, np * sc->es, sc->st), "alloc refl");
         CK(cudaStreamSynchronize(sc->st), "sync");
         sc->view_ok = true;
     }

@@ -106,6 +106,30 @@ __device__ __forceinline__ T ray_sum(const GridC &g, const DTap *__restrict__ ta
     return acc;
 }
 
+// Optical depth of a long ray summed by a group of kRayLanes consecutive
+// lanes: lane s of the group adds the taps t = s (mod kRayLanes), then the
+// group combines its partial sums with a fixed butterfly (every lane gets
+// the same bits).  Every lane of the warp must call it.
+constexpr int kRayLanes = 4;
+template <typename T>
+__device__ __forceinline__ T ray_sum_lanes(const GridC &g, const RTap *__restrict__ taps, const T *__restrict__ len,
+                                           const T *__restrict__ mu_e, int off, int n, int bx, int by) {
+    const int s = threadIdx.x & (kRayLanes - 1);
+    T acc = T(0);
+#pragma unroll 2
+    for (int t = s; t < n; t += kRayLanes) {
+        const int2 r = __ldg(reinterpret_cast<const int2 *>(taps + off + t));
+        int x = bx + (r.x & 0xffff);
+        x -= x >= g.nx ? g.nx : 0;
+        int y = by + (r.x >> 16);
+        y -= y >= g.ny ? g.ny : 0;
+        acc += __ldg(len + off + t) * __ldg(mu_e + r.y + y * g.nx + x);
+    }
+#pragma unroll
+    for (int o = 1; o < kRayLanes; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ T hg(T g, T mu) {
     T d = T(1) + g * g - T(2) * g * mu;

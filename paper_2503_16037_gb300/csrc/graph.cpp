@@ -689,9 +689,14 @@ void transpose_templates(const Graph &G, int H, Transposed &T) {
     T.tstart[nz + 1] = (int)T.recv_layer.size();
 }
 
-std::string tile_layout(const Graph &G, int H, TileLayout &L) {
-    const int nx = G.nx, nz = G.nz, nxp = nx + 2 * H;
-    const long long nxy = (long long)nx * G.ny;
+namespace {
+// entry e of row layer z (tstart[z] <= e < tstart[z + 1]) gathers from layer
+// lay[e] at column offset (dx[e], dy[e])
+std::string tile_layout_of(int nx, int ny, int nz, int H, const std::vector<int> &tstart,
+                           const std::vector<int> &lay, const std::vector<int> &dx, const std::vector<int> &dy,
+                           TileLayout &L) {
+    const int nxp = nx + 2 * H;
+    const long long nxy = (long long)nx * ny;
     // rows spanned by a group of kGroup rows: at most ceil((kGroup - 1) / nx) + 1
     int span = 0;
     for (long long r0 = 0; r0 < nxy; r0 += kGroup) {
@@ -700,25 +705,49 @@ std::string tile_layout(const Graph &G, int H, TileLayout &L) {
     }
     L.tl = (span + 2 * H) * nxp;
     L.layers.assign((size_t)(nz + 1) * kTileLayers, -1);
-    L.ttile.assign(G.tmpl.size(), 0);
+    L.ttile.assign(lay.size(), 0);
     for (int z = 0; z <= nz; ++z) {
-        int *lay = &L.layers[(size_t)z * kTileLayers];
+        int *ls_of = &L.layers[(size_t)z * kTileLayers];
         int n = 0;
-        for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
-            const TSlot &t = G.tmpl[i];
-            const int szl = t.sz >= 0 ? t.sz : nz;
+        for (int e = tstart[z]; e < tstart[z + 1]; ++e) {
+            if (std::abs(dx[e]) > H || std::abs(dy[e]) > H) return "a gather offset lies beyond the halo";
             int ls = -1;
             for (int k = 0; k < n; ++k)
-                if (lay[k] == szl) ls = k;
+                if (ls_of[k] == lay[e]) ls = k;
             if (ls < 0) {
                 if (n == kTileLayers) return "a layer draws on more source layers than a tile holds";
                 ls = n;
-                lay[n++] = szl;
+                ls_of[n++] = lay[e];
             }
-            L.ttile[i] = ls * L.tl + t.sdy * nxp + t.sdx;
+            L.ttile[e] = ls * L.tl + dy[e] * nxp + dx[e];
         }
     }
     return std::string();
+}
+}  // namespace
+
+std::string tile_layout(const Graph &G, int H, TileLayout &L) {
+    const size_t n = G.tmpl.size();
+    std::vector<int> lay(n), dx(n), dy(n);
+    for (size_t i = 0; i < n; ++i) {
+        const TSlot &t = G.tmpl[i];
+        lay[i] = t.sz >= 0 ? t.sz : G.nz;
+        dx[i] = t.sdx;
+        dy[i] = t.sdy;
+    }
+    return tile_layout_of(G.nx, G.ny, G.nz, H, G.tmpl_start, lay, dx, dy, L);
+}
+
+std::string tile_layout(const Graph &G, const Transposed &T, int H, TileLayout &L) {
+    const size_t n = T.recv_layer.size();
+    std::vector<int> lay(n), dx(n), dy(n);
+    for (size_t e = 0; e < n; ++e) {
+        const TSlot &t = G.tmpl[T.tmpl_index[e]];
+        lay[e] = T.recv_layer[e];
+        dx[e] = -t.sdx;
+        dy[e] = -t.sdy;
+    }
+    return tile_layout_of(G.nx, G.ny, G.nz, H, T.tstart, lay, dx, dy, L);
 }
 
 }  // namespace tg

@@ -180,6 +180,9 @@ struct Transposed {
     int max_row = 0;
 };
 void transpose_templates(const Graph &G, int H, Transposed &T);
+// The gather tiles of the K^T passes: row layer zs gathers from the receiver
+// layers of its entries, at minus the template's column offset.
+std::string tile_layout(const Graph &G, const Transposed &T, int H, TileLayout &L);
 
 // Expand the templates into a CSR structure on the host.
 void expand_csr(const Graph &G, int32_t *row_ptr, int32_t *col, int16_t *dir, int8_t *k);

@@ -52,6 +52,15 @@ struct __align__(8) DTap {
     int16_t dx, dy, dz, pad;
 };
 
+// A tap of a long ray based at column (bx, by) of layer 0: the cell is
+// column (bx + (col & 0xffff), by + (col >> 16)) wrapped into the grid, in
+// the layer at node offset zoff (= dz nx ny).  Both column offsets are
+// stored already wrapped into [0, nx) x [0, ny), so one conditional
+// subtraction per axis finds the cell.
+struct __align__(8) RTap {
+    int col, zoff;
+};
+
 // Grid constants shared by most kernels.
 struct GridC {
     int nx, ny, nz, nxy, n_atm, n_ground, n_nodes;
@@ -100,6 +109,7 @@ struct GraphP {
     const int *top_off, *top_n;    // [nup * R]
     const int *lat_off, *lat_n;    // [nd]
     const int *gtop_off, *gtop_n;  // [ngd]
+    const RTap *rtaps;             // every tap of the graph as an RTap (read by the ground chains' rays)
     const int *canon_dirs;         // [nc] atmospheric index of each canonical direction
     const int *up_canon;           // [nup] canonical index of each upward direction
     int *status;                   // scene status word (STATUS_* bits; bounded waits set STATUS_TIMEOUT)
@@ -158,6 +168,7 @@ struct ViewC {
 
 struct ViewP {
     const DTap *sun_taps;
+    const RTap *sun_rt;          // the sun taps as RTaps
     const float *sun_len_f;
     const double *sun_len_d;
     const int *sun_off, *sun_n;  // [nz + 1]

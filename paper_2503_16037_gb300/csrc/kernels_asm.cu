@@ -161,8 +161,11 @@ __global__ void k_tables_norm(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
 
 template <typename T>
 __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n_nodes) return;
+    // kRayLanes lanes per node; lanes past the last node work on the last
+    // node and write nothing (they take part in the group's shuffles)
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool own = gt / kRayLanes < g.n_nodes && (threadIdx.x & (kRayLanes - 1)) == 0;
+    const int i = min(gt / kRayLanes, g.n_nodes - 1);
     int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
     int Zs = i < g.n_atm ? z + 1 : 0;
     const T *len;
@@ -170,7 +173,8 @@ __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
         len = (const T *)vp.sun_len_f;
     else
         len = (const T *)vp.sun_len_d;
-    T tau = ray_sum<T>(g, vp.sun_taps, len, f.mu_e, vp.sun_off[Zs], vp.sun_n[Zs], x, y, 0);
+    T tau = ray_sum_lanes<T>(g, vp.sun_rt, len, f.mu_e, __ldg(vp.sun_off + Zs), __ldg(vp.sun_n + Zs), x, y);
+    if (!own) return;
     T Ts = dexp<T>(-tau);
     f.tsun[i] = Ts;
     T base = (T)(vc.f0 * vc.mu0 * g.hx * g.hy);
@@ -190,19 +194,33 @@ __global__ void k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
 // ---------------------------------------------------------------------------
 // Optical depth of the lattice segment from every voxel centre a to a + u, for
 // each canonical direction u (one of each pair {u, -u}); a segment traversed
-// backwards (-u, from a + u) reads the same entry.  One thread per (u, a);
-// entries whose end lies above the TOA are not used and are set to 0.
+// backwards (-u, from a + u) reads the same entry.  One thread per voxel a
+// walks kSegChunk directions (blockIdx.y: the chunk), so its coordinates and
+// halo copies are worked out once per chunk; entries whose end lies above the
+// TOA are not used and are set to 0.
+constexpr int kSegChunk = 7;
 
 template <typename T>
 __global__ void k_segtau(GridC g, GraphP gp, FieldP<T> f) {
-    const int c = blockIdx.y, a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= g.n_atm) return;
-    int u = gp.canon_dirs[c];
-    int4 d = gp.dirs[u];
-    int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
-    T tau = T(0);
-    if (z + d.z < g.nz) tau = tap_sum_h<T>(gp, f.mu_e_h, gp.lat_off[u], gp.lat_n[u], (int)halo_pos(g, x, y, z));
-    store_halo(f.tseg + (size_t)c * g.npad, g, x, y, z, tau);
+    const int z = a / g.nxy, r = a - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    const int p = (int)halo_pos(g, x, y, z);
+    const int ax = x < g.H ? g.nx : (x >= g.nx - g.H ? -g.nx : 0);
+    const int ay = y < g.H ? g.ny * g.nxp : (y >= g.ny - g.H ? -g.ny * g.nxp : 0);
+    const int c1 = min((int)(blockIdx.y + 1) * kSegChunk, g.nc);
+    for (int c = blockIdx.y * kSegChunk; c < c1; ++c) {
+        const int u = __ldg(gp.canon_dirs + c);
+        T tau = T(0);
+        if (z + __ldg(&gp.dirs[u].z) < g.nz) tau = tap_sum_h<T>(gp, f.mu_e_h, __ldg(gp.lat_off + u), __ldg(gp.lat_n + u), p);
+        T *o = f.tseg + (size_t)c * g.npad + p;
+        o[0] = tau;
+        if (ax) o[ax] = tau;
+        if (ay) {
+            o[ay] = tau;
+            if (ax) o[ax + ay] = tau;
+        }
+    }
 }
 
 
@@ -234,15 +252,17 @@ __global__ void k_tinf(GridC g, GraphP gp, FieldP<T> f) {
 }
 
 // ground chains: optical depth from the terminal member to the TOA
+// (kRayLanes lanes per ray, as in k_sun)
 template <typename T>
 __global__ void k_tinfg(GridC g, GraphP gp, FieldP<T> f) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= g.ngd * g.nxy) return;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool own = gt / kRayLanes < g.ngd * g.nxy && (threadIdx.x & (kRayLanes - 1)) == 0;
+    const int t = min(gt / kRayLanes, g.ngd * g.nxy - 1);
     int gd = t / g.nxy, c = t - gd * g.nxy;
     int y = c / g.nx, x = c - y * g.nx;
+    const T tau = ray_sum_lanes<T>(g, gp.rtaps, tap_len<T>(gp), f.mu_e, __ldg(gp.gtop_off + gd), __ldg(gp.gtop_n + gd), x, y);
     // haloed plane of ground direction gd: layer index 0 of a (1 x lp) array
-    store_halo(f.tinfg + (size_t)gd * g.lp, g, x, y, 0,
-               ray_sum<T>(g, gp.taps, tap_len<T>(gp), f.mu_e, gp.gtop_off[gd], gp.gtop_n[gd], x, y, 0));
+    if (own) store_halo(f.tinfg + (size_t)gd * g.lp, g, x, y, 0, tau);
 }
 
 // ---------------------------------------------------------------------------
@@ -479,12 +499,12 @@ void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], cons
     k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st[0]>>>(g, f);
     cudaEventRecord(ev[1], st[0]);  // fields ready
     cudaStreamWaitEvent(st[2], ev[1], 0);
-    k_segtau<T><<<dim3((g.n_atm + th - 1) / th, g.nc), th, 0, st[2]>>>(g, gp, f);
+    k_segtau<T><<<dim3((g.n_atm + th - 1) / th, (g.nc + kSegChunk - 1) / kSegChunk), th, 0, st[2]>>>(g, gp, f);
     k_tinf<T><<<dim3((g.R * g.nxy + th - 1) / th, g.nup), th, 0, st[2]>>>(g, gp, f);
     cudaEventRecord(ev[3], st[2]);
     cudaStreamWaitEvent(st[3], ev[1], 0);
-    k_tinfg<T><<<(g.ngd * g.nxy + 127) / 128, 128, 0, st[3]>>>(g, gp, f);
-    k_sun<T><<<(g.n_nodes + 127) / 128, 128, 0, st[3]>>>(g, f, vc, vp);
+    k_tinfg<T><<<((long long)g.ngd * g.nxy * kRayLanes + 127) / 128, 128, 0, st[3]>>>(g, gp, f);
+    k_sun<T><<<((long long)g.n_nodes * kRayLanes + 127) / 128, 128, 0, st[3]>>>(g, f, vc, vp);
     cudaEventRecord(ev[4], st[3]);
     cudaStreamWaitEvent(st[0], ev[2], 0);
     k_znorm<T><<<(g.n_nodes + 127) / 128, 128, 0, st[0]>>>(g, gp, f, vc);

@@ -298,3 +298,21 @@ def test_cloud_full_size_configuration():
     assert err.max() < 1e-4
     assert rel_err(refl, r["refl"]).max() < 1e-4
 
+
+
+@pytest.mark.parametrize("precision", [T.FP32_REFINE, T.FP64])
+def test_repeated_runs_on_one_runner_identical(precision):
+    """A Runner re-assembles, re-solves and re-renders with its geometry
+    buffers kept from the first run: every run must give the same bits."""
+    sc = SMALL["plume_small"]()
+    rn = T.Runner(sc, precision)
+    mu_a, mu_s = rn.fields("cuda")
+    rads = []
+    for _ in range(3):
+        rad, refl = rn.run(mu_a, mu_s, rtol=1e-10 if precision == T.FP32_REFINE else 1e-13)
+        torch.cuda.synchronize()
+        rads.append((rad.cpu().numpy().copy(), refl.cpu().numpy().copy()))
+    rn.close()
+    for r in rads[1:]:
+        assert np.array_equal(r[0], rads[0][0])
+        assert np.array_equal(r[1], rads[0][1])
