@@ -342,10 +342,15 @@ __global__ void k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
 // Every lookup is one add from the receiver's haloed position (the slot's
 // ASlot descriptor holds the offsets), so a warp's loads of one slot cover
 // contiguous lines.
-constexpr int kAsmW = 4;
+// warps per group and the register budget (blocks per SM): measured best on
+// GB300 at 8 warps and 4 blocks (64 registers)
+#ifndef TK_ASM_W
+#define TK_ASM_W 8
+#endif
+constexpr int kAsmW = TK_ASM_W;
 
 #ifndef TK_ASM_MINB
-#define TK_ASM_MINB 8
+#define TK_ASM_MINB 4
 #endif
 template <typename T, int S>
 __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
