@@ -726,9 +726,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     const double floor32 = 3e-7;  // relative accuracy the FP32 inner iterations can reach
     while (rel > rtol && ss.iters < max_iter) {
         const int budget = max_iter - ss.iters;
-        T *bb = (T *)sc->b;
-        tk::launch_convert<double, T>(sc->st, n, sc->r64, bb);
-        sc->launches++;
+        T *bb = (T *)sc->b;  // r in the compute type (written below, with the first pass of each solver)
         // reduction asked of this refinement: all that is left if one
         // refinement can reach it, else an equal share over the fewest
         // refinements the FP32 floor allows
@@ -753,17 +751,23 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             else if (rho + widen >= 0.85 || use_gmres)
                 kind = TURSCA_SOLVER_GMRES;
         }
+        if (power || kind != TURSCA_SOLVER_CHEBYSHEV) {
+            tk::launch_convert<double, T>(sc->st, n, sc->r64, bb);
+            sc->launches++;
+        }
         if (power) {
             // Neumann sweeps d <- r + K d from d = r; the norms of successive
             // differences (K^k r) give the power estimate of the largest eigenvalue
             const int n1 = std::max(2, std::min(6, budget - 1));
-            T *cur = (T *)sc->d0, *nxt = (T *)sc->d1;
-            CK(cudaMemcpyAsync(cur, bb, (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, sc->st), "copy");
+            // the first sweep reads d = r from bb itself; the later ones
+            // alternate between d0 and d1, so bb is never overwritten
+            T *cur = bb, *nxt = (T *)sc->d0;
             for (int it = 0; it < n1; ++it) {
                 int pi = prof_begin(sc, P_SPMV);
                 tk::launch_sweep_pow<T>(sc->st, g, gp, val, cur, bb, nxt, sc->part + (it & 1) * nsw);
                 prof_end(sc, pi);
-                std::swap(cur, nxt);
+                cur = nxt;
+                nxt = cur == (T *)sc->d0 ? (T *)sc->d1 : (T *)sc->d0;
             }
             tk::launch_finalize2(sc->st, sc->part, nsw, sc->dred + 2);
             sc->launches += n1 + 1;
@@ -782,8 +786,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             nc = std::max(1, std::min(nc, budget - 1));
             predicted = 2.0 * std::pow(eff, nc);
             T *r = bb, *d = (T *)sc->w, *p0 = (T *)sc->d0, *p1 = (T *)sc->d1;
-            CK(cudaMemsetAsync(d, 0, (size_t)n * sizeof(T), sc->st), "memset");
-            tk::launch_scale<T>(sc->st, n, r, 1.0 / cp.theta, p0);
+            tk::launch_cheb_start<T>(sc->st, n, sc->r64, 1.0 / cp.theta, r, d, p0);
             sc->launches++;
             double rk = 1.0 / cp.sigma;
             for (int k = 0; k < nc; ++k) {

@@ -314,6 +314,9 @@ template <typename T>
 void launch_axpy_to64(cudaStream_t st, int n, const T *d, double *x);  // x += d
 template <typename T>
 void launch_scale(cudaStream_t st, int n, const T *a, double alpha, T *b);  // b = alpha a
+// start of a Chebyshev refinement in one pass: b = (T) r64, d = 0, p = alpha b
+template <typename T>
+void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, T *b, T *d, T *p);
 template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h);  // w -= V h
 template <typename T>

@@ -513,6 +513,16 @@ __global__ void k_scale(int n, const T *__restrict__ a, double alpha, T *__restr
     if (i < n) b[i] = (T)(alpha * (double)a[i]);
 }
 template <typename T>
+__global__ void k_cheb_start(int n, const double *__restrict__ r64, double alpha, T *__restrict__ b,
+                             T *__restrict__ d, T *__restrict__ p) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const T v = (T)r64[i];
+    b[i] = v;
+    d[i] = T(0);
+    p[i] = (T)(alpha * (double)v);
+}
+template <typename T>
 __global__ void k_gupdate(int n, T *__restrict__ w, const T *__restrict__ V, size_t ldv, int k,
                           const double *__restrict__ h, double sign) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -533,6 +543,10 @@ void launch_axpy_to64(cudaStream_t st, int n, const T *d, double *x) {
 template <typename T>
 void launch_scale(cudaStream_t st, int n, const T *a, double alpha, T *b) {
     k_scale<T><<<(n + 255) / 256, 256, 0, st>>>(n, a, alpha, b);
+}
+template <typename T>
+void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, T *b, T *d, T *p) {
+    k_cheb_start<T><<<(n + 255) / 256, 256, 0, st>>>(n, r64, alpha, b, d, p);
 }
 template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h) {
@@ -566,6 +580,7 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
     template void launch_from_halo<T>(cudaStream_t, const GridC &, const T *, T *);                                 \
     template void launch_axpy_to64<T>(cudaStream_t, int, const T *, double *);                                      \
     template void launch_scale<T>(cudaStream_t, int, const T *, double, T *);                                       \
+    template void launch_cheb_start<T>(cudaStream_t, int, const double *, double, T *, T *, T *);                  \
     template void launch_gmres_update<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);           \
     template void launch_combine<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);            \
     template void launch_axpby<T>(cudaStream_t, int, double, const T *, double, const T *, T *);                   \
