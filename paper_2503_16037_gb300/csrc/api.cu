@@ -739,6 +739,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             target = 0.3 * std::max(std::pow(need, 1.0 / m), 10.0 * floor32);
         }
         const T *dd = nullptr;
+        bool x_done = false;  // x += dd already applied by the last pass of the inner solve
         int kind = solver;
         bool power = false;
         double predicted = 1.0;
@@ -764,7 +765,11 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             T *cur = bb, *nxt = (T *)sc->d0;
             for (int it = 0; it < n1; ++it) {
                 int pi = prof_begin(sc, P_SPMV);
-                tk::launch_sweep_pow<T>(sc->st, g, gp, val, cur, bb, nxt, sc->part + (it & 1) * nsw);
+                // the last sweep also applies x += d (its output) row by row
+                const bool last = it == n1 - 1;
+                tk::launch_sweep_pow<T>(sc->st, g, gp, val, cur, bb, nxt, sc->part + (it & 1) * nsw,
+                                        last ? io.x : nullptr, last && ds ? sc->xh : nullptr,
+                                        last && ds ? sc->xl : nullptr);
                 prof_end(sc, pi);
                 cur = nxt;
                 nxt = cur == (T *)sc->d0 ? (T *)sc->d1 : (T *)sc->d0;
@@ -773,6 +778,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             sc->launches += n1 + 1;
             ss.iters += n1;
             dd = cur;
+            x_done = true;
             ss.solver = TURSCA_SOLVER_NEUMANN;
             // columns: last sweep (n1 - 1) & 1, the one before (n1 - 2) & 1
             inner_n = n1;
@@ -792,7 +798,10 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             for (int k = 0; k < nc; ++k) {
                 double rk1 = 1.0 / (2.0 * cp.sigma - rk);
                 int pi = prof_begin(sc, P_CHEB);
-                tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta);
+                // the last step also applies x += d row by row
+                const bool last = k == nc - 1;
+                tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta,
+                                   last ? io.x : nullptr, last && ds ? sc->xh : nullptr, last && ds ? sc->xl : nullptr);
                 prof_end(sc, pi);
                 std::swap(p0, p1);
                 rk = rk1;
@@ -800,6 +809,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             sc->launches += nc;
             ss.iters += nc;
             dd = d;
+            x_done = true;
             ss.solver = TURSCA_SOLVER_CHEBYSHEV;
         } else if (kind == TURSCA_SOLVER_GMRES) {
             tursca_status e = ensure_basis();
@@ -820,7 +830,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             inner_n = nn;
             ss.solver = TURSCA_SOLVER_NEUMANN;
         }
-        tk::launch_update_x<T>(sc->st, n, dd, io.x, ds ? sc->xh : nullptr, ds ? sc->xl : nullptr);
+        if (!x_done) tk::launch_update_x<T>(sc->st, n, dd, io.x, ds ? sc->xh : nullptr, ds ? sc->xl : nullptr);
         int pr = prof_begin(sc, P_RESID);
         if (ds)
             tk::launch_resid_ds(sc->st, g, gp, (const float *)val, (const float *)io.s, io.x, sc->xh, sc->xl,

@@ -324,12 +324,14 @@ void launch_combine(cudaStream_t st, int n, T *x, const T *V, size_t ldv, int k,
 // Neumann sweep y = b + K x that also writes per-block sums of (y - x)^2 to part[sweep_blocks]
 template <typename T>
 void launch_sweep_pow(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y,
-                      double *part);
+                      double *part, double *x64 = nullptr, float *xh = nullptr, float *xl = nullptr);
 int sweep_blocks(const GridC &g);
-// Chebyshev step: q = K p; r <- r - p + q; d <- d + p; pn = c1 p + c2 r
+// Chebyshev step: q = K p; r <- r - p + q; d <- d + p; pn = c1 p + c2 r.
+// With x64 set (the last step of a refinement) the step also applies
+// x64 += d row by row, with the FP32-pair split into xh, xl when those are set.
 template <typename T>
 void launch_cheb(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *p, T *r, T *d, T *pn,
-                 double c1, double c2);
+                 double c1, double c2, double *x64 = nullptr, float *xh = nullptr, float *xl = nullptr);
 template <typename T>
 void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const T *y, T *out);  // out = a x + b y
 template <typename T>

@@ -34,6 +34,25 @@ namespace tk {
 // combine_row: the words of row k summed over the W warps in a fixed order;
 // finish_row: the row update, returning the row's share of the partial sum.
 
+// The refinement update x += d (with the FP32-pair split of x when xh is
+// set), done row by row in the epilogue of the pass that produces d
+// (x == nullptr: none); the same arithmetic as k_update_x.
+struct XUpd {
+    double *x = nullptr;
+    float *xh = nullptr, *xl = nullptr;
+    template <typename T>
+    __device__ __forceinline__ void apply(const GroupRows &G, int k, T d) const {
+        if (x == nullptr) return;
+        const double v = x[G.rp[k]] + (double)d;
+        store_h(x, G, k, v);
+        if (xh) {
+            const float h = (float)v;
+            store_h(xh, G, k, h);
+            store_h(xl, G, k, (float)(v - (double)h));
+        }
+    }
+};
+
 // MODE 0: y = b + K x (b may be null); MODE 1: y = x - K x
 template <typename T, int MODE>
 struct OpSpmv {
@@ -108,6 +127,7 @@ struct OpSweepPow {
     const T *x, *b;
     T *y;
     double *part;
+    XUpd xu;
     static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
     __device__ __forceinline__ const T *gsrc(int) const { return x; }
     __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
@@ -127,6 +147,7 @@ struct OpSweepPow {
         const T vv = p.b + a[k];
         const T dd = vv - p.x;
         store_h(y, G, k, vv);
+        xu.apply(G, k, vv);
         return (double)(dd * dd);
     }
 };
@@ -144,6 +165,7 @@ struct OpCheb {
     const T *p;
     T *r, *d, *pn;
     T c1, c2;
+    XUpd xu;
     static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
     __device__ __forceinline__ const T *gsrc(int) const { return p; }
     __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
@@ -164,7 +186,9 @@ struct OpCheb {
     __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &q) const {
         const T rr = q.r - q.p + a[k];
         store_h(r, G, k, rr);
-        store_h(d, G, k, q.d + q.p);
+        const T dn = q.d + q.p;
+        store_h(d, G, k, dn);
+        xu.apply(G, k, dn);
         store_h(pn, G, k, c1 * q.p + c2 * rr);
         return 0.0;
     }
@@ -321,19 +345,25 @@ void launch_imk(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val,
 
 template <typename T>
 void launch_sweep_pow(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *x, const T *b, T *y,
-                      double *part) {
+                      double *part, double *x64, float *xh, float *xl) {
     OpSweepPow<T> op;
     op.x = x;
     op.b = b;
     op.y = y;
     op.part = part;
+    op.xu.x = x64;
+    op.xu.xh = xh;
+    op.xu.xl = xl;
     run_op(st, g, gp, val, op, 0);
 }
 
 template <typename T>
 void launch_cheb(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val, const T *p, T *r, T *d, T *pn,
-                 double c1, double c2) {
+                 double c1, double c2, double *x64, float *xh, float *xl) {
     OpCheb<T> op;
+    op.xu.x = x64;
+    op.xu.xh = xh;
+    op.xu.xl = xl;
     op.p = p;
     op.r = r;
     op.d = d;
@@ -586,9 +616,9 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
     template void launch_axpby<T>(cudaStream_t, int, double, const T *, double, const T *, T *);                   \
     template void launch_update_x<T>(cudaStream_t, int, const T *, double *, float *, float *);                   \
     template void launch_sweep_pow<T>(cudaStream_t, const GridC &, const GraphP &, const T *, const T *,          \
-                                      const T *, T *, double *);                                                \
+                                      const T *, T *, double *, double *, float *, float *);                    \
     template void launch_cheb<T>(cudaStream_t, const GridC &, const GraphP &, const T *, const T *, T *, T *,     \
-                                 T *, double, double);
+                                 T *, double, double, double *, float *, float *);
 INST(float)
 INST(double)
 #undef INST
