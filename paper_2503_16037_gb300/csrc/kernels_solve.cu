@@ -467,9 +467,69 @@ int dot_blocks(const GridC &g) {
     return (int)b;
 }
 
+// The same dot products for FP32 vectors without FP64 arithmetic in the
+// pass (FP64 runs at a small fraction of the FP32 rate on this GPU): each
+// product and each thread's running sum is kept in FP32-pair arithmetic
+// (ds_add_prod, about 48 significant bits), kDotCols columns per pass over
+// y; the pairs enter the FP64 block and grid sums only at the end.
+constexpr int kDotCols = 8;
+constexpr int kDotBlocksPerSM = 4;
+__global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restrict__ V, size_t ldv, int ncol,
+                                                 const float *__restrict__ y, double *__restrict__ part) {
+    __shared__ double red[kDotCols][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int gw = blockIdx.x * 8 + wid, nw = gridDim.x * 8;
+    const int nlines = (g.nz + 1) * g.ny;
+    for (int c0 = 0; c0 < ncol; c0 += kDotCols) {
+        float hi[kDotCols], lo[kDotCols];
+#pragma unroll
+        for (int c = 0; c < kDotCols; ++c) hi[c] = lo[c] = 0.f;
+        for (int l = gw; l < nlines; l += nw) {
+            const int z = l / g.ny, yy = l - z * g.ny;
+            const long long base = halo_pos(g, 0, yy, z);
+            for (int x = lane; x < g.nx; x += 32) {
+                const float yv = y[base + x];
+#pragma unroll
+                for (int c = 0; c < kDotCols; ++c)
+                    if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + base + x], yv, 0.f);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kDotCols; ++c) {
+            double v = (double)hi[c] + (double)lo[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[c][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kDotCols && c0 + (int)threadIdx.x < ncol) {
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) t += red[threadIdx.x][q];
+            part[(size_t)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+int dot_blocks_ds() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        n = std::max(1, sms) * kDotBlocksPerSM;
+    }
+    return n;
+}
+
 template <typename A, typename B>
 void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int ncol, const B *y, double *part,
                  int nblk, double *out) {
+    if constexpr (sizeof(A) == 4 && sizeof(B) == 4) {
+        const int nb = std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
+        k_dots_ds<<<nb, 256, 0, st>>>(g, (const float *)V, ldv, ncol, (const float *)y, part);
+        k_finalize<<<ncol, 256, 0, st>>>(part, nb, ncol, out);
+        return;
+    }
     k_dots<A, B><<<nblk, 256, 0, st>>>(g, V, ldv, ncol, y, part);
     k_finalize<<<ncol, 256, 0, st>>>(part, nblk, ncol, out);
 }
@@ -562,6 +622,27 @@ __global__ void k_gupdate(int n, T *__restrict__ w, const T *__restrict__ V, siz
     w[i] = (T)acc;
 }
 
+// w += sign sum_j h_j V_j for FP32 vectors in FP32-pair arithmetic: the
+// coefficients are split once per block into (high, low) FP32 pairs, and
+// each element's sum is carried as a pair and rounded to FP32 at the end
+constexpr int kGupdateMaxK = 64;
+__global__ void __launch_bounds__(256) k_gupdate_ds(int n, float *__restrict__ w, const float *__restrict__ V,
+                                                    size_t ldv, int k, const double *__restrict__ h, double sign) {
+    __shared__ float hh[kGupdateMaxK], hl[kGupdateMaxK];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double c = sign * h[j];
+        const float a = (float)c;
+        hh[j] = a;
+        hl[j] = (float)(c - (double)a);
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float hi = w[i], lo = 0.f;
+    for (int j = 0; j < k; ++j) ds_add_prod(hi, lo, V[(size_t)j * ldv + i], hh[j], hl[j]);
+    w[i] = __fadd_rn(hi, lo);
+}
+
 template <typename T, typename U>
 void launch_convert(cudaStream_t st, int n, const T *a, U *b) {
     k_convert<T, U><<<(n + 255) / 256, 256, 0, st>>>(n, a, b);
@@ -580,10 +661,18 @@ void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, 
 }
 template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h) {
+    if constexpr (sizeof(T) == 4) {
+        k_gupdate_ds<<<(n + 255) / 256, 256, 0, st>>>(n, (float *)w, (const float *)V, ldv, k, h, -1.0);
+        return;
+    }
     k_gupdate<T><<<(n + 255) / 256, 256, 0, st>>>(n, w, V, ldv, k, h, -1.0);
 }
 template <typename T>
 void launch_combine(cudaStream_t st, int n, T *x, const T *V, size_t ldv, int k, const double *y) {
+    if constexpr (sizeof(T) == 4) {
+        k_gupdate_ds<<<(n + 255) / 256, 256, 0, st>>>(n, (float *)x, (const float *)V, ldv, k, y, 1.0);
+        return;
+    }
     k_gupdate<T><<<(n + 255) / 256, 256, 0, st>>>(n, x, V, ldv, k, y, 1.0);
 }
 
