@@ -473,7 +473,15 @@ int dot_blocks(const GridC &g) {
 // (ds_add_prod, about 48 significant bits), kDotCols columns per pass over
 // y; the pairs enter the FP64 block and grid sums only at the end.
 constexpr int kDotCols = 8;
-constexpr int kDotBlocksPerSM = 4;
+constexpr int kDotBlocksPerSM = 2;
+// (hi, lo) += (h2, l2) for FP32 pairs, with Knuth's two-sum on the high parts
+__device__ __forceinline__ void ds_add_pair(float &hi, float &lo, float h2, float l2) {
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, l2));
+}
 __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restrict__ V, size_t ldv, int ncol,
                                                  const float *__restrict__ y, double *__restrict__ part) {
     __shared__ double red[kDotCols][8];
@@ -487,6 +495,7 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
         for (int l = gw; l < nlines; l += nw) {
             const int z = l / g.ny, yy = l - z * g.ny;
             const long long base = halo_pos(g, 0, yy, z);
+#pragma unroll 4
             for (int x = lane; x < g.nx; x += 32) {
                 const float yv = y[base + x];
 #pragma unroll
@@ -494,11 +503,13 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
                     if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + base + x], yv, 0.f);
             }
         }
+        // warp sums in FP32-pair arithmetic; FP64 only for the warps' results
 #pragma unroll
         for (int c = 0; c < kDotCols; ++c) {
-            double v = (double)hi[c] + (double)lo[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[c][wid] = v;
+            float h = hi[c], q = lo[c];
+            for (int o = 16; o > 0; o >>= 1)
+                ds_add_pair(h, q, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, q, o));
+            if (lane == 0) red[c][wid] = (double)h + (double)q;
         }
         __syncthreads();
         if (threadIdx.x < kDotCols && c0 + (int)threadIdx.x < ncol) {
@@ -639,6 +650,7 @@ __global__ void __launch_bounds__(256) k_gupdate_ds(int n, float *__restrict__ w
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float hi = w[i], lo = 0.f;
+#pragma unroll 4
     for (int j = 0; j < k; ++j) ds_add_prod(hi, lo, V[(size_t)j * ldv + i], hh[j], hl[j]);
     w[i] = __fadd_rn(hi, lo);
 }
