@@ -550,9 +550,8 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred + 64);
-            tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred + 64);
-            tk::launch_sumsq<T>(sc->st, g, w, sc->part, nb, sc->dred + 128);
-            sc->launches += 10;
+            tk::launch_gmres_update_norm<T>(sc->st, g, n, w, V, ld, k + 1, sc->dred + 64, sc->part, nb, sc->dred + 128);
+            sc->launches += 9;
             ss.iters++;
             total++;
             CK(cudaMemcpyAsync(sc->hred, sc->dred, 129 * sizeof(double), cudaMemcpyDeviceToHost, sc->st), "d2h");

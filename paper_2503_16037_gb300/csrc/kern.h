@@ -319,6 +319,11 @@ template <typename T>
 void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, T *b, T *d, T *p);
 template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h);  // w -= V h
+// w -= V h, then the interior sum of w^2 into *out (part: scratch of at least
+// max(nblk, n / 256 + 1) doubles)
+template <typename T>
+void launch_gmres_update_norm(cudaStream_t st, const GridC &g, int n, T *w, const T *V, size_t ldv, int k,
+                              const double *h, double *part, int nblk, double *out);
 template <typename T>
 void launch_combine(cudaStream_t st, int n, T *x, const T *V, size_t ldv, int k, const double *y);  // x += V y
 // Neumann sweep y = b + K x that also writes per-block sums of (y - x)^2 to part[sweep_blocks]

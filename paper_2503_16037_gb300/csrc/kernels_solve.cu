@@ -473,7 +473,13 @@ int dot_blocks(const GridC &g) {
 // (ds_add_prod, about 48 significant bits), kDotCols columns per pass over
 // y; the pairs enter the FP64 block and grid sums only at the end.
 constexpr int kDotCols = 8;
-constexpr int kDotBlocksPerSM = 2;
+#ifndef TK_DOTS_FLAT
+#define TK_DOTS_FLAT 0
+#endif
+#ifndef TK_DOTS_BPS
+#define TK_DOTS_BPS 2
+#endif
+constexpr int kDotBlocksPerSM = TK_DOTS_BPS;
 // (hi, lo) += (h2, l2) for FP32 pairs, with Knuth's two-sum on the high parts
 __device__ __forceinline__ void ds_add_pair(float &hi, float &lo, float h2, float l2) {
     const float s = __fadd_rn(hi, h2);
@@ -492,6 +498,22 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
         float hi[kDotCols], lo[kDotCols];
 #pragma unroll
         for (int c = 0; c < kDotCols; ++c) hi[c] = lo[c] = 0.f;
+#if TK_DOTS_FLAT
+        // interior elements flattened over the grid's threads
+        const int ne = nlines * g.nx;
+#pragma unroll 2
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+            const int l = e / g.nx, x = e - l * g.nx;
+            const int z = l / g.ny, yy = l - z * g.ny;
+            const long long p = halo_pos(g, x, yy, z);
+            const float yv = y[p];
+#pragma unroll
+            for (int c = 0; c < kDotCols; ++c)
+                if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + p], yv, 0.f);
+        }
+        (void)gw;
+        (void)nw;
+#else
         for (int l = gw; l < nlines; l += nw) {
             const int z = l / g.ny, yy = l - z * g.ny;
             const long long base = halo_pos(g, 0, yy, z);
@@ -503,6 +525,7 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
                     if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + base + x], yv, 0.f);
             }
         }
+#endif
         // warp sums in FP32-pair arithmetic; FP64 only for the warps' results
 #pragma unroll
         for (int c = 0; c < kDotCols; ++c) {
@@ -536,7 +559,7 @@ template <typename A, typename B>
 void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int ncol, const B *y, double *part,
                  int nblk, double *out) {
     if constexpr (sizeof(A) == 4 && sizeof(B) == 4) {
-        const int nb = std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
+        const int nb = TK_DOTS_FLAT ? dot_blocks_ds() : std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
         k_dots_ds<<<nb, 256, 0, st>>>(g, (const float *)V, ldv, ncol, (const float *)y, part);
         k_finalize<<<ncol, 256, 0, st>>>(part, nb, ncol, out);
         return;
@@ -637,9 +660,12 @@ __global__ void k_gupdate(int n, T *__restrict__ w, const T *__restrict__ V, siz
 // coefficients are split once per block into (high, low) FP32 pairs, and
 // each element's sum is carried as a pair and rounded to FP32 at the end
 constexpr int kGupdateMaxK = 64;
-__global__ void __launch_bounds__(256) k_gupdate_ds(int n, float *__restrict__ w, const float *__restrict__ V,
-                                                    size_t ldv, int k, const double *__restrict__ h, double sign) {
+template <bool kNorm>
+__global__ void __launch_bounds__(256) k_gupdate_ds(GridC g, int n, float *__restrict__ w, const float *__restrict__ V,
+                                                    size_t ldv, int k, const double *__restrict__ h, double sign,
+                                                    double *__restrict__ part) {
     __shared__ float hh[kGupdateMaxK], hl[kGupdateMaxK];
+    __shared__ double red[8];
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         const double c = sign * h[j];
         const float a = (float)c;
@@ -648,11 +674,32 @@ __global__ void __launch_bounds__(256) k_gupdate_ds(int n, float *__restrict__ w
     }
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float hi = w[i], lo = 0.f;
+    float r = 0.f;
+    if (i < n) {
+        float hi = w[i], lo = 0.f;
 #pragma unroll 4
-    for (int j = 0; j < k; ++j) ds_add_prod(hi, lo, V[(size_t)j * ldv + i], hh[j], hl[j]);
-    w[i] = __fadd_rn(hi, lo);
+        for (int j = 0; j < k; ++j) ds_add_prod(hi, lo, V[(size_t)j * ldv + i], hh[j], hl[j]);
+        r = __fadd_rn(hi, lo);
+        w[i] = r;
+    }
+    if constexpr (kNorm) {
+        // ||w||^2 over the interior (halo copies excluded), as FP32 pairs per
+        // warp and FP64 per block: part[blockIdx.x]
+        float sh = 0.f, sl = 0.f;
+        if (i < n) {
+            const int rem = i % g.lp, yy = rem / g.nxp, xx = rem - yy * g.nxp;
+            if (xx >= g.H && xx < g.nx + g.H && yy >= g.H && yy < g.ny + g.H) ds_add_prod(sh, sl, r, r, 0.f);
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            ds_add_pair(sh, sl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)sh + (double)sl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+            part[blockIdx.x] = t;
+        }
+    }
 }
 
 template <typename T, typename U>
@@ -674,15 +721,31 @@ void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, 
 template <typename T>
 void launch_gmres_update(cudaStream_t st, int n, T *w, const T *V, size_t ldv, int k, const double *h) {
     if constexpr (sizeof(T) == 4) {
-        k_gupdate_ds<<<(n + 255) / 256, 256, 0, st>>>(n, (float *)w, (const float *)V, ldv, k, h, -1.0);
+        k_gupdate_ds<false><<<(n + 255) / 256, 256, 0, st>>>(GridC(), n, (float *)w, (const float *)V, ldv, k, h,
+                                                               -1.0, nullptr);
         return;
     }
     k_gupdate<T><<<(n + 255) / 256, 256, 0, st>>>(n, w, V, ldv, k, h, -1.0);
 }
+// w -= V h, then ||w||^2 (interior) into *out; part: scratch partial sums
+template <typename T>
+void launch_gmres_update_norm(cudaStream_t st, const GridC &g, int n, T *w, const T *V, size_t ldv, int k,
+                              const double *h, double *part, int nblk, double *out) {
+    if constexpr (sizeof(T) == 4) {
+        const int nb = (n + 255) / 256;
+        k_gupdate_ds<true><<<nb, 256, 0, st>>>(g, n, (float *)w, (const float *)V, ldv, k, h, -1.0, part);
+        k_finalize<<<1, 256, 0, st>>>(part, nb, 1, out);
+        return;
+    }
+    launch_gmres_update<T>(st, n, w, V, ldv, k, h);
+    launch_sumsq<T>(st, g, w, part, nblk, out);
+}
+
 template <typename T>
 void launch_combine(cudaStream_t st, int n, T *x, const T *V, size_t ldv, int k, const double *y) {
     if constexpr (sizeof(T) == 4) {
-        k_gupdate_ds<<<(n + 255) / 256, 256, 0, st>>>(n, (float *)x, (const float *)V, ldv, k, y, 1.0);
+        k_gupdate_ds<false><<<(n + 255) / 256, 256, 0, st>>>(GridC(), n, (float *)x, (const float *)V, ldv, k, y, 1.0,
+                                                               nullptr);
         return;
     }
     k_gupdate<T><<<(n + 255) / 256, 256, 0, st>>>(n, x, V, ldv, k, y, 1.0);
@@ -713,6 +776,8 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
     template void launch_scale<T>(cudaStream_t, int, const T *, double, T *);                                       \
     template void launch_cheb_start<T>(cudaStream_t, int, const double *, double, T *, T *, T *);                  \
     template void launch_gmres_update<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);           \
+    template void launch_gmres_update_norm<T>(cudaStream_t, const GridC &, int, T *, const T *, size_t, int,       \
+                                              const double *, double *, int, double *);                          \
     template void launch_combine<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);            \
     template void launch_axpby<T>(cudaStream_t, int, double, const T *, double, const T *, T *);                   \
     template void launch_update_x<T>(cudaStream_t, int, const T *, double *, float *, float *);                   \
