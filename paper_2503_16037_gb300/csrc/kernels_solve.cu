@@ -473,13 +473,9 @@ int dot_blocks(const GridC &g) {
 // (ds_add_prod, about 48 significant bits), kDotCols columns per pass over
 // y; the pairs enter the FP64 block and grid sums only at the end.
 constexpr int kDotCols = 8;
-#ifndef TK_DOTS_FLAT
-#define TK_DOTS_FLAT 0
-#endif
-#ifndef TK_DOTS_BPS
-#define TK_DOTS_BPS 2
-#endif
-constexpr int kDotBlocksPerSM = TK_DOTS_BPS;
+// blocks per SM (measured on the 128 x 128 x 40 cloud: 4 beats 2; a flat
+// element decomposition at 4 or 8 blocks per SM was slower than warps per line)
+constexpr int kDotBlocksPerSM = 4;
 // (hi, lo) += (h2, l2) for FP32 pairs, with Knuth's two-sum on the high parts
 __device__ __forceinline__ void ds_add_pair(float &hi, float &lo, float h2, float l2) {
     const float s = __fadd_rn(hi, h2);
@@ -498,22 +494,6 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
         float hi[kDotCols], lo[kDotCols];
 #pragma unroll
         for (int c = 0; c < kDotCols; ++c) hi[c] = lo[c] = 0.f;
-#if TK_DOTS_FLAT
-        // interior elements flattened over the grid's threads
-        const int ne = nlines * g.nx;
-#pragma unroll 2
-        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-            const int l = e / g.nx, x = e - l * g.nx;
-            const int z = l / g.ny, yy = l - z * g.ny;
-            const long long p = halo_pos(g, x, yy, z);
-            const float yv = y[p];
-#pragma unroll
-            for (int c = 0; c < kDotCols; ++c)
-                if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + p], yv, 0.f);
-        }
-        (void)gw;
-        (void)nw;
-#else
         for (int l = gw; l < nlines; l += nw) {
             const int z = l / g.ny, yy = l - z * g.ny;
             const long long base = halo_pos(g, 0, yy, z);
@@ -525,7 +505,6 @@ __global__ void __launch_bounds__(256) k_dots_ds(GridC g, const float *__restric
                     if (c0 + c < ncol) ds_add_prod(hi[c], lo[c], V[(size_t)(c0 + c) * ldv + base + x], yv, 0.f);
             }
         }
-#endif
         // warp sums in FP32-pair arithmetic; FP64 only for the warps' results
 #pragma unroll
         for (int c = 0; c < kDotCols; ++c) {
@@ -559,7 +538,7 @@ template <typename A, typename B>
 void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int ncol, const B *y, double *part,
                  int nblk, double *out) {
     if constexpr (sizeof(A) == 4 && sizeof(B) == 4) {
-        const int nb = TK_DOTS_FLAT ? dot_blocks_ds() : std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
+        const int nb = std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
         k_dots_ds<<<nb, 256, 0, st>>>(g, (const float *)V, ldv, ncol, (const float *)y, part);
         k_finalize<<<ncol, 256, 0, st>>>(part, nb, ncol, out);
         return;
