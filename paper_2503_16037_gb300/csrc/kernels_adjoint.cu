@@ -223,11 +223,20 @@ __global__ void k_pix_adj(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__r
 //   c = lambda_i + E-bar_i theta_{i,t}          (s-bar = lambda, g-bar = E-bar)
 //   P-bar = rho_i c (x_j W^iso + W^sun e1_j)
 // the adjoints go to rho_i, e1_j and the optical depths of the slot.
+#ifndef TK_ADJ_W
+#define TK_ADJ_W 4
+#endif
+// blocks per SM the register budget is sized for: 8 (64 registers) measured
+// best on GB300 (gradient 1.380 -> 1.348 ms against the uncapped 96 registers)
+#ifndef TK_ADJ_MINB
+#define TK_ADJ_MINB 8
+#endif
+constexpr int kAdjW = TK_ADJ_W;  // warps per 128-row group of the reverse edge march
 template <typename T, int S>
-__global__ void __launch_bounds__(32 * 4) k_asm_adj(GridC g, GraphP gp, FieldP<T> f, ViewC vc,
-                                                    const double *__restrict__ x64, const double *__restrict__ lam64,
-                                                    AdjP<T> ad) {
-    constexpr int W = 4;
+__global__ void __launch_bounds__(32 * kAdjW, TK_ADJ_MINB) k_asm_adj(GridC g, GraphP gp, FieldP<T> f, ViewC vc,
+                                                                     const double *__restrict__ x64,
+                                                                     const double *__restrict__ lam64, AdjP<T> ad) {
+    constexpr int W = kAdjW;
     __shared__ T sh[W][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
@@ -532,10 +541,10 @@ void launch_asm_adj(cudaStream_t st, const GridC &g, const GraphP &gp, const Fie
                     const double *x64, const double *lam64, const AdjP<T> &ad) {
     const int nb = (g.nz + 1) * g.gpl;
     switch (g.S) {
-        case 1: k_asm_adj<T, 1><<<nb, 128, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        case 2: k_asm_adj<T, 2><<<nb, 128, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        case 3: k_asm_adj<T, 3><<<nb, 128, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        default: k_asm_adj<T, 4><<<nb, 128, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
+        case 1: k_asm_adj<T, 1><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
+        case 2: k_asm_adj<T, 2><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
+        case 3: k_asm_adj<T, 3><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
+        default: k_asm_adj<T, 4><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
     }
 }
 
