@@ -260,7 +260,8 @@ size_t tursca_scene_device_bytes(const tursca_scene *scene);
 /* Per-kernel device time measured with CUDA events recorded on the scene's
  * stream around each launch of the hot kernels (profiling only). */
 typedef struct {
-    char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb" */
+    char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb",
+                           "gmres_orth" (both Gram-Schmidt passes of one Arnoldi step) */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;

@@ -130,9 +130,9 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb"};
-constexpr int kNProf = 6;
-enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5 };
+const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb", "gmres_orth"};
+constexpr int kNProf = 7;
+enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6 };
 
 // returns the index of the pair, or -1 when profiling is off
 int prof_begin(tursca_scene *sc, int cat) {
@@ -547,10 +547,12 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
             int pi = prof_begin(sc, P_SPMV);
             tk::launch_imk<T>(sc->st, g, gp, val, vk, w);
             prof_end(sc, pi);
+            int po = prof_begin(sc, P_ORTH);
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred + 64);
             tk::launch_gmres_update_norm<T>(sc->st, g, n, w, V, ld, k + 1, sc->dred + 64, sc->part, nb, sc->dred + 128);
+            prof_end(sc, po);
             sc->launches += 9;
             ss.iters++;
             total++;
@@ -1580,8 +1582,8 @@ tursca_status tursca_profile_enable(tursca_scene *sc, int on) {
 tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int n, int *n_out) {
     if (!sc || !out || n < 0) return fail(sc, TURSCA_E_INVALID, "bad arguments");
     CK(cudaStreamSynchronize(sc->st), "sync");
-    double ms[kNProf] = {0, 0, 0, 0, 0, 0};
-    long long cnt[kNProf] = {0, 0, 0, 0, 0, 0};
+    double ms[kNProf] = {};
+    long long cnt[kNProf] = {};
     for (size_t i = 0; i < sc->ev_used; ++i) {
         float t = 0.f;
         CK(cudaEventElapsedTime(&t, sc->ev[2 * i], sc->ev[2 * i + 1]), "event time");
