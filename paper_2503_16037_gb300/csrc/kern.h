@@ -314,6 +314,9 @@ template <typename T>
 void launch_axpy_to64(cudaStream_t st, int n, const T *d, double *x);  // x += d
 template <typename T>
 void launch_scale(cudaStream_t st, int n, const T *a, double alpha, T *b);  // b = alpha a
+// a += b
+template <typename T>
+void launch_add(cudaStream_t st, int n, T *a, const T *b);
 // start of a Chebyshev refinement in one pass: b = (T) r64, d = 0, p = alpha b
 template <typename T>
 void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, T *b, T *d, T *p);

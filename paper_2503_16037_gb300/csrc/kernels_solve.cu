@@ -616,6 +616,11 @@ __global__ void k_scale(int n, const T *__restrict__ a, double alpha, T *__restr
     if (i < n) b[i] = (T)(alpha * (double)a[i]);
 }
 template <typename T>
+__global__ void k_add(int n, T *a, const T *b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += b[i];
+}
+template <typename T>
 __global__ void k_cheb_start(int n, const double *__restrict__ r64, double alpha, T *__restrict__ b,
                              T *__restrict__ d, T *__restrict__ p) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,6 +699,10 @@ void launch_scale(cudaStream_t st, int n, const T *a, double alpha, T *b) {
     k_scale<T><<<(n + 255) / 256, 256, 0, st>>>(n, a, alpha, b);
 }
 template <typename T>
+void launch_add(cudaStream_t st, int n, T *a, const T *b) {
+    k_add<T><<<(n + 255) / 256, 256, 0, st>>>(n, a, b);
+}
+template <typename T>
 void launch_cheb_start(cudaStream_t st, int n, const double *r64, double alpha, T *b, T *d, T *p) {
     k_cheb_start<T><<<(n + 255) / 256, 256, 0, st>>>(n, r64, alpha, b, d, p);
 }
@@ -754,6 +763,7 @@ void launch_axpby(cudaStream_t st, int n, double a, const T *x, double b, const 
     template void launch_axpy_to64<T>(cudaStream_t, int, const T *, double *);                                      \
     template void launch_scale<T>(cudaStream_t, int, const T *, double, T *);                                       \
     template void launch_cheb_start<T>(cudaStream_t, int, const double *, double, T *, T *, T *);                  \
+    template void launch_add<T>(cudaStream_t, int, T *, const T *);                                                \
     template void launch_gmres_update<T>(cudaStream_t, int, T *, const T *, size_t, int, const double *);           \
     template void launch_gmres_update_norm<T>(cudaStream_t, const GridC &, int, T *, const T *, size_t, int,       \
                                               const double *, double *, int, double *);                          \
