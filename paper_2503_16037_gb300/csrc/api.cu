@@ -39,6 +39,11 @@ struct DevBuf {
 #define TK_GMRES_POLY 2
 #endif
 constexpr int kGmresPoly = TK_GMRES_POLY;
+// restart length of GMRES on FP32 scenes (FP64 scenes: 40); measured on the
+// broken cloud: 20 / 30 / 40 gave 39.4 / 37.4 / 38.1 ms
+#ifndef TK_GMRES_M32
+#define TK_GMRES_M32 30
+#endif
 
 // one geometry-dependent device buffer per slot
 enum VSlot {
@@ -734,7 +739,7 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
     const bool fp64 = sc->d.precision == TURSCA_FP64;
     if (solver == TURSCA_SOLVER_AUTO) solver = fp64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
     auto ensure_basis = [&]() -> tursca_status {
-        int m = fp64 ? 40 : 30;
+        int m = fp64 ? 40 : TK_GMRES_M32;
         if (!sc->V || sc->gm_m != m) {
             T *V;
             // m + 1 basis vectors and two work vectors of the preconditioner
