@@ -41,40 +41,48 @@ __device__ __forceinline__ int rwrap(int a, int n) {
 // sum_slots hg_sp(slot direction) K_ij x_j, and the row's species weights
 // are applied once at the end.  x is gathered from a compute-type copy (xc)
 // of the FP64 solution, in the solver's haloed layout.
-template <typename T>
+#ifndef TK_EMIS_TILE
+#define TK_EMIS_TILE 1
+#endif
+template <typename T, int S>
 struct OpEmission {
     using A = T;
-    static constexpr int NA = 4 * MAX_SPECIES;
+    static constexpr int NA = 4 * S;
     static constexpr bool kPart = false;
     struct Slot {
-        T hv[MAX_SPECIES];
+        T hv[S];
     };
     struct Pre {
-        T w[MAX_SPECIES];
+        T w[S];
         T e1, gsun;
     };
     FieldP<T> f;
     const T *xc;
     T *emis;
-    int S, ndir, n_atm;
+    int ndir, n_atm;
+    static constexpr int kTile = (sizeof(T) == 4 && TK_EMIS_TILE) ? 1 : 0;
+    __device__ __forceinline__ const T *gsrc(int) const { return xc; }
+    // the slot's phase-function values toward the instrument, per species
     __device__ __forceinline__ Slot slot(const GraphP &gp, int t) const {
         Slot si;
-        const int hgd = gp.cls[__ldg(&gp.tmpl[t].x)].hgdir;
+        const int hgd = __ldg(&gp.aslot[t].hgdir);
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) si.hv[sp] = sp < S ? f.hgv[sp * ndir + hgd] : T(0);
+        for (int sp = 0; sp < S; ++sp) si.hv[sp] = f.hgv[sp * ndir + hgd];
         return si;
     }
-    __device__ __forceinline__ void add(A *a, int k, T v, int j, const Slot &si) const {
-        const T vx = v * __ldg(xc + j);
+    __device__ __forceinline__ void acc(A *a, int k, T vx, const Slot &si) const {
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp)
-            if (sp < S) a[sp * 4 + k] += vx * si.hv[sp];
+        for (int sp = 0; sp < S; ++sp) a[sp * 4 + k] += vx * si.hv[sp];
+    }
+    __device__ __forceinline__ void add(A *a, int k, T v, int j, const Slot &si) const { acc(a, k, v * __ldg(xc + j), si); }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int, const Slot &si) const {
+        acc(a, k, v * s[0], si);
     }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
         Pre p;
         const int i = G.row[k];
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) p.w[sp] = sp < S ? f.wsp[(size_t)sp * n_atm + i] : T(0);
+        for (int sp = 0; sp < S; ++sp) p.w[sp] = f.wsp[(size_t)sp * n_atm + i];
         p.e1 = f.e1[i];
         p.gsun = f.gsun[i];
         return p;
@@ -82,13 +90,12 @@ struct OpEmission {
     template <int W>
     __device__ __forceinline__ static void combine_row(const A (*sh)[NA][32], int lane, int k, A *a) {
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) sum_word<W, A, NA>(sh, lane, sp * 4 + k, a);
+        for (int sp = 0; sp < S; ++sp) sum_word<W, A, NA>(sh, lane, sp * 4 + k, a);
     }
     __device__ __forceinline__ double finish_row(const GroupRows &G, int k, const A *a, const Pre &p) const {
         T tot = T(0), th0 = T(0);
 #pragma unroll
-        for (int sp = 0; sp < MAX_SPECIES; ++sp) {
-            if (sp >= S) continue;
+        for (int sp = 0; sp < S; ++sp) {
             tot += p.w[sp] * a[sp * 4 + k];
             th0 += p.w[sp] * f.hg0v[sp];
         }
@@ -153,15 +160,12 @@ __global__ void k_pixels(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__re
     }
 }
 
-template <typename T>
-void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                     const T *xc, T *emis) {
-    (void)vc;
-    OpEmission<T> op;
+template <typename T, int S>
+static void run_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const T *xc, T *emis) {
+    OpEmission<T, S> op;
     op.f = f;
     op.xc = xc;
     op.emis = emis;
-    op.S = g.S;
     op.ndir = g.nd + g.ngd;
     op.n_atm = g.n_atm;
     // atmospheric layers only: the ground emits nothing toward the instrument
@@ -170,6 +174,17 @@ void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const Fi
     run_op(st, ge, gp, f.val, op, 1);
 }
 
+template <typename T>
+void launch_emission(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                     const T *xc, T *emis) {
+    (void)vc;
+    switch (g.S) {  // the species count as a compile-time constant
+        case 1: run_emission<T, 1>(st, g, gp, f, xc, emis); break;
+        case 2: run_emission<T, 2>(st, g, gp, f, xc, emis); break;
+        case 3: run_emission<T, 3>(st, g, gp, f, xc, emis); break;
+        default: run_emission<T, 4>(st, g, gp, f, xc, emis); break;
+    }
+}
 
 template <typename T>
 void launch_pixels(cudaStream_t st, const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp,

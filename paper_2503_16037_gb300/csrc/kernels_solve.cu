@@ -66,7 +66,7 @@ struct OpSpmv {
     T *y;
     static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
     __device__ __forceinline__ const T *gsrc(int) const { return x; }
-    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int, NoSlot) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -130,7 +130,7 @@ struct OpSweepPow {
     XUpd xu;
     static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
     __device__ __forceinline__ const T *gsrc(int) const { return x; }
-    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int, NoSlot) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(x + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -168,7 +168,7 @@ struct OpCheb {
     XUpd xu;
     static constexpr int kTile = sizeof(T) == 4 ? 1 : 0;
     __device__ __forceinline__ const T *gsrc(int) const { return p; }
-    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int) const { a[k] += v * s[0]; }
+    __device__ __forceinline__ void add_t(A *a, int k, T v, const T *s, int, NoSlot) const { a[k] += v * s[0]; }
     __device__ __forceinline__ NoSlot slot(const GraphP &, int) const { return NoSlot(); }
     __device__ __forceinline__ void add(A *a, int k, T v, int j, NoSlot) const { a[k] += v * __ldg(p + j); }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {
@@ -229,7 +229,7 @@ struct OpResidDS {
     }
     static constexpr int kTile = 2;
     __device__ __forceinline__ const float *gsrc(int i) const { return i == 0 ? xh : xl; }
-    __device__ __forceinline__ void add_t(A *a, int k, float v, const float *s, int st) const {
+    __device__ __forceinline__ void add_t(A *a, int k, float v, const float *s, int st, NoSlot) const {
         ds_add_prod(a[k], a[4 + k], v, s[0], s[st]);
     }
     __device__ __forceinline__ Pre pre(const GroupRows &G, int k) const {

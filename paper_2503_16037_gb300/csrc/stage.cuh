@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(32 * W) k_plain(GridC g, GraphP gp, const T *_
 constexpr int kTileUnroll = TK_TILE_UNROLL;
 
 // Ops that gather from FP32 vectors only declare kTile = n (the number of
-// gathered vectors, 1 or 2), gsrc(i) (vector i) and add_t(a, k, v, s, st):
+// gathered vectors, 1 or 2), gsrc(i) (vector i) and add_t(a, k, v, s, st, si):
 // the accumulation of one value times the gathered values s[0], s[st], ...
-// (one tile per vector, st floats apart).
+// (one tile per vector, st floats apart), with the slot's constants si.
 template <class Op, class = void>
 struct tile_op {
     static constexpr int value = 0;
@@ -493,21 +493,24 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
     __syncthreads();
     if (tA < G.nt) {
         const int tt = __ldg(gp.ttile + G.t0 + tA);
+        const auto si = op.slot(gp, G.t0 + tA);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_t(a, k, v0[k], tile + tt + rl[k], ts);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v0[k], tile + tt + rl[k], ts, si);
     }
     if (tB < G.nt) {
         const int tt = __ldg(gp.ttile + G.t0 + tB);
+        const auto si = op.slot(gp, G.t0 + tB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_t(a, k, v1[k], tile + tt + rl[k], ts);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v1[k], tile + tt + rl[k], ts, si);
     }
 #pragma unroll kTileUnroll
     for (int t = w + 2 * W; t < G.nt; t += W) {
         const int tt = __ldg(gp.ttile + G.t0 + t);
+        const auto si = op.slot(gp, G.t0 + t);
         float q[4];
         ld_quad(v + (size_t)t * kGroup, q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_t(a, k, q[k], tile + tt + rl[k], ts);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, q[k], tile + tt + rl[k], ts, si);
     }
 #pragma unroll
     for (int m = 0; m < NA; ++m) sh[w][m][lane] = a[m];
