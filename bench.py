@@ -504,7 +504,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scenes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "kernel_timing": "CUDA events around each launch on the scene stream, on every %dth timed step (%d steps)"
+        "kernel_timing": "CUDA events on the scene stream, on every %dth timed step (%d steps): around each launch, and around each run of back-to-back Chebyshev steps or power sweeps (average per launch within the run)"
                          % (PROF_EVERY, len(prof_steps)),
         "clocks": clocks,
         "parity": parity,

@@ -141,6 +141,7 @@ struct tursca_scene {
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // pairs
     std::vector<int> ev_cat;
+    std::vector<int> ev_n;         // launches covered by each pair
     size_t ev_used = 0;
 };
 
@@ -159,14 +160,21 @@ int prof_begin(tursca_scene *sc, int cat) {
             sc->ev.push_back(e);
         }
         sc->ev_cat.resize(sc->ev.size() / 2);
+        sc->ev_n.resize(sc->ev.size() / 2);
     }
     size_t i = sc->ev_used++;
     sc->ev_cat[i] = cat;
+    sc->ev_n[i] = 1;
     cudaEventRecord(sc->ev[2 * i], sc->st);
     return (int)i;
 }
-void prof_end(tursca_scene *sc, int i) {
-    if (i >= 0) cudaEventRecord(sc->ev[2 * i + 1], sc->st);
+// n: launches of the category between the pair (a run of back-to-back
+// launches of one kernel is timed as a whole, so that the events do not
+// break the overlap of consecutive launches)
+void prof_end(tursca_scene *sc, int i, int n = 1) {
+    if (i < 0) return;
+    sc->ev_n[i] = n;
+    cudaEventRecord(sc->ev[2 * i + 1], sc->st);
 }
 }  // namespace
 
@@ -806,17 +814,18 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             // the first sweep reads d = r from bb itself; the later ones
             // alternate between d0 and d1, so bb is never overwritten
             T *cur = bb, *nxt = (T *)sc->d0;
+            int pi = prof_begin(sc, P_SPMV);
             for (int it = 0; it < n1; ++it) {
-                int pi = prof_begin(sc, P_SPMV);
                 // the last sweep also applies x += d (its output) row by row
                 const bool last = it == n1 - 1;
                 tk::launch_sweep_pow<T>(sc->st, g, gp, val, cur, bb, nxt, sc->part + (it & 1) * nsw,
                                         last ? io.x : nullptr, last && ds ? sc->xh : nullptr,
                                         last && ds ? sc->xl : nullptr);
-                prof_end(sc, pi);
+                
                 cur = nxt;
                 nxt = cur == (T *)sc->d0 ? (T *)sc->d1 : (T *)sc->d0;
             }
+            prof_end(sc, pi, n1);
             tk::launch_finalize2(sc->st, sc->part, nsw, sc->dred + 2);
             sc->launches += n1 + 1;
             ss.iters += n1;
@@ -838,17 +847,17 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             tk::launch_cheb_start<T>(sc->st, n, sc->r64, 1.0 / cp.theta, r, d, p0);
             sc->launches++;
             double rk = 1.0 / cp.sigma;
+            int pi = prof_begin(sc, P_CHEB);
             for (int k = 0; k < nc; ++k) {
                 double rk1 = 1.0 / (2.0 * cp.sigma - rk);
-                int pi = prof_begin(sc, P_CHEB);
                 // the last step also applies x += d row by row
                 const bool last = k == nc - 1;
                 tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta,
                                    last ? io.x : nullptr, last && ds ? sc->xh : nullptr, last && ds ? sc->xl : nullptr);
-                prof_end(sc, pi);
                 std::swap(p0, p1);
                 rk = rk1;
             }
+            prof_end(sc, pi, nc);
             sc->launches += nc;
             ss.iters += nc;
             dd = d;
@@ -1630,7 +1639,7 @@ tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int
         float t = 0.f;
         CK(cudaEventElapsedTime(&t, sc->ev[2 * i], sc->ev[2 * i + 1]), "event time");
         ms[sc->ev_cat[i]] += t;
-        cnt[sc->ev_cat[i]]++;
+        cnt[sc->ev_cat[i]] += sc->ev_n[i];
     }
     sc->ev_used = 0;
     int m = std::min(n, kNProf);

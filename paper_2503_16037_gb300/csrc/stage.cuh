@@ -454,9 +454,12 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
     constexpr int NA = Op::NA;
     __shared__ A sh[W][NA][32];
     extern __shared__ float tile[];
+    __shared__ int s_lay[kTileLayers];
     pdl_trigger();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
+    // the tile's source layers are graph data: read them before waiting
+    if (threadIdx.x < kTileLayers) s_lay[threadIdx.x] = __ldg(gp.tlay + G.z * kTileLayers + threadIdx.x);
     const int r0 = (blockIdx.x - G.z * g.gpl) * kGroup;
     const int y0 = r0 / g.nx;
     const int y1 = min(r0 + kGroup - 1, g.nxy - 1) / g.nx;
@@ -476,14 +479,16 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
     const int tA = w, tB = w + W;
     if (tA < G.nt) ld_quad(v + (size_t)tA * kGroup, v0);
     if (tB < G.nt) ld_quad(v + (size_t)tB * kGroup, v1);
+    const int ttA = tA < G.nt ? __ldg(gp.ttile + G.t0 + tA) : 0, ttB = tB < G.nt ? __ldg(gp.ttile + G.t0 + tB) : 0;
     pdl_wait();
     const typename Op::Pre pre = load_pre(op, G);
     const int ts = kTileLayers * g.tl;  // floats per vector's tile
+    __syncthreads();  // s_lay
 #pragma unroll
     for (int iv = 0; iv < tile_op<Op>::value; ++iv) {
         const float *src = op.gsrc(iv) + (long long)y0 * g.nxp;
         for (int ls = 0; ls < kTileLayers; ++ls) {
-            const int lay = __ldg(gp.tlay + G.z * kTileLayers + ls);
+            const int lay = s_lay[ls];
             if (lay < 0) break;  // the used tile layers come first
             const float *s = src + (long long)lay * g.lp;
             float *d = tile + iv * ts + ls * g.tl;
@@ -492,16 +497,14 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
     }
     __syncthreads();
     if (tA < G.nt) {
-        const int tt = __ldg(gp.ttile + G.t0 + tA);
         const auto si = op.slot(gp, G.t0 + tA);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_t(a, k, v0[k], tile + tt + rl[k], ts, si);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v0[k], tile + ttA + rl[k], ts, si);
     }
     if (tB < G.nt) {
-        const int tt = __ldg(gp.ttile + G.t0 + tB);
         const auto si = op.slot(gp, G.t0 + tB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) op.add_t(a, k, v1[k], tile + tt + rl[k], ts, si);
+        for (int k = 0; k < 4; ++k) op.add_t(a, k, v1[k], tile + ttB + rl[k], ts, si);
     }
 #pragma unroll kTileUnroll
     for (int t = w + 2 * W; t < G.nt; t += W) {
