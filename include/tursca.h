@@ -166,13 +166,17 @@ tursca_status tursca_build_graph(tursca_scene *scene);
 tursca_status tursca_assemble_flux(tursca_scene *scene, const tursca_geometry *geom);
 
 /* Solve (I - K) x = s (Eq. flux_system) to ||s - (I - K) x|| <= rtol ||s||
- * evaluated in FP64, with at most max_iter products with K.  The outer loop
- * is FP64 residual refinement; each refinement solves for the correction
- * with inner iterations in the scene's precision: FP32_REFINE scenes first run
- * a few Neumann sweeps (the series of Eq. fs_sum) that also estimate the
- * largest eigenvalue of K, then Chebyshev iterations on the interval that
- * estimate implies (GMRES when it is within 0.01 of 1); FP64 scenes run
- * GMRES.  Synchronises once per refinement.  info may be NULL. */
+ * evaluated in FP64, with at most max_iter inner steps (a sweep, a Chebyshev
+ * step, or a GMRES step, which applies K twice).  The outer loop is FP64
+ * residual refinement; each refinement solves for the correction with inner
+ * iterations in the scene's precision: FP32_REFINE scenes first run a few
+ * Neumann sweeps (the series of Eq. fs_sum) that also estimate the largest
+ * eigenvalue of K, then Chebyshev iterations on the interval that estimate
+ * implies, or GMRES when the estimate is 0.85 or more or a Chebyshev
+ * refinement under-delivers; FP64 scenes run GMRES.  GMRES(30) (FP64: 40)
+ * is right-preconditioned with I + K, the first two terms of that series.
+ * Synchronises once per refinement (GMRES: once per step).  info may be
+ * NULL. */
 tursca_status tursca_solve(tursca_scene *scene, double rtol, int max_iter, tursca_solve_info *info);
 
 /* Same as tursca_solve with an explicit solver choice (TURSCA_SOLVER_*). */
@@ -236,11 +240,13 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     the context to normal (which also affects other scenes running
  *     concurrently in the same context).  Pays only when the values fit in
  *     the set-aside; results are bit-identical either way.
- *   TURSCA_OPT_GATHER_TILE: 1 (default) lets the FP32 row-group passes that
- *     gather from one vector (sweeps, Chebyshev steps, products with I - K)
- *     copy each group's source rows into a shared-memory tile (at most
- *     48 KB per block; larger groups gather from global memory); 0 always
- *     gathers from global memory.  Results are bit-identical either way.
+ *   TURSCA_OPT_GATHER_TILE: 1 (default) lets the FP32 row-group passes
+ *     (sweeps, Chebyshev steps, products with I - K, the FP32-pair residual
+ *     and the emission pass, also over K^T in the adjoint) copy each group's
+ *     source rows of the vectors they gather from into shared-memory tiles
+ *     (at most 48 KB per block; larger groups gather from global memory);
+ *     0 always gathers from global memory.  Results are bit-identical
+ *     either way.
  */
 enum {
     TURSCA_OPT_RESIDUAL_FP64 = 1,

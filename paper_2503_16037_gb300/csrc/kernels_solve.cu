@@ -21,10 +21,12 @@ namespace tk {
 // row's values with the source values it gathers, and finishes the row
 // (combination of the warps' partial sums in a fixed order, the row update,
 // per-group partial sums of squares).  The plain driver runs one block of W
-// warps per group and reads the values directly; the pipelined driver
-// (k_pipe) streams them through shared memory.  Source values are gathered
-// from haloed vectors (the template offset is the only index arithmetic),
-// and every row result is stored with its halo copies.
+// warps per group and reads the values directly; for FP32 ops that gather
+// from FP32 vectors it first copies the group's source rows into a
+// shared-memory tile (k_tile); the pipelined driver (k_pipe) streams the
+// values through shared memory.  Source values are gathered from haloed
+// vectors (the template offset is the only index arithmetic), and every row
+// result is stored with its halo copies.
 
 // Op interface (both drivers): A / NA: accumulator type and words per lane;
 // kPart: the op writes per-row-block partial sums part[4 gi + k]; Pre: the
