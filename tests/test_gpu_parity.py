@@ -78,6 +78,7 @@ SMALL = {
     "random_R1_3species": lambda: scenes.make_random(13, 11, 7, seed=8, S=3, R=1, M=1024, sza=20.0, vza=55.0),
     "thin_nz_eq_R": lambda: scenes.make_random(9, 10, 2, seed=9, S=2, R=2, M=1024),
     "plume_small": lambda: scenes.make_plume(nx=24, ny=20, nz=12),
+    "random_4species": lambda: scenes.make_random(12, 11, 6, seed=10, S=4, R=2, M=1024),
 }
 
 
@@ -104,7 +105,8 @@ def test_fp64_parity_all_stages(name):
     assert rn.info.rel_resid64 <= 1e-13
 
 
-@pytest.mark.parametrize("name", ["random_R2_ragged", "random_R1_3species", "thin_nz_eq_R", "plume_small"])
+@pytest.mark.parametrize("name", ["random_R2_ragged", "random_R1_3species", "thin_nz_eq_R", "plume_small",
+                                  "random_4species"])
 def test_fp32_refined_parity(name):
     sc = SMALL[name]()
     r = O.run(sc)
