@@ -247,13 +247,23 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     (at most 48 KB per block; larger groups gather from global memory);
  *     0 always gathers from global memory.  Results are bit-identical
  *     either way.
+ *   TURSCA_OPT_SINGLE_SCATTER: 0 (default); 1 makes the following
+ *     assemblies first-order only (single scattering, the branch of the data
+ *     flow of Sec. 3 that stops after the direct beam): assemble_flux computes
+ *     the phase tables, the extinction and e1 and forms neither K nor
+ *     K^sun (s reads as 0); solve sets x = 0 without a product with K
+ *     (iters = refinements = 0, rel_resid64 = 0); render_radiance takes
+ *     E_i = e1_i Theta_i(s0 . v) and the ground's e1_c.  get(TURSCA_F_VAL)
+ *     and tursca_adjoint return TURSCA_E_STATE after such an assembly.
+ *     Changing the value invalidates the current assembly.
  */
 enum {
     TURSCA_OPT_RESIDUAL_FP64 = 1,
     TURSCA_OPT_GROUP_WARPS = 2,
     TURSCA_OPT_STAGE_VALUES = 3,
     TURSCA_OPT_L2_RESIDENT = 4,
-    TURSCA_OPT_GATHER_TILE = 5
+    TURSCA_OPT_GATHER_TILE = 5,
+    TURSCA_OPT_SINGLE_SCATTER = 6
 };
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "graph.h"
+#include "first_order.h"
 #include "kern.h"
 #include "tursca.h"
 
@@ -132,6 +133,8 @@ struct tursca_scene {
     int stage_values = 0;  // 1: FP32 passes stream the values through shared memory (persistent kernels)
     int l2_resident = 0;   // 1: the solves keep the values of K in the persisting part of L2
     int gather_tile = 1;   // 1: FP32 passes gather from a shared-memory tile
+    int single = 0;        // 1: the next assembly takes the first scattering order only
+    bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
     // auxiliary streams and events for the concurrent per-scene tables
@@ -951,16 +954,20 @@ tursca_status do_render(tursca_scene *sc, void *radiance, void *reflectance) {
     tk::ViewC vc = view_c(sc);
     tk::ViewP vp = view_p(sc);
     int pi = prof_begin(sc, P_RENDER);
-    // the solution in the compute type, gathered by the emission kernel
-    const T *xc;
-    if constexpr (sizeof(T) == 8) {
-        xc = (const T *)sc->x64;
+    if (sc->single_asm) {
+        tk::launch_emission_first<T>(sc->st, g, f, (T *)sc->emis);
     } else {
-        tk::launch_convert<double, T>(sc->st, (int)g.npad, sc->x64, (T *)sc->w);
-        sc->launches++;
-        xc = (const T *)sc->w;
+        // the solution in the compute type, gathered by the emission kernel
+        const T *xc;
+        if constexpr (sizeof(T) == 8) {
+            xc = (const T *)sc->x64;
+        } else {
+            tk::launch_convert<double, T>(sc->st, (int)g.npad, sc->x64, (T *)sc->w);
+            sc->launches++;
+            xc = (const T *)sc->w;
+        }
+        tk::launch_emission<T>(sc->st, g, gp, f, vc, xc, (T *)sc->emis);
     }
-    tk::launch_emission<T>(sc->st, g, gp, f, vc, xc, (T *)sc->emis);
     tk::launch_pixels<T>(sc->st, g, f, vc, vp, (const T *)sc->emis, sc->x64, (T *)sc->rad, (T *)sc->refl);
     prof_end(sc, pi);
     sc->launches += 2;
@@ -1429,6 +1436,21 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     const tk::GraphP gp = graph_p(sc);
     const tk::ViewC vc = view_c(sc);
     const tk::ViewP vp = view_p(sc);
+    if (sc->single) {
+        // first scattering order: the direct beam and the phase tables only
+        int pd = prof_begin(sc, P_PRE);
+        if (sc->d.precision == TURSCA_FP64)
+            tk::launch_assemble_direct<double>(sc->st, g, field_p<double>(sc), vc, vp, &sc->launches);
+        else
+            tk::launch_assemble_direct<float>(sc->st, g, field_p<float>(sc), vc, vp, &sc->launches);
+        prof_end(sc, pd);
+        CK(cudaMemsetAsync(sc->s, 0, (size_t)sc->G.n_nodes * sc->es, sc->st), "memset s");
+        CK(cudaMemsetAsync(sc->gsun, 0, (size_t)sc->G.n_atm * sc->es, sc->st), "memset gsun");
+        CK(cudaGetLastError(), "assemble launch");
+        sc->single_asm = sc->assembled = true;
+        sc->solved = sc->rendered = false;
+        return TURSCA_OK;
+    }
     int p0 = prof_begin(sc, P_PRE);
     const cudaStream_t streams[4] = {sc->st, sc->aux[0], sc->aux[1], sc->aux[2]};
     if (sc->d.precision == TURSCA_FP64)
@@ -1444,6 +1466,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     prof_end(sc, p1);
     CK(cudaGetLastError(), "assemble launch");
     sc->assembled = true;
+    sc->single_asm = false;
     sc->solved = sc->rendered = false;
     return TURSCA_OK;
 }
@@ -1456,6 +1479,17 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
     if (solver < 0 || solver > 3) return fail(sc, TURSCA_E_INVALID, "unknown solver");
     tursca_status e = sync_check(sc, "assemble");
     if (e) return e;
+    if (sc->single_asm) {
+        // s = 0: x = 0 solves the system exactly, with no products with K
+        const size_t H = (size_t)sc->d.stencil_radius;
+        const size_t np = (size_t)(sc->d.nz + 1) * (sc->d.nx + 2 * H) * (sc->d.ny + 2 * H);
+        CK(cudaMemsetAsync(sc->x64, 0, np * sizeof(double), sc->st), "memset x");
+        if (solver == TURSCA_SOLVER_AUTO)
+            solver = sc->d.precision == TURSCA_FP64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
+        if (info) *info = tursca_solve_info{0, 0, 0.0, 0.0, solver};
+        sc->solved = true;
+        return TURSCA_OK;
+    }
     if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc));
     return do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
 }
@@ -1475,6 +1509,7 @@ tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_a
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
     if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
+    if (sc->single_asm) return fail(sc, TURSCA_E_STATE, "the adjoint needs a multiple-scattering assembly");
     tursca_status e = ensure_adjoint(sc);
     if (e) return e;
     if (sc->d.precision == TURSCA_FP64) return do_adjoint<double>(sc, dJ_dL, dJ_dmu_abs);
@@ -1505,7 +1540,8 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
                    : which == TURSCA_F_SLOT_DIR ? nnz * 2
                                                 : nnz;
             if (bytes != need) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
-            if (which == TURSCA_F_VAL && !sc->assembled) return fail(sc, TURSCA_E_STATE, "K is not assembled");
+            if (which == TURSCA_F_VAL && (!sc->assembled || sc->single_asm))
+                return fail(sc, TURSCA_E_STATE, "K is not assembled");
             CK(cudaMalloc(&dtmp, need), "alloc");
             const tk::GridC gc = grid_c(sc);
             const tk::GraphP gp = graph_p(sc);
@@ -1595,6 +1631,13 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
             sc->l2_resident = (int)value;
             return TURSCA_OK;
         }
+        case TURSCA_OPT_SINGLE_SCATTER:
+            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "single scatter must be 0 or 1");
+            if ((int)value != sc->single) {
+                sc->single = (int)value;
+                sc->assembled = sc->solved = sc->rendered = false;
+            }
+            return TURSCA_OK;
         case TURSCA_OPT_GATHER_TILE:
             if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "gather tile must be 0 or 1");
             sc->gather_tile = (int)value;

@@ -22,6 +22,7 @@
 #include "kern.h"
 #include "stage.cuh"
 #include "asm_util.cuh"
+#include "first_order.h"
 
 namespace tk {
 
@@ -531,7 +532,23 @@ void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, con
     if (launches) *launches += 1;
 }
 
+// The first-order path: the phase tables, then the voxel fields and the
+// direct beam, all on the scene stream (the edge tables are not needed).
+template <typename T>
+void launch_assemble_direct(cudaStream_t st, const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp,
+                            long long *launches) {
+    const int th = 256;
+    k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st>>>(g, f, vc, vp);
+    k_tables_norm<T><<<g.S, 128, 0, st>>>(g, f, vc, vp);
+    cudaMemsetAsync(f.mus_max_bits, 0, sizeof(unsigned long long), st);
+    k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st>>>(g, f);
+    k_sun<T><<<((long long)g.n_nodes * kRayLanes + 127) / 128, 128, 0, st>>>(g, f, vc, vp);
+    if (launches) *launches += 4;
+}
+
 #define INST(T)                                                                                                   \
+    template void launch_assemble_direct<T>(cudaStream_t, const GridC &, const FieldP<T> &, const ViewC &,       \
+                                            const ViewP &, long long *);                                          \
     template void launch_assemble_pre<T>(cudaStream_t const[4], cudaEvent_t const[5], const GridC &,              \
                                          const GraphP &, const FieldP<T> &, const ViewC &, const ViewP &,         \
                                          long long *);                                                            \

@@ -14,6 +14,7 @@
 
 #include "kern.h"
 #include "stage.cuh"
+#include "first_order.h"
 
 namespace tk {
 
@@ -193,6 +194,24 @@ void launch_pixels(cudaStream_t st, const GridC &g, const FieldP<T> &f, const Vi
     k_pixels<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, f, vc, vp, emis, x, rad, refl);
 }
 
+// First scattering order only: E_i = e1_i Theta_i(s0 . v), one thread per
+// atmospheric node (the species sum in the order of the full pass).
+template <typename T>
+__global__ void k_emission_first(GridC g, FieldP<T> f, T *emis) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_atm) return;
+    T th0 = T(0);
+    for (int sp = 0; sp < g.S; ++sp) th0 += f.wsp[(size_t)sp * g.n_atm + i] * f.hg0v[sp];
+    emis[i] = f.e1[i] * th0;
+}
+
+template <typename T>
+void launch_emission_first(cudaStream_t st, const GridC &g, const FieldP<T> &f, T *emis) {
+    k_emission_first<T><<<(g.n_atm + 255) / 256, 256, 0, st>>>(g, f, emis);
+}
+
+template void launch_emission_first<float>(cudaStream_t, const GridC &, const FieldP<float> &, float *);
+template void launch_emission_first<double>(cudaStream_t, const GridC &, const FieldP<double> &, double *);
 template void launch_emission<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
                                      const ViewC &, const float *, float *);
 template void launch_emission<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,

@@ -205,6 +205,7 @@ OPT_GROUP_WARPS = 2
 OPT_STAGE_VALUES = 3
 OPT_L2_RESIDENT = 4
 OPT_GATHER_TILE = 5
+OPT_SINGLE_SCATTER = 6
 
 
 def tursca_set_option(scene, option: int, value: float):

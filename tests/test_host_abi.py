@@ -38,6 +38,20 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
 
 
+def test_binding_constants_match_header_enums():
+    """Every TURSCA_* enumerator of the header that the binding names (without
+    the prefix) has the same value there."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "tursca.h")).read(), flags=re.S)
+    pairs = re.findall(r"\bTURSCA_([A-Z0-9_]+)\s*=\s*(\d+)", src)
+    assert len(pairs) >= 20
+    seen = 0
+    for name, value in pairs:
+        if hasattr(T, name):
+            assert getattr(T, name) == int(value), name
+            seen += 1
+    assert seen >= 10 and T.OPT_SINGLE_SCATTER == 6
+
+
 def test_status_strings():
     for s in range(8):
         assert T.tursca_status_string(s)
