@@ -46,6 +46,7 @@ class OrcDesc(C.Structure):
         ("npx", C.c_int), ("npy", C.c_int),
         ("flags", C.c_int), ("threads", C.c_int),
         ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
+        ("c_min", C.c_double),
     ]
 
 
@@ -105,6 +106,8 @@ def _load():
         lib.orc_tau_segment.argtypes = [C.POINTER(OrcDesc), _dp, _dp, _dp, C.c_double, C.c_double]
         lib.orc_tau_segment.restype = C.c_double
         lib.orc_fibonacci.argtypes = [C.c_int, C.c_int, _dp]
+        lib.orc_partition.argtypes = [C.POINTER(OrcDesc), _dp, C.c_int, _ip, _dp, _dp]
+        lib.orc_partition.restype = C.c_int
         lib.orc_result_size.restype = C.c_int
         lib.orc_desc_size.restype = C.c_int
         assert lib.orc_result_size() == C.sizeof(OrcResult), "OrcResult layout mismatch"
@@ -124,6 +127,7 @@ def _desc(sc, flags=0, threads=0, gmres_tol=1e-13):
     d.npx, d.npy = sc.npx, sc.npy
     d.flags, d.threads = flags, threads
     d.gmres_tol, d.gmres_restart, d.gmres_maxit = gmres_tol, 60, 20000
+    d.c_min = getattr(sc, "c_min", 0.0)
     return d
 
 
@@ -194,6 +198,25 @@ def tau_segment(sc, mu_e, P, V, tend, lphys) -> float:
     V = np.ascontiguousarray(V, dtype=np.float64)
     return lib.orc_tau_segment(C.byref(d), me.ctypes.data_as(_dp), P.ctypes.data_as(_dp), V.ctypes.data_as(_dp),
                                float(tend), float(lphys))
+
+
+def partition(sc, kept, ground: bool = False):
+    """Quadrature weights of one source that keeps the directions where
+    ``kept`` is true (coupling selection): (q_iso, q_sun[S][n_dirs]) for the
+    atmospheric set, q_lamb for the ground set (``ground``)."""
+    lib = _load()
+    d = _desc(sc)
+    k = np.ascontiguousarray(kept, dtype=np.int32)
+    g = np.ascontiguousarray(sc.g, dtype=np.float64)
+    qi = np.zeros(MAXDIR)
+    qs = np.zeros(sc.n_species * MAXDIR)
+    n = lib.orc_partition(C.byref(d), g.ctypes.data_as(_dp), int(ground), k.ctypes.data_as(_ip),
+                          qi.ctypes.data_as(_dp), qs.ctypes.data_as(_dp))
+    if len(k) != n:
+        raise ValueError("kept has %d entries for %d directions" % (len(k), n))
+    if ground:
+        return qi[:n]
+    return qi[:n], qs[: sc.n_species * n].reshape(sc.n_species, n)
 
 
 def fibonacci(M: int) -> np.ndarray:

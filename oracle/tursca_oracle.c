@@ -16,7 +16,9 @@
  *     Fibonacci lattice (Sec. 3, phase-function integration paragraph) with a
  *     nearest-direction partition of the lattice;
  *   - the scattering coupling C(r, r') of Eq. scatt_coup, used as a
- *     normalised routing weight;
+ *     normalised routing weight and, with c_min > 0, to select the edges of
+ *     the scattering graph (C > c_min, Sec. 2) with the lattice re-partitioned
+ *     among the directions each source keeps;
  *   - the direct solar source S_a (Sec. 2, external source), the linear system
  *     (I - K) x = s of Eq. flux_system (equivalently the series of Eq. fs_sum),
  *     and the final radiance sum toward the instrument (Sec. 2, last equation)
@@ -67,6 +69,7 @@ typedef struct {
     double gmres_tol;
     int gmres_restart;
     int gmres_maxit;
+    double c_min; /* coupling threshold of the scattering graph; 0: full stencil */
 } orc_desc;
 
 typedef struct {
@@ -532,6 +535,97 @@ static void orc_gnd_chain(const orc_desc *d, const orc_result *r, const double *
 /*      receiver, normalised so that sum_u q c = 1 over the directions that  */
 /*      have a receiver other than the source (c = 1 elsewhere).             */
 
+/* Scattering coupling of Eq. scatt_coup between a source and the first
+ * receiver of its chain along one direction: sqrt(mu_s mu_s') / distance,
+ * with mu_s^Lamb for a ground receiver; -1 for a chain without a receiver. */
+static double orc_coupling(const orc_result *r, const double *mu_s_tot, const orc_chain *ch, double mus_src) {
+    if (ch->first < 0) return -1.0;
+    double mus_n = ch->first >= r->n_atm ? r->mu_s_lamb : mu_s_tot[ch->first];
+    return sqrt(mus_src * mus_n) / ch->first_dist;
+}
+
+/* Quadrature weights of one source over the directions it keeps (coupling
+ * selection, Sec. 2: the scattering graph holds the edges with C > c_min).
+ * The cells of Eq. F_term_phase are re-drawn among the kept directions: every
+ * lattice point joins the kept direction closest to it (largest cosine, exact
+ * ties to the lowest index), which is where the flood fill of Sec. 3 over the
+ * lattice adjacency, seeded at the kept directions, ends up.  Atmospheric
+ * source: qi[u] = points / M and qsun[sp][u] = the HG weight toward the
+ * cell over the whole-sphere total; ground source: qi[k] = the cosine-
+ * weighted share of the upper hemisphere (qsun unused).  With every
+ * direction kept this repeats orc_quadrature's sums in the same order.  A
+ * source that keeps nothing gets zero weights. */
+static void orc_partition_kept(const orc_desc *d, const orc_result *r, const double *g, int ground, const int *kept,
+                               double *qi, double *qsun) {
+    int M = d->M, S = d->S;
+    int n = ground ? r->n_gdirs : r->n_dirs;
+    double uh[ORC_MAXDIR][3], len;
+    for (int u = 0; u < n; ++u) {
+        if (ground)
+            orc_gnd_dir(d, r, u, uh[u]);
+        else
+            orc_atm_dir(d, r, u, uh[u], &len);
+    }
+    double s0[3];
+    orc_sun_dir(d, s0);
+    long cnt[ORC_MAXDIR];
+    double zsum[ORC_MAXGDIR], ztot = 0.0;
+    memset(cnt, 0, sizeof cnt);
+    memset(zsum, 0, sizeof zsum);
+    double *hsum = calloc((size_t)S * n, sizeof(double));
+    double *htot = calloc((size_t)S, sizeof(double));
+    for (int m = 0; m < M; ++m) {
+        double sm[3];
+        orc_fib_point(m, M, sm);
+        if (ground && !(sm[2] > 0.0)) continue;
+        int best = -1;
+        double bc = 0.0;
+        for (int u = 0; u < n; ++u) {
+            if (!kept[u]) continue;
+            double c = uh[u][0] * sm[0] + uh[u][1] * sm[1] + uh[u][2] * sm[2];
+            if (best < 0 || c > bc) {
+                bc = c;
+                best = u;
+            }
+        }
+        if (ground) {
+            if (best >= 0) zsum[best] += sm[2];
+            ztot += sm[2];
+            continue;
+        }
+        if (best >= 0) cnt[best]++;
+        double mu0 = s0[0] * sm[0] + s0[1] * sm[1] + s0[2] * sm[2];
+        for (int sp = 0; sp < S; ++sp) {
+            double h = orc_hg(g[sp], mu0);
+            if (best >= 0) hsum[sp * n + best] += h;
+            htot[sp] += h;
+        }
+    }
+    if (ground) {
+        for (int k = 0; k < n; ++k) qi[k] = zsum[k] / ztot;
+    } else {
+        for (int u = 0; u < n; ++u) qi[u] = (double)cnt[u] / (double)M;
+        for (int sp = 0; sp < S; ++sp)
+            for (int u = 0; u < n; ++u) qsun[sp * n + u] = hsum[sp * n + u] / htot[sp];
+    }
+    free(hsum);
+    free(htot);
+}
+
+/* Which directions a source keeps: those whose chain has a receiver with
+ * C > c_min, and every chain without a receiver (it carries no coupling).
+ * c_min = 0 keeps the full stencil.  Returns the number dropped. */
+static int orc_select(const orc_desc *d, const orc_result *r, const double *mu_s_tot, const orc_chain *ch, int ndir,
+                      double mus_src, int *kept) {
+    int ndrop = 0;
+    for (int u = 0; u < ndir; ++u) {
+        double C = orc_coupling(r, mu_s_tot, &ch[u], mus_src);
+        kept[u] = !(d->c_min > 0.0) || C < 0.0 || C > d->c_min;
+        ndrop += !kept[u];
+    }
+    return ndrop;
+}
+
 static void orc_source_weights(const orc_desc *d, const orc_result *r, const double *mu_s_tot,
                                const double *qdir, int ndir, const orc_chain *ch, int src_is_ground,
                                double mus_src, double *cw, double *zout) {
@@ -541,8 +635,7 @@ static void orc_source_weights(const orc_desc *d, const orc_result *r, const dou
     for (int u = 0; u < ndir; ++u) {
         C[u] = 0.0;
         if (ch[u].first < 0) continue;
-        double mus_n = ch[u].first >= r->n_atm ? r->mu_s_lamb : mu_s_tot[ch[u].first];
-        C[u] = sqrt(mus_src * mus_n) / ch[u].first_dist;
+        C[u] = orc_coupling(r, mu_s_tot, &ch[u], mus_src);
         sq += qdir[u];
         sqc += qdir[u] * C[u];
     }
@@ -769,6 +862,10 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     {
         orc_chain *ch = malloc(sizeof(orc_chain) * ORC_MAXDIR);
         double qs[ORC_MAXDIR], ci[ORC_MAXDIR], cs[ORC_MAXDIR];
+        /* per-source quadrature after coupling selection */
+        double qsel[ORC_MAXDIR];
+        double *qsun_sel = malloc(sizeof(double) * (size_t)S * ORC_MAXDIR);
+        int kept[ORC_MAXDIR];
 #pragma omp for schedule(dynamic, 32)
         for (int j = 0; j < nn; ++j) {
             size_t base;
@@ -778,16 +875,22 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                 base = (size_t)j * cap_a;
                 ndir = nd;
                 for (int u = 0; u < nd; ++u) orc_atm_chain(d, r, mue, j, u, &ch[u]);
+                const double *qsun_j = r->q_sun;
+                qi = r->q_iso;
+                if (orc_select(d, r, mus, ch, nd, mus[j], kept) > 0) {
+                    orc_partition_kept(d, r, g, 0, kept, qsel, qsun_sel);
+                    qi = qsel;
+                    qsun_j = qsun_sel;
+                }
                 /* q^sun_{j,u}: species mixture of the source's phase function */
                 for (int u = 0; u < nd; ++u) {
                     double acc = 0.0;
                     for (int sp = 0; sp < S; ++sp) {
                         double w = mus[j] > 0.0 ? mu_s[(size_t)sp * na + j] / mus[j] : 1.0 / S;
-                        acc += w * r->q_sun[sp * nd + u];
+                        acc += w * qsun_j[sp * nd + u];
                     }
                     qs[u] = acc;
                 }
-                qi = r->q_iso;
                 orc_source_weights(d, r, mus, qi, nd, ch, 0, mus[j], ci, &r->z_iso[j]);
                 orc_source_weights(d, r, mus, qs, nd, ch, 0, mus[j], cs, &r->z_sun[j]);
             } else {
@@ -795,6 +898,10 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                 ndir = ngd;
                 for (int k = 0; k < ngd; ++k) orc_gnd_chain(d, r, mue, j - na, k, &ch[k]);
                 qi = r->q_lamb;
+                if (orc_select(d, r, mus, ch, ngd, r->mu_s_lamb, kept) > 0) {
+                    orc_partition_kept(d, r, g, 1, kept, qsel, NULL);
+                    qi = qsel;
+                }
                 for (int k = 0; k < ngd; ++k) qs[k] = r->q_lamb[k];
                 orc_source_weights(d, r, mus, qi, ngd, ch, 1, r->mu_s_lamb, ci, &r->z_iso[j]);
                 for (int k = 0; k < ngd; ++k) cs[k] = ci[k];
@@ -821,6 +928,7 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
             t_cnt[j] = cnt;
         }
         free(ch);
+        free(qsun_sel);
     }
 
     /* gather into row-major order (stable: by source, then direction) */
@@ -994,6 +1102,18 @@ void orc_free(orc_result *r) {
 double orc_tau_segment(const orc_desc *d, const double *mu_e, const double *P, const double *V, double tend,
                        double lphys) {
     return orc_dda(d, mu_e, P, V, tend, lphys, NULL, NULL);
+}
+
+/* Quadrature weights of one source over a kept set of directions (coupling
+ * selection): ground = 0 for the atmospheric set (qi[n_dirs], qsun[S][n_dirs]),
+ * 1 for the ground set (qi[n_gdirs]).  Returns the number of directions. */
+int orc_partition(const orc_desc *d, const double *g, int ground, const int *kept, double *qi, double *qsun) {
+    orc_result *r = calloc(1, sizeof(orc_result));
+    orc_make_dirs(d, r);
+    int n = ground ? r->n_gdirs : r->n_dirs;
+    orc_partition_kept(d, r, g, ground, kept, qi, qsun);
+    free(r);
+    return n;
 }
 
 /* Fibonacci lattice point m of M (unit vector). */

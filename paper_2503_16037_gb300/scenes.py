@@ -47,6 +47,7 @@ class Scene:
     R: int = 1
     M: int = 8192
     coupling: int = 1
+    c_min: float = 0.0        # coupling threshold of the scattering graph (0: full stencil)
     precision: int = 0        # 0 FP64, 1 FP32 + FP64 refinement
     name: str = "scene"
 

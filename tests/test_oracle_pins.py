@@ -443,6 +443,142 @@ def test_p10_cells_converge_to_spherical_voronoi():
 
 
 # --------------------------------------------------------------------------
+# P11: coupling selection (scattering graph with C > c_min, Sec. 2) and the
+# re-partition of the lattice among the kept directions
+
+def _unit_dirs(r, h):
+    u = r["dirs"] * np.array(h)
+    return u / np.linalg.norm(u, axis=1, keepdims=True)
+
+
+def test_p11_threshold_below_every_coupling_is_the_full_stencil():
+    """Every voxel scatters and the surface reflects, so every coupling is
+    positive: a threshold below all of them keeps the full stencil.  With
+    non-scattering voxels the zero couplings go at any c_min > 0."""
+    sc = scenes.make_random(9, 8, 5, seed=21, S=2, R=2, M=1024, zero_frac=0.0)
+    r0 = O.run(sc)
+    r1 = O.run(sc.replace(c_min=1e-300))
+    for k in ("slot_val", "slot_valsun", "x", "rad"):
+        assert np.array_equal(r0[k], r1[k]), k
+    sz = scenes.make_random(9, 8, 5, seed=21, S=1, R=2, M=1024, zero_frac=0.1)
+    z0, z1 = O.run(sz, flags=O.NO_SOLVE), O.run(sz.replace(c_min=1e-300), flags=O.NO_SOLVE)
+    assert (z1["slot_val"] != 0).sum() < (z0["slot_val"] != 0).sum()
+
+
+def test_p11_partition_with_every_direction_kept_is_the_global_quadrature():
+    sc = scenes.make_random(5, 5, 3, seed=1, S=2, R=2, M=4096)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    qi, qs = O.partition(sc, np.ones(r["n_dirs"], dtype=int))
+    assert np.array_equal(qi, r["q_iso"]) and np.array_equal(qs, r["q_sun"])
+    assert np.array_equal(O.partition(sc, np.ones(r["n_gdirs"], dtype=int), ground=True), r["q_lamb"])
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_p11_partition_conserves_the_sphere(R):
+    """Dropped cells hand all their points to kept directions: the weights
+    still sum to one, dropped directions get nothing, kept cells only grow."""
+    sc = scenes.make_random(5, 5, 3, seed=2, S=3, R=R, M=4096)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    rng = np.random.default_rng(R)
+    for frac in (0.2, 0.6, 0.95):
+        kept = rng.random(r["n_dirs"]) > frac
+        kept[rng.integers(r["n_dirs"])] = True
+        qi, qs = O.partition(sc, kept.astype(int))
+        assert abs(qi.sum() - 1) < 1e-14
+        np.testing.assert_allclose(qs.sum(axis=1), 1.0, atol=1e-13)
+        assert not qi[~kept].any() and not qs[:, ~kept].any()
+        assert np.all(qi[kept] >= r["q_iso"][kept]) and np.all(qs[:, kept] >= r["q_sun"][:, kept])
+        kg = rng.random(r["n_gdirs"]) > frac
+        kg[rng.integers(r["n_gdirs"])] = True
+        ql = O.partition(sc, kg.astype(int), ground=True)
+        assert abs(ql.sum() - 1) < 1e-14 and not ql[~kg].any() and np.all(ql[kg] >= r["q_lamb"][kg])
+    none = O.partition(sc, np.zeros(r["n_dirs"], dtype=int))
+    assert not none[0].any() and not none[1].any()
+
+
+def test_p11_kept_cells_converge_to_the_spherical_voronoi_of_the_kept_set():
+    sv_mod = pytest.importorskip("scipy.spatial")
+    h = (0.05, 0.05, 0.1)
+    sc = scenes.make_layered(5, 5, 3, [0.1] * 3, [0.5], R=2, h=h, M=8192)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    kept = np.random.default_rng(11).random(r["n_dirs"]) < 0.4
+    u = _unit_dirs(r, h)[kept]
+    area = sv_mod.SphericalVoronoi(u, radius=1.0).calculate_areas() / (4 * math.pi)
+    e8 = np.abs(O.partition(sc, kept.astype(int))[0][kept] - area).max()
+    eb = np.abs(O.partition(sc.replace(M=262144), kept.astype(int))[0][kept] - area).max()
+    assert eb < 2.5e-4 and eb < e8
+
+
+def test_p11_kept_set_of_a_homogeneous_medium_is_the_short_directions():
+    """In a homogeneous medium C = mu_s / |r' - r|, so a source keeps exactly
+    the directions shorter than mu_s / c_min (plus those leaving the domain
+    without a receiver)."""
+    h = (0.1, 0.08, 0.12)
+    mus = 1.3
+    sc = scenes.make_layered(7, 6, 6, [2.0] * 6, [mus / 2.0], g=(0.5,), albedo=0.3, R=2, h=h, M=2048)
+    r0 = O.run(sc, flags=O.NO_SOLVE)
+
+    def length(v):  # physical length of a lattice vector, summed in x, y, z order
+        p = [v[0] * h[0], v[1] * h[1], v[2] * h[2]]
+        return math.sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2])
+
+    L = np.array([length(v) for v in r0["dirs"].tolist()])
+    # the threshold equals the coupling of the sixth-shortest length exactly:
+    # those directions go too (the graph keeps C > c_min)
+    c_min = mus / np.unique(L)[5]
+    r = O.run(sc.replace(c_min=c_min), flags=O.NO_SOLVE)
+    nx, ny = sc.nx, sc.ny
+    j = (3 * ny + 2) * nx + 3  # an interior source: every chain has a voxel receiver
+    want = {u for u in range(r["n_dirs"]) if mus / L[u] > c_min}
+    assert 0 < len(want) < r["n_dirs"]
+    for w in ("slot_dep", "slot_depsun"):
+        sel = (r["slot_col"] == j) & (r[w] != 0)
+        assert set(r["slot_dir"][sel].tolist()) == want, w
+
+
+def test_p11_nonzero_couplings_shrink_as_the_threshold_grows():
+    sc = scenes.make_random(8, 7, 5, seed=22, S=2, R=2, M=1024)
+    prev = None
+    for c_min in (0.0, 1.0, 3.0, 8.0, 1e300):
+        r = O.run(sc.replace(c_min=c_min), flags=O.NO_SOLVE)
+        nz = r["slot_val"] != 0
+        key = set(zip(r["slot_row"][nz].tolist(), r["slot_col"][nz].tolist(), r["slot_dir"][nz].tolist(),
+                      r["slot_k"][nz].tolist()))
+        if prev is not None:
+            assert key < prev
+        prev = key
+    # only chains without a receiver are left: they deposit on their source
+    assert all(row == col for row, col, _, _ in prev)
+
+
+@pytest.mark.parametrize("R,sza,saa", [(1, 35.0, 10.0), (2, 62.0, 130.0)])
+def test_p11_energy_conservation_with_selection(R, sza, saa):
+    """P5 with c_min > 0: with omega = 1 and a black surface every photon
+    leaves through the TOA or reaches the ground, as long as each source keeps
+    a direction (here: every axis neighbour stays coupled)."""
+    nx, ny, nz = 6, 5, 7
+    h = (0.1, 0.08, 0.12)
+    me = np.random.default_rng(5).uniform(0.5, 2.0, nz)
+    c_min = 0.99 * me.min() / max(h)
+    sc = scenes.make_layered(nx, ny, nz, me, [1.0], g=(0.6,), albedo=0.0, R=R, sza=sza, saa=saa,
+                             vza=10, h=h, M=2048).replace(c_min=c_min)
+    r = O.run(sc, gmres_tol=1e-15)
+    full = O.run(sc.replace(c_min=0.0), flags=O.NO_SOLVE)
+    assert (r["slot_val"] != 0).sum() < (full["slot_val"] != 0).sum()
+    na = r["n_atm"]
+    mu0 = math.cos(math.radians(sza))
+    incident = nx * ny * mu0 * sc.hx * sc.hy
+    escape = float(r["e1"] @ r["esc_sun"] + r["x"] @ r["esc_iso"])
+    direct_ground = float(mu0 * sc.hx * sc.hy * r["tsun"][na:].sum())
+    row, col = r["slot_row"], r["slot_col"]
+    gnd = row >= na
+    deposited_ground = float((r["slot_depsun"][gnd] * r["e1"][col[gnd]]).sum()
+                             + (r["slot_dep"][gnd] * r["x"][col[gnd]]).sum())
+    total = escape + direct_ground + deposited_ground
+    assert abs(total - incident) <= 1e-12 * incident
+
+
+# --------------------------------------------------------------------------
 # Emission toward the instrument (final radiance sum of Sec. 2)
 
 def test_isotropic_emission_identity():
