@@ -902,7 +902,9 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                     orc_partition_kept(d, r, g, 1, kept, qsel, NULL);
                     qi = qsel;
                 }
-                for (int k = 0; k < ngd; ++k) qs[k] = r->q_lamb[k];
+                /* Lambertian re-emission forgets the incoming direction: the
+                 * sun-lit and the diffusely lit ground share one quadrature */
+                for (int k = 0; k < ngd; ++k) qs[k] = qi[k];
                 orc_source_weights(d, r, mus, qi, ngd, ch, 1, r->mu_s_lamb, ci, &r->z_iso[j]);
                 for (int k = 0; k < ngd; ++k) cs[k] = ci[k];
                 r->z_sun[j] = r->z_iso[j];

@@ -551,6 +551,18 @@ def test_p11_nonzero_couplings_shrink_as_the_threshold_grows():
     assert all(row == col for row, col, _, _ in prev)
 
 
+def test_p11_ground_sources_share_one_quadrature_for_sun_and_diffuse_light():
+    """A Lambertian source re-emits without memory of the incoming direction,
+    so its sun-lit and diffusely lit deposits are equal, with and without
+    coupling selection."""
+    sc = scenes.make_random(9, 8, 5, seed=23, S=2, R=2, M=1024, albedo=0.4)
+    for c_min in (0.0, 3.0, 8.0):
+        r = O.run(sc.replace(c_min=c_min), flags=O.NO_SOLVE)
+        g = r["slot_col"] >= r["n_atm"]
+        assert np.array_equal(r["slot_depsun"][g], r["slot_dep"][g])
+        assert np.array_equal(r["esc_sun"][r["n_atm"]:], r["esc_iso"][r["n_atm"]:])
+
+
 @pytest.mark.parametrize("R,sza,saa", [(1, 35.0, 10.0), (2, 62.0, 130.0)])
 def test_p11_energy_conservation_with_selection(R, sza, saa):
     """P5 with c_min > 0: with omega = 1 and a black surface every photon
