@@ -256,6 +256,19 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     E_i = e1_i Theta_i(s0 . v) and the ground's e1_c.  get(TURSCA_F_VAL)
  *     and tursca_adjoint return TURSCA_E_STATE after such an assembly.
  *     Changing the value invalidates the current assembly.
+ *   TURSCA_OPT_COUPLING_MIN: c_min >= 0 of the scattering graph (Sec. 2: the
+ *     graph keeps the couplings C of Eq. scatt_coup above c_min; default 0,
+ *     the full stencil).  With c_min > 0 a chain whose first receiver has
+ *     C <= c_min gets the weight 0 (its slots stay in K), chains without a
+ *     receiver are always kept, and each source re-draws its quadrature cells
+ *     (Eq. F_term_phase) among the directions it keeps: a lattice point joins
+ *     the kept direction closest to it (exact ties to the lower index).  The
+ *     decision is taken in FP64 in every precision.  The first assembly with
+ *     c_min > 0 ranks the lattice (M x n_dirs bytes; M <= 2^20, else
+ *     TURSCA_E_UNSUPPORTED) and allocates two weight planes per direction
+ *     (2 x n_dirs x nodes of the haloed layout, compute type).
+ *     tursca_adjoint returns TURSCA_E_UNSUPPORTED after such an assembly.
+ *     Changing the value invalidates the current assembly.
  */
 enum {
     TURSCA_OPT_RESIDUAL_FP64 = 1,
@@ -263,7 +276,8 @@ enum {
     TURSCA_OPT_STAGE_VALUES = 3,
     TURSCA_OPT_L2_RESIDENT = 4,
     TURSCA_OPT_GATHER_TILE = 5,
-    TURSCA_OPT_SINGLE_SCATTER = 6
+    TURSCA_OPT_SINGLE_SCATTER = 6,
+    TURSCA_OPT_COUPLING_MIN = 7
 };
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 
@@ -277,7 +291,8 @@ size_t tursca_scene_device_bytes(const tursca_scene *scene);
  * stream around each launch of the hot kernels (profiling only). */
 typedef struct {
     char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb",
-                           "gmres_orth" (both Gram-Schmidt passes of one Arnoldi step) */
+                           "gmres_orth" (both Gram-Schmidt passes of one Arnoldi step),
+                           "select" (coupling selection) */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;

@@ -19,8 +19,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtursca_gb.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "kernels_adjoint.cu", "api.cu", "noalloc.cu", "server.cpp"]
-HEADERS = ["graph.h", "kern.h", "stage.cuh", "asm_util.cuh"]
+SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "kernels_adjoint.cu",
+           "kernels_select.cu", "api.cu", "noalloc.cu", "server.cpp"]
+HEADERS = ["graph.h", "kern.h", "stage.cuh", "asm_util.cuh", "first_order.h", "select.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,6 +12,7 @@
 #include "graph.h"
 #include "first_order.h"
 #include "kern.h"
+#include "select.h"
 #include "tursca.h"
 
 namespace {
@@ -134,6 +135,12 @@ struct tursca_scene {
     int l2_resident = 0;   // 1: the solves keep the values of K in the persisting part of L2
     int gather_tile = 1;   // 1: FP32 passes gather from a shared-memory tile
     int single = 0;        // 1: the next assembly takes the first scattering order only
+    // coupling selection (c_min > 0): lattice rankings, per-scene buffers and
+    // the weight planes of every (source, direction)
+    double c_min = 0.0;
+    bool sel_ready = false, sel_asm = false;
+    tk::SelP selp{};
+    void *w_iso = nullptr, *w_sun = nullptr;
     bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
@@ -149,9 +156,10 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb", "gmres_orth"};
-constexpr int kNProf = 7;
-enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6 };
+const char *const kProfNames[] = {"spmv",   "resid64", "assemble_rows", "assemble_pre",
+                                  "render", "cheb",    "gmres_orth",    "select"};
+constexpr int kNProf = 8;
+enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7 };
 
 // returns the index of the pair, or -1 when profiling is off
 int prof_begin(tursca_scene *sc, int cat) {
@@ -1381,6 +1389,94 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     return TURSCA_OK;
 }
 
+// Coupling selection: rank the directions by decreasing cosine to every
+// lattice point (exact ties to the lower index, as in the partition), group
+// the upper-hemisphere points by ground cell with their cosine weights, and
+// allocate the per-scene buffers and the weight planes.  Once per scene.
+tursca_status ensure_select(tursca_scene *sc) {
+    if (sc->sel_ready) return TURSCA_OK;
+    const tg::Graph &G = sc->G;
+    const int M = G.M, nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size();
+    if (M > (1 << 20) || nd > tk::kSelMaxDir || ngd > tk::kSelMaxDir)
+        return fail(sc, TURSCA_E_UNSUPPORTED, "coupling selection needs at most 2^20 lattice points");
+    auto ranked = [](const std::array<double, 3> &s, const std::vector<std::array<double, 3>> &uh,
+                     unsigned char *out) {
+        const int n = (int)uh.size();
+        std::vector<std::pair<double, int>> c(n);
+        for (int u = 0; u < n; ++u) c[u] = {-(uh[u][0] * s[0] + uh[u][1] * s[1] + uh[u][2] * s[2]), u};
+        std::sort(c.begin(), c.end());
+        for (int u = 0; u < n; ++u) out[u] = (unsigned char)c[u].second;
+    };
+    std::vector<unsigned char> rank((size_t)M * nd);
+    for (int p = 0; p < M; ++p) {
+        ranked(G.lattice[G.cell_order[p]], G.uhat, &rank[(size_t)p * nd]);
+        if (rank[(size_t)p * nd] != G.cell[G.cell_order[p]]) return fail(sc, TURSCA_E_INVALID, "lattice ranking");
+    }
+    std::vector<std::array<double, 3>> gh(ngd);
+    for (int k = 0; k < ngd; ++k) gh[k] = G.gdirs[k].uhat;
+    std::vector<int> gcell, upts;
+    std::vector<double> gzsum(ngd, 0.0);
+    double gztot = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const auto &pt = G.lattice[m];
+        if (!(pt[2] > 0.0)) continue;
+        int best = 0;
+        double bc = -2.0;
+        for (int k = 0; k < ngd; ++k) {
+            const double c = gh[k][0] * pt[0] + gh[k][1] * pt[1] + gh[k][2] * pt[2];
+            if (c > bc) {
+                bc = c;
+                best = k;
+            }
+        }
+        upts.push_back(m);
+        gcell.push_back(best);
+        gzsum[best] += pt[2];
+        gztot += pt[2];
+    }
+    const int nup = (int)upts.size();
+    std::vector<int> gstart(ngd + 1, 0);
+    for (int i = 0; i < nup; ++i) gstart[gcell[i] + 1]++;
+    for (int k = 0; k < ngd; ++k) gstart[k + 1] += gstart[k];
+    std::vector<int> fill(gstart.begin(), gstart.end() - 1), order(nup);
+    for (int i = 0; i < nup; ++i) order[fill[gcell[i]]++] = i;
+    std::vector<unsigned char> grank((size_t)std::max(nup, 1) * std::max(ngd, 1));
+    std::vector<double> gz(std::max(nup, 1));
+    for (int p = 0; p < nup; ++p) {
+        const auto &pt = G.lattice[upts[order[p]]];
+        ranked(pt, gh, &grank[(size_t)p * ngd]);
+        gz[p] = pt[2];
+    }
+    tk::SelP &q = sc->selp;
+    unsigned char *d_rank = nullptr, *d_grank = nullptr;
+    int *d_gstart = nullptr;
+    double *d_gz = nullptr, *d_gzsum = nullptr;
+    CK(upload(sc, sc->allocs, d_rank, rank.data(), rank.size()), "upload rank");
+    CK(upload(sc, sc->allocs, d_grank, grank.data(), grank.size()), "upload rank");
+    CK(upload(sc, sc->allocs, d_gstart, gstart.data(), gstart.size() * sizeof(int)), "upload ground cells");
+    CK(upload(sc, sc->allocs, d_gz, gz.data(), gz.size() * sizeof(double)), "upload ground cells");
+    CK(upload(sc, sc->allocs, d_gzsum, gzsum.data(), gzsum.size() * sizeof(double)), "upload ground cells");
+    CK(dalloc(sc->allocs, q.hgpt, (size_t)sc->d.n_species * M * sizeof(double)), "alloc select");
+    CK(dalloc(sc->allocs, q.musmax_bits, sizeof(unsigned long long)), "alloc select");
+    q.dmax = std::max(nd, ngd);
+    const size_t plane = (size_t)grid_c(sc).npad * sc->es;
+    CK(dalloc(sc->allocs, sc->w_iso, q.dmax * plane), "alloc select weights");
+    CK(dalloc(sc->allocs, sc->w_sun, q.dmax * plane), "alloc select weights");
+    CK(cudaMemsetAsync(sc->w_iso, 0, q.dmax * plane, sc->st), "memset select weights");
+    CK(cudaMemsetAsync(sc->w_sun, 0, q.dmax * plane, sc->st), "memset select weights");
+    CK(cudaStreamSynchronize(sc->st), "sync");  // the host tables die here
+    q.M = M;
+    q.n_up = nup;
+    q.rank = d_rank;
+    q.grank = d_grank;
+    q.gcell_start = d_gstart;
+    q.gz = d_gz;
+    q.gzsum = d_gzsum;
+    q.gztot = gztot;
+    sc->sel_ready = true;
+    return TURSCA_OK;
+}
+
 tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom) {
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!geom) return fail(sc, TURSCA_E_INVALID, "geometry is null");
@@ -1448,6 +1544,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         CK(cudaMemsetAsync(sc->gsun, 0, (size_t)sc->G.n_atm * sc->es, sc->st), "memset gsun");
         CK(cudaGetLastError(), "assemble launch");
         sc->single_asm = sc->assembled = true;
+        sc->sel_asm = false;
         sc->solved = sc->rendered = false;
         return TURSCA_OK;
     }
@@ -1458,12 +1555,36 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     else
         tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, &sc->launches);
     prof_end(sc, p0);
-    int p1 = prof_begin(sc, P_ROWS);
-    if (sc->d.precision == TURSCA_FP64)
-        tk::launch_assemble_rows<double>(sc->st, g, gp, field_p<double>(sc), vc, &sc->launches);
-    else
-        tk::launch_assemble_rows<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
-    prof_end(sc, p1);
+    if (sc->c_min > 0.0) {
+        tursca_status e = ensure_select(sc);
+        if (e) return e;
+        tk::SelP q = sc->selp;
+        q.c_min = sc->c_min;
+        int ps = prof_begin(sc, P_SEL);
+        if (sc->d.precision == TURSCA_FP64)
+            tk::launch_select<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, q, (double *)sc->w_iso,
+                                      (double *)sc->w_sun, &sc->launches);
+        else
+            tk::launch_select<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, q, (float *)sc->w_iso,
+                                     (float *)sc->w_sun, &sc->launches);
+        prof_end(sc, ps);
+        int p1 = prof_begin(sc, P_ROWS);
+        if (sc->d.precision == TURSCA_FP64)
+            tk::launch_assemble_rows_sel<double>(sc->st, g, gp, field_p<double>(sc), vc, (const double *)sc->w_iso,
+                                                 (const double *)sc->w_sun, &sc->launches);
+        else
+            tk::launch_assemble_rows_sel<float>(sc->st, g, gp, field_p<float>(sc), vc, (const float *)sc->w_iso,
+                                                (const float *)sc->w_sun, &sc->launches);
+        prof_end(sc, p1);
+    } else {
+        int p1 = prof_begin(sc, P_ROWS);
+        if (sc->d.precision == TURSCA_FP64)
+            tk::launch_assemble_rows<double>(sc->st, g, gp, field_p<double>(sc), vc, &sc->launches);
+        else
+            tk::launch_assemble_rows<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
+        prof_end(sc, p1);
+    }
+    sc->sel_asm = sc->c_min > 0.0;
     CK(cudaGetLastError(), "assemble launch");
     sc->assembled = true;
     sc->single_asm = false;
@@ -1510,6 +1631,7 @@ tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_a
     if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
     if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
     if (sc->single_asm) return fail(sc, TURSCA_E_STATE, "the adjoint needs a multiple-scattering assembly");
+    if (sc->sel_asm) return fail(sc, TURSCA_E_UNSUPPORTED, "the adjoint does not cover coupling selection");
     tursca_status e = ensure_adjoint(sc);
     if (e) return e;
     if (sc->d.precision == TURSCA_FP64) return do_adjoint<double>(sc, dJ_dL, dJ_dmu_abs);
@@ -1631,6 +1753,14 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
             sc->l2_resident = (int)value;
             return TURSCA_OK;
         }
+        case TURSCA_OPT_COUPLING_MIN:
+            if (!(value >= 0.0) || !std::isfinite(value))
+                return fail(sc, TURSCA_E_INVALID, "the coupling threshold must be finite and >= 0");
+            if (value != sc->c_min) {
+                sc->c_min = value;
+                sc->assembled = sc->solved = sc->rendered = false;
+            }
+            return TURSCA_OK;
         case TURSCA_OPT_SINGLE_SCATTER:
             if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "single scatter must be 0 or 1");
             if ((int)value != sc->single) {

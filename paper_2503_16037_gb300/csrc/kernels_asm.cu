@@ -23,6 +23,7 @@
 #include "stage.cuh"
 #include "asm_util.cuh"
 #include "first_order.h"
+#include "select.h"
 
 namespace tk {
 
@@ -353,8 +354,12 @@ constexpr int kAsmW = TK_ASM_W;
 #ifndef TK_ASM_MINB
 #define TK_ASM_MINB 4
 #endif
-template <typename T, int S>
-__global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
+// kSel: coupling selection, the weights q c of every (source, direction) come
+// from the planes wsi / wss (haloed, one per direction) instead of the
+// global quadrature and the source's normaliser.
+template <typename T, int S, bool kSel>
+__global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB)
+    k_asm(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const T *__restrict__ wsi, const T *__restrict__ wss) {
     __shared__ T sh[kAsmW][8][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
@@ -439,7 +444,11 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB) k_asm(GridC g, GraphP
                 P = split * fast_exp_neg<T>(tpre + thit);
             }
             T Wi, Ws;
-            if (!gsrc) {
+            if constexpr (kSel) {
+                const size_t o = (size_t)dir * g.npad + j;
+                Wi = __ldg(wsi + o);
+                Ws = gsrc ? Wi : __ldg(wss + o);
+            } else if (!gsrc) {
                 T qs = T(0);
 #pragma unroll
                 for (int sp = 0; sp < S; ++sp) qs += __ldg(f.wsp_h + (size_t)sp * g.npad + j) * qsun[sp];
@@ -524,10 +533,23 @@ void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, con
                           long long *launches) {
     const int nb = (g.nz + 1) * g.gpl;
     switch (g.S) {  // the species count as a compile-time constant
-        case 1: k_asm<T, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        case 2: k_asm<T, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        case 3: k_asm<T, 3><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        default: k_asm<T, 4><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+        case 1: k_asm<T, 1, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 2: k_asm<T, 2, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 3: k_asm<T, 3, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        default: k_asm<T, 4, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+    }
+    if (launches) *launches += 1;
+}
+
+template <typename T>
+void launch_assemble_rows_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                              const ViewC &vc, const T *w_iso, const T *w_sun, long long *launches) {
+    const int nb = (g.nz + 1) * g.gpl;
+    switch (g.S) {
+        case 1: k_asm<T, 1, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        case 2: k_asm<T, 2, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        case 3: k_asm<T, 3, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        default: k_asm<T, 4, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
     }
     if (launches) *launches += 1;
 }
@@ -549,6 +571,8 @@ void launch_assemble_direct(cudaStream_t st, const GridC &g, const FieldP<T> &f,
 #define INST(T)                                                                                                   \
     template void launch_assemble_direct<T>(cudaStream_t, const GridC &, const FieldP<T> &, const ViewC &,       \
                                             const ViewP &, long long *);                                          \
+    template void launch_assemble_rows_sel<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,     \
+                                              const ViewC &, const T *, const T *, long long *);                  \
     template void launch_assemble_pre<T>(cudaStream_t const[4], cudaEvent_t const[5], const GridC &,              \
                                          const GraphP &, const FieldP<T> &, const ViewC &, const ViewP &,         \
                                          long long *);                                                            \

@@ -1,0 +1,53 @@
+// Coupling selection: the scattering graph keeps the edges whose coupling
+// C (Eq. scatt_coup) exceeds c_min (Sec. 2), and each source re-draws its
+// quadrature cells (Eq. F_term_phase, Fibonacci lattice of Sec. 3) among the
+// directions it keeps.  The chains of the voxel graph keep their slots; a
+// dropped chain gets the weight 0.
+//
+//   kept(j, u)  = the chain has no receiver, or C(j, n1(j, u)) > c_min
+//   q'(j, u)    = share of the lattice whose closest kept direction of j is u
+//                 (largest cosine, exact ties to the lowest index); ground
+//                 sources: cosine-weighted share of the upper hemisphere
+//   W(j, u)     = q'(j, u) c(j, u), with the routing weight
+//                 c = C sum_v q'_v / sum_v q'_v C_v over the chains of j that
+//                 have a receiver (1 without a receiver, without coupling, or
+//                 when that sum is 0); the same for the sun weights q'^sun
+//
+// The decision C > c_min is taken in FP64 from the scene's fields (species
+// sums in FP64) in every precision.
+#pragma once
+
+#include "kern.h"
+
+namespace tk {
+
+constexpr int kSelMaxDir = 128;  // atmospheric (and ground) directions a source can have
+
+struct SelP {
+    double c_min;
+    int M;                           // lattice points
+    int n_up;                        // lattice points in the upper hemisphere
+    int dmax;                        // planes of the weight tables: max(nd, ngd)
+    const unsigned char *rank;       // [M][nd] directions by decreasing cosine to each point (cell order)
+    const unsigned char *grank;      // [n_up][ngd] ground directions, upper points in ground-cell order
+    const int *gcell_start;          // [ngd + 1]
+    const double *gz;                // [n_up] cosine weight (z) of each upper point
+    const double *gzsum;             // [ngd] cosine weight of each ground cell
+    double gztot;                    // cosine weight of the upper hemisphere
+    double *hgpt;                    // [S][M] HG toward each lattice point (cell order)
+    unsigned long long *musmax_bits; // max over voxels of the FP64 total scattering coefficient
+};
+
+// Weights W of every (source, direction) for the current fields and
+// geometry: w_iso, w_sun [dmax][npad] haloed (the ground sources' planes in
+// the ground layer).  Needs the phase tables of the assembly (cell sums).
+template <typename T>
+void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                   const ViewP &vp, const SelP &sp, T *w_iso, T *w_sun, long long *launches);
+
+// The edge kernel with the weights read from w_iso / w_sun.
+template <typename T>
+void launch_assemble_rows_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                              const ViewC &vc, const T *w_iso, const T *w_sun, long long *launches);
+
+}  // namespace tk

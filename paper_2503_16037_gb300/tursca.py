@@ -206,6 +206,7 @@ OPT_STAGE_VALUES = 3
 OPT_L2_RESIDENT = 4
 OPT_GATHER_TILE = 5
 OPT_SINGLE_SCATTER = 6
+OPT_COUPLING_MIN = 7
 
 
 def tursca_set_option(scene, option: int, value: float):
@@ -299,6 +300,8 @@ class Runner:
         self.stats = tursca_graph_info(self.desc)
         self.geom = geometry(sc)
         tursca_build_graph(self.handle)
+        if getattr(sc, "c_min", 0.0) > 0.0:
+            tursca_set_option(self.handle, OPT_COUPLING_MIN, sc.c_min)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.rad = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)
         self.refl = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)

@@ -1,0 +1,118 @@
+"""GPU coupling selection (c_min > 0) against the FP64 oracle.
+
+The selection decision C > c_min is taken in FP64 on both sides from the same
+inputs (the oracle gets the FP32 scene's fields rounded to FP32), so the set
+of zeroed chains must agree exactly.  Values: FP64 1e-10 relative (as the full
+path), FP32 + refinement 1e-4 relative on every radiance, K entries at the
+FP32-derived bound of the full path (2e-5 relative).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2503_16037_gb300 import scenes
+from paper_2503_16037_gb300 import tursca as T
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2503_16037_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def fp32_inputs(sc):
+    """The scene with its fields rounded to FP32 (what an FP32 scene sees)."""
+    return sc.replace(mu_a=sc.mu_a.astype(np.float32).astype(np.float64),
+                      mu_s=sc.mu_s.astype(np.float32).astype(np.float64))
+
+
+def run_gpu(sc, precision, rtol):
+    rn = T.Runner(sc, precision)
+    mu_a, mu_s = rn.fields("cuda")
+    rn.set_medium(mu_a, mu_s)
+    rn.assemble()
+    rn.solve(rtol=rtol)
+    rad, _ = rn.render()
+    torch.cuda.synchronize()
+    return rn, rad.cpu().numpy().astype(np.float64)
+
+
+def gpu_vs_oracle_slots(rn, r):
+    st = rn.stats
+    rp = rn.get(T.F_ROW_PTR, st.n_nodes + 1, torch.int32)
+    col = rn.get(T.F_COL, st.nnz, torch.int32)
+    dr = rn.get(T.F_SLOT_DIR, st.nnz, torch.int16)
+    k = rn.get(T.F_SLOT_K, st.nnz, torch.int8)
+    val = rn.get(T.F_VAL, st.nnz, rn.dtype)
+    rows = np.repeat(np.arange(st.n_nodes), np.diff(rp))
+    kg = np.stack([rows, col, dr.astype(np.int64), k.astype(np.int64)], 1)
+    ko = np.stack([r["slot_row"], r["slot_col"], r["slot_dir"], r["slot_k"]], 1)
+    ig = np.lexsort(kg.T[::-1])
+    io = np.lexsort(ko.T[::-1])
+    assert np.array_equal(kg[ig], ko[io])
+    return val[ig].astype(np.float64), r["slot_val"][io]
+
+
+CASES = {
+    "random_R2_cmin3": (lambda: scenes.make_random(21, 19, 9, seed=7, S=2, R=2, M=2048), 3.0),
+    "random_R2_cmin8": (lambda: scenes.make_random(21, 19, 9, seed=7, S=2, R=2, M=2048), 8.0),
+    "random_R1_3species": (lambda: scenes.make_random(13, 11, 7, seed=8, S=3, R=1, M=1024, sza=20.0, vza=55.0), 8.0),
+    "random_4species": (lambda: scenes.make_random(12, 11, 6, seed=10, S=4, R=2, M=1024), 5.0),
+    "plume_small": (lambda: scenes.make_plume(nx=24, ny=20, nz=12), 2.0),
+    "random_R2_all_dropped": (lambda: scenes.make_random(12, 11, 6, seed=11, S=2, R=2, M=1024), 1e30),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_selection_parity(name, prec):
+    make, c_min = CASES[name]
+    sc = make().replace(c_min=c_min)
+    ref = sc if prec == "fp64" else fp32_inputs(sc)
+    r = O.run(ref)
+    full = O.run(ref.replace(c_min=0.0), flags=O.NO_SOLVE)
+    dropped = (full["slot_val"] != 0).sum() - (r["slot_val"] != 0).sum()
+    assert dropped > 0
+    rn, rad = run_gpu(sc, T.FP64 if prec == "fp64" else T.FP32_REFINE, 1e-13 if prec == "fp64" else 1e-10)
+    vg, vo = gpu_vs_oracle_slots(rn, r)
+    # the same chains are zeroed on both sides
+    assert np.array_equal(vg == 0, vo == 0)
+    kt = 1e-11 if prec == "fp64" else 2e-5
+    floor = (1e-14 if prec == "fp64" else 1e-6) * vo.max()
+    assert (np.abs(vg - vo) / np.maximum(np.abs(vo), floor)).max() < kt
+    st = rn.stats
+    s = rn.get(T.F_S, st.n_nodes, rn.dtype)
+    assert np.abs(s - r["s"]).max() <= kt * np.abs(r["s"]).max()
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    err = (np.abs(rad - r["rad"]) / np.abs(r["rad"])).max()
+    print("%s %s: %d chains' slots zeroed, radiance max rel err %.2e" % (name, prec, dropped, err))
+    assert err < tol
+
+
+def test_selection_toggle_and_adjoint():
+    """Switching the threshold on and off on one scene: the full path gives the
+    same radiance bit for bit afterwards; the adjoint is refused after an
+    assembly with c_min > 0."""
+    sc = scenes.make_plume(nx=24, ny=20, nz=12)
+    rn, full0 = run_gpu(sc, T.FP32_REFINE, 1e-10)
+    mu_a, mu_s = rn.fields("cuda")
+    T.tursca_set_option(rn.handle, T.OPT_COUPLING_MIN, 0.5)
+    rn.run(mu_a, mu_s, rtol=1e-10)
+    sel = rn.rad.cpu().numpy().astype(np.float64)
+    with pytest.raises(T.TurscaError) as e:
+        rn.adjoint(torch.ones_like(rn.rad))
+    assert e.value.status == T.E_UNSUPPORTED
+    T.tursca_set_option(rn.handle, T.OPT_COUPLING_MIN, 0.0)
+    rn.run(mu_a, mu_s, rtol=1e-10)
+    torch.cuda.synchronize()
+    full1 = rn.rad.cpu().numpy().astype(np.float64)
+    assert np.array_equal(full0, full1)
+    assert not np.array_equal(sel, full0)
+    with pytest.raises(T.TurscaError) as e:
+        T.tursca_set_option(rn.handle, T.OPT_COUPLING_MIN, -1.0)
+    assert e.value.status == T.E_INVALID
