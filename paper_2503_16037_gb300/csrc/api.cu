@@ -1390,9 +1390,11 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
 }
 
 // Coupling selection: rank the directions by decreasing cosine to every
-// lattice point (exact ties to the lower index, as in the partition), group
-// the upper-hemisphere points by ground cell with their cosine weights, and
-// allocate the per-scene buffers and the weight planes.  Once per scene.
+// lattice point (exact ties to the lower index, as in the partition), order
+// the points of every cell by their rankings (so the points that a dropped
+// cell hands to one kept direction sit together), do the same for the
+// upper-hemisphere points and the ground cells, and allocate the per-scene
+// buffers and the weight planes.  Once per scene.
 tursca_status ensure_select(tursca_scene *sc) {
     if (sc->sel_ready) return TURSCA_OK;
     const tg::Graph &G = sc->G;
@@ -1407,51 +1409,79 @@ tursca_status ensure_select(tursca_scene *sc) {
         std::sort(c.begin(), c.end());
         for (int u = 0; u < n; ++u) out[u] = (unsigned char)c[u].second;
     };
+    // points of each cell, ordered by their rankings; rows in that order
+    auto order_cells = [](const std::vector<unsigned char> &rk, int n, const std::vector<int> &start,
+                          std::vector<int> &pts) {
+        for (size_t c = 0; c + 1 < start.size(); ++c)
+            std::sort(pts.begin() + start[c], pts.begin() + start[c + 1], [&](int a, int b) {
+                return std::memcmp(&rk[(size_t)a * n], &rk[(size_t)b * n], n) < 0;
+            });
+    };
+    std::vector<unsigned char> rk((size_t)M * nd);
+    for (int m = 0; m < M; ++m) {
+        ranked(G.lattice[m], G.uhat, &rk[(size_t)m * nd]);
+        if (rk[(size_t)m * nd] != G.cell[m]) return fail(sc, TURSCA_E_INVALID, "lattice ranking");
+    }
+    std::vector<int> pts(G.cell_order.begin(), G.cell_order.end());
+    order_cells(rk, nd, G.cell_start, pts);
     std::vector<unsigned char> rank((size_t)M * nd);
+    std::vector<double> lat((size_t)3 * M);
     for (int p = 0; p < M; ++p) {
-        ranked(G.lattice[G.cell_order[p]], G.uhat, &rank[(size_t)p * nd]);
-        if (rank[(size_t)p * nd] != G.cell[G.cell_order[p]]) return fail(sc, TURSCA_E_INVALID, "lattice ranking");
+        std::memcpy(&rank[(size_t)p * nd], &rk[(size_t)pts[p] * nd], nd);
+        for (int a = 0; a < 3; ++a) lat[(size_t)3 * p + a] = G.lattice[pts[p]][a];
     }
     std::vector<std::array<double, 3>> gh(ngd);
     for (int k = 0; k < ngd; ++k) gh[k] = G.gdirs[k].uhat;
-    std::vector<int> gcell, upts;
+    std::vector<int> upts;
     std::vector<double> gzsum(ngd, 0.0);
     double gztot = 0.0;
+    std::vector<unsigned char> grk;
     for (int m = 0; m < M; ++m) {
         const auto &pt = G.lattice[m];
         if (!(pt[2] > 0.0)) continue;
-        int best = 0;
-        double bc = -2.0;
-        for (int k = 0; k < ngd; ++k) {
-            const double c = gh[k][0] * pt[0] + gh[k][1] * pt[1] + gh[k][2] * pt[2];
-            if (c > bc) {
-                bc = c;
-                best = k;
-            }
-        }
+        const size_t i = upts.size();
         upts.push_back(m);
-        gcell.push_back(best);
-        gzsum[best] += pt[2];
+        grk.resize((i + 1) * ngd);
+        ranked(pt, gh, &grk[i * ngd]);
+        gzsum[grk[i * ngd]] += pt[2];
         gztot += pt[2];
     }
     const int nup = (int)upts.size();
     std::vector<int> gstart(ngd + 1, 0);
-    for (int i = 0; i < nup; ++i) gstart[gcell[i] + 1]++;
+    for (int i = 0; i < nup; ++i) gstart[grk[(size_t)i * ngd] + 1]++;
     for (int k = 0; k < ngd; ++k) gstart[k + 1] += gstart[k];
-    std::vector<int> fill(gstart.begin(), gstart.end() - 1), order(nup);
-    for (int i = 0; i < nup; ++i) order[fill[gcell[i]]++] = i;
+    std::vector<int> fill(gstart.begin(), gstart.end() - 1), gpts(nup);
+    for (int i = 0; i < nup; ++i) gpts[fill[grk[(size_t)i * ngd]]++] = i;
+    order_cells(grk, ngd, gstart, gpts);
     std::vector<unsigned char> grank((size_t)std::max(nup, 1) * std::max(ngd, 1));
-    std::vector<double> gz(std::max(nup, 1));
+    std::vector<double> gz(std::max(nup, 1)), glat((size_t)3 * std::max(nup, 1));
     for (int p = 0; p < nup; ++p) {
-        const auto &pt = G.lattice[upts[order[p]]];
-        ranked(pt, gh, &grank[(size_t)p * ngd]);
-        gz[p] = pt[2];
+        std::memcpy(&grank[(size_t)p * ngd], &grk[(size_t)gpts[p] * ngd], ngd);
+        gz[p] = G.lattice[upts[gpts[p]]][2];
+        for (int a = 0; a < 3; ++a) glat[(size_t)3 * p + a] = G.lattice[upts[gpts[p]]][a];
     }
+    // FP32 copies for the cosine search over short kept lists
+    auto to_f4 = [](const std::vector<double> &v3) {
+        std::vector<float4> f(std::max<size_t>(1, v3.size() / 3));
+        for (size_t i = 0; i < v3.size() / 3; ++i)
+            f[i] = make_float4((float)v3[3 * i], (float)v3[3 * i + 1], (float)v3[3 * i + 2], 0.f);
+        return f;
+    };
+    std::vector<double> dh;
+    for (int u = 0; u < nd; ++u) dh.insert(dh.end(), G.uhat[u].begin(), G.uhat[u].end());
+    for (int k = 0; k < ngd; ++k) dh.insert(dh.end(), gh[k].begin(), gh[k].end());
+    const std::vector<float4> latf = to_f4(lat), glatf = to_f4(glat), dirf = to_f4(dh);
     tk::SelP &q = sc->selp;
     unsigned char *d_rank = nullptr, *d_grank = nullptr;
     int *d_gstart = nullptr;
-    double *d_gz = nullptr, *d_gzsum = nullptr;
+    double *d_gz = nullptr, *d_gzsum = nullptr, *d_lat = nullptr, *d_glat = nullptr;
+    float4 *d_latf = nullptr, *d_glatf = nullptr, *d_dirf = nullptr;
+    CK(upload(sc, sc->allocs, d_glat, glat.data(), glat.size() * sizeof(double)), "upload rank");
+    CK(upload(sc, sc->allocs, d_latf, latf.data(), latf.size() * sizeof(float4)), "upload rank");
+    CK(upload(sc, sc->allocs, d_glatf, glatf.data(), glatf.size() * sizeof(float4)), "upload rank");
+    CK(upload(sc, sc->allocs, d_dirf, dirf.data(), dirf.size() * sizeof(float4)), "upload rank");
     CK(upload(sc, sc->allocs, d_rank, rank.data(), rank.size()), "upload rank");
+    CK(upload(sc, sc->allocs, d_lat, lat.data(), lat.size() * sizeof(double)), "upload rank");
     CK(upload(sc, sc->allocs, d_grank, grank.data(), grank.size()), "upload rank");
     CK(upload(sc, sc->allocs, d_gstart, gstart.data(), gstart.size() * sizeof(int)), "upload ground cells");
     CK(upload(sc, sc->allocs, d_gz, gz.data(), gz.size() * sizeof(double)), "upload ground cells");
@@ -1468,6 +1498,11 @@ tursca_status ensure_select(tursca_scene *sc) {
     q.M = M;
     q.n_up = nup;
     q.rank = d_rank;
+    q.lat = d_lat;
+    q.latf = d_latf;
+    q.glat = d_glat;
+    q.glatf = d_glatf;
+    q.dirf = d_dirf;
     q.grank = d_grank;
     q.gcell_start = d_gstart;
     q.gz = d_gz;

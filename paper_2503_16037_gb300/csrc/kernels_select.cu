@@ -28,11 +28,11 @@ __global__ void k_sel_musmax(GridC g, FieldP<T> f, unsigned long long *bits) {
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(bits, (unsigned long long)__double_as_longlong(m));
 }
 
-// HG of every species toward every lattice point (cell order)
-__global__ void k_sel_points(GridC g, ViewC vc, ViewP vp, int M, double *hgpt) {
+// HG of every species toward every lattice point (in the order of the rankings)
+__global__ void k_sel_points(GridC g, ViewC vc, const double *lat, int M, double *hgpt) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M) return;
-    const double *s = vp.lattice + 3 * (size_t)p;
+    const double *s = lat + 3 * (size_t)p;
     const double mu = vc.s0[0] * s[0] + vc.s0[1] * s[1] + vc.s0[2] * s[2];
     for (int sp = 0; sp < g.S; ++sp) hgpt[(size_t)sp * M + p] = hg<double>(vc.g[sp], mu);
 }
@@ -51,6 +51,9 @@ __device__ __forceinline__ double mus64(const GridC &g, const FieldP<T> &f, int 
 }
 
 constexpr int kSelWarps = 4;
+// kept directions up to which a point's target comes from cosines over the
+// kept list rather than from its ranking
+constexpr int kSelDots = 12;
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp,
@@ -59,6 +62,8 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     __shared__ double s_h[kSelWarps][MAX_SPECIES][kSelMaxDir];
     __shared__ double s_c[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_kept[kSelWarps][kSelMaxDir];
+    __shared__ unsigned char s_list[kSelWarps][kSelMaxDir];
+    __shared__ unsigned char s_klist[kSelWarps][kSelMaxDir];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x * kSelWarps + w;
     if (j >= g.n_nodes) return;  // whole warps leave together
@@ -76,11 +81,14 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     int ndrop = 0;
     for (int u = lane; u < nd; u += 32) {
         double C = -1.0;  // -1: the chain has no receiver
+        bool keep = true;
+        double mus_n = 0.0, dist = 1.0;
+        bool recv = false;
         if (!ground) {
             const int4 d = gp.dirs[u];
             const int rz = z + d.z;
             if (rz < g.nz) {
-                double mus_n, dist;
+                recv = true;
                 if (rz >= 0) {
                     const int xn = wrap_small(x + d.x, g.nx), yn = wrap_small(y + d.y, g.ny);
                     mus_n = mus64(g, f, (rz * g.ny + yn) * g.nx + xn);
@@ -89,16 +97,31 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                     mus_n = mus_lamb;
                     dist = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
                 }
-                C = sqrt(mus_src * mus_n) / dist;
             }
         } else {
             const int4 m = gp.gmem1[u];
             if ((double)m.z - 0.5 <= (double)g.nz) {
+                recv = true;
                 const int xn = wrap_small(x + m.x, g.nx), yn = wrap_small(y + m.y, g.ny);
-                C = sqrt(mus_src * mus64(g, f, ((m.z - 1) * g.ny + yn) * g.nx + xn)) / gp.gdist1[u];
+                mus_n = mus64(g, f, ((m.z - 1) * g.ny + yn) * g.nx + xn);
+                dist = gp.gdist1[u];
             }
         }
-        const bool k = !(sp.c_min > 0.0) || C < 0.0 || C > sp.c_min;
+        if (recv) {
+            if constexpr (sizeof(T) == 4) {
+                // FP32 value (relative error below 1e-6); the FP64 coupling
+                // decides only where the FP32 one is that close to c_min
+                const float c32 = sqrtf((float)mus_src * (float)mus_n) / (float)dist;
+                C = c32;
+                if (sp.c_min > 0.0)
+                    keep = fabs((double)c32 - sp.c_min) > 1e-5 * sp.c_min ? (double)c32 > sp.c_min
+                                                                          : sqrt(mus_src * mus_n) / dist > sp.c_min;
+            } else {
+                C = sqrt(mus_src * mus_n) / dist;
+                keep = !(sp.c_min > 0.0) || C > sp.c_min;
+            }
+        }
+        const bool k = keep;
         kept[u] = k;
         cc[u] = C;
         ndrop += !k;
@@ -112,43 +135,102 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     for (int o = 16; o > 0; o >>= 1) ndrop += __shfl_xor_sync(0xffffffffu, ndrop, o);
     __syncwarp();
 
-    // the points of every dropped cell join their closest kept direction
-    if (ndrop > 0) {
-        for (int u = 0; u < nd; ++u) {
-            if (kept[u]) continue;
-            if (!ground) {
-                for (int p = vp.cell_start[u] + lane; p < vp.cell_start[u + 1]; p += 32) {
-                    const unsigned char *rk = sp.rank + (size_t)p * nd;
-                    int v = -1;
+    // the points of every dropped cell join their closest kept direction: a
+    // lane walks whole cells, whose points are ordered by their rankings, so
+    // the target changes rarely and the lane adds a run at a time.  With many
+    // kept directions a point's target is the first kept one in its ranking;
+    // with few, the largest FP32 cosine over the kept list picks it, and exact
+    // FP64 cosines (the ranking's arithmetic) decide near-ties.  A source
+    // that keeps nothing has nothing to re-assign.
+    unsigned char *list = s_list[w], *klist = s_klist[w];
+    int nl = 0, nk = 0;
+    for (int b = 0; b < nd; b += 32) {
+        const int u = b + lane;
+        const bool dr = u < nd && !kept[u], kp = u < nd && kept[u];
+        const unsigned m = __ballot_sync(0xffffffffu, dr), mk = __ballot_sync(0xffffffffu, kp);
+        const unsigned below = (1u << lane) - 1u;
+        if (dr) list[nl + __popc(m & below)] = (unsigned char)u;
+        if (kp) klist[nk + __popc(mk & below)] = (unsigned char)u;
+        nl += __popc(m);
+        nk += __popc(mk);
+    }
+    __syncwarp();
+    if (nl > 0 && nk > 0) {
+        const unsigned char *rk = ground ? sp.grank : sp.rank;
+        const int *cs = ground ? sp.gcell_start : vp.cell_start;
+        const float4 *pf = ground ? sp.glatf : sp.latf;
+        const double *pd = ground ? sp.glat : sp.lat;
+        const float4 *df = sp.dirf + (ground ? g.nd : 0);
+        const double *dd = vp.dirhat + 3 * (ground ? g.nd : 0);
+        const bool dots = nk <= kSelDots;
+        for (int i = lane; i < nl; i += 32) {
+            const int u = list[i];
+            int cur = -1, n = 0;
+            double a[MAX_SPECIES] = {0.0, 0.0, 0.0, 0.0};
+            for (int p = cs[u]; p < cs[u + 1]; ++p) {
+                int v = -1;
+                if (dots) {
+                    const float4 pt = pf[p];
+                    float b1 = -3.f, b2 = -3.f;
+                    for (int t = 0; t < nk; ++t) {
+                        const int c = klist[t];
+                        const float4 d = df[c];
+                        const float co = d.x * pt.x + d.y * pt.y + d.z * pt.z;
+                        if (co > b1) {
+                            b2 = b1;
+                            b1 = co;
+                            v = c;
+                        } else if (co > b2) {
+                            b2 = co;
+                        }
+                    }
+                    if (b1 - b2 <= 4e-6f) {
+                        const double *q3 = pd + 3 * (size_t)p;
+                        double best = -3.0;
+                        for (int t = 0; t < nk; ++t) {
+                            const int c = klist[t];
+                            const double *h3 = dd + 3 * c;
+                            const double co = __dadd_rn(__dadd_rn(__dmul_rn(h3[0], q3[0]), __dmul_rn(h3[1], q3[1])),
+                                                        __dmul_rn(h3[2], q3[2]));
+                            if (co > best) {
+                                best = co;
+                                v = c;
+                            }
+                        }
+                    }
+                } else {
+                    const unsigned char *row = rk + (size_t)p * nd;
                     for (int q = 1; q < nd; ++q) {
-                        const int c = rk[q];
+                        const int c = row[q];
                         if (kept[c]) {
                             v = c;
                             break;
                         }
-                    }
-                    if (v >= 0) {
-                        atomicAdd(&cnt[v], 1);
-                        for (int s = 0; s < g.S; ++s) atomicAdd(&s_h[w][s][v], sp.hgpt[(size_t)s * sp.M + p]);
                     }
                 }
-            } else {
-                for (int p = sp.gcell_start[u] + lane; p < sp.gcell_start[u + 1]; p += 32) {
-                    const unsigned char *rk = sp.grank + (size_t)p * nd;
-                    int v = -1;
-                    for (int q = 1; q < nd; ++q) {
-                        const int c = rk[q];
-                        if (kept[c]) {
-                            v = c;
-                            break;
-                        }
+                if (v != cur) {
+                    if (cur >= 0) {
+                        if (!ground) atomicAdd(&cnt[cur], n);
+                        for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
                     }
-                    if (v >= 0) atomicAdd(&s_h[w][0][v], sp.gz[p]);
+                    cur = v;
+                    n = 0;
+                    for (int s = 0; s < MAX_SPECIES; ++s) a[s] = 0.0;
+                }
+                ++n;
+                if (ground) {
+                    a[0] += sp.gz[p];
+                } else {
+                    for (int s = 0; s < g.S; ++s) a[s] += sp.hgpt[(size_t)s * sp.M + p];
                 }
             }
+            if (cur >= 0) {
+                if (!ground) atomicAdd(&cnt[cur], n);
+                for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
+            }
         }
-        __syncwarp();
     }
+    __syncwarp();
 
     // weights and routing normalisers over the chains with a receiver
     double wsp[MAX_SPECIES], htot[MAX_SPECIES];
@@ -207,7 +289,7 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
                    const ViewP &vp, const SelP &sp, T *w_iso, T *w_sun, long long *launches) {
     cudaMemsetAsync(sp.musmax_bits, 0, sizeof(unsigned long long), st);
     k_sel_musmax<T><<<(g.n_atm + 255) / 256, 256, 0, st>>>(g, f, sp.musmax_bits);
-    k_sel_points<<<(sp.M + 127) / 128, 128, 0, st>>>(g, vc, vp, sp.M, sp.hgpt);
+    k_sel_points<<<(sp.M + 127) / 128, 128, 0, st>>>(g, vc, sp.lat, sp.M, sp.hgpt);
     k_select<T><<<(g.n_nodes + kSelWarps - 1) / kSelWarps, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, w_iso,
                                                                                      w_sun);
     if (launches) *launches += 3;

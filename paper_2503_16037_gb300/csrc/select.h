@@ -28,8 +28,15 @@ struct SelP {
     int M;                           // lattice points
     int n_up;                        // lattice points in the upper hemisphere
     int dmax;                        // planes of the weight tables: max(nd, ngd)
-    const unsigned char *rank;       // [M][nd] directions by decreasing cosine to each point (cell order)
+    const unsigned char *rank;       // [M][nd] directions by decreasing cosine to each point; points in cell
+                                     // order (cell_start of the graph), inside a cell by their rankings
+    const double *lat;               // [M][3] the lattice points in that order
+    const float4 *latf;              // [M] the same in FP32 (w = 0)
+    const double *glat;              // [n_up][3] the upper-hemisphere points in the order of grank
+    const float4 *glatf;             // [n_up] the same in FP32
+    const float4 *dirf;              // [nd + ngd] unit directions (atmospheric, then ground) in FP32
     const unsigned char *grank;      // [n_up][ngd] ground directions, upper points in ground-cell order
+                                     // (inside a cell by their rankings)
     const int *gcell_start;          // [ngd + 1]
     const double *gz;                // [n_up] cosine weight (z) of each upper point
     const double *gzsum;             // [ngd] cosine weight of each ground cell

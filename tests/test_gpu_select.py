@@ -65,6 +65,9 @@ CASES = {
     "random_4species": (lambda: scenes.make_random(12, 11, 6, seed=10, S=4, R=2, M=1024), 5.0),
     "plume_small": (lambda: scenes.make_plume(nx=24, ny=20, nz=12), 2.0),
     "random_R2_all_dropped": (lambda: scenes.make_random(12, 11, 6, seed=11, S=2, R=2, M=1024), 1e30),
+    # only the 9 upward chains that leave through the TOA stay (a short kept list)
+    "random_R1_all_dropped": (lambda: scenes.make_random(10, 9, 5, seed=12, S=2, R=1, M=2048), 1e30),
+    "random_R1_few_kept": (lambda: scenes.make_random(10, 9, 5, seed=13, S=1, R=1, M=2048), 9.0),
 }
 
 
