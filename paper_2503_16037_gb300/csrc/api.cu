@@ -1486,7 +1486,11 @@ tursca_status ensure_select(tursca_scene *sc) {
     CK(upload(sc, sc->allocs, d_gstart, gstart.data(), gstart.size() * sizeof(int)), "upload ground cells");
     CK(upload(sc, sc->allocs, d_gz, gz.data(), gz.size() * sizeof(double)), "upload ground cells");
     CK(upload(sc, sc->allocs, d_gzsum, gzsum.data(), gzsum.size() * sizeof(double)), "upload ground cells");
-    CK(dalloc(sc->allocs, q.hgpt, (size_t)sc->d.n_species * M * sizeof(double)), "alloc select");
+    // HG per lattice point in FP64, then its copy, the cell sums and the
+    // species totals in the compute type
+    CK(dalloc(sc->allocs, q.hgpt,
+              ((size_t)sc->d.n_species * M * 2 + (size_t)sc->d.n_species * (nd + 1)) * sizeof(double)),
+       "alloc select");
     CK(dalloc(sc->allocs, q.musmax_bits, sizeof(unsigned long long)), "alloc select");
     q.dmax = std::max(nd, ngd);
     const size_t plane = (size_t)grid_c(sc).npad * sc->es;

@@ -6,6 +6,7 @@
 // the edge kernel reads at source-relative positions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -55,12 +56,31 @@ constexpr int kSelWarps = 4;
 // kept list rather than from its ranking
 constexpr int kSelDots = 12;
 
+// Per-scene constants of the re-partition in the compute type: the HG
+// weight of every lattice point, the HG sum of every cell and each species'
+// total (the denominator of q^sun).
+template <typename T>
+__global__ void k_sel_consts(GridC g, SelP sp, const double *cellsum, T *hgpt_t, T *cellsum_t, T *htot_t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.S * sp.M) hgpt_t[i] = (T)sp.hgpt[i];
+    if (i < g.S * g.nd) cellsum_t[i] = (T)cellsum[i];
+    if (i < g.S) {
+        double t = 0.0;
+        for (int u = 0; u < g.nd; ++u) t += cellsum[i * g.nd + u];
+        htot_t[i] = (T)t;
+    }
+}
+
+// One warp per source node.  The values (weights, sums, normalisers) are in
+// the compute type T; the decisions (kept or not, which kept direction a
+// point joins) are exact.
 template <typename T>
 __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp,
-                                                          SelP sp, T *w_iso, T *w_sun) {
+                                                          SelP sp, const T *hgpt, const T *cellsum, const T *htot_g,
+                                                          T *w_iso, T *w_sun) {
     __shared__ int s_cnt[kSelWarps][kSelMaxDir];
-    __shared__ double s_h[kSelWarps][MAX_SPECIES][kSelMaxDir];
-    __shared__ double s_c[kSelWarps][kSelMaxDir];
+    __shared__ T s_h[kSelWarps][MAX_SPECIES][kSelMaxDir];
+    __shared__ T s_c[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_kept[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_list[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_klist[kSelWarps][kSelMaxDir];
@@ -68,22 +88,27 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     const int j = blockIdx.x * kSelWarps + w;
     if (j >= g.n_nodes) return;  // whole warps leave together
     int *cnt = s_cnt[w];
-    double *cc = s_c[w];
+    T *cc = s_c[w];
     unsigned char *kept = s_kept[w];
     const double mus_lamb = vc.albedo * __longlong_as_double((long long)*sp.musmax_bits);
     const bool ground = j >= g.n_atm;
     const int jj = ground ? j - g.n_atm : j;
     const int z = ground ? g.nz : jj / g.nxy, r = jj - (ground ? 0 : z * g.nxy), y = r / g.nx, x = r - y * g.nx;
     const int nd = ground ? g.ngd : g.nd;
-    const double mus_src = ground ? mus_lamb : mus64(g, f, j);
+    // total scattering coefficient of the source: FP64 on FP64 scenes; FP32
+    // scenes take the FP32 sum and the FP64 one only near the threshold
+    const double mus_src64 = (sizeof(T) == 8) ? (ground ? mus_lamb : mus64(g, f, j)) : 0.0;
+    const T mus_src = (sizeof(T) == 8) ? (T)mus_src64 : (ground ? (T)mus_lamb : f.mu_st[j]);
 
     // couplings of the chains and the kept set
     int ndrop = 0;
     for (int u = lane; u < nd; u += 32) {
-        double C = -1.0;  // -1: the chain has no receiver
+        T C = T(-1);  // -1: the chain has no receiver
         bool keep = true;
-        double mus_n = 0.0, dist = 1.0;
+        int nidx = -1;           // receiver voxel (-1: the ground)
         bool recv = false;
+        double dist64 = 0.0;
+        T dist = T(1);
         if (!ground) {
             const int4 d = gp.dirs[u];
             const int rz = z + d.z;
@@ -91,11 +116,12 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                 recv = true;
                 if (rz >= 0) {
                     const int xn = wrap_small(x + d.x, g.nx), yn = wrap_small(y + d.y, g.ny);
-                    mus_n = mus64(g, f, (rz * g.ny + yn) * g.nx + xn);
-                    dist = gp.dir_len[u];
+                    nidx = (rz * g.ny + yn) * g.nx + xn;
+                    dist64 = gp.dir_len[u];
+                    dist = Cst<T>::dir_len(gp, u);
                 } else {  // the chain hits the ground before its first node
-                    mus_n = mus_lamb;
-                    dist = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
+                    dist64 = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
+                    dist = ((T)z + T(0.5)) / (T)(-d.z) * Cst<T>::dir_len(gp, u);
                 }
             }
         } else {
@@ -103,33 +129,41 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
             if ((double)m.z - 0.5 <= (double)g.nz) {
                 recv = true;
                 const int xn = wrap_small(x + m.x, g.nx), yn = wrap_small(y + m.y, g.ny);
-                mus_n = mus64(g, f, ((m.z - 1) * g.ny + yn) * g.nx + xn);
-                dist = gp.gdist1[u];
+                nidx = ((m.z - 1) * g.ny + yn) * g.nx + xn;
+                dist64 = gp.gdist1[u];
+                dist = Cst<T>::gdist1(gp, u);
             }
         }
         if (recv) {
             if constexpr (sizeof(T) == 4) {
                 // FP32 value (relative error below 1e-6); the FP64 coupling
                 // decides only where the FP32 one is that close to c_min
-                const float c32 = sqrtf((float)mus_src * (float)mus_n) / (float)dist;
+                const float mus_n = nidx >= 0 ? f.mu_st[nidx] : (float)mus_lamb;
+                const float c32 = sqrtf(mus_src * mus_n) / dist;
                 C = c32;
-                if (sp.c_min > 0.0)
-                    keep = fabs((double)c32 - sp.c_min) > 1e-5 * sp.c_min ? (double)c32 > sp.c_min
-                                                                          : sqrt(mus_src * mus_n) / dist > sp.c_min;
+                if (sp.c_min > 0.0) {
+                    if (fabs((double)c32 - sp.c_min) > 1e-5 * sp.c_min) {
+                        keep = (double)c32 > sp.c_min;
+                    } else {
+                        const double ms = ground ? mus_lamb : mus64(g, f, j);
+                        const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
+                        keep = sqrt(ms * mn) / dist64 > sp.c_min;
+                    }
+                }
             } else {
-                C = sqrt(mus_src * mus_n) / dist;
+                const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
+                C = sqrt(mus_src64 * mn) / dist64;
                 keep = !(sp.c_min > 0.0) || C > sp.c_min;
             }
         }
-        const bool k = keep;
-        kept[u] = k;
+        kept[u] = keep;
         cc[u] = C;
-        ndrop += !k;
+        ndrop += !keep;
         if (!ground) {
-            cnt[u] = k ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
-            for (int s = 0; s < g.S; ++s) s_h[w][s][u] = k ? f.cellsum[s * g.nd + u] : 0.0;
+            cnt[u] = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
+            for (int s = 0; s < g.S; ++s) s_h[w][s][u] = keep ? cellsum[s * g.nd + u] : T(0);
         } else {
-            s_h[w][0][u] = k ? sp.gzsum[u] : 0.0;
+            s_h[w][0][u] = keep ? (T)sp.gzsum[u] : T(0);
         }
     }
     for (int o = 16; o > 0; o >>= 1) ndrop += __shfl_xor_sync(0xffffffffu, ndrop, o);
@@ -166,7 +200,7 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
         for (int i = lane; i < nl; i += 32) {
             const int u = list[i];
             int cur = -1, n = 0;
-            double a[MAX_SPECIES] = {0.0, 0.0, 0.0, 0.0};
+            T a[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
             for (int p = cs[u]; p < cs[u + 1]; ++p) {
                 int v = -1;
                 if (dots) {
@@ -215,13 +249,13 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                     }
                     cur = v;
                     n = 0;
-                    for (int s = 0; s < MAX_SPECIES; ++s) a[s] = 0.0;
+                    for (int s = 0; s < MAX_SPECIES; ++s) a[s] = T(0);
                 }
                 ++n;
                 if (ground) {
-                    a[0] += sp.gz[p];
+                    a[0] += (T)sp.gz[p];
                 } else {
-                    for (int s = 0; s < g.S; ++s) a[s] += sp.hgpt[(size_t)s * sp.M + p];
+                    for (int s = 0; s < g.S; ++s) a[s] += hgpt[(size_t)s * sp.M + p];
                 }
             }
             if (cur >= 0) {
@@ -233,66 +267,78 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     __syncwarp();
 
     // weights and routing normalisers over the chains with a receiver
-    double wsp[MAX_SPECIES], htot[MAX_SPECIES];
+    T wsp[MAX_SPECIES], rht[MAX_SPECIES];
     if (!ground) {
         for (int s = 0; s < g.S; ++s) {
-            const double ms = (double)f.mu_s[(size_t)s * g.n_atm + j];
-            wsp[s] = mus_src > 0.0 ? ms / mus_src : 1.0 / g.S;
-            double t = 0.0;
-            for (int u = lane; u < g.nd; u += 32) t += f.cellsum[s * g.nd + u];
-            htot[s] = warp_sum_d(t);
+            if constexpr (sizeof(T) == 8) {
+                const double ms = (double)f.mu_s[(size_t)s * g.n_atm + j];
+                wsp[s] = mus_src64 > 0.0 ? ms / mus_src64 : 1.0 / g.S;
+            } else {
+                wsp[s] = f.wsp[(size_t)s * g.n_atm + j];
+            }
+            rht[s] = T(1) / htot_g[s];
         }
     }
-    double sq = 0.0, sqc = 0.0, sqs = 0.0, sqcs = 0.0;
-    for (int u = lane; u < nd; u += 32) {
-        double qi, qs;
-        if (!ground) {
-            qi = (double)cnt[u] / (double)sp.M;
-            qs = 0.0;
-            for (int s = 0; s < g.S; ++s) qs += wsp[s] * (s_h[w][s][u] / htot[s]);
-        } else {
-            qi = s_h[w][0][u] / sp.gztot;
-            qs = qi;
+    const T rM = T(1) / (T)sp.M, rz = T(1) / (T)sp.gztot;
+    T sq = 0, sqc = 0, sqs = 0, sqcs = 0;
+    T qiv[kSelMaxDir / 32], qsv[kSelMaxDir / 32];
+#pragma unroll
+    for (int b = 0; b < kSelMaxDir / 32; ++b) {
+        const int u = b * 32 + lane;
+        T qi = T(0), qs = T(0);
+        if (u < nd) {
+            if (!ground) {
+                qi = (T)cnt[u] * rM;
+                for (int s = 0; s < g.S; ++s) qs += wsp[s] * (s_h[w][s][u] * rht[s]);
+            } else {
+                qi = s_h[w][0][u] * rz;
+                qs = qi;
+            }
+            if (cc[u] >= T(0)) {
+                sq += qi;
+                sqc += qi * cc[u];
+                sqs += qs;
+                sqcs += qs * cc[u];
+            }
         }
-        if (cc[u] >= 0.0) {
-            sq += qi;
-            sqc += qi * cc[u];
-            sqs += qs;
-            sqcs += qs * cc[u];
-        }
+        qiv[b] = qi;
+        qsv[b] = qs;
     }
-    sq = warp_sum_d(sq);
-    sqc = warp_sum_d(sqc);
-    sqs = warp_sum_d(sqs);
-    sqcs = warp_sum_d(sqcs);
-    const bool ci_on = vc.coupling && sqc > 0.0, cs_on = vc.coupling && sqcs > 0.0;
-    for (int u = lane; u < nd; u += 32) {
-        double qi, qs;
-        if (!ground) {
-            qi = (double)cnt[u] / (double)sp.M;
-            qs = 0.0;
-            for (int s = 0; s < g.S; ++s) qs += wsp[s] * (s_h[w][s][u] / htot[s]);
-        } else {
-            qi = s_h[w][0][u] / sp.gztot;
-            qs = qi;
-        }
-        const double C = cc[u];
-        const double ci = (ci_on && C >= 0.0) ? C * sq / sqc : 1.0;
-        const double cs = (cs_on && C >= 0.0) ? C * sqs / sqcs : 1.0;
-        store_halo(w_iso + (size_t)u * g.npad, g, x, y, z, (T)(qi * ci));
-        store_halo(w_sun + (size_t)u * g.npad, g, x, y, z, (T)(qs * cs));
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        sqc += __shfl_xor_sync(0xffffffffu, sqc, o);
+        sqs += __shfl_xor_sync(0xffffffffu, sqs, o);
+        sqcs += __shfl_xor_sync(0xffffffffu, sqcs, o);
+    }
+    const bool ci_on = vc.coupling && sqc > T(0), cs_on = vc.coupling && sqcs > T(0);
+    const T fi = ci_on ? sq / sqc : T(0), fs = cs_on ? sqs / sqcs : T(0);
+#pragma unroll
+    for (int b = 0; b < kSelMaxDir / 32; ++b) {
+        const int u = b * 32 + lane;
+        if (u >= nd) continue;
+        const T C = cc[u];
+        const T ci = (ci_on && C >= T(0)) ? C * fi : T(1);
+        const T cs = (cs_on && C >= T(0)) ? C * fs : T(1);
+        store_halo(w_iso + (size_t)u * g.npad, g, x, y, z, qiv[b] * ci);
+        store_halo(w_sun + (size_t)u * g.npad, g, x, y, z, qsv[b] * cs);
     }
 }
 
 template <typename T>
 void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                    const ViewP &vp, const SelP &sp, T *w_iso, T *w_sun, long long *launches) {
+    // per-scene constants in the compute type live at the end of hgpt
+    T *hgpt_t = reinterpret_cast<T *>(sp.hgpt + (size_t)g.S * sp.M);
+    T *cellsum_t = hgpt_t + (size_t)g.S * sp.M;
+    T *htot_t = cellsum_t + (size_t)g.S * g.nd;
     cudaMemsetAsync(sp.musmax_bits, 0, sizeof(unsigned long long), st);
     k_sel_musmax<T><<<(g.n_atm + 255) / 256, 256, 0, st>>>(g, f, sp.musmax_bits);
     k_sel_points<<<(sp.M + 127) / 128, 128, 0, st>>>(g, vc, sp.lat, sp.M, sp.hgpt);
-    k_select<T><<<(g.n_nodes + kSelWarps - 1) / kSelWarps, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, w_iso,
-                                                                                     w_sun);
-    if (launches) *launches += 3;
+    const int nc = std::max(g.S * sp.M, g.S * g.nd);
+    k_sel_consts<T><<<(nc + 255) / 256, 256, 0, st>>>(g, sp, f.cellsum, hgpt_t, cellsum_t, htot_t);
+    k_select<T><<<(g.n_nodes + kSelWarps - 1) / kSelWarps, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, hgpt_t,
+                                                                                     cellsum_t, htot_t, w_iso, w_sun);
+    if (launches) *launches += 4;
 }
 
 template void launch_select<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &, const ViewC &,

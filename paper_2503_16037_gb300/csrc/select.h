@@ -41,7 +41,8 @@ struct SelP {
     const double *gz;                // [n_up] cosine weight (z) of each upper point
     const double *gzsum;             // [ngd] cosine weight of each ground cell
     double gztot;                    // cosine weight of the upper hemisphere
-    double *hgpt;                    // [S][M] HG toward each lattice point (cell order)
+    double *hgpt;                    // [S][M] HG toward each lattice point (order of the rankings), followed by
+                                     // its compute-type copy, the cell sums [S][nd] and the totals [S] in it
     unsigned long long *musmax_bits; // max over voxels of the FP64 total scattering coefficient
 };
 
