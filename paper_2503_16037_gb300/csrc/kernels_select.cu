@@ -107,7 +107,6 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
         bool keep = true;
         int nidx = -1;           // receiver voxel (-1: the ground)
         bool recv = false;
-        double dist64 = 0.0;
         T dist = T(1);
         if (!ground) {
             const int4 d = gp.dirs[u];
@@ -117,10 +116,8 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                 if (rz >= 0) {
                     const int xn = wrap_small(x + d.x, g.nx), yn = wrap_small(y + d.y, g.ny);
                     nidx = (rz * g.ny + yn) * g.nx + xn;
-                    dist64 = gp.dir_len[u];
                     dist = Cst<T>::dir_len(gp, u);
                 } else {  // the chain hits the ground before its first node
-                    dist64 = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
                     dist = ((T)z + T(0.5)) / (T)(-d.z) * Cst<T>::dir_len(gp, u);
                 }
             }
@@ -130,10 +127,15 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                 recv = true;
                 const int xn = wrap_small(x + m.x, g.nx), yn = wrap_small(y + m.y, g.ny);
                 nidx = ((m.z - 1) * g.ny + yn) * g.nx + xn;
-                dist64 = gp.gdist1[u];
                 dist = Cst<T>::gdist1(gp, u);
             }
         }
+        // the FP64 distance to the first receiver (the oracle's arithmetic)
+        auto dist64 = [&]() -> double {
+            if (ground) return gp.gdist1[u];
+            const int dz = gp.dirs[u].z;
+            return z + dz >= 0 ? gp.dir_len[u] : ((double)z + 0.5) / (double)(-dz) * gp.dir_len[u];
+        };
         if (recv) {
             if constexpr (sizeof(T) == 4) {
                 // FP32 value (relative error below 1e-6); the FP64 coupling
@@ -147,12 +149,12 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
                     } else {
                         const double ms = ground ? mus_lamb : mus64(g, f, j);
                         const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
-                        keep = sqrt(ms * mn) / dist64 > sp.c_min;
+                        keep = sqrt(ms * mn) / dist64() > sp.c_min;
                     }
                 }
             } else {
                 const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
-                C = sqrt(mus_src64 * mn) / dist64;
+                C = sqrt(mus_src64 * mn) / dist64();
                 keep = !(sp.c_min > 0.0) || C > sp.c_min;
             }
         }
