@@ -12,6 +12,9 @@ write) between timed steps, outside the timed interval.  Under torchrun each
 rank runs an independent replica (weak scaling; the path has no exchange).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+``--c-min C`` (coupling selection, scattering graph with C > c_min) and
+``--shape NXxNYxNZ`` time variants of the plume scene; their lines are not the
+headline and skip the CPU baseline, the adjoint, the cloud and serving.
 """
 from __future__ import annotations
 
@@ -43,6 +46,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--solver", type=int, default=0)
+    # variants (not the headline): coupling selection with threshold c_min
+    # (Sec. 2, scattering graph C > c_min) and other plume shapes
+    p.add_argument("--c-min", type=float, default=0.0)
+    p.add_argument("--shape", default="64x64x32")
     return p.parse_args()
 
 
@@ -300,7 +307,9 @@ def main():
     from paper_2503_16037_gb300 import scenes
     from paper_2503_16037_gb300 import tursca as T
 
-    sc = scenes.make_plume()
+    nx, ny, nz = (int(v) for v in args.shape.lower().split("x"))
+    variant = args.c_min > 0.0 or (nx, ny, nz) != (64, 64, 32)
+    sc = scenes.make_plume(nx=nx, ny=ny, nz=nz).replace(c_min=args.c_min)
     stream = torch.cuda.current_stream()
     rn = T.Runner(sc, T.FP32_REFINE, stream=stream)
     st = rn.stats
@@ -398,6 +407,8 @@ def main():
     # voxel's absorption), outside the timed region: time per gradient
     adj = None
     try:
+        if variant:
+            raise RuntimeError("not measured on a variant run")
         rn.run(mu_a, mu_s, rtol=RTOL)
         lbar = 2.0 * rn.rad
         rn.adjoint(lbar)  # first call allocates the K^T copy
@@ -419,7 +430,7 @@ def main():
     # ---- the broken-cloud configuration (128 x 128 x 40, ~81M edges), a few
     # scenes outside the timed region: scenes/s of the same FP32 + refinement path
     cloud = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and not args.no_serving and not variant:
         try:
             csc = scenes.make_cloud()
             crn = T.Runner(csc, T.FP32_REFINE, stream=stream)
@@ -446,7 +457,7 @@ def main():
 
     # ---- serving (continuous batching over resident slots), rank 0 of one GPU
     serve = None
-    if rank == 0 and not args.no_serving:
+    if rank == 0 and not args.no_serving and not variant:
         try:
             serve = serving(T, scenes, torch, np)
         except Exception as e:  # the bench line must still print
@@ -477,12 +488,13 @@ def main():
                 "achieved": ach,
                 "peak": peak,
                 "unit": "GB/s", "frac": ach / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
-                "traffic": traffic_record("k_tile_OpCheb"), "algorithmic_bytes_per_launch": spmv_bytes,
+                "traffic": traffic_record("k_tile_OpCheb") if not variant else None,
+                "algorithmic_bytes_per_launch": spmv_bytes,
                 "avg_launch_us": avg_s * 1e6}
     # ---- accuracy of this run against the FP64 oracle (also the CPU baseline)
     cpu = None
     parity = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not variant:
         r, t, cores = cpu_baseline(sc)
         got = rn.rad.float().cpu().numpy().astype(np.float64)
         err = np.abs(got - r["rad"]) / np.abs(r["rad"])
@@ -495,7 +507,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "scenes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nnz_edges": st.nnz_edges, "nnz_stored": st.nnz, "nodes": st.n_nodes,
+        "config": {"workload": WORKLOAD if not variant else
+                   "plume %dx%dx%d voxels, R=2, coupling selection c_min = %g (variant, not the headline)"
+                   % (nx, ny, nz, args.c_min),
+                   "nnz_edges": st.nnz_edges, "nnz_stored": st.nnz, "nodes": st.n_nodes,
                    "l2": "flushed between timed steps (256 MB write, outside the timed interval)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "edges_per_s": value * st.nnz_edges,
