@@ -266,8 +266,9 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     decision is taken in FP64 in every precision.  The first assembly with
  *     c_min > 0 ranks the lattice (M x n_dirs bytes; M <= 2^20, else
  *     TURSCA_E_UNSUPPORTED) and allocates two weight planes per direction
- *     (2 x n_dirs x nodes of the haloed layout, compute type).
- *     tursca_adjoint returns TURSCA_E_UNSUPPORTED after such an assembly.
+ *     (2 x n_dirs x nodes of the haloed layout, compute type).  The
+ *     weights depend on the scattering coefficients only, so tursca_adjoint
+ *     (a gradient with respect to absorption) reads the same weights.
  *     Changing the value invalidates the current assembly.
  */
 enum {

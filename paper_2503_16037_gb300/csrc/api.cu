@@ -1085,7 +1085,11 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
     const double rtol = sc->d.precision == TURSCA_FP64 ? 1e-12 : 1e-9;
     tursca_status rs = do_solve<T>(sc, TURSCA_SOLVER_AUTO, rtol, 5000, &info, io);
     if (rs) return rs;
-    tk::launch_asm_adj<T>(sc->st, grid_c(sc), gp, f, vc, sc->x64, sc->lam64, ad);
+    if (sc->sel_asm)
+        tk::launch_asm_adj_sel<T>(sc->st, grid_c(sc), gp, f, vc, sc->x64, sc->lam64, ad, (const T *)sc->w_iso,
+                                  (const T *)sc->w_sun);
+    else
+        tk::launch_asm_adj<T>(sc->st, grid_c(sc), gp, f, vc, sc->x64, sc->lam64, ad);
     tk::launch_tables_adj<T>(sc->st, grid_c(sc), gp, f, vc, vp, ad);
     sc->launches += 6;
     CK(cudaGetLastError(), "adjoint launch");
@@ -1670,7 +1674,6 @@ tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_a
     if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
     if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
     if (sc->single_asm) return fail(sc, TURSCA_E_STATE, "the adjoint needs a multiple-scattering assembly");
-    if (sc->sel_asm) return fail(sc, TURSCA_E_UNSUPPORTED, "the adjoint does not cover coupling selection");
     tursca_status e = ensure_adjoint(sc);
     if (e) return e;
     if (sc->d.precision == TURSCA_FP64) return do_adjoint<double>(sc, dJ_dL, dJ_dmu_abs);

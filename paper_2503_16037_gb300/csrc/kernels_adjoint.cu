@@ -25,6 +25,7 @@
 
 #include "asm_util.cuh"
 #include "kern.h"
+#include "select.h"
 #include "stage.cuh"
 
 namespace tk {
@@ -232,10 +233,13 @@ __global__ void k_pix_adj(GridC g, FieldP<T> f, ViewC vc, ViewP vp, const T *__r
 #define TK_ADJ_MINB 8
 #endif
 constexpr int kAdjW = TK_ADJ_W;  // warps per 128-row group of the reverse edge march
-template <typename T, int S>
-__global__ void __launch_bounds__(32 * kAdjW, TK_ADJ_MINB) k_asm_adj(GridC g, GraphP gp, FieldP<T> f, ViewC vc,
-                                                                     const double *__restrict__ x64,
-                                                                     const double *__restrict__ lam64, AdjP<T> ad) {
+// kSel: coupling selection, the weights q c come from the planes wsi / wss
+// (they depend on the scattering coefficients only, so absorption has no
+// path through them)
+template <typename T, int S, bool kSel>
+__global__ void __launch_bounds__(32 * kAdjW, TK_ADJ_MINB)
+    k_asm_adj(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const double *__restrict__ x64,
+              const double *__restrict__ lam64, AdjP<T> ad, const T *__restrict__ wsi, const T *__restrict__ wss) {
     constexpr int W = kAdjW;
     __shared__ T sh[W][4][32];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -306,7 +310,11 @@ __global__ void __launch_bounds__(32 * kAdjW, TK_ADJ_MINB) k_asm_adj(GridC g, Gr
                 tsg = tap_sum_h<T>(gp, f.mu_e_h, seg_off, seg_n, rp + tbase);
             if (hit_n) thit = tap_sum_h<T>(gp, f.mu_e_h, hit_off, hit_n, rp + tbase);
             T Wi, Ws;
-            if (!gsrc) {
+            if constexpr (kSel) {
+                const size_t o = (size_t)dir * g.npad + j;
+                Wi = __ldg(wsi + o);
+                Ws = gsrc ? Wi : __ldg(wss + o);
+            } else if (!gsrc) {
                 T qs = T(0);
 #pragma unroll
                 for (int sp = 0; sp < S; ++sp) qs += __ldg(f.wsp_h + (size_t)sp * g.npad + j) * qsun[sp];
@@ -541,10 +549,23 @@ void launch_asm_adj(cudaStream_t st, const GridC &g, const GraphP &gp, const Fie
                     const double *x64, const double *lam64, const AdjP<T> &ad) {
     const int nb = (g.nz + 1) * g.gpl;
     switch (g.S) {
-        case 1: k_asm_adj<T, 1><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        case 2: k_asm_adj<T, 2><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        case 3: k_asm_adj<T, 3><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
-        default: k_asm_adj<T, 4><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad); break;
+        case 1: k_asm_adj<T, 1, false><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, nullptr, nullptr); break;
+        case 2: k_asm_adj<T, 2, false><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, nullptr, nullptr); break;
+        case 3: k_asm_adj<T, 3, false><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, nullptr, nullptr); break;
+        default: k_asm_adj<T, 4, false><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, nullptr, nullptr); break;
+    }
+}
+
+template <typename T>
+void launch_asm_adj_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                        const double *x64, const double *lam64, const AdjP<T> &ad, const T *w_iso,
+                        const T *w_sun) {
+    const int nb = (g.nz + 1) * g.gpl;
+    switch (g.S) {
+        case 1: k_asm_adj<T, 1, true><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, w_iso, w_sun); break;
+        case 2: k_asm_adj<T, 2, true><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, w_iso, w_sun); break;
+        case 3: k_asm_adj<T, 3, true><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, w_iso, w_sun); break;
+        default: k_asm_adj<T, 4, true><<<nb, 32 * kAdjW, 0, st>>>(g, gp, f, vc, x64, lam64, ad, w_iso, w_sun); break;
     }
 }
 
@@ -568,6 +589,9 @@ void launch_tables_adj(cudaStream_t st, const GridC &g, const GraphP &gp, const 
                                      const FieldP<T> &, const T *, const AdjP<T> &);                           \
     template void launch_asm_adj<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,             \
                                     const ViewC &, const double *, const double *, const AdjP<T> &);            \
+    template void launch_asm_adj_sel<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,         \
+                                        const ViewC &, const double *, const double *, const AdjP<T> &,         \
+                                        const T *, const T *);                                                  \
     template void launch_tables_adj<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
                                        const ViewC &, const ViewP &, const AdjP<T> &);
 INST(float)

@@ -58,4 +58,11 @@ template <typename T>
 void launch_assemble_rows_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
                               const ViewC &vc, const T *w_iso, const T *w_sun, long long *launches);
 
+// The reverse edge march of the adjoint with the weights read from w_iso /
+// w_sun (the adjoint of the assembly that launch_assemble_rows_sel made).
+template <typename T>
+void launch_asm_adj_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                        const double *x64, const double *lam64, const AdjP<T> &ad, const T *w_iso,
+                        const T *w_sun);
+
 }  // namespace tk
