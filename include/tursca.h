@@ -347,6 +347,17 @@ tursca_status tursca_csr_solve_noalloc(const int32_t *row_ptr, const int32_t *co
                                        const float *s, double *x, int sweeps, int refinements, double *resid2,
                                        void *cuda_stream);
 
+/* Self-test of the bounded device wait used by the pipelined passes
+ * (TURSCA_OPT_STAGE_VALUES): one thread of one block waits, with those
+ * passes' own wait (a bounded number of polls of an mbarrier phase), on a
+ * barrier that receives its single expected arrival (arrive != 0) or none
+ * (arrive == 0).  Returns TURSCA_OK when the wait completed and
+ * TURSCA_E_TIMEOUT when it ran out (the kernel then returns normally and the
+ * context stays usable); *seconds (may be NULL) receives the host time of the
+ * call.  Allocates and frees 4 bytes of device memory and synchronises
+ * cuda_stream.  TURSCA_E_CUDA on a CUDA error. */
+tursca_status tursca_selftest_wait(void *cuda_stream, int arrive, double *seconds);
+
 /* Static description of a status code. */
 const char *tursca_status_string(tursca_status status);
 

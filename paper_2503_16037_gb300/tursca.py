@@ -115,6 +115,7 @@ def lib() -> C.CDLL:
             "tursca_set_option": (st, [_vp, C.c_int, C.c_double]),
             "tursca_profile_read": (st, [_vp, C.POINTER(tursca_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
             "tursca_csr_solve_noalloc": (st, [_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp]),
+            "tursca_selftest_wait": (st, [_vp, C.c_int, C.POINTER(C.c_double)]),
             "tursca_status_string": (C.c_char_p, [C.c_int]),
             "tursca_last_error": (st, [_vp, C.c_char_p, C.c_size_t]),
         }
@@ -254,6 +255,14 @@ def tursca_csr_solve_noalloc(row_ptr, col, val, n_nodes: int, s, x, sweeps: int,
     """Allocation-free refined solve on caller device arrays (see tursca.h)."""
     _check(None, lib().tursca_csr_solve_noalloc(_ptr(row_ptr), _ptr(col), _ptr(val), int(n_nodes), _ptr(s), _ptr(x),
                                                 int(sweeps), int(refinements), _ptr(resid2), cuda_stream or None))
+
+
+def tursca_selftest_wait(arrive: bool, cuda_stream: int = 0):
+    """(status, seconds) of the bounded-wait self-test; the status is
+    returned, not raised."""
+    sec = C.c_double(0.0)
+    rc = lib().tursca_selftest_wait(C.c_void_p(cuda_stream), int(bool(arrive)), C.byref(sec))
+    return int(rc), float(sec.value)
 
 
 def tursca_status_string(status: int) -> str:
