@@ -157,3 +157,29 @@ def test_adjoint_gather_tile_identical():
     scale = np.abs(grads[0]).max()
     assert scale > 0
     assert np.abs(grads[0] - grads[1]).max() <= 1e-5 * scale
+
+
+def test_adjoint_dot_product_over_every_voxel():
+    """Dot-product test of the whole adjoint: for a random direction d over
+    all voxels (scaled to the local absorption) and a random weighting w of
+    the pixels, <dL/dmu_a d, w> from central differences of the FP64 forward
+    equals <d, adjoint(w)>."""
+    sc = scenes.make_plume(nx=16, ny=14, nz=8)
+    rn = T.Runner(sc, T.FP64)
+    mu_a, mu_s = rn.fields("cuda")
+    gen = torch.Generator(device="cpu").manual_seed(5)
+    d = (torch.rand(mu_a.shape, generator=gen, dtype=torch.float64) - 0.5).to(mu_a.device) * mu_a
+    w = torch.randn(rn.rad.shape, generator=gen, dtype=torch.float64).to(mu_a.device)
+    rn.run(mu_a, mu_s, rtol=1e-13)
+    lhs_adj = float((rn.adjoint(w) * d).sum())
+    h = 1e-4
+    js = []
+    for sgn in (1.0, -1.0):
+        rn.run(mu_a + sgn * h * d, mu_s, rtol=1e-13)
+        torch.cuda.synchronize()
+        js.append(float((rn.rad * w).sum()))
+    fd = (js[0] - js[1]) / (2 * h)
+    rn.close()
+    print("dot-product test: adjoint %.12e, differences %.12e" % (lhs_adj, fd))
+    assert abs(fd) > 0
+    assert abs(lhs_adj - fd) <= 1e-7 * abs(fd)
