@@ -1,6 +1,7 @@
 // C ABI of libtursca_gb (declared in include/tursca.h): scene lifecycle,
 // uploads, stage orchestration and the solver control loop.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -160,6 +161,15 @@ const char *const kProfNames[] = {"spmv",   "resid64", "assemble_rows", "assembl
                                   "render", "cheb",    "gmres_orth",    "select"};
 constexpr int kNProf = 8;
 enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7 };
+
+// NVTX range around one call of the C ABI (a stage of the path), for
+// profilers that filter or group by range; free when no tool is attached
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // returns the index of the pair, or -1 when profiling is off
 int prof_begin(tursca_scene *sc, int cat) {
@@ -1136,6 +1146,7 @@ tursca_status tursca_scene_destroy(tursca_scene *sc) {
 
 tursca_status tursca_set_medium(tursca_scene *sc, const void *mu_abs, const void *mu_sca, const double *g,
                                 double albedo) {
+    const NvtxRange nvtx("tursca_set_medium");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!mu_abs || !mu_sca || !g) return fail(sc, TURSCA_E_INVALID, "null field pointer");
     for (int s = 0; s < sc->d.n_species; ++s)
@@ -1155,6 +1166,7 @@ tursca_status tursca_set_medium(tursca_scene *sc, const void *mu_abs, const void
 }
 
 tursca_status tursca_build_graph(tursca_scene *sc) {
+    const NvtxRange nvtx("tursca_build_graph");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (sc->built) return TURSCA_OK;
     const tursca_grid_desc &d = sc->d;
@@ -1521,6 +1533,7 @@ tursca_status ensure_select(tursca_scene *sc) {
 }
 
 tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom) {
+    const NvtxRange nvtx("tursca_assemble_flux");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!geom) return fail(sc, TURSCA_E_INVALID, "geometry is null");
     if (!sc->built) return fail(sc, TURSCA_E_STATE, "build_graph has not been called");
@@ -1636,6 +1649,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
 }
 
 tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+    const NvtxRange nvtx("tursca_solve");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!sc->assembled) return fail(sc, TURSCA_E_STATE, "assemble_flux has not been called");
     if (!(rtol > 0.0) || max_iter < 1) return fail(sc, TURSCA_E_INVALID, "rtol must be > 0 and max_iter >= 1");
@@ -1663,6 +1677,7 @@ tursca_status tursca_solve(tursca_scene *sc, double rtol, int max_iter, tursca_s
 }
 
 tursca_status tursca_render_radiance(tursca_scene *sc, void *radiance, void *reflectance) {
+    const NvtxRange nvtx("tursca_render_radiance");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!sc->solved) return fail(sc, TURSCA_E_STATE, "solve has not been called");
     if (sc->d.precision == TURSCA_FP64) return do_render<double>(sc, radiance, reflectance);
@@ -1670,6 +1685,7 @@ tursca_status tursca_render_radiance(tursca_scene *sc, void *radiance, void *ref
 }
 
 tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) {
+    const NvtxRange nvtx("tursca_adjoint");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
     if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
     if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
