@@ -29,6 +29,7 @@ _lib = None
 
 SINGLE_SCATTER = 1
 NO_SOLVE = 2
+ANISO = 4
 K_SELF = 0
 K_GROUND = 7
 MAXDIR = 128
@@ -79,6 +80,11 @@ class OrcResult(C.Structure):
         ("rad", _dp), ("refl", _dp),
         ("gmres_iters", C.c_int),
         ("rel_resid", C.c_double),
+        ("slot_P", _dp),
+        ("chain_C", _dp), ("chain_E", _dp),
+        ("X", _dp),
+        ("arrive", _dp), ("esc_out", _dp),
+        ("aniso_iters", C.c_int),
     ]
 
 
@@ -108,6 +114,8 @@ def _load():
         lib.orc_fibonacci.argtypes = [C.c_int, C.c_int, _dp]
         lib.orc_partition.argtypes = [C.POINTER(OrcDesc), _dp, C.c_int, _ip, _dp, _dp]
         lib.orc_partition.restype = C.c_int
+        lib.orc_phase_quadrature.argtypes = [C.POINTER(OrcDesc), _dp, _dp, C.POINTER(C.c_int)]
+        lib.orc_phase_quadrature.restype = C.c_int
         lib.orc_result_size.restype = C.c_int
         lib.orc_desc_size.restype = C.c_int
         assert lib.orc_result_size() == C.sizeof(OrcResult), "OrcResult layout mismatch"
@@ -182,6 +190,12 @@ def run(sc, flags: int = 0, threads: int = 0, gmres_tol: float = 1e-13) -> dict:
                 "gmres_iters": r.gmres_iters, "rel_resid": r.rel_resid,
             })
             res["emis"] = res["emis1"] + res["emis_sun"] + res["emis_ms"]
+            if flags & ANISO and not flags & SINGLE_SCATTER:
+                res.update({
+                    "X": _arr(r.X, nn * (nd + ngd)).reshape(nn, nd + ngd),
+                    "arrive": _arr(r.arrive, nn), "esc_out": _arr(r.esc_out, nn),
+                    "aniso_iters": r.aniso_iters,
+                })
         return res
     finally:
         lib.orc_free(out)
@@ -217,6 +231,19 @@ def partition(sc, kept, ground: bool = False):
     if ground:
         return qi[:n]
     return qi[:n], qs[: sc.n_species * n].reshape(sc.n_species, n)
+
+
+def phase_quadrature(sc) -> np.ndarray:
+    """Q[S][n_dirs + n_gdirs][n_dirs]: HG of each species integrated over the
+    cell of each atmospheric direction, by arrival direction (atmospheric
+    directions, then the ground chains' directions); rows sum to one."""
+    lib = _load()
+    d = _desc(sc)
+    g = np.ascontiguousarray(sc.g, dtype=np.float64)
+    buf = np.zeros(sc.n_species * (MAXDIR + MAXGDIR) * MAXDIR)
+    nd = C.c_int(0)
+    nin = lib.orc_phase_quadrature(C.byref(d), g.ctypes.data_as(_dp), buf.ctypes.data_as(_dp), C.byref(nd))
+    return buf[: sc.n_species * nin * nd.value].reshape(sc.n_species, nin, nd.value)
 
 
 def fibonacci(M: int) -> np.ndarray:

@@ -52,6 +52,7 @@
 /* flags */
 #define ORC_SINGLE_SCATTER 1 /* first order only: K and s are zeroed (pin P3) */
 #define ORC_NO_SOLVE 2       /* stop after the matrices and the source */
+#define ORC_ANISO 4          /* multiple scattering with the arrival direction kept (every order HG) */
 
 typedef struct {
     int nx, ny, nz;
@@ -98,6 +99,12 @@ typedef struct {
     double *rad, *refl;        /* [npy][npx] */
     int gmres_iters;
     double rel_resid;
+    /* ORC_ANISO only */
+    double *slot_P;            /* deposit fraction of each slot (no weights) */
+    double *chain_C, *chain_E; /* [n_nodes][n_dirs]: coupling of each chain (-1: no receiver), escape */
+    double *X;                 /* [n_nodes][n_dirs + n_gdirs]: scattered power by arrival direction */
+    double *arrive, *esc_out;  /* [n_nodes]: power arriving at a node; power its chains carry out of the TOA */
+    int aniso_iters;
 } orc_result;
 
 /* ------------------------------------------------------------------------ */
@@ -626,27 +633,34 @@ static int orc_select(const orc_desc *d, const orc_result *r, const double *mu_s
     return ndrop;
 }
 
-static void orc_source_weights(const orc_desc *d, const orc_result *r, const double *mu_s_tot,
-                               const double *qdir, int ndir, const orc_chain *ch, int src_is_ground,
-                               double mus_src, double *cw, double *zout) {
-    /* qdir: q_{j,u}; returns c_{j,u} in cw */
+/* Routing weight of G15: c_u = C_u sum_v q_v / sum_v q_v C_v over the
+ * directions with a receiver (C_v >= 0), 1 for a direction without one; 1
+ * everywhere when the coupling is off or the weighted sum is 0.  *zout gets
+ * sum q C / sum q (1 in those cases). */
+static void orc_route(const orc_desc *d, const double *C, const double *qdir, int ndir, double *cw, double *zout) {
     double sq = 0.0, sqc = 0.0;
-    double C[ORC_MAXDIR];
     for (int u = 0; u < ndir; ++u) {
-        C[u] = 0.0;
-        if (ch[u].first < 0) continue;
-        C[u] = orc_coupling(r, mu_s_tot, &ch[u], mus_src);
+        if (C[u] < 0.0) continue;
         sq += qdir[u];
         sqc += qdir[u] * C[u];
     }
-    (void)src_is_ground;
     if (d->coupling == 0 || !(sqc > 0.0)) {
         for (int u = 0; u < ndir; ++u) cw[u] = 1.0;
         *zout = 1.0;
         return;
     }
-    for (int u = 0; u < ndir; ++u) cw[u] = ch[u].first >= 0 ? C[u] * sq / sqc : 1.0;
+    for (int u = 0; u < ndir; ++u) cw[u] = C[u] >= 0.0 ? C[u] * sq / sqc : 1.0;
     *zout = sqc / sq;
+}
+
+static void orc_source_weights(const orc_desc *d, const orc_result *r, const double *mu_s_tot,
+                               const double *qdir, int ndir, const orc_chain *ch, int src_is_ground,
+                               double mus_src, double *cw, double *zout) {
+    /* qdir: q_{j,u}; returns c_{j,u} in cw */
+    double C[ORC_MAXDIR];
+    (void)src_is_ground;
+    for (int u = 0; u < ndir; ++u) C[u] = orc_coupling(r, mu_s_tot, &ch[u], mus_src);
+    orc_route(d, C, qdir, ndir, cw, zout);
 }
 
 static void orc_ray_sun(const orc_desc *d, const double *mu_e, const double P[3], double *T) {
@@ -781,11 +795,189 @@ static void los_seg(void *ctx, int cell, double t0, double t1) {
 
 /* ------------------------------------------------------------------------ */
 
+void orc_free(orc_result *r);
+
+/* ------------------------------------------------------------------------ */
+/* Anisotropic multiple scattering: the edge unknowns of Eq. flux_system.    */
+/* phi per directed edge carries its arrival direction into the next         */
+/* scattering; the edges that reach a node along one direction are merged    */
+/* (re-emission there depends on the arrival direction only), so the unknown */
+/* is the power scattered at node i from light that arrived along w, X(i,w). */
+
+/* p' of Eq. F_term_phase with the arrival direction kept: for every arrival
+ * direction w (the atmospheric directions, then the ground chains' upward
+ * directions) and species, the HG weight toward each lattice point, the angle
+ * measured from w, summed over the cell of each atmospheric direction (the
+ * nearest-direction partition of orc_quadrature) and divided by the
+ * whole-sphere sum: Q[sp][w][u], every row summing to one. */
+static void orc_phase_quadrature_fill(const orc_desc *d, const orc_result *r, const double *g, double *Q) {
+    int M = d->M, nd = r->n_dirs, ngd = r->n_gdirs, S = d->S, nin = nd + ngd;
+    double uh[ORC_MAXDIR][3], wh[ORC_MAXDIR + ORC_MAXGDIR][3], len;
+    for (int u = 0; u < nd; ++u) {
+        orc_atm_dir(d, r, u, uh[u], &len);
+        memcpy(wh[u], uh[u], sizeof uh[u]);
+    }
+    for (int k = 0; k < ngd; ++k) orc_gnd_dir(d, r, k, wh[nd + k]);
+    int *cell = malloc(sizeof(int) * M);
+    double *pt = malloc(sizeof(double) * 3 * (size_t)M);
+    for (int m = 0; m < M; ++m) {
+        double *sm = pt + 3 * (size_t)m;
+        orc_fib_point(m, M, sm);
+        int best = 0;
+        double bc = uh[0][0] * sm[0] + uh[0][1] * sm[1] + uh[0][2] * sm[2];
+        for (int u = 1; u < nd; ++u) {
+            double c = uh[u][0] * sm[0] + uh[u][1] * sm[1] + uh[u][2] * sm[2];
+            if (c > bc) {
+                bc = c;
+                best = u;
+            }
+        }
+        cell[m] = best;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int w = 0; w < nin; ++w)
+        for (int sp = 0; sp < S; ++sp) {
+            double *row = Q + ((size_t)sp * nin + w) * nd;
+            double tot = 0.0;
+            for (int u = 0; u < nd; ++u) row[u] = 0.0;
+            for (int m = 0; m < M; ++m) {
+                const double *sm = pt + 3 * (size_t)m;
+                double h = orc_hg(g[sp], wh[w][0] * sm[0] + wh[w][1] * sm[1] + wh[w][2] * sm[2]);
+                row[cell[m]] += h;
+                tot += h;
+            }
+            for (int u = 0; u < nd; ++u) row[u] /= tot;
+        }
+    free(cell);
+    free(pt);
+}
+
+/* The series of Eq. fs_sum over the edge unknowns, phi = S + F S + F^2 S ...,
+ * in the merged form:
+ *   L(j,u)  = sum_w X(j,w) Q_j(w -> u) c_j(u | w)   power leaving atmospheric j along u
+ *             (Q_j: species mixture of Q by the source's mu_s shares; c: the
+ *             routing weight of G15 normalised with Q_j(w -> .))
+ *   L(c,k)  = (sum_w X(c,w)) q_lamb_k c_k           Lambertian node: no memory of w
+ *   X(i,w)  = Xs(i,w) + rho_i sum_{chains (j,u=w) depositing on i} P L(j,u)
+ * with Xs the first-order part (the sun's light scattered once at j and
+ * arriving at i), iterated until the relative change is below 1e-15.
+ * Fills r->X, r->x (the total, as the isotropic solve does), r->arrive and
+ * r->esc_out.  Returns 0, or 3 when the weights do not fit in memory. */
+static int orc_aniso(const orc_desc *d, orc_result *r, const double *g, const double *mu_s, const double *mus,
+                     const double *om, const int *rowcnt) {
+    int na = r->n_atm, nn = r->n_nodes, nd = r->n_dirs, ngd = r->n_gdirs, S = d->S, nin = nd + ngd;
+    int ng = nn - na;
+    double *Q = malloc(sizeof(double) * (size_t)S * nin * nd);
+    double *W = malloc(sizeof(double) * (size_t)na * nin * nd);
+    if (!Q || !W) {
+        free(Q);
+        free(W);
+        return 3;
+    }
+    orc_phase_quadrature_fill(d, r, g, Q);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < na; ++j) {
+        double q[ORC_MAXDIR], cw[ORC_MAXDIR], z, wsp[16];
+        for (int sp = 0; sp < S; ++sp) wsp[sp] = mus[j] > 0.0 ? mu_s[(size_t)sp * na + j] / mus[j] : 1.0 / S;
+        for (int w = 0; w < nin; ++w) {
+            for (int u = 0; u < nd; ++u) {
+                double acc = 0.0;
+                for (int sp = 0; sp < S; ++sp) acc += wsp[sp] * Q[((size_t)sp * nin + w) * nd + u];
+                q[u] = acc;
+            }
+            orc_route(d, &r->chain_C[(size_t)j * nd], q, nd, cw, &z);
+            for (int u = 0; u < nd; ++u) W[((size_t)j * nin + w) * nd + u] = q[u] * cw[u];
+        }
+    }
+    double *Wg = malloc(sizeof(double) * (size_t)(ng > 0 ? ng : 1) * (ngd > 0 ? ngd : 1));
+    for (int c = 0; c < ng; ++c) {
+        double cw[ORC_MAXGDIR], z;
+        orc_route(d, &r->chain_C[(size_t)(na + c) * nd], r->q_lamb, ngd, cw, &z);
+        for (int k = 0; k < ngd; ++k) Wg[(size_t)c * ngd + k] = r->q_lamb[k] * cw[k];
+    }
+    size_t nx = (size_t)nn * nin;
+    double *Xs = calloc(nx, sizeof(double)), *X = calloc(nx, sizeof(double)), *Arr = calloc(nx, sizeof(double));
+    double *L = calloc((size_t)nn * nd, sizeof(double));
+    double *first = calloc(nn, sizeof(double));
+    for (int i = 0; i < nn; ++i) {
+        double rho = i < na ? om[i] : d->albedo;
+        for (int e = rowcnt[i]; e < rowcnt[i + 1]; ++e) {
+            double a = r->slot_depsun[e] * r->e1[r->slot_col[e]];
+            Xs[(size_t)i * nin + r->slot_dir[e]] += rho * a;
+            first[i] += a;
+        }
+    }
+    memcpy(X, Xs, sizeof(double) * nx);
+    int it;
+    for (it = 0; it < 100000; ++it) {
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < nn; ++j) {
+            if (j < na) {
+                for (int u = 0; u < nd; ++u) {
+                    double acc = 0.0;
+                    for (int w = 0; w < nin; ++w) acc += X[(size_t)j * nin + w] * W[((size_t)j * nin + w) * nd + u];
+                    L[(size_t)j * nd + u] = acc;
+                }
+            } else {
+                double xt = 0.0;
+                for (int w = 0; w < nin; ++w) xt += X[(size_t)j * nin + w];
+                for (int k = 0; k < ngd; ++k) L[(size_t)j * nd + k] = xt * Wg[(size_t)(j - na) * ngd + k];
+            }
+        }
+        double num = 0.0, den = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : num, den)
+        for (int i = 0; i < nn; ++i) {
+            double *ar = Arr + (size_t)i * nin;
+            for (int w = 0; w < nin; ++w) ar[w] = 0.0;
+            for (int e = rowcnt[i]; e < rowcnt[i + 1]; ++e) {
+                int src = r->slot_col[e], dir = r->slot_dir[e];
+                int loc = dir < nd ? dir : dir - nd;
+                ar[dir] += L[(size_t)src * nd + loc] * r->slot_P[e];
+            }
+            double rho = i < na ? om[i] : d->albedo;
+            for (int w = 0; w < nin; ++w) {
+                size_t q = (size_t)i * nin + w;
+                double xn = Xs[q] + rho * ar[w];
+                num += (xn - X[q]) * (xn - X[q]);
+                den += xn * xn;
+                X[q] = xn;
+            }
+        }
+        if (num <= 1e-30 * den) break;
+    }
+    r->aniso_iters = it + 1;
+    r->X = X;
+    r->arrive = calloc(nn, sizeof(double));
+    r->esc_out = calloc(nn, sizeof(double));
+    for (int i = 0; i < nn; ++i) {
+        double xt = 0.0, at = first[i];
+        for (int w = 0; w < nin; ++w) {
+            xt += X[(size_t)i * nin + w];
+            at += Arr[(size_t)i * nin + w];
+        }
+        r->x[i] = xt;
+        r->arrive[i] = at;
+        int n = i < na ? nd : ngd;
+        double eo = r->e1[i] * r->esc_sun[i];
+        for (int u = 0; u < n; ++u) eo += L[(size_t)i * nd + u] * r->chain_E[(size_t)i * nd + u];
+        r->esc_out[i] = eo;
+    }
+    free(Q);
+    free(W);
+    free(Wg);
+    free(Xs);
+    free(Arr);
+    free(L);
+    free(first);
+    return 0;
+}
+
 int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const double *g, orc_result **out) {
 #ifdef _OPENMP
     if (d->threads > 0) omp_set_num_threads(d->threads);
 #endif
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->R < 1 || d->R > 2 || d->M < 8 || d->S < 1) return 1;
+    if ((d->flags & ORC_ANISO) && d->c_min > 0.0) return 2; /* not combined with coupling selection */
     orc_result *r = calloc(1, sizeof(orc_result));
     int nx = d->nx, ny = d->ny, nz = d->nz, S = d->S;
     int na = nx * ny * nz, ng = nx * ny, nn = na + ng;
@@ -852,6 +1044,12 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     int16_t *t_dir = malloc(sizeof(int16_t) * cap);
     int8_t *t_k = malloc(sizeof(int8_t) * cap);
     double *t_dep = malloc(sizeof(double) * cap), *t_dsun = malloc(sizeof(double) * cap);
+    const int aniso = (d->flags & ORC_ANISO) != 0;
+    double *t_P = aniso ? malloc(sizeof(double) * cap) : NULL;
+    if (aniso) {
+        r->chain_C = calloc((size_t)nn * nd, sizeof(double));
+        r->chain_E = calloc((size_t)nn * nd, sizeof(double));
+    }
     int *t_cnt = calloc(nn, sizeof(int));
     r->z_iso = calloc(nn, sizeof(double));
     r->z_sun = calloc(nn, sizeof(double));
@@ -909,6 +1107,11 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                 for (int k = 0; k < ngd; ++k) cs[k] = ci[k];
                 r->z_sun[j] = r->z_iso[j];
             }
+            if (aniso)
+                for (int u = 0; u < ndir; ++u) {
+                    r->chain_C[(size_t)j * nd + u] = orc_coupling(r, mus, &ch[u], j < na ? mus[j] : r->mu_s_lamb);
+                    r->chain_E[(size_t)j * nd + u] = ch[u].escape;
+                }
             int cnt = 0;
             double ei = 0.0, es = 0.0;
             for (int u = 0; u < ndir; ++u) {
@@ -923,6 +1126,7 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                     t_k[e] = (int8_t)ch[u].dep[t].k;
                     t_dep[e] = wi * ch[u].dep[t].P;
                     t_dsun[e] = ws * ch[u].dep[t].P;
+                    if (aniso) t_P[e] = ch[u].dep[t].P;
                 }
             }
             r->esc_iso[j] = ei;
@@ -949,6 +1153,7 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     r->slot_k = malloc(sizeof(int8_t) * tot);
     r->slot_dep = malloc(sizeof(double) * tot);
     r->slot_depsun = malloc(sizeof(double) * tot);
+    if (aniso) r->slot_P = malloc(sizeof(double) * tot);
     r->slot_val = malloc(sizeof(double) * tot);
     r->slot_valsun = malloc(sizeof(double) * tot);
     int *fill = malloc(sizeof(int) * nn);
@@ -966,6 +1171,7 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
             r->slot_k[e] = t_k[src];
             r->slot_dep[e] = t_dep[src];
             r->slot_depsun[e] = t_dsun[src];
+            if (aniso) r->slot_P[e] = t_P[src];
             r->slot_val[e] = rho * t_dep[src];
             r->slot_valsun[e] = rho * t_dsun[src];
         }
@@ -977,6 +1183,7 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     free(t_k);
     free(t_dep);
     free(t_dsun);
+    free(t_P);
     free(t_cnt);
 
     /* s = K^sun e1 */
@@ -999,7 +1206,20 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
         *out = r;
         return 0;
     }
-    if (!single) orc_gmres(d, r, rowcnt, r->slot_col, r->slot_val);
+    if (!single) {
+        if (aniso) {
+            if (orc_aniso(d, r, g, mu_s, mus, om, rowcnt) != 0) {
+                free(rowcnt);
+                free(mus);
+                free(mue);
+                free(om);
+                orc_free(r);
+                return 3;
+            }
+        } else {
+            orc_gmres(d, r, rowcnt, r->slot_col, r->slot_val);
+        }
+    }
 
     /* emission toward the instrument */
     double s0[3], vv[3];
@@ -1035,8 +1255,18 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                 double th = 0.0;
                 for (int sp = 0; sp < S; ++sp) th += w[sp] * orc_hg(g[sp], ucos[r->slot_dir[e]]);
                 es += th * r->slot_valsun[e] * r->e1[r->slot_col[e]];
-                em += th * r->slot_val[e] * r->x[r->slot_col[e]];
+                if (!aniso) em += th * r->slot_val[e] * r->x[r->slot_col[e]];
             }
+        if (!single && aniso) {
+            /* every arrival direction's scattered power, less the first-order part */
+            double et = 0.0;
+            for (int wv = 0; wv < nd + ngd; ++wv) {
+                double th = 0.0;
+                for (int sp = 0; sp < S; ++sp) th += w[sp] * orc_hg(g[sp], ucos[wv]);
+                et += th * r->X[(size_t)i * (nd + ngd) + wv];
+            }
+            em = et - es;
+        }
         r->emis_sun[i] = es;
         r->emis_ms[i] = em;
         emis[i] = r->emis1[i] + es + em;
@@ -1074,6 +1304,12 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
 
 void orc_free(orc_result *r) {
     if (!r) return;
+    free(r->slot_P);
+    free(r->chain_C);
+    free(r->chain_E);
+    free(r->X);
+    free(r->arrive);
+    free(r->esc_out);
     free(r->q_sun);
     free(r->tsun);
     free(r->e1);
@@ -1116,6 +1352,19 @@ int orc_partition(const orc_desc *d, const double *g, int ground, const int *kep
     orc_partition_kept(d, r, g, ground, kept, qi, qsun);
     free(r);
     return n;
+}
+
+/* Q[S][n_dirs + n_gdirs][n_dirs]: the phase quadrature by arrival direction
+ * (see orc_phase_quadrature_fill); *n_dirs gets n_dirs.  Returns
+ * n_dirs + n_gdirs. */
+int orc_phase_quadrature(const orc_desc *d, const double *g, double *Q, int *n_dirs) {
+    orc_result *r = calloc(1, sizeof(orc_result));
+    orc_make_dirs(d, r);
+    int nin = r->n_dirs + r->n_gdirs;
+    *n_dirs = r->n_dirs;
+    orc_phase_quadrature_fill(d, r, g, Q);
+    free(r);
+    return nin;
 }
 
 /* Fibonacci lattice point m of M (unit vector). */

@@ -591,6 +591,95 @@ def test_p11_energy_conservation_with_selection(R, sza, saa):
 
 
 # --------------------------------------------------------------------------
+# P12: anisotropic multiple scattering, the edge unknowns of Eq. flux_system
+# (the arrival direction kept into every scattering)
+
+@pytest.mark.parametrize("R,S", [(1, 1), (2, 2), (2, 3)])
+def test_p12_isotropic_phase_reduces_to_the_node_form(R, S):
+    """With g = 0 the re-emission does not depend on the arrival direction,
+    so the edge form gives the node-collapsed solution."""
+    sc = scenes.make_random(8, 7, 4, seed=30 + R + S, S=S, R=R, M=1024)
+    sc = sc.replace(g=np.zeros(S))
+    a, i = O.run(sc, flags=O.ANISO), O.run(sc)
+    assert np.abs(a["x"] - i["x"]).max() <= 1e-12 * np.abs(i["x"]).max()
+    assert np.abs(a["X"].sum(axis=1) - i["x"]).max() <= 1e-12 * np.abs(i["x"]).max()
+    assert (np.abs(a["rad"] - i["rad"]) / i["rad"]).max() < 1e-12
+
+
+def test_p12_phase_quadrature_rows_peak_forward_and_reduce_to_cells():
+    sc = scenes.make_random(5, 5, 3, seed=1, S=3, R=2, M=4096).replace(g=np.array([0.0, 0.5, 0.85]))
+    Q = O.phase_quadrature(sc)
+    r = O.run(sc, flags=O.NO_SOLVE)
+    nd, ngd = r["n_dirs"], r["n_gdirs"]
+    assert Q.shape == (3, nd + ngd, nd)
+    np.testing.assert_allclose(Q.sum(axis=2), 1.0, atol=1e-13)
+    # g = 0: the cells' shares of the lattice for every arrival direction
+    np.testing.assert_allclose(Q[0], np.broadcast_to(r["q_iso"], (nd + ngd, nd)), rtol=1e-12)
+    # forward scattering: the mean of HG over a cell (Q / the cell's share)
+    # peaks at the cell of the arrival direction itself; a ground chain's
+    # direction peaks at the cell that holds it
+    u = r["dirs"] * np.array([sc.hx, sc.hy, sc.hz])
+    u = u / np.linalg.norm(u, axis=1, keepdims=True)
+    gm = r["gdir_mem"][:, 0, :].astype(float) - np.array([0.0, 0.0, 0.5])
+    gu = gm * np.array([sc.hx, sc.hy, sc.hz])
+    gu = gu / np.linalg.norm(gu, axis=1, keepdims=True)
+    for sp in (1, 2):
+        dens = Q[sp] / r["q_iso"]
+        assert np.array_equal(dens[:nd].argmax(axis=1), np.arange(nd))
+        assert np.array_equal(dens[nd:].argmax(axis=1), (gu @ u.T).argmax(axis=1))
+
+
+@pytest.mark.parametrize("R,sza,saa,g", [(1, 35.0, 10.0, 0.6), (2, 62.0, 130.0, 0.85)])
+def test_p12_energy_conservation(R, sza, saa, g):
+    """P5 for the edge form: with omega = 1 and a black surface all incident
+    power leaves through the TOA or reaches the ground."""
+    nx, ny, nz = 6, 5, 7
+    me = np.random.default_rng(5).uniform(0.1, 2.0, nz)
+    sc = scenes.make_layered(nx, ny, nz, me, [1.0], g=(g,), albedo=0.0, R=R, sza=sza, saa=saa,
+                             vza=10, h=(0.1, 0.08, 0.12), M=2048)
+    r = O.run(sc, flags=O.ANISO)
+    na = r["n_atm"]
+    mu0 = math.cos(math.radians(sza))
+    incident = nx * ny * mu0 * sc.hx * sc.hy
+    direct_ground = mu0 * sc.hx * sc.hy * r["tsun"][na:].sum()
+    total = r["esc_out"].sum() + direct_ground + r["arrive"][na:].sum()
+    assert abs(total - incident) <= 1e-12 * incident
+
+
+def test_p12_forward_peaked_light_penetrates_deeper():
+    """Strong forward scattering keeps multiply scattered light moving away
+    from the sun: against the node form (isotropic re-emission after the
+    first scattering), the edge form sends more light to a black ground under
+    a thick scattering layer and less back to space."""
+    nx, ny, nz = 6, 6, 8
+    sc = scenes.make_layered(nx, ny, nz, [1.5] * nz, [1.0], g=(0.85,), albedo=0.0, R=2, sza=30, vza=0,
+                             h=(0.1, 0.1, 0.1), M=2048)
+    a, i = O.run(sc, flags=O.ANISO), O.run(sc)
+    na = a["n_atm"]
+    gnd_a = a["arrive"][na:].sum()
+    gnd_i = float((i["slot_depsun"][i["slot_row"] >= na] * i["e1"][i["slot_col"][i["slot_row"] >= na]]).sum()
+                  + (i["slot_dep"][i["slot_row"] >= na] * i["x"][i["slot_col"][i["slot_row"] >= na]]).sum())
+    assert gnd_a > gnd_i
+    assert a["rad"].mean() < i["rad"].mean()
+
+
+def test_p12_a_species_that_never_scatters_has_no_effect():
+    """The per-node phase quadrature mixes the species by their share of
+    mu_s: a second species with mu_s = 0 everywhere (whatever its g) leaves
+    the edge form's solution unchanged."""
+    one = scenes.make_random(7, 6, 4, seed=41, S=1, R=2, M=1024).replace(g=np.array([0.7]))
+    two = one.replace(mu_s=np.concatenate([one.mu_s, np.zeros_like(one.mu_s)]), g=np.array([0.7, -0.5]))
+    a1, a2 = O.run(one, flags=O.ANISO), O.run(two, flags=O.ANISO)
+    assert (np.abs(a2["rad"] - a1["rad"]) / a1["rad"]).max() < 1e-13
+
+
+def test_p12_rejects_coupling_selection():
+    sc = scenes.make_random(5, 5, 3, seed=1, S=1, R=1, M=512).replace(c_min=1.0)
+    with pytest.raises(ValueError):
+        O.run(sc, flags=O.ANISO)
+
+
+# --------------------------------------------------------------------------
 # Emission toward the instrument (final radiance sum of Sec. 2)
 
 def test_isotropic_emission_identity():
