@@ -270,6 +270,24 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     weights depend on the scattering coefficients only, so tursca_adjoint
  *     (a gradient with respect to absorption) reads the same weights.
  *     Changing the value invalidates the current assembly.
+ *   TURSCA_OPT_ANISO: 0 (default); 1 keeps the arrival direction of the
+ *     light into every scattering (the edge unknowns of Eq. flux_system;
+ *     the default node form re-emits isotropically after the first
+ *     scattering).  The unknown is X(i, w), the power scattered at node i from
+ *     light that arrived along w (the n_dirs atmospheric directions, then the
+ *     n_gdirs ground chains' directions).  At every scattering the species' HG
+ *     is integrated over the cell of each outgoing direction with the angle
+ *     measured from w (Eq. F_term_phase).  assemble_flux stores each slot's
+ *     deposit fraction in place of K (get(TURSCA_F_VAL) then returns
+ *     TURSCA_E_STATE) and builds the quadrature by arrival direction.  solve
+ *     sums the series of Eq. fs_sum until the relative change of X is at most
+ *     rtol (FP32 scenes: at least 1e-6); iters counts its terms and
+ *     rel_resid64 holds the last relative change.  Combines with neither
+ *     TURSCA_OPT_SINGLE_SCATTER nor c_min > 0 (TURSCA_E_INVALID at
+ *     assembly); tursca_adjoint returns TURSCA_E_UNSUPPORTED.  Memory:
+ *     2 (n_dirs + n_gdirs) + 2 n_dirs values per node plus n_dirs haloed
+ *     planes, in the compute type.  Changing the value invalidates the
+ *     current assembly.
  */
 enum {
     TURSCA_OPT_RESIDUAL_FP64 = 1,
@@ -278,7 +296,8 @@ enum {
     TURSCA_OPT_L2_RESIDENT = 4,
     TURSCA_OPT_GATHER_TILE = 5,
     TURSCA_OPT_SINGLE_SCATTER = 6,
-    TURSCA_OPT_COUPLING_MIN = 7
+    TURSCA_OPT_COUPLING_MIN = 7,
+    TURSCA_OPT_ANISO = 8
 };
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
 

@@ -14,6 +14,7 @@
 #include "first_order.h"
 #include "kern.h"
 #include "select.h"
+#include "aniso.h"
 #include "tursca.h"
 
 namespace {
@@ -142,6 +143,12 @@ struct tursca_scene {
     bool sel_ready = false, sel_asm = false;
     tk::SelP selp{};
     void *w_iso = nullptr, *w_sun = nullptr;
+    // anisotropic multiple scattering (edge unknowns): option, state, buffers
+    int aniso = 0;
+    bool aniso_asm = false, ani_ready = false;
+    void *ani_Q = nullptr, *ani_C = nullptr, *ani_Ls = nullptr, *ani_Wg = nullptr, *ani_Lh = nullptr,
+         *ani_X = nullptr, *ani_Xn = nullptr;
+    double *ani_Qraw = nullptr, *ani_acc = nullptr;
     bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
@@ -972,7 +979,9 @@ tursca_status do_render(tursca_scene *sc, void *radiance, void *reflectance) {
     tk::ViewC vc = view_c(sc);
     tk::ViewP vp = view_p(sc);
     int pi = prof_begin(sc, P_RENDER);
-    if (sc->single_asm) {
+    if (sc->aniso_asm) {
+        // the emission came with the solve (from X)
+    } else if (sc->single_asm) {
         tk::launch_emission_first<T>(sc->st, g, f, (T *)sc->emis);
     } else {
         // the solution in the compute type, gathered by the emission kernel
@@ -1111,6 +1120,205 @@ tursca_status do_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) 
 
 // ===========================================================================
 // C ABI
+
+// Coupling selection: rank the directions by decreasing cosine to every
+// lattice point (exact ties to the lower index, as in the partition), order
+// the points of every cell by their rankings (so the points that a dropped
+// cell hands to one kept direction sit together), do the same for the
+// upper-hemisphere points and the ground cells, and allocate the per-scene
+// buffers and the weight planes.  Once per scene.
+tursca_status ensure_select(tursca_scene *sc) {
+    if (sc->sel_ready) return TURSCA_OK;
+    const tg::Graph &G = sc->G;
+    const int M = G.M, nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size();
+    if (M > (1 << 20) || nd > tk::kSelMaxDir || ngd > tk::kSelMaxDir)
+        return fail(sc, TURSCA_E_UNSUPPORTED, "coupling selection needs at most 2^20 lattice points");
+    auto ranked = [](const std::array<double, 3> &s, const std::vector<std::array<double, 3>> &uh,
+                     unsigned char *out) {
+        const int n = (int)uh.size();
+        std::vector<std::pair<double, int>> c(n);
+        for (int u = 0; u < n; ++u) c[u] = {-(uh[u][0] * s[0] + uh[u][1] * s[1] + uh[u][2] * s[2]), u};
+        std::sort(c.begin(), c.end());
+        for (int u = 0; u < n; ++u) out[u] = (unsigned char)c[u].second;
+    };
+    // points of each cell, ordered by their rankings; rows in that order
+    auto order_cells = [](const std::vector<unsigned char> &rk, int n, const std::vector<int> &start,
+                          std::vector<int> &pts) {
+        for (size_t c = 0; c + 1 < start.size(); ++c)
+            std::sort(pts.begin() + start[c], pts.begin() + start[c + 1], [&](int a, int b) {
+                return std::memcmp(&rk[(size_t)a * n], &rk[(size_t)b * n], n) < 0;
+            });
+    };
+    std::vector<unsigned char> rk((size_t)M * nd);
+    for (int m = 0; m < M; ++m) {
+        ranked(G.lattice[m], G.uhat, &rk[(size_t)m * nd]);
+        if (rk[(size_t)m * nd] != G.cell[m]) return fail(sc, TURSCA_E_INVALID, "lattice ranking");
+    }
+    std::vector<int> pts(G.cell_order.begin(), G.cell_order.end());
+    order_cells(rk, nd, G.cell_start, pts);
+    std::vector<unsigned char> rank((size_t)M * nd);
+    std::vector<double> lat((size_t)3 * M);
+    for (int p = 0; p < M; ++p) {
+        std::memcpy(&rank[(size_t)p * nd], &rk[(size_t)pts[p] * nd], nd);
+        for (int a = 0; a < 3; ++a) lat[(size_t)3 * p + a] = G.lattice[pts[p]][a];
+    }
+    std::vector<std::array<double, 3>> gh(ngd);
+    for (int k = 0; k < ngd; ++k) gh[k] = G.gdirs[k].uhat;
+    std::vector<int> upts;
+    std::vector<double> gzsum(ngd, 0.0);
+    double gztot = 0.0;
+    std::vector<unsigned char> grk;
+    for (int m = 0; m < M; ++m) {
+        const auto &pt = G.lattice[m];
+        if (!(pt[2] > 0.0)) continue;
+        const size_t i = upts.size();
+        upts.push_back(m);
+        grk.resize((i + 1) * ngd);
+        ranked(pt, gh, &grk[i * ngd]);
+        gzsum[grk[i * ngd]] += pt[2];
+        gztot += pt[2];
+    }
+    const int nup = (int)upts.size();
+    std::vector<int> gstart(ngd + 1, 0);
+    for (int i = 0; i < nup; ++i) gstart[grk[(size_t)i * ngd] + 1]++;
+    for (int k = 0; k < ngd; ++k) gstart[k + 1] += gstart[k];
+    std::vector<int> fill(gstart.begin(), gstart.end() - 1), gpts(nup);
+    for (int i = 0; i < nup; ++i) gpts[fill[grk[(size_t)i * ngd]]++] = i;
+    order_cells(grk, ngd, gstart, gpts);
+    std::vector<unsigned char> grank((size_t)std::max(nup, 1) * std::max(ngd, 1));
+    std::vector<double> gz(std::max(nup, 1)), glat((size_t)3 * std::max(nup, 1));
+    for (int p = 0; p < nup; ++p) {
+        std::memcpy(&grank[(size_t)p * ngd], &grk[(size_t)gpts[p] * ngd], ngd);
+        gz[p] = G.lattice[upts[gpts[p]]][2];
+        for (int a = 0; a < 3; ++a) glat[(size_t)3 * p + a] = G.lattice[upts[gpts[p]]][a];
+    }
+    // FP32 copies for the cosine search over short kept lists
+    auto to_f4 = [](const std::vector<double> &v3) {
+        std::vector<float4> f(std::max<size_t>(1, v3.size() / 3));
+        for (size_t i = 0; i < v3.size() / 3; ++i)
+            f[i] = make_float4((float)v3[3 * i], (float)v3[3 * i + 1], (float)v3[3 * i + 2], 0.f);
+        return f;
+    };
+    std::vector<double> dh;
+    for (int u = 0; u < nd; ++u) dh.insert(dh.end(), G.uhat[u].begin(), G.uhat[u].end());
+    for (int k = 0; k < ngd; ++k) dh.insert(dh.end(), gh[k].begin(), gh[k].end());
+    const std::vector<float4> latf = to_f4(lat), glatf = to_f4(glat), dirf = to_f4(dh);
+    tk::SelP &q = sc->selp;
+    unsigned char *d_rank = nullptr, *d_grank = nullptr;
+    int *d_gstart = nullptr;
+    double *d_gz = nullptr, *d_gzsum = nullptr, *d_lat = nullptr, *d_glat = nullptr;
+    float4 *d_latf = nullptr, *d_glatf = nullptr, *d_dirf = nullptr;
+    CK(upload(sc, sc->allocs, d_glat, glat.data(), glat.size() * sizeof(double)), "upload rank");
+    CK(upload(sc, sc->allocs, d_latf, latf.data(), latf.size() * sizeof(float4)), "upload rank");
+    CK(upload(sc, sc->allocs, d_glatf, glatf.data(), glatf.size() * sizeof(float4)), "upload rank");
+    CK(upload(sc, sc->allocs, d_dirf, dirf.data(), dirf.size() * sizeof(float4)), "upload rank");
+    CK(upload(sc, sc->allocs, d_rank, rank.data(), rank.size()), "upload rank");
+    CK(upload(sc, sc->allocs, d_lat, lat.data(), lat.size() * sizeof(double)), "upload rank");
+    CK(upload(sc, sc->allocs, d_grank, grank.data(), grank.size()), "upload rank");
+    CK(upload(sc, sc->allocs, d_gstart, gstart.data(), gstart.size() * sizeof(int)), "upload ground cells");
+    CK(upload(sc, sc->allocs, d_gz, gz.data(), gz.size() * sizeof(double)), "upload ground cells");
+    CK(upload(sc, sc->allocs, d_gzsum, gzsum.data(), gzsum.size() * sizeof(double)), "upload ground cells");
+    // HG per lattice point in FP64, then its copy, the cell sums and the
+    // species totals in the compute type
+    CK(dalloc(sc->allocs, q.hgpt,
+              ((size_t)sc->d.n_species * M * 2 + (size_t)sc->d.n_species * (nd + 1)) * sizeof(double)),
+       "alloc select");
+    CK(dalloc(sc->allocs, q.musmax_bits, sizeof(unsigned long long)), "alloc select");
+    q.dmax = std::max(nd, ngd);
+    const size_t plane = (size_t)grid_c(sc).npad * sc->es;
+    CK(dalloc(sc->allocs, sc->w_iso, q.dmax * plane), "alloc select weights");
+    CK(dalloc(sc->allocs, sc->w_sun, q.dmax * plane), "alloc select weights");
+    CK(cudaMemsetAsync(sc->w_iso, 0, q.dmax * plane, sc->st), "memset select weights");
+    CK(cudaMemsetAsync(sc->w_sun, 0, q.dmax * plane, sc->st), "memset select weights");
+    CK(cudaStreamSynchronize(sc->st), "sync");  // the host tables die here
+    q.M = M;
+    q.n_up = nup;
+    q.rank = d_rank;
+    q.lat = d_lat;
+    q.latf = d_latf;
+    q.glat = d_glat;
+    q.glatf = d_glatf;
+    q.dirf = d_dirf;
+    q.grank = d_grank;
+    q.gcell_start = d_gstart;
+    q.gz = d_gz;
+    q.gzsum = d_gzsum;
+    q.gztot = gztot;
+    sc->sel_ready = true;
+    return TURSCA_OK;
+}
+
+// Buffers of the anisotropic mode, allocated by its first assembly.
+tursca_status ensure_aniso(tursca_scene *sc) {
+    if (sc->ani_ready) return TURSCA_OK;
+    const tk::GridC g = grid_c(sc);
+    const size_t es = sc->es, nin = (size_t)g.nd + g.ngd, S = (size_t)g.S;
+    CK(dalloc(sc->allocs, sc->ani_Q, S * nin * g.nd * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Qraw, S * nin * g.nd * sizeof(double)), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_C, (size_t)g.n_nodes * g.nd * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Ls, (size_t)g.n_nodes * g.nd * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Wg, (size_t)std::max(1, g.n_ground) * std::max(1, g.ngd) * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Lh, (size_t)g.nd * g.npad * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_X, nin * g.n_nodes * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Xn, nin * g.n_nodes * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_acc, 2 * sizeof(double)), "alloc aniso");
+    CK(cudaMemsetAsync(sc->ani_Lh, 0, (size_t)g.nd * g.npad * es, sc->st), "memset aniso");
+    sc->ani_ready = true;
+    return TURSCA_OK;
+}
+
+template <typename T>
+tk::AniP<T> ani_p(tursca_scene *sc) {
+    tk::AniP<T> a;
+    a.Q = (T *)sc->ani_Q;
+    a.Qraw = sc->ani_Qraw;
+    a.C = (T *)sc->ani_C;
+    a.Lsun = (T *)sc->ani_Ls;
+    a.Wg = (T *)sc->ani_Wg;
+    a.Lh = (T *)sc->ani_Lh;
+    a.acc = sc->ani_acc;
+    return a;
+}
+
+// The series of Eq. fs_sum over the edge unknowns until the relative change
+// of X is at most the tolerance (FP32 scenes: at least 1e-6, about the
+// rounding floor of an FP32 iterate), then x and the emission from X.
+template <typename T>
+tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+    const tk::GridC g = grid_c(sc);
+    const tk::GraphP gp = graph_p(sc);
+    const tk::FieldP<T> f = field_p<T>(sc);
+    const tk::ViewC vc = view_c(sc);
+    const tk::AniP<T> a = ani_p<T>(sc);
+    const double tol = sizeof(T) == 8 ? rtol : std::max(rtol, 1e-6);
+    const size_t nx = ((size_t)g.nd + g.ngd) * g.n_nodes;
+    T *X = (T *)sc->ani_X, *Xn = (T *)sc->ani_Xn;
+    CK(cudaMemsetAsync(X, 0, nx * sizeof(T), sc->st), "memset X");
+    double rel = 1.0;
+    int it = 0;
+    while (it < max_iter) {
+        tk::launch_aniso_step<T>(sc->st, g, gp, f, vc, a, X, Xn, &sc->launches);
+        double h[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(h, a.acc, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read change");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        std::swap(X, Xn);
+        ++it;
+        rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
+        if (rel <= tol) break;
+    }
+    sc->ani_X = X;
+    sc->ani_Xn = Xn;
+    tk::launch_aniso_finish<T>(sc->st, g, f, X, sc->x64, (T *)sc->emis, &sc->launches);
+    CK(cudaGetLastError(), "aniso launch");
+    if (solver == TURSCA_SOLVER_AUTO)
+        solver = sc->d.precision == TURSCA_FP64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
+    if (info) *info = tursca_solve_info{it, 0, rel, 0.0, solver};
+    tursca_status e = sync_check(sc, "solve");
+    if (e) return e;
+    sc->solved = true;
+    if (rel > tol) return fail(sc, TURSCA_E_NOT_CONVERGED, "series stopped above the tolerance");
+    return TURSCA_OK;
+}
 
 extern "C" {
 
@@ -1405,133 +1613,6 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     return TURSCA_OK;
 }
 
-// Coupling selection: rank the directions by decreasing cosine to every
-// lattice point (exact ties to the lower index, as in the partition), order
-// the points of every cell by their rankings (so the points that a dropped
-// cell hands to one kept direction sit together), do the same for the
-// upper-hemisphere points and the ground cells, and allocate the per-scene
-// buffers and the weight planes.  Once per scene.
-tursca_status ensure_select(tursca_scene *sc) {
-    if (sc->sel_ready) return TURSCA_OK;
-    const tg::Graph &G = sc->G;
-    const int M = G.M, nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size();
-    if (M > (1 << 20) || nd > tk::kSelMaxDir || ngd > tk::kSelMaxDir)
-        return fail(sc, TURSCA_E_UNSUPPORTED, "coupling selection needs at most 2^20 lattice points");
-    auto ranked = [](const std::array<double, 3> &s, const std::vector<std::array<double, 3>> &uh,
-                     unsigned char *out) {
-        const int n = (int)uh.size();
-        std::vector<std::pair<double, int>> c(n);
-        for (int u = 0; u < n; ++u) c[u] = {-(uh[u][0] * s[0] + uh[u][1] * s[1] + uh[u][2] * s[2]), u};
-        std::sort(c.begin(), c.end());
-        for (int u = 0; u < n; ++u) out[u] = (unsigned char)c[u].second;
-    };
-    // points of each cell, ordered by their rankings; rows in that order
-    auto order_cells = [](const std::vector<unsigned char> &rk, int n, const std::vector<int> &start,
-                          std::vector<int> &pts) {
-        for (size_t c = 0; c + 1 < start.size(); ++c)
-            std::sort(pts.begin() + start[c], pts.begin() + start[c + 1], [&](int a, int b) {
-                return std::memcmp(&rk[(size_t)a * n], &rk[(size_t)b * n], n) < 0;
-            });
-    };
-    std::vector<unsigned char> rk((size_t)M * nd);
-    for (int m = 0; m < M; ++m) {
-        ranked(G.lattice[m], G.uhat, &rk[(size_t)m * nd]);
-        if (rk[(size_t)m * nd] != G.cell[m]) return fail(sc, TURSCA_E_INVALID, "lattice ranking");
-    }
-    std::vector<int> pts(G.cell_order.begin(), G.cell_order.end());
-    order_cells(rk, nd, G.cell_start, pts);
-    std::vector<unsigned char> rank((size_t)M * nd);
-    std::vector<double> lat((size_t)3 * M);
-    for (int p = 0; p < M; ++p) {
-        std::memcpy(&rank[(size_t)p * nd], &rk[(size_t)pts[p] * nd], nd);
-        for (int a = 0; a < 3; ++a) lat[(size_t)3 * p + a] = G.lattice[pts[p]][a];
-    }
-    std::vector<std::array<double, 3>> gh(ngd);
-    for (int k = 0; k < ngd; ++k) gh[k] = G.gdirs[k].uhat;
-    std::vector<int> upts;
-    std::vector<double> gzsum(ngd, 0.0);
-    double gztot = 0.0;
-    std::vector<unsigned char> grk;
-    for (int m = 0; m < M; ++m) {
-        const auto &pt = G.lattice[m];
-        if (!(pt[2] > 0.0)) continue;
-        const size_t i = upts.size();
-        upts.push_back(m);
-        grk.resize((i + 1) * ngd);
-        ranked(pt, gh, &grk[i * ngd]);
-        gzsum[grk[i * ngd]] += pt[2];
-        gztot += pt[2];
-    }
-    const int nup = (int)upts.size();
-    std::vector<int> gstart(ngd + 1, 0);
-    for (int i = 0; i < nup; ++i) gstart[grk[(size_t)i * ngd] + 1]++;
-    for (int k = 0; k < ngd; ++k) gstart[k + 1] += gstart[k];
-    std::vector<int> fill(gstart.begin(), gstart.end() - 1), gpts(nup);
-    for (int i = 0; i < nup; ++i) gpts[fill[grk[(size_t)i * ngd]]++] = i;
-    order_cells(grk, ngd, gstart, gpts);
-    std::vector<unsigned char> grank((size_t)std::max(nup, 1) * std::max(ngd, 1));
-    std::vector<double> gz(std::max(nup, 1)), glat((size_t)3 * std::max(nup, 1));
-    for (int p = 0; p < nup; ++p) {
-        std::memcpy(&grank[(size_t)p * ngd], &grk[(size_t)gpts[p] * ngd], ngd);
-        gz[p] = G.lattice[upts[gpts[p]]][2];
-        for (int a = 0; a < 3; ++a) glat[(size_t)3 * p + a] = G.lattice[upts[gpts[p]]][a];
-    }
-    // FP32 copies for the cosine search over short kept lists
-    auto to_f4 = [](const std::vector<double> &v3) {
-        std::vector<float4> f(std::max<size_t>(1, v3.size() / 3));
-        for (size_t i = 0; i < v3.size() / 3; ++i)
-            f[i] = make_float4((float)v3[3 * i], (float)v3[3 * i + 1], (float)v3[3 * i + 2], 0.f);
-        return f;
-    };
-    std::vector<double> dh;
-    for (int u = 0; u < nd; ++u) dh.insert(dh.end(), G.uhat[u].begin(), G.uhat[u].end());
-    for (int k = 0; k < ngd; ++k) dh.insert(dh.end(), gh[k].begin(), gh[k].end());
-    const std::vector<float4> latf = to_f4(lat), glatf = to_f4(glat), dirf = to_f4(dh);
-    tk::SelP &q = sc->selp;
-    unsigned char *d_rank = nullptr, *d_grank = nullptr;
-    int *d_gstart = nullptr;
-    double *d_gz = nullptr, *d_gzsum = nullptr, *d_lat = nullptr, *d_glat = nullptr;
-    float4 *d_latf = nullptr, *d_glatf = nullptr, *d_dirf = nullptr;
-    CK(upload(sc, sc->allocs, d_glat, glat.data(), glat.size() * sizeof(double)), "upload rank");
-    CK(upload(sc, sc->allocs, d_latf, latf.data(), latf.size() * sizeof(float4)), "upload rank");
-    CK(upload(sc, sc->allocs, d_glatf, glatf.data(), glatf.size() * sizeof(float4)), "upload rank");
-    CK(upload(sc, sc->allocs, d_dirf, dirf.data(), dirf.size() * sizeof(float4)), "upload rank");
-    CK(upload(sc, sc->allocs, d_rank, rank.data(), rank.size()), "upload rank");
-    CK(upload(sc, sc->allocs, d_lat, lat.data(), lat.size() * sizeof(double)), "upload rank");
-    CK(upload(sc, sc->allocs, d_grank, grank.data(), grank.size()), "upload rank");
-    CK(upload(sc, sc->allocs, d_gstart, gstart.data(), gstart.size() * sizeof(int)), "upload ground cells");
-    CK(upload(sc, sc->allocs, d_gz, gz.data(), gz.size() * sizeof(double)), "upload ground cells");
-    CK(upload(sc, sc->allocs, d_gzsum, gzsum.data(), gzsum.size() * sizeof(double)), "upload ground cells");
-    // HG per lattice point in FP64, then its copy, the cell sums and the
-    // species totals in the compute type
-    CK(dalloc(sc->allocs, q.hgpt,
-              ((size_t)sc->d.n_species * M * 2 + (size_t)sc->d.n_species * (nd + 1)) * sizeof(double)),
-       "alloc select");
-    CK(dalloc(sc->allocs, q.musmax_bits, sizeof(unsigned long long)), "alloc select");
-    q.dmax = std::max(nd, ngd);
-    const size_t plane = (size_t)grid_c(sc).npad * sc->es;
-    CK(dalloc(sc->allocs, sc->w_iso, q.dmax * plane), "alloc select weights");
-    CK(dalloc(sc->allocs, sc->w_sun, q.dmax * plane), "alloc select weights");
-    CK(cudaMemsetAsync(sc->w_iso, 0, q.dmax * plane, sc->st), "memset select weights");
-    CK(cudaMemsetAsync(sc->w_sun, 0, q.dmax * plane, sc->st), "memset select weights");
-    CK(cudaStreamSynchronize(sc->st), "sync");  // the host tables die here
-    q.M = M;
-    q.n_up = nup;
-    q.rank = d_rank;
-    q.lat = d_lat;
-    q.latf = d_latf;
-    q.glat = d_glat;
-    q.glatf = d_glatf;
-    q.dirf = d_dirf;
-    q.grank = d_grank;
-    q.gcell_start = d_gstart;
-    q.gz = d_gz;
-    q.gzsum = d_gzsum;
-    q.gztot = gztot;
-    sc->sel_ready = true;
-    return TURSCA_OK;
-}
-
 tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom) {
     const NvtxRange nvtx("tursca_assemble_flux");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
@@ -1539,6 +1620,8 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     if (!sc->built) return fail(sc, TURSCA_E_STATE, "build_graph has not been called");
     if (!sc->medium) return fail(sc, TURSCA_E_STATE, "set_medium has not been called");
     if (!(geom->f0 > 0.0) || !std::isfinite(geom->f0)) return fail(sc, TURSCA_E_INVALID, "f0 must be positive");
+    if (sc->aniso && (sc->single || sc->c_min > 0.0))
+        return fail(sc, TURSCA_E_INVALID, "the anisotropic mode combines with neither single scattering nor c_min > 0");
     bool same = sc->view_ok && geom->sza == sc->geom.sza && geom->saa == sc->geom.saa && geom->vza == sc->geom.vza &&
                 geom->vaa == sc->geom.vaa && geom->npx == sc->geom.npx && geom->npy == sc->geom.npy;
     if (!same) {
@@ -1600,7 +1683,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         CK(cudaMemsetAsync(sc->gsun, 0, (size_t)sc->G.n_atm * sc->es, sc->st), "memset gsun");
         CK(cudaGetLastError(), "assemble launch");
         sc->single_asm = sc->assembled = true;
-        sc->sel_asm = false;
+        sc->sel_asm = sc->aniso_asm = false;
         sc->solved = sc->rendered = false;
         return TURSCA_OK;
     }
@@ -1632,6 +1715,20 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
             tk::launch_assemble_rows_sel<float>(sc->st, g, gp, field_p<float>(sc), vc, (const float *)sc->w_iso,
                                                 (const float *)sc->w_sun, &sc->launches);
         prof_end(sc, p1);
+    } else if (sc->aniso) {
+        tursca_status e = ensure_aniso(sc);
+        if (e) return e;
+        int p1 = prof_begin(sc, P_ROWS);
+        if (sc->d.precision == TURSCA_FP64) {
+            tk::launch_assemble_rows_p<double>(sc->st, g, gp, field_p<double>(sc), vc, &sc->launches);
+            tk::launch_aniso_prep<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, ani_p<double>(sc),
+                                          &sc->launches);
+        } else {
+            tk::launch_assemble_rows_p<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
+            tk::launch_aniso_prep<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, ani_p<float>(sc),
+                                         &sc->launches);
+        }
+        prof_end(sc, p1);
     } else {
         int p1 = prof_begin(sc, P_ROWS);
         if (sc->d.precision == TURSCA_FP64)
@@ -1641,6 +1738,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         prof_end(sc, p1);
     }
     sc->sel_asm = sc->c_min > 0.0;
+    sc->aniso_asm = sc->aniso != 0;
     CK(cudaGetLastError(), "assemble launch");
     sc->assembled = true;
     sc->single_asm = false;
@@ -1668,6 +1766,10 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
         sc->solved = true;
         return TURSCA_OK;
     }
+    if (sc->aniso_asm) {
+        if (sc->d.precision == TURSCA_FP64) return do_solve_aniso<double>(sc, solver, rtol, max_iter, info);
+        return do_solve_aniso<float>(sc, solver, rtol, max_iter, info);
+    }
     if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc));
     return do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
 }
@@ -1690,6 +1792,7 @@ tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_a
     if (!dJ_dL || !dJ_dmu_abs) return fail(sc, TURSCA_E_INVALID, "dJ_dL and dJ_dmu_abs must not be null");
     if (!sc->rendered) return fail(sc, TURSCA_E_STATE, "render_radiance has not been called since the last solve");
     if (sc->single_asm) return fail(sc, TURSCA_E_STATE, "the adjoint needs a multiple-scattering assembly");
+    if (sc->aniso_asm) return fail(sc, TURSCA_E_UNSUPPORTED, "the adjoint does not cover the anisotropic mode");
     tursca_status e = ensure_adjoint(sc);
     if (e) return e;
     if (sc->d.precision == TURSCA_FP64) return do_adjoint<double>(sc, dJ_dL, dJ_dmu_abs);
@@ -1720,7 +1823,7 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
                    : which == TURSCA_F_SLOT_DIR ? nnz * 2
                                                 : nnz;
             if (bytes != need) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
-            if (which == TURSCA_F_VAL && (!sc->assembled || sc->single_asm))
+            if (which == TURSCA_F_VAL && (!sc->assembled || sc->single_asm || sc->aniso_asm))
                 return fail(sc, TURSCA_E_STATE, "K is not assembled");
             CK(cudaMalloc(&dtmp, need), "alloc");
             const tk::GridC gc = grid_c(sc);
@@ -1816,6 +1919,13 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
                 return fail(sc, TURSCA_E_INVALID, "the coupling threshold must be finite and >= 0");
             if (value != sc->c_min) {
                 sc->c_min = value;
+                sc->assembled = sc->solved = sc->rendered = false;
+            }
+            return TURSCA_OK;
+        case TURSCA_OPT_ANISO:
+            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "anisotropic mode must be 0 or 1");
+            if ((int)value != sc->aniso) {
+                sc->aniso = (int)value;
                 sc->assembled = sc->solved = sc->rendered = false;
             }
             return TURSCA_OK;

@@ -24,6 +24,7 @@
 #include "asm_util.cuh"
 #include "first_order.h"
 #include "select.h"
+#include "aniso.h"
 
 namespace tk {
 
@@ -354,10 +355,12 @@ constexpr int kAsmW = TK_ASM_W;
 #ifndef TK_ASM_MINB
 #define TK_ASM_MINB 4
 #endif
-// kSel: coupling selection, the weights q c of every (source, direction) come
-// from the planes wsi / wss (haloed, one per direction) instead of the
-// global quadrature and the source's normaliser.
-template <typename T, int S, bool kSel>
+// kMode 0: K.  kMode 1 (coupling selection): K with the weights q c of every
+// (source, direction) read from the planes wsi / wss (haloed, one per
+// direction) instead of the global quadrature and the source's normaliser.
+// kMode 2 (anisotropic multiple scattering): the raw deposit fraction P of
+// every slot instead of K (s and g^sun as in mode 0).
+template <typename T, int S, int kMode>
 __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB)
     k_asm(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const T *__restrict__ wsi, const T *__restrict__ wss) {
     __shared__ T sh[kAsmW][8][32];
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB)
                 P = split * fast_exp_neg<T>(tpre + thit);
             }
             T Wi, Ws;
-            if constexpr (kSel) {
+            if constexpr (kMode == 1) {
                 const size_t o = (size_t)dir * g.npad + j;
                 Wi = __ldg(wsi + o);
                 Ws = gsrc ? Wi : __ldg(wss + o);
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB)
                 Wi = q * (a > T(0) ? a * rtn * dinv : T(1));
                 Ws = Wi;
             }
-            kv[k] = rho[k] * Wi * P;
+            kv[k] = kMode == 2 ? P : rho[k] * Wi * P;
             const T sun = rho[k] * Ws * P * __ldg(f.e1_h + j);
             acc_s[k] += sun;
             acc_g[k] += th[k] * sun;
@@ -533,10 +536,10 @@ void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, con
                           long long *launches) {
     const int nb = (g.nz + 1) * g.gpl;
     switch (g.S) {  // the species count as a compile-time constant
-        case 1: k_asm<T, 1, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
-        case 2: k_asm<T, 2, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
-        case 3: k_asm<T, 3, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
-        default: k_asm<T, 4, false><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 1: k_asm<T, 1, 0><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 2: k_asm<T, 2, 0><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 3: k_asm<T, 3, 0><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        default: k_asm<T, 4, 0><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
     }
     if (launches) *launches += 1;
 }
@@ -546,10 +549,23 @@ void launch_assemble_rows_sel(cudaStream_t st, const GridC &g, const GraphP &gp,
                               const ViewC &vc, const T *w_iso, const T *w_sun, long long *launches) {
     const int nb = (g.nz + 1) * g.gpl;
     switch (g.S) {
-        case 1: k_asm<T, 1, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
-        case 2: k_asm<T, 2, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
-        case 3: k_asm<T, 3, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
-        default: k_asm<T, 4, true><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        case 1: k_asm<T, 1, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        case 2: k_asm<T, 2, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        case 3: k_asm<T, 3, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+        default: k_asm<T, 4, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, w_iso, w_sun); break;
+    }
+    if (launches) *launches += 1;
+}
+
+template <typename T>
+void launch_assemble_rows_p(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                            const ViewC &vc, long long *launches) {
+    const int nb = (g.nz + 1) * g.gpl;
+    switch (g.S) {
+        case 1: k_asm<T, 1, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 2: k_asm<T, 2, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        case 3: k_asm<T, 3, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
+        default: k_asm<T, 4, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc, nullptr, nullptr); break;
     }
     if (launches) *launches += 1;
 }
@@ -573,6 +589,8 @@ void launch_assemble_direct(cudaStream_t st, const GridC &g, const FieldP<T> &f,
                                             const ViewP &, long long *);                                          \
     template void launch_assemble_rows_sel<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,     \
                                               const ViewC &, const T *, const T *, long long *);                  \
+    template void launch_assemble_rows_p<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,       \
+                                            const ViewC &, long long *);                                          \
     template void launch_assemble_pre<T>(cudaStream_t const[4], cudaEvent_t const[5], const GridC &,              \
                                          const GraphP &, const FieldP<T> &, const ViewC &, const ViewP &,         \
                                          long long *);                                                            \

@@ -208,6 +208,7 @@ OPT_L2_RESIDENT = 4
 OPT_GATHER_TILE = 5
 OPT_SINGLE_SCATTER = 6
 OPT_COUPLING_MIN = 7
+OPT_ANISO = 8
 
 
 def tursca_set_option(scene, option: int, value: float):
