@@ -13,7 +13,8 @@ rank runs an independent replica (weak scaling; the path has no exchange).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
 ``--c-min C`` (coupling selection, scattering graph with C > c_min) and
-``--shape NXxNYxNZ`` time variants of the plume scene; their lines are not the
+``--shape NXxNYxNZ`` and ``--aniso`` (the edge unknowns, arrival direction
+kept) time variants of the plume scene; their lines are not the
 headline and skip the CPU baseline, the adjoint, the cloud and serving.
 """
 from __future__ import annotations
@@ -50,6 +51,7 @@ def parse():
     # (Sec. 2, scattering graph C > c_min) and other plume shapes
     p.add_argument("--c-min", type=float, default=0.0)
     p.add_argument("--shape", default="64x64x32")
+    p.add_argument("--aniso", action="store_true")  # edge unknowns (arrival direction kept)
     return p.parse_args()
 
 
@@ -308,10 +310,12 @@ def main():
     from paper_2503_16037_gb300 import tursca as T
 
     nx, ny, nz = (int(v) for v in args.shape.lower().split("x"))
-    variant = args.c_min > 0.0 or (nx, ny, nz) != (64, 64, 32)
+    variant = args.c_min > 0.0 or (nx, ny, nz) != (64, 64, 32) or args.aniso
     sc = scenes.make_plume(nx=nx, ny=ny, nz=nz).replace(c_min=args.c_min)
     stream = torch.cuda.current_stream()
     rn = T.Runner(sc, T.FP32_REFINE, stream=stream)
+    if args.aniso:
+        T.tursca_set_option(rn.handle, T.OPT_ANISO, 1)
     st = rn.stats
     mu_a, mu_s = rn.fields("cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -508,8 +512,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not variant else
-                   "plume %dx%dx%d voxels, R=2, coupling selection c_min = %g (variant, not the headline)"
-                   % (nx, ny, nz, args.c_min),
+                   "plume %dx%dx%d voxels, R=2, coupling selection c_min = %g%s (variant, not the headline)"
+                   % (nx, ny, nz, args.c_min, ", edge unknowns (arrival direction kept)" if args.aniso else ""),
                    "nnz_edges": st.nnz_edges, "nnz_stored": st.nnz, "nodes": st.n_nodes,
                    "l2": "flushed between timed steps (256 MB write, outside the timed interval)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
