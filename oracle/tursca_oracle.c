@@ -22,7 +22,10 @@
  *   - the direct solar source S_a (Sec. 2, external source), the linear system
  *     (I - K) x = s of Eq. flux_system (equivalently the series of Eq. fs_sum),
  *     and the final radiance sum toward the instrument (Sec. 2, last equation)
- *     integrated along each line of sight.
+ *     integrated along each line of sight;
+ *   - with ORC_ANISO, the edge unknowns of Eq. flux_system: the arrival
+ *     direction kept into every scattering (p' of Eq. F_term_phase with the
+ *     angle from the incoming edge), summed as the series of Eq. fs_sum.
  * Readings of points the paper leaves open (orientation of F, chain lumping of
  * extinction beyond the stencil, periodic horizontal boundaries, exact tie
  * rules) are the ones listed in the design notes; each is restated at the
@@ -31,7 +34,9 @@
  * Pins: every function here is checked by the CPU tests against closed forms,
  * invariants or brute force (DDA exactness, Beer-Lambert slab, discrete single
  * scattering, energy conservation, translation equivariance, dense solve,
- * quadrature sums).
+ * quadrature sums; for coupling selection, conservation of the re-partitioned
+ * sphere and its spherical-Voronoi limit; for the edge form, its reduction to
+ * the node form at g = 0 and energy conservation).
  */
 #include <math.h>
 #include <stdint.h>
