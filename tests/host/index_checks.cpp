@@ -1,9 +1,13 @@
 // Host checks of the index arithmetic behind the gather tiles, the
-// pre-wrapped ray taps and the segment table, for a set of grid shapes: the
+// pre-wrapped ray taps, the segment table and the per-direction planes (the
+// coupling-selection weights and the edge form's leaving power, read at
+// source-relative positions, and the edge form's arrival planes), for a set
+// of grid shapes: the
 // kernels compute these positions on the device, and every one of them must
 // land inside its buffer and on the right node.  Built and run by
 // tests/test_host_index_checks.py; prints one line per check and returns the
 // number of failing shapes.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -143,6 +147,47 @@ long check_segments(const Graph &G, int H) {
     return bad;
 }
 
+// per-direction planes: for every slot of every row, the source position
+// rp + src lies in the source's layer and decodes to the template's source
+// node (or one of its halo copies, which the planes hold too); the plane of
+// the slot's direction exists (atmospheric sources: n_dirs planes, ground
+// sources: n_gdirs) and the edge form's arrival index fits its planes
+long check_planes(const Graph &G, int H) {
+    std::vector<EdgeDesc> ed;
+    std::vector<int> th, dh;
+    if (!edge_descriptors(G, H, ed, th, dh).empty()) return 1;
+    const int nx = G.nx, ny = G.ny, nz = G.nz, nxp = nx + 2 * H;
+    const long lp = (long)nxp * (ny + 2 * H), npad = (long)(nz + 1) * lp;
+    const int nd = (int)G.dirs.size(), ngd = (int)G.gdirs.size(), nin = nd + ngd, dmax = std::max(nd, ngd);
+    const long nxy = (long)nx * ny, n_nodes = nxy * (nz + 1);
+    long bad = 0;
+    for (int z = 0; z <= nz; ++z)
+        for (long r = 0; r < nxy; ++r) {
+            const int y = (int)(r / nx), x = (int)(r - (long)y * nx);
+            const long rp = z * lp + (long)(y + H) * nxp + x + H, row = z * nxy + r;
+            for (int i = G.tmpl_start[z]; i < G.tmpl_start[z + 1]; ++i) {
+                const EdgeDesc &d = ed[i];
+                const TSlot &t = G.tmpl[i];
+                const bool gsrc = (d.bits >> 11) & 1;
+                if (gsrc != (t.sz < 0)) ++bad;
+                const int szl = t.sz >= 0 ? t.sz : nz;
+                const long j = rp + d.src;
+                if (j < szl * lp || j >= (szl + 1) * lp) {
+                    ++bad;
+                    continue;
+                }
+                const long in = j - szl * lp;
+                const int xx = (int)(in % nxp), yy = (int)(in / nxp);
+                const int xs = ((xx - H) % nx + nx) % nx, ys = ((yy - H) % ny + ny) % ny;
+                if (xs != ((x + t.sdx) % nx + nx) % nx || ys != ((y + t.sdy) % ny + ny) % ny) ++bad;
+                if (d.dir < 0 || d.dir >= (gsrc ? ngd : nd) || (long)d.dir * npad + j >= (long)dmax * npad) ++bad;
+                const int din = gsrc ? nd + d.dir : d.dir;
+                if (din < 0 || din >= nin || (long)din * n_nodes + row >= (long)nin * n_nodes) ++bad;
+            }
+        }
+    return bad;
+}
+
 }  // namespace
 
 int main() {
@@ -166,10 +211,10 @@ int main() {
             continue;
         }
         const long bt = check_tiles(G, s.R, false), btt = check_tiles(G, s.R, true);
-        const long br = check_rays(G, V), bs = check_segments(G, s.R);
-        std::printf("%dx%dx%d R%d: tiles %ld, K^T tiles %ld, rays %ld, segments %ld bad\n", s.nx, s.ny, s.nz, s.R, bt,
-                    btt, br, bs);
-        if (bt || btt || br || bs) ++failing;
+        const long br = check_rays(G, V), bs = check_segments(G, s.R), bp = check_planes(G, s.R);
+        std::printf("%dx%dx%d R%d: tiles %ld, K^T tiles %ld, rays %ld, segments %ld, planes %ld bad\n", s.nx, s.ny, s.nz,
+                    s.R, bt, btt, br, bs, bp);
+        if (bt || btt || br || bs || bp) ++failing;
     }
     return failing;
 }

@@ -1,5 +1,6 @@
 """Host checks of the index arithmetic the device kernels rely on: the
-gather tiles of K and K^T, the pre-wrapped ray taps and the segment table,
+gather tiles of K and K^T, the pre-wrapped ray taps, the segment table and the
+per-direction planes of coupling selection and the edge form,
 computed with the library's own graph and view builders for several grid
 shapes (tests/host/index_checks.cpp, built here with the host compiler)."""
 import os
