@@ -33,10 +33,13 @@
  *
  * Pins: every function here is checked by the CPU tests against closed forms,
  * invariants or brute force (DDA exactness, Beer-Lambert slab, discrete single
- * scattering, energy conservation, translation equivariance, dense solve,
- * quadrature sums; for coupling selection, conservation of the re-partitioned
- * sphere and its spherical-Voronoi limit; for the edge form, its reduction to
- * the node form at g = 0 and energy conservation).
+ * scattering, energy conservation with a black and with a reflecting ground,
+ * translation equivariance, dense solve, quadrature sums; the per-cell
+ * quadrature weights against integrals over the exact spherical-Voronoi cells:
+ * cell areas for q_iso, HG for q_sun, the cosine for q_lamb; for coupling
+ * selection, conservation of the re-partitioned sphere and its
+ * spherical-Voronoi limit; for the edge form, its reduction to the node form
+ * at g = 0 and energy conservation).
  */
 #include <math.h>
 #include <stdint.h>

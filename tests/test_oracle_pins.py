@@ -19,6 +19,10 @@ def hg(g, mu):
     return (1 - g * g) / (4 * math.pi * (1 + g * g - 2 * g * mu) ** 1.5)
 
 
+def hg_vec(g, mu):
+    return (1 - g * g) / (4 * np.pi * (1 + g * g - 2 * g * mu) ** 1.5)
+
+
 def sun_vec(sza, saa):
     t, p = math.radians(sza), math.radians(saa)
     return -np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), math.cos(t)])
@@ -225,6 +229,37 @@ def test_p5_energy_conservation(R, sza, saa):
     deposited_ground = float((r["slot_depsun"][gnd] * r["e1"][col[gnd]]).sum()
                              + (r["slot_dep"][gnd] * r["x"][col[gnd]]).sum())
     total = escape + direct_ground + deposited_ground
+    assert abs(total - incident) <= 1e-12 * incident
+
+
+@pytest.mark.parametrize("R,sza,saa,A", [(1, 35.0, 10.0, 0.3), (2, 62.0, 130.0, 0.8), (2, 20.0, 250.0, 0.5)])
+def test_p5_energy_conservation_with_a_reflecting_ground(R, sza, saa, A):
+    """omega = 1 and a Lambertian ground of albedo A: the ground re-emits the
+    fraction A of what reaches it (e1_c + x_c, routed by the Lambertian
+    weights q^lamb over the ground chains) and absorbs the rest, so
+    incident = TOA escape + (1 - A) (direct + diffuse power reaching the ground)."""
+    nx, ny, nz = 6, 5, 7
+    rng = np.random.default_rng(7)
+    me = rng.uniform(0.1, 2.0, nz)
+    sc = scenes.make_layered(nx, ny, nz, me, [1.0], g=(0.6,), albedo=A, R=R, sza=sza, saa=saa,
+                             vza=10, h=(0.1, 0.08, 0.12), M=2048)
+    r = O.run(sc, gmres_tol=1e-15)
+    na = r["n_atm"]
+    mu0 = math.cos(math.radians(sza))
+    incident = nx * ny * mu0 * sc.hx * sc.hy
+    escape = float(r["e1"] @ r["esc_sun"] + r["x"] @ r["esc_iso"])
+    direct_ground = float(mu0 * sc.hx * sc.hy * r["tsun"][na:].sum())
+    row, col = r["slot_row"], r["slot_col"]
+    gnd = row >= na
+    diffuse_ground = float((r["slot_depsun"][gnd] * r["e1"][col[gnd]]).sum()
+                           + (r["slot_dep"][gnd] * r["x"][col[gnd]]).sum())
+    # what the ground re-emits is A times what reaches it
+    np.testing.assert_allclose(r["e1"][na:], A * mu0 * sc.hx * sc.hy * r["tsun"][na:], rtol=1e-14)
+    reemitted = float(r["e1"][na:].sum() + r["x"][na:].sum())
+    assert abs(reemitted - A * (direct_ground + diffuse_ground)) <= 1e-12 * incident
+    # the ground's own chains carry part of the escape
+    assert float(r["e1"][na:] @ r["esc_sun"][na:] + r["x"][na:] @ r["esc_iso"][na:]) > 0.01 * escape
+    total = escape + (1.0 - A) * (direct_ground + diffuse_ground)
     assert abs(total - incident) <= 1e-12 * incident
 
 
@@ -440,6 +475,145 @@ def test_p10_cells_converge_to_spherical_voronoi():
         rb = O.run(sc.replace(M=262144), flags=O.NO_SOLVE)
         eb = np.abs(rb["q_iso"] - area).max()
         assert eb < 2.5e-4 and eb < e8
+
+
+# Per-cell weights of Eq. F_term_phase, pinned to integrals over the exact
+# spherical-Voronoi cells of the directions (Sec. 3: each lattice point belongs
+# to its nearest coupled direction, so as M grows a cell's lattice sum tends
+# to the integral over that direction's Voronoi cell).  The cells come from
+# SciPy; the integrals are computed here, independently of the lattice: HG by
+# recursive subdivision of each cell into small spherical triangles (exact
+# areas, edge-midpoint rule), the cosine weight of the Lambertian ground in
+# closed form from the polygon's first moment.
+
+def _nrm(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _moment(poly):
+    """First moment (integral of the unit vector) of a spherical polygon whose
+    vertices run counter-clockwise seen from outside: half the sum over the
+    edges of the arc angle times the unit normal of the edge's plane (the
+    divergence theorem on the cone over the polygon)."""
+    m = np.zeros(3)
+    for a, b in zip(poly, np.roll(poly, -1, axis=0)):
+        c = np.cross(a, b)
+        s = np.linalg.norm(c)
+        if s > 0.0:
+            m += 0.5 * math.atan2(s, float(a @ b)) * c / s
+    return m
+
+
+def _voronoi_cells(gen):
+    """Vertex loops of the spherical-Voronoi cells of unit vectors gen,
+    oriented counter-clockwise seen from outside (the cell's moment points
+    toward its generator)."""
+    sv_mod = pytest.importorskip("scipy.spatial")
+    sv = sv_mod.SphericalVoronoi(gen, radius=1.0)
+    sv.sort_vertices_of_regions()
+    out = []
+    for k, reg in enumerate(sv.regions):
+        poly = sv.vertices[reg]
+        out.append(poly if _moment(poly) @ gen[k] > 0 else poly[::-1])
+    return out
+
+
+def _tri_area(a, b, c):
+    num = np.abs(np.einsum("ij,ij->i", a, np.cross(b, c)))
+    den = 1.0 + (a * b).sum(1) + (b * c).sum(1) + (c * a).sum(1)
+    return 2.0 * np.arctan2(num, den)  # Van Oosterom & Strackee
+
+
+def _cell_integral(gen, poly, f, level=5):
+    """Integral of f over the convex spherical polygon poly containing gen:
+    the fan of triangles (gen, v_k, v_k+1), each split 4**level times."""
+    A = np.repeat(gen[None], len(poly), 0)
+    B, C = poly, np.roll(poly, -1, axis=0)
+    for _ in range(level):
+        ab, bc, ca = _nrm(A + B), _nrm(B + C), _nrm(C + A)
+        A, B, C = (np.concatenate(t) for t in ((A, ab, ca, ab), (ab, B, bc, bc), (ca, bc, C, ca)))
+    mid = (f(_nrm(A + B)) + f(_nrm(B + C)) + f(_nrm(C + A))) / 3.0
+    return float((_tri_area(A, B, C) * mid).sum())
+
+
+def _clip_upper(poly):
+    """The part z >= 0 of a convex spherical polygon (great-circle clipping)."""
+    out = []
+    for P, Q in zip(poly, np.roll(poly, -1, axis=0)):
+        if P[2] >= 0.0:
+            out.append(P)
+        if (P[2] >= 0.0) != (Q[2] >= 0.0):
+            out.append(_nrm(abs(Q[2]) * P + abs(P[2]) * Q))
+    return np.array(out)
+
+
+def test_p10_hg_helper_has_unit_norm_and_mean_cosine_g():
+    """The textbook HG used by these pins: unit integral over the sphere and
+    mean cosine g (Gauss-Legendre in mu, exact to rounding here)."""
+    x, w = np.polynomial.legendre.leggauss(400)
+    for g in (0.0, 0.3, 0.65, 0.85):
+        f = np.array([hg(g, mu) for mu in x])
+        assert abs(2 * math.pi * (w * f).sum() - 1.0) < 1e-11
+        assert abs(2 * math.pi * (w * f * x).sum() - g) < 1e-11
+
+
+@pytest.mark.parametrize("R,sza,saa", [(1, 30.0, 0.0), (1, 63.0, 27.0), (2, 30.0, 0.0), (2, 63.0, 27.0)])
+def test_p10_sun_weights_converge_to_hg_over_voronoi_cells(R, sza, saa):
+    """q^sun[s, u] tends to the integral of HG_g(s0 . s) over the Voronoi cell
+    of u (s0 the sun's propagation direction), for g = 0.3 and 0.85."""
+    h = (0.1, 0.1, 0.1) if R == 1 else (0.05, 0.05, 0.1)
+    sc = scenes.make_random(5, 5, 3, seed=3, S=2, R=R, h=h, sza=sza, saa=saa, M=8192, precision=0)
+    sc = sc.replace(g=np.array([0.3, 0.85]))
+    r8 = O.run(sc, flags=O.NO_SOLVE)
+    rb = O.run(sc.replace(M=1 << 20), flags=O.NO_SOLVE)
+    gen = _unit_dirs(r8, h)
+    cells = _voronoi_cells(gen)
+    s0 = sun_vec(sza, saa)
+    for sp, g in enumerate(sc.g):
+        ref = np.array([_cell_integral(gen[u], cells[u], lambda s: hg_vec(g, s @ s0)) for u in range(len(gen))])
+        assert abs(ref.sum() - 1.0) < 1e-6  # the subdivision integrates the whole sphere
+        e8 = np.abs(r8["q_sun"][sp] - ref).max()
+        eb = np.abs(rb["q_sun"][sp] - ref).max()
+        assert eb < 4e-4 and eb < e8 / 8, (g, e8, eb)
+
+
+@pytest.mark.parametrize("R,h", [(1, (0.1, 0.1, 0.1)), (2, (0.05, 0.05, 0.1)), (2, (0.1, 0.08, 0.12))])
+def test_p10_lambertian_weights_converge_to_cosine_over_voronoi_cells(R, h):
+    """q^lamb[u] tends to (1/pi) times the integral of cos(theta) over the
+    upper half of the Voronoi cell of ground direction u.  The cells are those
+    of the ground directions plus the nadir, whose cell lies below the horizon
+    (the bisector of the nadir and a direction at elevation e sits at (e - 90)/2)
+    and keeps the set from lying in one hemisphere."""
+    sc = scenes.make_layered(5, 5, 3, [0.1] * 3, [0.5], R=R, h=h, M=8192)
+    r8 = O.run(sc, flags=O.NO_SOLVE)
+    rb = O.run(sc.replace(M=1 << 20), flags=O.NO_SOLVE)
+    m = r8["gdir_mem"][:, 0, :].astype(np.float64)
+    gen = _nrm(np.stack([m[:, 0] * h[0], m[:, 1] * h[1], (m[:, 2] - 0.5) * h[2]], axis=1))
+    cells = _voronoi_cells(np.vstack([gen, [[0.0, 0.0, -1.0]]]))
+    assert np.all(cells[-1][:, 2] < 0.0)
+    ref = np.array([_moment(_clip_upper(cells[u]))[2] / math.pi for u in range(len(gen))])
+    assert abs(ref.sum() - 1.0) < 1e-13  # the upper hemisphere's cosine integral is pi
+    e8 = np.abs(r8["q_lamb"] - ref).max()
+    eb = np.abs(rb["q_lamb"] - ref).max()
+    assert eb < 1e-4 and eb < e8 / 8, (e8, eb)
+
+
+@pytest.mark.parametrize("sza,saa", [(20.0, 0.0), (40.0, 10.0), (45.0, 60.0), (63.0, 27.0), (75.0, 200.0)])
+def test_p10_sun_weights_peak_forward(sza, saa):
+    """Sign of the scattering angle: for a forward-peaked phase function
+    (g = 0.85, forward / backward HG ratio ((1 + g) / (1 - g))^3 = 1876) the
+    mean HG over a cell (q^sun / q^iso) peaks among the directions nearest
+    the sun's propagation direction s0 and bottoms out among those nearest
+    -s0 (the cells' shapes decide between near neighbours)."""
+    h = (0.05, 0.05, 0.1)
+    sc = scenes.make_random(5, 5, 3, seed=3, S=1, R=2, h=h, sza=sza, saa=saa, M=8192, precision=0)
+    r = O.run(sc.replace(g=np.array([0.85])), flags=O.NO_SOLVE)
+    u = _unit_dirs(r, h)
+    s0 = sun_vec(sza, saa)
+    mean_hg = r["q_sun"][0] / r["q_iso"]
+    fwd, back = np.argsort(-(u @ s0))[:3], np.argsort(u @ s0)[:3]
+    assert np.argmax(mean_hg) in fwd and np.argmin(mean_hg) in back
+    assert mean_hg[fwd[0]] > 100.0 * mean_hg[back[0]]
 
 
 # --------------------------------------------------------------------------
