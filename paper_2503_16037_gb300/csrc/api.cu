@@ -100,6 +100,12 @@ struct tursca_scene {
     double *lattice = nullptr, *dirhat = nullptr;
     int *cell_start = nullptr;
     int *canon_dirs = nullptr, *up_canon = nullptr;
+    int4 *cseg = nullptr;   // per canonical direction: (first tap in ctap, tap count, u_z, 0)
+    int *ctap = nullptr;    // graph tap index of each tap of the canonical segments
+    int nctap = 0;
+    tk::SegTab<float> segtab_f;   // the canonical segments as kernel parameters (n = 0: not used)
+    tk::SegTab<double> segtab_d;
+    void *srec = nullptr;   // source records of the edge kernel (haloed, srec_stride(S) per node)
     int *tflat = nullptr;  // template offsets in the haloed layout
     tk::RTap *rtaps = nullptr, *sun_rt = nullptr;  // taps of long rays, pre-wrapped (graph, sun)
     int *ttile = nullptr, *tlay = nullptr;  // gather-tile offsets and layers of the row-group passes
@@ -109,6 +115,7 @@ struct tursca_scene {
     tk::ASlot *aslot = nullptr;  // edge-kernel descriptors of the template entries
     int *tap_h = nullptr, *dir_h = nullptr;  // haloed offsets of the taps and the directions
     void *rt_h = nullptr, *wsp_h = nullptr, *mu_e_h = nullptr, *e1_h = nullptr;  // haloed copies
+    void *mu_x = nullptr;  // extinction repeated 2 x 2 horizontally (long rays)
     int *run_g[2] = {nullptr, nullptr};  // runs of the persistent streamed passes
     long long *run_v[2] = {nullptr, nullptr};
     int run_n[2] = {0, 0};
@@ -328,6 +335,9 @@ tk::GraphP graph_p(const tursca_scene *sc) {
     p.gtop_n = sc->gtop_n;
     p.rtaps = sc->rtaps;
     p.canon_dirs = sc->canon_dirs;
+    p.cseg = sc->cseg;
+    p.ctap = sc->ctap;
+    p.nctap = sc->nctap;
     p.up_canon = sc->up_canon;
     p.status = sc->status;
     p.tflat = sc->tflat;
@@ -363,6 +373,7 @@ tk::FieldP<T> field_p(const tursca_scene *sc) {
     f.rt_h = (T *)sc->rt_h;
     f.wsp_h = (T *)sc->wsp_h;
     f.mu_e_h = (T *)sc->mu_e_h;
+    f.mu_x = (T *)sc->mu_x;
     f.e1_h = (T *)sc->e1_h;
     f.q_sun = (T *)sc->q_sun;
     f.hgv = (T *)sc->hgv;
@@ -373,6 +384,7 @@ tk::FieldP<T> field_p(const tursca_scene *sc) {
     f.mus_max_bits = sc->musmax;
     f.status = sc->status;
     f.cellsum = sc->cellsum;
+    f.srec = (T *)sc->srec;
     return f;
 }
 
@@ -481,6 +493,10 @@ tursca_status ensure_fields(tursca_scene *sc) {
             CK(dalloc(sc->allocs, *hal[k], bytes), "alloc haloed");
             CK(cudaMemsetAsync(*hal[k], 0, bytes, sc->st), "memset haloed");
         }
+        CK(dalloc(sc->allocs, sc->mu_x, 4 * na * es), "alloc extended extinction");
+        const size_t rbytes = npd * es * (size_t)tk::srec_stride(sc->d.n_species);
+        CK(dalloc(sc->allocs, sc->srec, rbytes), "alloc haloed");
+        CK(cudaMemsetAsync(sc->srec, 0, rbytes, sc->st), "memset haloed");
     }
     CK(dalloc(sc->allocs, sc->s, nn * es), "alloc s");
     CK(dalloc(sc->allocs, sc->gsun, na * es), "alloc gsun");
@@ -1529,7 +1545,24 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
             d.n1 = e.n1;
             d.aux = e.aux;
             d.tbase = e.tbase;
-            d.bits = e.bits;
+            // bit 12: the chain's first receiver is the receiver row itself;
+            // bits 13-14: the edge kernel's straight-line kind of an
+            // atmospheric source's chain node with table-read optical depths
+            // (1: before the chain's end, 2: terminal with nothing beyond,
+            // 3: terminal below the TOA), 0: the general code
+            {
+                const bool gs = (e.bits >> 11) & 1, cone = (e.bits >> 8) & 1, n1g = (e.bits >> 9) & 1;
+                const bool n1_row = e.n1 == 0 && (gs || (!cone && !n1g));
+                const int kind = e.bits & 15, bkind = (e.bits >> 4) & 15;
+                const bool has_pre = (e.bits >> 10) & 1;
+                int ft = 0;
+                if (kind == 0 && !gs && !cone && !n1g && has_pre == !n1_row && (!has_pre || e.pre >= 0)) {
+                    if (bkind == 0 && e.seg >= 0) ft = 1;
+                    else if (bkind == 1) ft = 2;
+                    else if (bkind == 2 && e.seg >= 0) ft = 3;
+                }
+                d.bits = e.bits | (n1_row ? 1 << 12 : 0) | (ft << 13);
+            }
             d.dir = e.dir;
             d.hgdir = e.hgdir;
             d.taps = e.taps;
@@ -1597,6 +1630,53 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->hg0v, (size_t)sc->d.n_species * es), "alloc hg0v");
     CK(dalloc(sc->allocs, sc->cellsum, (size_t)sc->d.n_species * nd * sizeof(double)), "alloc cellsum");
     CK(upload(sc, sc->allocs, sc->canon_dirs, G.canon_dirs.data(), G.canon_dirs.size() * sizeof(int)), "upload canon");
+    {
+        // the taps of every canonical lattice segment, for the segment-table
+        // kernel: each lies in the source's layer or the R above it and within
+        // H columns and rows of it (the kernel's shared-memory tile)
+        const int H = sc->d.stencil_radius;
+        std::vector<int4> cs;
+        std::vector<int> ct;
+        for (int c = 0; c < (int)G.canon_dirs.size(); ++c) {
+            const int u = G.canon_dirs[c];
+            cs.push_back(make_int4((int)ct.size(), G.lat_n[u], G.dirs[u][2], 0));
+            for (int k = 0; k < G.lat_n[u]; ++k) {
+                const tg::Tap &t = G.taps[G.lat_off[u] + k];
+                if (t.dz < 0 || t.dz > sc->d.stencil_radius || std::abs(t.dx) > H || std::abs(t.dy) > H)
+                    return fail(sc, TURSCA_E_INVALID, "internal error: lattice tap outside the segment tile");
+                ct.push_back(G.lat_off[u] + k);
+            }
+        }
+        if (ct.size() > (size_t)tk::kSegMaxTaps || cs.size() > 64 || H > 2)
+            return fail(sc, TURSCA_E_INVALID, "internal error: segment taps exceed the kernel's tables");
+        if (G.dirs.size() > 128 || G.gdirs.size() > 128)
+            return fail(sc, TURSCA_E_INVALID, "internal error: too many directions for the normaliser kernel");
+        if (ct.empty()) ct.push_back(0);
+        CK(upload(sc, sc->allocs, sc->cseg, cs.data(), cs.size() * sizeof(int4)), "upload canon");
+        CK(upload(sc, sc->allocs, sc->ctap, ct.data(), ct.size() * sizeof(int)), "upload canon");
+        sc->nctap = (int)(ct.size() == 1 && cs.empty() ? 0 : ct.size());
+        // the same taps as kernel parameters, padded to tk::kSegTapsPer per
+        // direction, at offsets into the kernel's tile (R + 1 layers of
+        // (kSegTY + 2H) rows of kSegTX + 2H columns)
+        const int TXh = tk::kSegTX + 2 * H, tpl = TXh * (tk::kSegTY + 2 * H);
+        std::memset(&sc->segtab_f, 0, sizeof(sc->segtab_f));
+        std::memset(&sc->segtab_d, 0, sizeof(sc->segtab_d));
+        bool fits = cs.size() <= 64;
+        for (size_t c = 0; c < cs.size() && fits; ++c) fits = cs[c].y <= tk::kSegTapsPer;
+        if (fits) {
+            for (size_t c = 0; c < cs.size(); ++c) {
+                const int u = G.canon_dirs[c];
+                sc->segtab_f.uz[c] = sc->segtab_d.uz[c] = G.dirs[u][2];
+                for (int k = 0; k < cs[c].y; ++k) {
+                    const tg::Tap &t = G.taps[G.lat_off[u] + k];
+                    sc->segtab_f.off[c][k] = sc->segtab_d.off[c][k] = t.dz * tpl + t.dy * TXh + t.dx;
+                    sc->segtab_f.len[c][k] = (float)t.len;
+                    sc->segtab_d.len[c][k] = t.len;
+                }
+            }
+            sc->segtab_f.n = sc->segtab_d.n = (int)cs.size();
+        }
+    }
     std::vector<int> upc(G.up_dirs.size());
     for (size_t i = 0; i < upc.size(); ++i) upc[i] = G.canon_of_dir[G.up_dirs[i]];
     CK(upload(sc, sc->allocs, sc->up_canon, upc.data(), upc.size() * sizeof(int)), "upload canon");
@@ -1690,9 +1770,11 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     int p0 = prof_begin(sc, P_PRE);
     const cudaStream_t streams[4] = {sc->st, sc->aux[0], sc->aux[1], sc->aux[2]};
     if (sc->d.precision == TURSCA_FP64)
-        tk::launch_assemble_pre<double>(streams, sc->fork, g, gp, field_p<double>(sc), vc, vp, &sc->launches);
+        tk::launch_assemble_pre<double>(streams, sc->fork, g, gp, field_p<double>(sc), vc, vp, sc->segtab_d,
+                                        &sc->launches);
     else
-        tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, &sc->launches);
+        tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, sc->segtab_f,
+                                       &sc->launches);
     prof_end(sc, p0);
     if (sc->c_min > 0.0) {
         tursca_status e = ensure_select(sc);

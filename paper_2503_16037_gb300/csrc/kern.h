@@ -126,6 +126,12 @@ struct GraphP {
     const int *run_g[2];
     const long long *run_v[2];
     int run_n[2];
+    // lattice segments of the canonical directions, for the segment-table
+    // kernel: per canonical direction (first entry in ctap, tap count, u_z, 0)
+    // and the graph tap index of each of its taps
+    const int4 *cseg;
+    const int *ctap;
+    int nctap;                     // total taps of the canonical directions
 };
 
 // Per-scene optical fields and assembled quantities (element type T).
@@ -148,6 +154,10 @@ struct FieldP {
     T *rt_h;         // [npad]
     T *wsp_h;        // [S][npad]
     T *mu_e_h;       // [npad]
+    // [nz][2 ny][2 nx]: the extinction repeated twice along x and y, so that a
+    // long ray's cell (x + dx, y + dy) with x, dx in [0, nx) and y, dy in
+    // [0, ny) needs no wrap
+    T *mu_x;
     T *e1_h;         // [npad]
     T *q_sun;        // [S][nd]
     T *hgv;          // [S][nd + ngd]
@@ -156,6 +166,12 @@ struct FieldP {
     double *cellsum; // [S][nd] HG sums per Fibonacci cell
     T *s;            // [n_nodes]
     T *gsun;         // [n_atm]
+    // [npad][srec_stride(S)] haloed source records of the edge kernel:
+    // element 0 is a_iso; element 1 + sp, per species, the species share of
+    // the scattering coefficient times the first-order power e1 times the sun
+    // coupling factor a_sun, negated when the source's sun coupling weight is
+    // 1 (a_sun = 0); ground sources carry e1 times a_iso in element 1
+    T *srec;
     unsigned long long *mus_max_bits;  // max of mu_s (bits of a non-negative double)
     int *status;     // device status flags
 };
@@ -214,6 +230,27 @@ struct Cst<double> {
 // are one aligned 16-byte (FP32) or 32-byte (FP64) quad.
 constexpr int kGroup = 128;
 __host__ __device__ __forceinline__ int val_lane_pos(int i) { return ((i & 31) << 2) | (i >> 5); }
+// stride of the edge kernel's source records (FieldP::srec): a_iso and S sun factors
+__host__ __device__ constexpr int srec_stride(int S) { return S <= 3 ? 4 : 8; }
+// most taps the canonical lattice segments may have (segment-table kernel)
+constexpr int kSegMaxTaps = 512;
+// The segment-table kernel's shared-memory tile: a block of kSegTX x kSegTY
+// voxels of one layer holds its columns and rows +- R and its layer and the
+// R above (R <= 2).
+constexpr int kSegTX = 32, kSegTY = 4;
+// The canonical lattice segments as kernel parameters, each padded to
+// kSegTapsPer taps (zero lengths): tap k of direction c at tile offset
+// off[c][k] with length len[c][k]; uz[c] is the direction's z component.
+// n = 0 when a segment has more taps than that (the kernel then reads the
+// graph's tap lists instead).
+constexpr int kSegTapsPer = 4;
+template <typename T>
+struct SegTab {
+    int n;
+    int uz[64];
+    int off[64][kSegTapsPer];
+    T len[64][kSegTapsPer];
+};
 // source layers a group's gather tile holds (the receiver layer +- R and the ground)
 constexpr int kTileLayers = 6;
 // largest gather tile (bytes of shared memory per block)
@@ -260,7 +297,8 @@ __host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x,
 // st[0]: scene stream; st[1..3]: auxiliary streams; ev: five events (no timing)
 template <typename T>
 void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], const GridC &g, const GraphP &gp,
-                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, long long *launches);
+                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, const SegTab<T> &segtab,
+                         long long *launches);
 // the fused edge march + edge weights over all receiver rows
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,

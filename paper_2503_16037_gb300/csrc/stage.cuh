@@ -348,6 +348,15 @@ __device__ __forceinline__ void st_quad(double *p, const double (&v)[4]) {
     reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
 }
+// the same with the streaming (evict-first) cache hint: values written once
+// and read only by later passes
+__device__ __forceinline__ void st_quad_cs(float *p, const float (&v)[4]) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+}
+__device__ __forceinline__ void st_quad_cs(double *p, const double (&v)[4]) {
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
+}
 
 // Programmatic dependent launch: a pass may be launched while the previous
 // pass on the stream is still running.  Everything it reads before
