@@ -10,7 +10,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "tursca.h"
 
@@ -28,24 +27,18 @@ constexpr size_t kScratchBytes = kOffPart + 8ull * kPartBlocks;  // about 12 MiB
 // Shared by every call on a device; holds the previous call's contents.
 static __device__ __align__(256) unsigned char g_solve_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_of_device[256] = {nullptr};
+// Most kernel launches one call may issue (sweeps and residual passes).
+constexpr long long kMaxLaunches = 1000000;
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the first call on a device does this set-up).
+// Device address of the scratch array in the current device's context,
+// looked up on every call: the lookup is cheap once the module is loaded, and
+// a cached address would go stale if the context were reset or replaced
+// between calls.  The first call in a context loads the module there.
 cudaError_t scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_solve_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_of_device[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_solve_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_of_device[dev] = p;
-    }
-    *out = g_scratch_of_device[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -114,6 +107,10 @@ extern "C" tursca_status tursca_csr_solve_noalloc(const int32_t *row_ptr, const 
     if (!row_ptr || !col || !val || !s || !x) return TURSCA_E_INVALID;
     if (n_nodes < 1 || n_nodes > kMaxNodes) return TURSCA_E_INVALID;
     if (sweeps < 0 || sweeps > 100000 || refinements < 1 || refinements > 1000) return TURSCA_E_INVALID;
+    if ((long long)(sweeps + 2) * refinements + 2 > kMaxLaunches) return TURSCA_E_INVALID;
+    // an error left pending by earlier work belongs to its owner: report it
+    // without clearing it, before launching anything
+    if (cudaPeekAtLastError() != cudaSuccess) return TURSCA_E_CUDA;
     void *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return TURSCA_E_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -126,6 +123,8 @@ extern "C" tursca_status tursca_csr_solve_noalloc(const int32_t *row_ptr, const 
     int nres = (n_nodes + 7) / 8;
     if (nres > kPartBlocks) nres = kPartBlocks;
     k_na_init<<<nvec, th, 0, st>>>(n_nodes, s, x, b);
+    // a launch that fails (a bad stream, say) fails them all: stop at the first
+    if (cudaGetLastError() != cudaSuccess) return TURSCA_E_CUDA;
     for (int r = 0; r < refinements; ++r) {
         const float *cur = b;
         for (int k = 0; k < sweeps; ++k) {

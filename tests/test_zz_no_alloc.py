@@ -24,8 +24,11 @@ def built():
     build.build()
 
 
-def test_noalloc_solve_matches_scene_solve_twice():
-    sc = scenes.make_plume(nx=24, ny=20, nz=12)
+@pytest.mark.parametrize("shape", [(24, 20, 12), (32, 32, 16)])
+def test_noalloc_solve_matches_scene_solve_twice(shape):
+    # 32 x 32 x 16 has 17,408 nodes: the residual pass's grid (capped at 1024
+    # blocks of 8 warps) then walks its rows more than once per warp
+    sc = scenes.make_plume(nx=shape[0], ny=shape[1], nz=shape[2])
     rn = T.Runner(sc, T.FP32_REFINE)
     mu_a, mu_s = rn.fields("cuda")
     rn.set_medium(mu_a, mu_s)
@@ -56,4 +59,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     dummy = torch.zeros(8, dtype=torch.int32, device="cuda")
     with pytest.raises(T.TurscaError) as ei:
         T.tursca_csr_solve_noalloc(dummy, dummy, dummy, (1 << 20) + 1, dummy, dummy, 4, 1, None, 0)
+    assert ei.value.status == T.E_INVALID
+    # more than 10^6 launches in one call
+    with pytest.raises(T.TurscaError) as ei:
+        T.tursca_csr_solve_noalloc(dummy, dummy, dummy, 8, dummy, dummy, 100000, 1000, None, 0)
     assert ei.value.status == T.E_INVALID
