@@ -46,12 +46,15 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-cloud", action="store_true")  # skip the cloud scene and the per-config timings
     p.add_argument("--solver", type=int, default=0)
     # variants (not the headline): coupling selection with threshold c_min
     # (Sec. 2, scattering graph C > c_min) and other plume shapes
     p.add_argument("--c-min", type=float, default=0.0)
     p.add_argument("--shape", default="64x64x32")
+    p.add_argument("--workload", default="plume", choices=["plume", "cloud"])  # cloud: a variant line
     p.add_argument("--aniso", action="store_true")  # edge unknowns (arrival direction kept)
+    p.add_argument("--oracle-times", action="store_true", help=argparse.SUPPRESS)  # child: oracle timings
     return p.parse_args()
 
 
@@ -64,6 +67,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# the sources each traffic record depends on
+TRAFFIC_SOURCES = {
+    "k_tile_OpCheb": ("kernels_solve.cu", "stage.cuh", "kern.h"),
+    "assembly": ("kernels_asm.cu", "asm_util.cuh", "stage.cuh", "kern.h"),
+    "cloud_gmres_prod": ("kernels_solve.cu", "stage.cuh", "kern.h"),
+}
+
+
 def traffic_record(kernel: str):
     """Per-launch DRAM bytes of a kernel from the committed ncu summary, if the
     summary's source hash matches the kernel source as it is now."""
@@ -72,7 +83,7 @@ def traffic_record(kernel: str):
     csrc = os.path.join(ROOT, "paper_2503_16037_gb300", "csrc")
     try:
         h = hashlib.sha256()
-        for f in ("kernels_solve.cu", "stage.cuh", "kern.h"):
+        for f in TRAFFIC_SOURCES[kernel]:
             h.update(open(os.path.join(csrc, f), "rb").read())
         sha = h.hexdigest()[:16]
         for line in open(path):
@@ -82,6 +93,77 @@ def traffic_record(kernel: str):
     except OSError:
         pass
     return None
+
+
+class NvmlClocks:
+    """SM clock and throttle-reason sampling through NVML (read-only queries),
+    every ~2 ms in a thread during the timed region."""
+
+    HW_SLOWDOWN, SW_THERMAL, HW_THERMAL, SW_POWER_CAP = 0x8, 0x20, 0x40, 0x4
+
+    def __init__(self, uuid=None, pci=None):
+        import ctypes
+        self.ok = False
+        self.samples = []
+        try:
+            self.L = ctypes.CDLL("libnvidia-ml.so.1")
+        except OSError:
+            return
+        self.c = ctypes
+        if self.L.nvmlInit_v2() != 0:
+            return
+        self.h = ctypes.c_void_p()
+        # the device torch runs on, by UUID (else PCI address): NVML indices
+        # need not follow CUDA_VISIBLE_DEVICES
+        found = False
+        if uuid:
+            found = self.L.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h)) == 0
+        if not found and pci:
+            found = self.L.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(self.h)) == 0
+        self.ok = found
+
+    def _one(self):
+        c = self.c
+        sm, mx, rs = c.c_uint(0), c.c_uint(0), c.c_ulonglong(0)
+        if self.L.nvmlDeviceGetClockInfo(self.h, 1, c.byref(sm)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.L.nvmlDeviceGetMaxClockInfo(self.h, 1, c.byref(mx))
+        self.L.nvmlDeviceGetCurrentClocksEventReasons(self.h, c.byref(rs))
+        return sm.value, mx.value, rs.value
+
+    def start(self):
+        if not self.ok:
+            return
+        self.stop_flag = False
+
+        def run():
+            while not self.stop_flag:
+                v = self._one()
+                if v:
+                    self.samples.append(v)
+                time.sleep(0.002)
+        self.th = threading.Thread(target=run, daemon=True)
+        self.th.start()
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self.stop_flag = True
+        self.th.join(timeout=2)
+        v = self._one()  # at least one sample taken at the end of the region
+        if v:
+            self.samples.append(v)
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, _, r in self.samples:
+            for bit, name in ((self.HW_SLOWDOWN, "hw_slowdown"), (self.HW_THERMAL, "hw_thermal_slowdown"),
+                              (self.SW_THERMAL, "sw_thermal_slowdown"), (self.SW_POWER_CAP, "sw_power_cap")):
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(x[0] for x in self.samples),
+                "sm_max_mhz": max(x[1] for x in self.samples), "samples": len(self.samples),
+                "reasons": sorted(reasons), "source": "NVML, polled every ~2 ms"}
 
 
 class Clocks:
@@ -152,16 +234,14 @@ def cpu_baseline(sc, full=True):
 
 
 def run_reference(args, rank):
-    """Reference arm: the FP64 CPU oracle, timed on the host cores."""
+    """Reference arm: the FP64 CPU oracle, timed on the host cores, one full
+    plume scene (64x64x32, the headline workload) per step."""
     if rank != 0:
         return
     from paper_2503_16037_gb300 import scenes
     from oracle import oracle
     oracle.build()
-    # bounded sample: a quarter of the plume's columns (32x32x32, same physics);
-    # oracle work is proportional to the column count, so the rate is scaled by 1/4
-    sample = scenes.make_plume(nx=32, ny=32, nz=32)
-    frac = (32 * 32) / (64 * 64)
+    sample = scenes.make_plume()
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.run(sample, threads=cores)
@@ -171,17 +251,39 @@ def run_reference(args, rank):
         oracle.run(sample, threads=cores)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    value = frac * args.steps / tot
+    value = args.steps / tot
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "scenes/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "32x32x32 plume per step (1/4 of the columns), rate scaled x1/4"},
+        "config": {"workload": WORKLOAD, "sample": "one full plume scene 64x64x32 per step (all stages)"},
         "cpu_baseline": {"value": value, "unit": "scenes/s", "cores": cores, "kind": "oracle",
-                         "sample": "32x32x32 plume per step, FP64 C oracle with OpenMP on all host cores"},
+                         "sample": "one full plume scene 64x64x32 per step, FP64 C oracle with OpenMP on all "
+                                   "host cores"},
         "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def oracle_times():
+    """FP64 oracle wall time per scene for the three workloads of the method
+    (8^3 plain, 64x64x32 plume, 128x128x40 cloud), single-threaded and on all
+    host cores; run in a child process (bench.py --oracle-times)."""
+    from paper_2503_16037_gb300 import scenes
+    from oracle import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    out = {"cores": cores}
+    for name, sc in (("plain 8x8x8 R1", scenes.make_plain()), ("plume 64x64x32 R2", scenes.make_plume()),
+                     ("cloud 128x128x40 R2", scenes.make_cloud())):
+        row = {}
+        for th, key in ((cores, "all_cores_s"), (1, "one_thread_s")):
+            t0 = time.perf_counter()
+            r = oracle.run(sc, threads=th)
+            row[key] = time.perf_counter() - t0
+            row["gmres_iters"] = r["gmres_iters"]
+        out[name] = row
+        print(json.dumps(out), flush=True)  # partial results survive a timeout
 
 
 SERVE_SHAPES = [(16, 16, 16), (32, 32, 24), (48, 48, 32), (64, 64, 32), (96, 96, 32)]
@@ -289,6 +391,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.oracle_times:
+        oracle_times()
+        return
 
     import numpy as np
     import torch
@@ -310,8 +415,12 @@ def main():
     from paper_2503_16037_gb300 import tursca as T
 
     nx, ny, nz = (int(v) for v in args.shape.lower().split("x"))
-    variant = args.c_min > 0.0 or (nx, ny, nz) != (64, 64, 32) or args.aniso
-    sc = scenes.make_plume(nx=nx, ny=ny, nz=nz).replace(c_min=args.c_min)
+    variant = args.c_min > 0.0 or (nx, ny, nz) != (64, 64, 32) or args.aniso or args.workload != "plume"
+    if args.workload == "cloud":
+        sc = scenes.make_cloud().replace(c_min=args.c_min)
+        nx, ny, nz = sc.nx, sc.ny, sc.nz
+    else:
+        sc = scenes.make_plume(nx=nx, ny=ny, nz=nz).replace(c_min=args.c_min)
     stream = torch.cuda.current_stream()
     rn = T.Runner(sc, T.FP32_REFINE, stream=stream)
     if args.aniso:
@@ -331,12 +440,16 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    bus = None
+    uuid = pci = None
     try:
-        bus = torch.cuda.get_device_properties(torch.cuda.current_device()).pci_bus_id
+        pr = torch.cuda.get_device_properties(torch.cuda.current_device())
+        uuid = str(pr.uuid)
+        pci = "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
     except Exception:
-        bus = None
-    clk = Clocks(bus)
+        pass
+    clk = NvmlClocks(uuid, pci)
+    if not clk.ok:
+        clk = Clocks(pci)
     clk.start()
     if dist:
         dist.barrier()
@@ -434,7 +547,7 @@ def main():
     # ---- the broken-cloud configuration (128 x 128 x 40, ~81M edges), a few
     # scenes outside the timed region: scenes/s of the same FP32 + refinement path
     cloud = None
-    if rank == 0 and not args.no_serving and not variant:
+    if rank == 0 and not args.no_cloud and not variant:
         try:
             csc = scenes.make_cloud()
             crn = T.Runner(csc, T.FP32_REFINE, stream=stream)
@@ -455,9 +568,82 @@ def main():
                      "solve": {"iters": crn.info.iters, "refinements": crn.info.refinements,
                                "solver": crn.info.solver, "rel_resid64": crn.info.rel_resid64},
                      "timing": "host clock around a synchronised scene, median of 5, L2 flushed"}
+            # roofline of the passes over K inside GMRES (K = 4 nnz bytes of
+            # values, far beyond L2): one profiled scene, events around each
+            # Arnoldi step's run of passes (preconditioner and I - K product)
+            flush.zero_()
+            T.tursca_profile_enable(crn.handle, True)
+            crn.run(ca, cm, rtol=RTOL)
+            cprof = T.tursca_profile_read(crn.handle)
+            T.tursca_profile_enable(crn.handle, False)
+            n_gp, ms_gp = cprof.get("gmres_prod", (0, 0.0))
+            if n_gp:
+                pb = 4 * crn.stats.nnz + 12 * crn.stats.n_nodes
+                avg_s = ms_gp / n_gp / 1000.0
+                peak, peak_kind = peaks()
+                cloud["roofline"] = {
+                    "kernel": "passes over K inside GMRES (k_tile<6, OpSpmv/OpImk<float>>: y = b + K x or "
+                              "y = x - K x, K read once per pass)", "bound": "hbm",
+                    "achieved": pb / avg_s / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": pb / avg_s / 1e9 / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
+                    "algorithmic_bytes_per_launch": pb, "avg_launch_us": avg_s * 1e6, "launches": n_gp,
+                    "traffic": traffic_record("cloud_gmres_prod"),
+                    "timing": "CUDA events on the scene stream around each Arnoldi step's passes over K, one "
+                              "profiled scene, averaged per pass"}
             crn.close()
         except Exception as e:
             cloud = {"error": str(e)[:200]}
+
+    # ---- the three workloads of the method on this GPU in both precisions
+    # (host clock around a synchronised scene, median of 5, L2 flushed) and
+    # the FP64 oracle on the host cores, one thread and all cores (a child
+    # process, bounded by a timeout)
+    configs = None
+    if rank == 0 and not args.no_cloud and not variant:
+        configs = {}
+        try:
+            for name, mk in (("plain 8x8x8 R1", lambda p: scenes.make_plain().replace(precision=p)),
+                             ("plume 64x64x32 R2", lambda p: scenes.make_plume(precision=p)),
+                             ("cloud 128x128x40 R2", lambda p: scenes.make_cloud(precision=p))):
+                row = {}
+                for prec, key in ((T.FP64, "gpu_fp64_ms"), (T.FP32_REFINE, "gpu_fp32_refine_ms")):
+                    xrn = T.Runner(mk(0 if prec == T.FP64 else 1), prec, stream=stream)
+                    xa, xm = xrn.fields("cuda")
+                    xrn.run(xa, xm, rtol=RTOL)
+                    xt = []
+                    for _ in range(5):
+                        flush.zero_()
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        xrn.run(xa, xm, rtol=RTOL)
+                        torch.cuda.synchronize()
+                        xt.append(time.perf_counter() - t0)
+                    row[key] = 1000.0 * statistics.median(xt)
+                    row["edges"] = xrn.stats.nnz_edges
+                    xrn.close()
+                configs[name] = row
+        except Exception as e:
+            configs["error"] = str(e)[:200]
+        if not args.no_cpu_baseline:
+            try:
+                r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-times"],
+                                   capture_output=True, text=True, timeout=600)
+                lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+                if lines:
+                    ot = json.loads(lines[-1])
+                    for name, row in ot.items():
+                        if name != "cores" and name in configs:
+                            configs[name].update({"oracle_" + k: v for k, v in row.items()})
+                    configs["oracle_cores"] = ot.get("cores")
+            except subprocess.TimeoutExpired as e:
+                configs["oracle_error"] = "oracle timings exceeded 600 s"
+                out = e.stdout.decode() if isinstance(e.stdout, bytes) else (e.stdout or "")
+                lines = [x for x in out.splitlines() if x.startswith("{")]
+                if lines:
+                    ot = json.loads(lines[-1])
+                    for name, row in ot.items():
+                        if name != "cores" and name in configs:
+                            configs[name].update({"oracle_" + k: v for k, v in row.items()})
 
     # ---- serving (continuous batching over resident slots), rank 0 of one GPU
     serve = None
@@ -495,6 +681,26 @@ def main():
                 "traffic": traffic_record("k_tile_OpCheb") if not variant else None,
                 "algorithmic_bytes_per_launch": spmv_bytes,
                 "avg_launch_us": avg_s * 1e6}
+    # ---- roofline of the assembly (edge march and edge weights, with the
+    # per-scene tables): algorithmic bytes per scene = fields read 4 N (2 + S)
+    # + values written 4 nnz + s, e1, g^sun 12 N + tau_inf round trip
+    # 8 N n_up, over the summed event time of the table stage and the edge
+    # kernel
+    roof_asm = None
+    n_pre, ms_pre = prof.get("assemble_pre", (0, 0.0))
+    n_rows, ms_rows = prof.get("assemble_rows", (0, 0.0))
+    if n_pre and n_rows:
+        asm_bytes = (4 * st.n_nodes * (2 + sc.n_species) + 4 * st.nnz + 12 * st.n_nodes
+                     + 8 * st.n_nodes * st.n_up_dirs)
+        t_asm = (ms_pre / n_pre + ms_rows / n_rows) / 1000.0
+        roof_asm = {"kernel": "assembly: per-scene tables (k_prep, k_segtau_fixed, k_tinf, k_tinfg, k_sun, "
+                              "k_znorm on four streams) + edge kernel k_asm0", "bound": "hbm",
+                    "achieved": asm_bytes / t_asm / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": asm_bytes / t_asm / 1e9 / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
+                    "algorithmic_bytes_per_scene": asm_bytes, "us_per_scene": t_asm * 1e6,
+                    "edge_kernel_us": ms_rows / n_rows * 1000.0, "tables_us": ms_pre / n_pre * 1000.0,
+                    "edges_per_s": st.nnz_edges / t_asm,
+                    "traffic": traffic_record("assembly") if not variant else None}
     # ---- accuracy of this run against the FP64 oracle (also the CPU baseline)
     cpu = None
     parity = None
@@ -512,13 +718,15 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if not variant else
-                   "plume %dx%dx%d voxels, R=2, coupling selection c_min = %g%s (variant, not the headline)"
-                   % (nx, ny, nz, args.c_min, ", edge unknowns (arrival direction kept)" if args.aniso else ""),
+                   "%s %dx%dx%d voxels, R=2, coupling selection c_min = %g%s (variant, not the headline)"
+                   % (args.workload, nx, ny, nz, args.c_min,
+                      ", edge unknowns (arrival direction kept)" if args.aniso else ""),
                    "nnz_edges": st.nnz_edges, "nnz_stored": st.nnz, "nodes": st.n_nodes,
                    "l2": "flushed between timed steps (256 MB write, outside the timed interval)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "edges_per_s": value * st.nnz_edges,
         "roofline": roof,
+        "roofline_assembly": roof_asm,
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scenes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -531,6 +739,7 @@ def main():
         "adjoint": adj,
         "serving": serve,
         "cloud": cloud,
+        "configs": configs,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
     }
     print(json.dumps(line), flush=True)

@@ -312,7 +312,9 @@ size_t tursca_scene_device_bytes(const tursca_scene *scene);
 typedef struct {
     char name[32];      /* "spmv", "resid64", "assemble_rows", "assemble_pre", "render", "cheb",
                            "gmres_orth" (both Gram-Schmidt passes of one Arnoldi step),
-                           "select" (coupling selection) */
+                           "select" (coupling selection), "gmres_prod" (the passes over K of
+                           one Arnoldi step: preconditioner and product with I - K, each
+                           counted as a launch) */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;
@@ -353,14 +355,21 @@ tursca_status tursca_quadrature(const tursca_grid_desc *desc, double *q_iso, dou
  *     TURSCA_F_COL, TURSCA_F_VAL of an FP32 scene); s [n_nodes] float;
  *     x [n_nodes] double (output); resid2: optional device double receiving
  *     ||r||^2 of the last refinement.  All are caller-owned device pointers.
- *   1 <= n_nodes <= 1048576, 0 <= sweeps <= 100000, 1 <= refinements <= 1000;
- *     larger sizes or null pointers return TURSCA_E_INVALID before any work.
+ *   1 <= n_nodes <= 1048576, 0 <= sweeps <= 100000, 1 <= refinements <= 1000,
+ *     and at most 10^6 launches ((sweeps + 2) * refinements + 2); larger sizes
+ *     or null pointers return TURSCA_E_INVALID before any work.
  * Its work vectors live in one fixed device array of about 12 MiB that every
- * GPU loading the library holds until the process exits.  The first call on
- * each device looks up that array's address (with that device current); make
- * that first call before any stream capture.  Every call shares the array and
- * finds the previous call's contents in it, so calls whose work overlaps on
- * the GPU (different streams, or different host threads) race with each other.
+ * GPU loading the library holds until the process exits.  Every call looks up
+ * that array's address in the current device's context (the first call in a
+ * context loads the library's device code there; make that first call before
+ * any stream capture).  Every call shares the array and finds the previous
+ * call's contents in it, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race with each other.
+ * Errors: TURSCA_E_CUDA, without launching anything, when a CUDA error is
+ * already pending in the calling thread (it is left pending for its owner) or
+ * the array's address cannot be found; TURSCA_E_CUDA when a launch fails (the
+ * call stops at the first failed launch; later asynchronous faults surface at
+ * the caller's next synchronisation).
  * The call allocates nothing and returns without synchronising. */
 tursca_status tursca_csr_solve_noalloc(const int32_t *row_ptr, const int32_t *col, const float *val, int n_nodes,
                                        const float *s, double *x, int sweeps, int refinements, double *resid2,

@@ -171,10 +171,12 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv",   "resid64", "assemble_rows", "assemble_pre",
-                                  "render", "cheb",    "gmres_orth",    "select"};
-constexpr int kNProf = 8;
-enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7 };
+const char *const kProfNames[] = {"spmv",   "resid64", "assemble_rows", "assemble_pre", "render",
+                                  "cheb",   "gmres_orth", "select",      "gmres_prod"};
+constexpr int kNProf = 9;
+// P_GPROD: the passes over K of one Arnoldi step (preconditioner and product
+// with I - K), counted as launches
+enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7, P_GPROD = 8 };
 
 // NVTX range around one call of the C ABI (a stage of the path), for
 // profilers that filter or group by range; free when no tool is attached
@@ -623,14 +625,14 @@ tursca_status gmres(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp, 
         bool done = false;
         for (k = 0; k < m; ++k) {
             T *vk = V + (size_t)k * ld, *vn = V + (size_t)(k + 1) * ld;
-            int pi = prof_begin(sc, P_SPMV);
+            int pi = prof_begin(sc, P_GPROD);
             if (kGmresPoly > 1) {
                 apply_poly(vk, z0, z1);  // z = M^-1 v_k
                 tk::launch_imk<T>(sc->st, g, gp, val, z0, w);
             } else {
                 tk::launch_imk<T>(sc->st, g, gp, val, vk, w);
             }
-            prof_end(sc, pi);
+            prof_end(sc, pi, kGmresPoly);
             int po = prof_begin(sc, P_ORTH);
             tk::launch_dots<T, T>(sc->st, g, V, ld, k + 1, w, sc->part, nb, sc->dred);
             tk::launch_gmres_update<T>(sc->st, n, w, V, ld, k + 1, sc->dred);

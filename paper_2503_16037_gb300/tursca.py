@@ -220,9 +220,9 @@ def tursca_profile_enable(scene, on: bool):
 
 
 def tursca_profile_read(scene) -> dict:
-    arr = (tursca_kernel_stat * 8)()
+    arr = (tursca_kernel_stat * 16)()
     n = C.c_int(0)
-    _check(scene, lib().tursca_profile_read(scene, arr, 8, C.byref(n)))
+    _check(scene, lib().tursca_profile_read(scene, arr, 16, C.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
 
 
