@@ -48,6 +48,7 @@ class OrcDesc(C.Structure):
         ("flags", C.c_int), ("threads", C.c_int),
         ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
         ("c_min", C.c_double),
+        ("max_couplings", C.c_long),
     ]
 
 
@@ -85,6 +86,8 @@ class OrcResult(C.Structure):
         ("X", _dp),
         ("arrive", _dp), ("esc_out", _dp),
         ("aniso_iters", C.c_int),
+        ("c_min_used", C.c_double),
+        ("n_couplings", C.c_long), ("n_kept", C.c_long),
     ]
 
 
@@ -136,6 +139,7 @@ def _desc(sc, flags=0, threads=0, gmres_tol=1e-13):
     d.flags, d.threads = flags, threads
     d.gmres_tol, d.gmres_restart, d.gmres_maxit = gmres_tol, 60, 20000
     d.c_min = getattr(sc, "c_min", 0.0)
+    d.max_couplings = int(getattr(sc, "max_couplings", 0))
     return d
 
 
@@ -180,6 +184,7 @@ def run(sc, flags: int = 0, threads: int = 0, gmres_tol: float = 1e-13) -> dict:
             "slot_dep": _arr(r.slot_dep, ns), "slot_depsun": _arr(r.slot_depsun, ns),
             "slot_val": _arr(r.slot_val, ns), "slot_valsun": _arr(r.slot_valsun, ns),
             "s": _arr(r.s, nn),
+            "c_min_used": r.c_min_used, "n_couplings": int(r.n_couplings), "n_kept": int(r.n_kept),
         }
         if not flags & NO_SOLVE:
             res.update({

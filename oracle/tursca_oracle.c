@@ -79,6 +79,7 @@ typedef struct {
     int gmres_restart;
     int gmres_maxit;
     double c_min; /* coupling threshold of the scattering graph; 0: full stencil */
+    long max_couplings; /* > 0: keep the max_couplings largest couplings (Sec. 3); c_min must be 0 */
 } orc_desc;
 
 typedef struct {
@@ -113,6 +114,11 @@ typedef struct {
     double *X;                 /* [n_nodes][n_dirs + n_gdirs]: scattered power by arrival direction */
     double *arrive, *esc_out;  /* [n_nodes]: power arriving at a node; power its chains carry out of the TOA */
     int aniso_iters;
+    /* coupling selection: the threshold applied (0: none), the chains that
+     * carry a coupling (have a receiver other than their source) and how
+     * many of them were kept */
+    double c_min_used;
+    long n_couplings, n_kept;
 } orc_result;
 
 /* ------------------------------------------------------------------------ */
@@ -980,12 +986,61 @@ static int orc_aniso(const orc_desc *d, orc_result *r, const double *g, const do
     return 0;
 }
 
-int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const double *g, orc_result **out) {
+/* The preselected maximum number of couplings (Sec. 3: TURSCA keeps a
+ * fixed count of the largest couplings instead of a threshold).  Every chain
+ * (j, u) with a receiver other than its source carries one coupling C; with
+ * K = max_couplings the scattering graph keeps the chains whose C exceeds the
+ * (K + 1)-th largest of them, so exactly K are kept when that value is not
+ * tied with the K-th (a tie at the boundary drops the whole tied group).
+ * K at or above the count keeps every chain.  Returns the threshold for the
+ * C > c_min rule: 0 for no selection, the smallest positive double when the
+ * (K + 1)-th largest coupling is 0 (the zero couplings go). */
+static int orc_cmp_desc(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+static double orc_topk_threshold(const orc_desc *d, const orc_result *r, const double *mu_e,
+                                 const double *mus, long *n_couplings) {
+    int na = r->n_atm, nn = r->n_nodes, nd = r->n_dirs, ngd = r->n_gdirs;
+    double *all = malloc(sizeof(double) * ((size_t)na * nd + (size_t)r->n_ground * ngd));
+    long n = 0;
+    orc_chain *ch = malloc(sizeof(orc_chain));
+    for (int j = 0; j < nn; ++j) {
+        int ndir = j < na ? nd : ngd;
+        double mus_src = j < na ? mus[j] : r->mu_s_lamb;
+        for (int u = 0; u < ndir; ++u) {
+            if (j < na)
+                orc_atm_chain(d, r, mu_e, j, u, ch);
+            else
+                orc_gnd_chain(d, r, mu_e, j - na, u, ch);
+            double C = orc_coupling(r, mus, ch, mus_src);
+            if (C >= 0.0) all[n++] = C;
+        }
+    }
+    free(ch);
+    *n_couplings = n;
+    double thr = 0.0;
+    if (d->max_couplings < n) {
+        qsort(all, (size_t)n, sizeof(double), orc_cmp_desc);
+        thr = all[d->max_couplings];
+        if (!(thr > 0.0)) thr = 4.9406564584124654e-324; /* keep C > 0 */
+    }
+    free(all);
+    return thr;
+}
+
+int orc_run(const orc_desc *d_in, const double *mu_a, const double *mu_s, const double *g, orc_result **out) {
 #ifdef _OPENMP
-    if (d->threads > 0) omp_set_num_threads(d->threads);
+    if (d_in->threads > 0) omp_set_num_threads(d_in->threads);
 #endif
-    if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->R < 1 || d->R > 2 || d->M < 8 || d->S < 1) return 1;
-    if ((d->flags & ORC_ANISO) && d->c_min > 0.0) return 2; /* not combined with coupling selection */
+    if (d_in->nx < 1 || d_in->ny < 1 || d_in->nz < 1 || d_in->R < 1 || d_in->R > 2 || d_in->M < 8 || d_in->S < 1)
+        return 1;
+    if ((d_in->flags & ORC_ANISO) && (d_in->c_min > 0.0 || d_in->max_couplings > 0))
+        return 2; /* not combined with coupling selection */
+    if (d_in->max_couplings < 0 || (d_in->max_couplings > 0 && d_in->c_min > 0.0)) return 3;
+    orc_desc dsel = *d_in; /* c_min replaced by the threshold of a preselected count */
+    const orc_desc *d = &dsel;
     orc_result *r = calloc(1, sizeof(orc_result));
     int nx = d->nx, ny = d->ny, nz = d->nz, S = d->S;
     int na = nx * ny * nz, ng = nx * ny, nn = na + ng;
@@ -1010,6 +1065,8 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     }
     /* Lambertian surface nodes couple with mu_s^Lamb = A max mu_s (Sec. 3) */
     r->mu_s_lamb = d->albedo * mus_max;
+    if (d_in->max_couplings > 0) dsel.c_min = orc_topk_threshold(d_in, r, mue, mus, &r->n_couplings);
+    r->c_min_used = dsel.c_min;
 
     double mu0 = cos(d->sza * ORC_PI / 180.0);
     double f0 = d->f0;
@@ -1064,8 +1121,10 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
     r->esc_iso = calloc(nn, sizeof(double));
     r->esc_sun = calloc(nn, sizeof(double));
 
+    long n_cpl_all = 0, n_kpt_all = 0;
 #pragma omp parallel
     {
+        long n_cpl = 0, n_kpt = 0;
         orc_chain *ch = malloc(sizeof(orc_chain) * ORC_MAXDIR);
         double qs[ORC_MAXDIR], ci[ORC_MAXDIR], cs[ORC_MAXDIR];
         /* per-source quadrature after coupling selection */
@@ -1120,6 +1179,11 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
                     r->chain_C[(size_t)j * nd + u] = orc_coupling(r, mus, &ch[u], j < na ? mus[j] : r->mu_s_lamb);
                     r->chain_E[(size_t)j * nd + u] = ch[u].escape;
                 }
+            for (int u = 0; u < ndir; ++u)
+                if (orc_coupling(r, mus, &ch[u], j < na ? mus[j] : r->mu_s_lamb) >= 0.0) {
+                    n_cpl++;
+                    n_kpt += kept[u];
+                }
             int cnt = 0;
             double ei = 0.0, es = 0.0;
             for (int u = 0; u < ndir; ++u) {
@@ -1143,7 +1207,13 @@ int orc_run(const orc_desc *d, const double *mu_a, const double *mu_s, const dou
         }
         free(ch);
         free(qsun_sel);
+#pragma omp atomic
+        n_cpl_all += n_cpl;
+#pragma omp atomic
+        n_kpt_all += n_kpt;
     }
+    r->n_couplings = n_cpl_all;
+    r->n_kept = n_kpt_all;
 
     /* gather into row-major order (stable: by source, then direction) */
     int *rowcnt = calloc(nn + 1, sizeof(int));

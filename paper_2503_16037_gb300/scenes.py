@@ -48,6 +48,7 @@ class Scene:
     M: int = 8192
     coupling: int = 1
     c_min: float = 0.0        # coupling threshold of the scattering graph (0: full stencil)
+    max_couplings: int = 0    # > 0: keep this many of the largest couplings instead (c_min must be 0)
     precision: int = 0        # 0 FP64, 1 FP32 + FP64 refinement
     name: str = "scene"
 

@@ -764,6 +764,135 @@ def test_p11_energy_conservation_with_selection(R, sza, saa):
     assert abs(total - incident) <= 1e-12 * incident
 
 
+# P11 (top-K): the preselected maximum number of couplings of Sec. 3
+
+def _all_couplings(sc, r):
+    """Every chain's coupling C = sqrt(mu_s(source) mu_s(first receiver)) / d
+    (Eq. scatt_coup), computed here from the grid and the fields: atmospheric
+    sources along each direction u (first receiver j + u, or the ground when
+    the chain crosses z = 0 first, none when it leaves through the TOA),
+    ground sources along each ground chain (first member voxel)."""
+    nx, ny, nz = sc.nx, sc.ny, sc.nz
+    mus = np.zeros((nz, ny, nx))
+    for sp in range(sc.n_species):
+        mus = mus + np.asarray(sc.mu_s[sp], dtype=np.float64)
+    mus_lamb = sc.albedo * float(mus.max())
+    h = (sc.hx, sc.hy, sc.hz)
+    out = []
+    for (ux, uy, uz) in r["dirs"]:
+        p0, p1, p2 = ux * h[0], uy * h[1], uz * h[2]
+        L = math.sqrt(p0 * p0 + p1 * p1 + p2 * p2)
+        for z in range(nz):
+            rz = z + uz
+            if rz >= nz:
+                continue
+            for y in range(ny):
+                for x in range(nx):
+                    if rz >= 0:
+                        mn, d = float(mus[rz, (y + uy) % ny, (x + ux) % nx]), L
+                    else:
+                        mn, d = mus_lamb, (z + 0.5) / -uz * L
+                    out.append(math.sqrt(float(mus[z, y, x]) * mn) / d)
+    for mem in r["gdir_mem"][: r["n_gdirs"]]:
+        m0, m1, m2 = (int(v) for v in mem[0])
+        p0, p1, p2 = m0 * h[0], m1 * h[1], (m2 - 0.5) * h[2]
+        L = math.sqrt(p0 * p0 + p1 * p1 + p2 * p2)
+        for y in range(ny):
+            for x in range(nx):
+                out.append(math.sqrt(mus_lamb * float(mus[m2 - 1, (y + m1) % ny, (x + m0) % nx])) / L)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("R", [1, 2])
+def test_p11_topk_threshold_is_the_k_plus_first_largest_coupling(R):
+    """Keeping the K largest couplings is the threshold rule C > c_min with
+    c_min the (K + 1)-th largest coupling (brute force over every chain);
+    couplings tie in pairs (a chain and its reverse), so a boundary inside a
+    tied group keeps fewer than K."""
+    sc = scenes.make_random(7, 6, 4, seed=31, S=2, R=R, M=512, zero_frac=0.0, albedo=0.3)
+    r0 = O.run(sc, flags=O.NO_SOLVE)
+    C = np.sort(_all_couplings(sc, r0))[::-1]
+    assert r0["n_couplings"] == C.size and r0["n_kept"] == C.size and r0["c_min_used"] == 0.0
+    for K in (1, 2, 3, C.size // 3, C.size // 3 + 1, C.size // 2, C.size - 1):
+        r = O.run(sc.replace(max_couplings=int(K)), flags=O.NO_SOLVE)
+        assert r["c_min_used"] == C[K], K
+        assert r["n_kept"] == int((C > C[K]).sum()) <= K, K
+    assert r["n_kept"] == C.size - 1 or C[-1] == C[-2]
+
+
+def test_p11_topk_at_or_above_the_count_is_the_full_stencil():
+    sc = scenes.make_random(9, 8, 5, seed=21, S=2, R=2, M=1024, zero_frac=0.0)
+    r0 = O.run(sc)
+    for K in (r0["n_couplings"], 10 ** 9):
+        r1 = O.run(sc.replace(max_couplings=K))
+        assert r1["c_min_used"] == 0.0 and r1["n_kept"] == r0["n_couplings"]
+        for k in ("slot_val", "slot_valsun", "x", "rad"):
+            assert np.array_equal(r0[k], r1[k]), k
+
+
+def test_p11_topk_equals_the_threshold_rule_and_nests():
+    """Top-K reproduces the c_min selection at its threshold bit for bit, and
+    the kept edges shrink as K does; zero couplings (non-scattering voxels)
+    go first."""
+    sc = scenes.make_random(8, 7, 5, seed=22, S=2, R=2, M=1024, zero_frac=0.1)
+    full = O.run(sc, flags=O.NO_SOLVE)
+    prev = None
+    for frac in (0.9, 0.6, 0.3, 0.1):
+        K = int(frac * full["n_couplings"])
+        rk = O.run(sc.replace(max_couplings=K))
+        rc = O.run(sc.replace(c_min=rk["c_min_used"]))
+        for k in ("slot_val", "slot_valsun", "x", "rad"):
+            assert np.array_equal(rk[k], rc[k]), (frac, k)
+        nz_now = set(zip(rk["slot_row"][rk["slot_val"] != 0], rk["slot_col"][rk["slot_val"] != 0],
+                         rk["slot_dir"][rk["slot_val"] != 0]))
+        if prev is not None:
+            assert nz_now < prev
+        prev = nz_now
+    zero = _all_couplings(sc, full) == 0.0
+    assert zero.any()
+    K = int((~zero).sum())  # exactly the positive couplings survive
+    rz = O.run(sc.replace(max_couplings=K), flags=O.NO_SOLVE)
+    assert rz["c_min_used"] > 0.0 and rz["c_min_used"] < 1e-300 and rz["n_kept"] == K
+
+
+@pytest.mark.parametrize("R,A", [(1, 0.0), (2, 0.4)])
+def test_p11_energy_conservation_with_topk(R, A):
+    """Energy balance with a quarter of the couplings kept.  Sources that keep
+    no direction scatter their power out of the graph ("lost"), and with
+    omega = 1 a set of sources that keep only directions among themselves
+    (horizontal chains deposit everything) would trap power (rho(K) = 1), so
+    the layers absorb a little (omega = 0.97): incident = TOA escape + ground
+    absorption + voxel absorption (of the direct beam and of what arrives) +
+    lost."""
+    nx, ny, nz = 6, 5, 6
+    om = 0.97
+    rng = np.random.default_rng(9)
+    sc = scenes.make_layered(nx, ny, nz, rng.uniform(0.1, 2.0, nz), [om], g=(0.6,), albedo=A, R=R, sza=40.0,
+                             saa=70.0, vza=10, h=(0.1, 0.08, 0.12), M=1024)
+    n = O.run(sc, flags=O.NO_SOLVE)["n_couplings"]
+    r = O.run(sc.replace(max_couplings=n // 4), gmres_tol=1e-15)
+    assert 0 < r["n_kept"] <= n // 4 and r["rel_resid"] < 1e-14
+    na, nn = r["n_atm"], r["n_nodes"]
+    mu0 = math.cos(math.radians(40.0))
+    incident = nx * ny * mu0 * sc.hx * sc.hy
+    e1, x = r["e1"], r["x"]
+    escape = float(e1 @ r["esc_sun"] + x @ r["esc_iso"])
+    direct = float(mu0 * sc.hx * sc.hy * r["tsun"][na:].sum())
+    row, col = r["slot_row"], r["slot_col"]
+    gnd = row >= na
+    diffuse = float((r["slot_depsun"][gnd] * e1[col[gnd]]).sum() + (r["slot_dep"][gnd] * x[col[gnd]]).sum())
+    dep_iso = np.zeros(nn)
+    np.add.at(dep_iso, col, r["slot_dep"])
+    dep_sun = np.zeros(nn)
+    np.add.at(dep_sun, col, r["slot_depsun"])
+    lost = float(e1 @ (1.0 - dep_sun - r["esc_sun"]) + x @ (1.0 - dep_iso - r["esc_iso"]))
+    assert lost > 0.0
+    # voxels: e1 = omega x (beam extinction), x = omega x (power arriving)
+    absorbed = (1.0 - om) / om * float(e1[:na].sum() + x[:na].sum())
+    total = escape + (1.0 - A) * (direct + diffuse) + absorbed + lost
+    assert abs(total - incident) <= 1e-12 * incident
+
+
 # --------------------------------------------------------------------------
 # P12: anisotropic multiple scattering, the edge unknowns of Eq. flux_system
 # (the arrival direction kept into every scattering)
