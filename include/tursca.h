@@ -270,6 +270,20 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     weights depend on the scattering coefficients only, so tursca_adjoint
  *     (a gradient with respect to absorption) reads the same weights.
  *     Changing the value invalidates the current assembly.
+ *   TURSCA_OPT_MAX_COUPLINGS: K >= 0, a whole number (default 0: off).  The
+ *     preselected maximum number of couplings of Sec. 3: the graph keeps the
+ *     chains whose coupling exceeds the (K + 1)-th largest coupling over
+ *     every chain that has a receiver other than its source, found in FP64
+ *     at every assembly (an exact radix select over the chains' couplings);
+ *     then everything proceeds as TURSCA_OPT_COUPLING_MIN with that
+ *     threshold (the smallest positive double when that coupling is 0, so
+ *     zero couplings go first).  Exactly K chains are kept unless couplings
+ *     tie at the boundary (a chain and its reverse share one coupling; a tied
+ *     group at the boundary goes as a whole); K at or above the number of
+ *     chains keeps the full stencil.  Excludes c_min > 0 (TURSCA_E_INVALID at
+ *     assembly).  Memory: 8 bytes per chain (n_atm n_dirs + n_ground
+ *     n_gdirs) for the keys, besides what TURSCA_OPT_COUPLING_MIN allocates.
+ *     Changing the value invalidates the current assembly.
  *   TURSCA_OPT_ANISO: 0 (default); 1 keeps the arrival direction of the
  *     light into every scattering (the edge unknowns of Eq. flux_system;
  *     the default node form re-emits isotropically after the first
@@ -283,7 +297,7 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     sums the series of Eq. fs_sum until the relative change of X is at most
  *     rtol (FP32 scenes: at least 1e-6); iters counts its terms and
  *     rel_resid64 holds the last relative change.  Combines with neither
- *     TURSCA_OPT_SINGLE_SCATTER nor c_min > 0 (TURSCA_E_INVALID at
+ *     TURSCA_OPT_SINGLE_SCATTER nor coupling selection (TURSCA_E_INVALID at
  *     assembly); tursca_adjoint returns TURSCA_E_UNSUPPORTED.  Memory:
  *     2 (n_dirs + n_gdirs) + 2 n_dirs values per node plus n_dirs haloed
  *     planes, in the compute type.  Changing the value invalidates the
@@ -297,9 +311,18 @@ enum {
     TURSCA_OPT_GATHER_TILE = 5,
     TURSCA_OPT_SINGLE_SCATTER = 6,
     TURSCA_OPT_COUPLING_MIN = 7,
-    TURSCA_OPT_ANISO = 8
+    TURSCA_OPT_ANISO = 8,
+    TURSCA_OPT_MAX_COUPLINGS = 9
 };
 tursca_status tursca_set_option(tursca_scene *scene, int option, double value);
+
+/* The coupling selection of the current assembly: *threshold the c_min
+ * applied (0: the full stencil); with TURSCA_OPT_MAX_COUPLINGS also
+ * *n_couplings, the chains that carry a coupling, and *n_kept, those kept
+ * (both -1 otherwise).  Any output may be NULL.  TURSCA_E_STATE before the
+ * first assembly. */
+tursca_status tursca_selection_info(const tursca_scene *scene, double *threshold, long long *n_couplings,
+                                    long long *n_kept);
 
 /* Number of kernel launches the scene has issued since creation. */
 long long tursca_launch_count(const tursca_scene *scene);

@@ -147,6 +147,14 @@ struct tursca_scene {
     // coupling selection (c_min > 0): lattice rankings, per-scene buffers and
     // the weight planes of every (source, direction)
     double c_min = 0.0;
+    // the preselected maximum number of couplings (0: off) and the state of
+    // its selection: per-chain keys, the radix histogram, the last threshold,
+    // the number of chains with a receiver
+    long long max_couplings = 0;
+    unsigned long long *topk_keys = nullptr;
+    unsigned int *topk_hist = nullptr, *topk_hist_h = nullptr;
+    double c_eff = 0.0;
+    long long n_couplings = -1, n_kept = -1;
     bool sel_ready = false, sel_asm = false;
     tk::SelP selp{};
     void *w_iso = nullptr, *w_sun = nullptr;
@@ -1361,6 +1369,7 @@ tursca_status tursca_scene_destroy(tursca_scene *sc) {
     for (DevBuf &v : sc->vbuf)
         if (v.p) cudaFree(v.p);
     if (sc->hred) cudaFreeHost(sc->hred);
+    if (sc->topk_hist_h) cudaFreeHost(sc->topk_hist_h);
     for (cudaEvent_t e : sc->ev) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i)
         if (sc->aux[i]) cudaStreamDestroy(sc->aux[i]);
@@ -1695,6 +1704,82 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     return TURSCA_OK;
 }
 
+// The preselected maximum number of couplings K (Sec. 3): sc->c_eff becomes
+// the (K + 1)-th largest FP64 coupling over every chain with a receiver (0
+// when K reaches the count: the full stencil; the smallest positive double
+// when that coupling is 0), found by a radix select over the chains' keys:
+// six passes of at most 11 bits from the top, each a histogram over the keys
+// that share the digits found so far, read back to pick the digit that
+// holds the wanted rank.  Needs the fields of set_medium (the keys are
+// formed from them before the rest of the assembly).
+tursca_status topk_threshold(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp) {
+    const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
+    if (!sc->topk_keys) {
+        CK(dalloc(sc->allocs, sc->topk_keys, (size_t)tot * sizeof(unsigned long long)), "alloc topk keys");
+        CK(dalloc(sc->allocs, sc->topk_hist, sizeof(unsigned int) << tk::kTopkDigitBits), "alloc topk hist");
+        cudaError_t e = cudaMallocHost((void **)&sc->topk_hist_h, sizeof(unsigned int) << tk::kTopkDigitBits);
+        if (e != cudaSuccess) return cuda_fail(sc, e, "alloc pinned");
+    }
+    if (!sc->selp.musmax_bits) {
+        tursca_status e = ensure_select(sc);
+        if (e) return e;
+    }
+    if (sc->d.precision == TURSCA_FP64)
+        tk::launch_topk_keys<double>(sc->st, g, gp, field_p<double>(sc), view_c(sc), sc->selp.musmax_bits,
+                                     sc->topk_keys, &sc->launches);
+    else
+        tk::launch_topk_keys<float>(sc->st, g, gp, field_p<float>(sc), view_c(sc), sc->selp.musmax_bits,
+                                    sc->topk_keys, &sc->launches);
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev), "device");
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "device");
+    const int nb = std::max(1, nsm) * 8;
+    const int nbins = 1 << tk::kTopkDigitBits;
+    unsigned long long prefix = 0ull;
+    int hi = 64;
+    long long rank = sc->max_couplings + 1;  // wanted rank from the top (1-based)
+    long long count = -1;
+    for (int pass = 0; hi > 0; ++pass) {
+        const int width = std::min(tk::kTopkDigitBits, hi), shift = hi - width;
+        tk::launch_topk_hist(sc->st, sc->topk_keys, tot, shift, width, hi, prefix, sc->topk_hist, nb);
+        sc->launches += 1;
+        CK(cudaMemcpyAsync(sc->topk_hist_h, sc->topk_hist, sizeof(unsigned int) * nbins, cudaMemcpyDeviceToHost,
+                           sc->st), "d2h");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        const unsigned int *h = sc->topk_hist_h;
+        if (pass == 0) {
+            count = 0;
+            for (int b = 0; b < nbins; ++b) count += h[b];
+            sc->n_couplings = count;
+            sc->n_kept = 0;
+            if (sc->max_couplings >= count) {
+                sc->c_eff = 0.0;
+                sc->n_kept = count;
+                return TURSCA_OK;
+            }
+        }
+        long long acc = 0;
+        int pick = -1;
+        for (int b = (1 << width) - 1; b >= 0; --b) {
+            if (acc + (long long)h[b] >= rank) {
+                pick = b;
+                break;
+            }
+            acc += h[b];
+        }
+        if (pick < 0) return fail(sc, TURSCA_E_INVALID, "internal error: coupling rank not found");
+        rank -= acc;
+        sc->n_kept += acc;  // keys in higher bins: couplings above the threshold
+        prefix = (prefix << width) | (unsigned long long)pick;
+        hi = shift;
+    }
+    double thr;
+    const unsigned long long bits = prefix - 1ull;
+    std::memcpy(&thr, &bits, sizeof(thr));
+    sc->c_eff = thr > 0.0 ? thr : 4.9406564584124654e-324;  // a zero coupling: keep C > 0
+    return TURSCA_OK;
+}
+
 tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom) {
     const NvtxRange nvtx("tursca_assemble_flux");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
@@ -1702,8 +1787,11 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     if (!sc->built) return fail(sc, TURSCA_E_STATE, "build_graph has not been called");
     if (!sc->medium) return fail(sc, TURSCA_E_STATE, "set_medium has not been called");
     if (!(geom->f0 > 0.0) || !std::isfinite(geom->f0)) return fail(sc, TURSCA_E_INVALID, "f0 must be positive");
-    if (sc->aniso && (sc->single || sc->c_min > 0.0))
-        return fail(sc, TURSCA_E_INVALID, "the anisotropic mode combines with neither single scattering nor c_min > 0");
+    if (sc->aniso && (sc->single || sc->c_min > 0.0 || sc->max_couplings > 0))
+        return fail(sc, TURSCA_E_INVALID,
+                    "the anisotropic mode combines with neither single scattering nor coupling selection");
+    if (sc->c_min > 0.0 && sc->max_couplings > 0)
+        return fail(sc, TURSCA_E_INVALID, "c_min and a maximum number of couplings exclude each other");
     bool same = sc->view_ok && geom->sza == sc->geom.sza && geom->saa == sc->geom.saa && geom->vza == sc->geom.vza &&
                 geom->vaa == sc->geom.vaa && geom->npx == sc->geom.npx && geom->npy == sc->geom.npy;
     if (!same) {
@@ -1778,11 +1866,17 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, sc->segtab_f,
                                        &sc->launches);
     prof_end(sc, p0);
-    if (sc->c_min > 0.0) {
+    sc->c_eff = sc->c_min;
+    sc->n_couplings = sc->n_kept = -1;
+    if (sc->max_couplings > 0) {
+        tursca_status e = topk_threshold(sc, g, gp);
+        if (e) return e;
+    }
+    if (sc->c_eff > 0.0) {
         tursca_status e = ensure_select(sc);
         if (e) return e;
         tk::SelP q = sc->selp;
-        q.c_min = sc->c_min;
+        q.c_min = sc->c_eff;
         int ps = prof_begin(sc, P_SEL);
         if (sc->d.precision == TURSCA_FP64)
             tk::launch_select<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, q, (double *)sc->w_iso,
@@ -1821,7 +1915,7 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
             tk::launch_assemble_rows<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
         prof_end(sc, p1);
     }
-    sc->sel_asm = sc->c_min > 0.0;
+    sc->sel_asm = sc->c_eff > 0.0;
     sc->aniso_asm = sc->aniso != 0;
     CK(cudaGetLastError(), "assemble launch");
     sc->assembled = true;
@@ -2006,6 +2100,14 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
                 sc->assembled = sc->solved = sc->rendered = false;
             }
             return TURSCA_OK;
+        case TURSCA_OPT_MAX_COUPLINGS:
+            if (!(value >= 0.0) || value > 9.0e15 || value != std::floor(value))
+                return fail(sc, TURSCA_E_INVALID, "the maximum number of couplings must be a whole number >= 0");
+            if ((long long)value != sc->max_couplings) {
+                sc->max_couplings = (long long)value;
+                sc->assembled = sc->solved = sc->rendered = false;
+            }
+            return TURSCA_OK;
         case TURSCA_OPT_ANISO:
             if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "anisotropic mode must be 0 or 1");
             if ((int)value != sc->aniso) {
@@ -2074,6 +2176,16 @@ tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int
         out[c].total_ms = ms[c];
     }
     if (n_out) *n_out = m;
+    return TURSCA_OK;
+}
+
+tursca_status tursca_selection_info(const tursca_scene *sc, double *threshold, long long *n_couplings,
+                                    long long *n_kept) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (!sc->assembled) return fail(const_cast<tursca_scene *>(sc), TURSCA_E_STATE, "no assembly yet");
+    if (threshold) *threshold = sc->c_eff;
+    if (n_couplings) *n_couplings = sc->n_couplings;
+    if (n_kept) *n_kept = sc->n_kept;
     return TURSCA_OK;
 }
 

@@ -343,6 +343,111 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
     if (launches) *launches += 4;
 }
 
+// ---------------------------------------------------------------------------
+// The preselected maximum number of couplings (Sec. 3): the threshold that
+// keeps the K largest couplings is the (K + 1)-th largest coupling over every
+// chain that has a receiver.  Each chain's coupling is formed once in FP64
+// with the arithmetic of the selection's FP64 decision above (FP64 species
+// sums, sqrt(mu_s(src) mu_s(n1)) / d), and its bit pattern (a non-negative
+// double orders like its bits) plus one is the chain's key (0: no
+// receiver).  A radix select finds the key of rank K + 1 from the top in
+// passes of kTopkBits bits: every pass histograms, over the keys that share
+// the prefix found so far, the next digit; the host picks the digit that
+// holds the wanted rank.  Keys are [n_atm][nd] then [n_ground][ngd].
+template <typename T>
+__global__ void k_topk_keys(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const unsigned long long *musmax_bits,
+                            unsigned long long *keys) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long na_ch = (long long)g.n_atm * g.nd;
+    const long long tot = na_ch + (long long)g.n_ground * g.ngd;
+    if (e >= tot) return;
+    const double mus_lamb = vc.albedo * __longlong_as_double((long long)*musmax_bits);
+    const bool ground = e >= na_ch;
+    int j, u;
+    if (!ground) {
+        j = (int)(e / g.nd);
+        u = (int)(e - (long long)j * g.nd);
+    } else {
+        const long long q = e - na_ch;
+        j = (int)(q / g.ngd);
+        u = (int)(q - (long long)j * g.ngd);
+    }
+    const int z = ground ? g.nz : j / g.nxy, r = ground ? j : j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    bool recv = false;
+    int nidx = -1;
+    double dist = 1.0;
+    if (!ground) {
+        const int4 d = gp.dirs[u];
+        const int rz = z + d.z;
+        if (rz < g.nz) {
+            recv = true;
+            if (rz >= 0) {
+                nidx = (rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx);
+                dist = gp.dir_len[u];
+            } else {
+                dist = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
+            }
+        }
+    } else {
+        const int4 m = gp.gmem1[u];
+        if ((double)m.z - 0.5 <= (double)g.nz) {
+            recv = true;
+            nidx = ((m.z - 1) * g.ny + wrap_small(y + m.y, g.ny)) * g.nx + wrap_small(x + m.x, g.nx);
+            dist = gp.gdist1[u];
+        }
+    }
+    unsigned long long key = 0ull;
+    if (recv) {
+        const double ms = ground ? mus_lamb : mus64(g, f, j);
+        const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
+        key = (unsigned long long)__double_as_longlong(sqrt(ms * mn) / dist) + 1ull;
+    }
+    keys[e] = key;
+}
+
+constexpr int kTopkBits = 11;
+
+// histogram of digit (key >> shift) & mask over the keys whose bits above
+// shift + kTopkBits equal prefix (pass 0: every key that has a receiver)
+__global__ void k_topk_hist(const unsigned long long *__restrict__ keys, long long n, int shift, int width,
+                            int hi_shift, unsigned long long prefix, unsigned int *hist) {
+    __shared__ unsigned int h[1 << kTopkBits];
+    for (int b = threadIdx.x; b < (1 << kTopkBits); b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const unsigned long long mask = (1ull << width) - 1ull;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[i];
+        if (k == 0ull) continue;
+        if (hi_shift < 64 && (k >> hi_shift) != prefix) continue;
+        atomicAdd(&h[(k >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < (1 << kTopkBits); b += blockDim.x)
+        if (h[b]) atomicAdd(hist + b, h[b]);
+}
+
+template <typename T>
+void launch_topk_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                      unsigned long long *musmax_bits, unsigned long long *keys, long long *launches) {
+    const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
+    cudaMemsetAsync(musmax_bits, 0, sizeof(unsigned long long), st);
+    k_sel_musmax<T><<<(g.n_atm + 255) / 256, 256, 0, st>>>(g, f, musmax_bits);
+    k_topk_keys<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, gp, f, vc, musmax_bits, keys);
+    if (launches) *launches += 2;
+}
+
+void launch_topk_hist(cudaStream_t st, const unsigned long long *keys, long long n, int shift, int width,
+                      int hi_shift, unsigned long long prefix, unsigned int *hist, int nblocks) {
+    cudaMemsetAsync(hist, 0, sizeof(unsigned int) << kTopkBits, st);
+    k_topk_hist<<<nblocks, 256, 0, st>>>(keys, n, shift, width < kTopkBits ? width : kTopkBits, hi_shift, prefix,
+                                         hist);
+}
+
+template void launch_topk_keys<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
+                                      const ViewC &, unsigned long long *, unsigned long long *, long long *);
+template void launch_topk_keys<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,
+                                       const ViewC &, unsigned long long *, unsigned long long *, long long *);
+
 template void launch_select<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &, const ViewC &,
                                    const ViewP &, const SelP &, float *, float *, long long *);
 template void launch_select<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,

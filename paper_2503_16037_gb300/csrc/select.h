@@ -53,6 +53,19 @@ template <typename T>
 void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                    const ViewP &vp, const SelP &sp, T *w_iso, T *w_sun, long long *launches);
 
+// The preselected maximum number of couplings: keys[e] = 1 + the bits of the
+// FP64 coupling of chain e ([n_atm][nd], then [n_ground][ngd]; 0: the chain
+// has no receiver), and one radix-select pass: the histogram hist[2^11] of
+// the digit (key >> shift) & (2^width - 1) over the non-zero keys whose bits
+// from hi_shift up equal prefix (hi_shift >= 64: all of them); the digit
+// is width <= 11 bits wide.
+template <typename T>
+void launch_topk_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                      unsigned long long *musmax_bits, unsigned long long *keys, long long *launches);
+void launch_topk_hist(cudaStream_t st, const unsigned long long *keys, long long n, int shift, int width,
+                      int hi_shift, unsigned long long prefix, unsigned int *hist, int nblocks);
+constexpr int kTopkDigitBits = 11;
+
 // The edge kernel with the weights read from w_iso / w_sun.
 template <typename T>
 void launch_assemble_rows_sel(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,

@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
             "tursca_quadrature": (st, [C.POINTER(tursca_grid_desc), _vp, _vp]),
             "tursca_profile_enable": (st, [_vp, C.c_int]),
             "tursca_set_option": (st, [_vp, C.c_int, C.c_double]),
+            "tursca_selection_info": (st, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                           C.POINTER(C.c_longlong)]),
             "tursca_profile_read": (st, [_vp, C.POINTER(tursca_kernel_stat), C.c_int, C.POINTER(C.c_int)]),
             "tursca_csr_solve_noalloc": (st, [_vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp]),
             "tursca_selftest_wait": (st, [_vp, C.c_int, C.POINTER(C.c_double)]),
@@ -209,10 +211,19 @@ OPT_GATHER_TILE = 5
 OPT_SINGLE_SCATTER = 6
 OPT_COUPLING_MIN = 7
 OPT_ANISO = 8
+OPT_MAX_COUPLINGS = 9
 
 
 def tursca_set_option(scene, option: int, value: float):
     _check(scene, lib().tursca_set_option(scene, int(option), float(value)))
+
+
+def tursca_selection_info(scene) -> dict:
+    thr = C.c_double(0.0)
+    nc = C.c_longlong(0)
+    nk = C.c_longlong(0)
+    _check(scene, lib().tursca_selection_info(scene, C.byref(thr), C.byref(nc), C.byref(nk)))
+    return {"threshold": thr.value, "n_couplings": nc.value, "n_kept": nk.value}
 
 
 def tursca_profile_enable(scene, on: bool):
@@ -312,6 +323,8 @@ class Runner:
         tursca_build_graph(self.handle)
         if getattr(sc, "c_min", 0.0) > 0.0:
             tursca_set_option(self.handle, OPT_COUPLING_MIN, sc.c_min)
+        if getattr(sc, "max_couplings", 0) > 0:
+            tursca_set_option(self.handle, OPT_MAX_COUPLINGS, sc.max_couplings)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.rad = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)
         self.refl = torch.empty((sc.npy, sc.npx), dtype=self.dtype, device=dev)

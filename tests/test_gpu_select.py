@@ -148,3 +148,77 @@ def test_selection_adjoint_matches_oracle_finite_differences():
         err = (np.abs(g - ref) / np.maximum(np.abs(ref), 1e-2 * np.abs(ref).max())).max()
         print("selection adjoint (precision %d) vs oracle fd: max rel err %.2e" % (prec, err))
         assert err < tol
+
+
+# The preselected maximum number of couplings (Sec. 3): the GPU finds the
+# (K + 1)-th largest FP64 coupling by a radix select and must reproduce the
+# oracle's sorted threshold bit for bit, hence the same kept chains.
+TOPK_CASES = {
+    "random_R2": (lambda: scenes.make_random(21, 19, 9, seed=7, S=2, R=2, M=2048), 0.3),
+    "random_R1_3species": (lambda: scenes.make_random(13, 11, 7, seed=8, S=3, R=1, M=1024, sza=20.0, vza=55.0), 0.5),
+    "plume_small": (lambda: scenes.make_plume(nx=24, ny=20, nz=12), 0.1),
+    # non-scattering voxels: zero couplings at the boundary (threshold: the smallest positive double)
+    "zero_couplings": (lambda: scenes.make_random(12, 11, 6, seed=14, S=1, R=2, M=1024, zero_frac=0.3), None),
+}
+
+
+@pytest.mark.parametrize("name", list(TOPK_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_topk_parity(name, prec):
+    make, frac = TOPK_CASES[name]
+    sc0 = make()
+    ref0 = sc0 if prec == "fp64" else fp32_inputs(sc0)
+    full = O.run(ref0, flags=O.NO_SOLVE)
+    n = full["n_couplings"]
+    if frac is None:
+        # keep exactly the positive couplings (with K = n - 1 the threshold is
+        # the smallest coupling, 0, so what stays is every positive one)
+        K = int(O.run(ref0.replace(max_couplings=n - 1), flags=O.NO_SOLVE)["n_kept"])
+        assert 0 < K < n - 1
+    else:
+        K = int(frac * n)
+    sc = sc0.replace(max_couplings=K)
+    r = O.run(ref0.replace(max_couplings=K))
+    if frac is None:
+        assert 0.0 < r["c_min_used"] < 1e-300 and r["n_kept"] == K
+    rn, rad = run_gpu(sc, T.FP64 if prec == "fp64" else T.FP32_REFINE, 1e-13 if prec == "fp64" else 1e-10)
+    info = T.tursca_selection_info(rn.handle)
+    assert info["threshold"] == r["c_min_used"]
+    assert info["n_couplings"] == r["n_couplings"] and info["n_kept"] == r["n_kept"]
+    vg, vo = gpu_vs_oracle_slots(rn, r)
+    assert np.array_equal(vg == 0, vo == 0)
+    kt = 1e-11 if prec == "fp64" else 2e-5
+    floor = (1e-14 if prec == "fp64" else 1e-6) * vo.max()
+    assert (np.abs(vg - vo) / np.maximum(np.abs(vo), floor)).max() < kt
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    err = (np.abs(rad - r["rad"]) / np.abs(r["rad"])).max()
+    print("%s %s: K = %d of %d, kept %d, threshold %.6e, radiance max rel err %.2e"
+          % (name, prec, K, n, info["n_kept"], info["threshold"], err))
+    assert err < tol
+
+
+def test_topk_edges_and_errors():
+    """K at or above the number of couplings is the full stencil (bit for
+    bit); c_min and K together, and a negative or fractional K, are
+    rejected."""
+    sc = scenes.make_plume(nx=24, ny=20, nz=12)
+    rn, full0 = run_gpu(sc, T.FP32_REFINE, 1e-10)
+    mu_a, mu_s = rn.fields("cuda")
+    n = O.run(fp32_inputs(sc), flags=O.NO_SOLVE)["n_couplings"]
+    for K in (n, 10 ** 12):
+        T.tursca_set_option(rn.handle, T.OPT_MAX_COUPLINGS, K)
+        rn.run(mu_a, mu_s, rtol=1e-10)
+        torch.cuda.synchronize()
+        assert np.array_equal(rn.rad.cpu().numpy().astype(np.float64), full0)
+        info = T.tursca_selection_info(rn.handle)
+        assert info["threshold"] == 0.0 and info["n_couplings"] == n and info["n_kept"] == n
+    T.tursca_set_option(rn.handle, T.OPT_COUPLING_MIN, 1.0)
+    with pytest.raises(T.TurscaError) as e:
+        rn.run(mu_a, mu_s, rtol=1e-10)
+    assert e.value.status == T.E_INVALID
+    T.tursca_set_option(rn.handle, T.OPT_COUPLING_MIN, 0.0)
+    for bad in (-1.0, 2.5):
+        with pytest.raises(T.TurscaError) as e:
+            T.tursca_set_option(rn.handle, T.OPT_MAX_COUPLINGS, bad)
+        assert e.value.status == T.E_INVALID
+    rn.close()
