@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--workload", default="plume", choices=["plume", "cloud"])  # cloud: a variant line
     p.add_argument("--aniso", action="store_true")  # edge unknowns (arrival direction kept)
     p.add_argument("--oracle-times", action="store_true", help=argparse.SUPPRESS)  # child: oracle timings
+    # the coupling study of the paper on the synthetic plume: radiance against the kept number of couplings
+    p.add_argument("--coupling-sweep", action="store_true")
     return p.parse_args()
 
 
@@ -383,6 +385,64 @@ def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
     }
 
 
+def coupling_sweep(args):
+    """Synthetic analogue of the paper's study of the result against the
+    amount of scattering coupling (Sec. 4): the plume 64x64x32 solved with the
+    K largest couplings kept (TURSCA_OPT_MAX_COUPLINGS), K from all of them
+    down to 1%; per K the kept fraction, the radiance change against the full
+    stencil (mean and max relative, and of the scene mean), the mean
+    reflectance and the time per scene (host clock around a synchronised
+    scene, median of 5, L2 flushed; the selection included)."""
+    import numpy as np
+    import torch
+    from paper_2503_16037_gb300 import build as B
+    B.build()
+    from paper_2503_16037_gb300 import scenes
+    from paper_2503_16037_gb300 import tursca as T
+    torch.cuda.set_device(0)
+    sc = scenes.make_plume()
+    stream = torch.cuda.current_stream()
+    rn = T.Runner(sc, T.FP32_REFINE, stream=stream)
+    mu_a, mu_s = rn.fields("cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed():
+        ts = []
+        for k in range(args.warmup + 5):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rn.run(mu_a, mu_s, rtol=RTOL)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        return 1000.0 * statistics.median(ts)
+
+    ms_full = timed()
+    full = rn.rad.double().cpu().numpy()
+    refl_full = rn.refl.double().cpu().numpy()
+    T.tursca_set_option(rn.handle, T.OPT_MAX_COUPLINGS, 1)
+    rn.run(mu_a, mu_s, rtol=RTOL)
+    n = T.tursca_selection_info(rn.handle)["n_couplings"]
+    rows = [{"K": n, "kept": n, "kept_fraction": 1.0, "ms_per_scene": ms_full, "mean_rel_change": 0.0,
+             "max_rel_change": 0.0, "mean_radiance": float(full.mean()), "mean_reflectance": float(refl_full.mean())}]
+    for frac in (0.75, 0.5, 0.3, 0.2, 0.1, 0.05, 0.02, 0.01):
+        K = int(frac * n)
+        T.tursca_set_option(rn.handle, T.OPT_MAX_COUPLINGS, K)
+        ms = timed()
+        info = T.tursca_selection_info(rn.handle)
+        rad = rn.rad.double().cpu().numpy()
+        rel = np.abs(rad - full) / np.abs(full)
+        rows.append({"K": K, "kept": info["n_kept"], "kept_fraction": info["n_kept"] / n, "threshold": info["threshold"],
+                     "ms_per_scene": ms, "mean_rel_change": float(rel.mean()), "max_rel_change": float(rel.max()),
+                     "mean_radiance": float(rad.mean()), "mean_reflectance": float(rn.refl.double().mean().item()),
+                     "solve_iters": rn.info.iters})
+    rn.close()
+    print(json.dumps({"metric": "radiance against the kept number of couplings (plume 64x64x32, FP32 + refinement)",
+                      "unit": "relative radiance change against the full stencil", "data": "synthetic",
+                      "couplings": n, "sweep": rows}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -393,6 +453,9 @@ def main():
         return
     if args.oracle_times:
         oracle_times()
+        return
+    if args.coupling_sweep:
+        coupling_sweep(args)
         return
 
     import numpy as np
@@ -666,6 +729,11 @@ def main():
     for name, (n, ms) in prof.items():
         if n:
             kernels[name] = {"launches": n, "avg_us": 1000.0 * ms / n, "share_of_step": ms / prof_ms}
+    # the stages of a step (the solve's own kernels lie inside "solve"): what
+    # of the sampled steps' time the event profile accounts for
+    stage_names = ("set_medium", "assemble_pre", "select", "assemble_rows", "solve", "render")
+    stages = {k: prof[k][1] / prof_ms for k in stage_names if k in prof and prof[k][0]}
+    stages["accounted"] = sum(stages.values())
     # 4 B per stored value (columns are implicit), per row: p gathered (4),
     # r read + written (8), d read + written (8), new p written (4)
     spmv_bytes = st.nnz * 4 + st.n_nodes * 24
@@ -728,6 +796,7 @@ def main():
         "roofline": roof,
         "roofline_assembly": roof_asm,
         "kernels": kernels,
+        "stage_shares": stages,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scenes/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,

@@ -337,7 +337,10 @@ typedef struct {
                            "gmres_orth" (both Gram-Schmidt passes of one Arnoldi step),
                            "select" (coupling selection), "gmres_prod" (the passes over K of
                            one Arnoldi step: preconditioner and product with I - K, each
-                           counted as a launch) */
+                           counted as a launch), "set_medium" (its copies), "solve" (a whole
+                           solve, from its first to its last operation on the stream,
+                           host round trips included; the solve's other categories lie
+                           inside it) */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;

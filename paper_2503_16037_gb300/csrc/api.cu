@@ -179,12 +179,17 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv",   "resid64", "assemble_rows", "assemble_pre", "render",
-                                  "cheb",   "gmres_orth", "select",      "gmres_prod"};
-constexpr int kNProf = 9;
+const char *const kProfNames[] = {"spmv",   "resid64",    "assemble_rows", "assemble_pre", "render", "cheb",
+                                  "gmres_orth", "select", "gmres_prod",   "set_medium",   "solve"};
+constexpr int kNProf = 11;
 // P_GPROD: the passes over K of one Arnoldi step (preconditioner and product
-// with I - K), counted as launches
-enum { P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7, P_GPROD = 8 };
+// with I - K), counted as launches; P_MEDIUM: the copies of set_medium;
+// P_SOLVE: a whole solve, from its first to its last operation on the stream
+// (the other categories of the solve lie inside it)
+enum {
+    P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7, P_GPROD = 8,
+    P_MEDIUM = 9, P_SOLVE = 10
+};
 
 // NVTX range around one call of the C ABI (a stage of the path), for
 // profilers that filter or group by range; free when no tool is attached
@@ -1390,8 +1395,10 @@ tursca_status tursca_set_medium(tursca_scene *sc, const void *mu_abs, const void
     tursca_status e = ensure_fields(sc);
     if (e) return e;
     const size_t na = (size_t)sc->d.nx * sc->d.ny * sc->d.nz;
+    const int pm = prof_begin(sc, P_MEDIUM);
     CK(cudaMemcpyAsync(sc->mu_a, mu_abs, na * sc->es, cudaMemcpyDefault, sc->st), "copy mu_abs");
     CK(cudaMemcpyAsync(sc->mu_s, mu_sca, na * sc->es * sc->d.n_species, cudaMemcpyDefault, sc->st), "copy mu_sca");
+    prof_end(sc, pm);
     CK(cudaMemsetAsync(sc->status, 0, sizeof(int), sc->st), "memset status");
     for (int s = 0; s < tk::MAX_SPECIES; ++s) sc->g[s] = s < sc->d.n_species ? g[s] : 0.0;
     sc->albedo = albedo;
@@ -1948,8 +1955,12 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
         if (sc->d.precision == TURSCA_FP64) return do_solve_aniso<double>(sc, solver, rtol, max_iter, info);
         return do_solve_aniso<float>(sc, solver, rtol, max_iter, info);
     }
-    if (sc->d.precision == TURSCA_FP64) return do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc));
-    return do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
+    const int ps = prof_begin(sc, P_SOLVE);
+    const tursca_status r = sc->d.precision == TURSCA_FP64
+                                ? do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc))
+                                : do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
+    prof_end(sc, ps);
+    return r;
 }
 
 tursca_status tursca_solve(tursca_scene *sc, double rtol, int max_iter, tursca_solve_info *info) {

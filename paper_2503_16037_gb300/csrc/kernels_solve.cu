@@ -447,18 +447,33 @@ __global__ void k_dots(GridC g, const A *__restrict__ V, size_t ldv, int ncol, c
 }
 
 // one block per column; fixed strided partial sums then a fixed-order tree
-__global__ void k_finalize(const double *__restrict__ part, int nblk, int ncol, double *__restrict__ out) {
-    __shared__ double sh[256];
-    int k = blockIdx.x;
+// Column k of the block partials part[k][nblk] summed into out[k] by one
+// block of kFinThreads threads: each thread adds its strided share with four
+// loads in flight at a time (one memory round trip per four values instead
+// of one per value), then the warps' fixed butterflies and warp 0 over the
+// warps' sums.  The order depends on nblk only, so the sum is deterministic.
+constexpr int kFinThreads = 1024;
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const double *__restrict__ part, int nblk, int ncol,
+                                                         double *__restrict__ out) {
+    __shared__ double sh[32];
+    const int k = blockIdx.x;
+    const double *p = part + (size_t)k * nblk;
     double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(size_t)k * nblk + b];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    int b = threadIdx.x;
+    for (; b + 3 * kFinThreads < nblk; b += 4 * kFinThreads) {
+        const double a0 = p[b], a1 = p[b + kFinThreads], a2 = p[b + 2 * kFinThreads], a3 = p[b + 3 * kFinThreads];
+        s += (a0 + a1) + (a2 + a3);
     }
-    if (threadIdx.x == 0) out[k] = sh[0];
+    for (; b < nblk; b += kFinThreads) s += p[b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = s;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[k] = t;
+    }
     (void)ncol;
 }
 
@@ -542,11 +557,11 @@ void launch_dots(cudaStream_t st, const GridC &g, const A *V, size_t ldv, int nc
     if constexpr (sizeof(A) == 4 && sizeof(B) == 4) {
         const int nb = std::min(dot_blocks_ds(), std::max(1, (g.nz + 1) * g.ny / 8));
         k_dots_ds<<<nb, 256, 0, st>>>(g, (const float *)V, ldv, ncol, (const float *)y, part);
-        k_finalize<<<ncol, 256, 0, st>>>(part, nb, ncol, out);
+        k_finalize<<<ncol, kFinThreads, 0, st>>>(part, nb, ncol, out);
         return;
     }
     k_dots<A, B><<<nblk, 256, 0, st>>>(g, V, ldv, ncol, y, part);
-    k_finalize<<<ncol, 256, 0, st>>>(part, nblk, ncol, out);
+    k_finalize<<<ncol, kFinThreads, 0, st>>>(part, nblk, ncol, out);
 }
 
 template <typename T>
@@ -592,11 +607,11 @@ void launch_from_halo(cudaStream_t st, const GridC &g, const U *src, U *dst) {
 }
 
 void launch_finalize2(cudaStream_t st, const double *part, int nblk, double *out) {
-    k_finalize<<<2, 256, 0, st>>>(part, nblk, 2, out);
+    k_finalize<<<2, kFinThreads, 0, st>>>(part, nblk, 2, out);
 }
 
 void launch_finalize(cudaStream_t st, const double *part, int nblk, double *out) {
-    k_finalize<<<1, 256, 0, st>>>(part, nblk, 1, out);
+    k_finalize<<<1, kFinThreads, 0, st>>>(part, nblk, 1, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -724,7 +739,7 @@ void launch_gmres_update_norm(cudaStream_t st, const GridC &g, int n, T *w, cons
     if constexpr (sizeof(T) == 4) {
         const int nb = (n + 255) / 256;
         k_gupdate_ds<true><<<nb, 256, 0, st>>>(g, n, (float *)w, (const float *)V, ldv, k, h, -1.0, part);
-        k_finalize<<<1, 256, 0, st>>>(part, nb, 1, out);
+        k_finalize<<<1, kFinThreads, 0, st>>>(part, nb, 1, out);
         return;
     }
     launch_gmres_update<T>(st, n, w, V, ldv, k, h);
