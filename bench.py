@@ -291,7 +291,7 @@ def oracle_times():
 SERVE_SHAPES = [(16, 16, 16), (32, 32, 24), (48, 48, 32), (64, 64, 32), (96, 96, 32)]
 
 
-def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
+def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0, batch_solves=False, plain=True):
     """Continuous-batching serving of plume scenes of uneven sizes (uniform
     over SERVE_SHAPES, SZA ~ U(20, 75) deg, FP32 + refinement to 1e-10):
     the saturation rate with all requests queued at once, then an open-loop
@@ -308,7 +308,7 @@ def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
               for sh, l in pool.items() for k, sc in enumerate(l)}
     reqs = [(SERVE_SHAPES[rng.integers(len(SERVE_SHAPES))], int(rng.integers(nvar))) for _ in range(n_requests)]
     outs = [torch.empty((sh[1], sh[0]), dtype=torch.float32).pin_memory() for sh, _ in reqs]
-    srv = T.Server(40 << 30, workers)
+    srv = T.Server(40 << 30, workers, batch_solves=batch_solves)
     for sh in SERVE_SHAPES:  # one warm request per shape builds its first slot
         srv.wait(srv.submit(pool[sh][0], T.FP32_REFINE, 1e-10, fields=fields[(sh, 0)]))
 
@@ -346,6 +346,12 @@ def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
     th.join()
     wall = time.perf_counter() - t0
     lat = np.array([i["end_ms"] - i["submit_ms"] for i in infos])
+    svc = np.array([i["end_ms"] - i["start_ms"] for i in infos])
+    per_shape = {}
+    for (sh, _), v in zip(reqs, svc):
+        per_shape.setdefault("%dx%dx%d" % sh, []).append(v)
+    per_shape = {k: {"requests": len(v), "service_p50_ms": float(np.percentile(v, 50)),
+                     "service_p99_ms": float(np.percentile(v, 99))} for k, v in sorted(per_shape.items())}
     subm = np.array([i["submit_ms"] for i in infos])
     st = srv.stats()
     srv.close()
@@ -353,7 +359,7 @@ def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
     # the plain FP64 path: one scene per call sequence, nothing overlapped
     base = []
     rn_of = {}
-    for sh, k in reqs[:64]:
+    for sh, k in (reqs[:64] if plain else []):
         if sh not in rn_of:
             rn_of[sh] = T.Runner(pool[sh][0], T.FP64)
         rn = rn_of[sh]
@@ -368,16 +374,18 @@ def serving(T, scenes, torch, np, n_requests=1024, workers=8, load=0.8, seed=0):
         base.append(1000.0 * (time.perf_counter() - t1))
     for rn in rn_of.values():
         rn.close()
-    base = np.array(base)
+    base = np.array(base if base else [float("nan")])
     return {
         "workload": "1024 plume scenes, shapes uniform over 16^3, 32^2x24, 48^2x32, 64^2x32, 96^2x32 "
                     "(R = 2), SZA ~ U(20, 75) deg, FP32 + FP64 refinement to 1e-10, host inputs (pinned)",
         "workers": workers, "saturation_scenes_per_s": sat,
         "arrivals": "Poisson at %.2f x saturation (%.0f /s requested, %.0f /s achieved)"
                     % (load, rate, (n_requests - 1) / max(1e-9, (subm.max() - subm.min()) / 1000.0)),
-        "scenes_per_s": n_requests / wall, "p50_ms": float(np.percentile(lat, 50)),
+        "scenes_per_s": n_requests / wall, "per_shape_service": per_shape, "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()), "all_converged": ok,
         "slots_built": st["slots_built"], "peak_device_bytes": st["peak_bytes"], "evictions": st["evictions"],
+        "batched_refinements": {"on": batch_solves, "launches": st["batches"],
+                                "refinements": st["batched_refinements"], "max_in_one_launch": st["max_batch"]},
         "plain_fp64_one_scene_at_a_time": {
             "requests": int(base.size), "scenes_per_s": 1000.0 / float(base.mean()),
             "p50_ms": float(np.percentile(base, 50)), "p99_ms": float(np.percentile(base, 99)),
@@ -713,6 +721,12 @@ def main():
     if rank == 0 and not args.no_serving and not variant:
         try:
             serve = serving(T, scenes, torch, np)
+            # the same requests with the Chebyshev refinements of concurrent
+            # requests batched into persistent kernels
+            bat = serving(T, scenes, torch, np, batch_solves=True, plain=False)
+            serve["batched_refinements_on"] = {k: bat[k] for k in (
+                "saturation_scenes_per_s", "scenes_per_s", "p50_ms", "p99_ms", "max_ms", "all_converged",
+                "arrivals", "per_shape_service", "batched_refinements")}
         except Exception as e:  # the bench line must still print
             serve = {"error": str(e)[:200]}
 

@@ -449,7 +449,35 @@ typedef struct {
 typedef struct {
     size_t budget_bytes, used_bytes, peak_bytes;
     int slots, busy_slots, pending, evictions, slots_built;
+    /* batched Chebyshev refinements (see tursca_server_configure): launches,
+     * refinements run in them, and the most in one launch */
+    long long batches, batched_refinements;
+    int max_batch;
 } tursca_server_stats;
+
+/* Server options (tursca_server_configure), to be set before the first
+ * request:
+ *   TURSCA_SERVER_BATCH_SOLVES: 0 (default) runs every request's passes on
+ *     its own stream; 1 batches the Chebyshev refinements of the requests
+ *     that run at the same time: a refinement handed over while others wait
+ *     is launched together with them in one persistent kernel, which runs
+ *     every request's row groups step after step with a grid-wide barrier
+ *     between steps (every wait bounded); each request keeps its own step
+ *     count and coefficients, and each group is computed by the same device
+ *     code as the request's own Chebyshev pass, so a result does not depend
+ *     on what it ran beside.  FP32 + refinement scenes whose pass has at most
+ *     640 row groups (larger ones fill the GPU by themselves); two such
+ *     launches may run at once, each on at most half the GPU. */
+enum { TURSCA_SERVER_BATCH_SOLVES = 1 };
+tursca_status tursca_server_configure(tursca_server *srv, int option, double value);
+
+/* Self-test of the bounded grid barrier of the batched refinements: `blocks`
+ * blocks of one cooperative launch wait at a barrier that expects all of
+ * them (arrive != 0) or one more (arrive == 0, so it never completes).
+ * TURSCA_OK when the barrier completed, TURSCA_E_TIMEOUT when every block
+ * gave up (about a second; the kernel returns and the context stays
+ * usable), TURSCA_E_CUDA on a CUDA error.  Synchronises cuda_stream. */
+tursca_status tursca_selftest_barrier(void *cuda_stream, int blocks, int arrive);
 
 /* hbm_budget_bytes: device memory the slots may hold together (>= the
  * largest single slot); max_concurrent: worker threads (1..64), i.e. requests

@@ -13,6 +13,7 @@
 #include "graph.h"
 #include "first_order.h"
 #include "kern.h"
+#include "batch.h"
 #include "select.h"
 #include "aniso.h"
 #include "tursca.h"
@@ -151,6 +152,9 @@ struct tursca_scene {
     // its selection: per-chain keys, the radix histogram, the last threshold,
     // the number of chains with a receiver
     long long max_couplings = 0;
+    // the serving loop's batcher of Chebyshev refinements (null: own passes)
+    tk::ChebBatcher *batcher = nullptr;
+    cudaEvent_t bready = nullptr, bdone = nullptr;
     unsigned long long *topk_keys = nullptr;
     unsigned int *topk_hist = nullptr, *topk_hist_h = nullptr;
     double c_eff = 0.0;
@@ -905,19 +909,55 @@ tursca_status do_solve(tursca_scene *sc, int solver, double rtol, int max_iter, 
             T *r = bb, *d = (T *)sc->w, *p0 = (T *)sc->d0, *p1 = (T *)sc->d1;
             tk::launch_cheb_start<T>(sc->st, n, sc->r64, 1.0 / cp.theta, r, d, p0);
             sc->launches++;
-            double rk = 1.0 / cp.sigma;
-            int pi = prof_begin(sc, P_CHEB);
-            for (int k = 0; k < nc; ++k) {
-                double rk1 = 1.0 / (2.0 * cp.sigma - rk);
-                // the last step also applies x += d row by row
-                const bool last = k == nc - 1;
-                tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta,
-                                   last ? io.x : nullptr, last && ds ? sc->xh : nullptr, last && ds ? sc->xl : nullptr);
-                std::swap(p0, p1);
-                rk = rk1;
+            // in a server: hand the refinement to the batcher, which runs it
+            // in one persistent launch with the refinements of other requests
+            bool batched = false;
+            if constexpr (sizeof(T) == 4) {
+                if (sc->batcher && tk::batch_eligible(g, nc)) {
+                    tk::ChebJob job;
+                    std::memset(&job, 0, sizeof(job));
+                    job.g = g;
+                    job.gp = gp;
+                    job.val = (const float *)val;
+                    job.r = (float *)r;
+                    job.d = (float *)d;
+                    job.p[0] = (float *)p0;
+                    job.p[1] = (float *)p1;
+                    job.x64 = io.x;
+                    job.xh = ds ? sc->xh : nullptr;
+                    job.xl = ds ? sc->xl : nullptr;
+                    job.nsteps = nc;
+                    job.W = g.wq;
+                    double rk = 1.0 / cp.sigma;
+                    for (int k = 0; k < nc; ++k) {  // the coefficients the scene's own passes would take
+                        const double rk1 = 1.0 / (2.0 * cp.sigma - rk);
+                        job.c1[k] = (float)(rk1 * rk);
+                        job.c2[k] = (float)(2.0 * rk1 / cp.delta);
+                        rk = rk1;
+                    }
+                    CK(cudaEventRecord(sc->bready, sc->st), "batch event");
+                    if (tk::batcher_run(sc->batcher, job, sc->bready, sc->bdone)) {
+                        CK(cudaStreamWaitEvent(sc->st, sc->bdone, 0), "batch wait");
+                        batched = true;
+                    }
+                }
             }
-            prof_end(sc, pi, nc);
-            sc->launches += nc;
+            if (!batched) {
+                double rk = 1.0 / cp.sigma;
+                int pi = prof_begin(sc, P_CHEB);
+                for (int k = 0; k < nc; ++k) {
+                    double rk1 = 1.0 / (2.0 * cp.sigma - rk);
+                    // the last step also applies x += d row by row
+                    const bool last = k == nc - 1;
+                    tk::launch_cheb<T>(sc->st, g, gp, val, p0, r, d, p1, rk1 * rk, 2.0 * rk1 / cp.delta,
+                                       last ? io.x : nullptr, last && ds ? sc->xh : nullptr,
+                                       last && ds ? sc->xl : nullptr);
+                    std::swap(p0, p1);
+                    rk = rk1;
+                }
+                prof_end(sc, pi, nc);
+                sc->launches += nc;
+            }
             ss.iters += nc;
             dd = d;
             x_done = true;
@@ -1375,6 +1415,8 @@ tursca_status tursca_scene_destroy(tursca_scene *sc) {
         if (v.p) cudaFree(v.p);
     if (sc->hred) cudaFreeHost(sc->hred);
     if (sc->topk_hist_h) cudaFreeHost(sc->topk_hist_h);
+    if (sc->bready) cudaEventDestroy(sc->bready);
+    if (sc->bdone) cudaEventDestroy(sc->bdone);
     for (cudaEvent_t e : sc->ev) cudaEventDestroy(e);
     for (int i = 0; i < 3; ++i)
         if (sc->aux[i]) cudaStreamDestroy(sc->aux[i]);
@@ -2190,6 +2232,13 @@ tursca_status tursca_profile_read(tursca_scene *sc, tursca_kernel_stat *out, int
     return TURSCA_OK;
 }
 
+tursca_status tursca_selftest_barrier(void *cuda_stream, int blocks, int arrive) {
+    if (blocks < 1 || blocks > 1024) return fail(nullptr, TURSCA_E_INVALID, "blocks must be in 1..1024");
+    const int r = tk::batch_barrier_selftest((cudaStream_t)cuda_stream, blocks, arrive);
+    if (r < 0) return fail(nullptr, TURSCA_E_CUDA, "barrier self-test: CUDA error");
+    return r ? TURSCA_E_TIMEOUT : TURSCA_OK;
+}
+
 tursca_status tursca_selection_info(const tursca_scene *sc, double *threshold, long long *n_couplings,
                                     long long *n_kept) {
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
@@ -2268,3 +2317,16 @@ tursca_status tursca_last_error(const tursca_scene *sc, char *buf, size_t n) {
 }
 
 }  // extern "C"
+
+namespace tk {
+void scene_attach_batcher(tursca_scene *sc, ChebBatcher *b) {
+    if (!sc || sc->d.precision == TURSCA_FP64) return;
+    if (b && !sc->bready) {
+        if (cudaEventCreateWithFlags(&sc->bready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sc->bdone, cudaEventDisableTiming) != cudaSuccess)
+            return;
+    }
+    sc->batcher = b;
+}
+}  // namespace tk
+

@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "kern.h"
+#include "batch.h"
 #include "stage.cuh"
 
 namespace tk {
@@ -373,6 +374,162 @@ void launch_cheb(cudaStream_t st, const GridC &g, const GraphP &gp, const T *val
     op.c1 = (T)c1;
     op.c2 = (T)c2;
     run_op(st, g, gp, val, op, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev refinements of several scenes in one persistent launch (the
+// serving loop's batches, batch.h).  Tile t of the launch is row group
+// t - tile0 of the job whose tiles hold it; block b handles tiles b, b + G,
+// b + 2G, ... in every step (G = gridDim.x), so the rows a block finishes are
+// always its own; the gathered vector comes from other blocks and is read
+// around L1.  Between steps a grid-wide barrier: every wait is bounded, and a
+// barrier that gives up sets the launch's abort flag, after which every
+// block skips the remaining steps and the jobs' scenes get STATUS_TIMEOUT.
+constexpr long long kBarrierPolls = 1ll << 21;  // with a 256 ns sleep per poll: about a second
+
+__device__ bool grid_barrier(BatchBarrier *b, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *vgen = &b->gen;
+        volatile int *vab = &b->abort;
+        if (*vab) {
+            ok = 0;
+        } else {
+            const unsigned g0 = *vgen;  // read before arriving: the last arrival changes it
+            __threadfence();
+            if (atomicAdd(&b->count, 1u) + 1u == nblocks) {
+                atomicExch(&b->count, 0u);
+                __threadfence();
+                atomicAdd(&b->gen, 1u);
+            } else {
+                for (long long i = 0; *vgen == g0; ++i) {
+                    if (*vab) {
+                        ok = 0;
+                        break;
+                    }
+                    if (i >= kBarrierPolls) {
+                        atomicExch(&b->abort, 1);
+                        atomicOr(&b->status, STATUS_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+int batch_tiles(const GridC &g) { return (g.nz + 1) * g.gpl; }
+
+template <int W>
+__global__ void __launch_bounds__(32 * W) k_cheb_batch(const ChebJob *__restrict__ jobs, int njobs, int ntiles,
+                                                      int max_steps, BatchBarrier *bar) {
+    __shared__ float sh[W][4][32];
+    extern __shared__ float tile[];
+    __shared__ int s_lay[kTileLayers];
+    __shared__ ChebJob sj;
+    __shared__ int s_tile0[kChebMaxJobs + 1];
+    for (int i = threadIdx.x; i <= njobs; i += blockDim.x) s_tile0[i] = i < njobs ? jobs[i].tile0 : ntiles;
+    __syncthreads();
+    int cur = -1;
+    for (int step = 0; step < max_steps; ++step) {
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int j = 0;
+            while (j + 1 < njobs && s_tile0[j + 1] <= t) ++j;
+            if (j != cur) {  // the job's constants into shared memory
+                __syncthreads();
+                const int4 *src = reinterpret_cast<const int4 *>(jobs + j);
+                int4 *dst = reinterpret_cast<int4 *>(&sj);
+                for (int k = threadIdx.x; k < (int)(sizeof(ChebJob) / 16); k += blockDim.x) dst[k] = src[k];
+                __syncthreads();
+                cur = j;
+            }
+            if (step >= sj.nsteps) continue;
+            OpCheb<float> op;
+            op.p = sj.p[step & 1];
+            op.pn = sj.p[(step + 1) & 1];
+            op.r = sj.r;
+            op.d = sj.d;
+            op.c1 = sj.c1[step];
+            op.c2 = sj.c2[step];
+            if (step == sj.nsteps - 1) {
+                op.xu.x = sj.x64;
+                op.xu.xh = sj.xh;
+                op.xu.xl = sj.xl;
+            }
+            __syncthreads();
+            tile_group<W, OpCheb<float>, false, true>(sj.g, sj.gp, sj.val, op, t - sj.tile0, sh, tile, s_lay);
+        }
+        if (!grid_barrier(bar, gridDim.x)) break;
+    }
+    __syncthreads();
+    // a barrier that gave up: every job's scene learns it at its next read-back
+    if (threadIdx.x == 0 && *(volatile int *)&bar->abort)
+        for (int j = blockIdx.x; j < njobs; j += gridDim.x) atomicOr(jobs[j].gp.status, STATUS_TIMEOUT);
+}
+
+bool batch_eligible(const GridC &g, int nsteps) {
+    return nsteps >= 1 && nsteps <= kChebMaxSteps && !g.stage && g.tl > 0 && batch_tiles(g) <= kBatchMaxTiles &&
+           (size_t)kTileLayers * g.tl * sizeof(float) <= (size_t)kTileMaxBytes &&
+           (g.wq == 4 || g.wq == 6 || g.wq == 8);
+}
+
+template <int W>
+static cudaError_t launch_cheb_batch_w(cudaStream_t st, const ChebJob *d_jobs, const ChebJob *h_jobs, int njobs,
+                                       BatchBarrier *bar, int share) {
+    int ntiles = 0, max_steps = 0, tl = 0;
+    for (int j = 0; j < njobs; ++j) {
+        ntiles += batch_tiles(h_jobs[j].g);
+        max_steps = max(max_steps, h_jobs[j].nsteps);
+        tl = max(tl, h_jobs[j].g.tl);
+    }
+    const size_t smem = (size_t)kTileLayers * tl * sizeof(float);
+    int dev = 0, nsm = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cheb_batch<W>, 32 * W, smem);
+    if (e != cudaSuccess) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    const int grid = min(ntiles, max(1, per * nsm / max(1, share)));
+    void *args[] = {(void *)&d_jobs, (void *)&njobs, (void *)&ntiles, (void *)&max_steps, (void *)&bar};
+    return cudaLaunchCooperativeKernel((const void *)k_cheb_batch<W>, dim3(grid), dim3(32 * W), args, smem, st);
+}
+
+cudaError_t launch_cheb_batch(cudaStream_t st, const ChebJob *d_jobs, const ChebJob *h_jobs, int njobs, int W,
+                              BatchBarrier *bar, int share) {
+    if (njobs < 1 || njobs > kChebMaxJobs) return cudaErrorInvalidValue;
+    if (W == 4) return launch_cheb_batch_w<4>(st, d_jobs, h_jobs, njobs, bar, share);
+    if (W == 6) return launch_cheb_batch_w<6>(st, d_jobs, h_jobs, njobs, bar, share);
+    if (W == 8) return launch_cheb_batch_w<8>(st, d_jobs, h_jobs, njobs, bar, share);
+    return cudaErrorInvalidValue;
+}
+
+// the self-test: every block meets one barrier that expects `expect` arrivals
+__global__ void k_barrier_test(BatchBarrier *bar, unsigned expect) { grid_barrier(bar, expect); }
+
+int batch_barrier_selftest(cudaStream_t st, int blocks, int arrive) {
+    BatchBarrier *bar = nullptr;
+    if (cudaMalloc((void **)&bar, sizeof(BatchBarrier)) != cudaSuccess) return -1;
+    int result = -1;
+    BatchBarrier h{};
+    if (cudaMemsetAsync(bar, 0, sizeof(BatchBarrier), st) == cudaSuccess) {
+        unsigned expect = (unsigned)blocks + (arrive ? 0u : 1u);
+        void *args[] = {(void *)&bar, (void *)&expect};
+        if (cudaLaunchCooperativeKernel((const void *)k_barrier_test, dim3(blocks), dim3(32), args, 0, st) ==
+                cudaSuccess &&
+            cudaMemcpyAsync(&h, bar, sizeof(h), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+            result = h.status & STATUS_TIMEOUT;
+    }
+    cudaFree(bar);
+    return result;
 }
 
 bool resid_ds_ok(const GridC &g) { return true; }

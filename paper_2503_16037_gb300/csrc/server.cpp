@@ -26,6 +26,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "batcher.h"
 #include "tursca.h"
 
 namespace {
@@ -78,6 +79,8 @@ struct tursca_server {
     long long next_ticket = 1, use_clock = 0;
     int evictions = 0, built = 0, reserving = 0;
     bool stop = false;
+    bool batch_solves = false;          // TURSCA_SERVER_BATCH_SOLVES
+    tk::ChebBatcher *batcher = nullptr;  // created with the first FP32 slot
     Clock::time_point t0 = Clock::now();
 
     double now_ms() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
@@ -232,6 +235,10 @@ void worker(tursca_server *srv) {
             if (!e) e = tursca_scene_create(&r->desc, s->st, &s->sc);
             if (!e) e = tursca_build_graph(s->sc);
             lk.lock();
+            if (!e && srv->batch_solves && r->desc.precision == TURSCA_FP32_REFINE) {
+                if (!srv->batcher) srv->batcher = tk::batcher_create();
+                tk::scene_attach_batcher(s->sc, srv->batcher);  // a null batcher leaves the scene's own passes
+            }
             if (e) {
                 if (s->sc) tursca_scene_destroy(s->sc);
                 if (s->st) cudaStreamDestroy(s->st);
@@ -356,6 +363,18 @@ tursca_status tursca_server_stats_get(tursca_server *srv, tursca_server_stats *o
     out->pending = (int)srv->pending.size();
     out->evictions = srv->evictions;
     out->slots_built = srv->built;
+    out->batches = out->batched_refinements = 0;
+    out->max_batch = 0;
+    if (srv->batcher) tk::batcher_stats(srv->batcher, &out->batches, &out->batched_refinements, &out->max_batch);
+    return TURSCA_OK;
+}
+
+tursca_status tursca_server_configure(tursca_server *srv, int option, double value) {
+    if (!srv) return TURSCA_E_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (option != TURSCA_SERVER_BATCH_SOLVES || (value != 0.0 && value != 1.0)) return TURSCA_E_INVALID;
+    if (srv->built > 0 || srv->next_ticket > 1) return TURSCA_E_STATE;  // before the first request
+    srv->batch_solves = value != 0.0;
     return TURSCA_OK;
 }
 
@@ -367,6 +386,7 @@ tursca_status tursca_server_destroy(tursca_server *srv) {
         srv->cv_work.notify_all();
     }
     for (auto &t : srv->workers) t.join();
+    tk::batcher_destroy(srv->batcher);  // idle: every request has finished
     for (auto &s : srv->slots) {
         tursca_scene_destroy(s->sc);
         cudaStreamDestroy(s->st);

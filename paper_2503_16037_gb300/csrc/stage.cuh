@@ -459,19 +459,23 @@ struct tile_op<Op, std::void_t<decltype(Op::kTile)>> {
 // previous pass has completed, and every slot then gathers from the tile:
 // tile[ttile[t] + rl], with rl the row's position within one tile layer.
 // Products and their order are those of k_plain.
-template <int W, class Op>
-__global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, GraphP gp, const float *__restrict__ val, Op op) {
+// One group gi of the tiled driver, shared by k_tile (one block per group,
+// kPdl: the previous pass is waited for after the graph data are read) and
+// the persistent batch of Chebyshev steps across requests (kCoherent: the
+// gathered vector was written by other blocks of the same launch since this
+// block last read it, so it is read around L1).  sh, tile, s_lay: the
+// block's shared memory; a block may run several groups one after another.
+template <int W, class Op, bool kPdl, bool kCoherent>
+__device__ __forceinline__ void tile_group(const GridC &g, const GraphP &gp, const float *__restrict__ val,
+                                           const Op &op, int gi, typename Op::A (*sh)[Op::NA][32], float *tile,
+                                           int *s_lay) {
     using A = typename Op::A;
     constexpr int NA = Op::NA;
-    __shared__ A sh[W][NA][32];
-    extern __shared__ float tile[];
-    __shared__ int s_lay[kTileLayers];
-    pdl_trigger();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const GroupRows G = group_rows(g, gp, blockIdx.x);
+    const GroupRows G = group_rows(g, gp, gi);
     // the tile's source layers are graph data: read them before waiting
     if (threadIdx.x < kTileLayers) s_lay[threadIdx.x] = __ldg(gp.tlay + G.z * kTileLayers + threadIdx.x);
-    const int r0 = (blockIdx.x - G.z * g.gpl) * kGroup;
+    const int r0 = (gi - G.z * g.gpl) * kGroup;
     const int y0 = r0 / g.nx;
     const int y1 = min(r0 + kGroup - 1, g.nxy - 1) / g.nx;
     const int tla = (y1 - y0 + 2 * g.H + 1) * g.nxp;  // floats copied per tile layer (<= tl)
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
     if (tA < G.nt) ld_quad(v + (size_t)tA * kGroup, v0);
     if (tB < G.nt) ld_quad(v + (size_t)tB * kGroup, v1);
     const int ttA = tA < G.nt ? __ldg(gp.ttile + G.t0 + tA) : 0, ttB = tB < G.nt ? __ldg(gp.ttile + G.t0 + tB) : 0;
-    pdl_wait();
+    if constexpr (kPdl) pdl_wait();
     const typename Op::Pre pre = load_pre(op, G);
     const int ts = kTileLayers * g.tl;  // floats per vector's tile
     __syncthreads();  // s_lay
@@ -503,7 +507,7 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
             if (lay < 0) break;  // the used tile layers come first
             const float *s = src + (long long)lay * g.lp;
             float *d = tile + iv * ts + ls * g.tl;
-            for (int j = threadIdx.x; j < tla; j += 32 * W) d[j] = s[j];
+            for (int j = threadIdx.x; j < tla; j += 32 * W) d[j] = kCoherent ? __ldcg(s + j) : s[j];
         }
     }
     __syncthreads();
@@ -529,7 +533,18 @@ __global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, Gra
 #pragma unroll
     for (int m = 0; m < NA; ++m) sh[w][m][lane] = a[m];
     __syncthreads();
-    finish_rows<W>(op, sh, G, pre, blockIdx.x);
+    finish_rows<W>(op, sh, G, pre, gi);
+}
+
+template <int W, class Op>
+__global__ void __launch_bounds__(32 * W, TK_TILE_WARPS / W) k_tile(GridC g, GraphP gp, const float *__restrict__ val, Op op) {
+    using A = typename Op::A;
+    constexpr int NA = Op::NA;
+    __shared__ A sh[W][NA][32];
+    extern __shared__ float tile[];
+    __shared__ int s_lay[kTileLayers];
+    pdl_trigger();
+    tile_group<W, Op, true, false>(g, gp, val, op, blockIdx.x, sh, tile, s_lay);
 }
 
 // pipelined launch: one block per run (one run per SM, at most one per group)

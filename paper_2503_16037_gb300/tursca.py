@@ -55,7 +55,8 @@ class tursca_request_info(C.Structure):
 class tursca_server_stats(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("used_bytes", C.c_size_t), ("peak_bytes", C.c_size_t),
                 ("slots", C.c_int), ("busy_slots", C.c_int), ("pending", C.c_int), ("evictions", C.c_int),
-                ("slots_built", C.c_int)]
+                ("slots_built", C.c_int), ("batches", C.c_longlong), ("batched_refinements", C.c_longlong),
+                ("max_batch", C.c_int)]
 
 
 class tursca_solve_info(C.Structure):
@@ -107,6 +108,8 @@ def lib() -> C.CDLL:
                                           C.POINTER(C.c_longlong)]),
             "tursca_server_wait": (st, [_vp, C.c_longlong, C.POINTER(tursca_request_info)]),
             "tursca_server_stats_get": (st, [_vp, C.POINTER(tursca_server_stats)]),
+            "tursca_server_configure": (st, [_vp, C.c_int, C.c_double]),
+            "tursca_selftest_barrier": (st, [_vp, C.c_int, C.c_int]),
             "tursca_server_destroy": (st, [_vp]),
             "tursca_graph_info": (st, [C.POINTER(tursca_grid_desc), C.POINTER(tursca_graph_stats)]),
             "tursca_graph_structure": (st, [C.POINTER(tursca_grid_desc), _vp, _vp, _vp, _vp]),
@@ -212,10 +215,16 @@ OPT_SINGLE_SCATTER = 6
 OPT_COUPLING_MIN = 7
 OPT_ANISO = 8
 OPT_MAX_COUPLINGS = 9
+SERVER_BATCH_SOLVES = 1
 
 
 def tursca_set_option(scene, option: int, value: float):
     _check(scene, lib().tursca_set_option(scene, int(option), float(value)))
+
+
+def tursca_selftest_barrier(blocks: int, arrive: bool, stream: int = 0) -> int:
+    """Status of the batched refinements' barrier self-test (OK or E_TIMEOUT)."""
+    return int(lib().tursca_selftest_barrier(C.c_void_p(stream), int(blocks), 1 if arrive else 0))
 
 
 def tursca_selection_info(scene) -> dict:
@@ -430,7 +439,7 @@ class Server:
     worker threads, and collected with wait().  Inputs are copied to pinned
     host buffers at submit and kept alive until wait() returns."""
 
-    def __init__(self, budget_bytes: int, workers: int):
+    def __init__(self, budget_bytes: int, workers: int, batch_solves: bool = False):
         import torch
         self.torch = torch
         h = _vp()
@@ -439,6 +448,9 @@ class Server:
             raise TurscaError(st, "tursca_server_create failed")
         self.handle = h.value
         self._live = {}
+        st = lib().tursca_server_configure(self.handle, SERVER_BATCH_SOLVES, 1.0 if batch_solves else 0.0)
+        if st != OK:
+            raise TurscaError(st, "tursca_server_configure failed")
 
     def submit(self, sc, precision: Optional[int] = None, rtol: float = 1e-10, fields=None, out=None) -> int:
         """Queue scene ``sc``; fields = (mu_a, mu_s) tensors (host pinned or

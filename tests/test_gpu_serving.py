@@ -42,8 +42,8 @@ def alone(sc, rtol=1e-10):
     return r
 
 
-def served(reqs, budget, workers):
-    srv = T.Server(budget, workers)
+def served(reqs, budget, workers, batch_solves=False):
+    srv = T.Server(budget, workers, batch_solves=batch_solves)
     tickets = [srv.submit(sc, T.FP32_REFINE, 1e-10) for sc in reqs]
     outs = [srv.wait(t) for t in tickets]
     st = srv.stats()
@@ -91,3 +91,51 @@ def test_request_that_cannot_fit_fails():
         srv.wait(t)
     assert e.value.status == T.E_NOMEM
     srv.close()
+
+
+# Batched refinements (tursca_server_configure(TURSCA_SERVER_BATCH_SOLVES)):
+# the Chebyshev refinements of concurrent requests run in one persistent
+# kernel; each request keeps its own schedule and every group is computed by
+# the code of the request's own pass, so results are bit for bit those of the
+# request alone.
+
+def test_batched_refinements_run_together_and_change_no_bit():
+    reqs = requests(32, seed=3)
+    ref = [alone(sc) for sc in reqs]
+    outs_on, st_on = served(reqs, 8 << 30, 8, batch_solves=True)
+    assert st_on["batches"] > 0 and st_on["max_batch"] >= 2
+    assert st_on["batched_refinements"] > st_on["batches"]
+    srv = T.Server(8 << 30, 8, batch_solves=False)
+    tickets = [srv.submit(sc, T.FP32_REFINE, 1e-10) for sc in reqs]
+    outs_off = [srv.wait(t) for t in tickets]
+    st_off = srv.stats()
+    srv.close()
+    assert st_off["batches"] == 0
+    for (a, ia), (b, ib), r in zip(outs_on, outs_off, ref):
+        assert ia["status"] == T.OK and ib["status"] == T.OK and ia["rel_resid64"] <= 1e-10
+        assert np.array_equal(a.numpy(), r) and np.array_equal(b.numpy(), r)
+    print("batched: %d launches, %d refinements, at most %d in one"
+          % (st_on["batches"], st_on["batched_refinements"], st_on["max_batch"]))
+
+
+def test_served_mix_matches_the_oracle():
+    """A small mixed batch of shapes and species against the FP64 oracle,
+    1e-4 relative on every pixel."""
+    from oracle import oracle as O
+    reqs = [scenes.make_plume(nx=16, ny=16, nz=8, sza=35.0), scenes.make_random(13, 11, 7, seed=8, S=3, R=1, M=1024),
+            scenes.make_plume(nx=20, ny=16, nz=10, sza=65.0), scenes.make_random(12, 11, 6, seed=10, S=2, R=2, M=1024)]
+    outs, st = served(reqs * 3, 4 << 30, 6, batch_solves=True)
+    for (rad, info), sc in zip(outs, reqs * 3):
+        assert info["status"] == T.OK
+        ref = O.run(sc)["rad"]
+        err = (np.abs(rad.numpy().astype(np.float64) - ref) / np.abs(ref)).max()
+        assert err < 1e-4, err
+
+
+def test_barrier_that_completes_and_one_that_runs_out():
+    s = torch.cuda.current_stream().cuda_stream
+    assert T.tursca_selftest_barrier(8, True, s) == T.OK
+    assert T.tursca_selftest_barrier(8, False, s) == T.E_TIMEOUT
+    # the device still serves afterwards
+    outs, _ = served(requests(4, seed=5), 2 << 30, 2, batch_solves=True)
+    assert all(info["status"] == T.OK for _, info in outs)
