@@ -284,7 +284,7 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     assembly).  Memory: 8 bytes per chain (n_atm n_dirs + n_ground
  *     n_gdirs) for the keys, besides what TURSCA_OPT_COUPLING_MIN allocates.
  *     Changing the value invalidates the current assembly.
- *   TURSCA_OPT_ANISO: 0 (default); 1 keeps the arrival direction of the
+ *   TURSCA_OPT_ANISO: 0 (default); 1 (or 2) keeps the arrival direction of the
  *     light into every scattering (the edge unknowns of Eq. flux_system;
  *     the default node form re-emits isotropically after the first
  *     scattering).  The unknown is X(i, w), the power scattered at node i from
@@ -295,13 +295,22 @@ tursca_status tursca_get(tursca_scene *scene, tursca_field which, void *dst, siz
  *     deposit fraction in place of K (get(TURSCA_F_VAL) then returns
  *     TURSCA_E_STATE) and builds the quadrature by arrival direction.  solve
  *     sums the series of Eq. fs_sum until the relative change of X is at most
- *     rtol (FP32 scenes: at least 1e-6); iters counts its terms and
- *     rel_resid64 holds the last relative change.  Combines with neither
+ *     rtol; FP32 scenes sum it in FP32 to a change of max(rtol, 1e-6), then
+ *     refine: while the residual |F(X) - X| / |X| of the fixed point, with X
+ *     in FP64 and double-single sums, is above rtol, an FP32 series for the
+ *     correction, added in FP64.  iters counts the terms of all series,
+ *     refinements the residual evaluations, and rel_resid64 holds the last
+ *     residual (FP64 scenes: the last relative change).  FP32 scenes compute
+ *     each term's dense per-node contraction on the tensor cores (tcgen05,
+ *     TF32 operands split in high and low parts) with 1 and on the CUDA cores
+ *     with 2; FP64 scenes on the CUDA cores.  Every term is deterministic (no
+ *     atomics).  Combines with neither
  *     TURSCA_OPT_SINGLE_SCATTER nor coupling selection (TURSCA_E_INVALID at
  *     assembly); tursca_adjoint returns TURSCA_E_UNSUPPORTED.  Memory:
- *     2 (n_dirs + n_gdirs) + 2 n_dirs values per node plus n_dirs haloed
- *     planes, in the compute type.  Changing the value invalidates the
- *     current assembly.
+ *     3 (n_dirs + n_gdirs) + 2 n_dirs values per node plus n_dirs haloed
+ *     planes, in the compute type; FP32 scenes add, at the first solve,
+ *     (n_dirs + n_gdirs) (8 + 4 + 4) bytes per node and n_dirs haloed FP64
+ *     planes.  Changing the value invalidates the current assembly.
  */
 enum {
     TURSCA_OPT_RESIDUAL_FP64 = 1,
@@ -470,6 +479,20 @@ typedef struct {
  *     launches may run at once, each on at most half the GPU. */
 enum { TURSCA_SERVER_BATCH_SOLVES = 1 };
 tursca_status tursca_server_configure(tursca_server *srv, int option, double value);
+
+/* Self-test of the anisotropic mode's dense contractions (FP32 scenes with
+ * a current assembly with TURSCA_OPT_ANISO): out[n][n_atm] (device, FP32)
+ * gets the raw contraction of the current tables for every atmospheric
+ * node, which = 0: sum_(w,sp) w_sp(j) zf(j,w) X(j,w) Q_sp(w -> n) with X a
+ * device array [n_dirs + n_gdirs][n_nodes] (n < n_dirs); which = 1:
+ * sum_(u,sp) w_sp(j) C(j,u) Q_sp(n -> u) (n < n_dirs + n_gdirs), the
+ * denominators of the routing factors.  tensor_cores: 1 the tcgen05 kernel
+ * (which = 0 only, TURSCA_E_UNSUPPORTED for 1; needs TURSCA_OPT_ANISO = 1 at
+ * assembly), 0 the CUDA-core kernel.
+ * Synchronises the scene's stream.  TURSCA_E_UNSUPPORTED for FP64 scenes,
+ * TURSCA_E_STATE without such an assembly. */
+tursca_status tursca_selftest_aniso_contract(tursca_scene *scene, int which, int tensor_cores, const void *X,
+                                            void *out);
 
 /* Self-test of the bounded grid barrier of the batched refinements: `blocks`
  * blocks of one cooperative launch wait at a barrier that expects all of

@@ -21,7 +21,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["graph.cpp", "kernels_asm.cu", "kernels_solve.cu", "kernels_render.cu", "kernels_adjoint.cu",
            "kernels_select.cu", "kernels_aniso.cu", "api.cu", "noalloc.cu", "selftest.cu", "server.cpp", "batch.cu"]
-HEADERS = ["graph.h", "kern.h", "stage.cuh", "asm_util.cuh", "first_order.h", "select.h", "aniso.h", "batch.h",
+HEADERS = ["graph.h", "kern.h", "stage.cuh", "asm_util.cuh", "first_order.h", "select.h", "aniso.h", "aniso_mma.cuh", "aniso_contract.cuh", "batch.h",
            "batcher.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -11,31 +11,91 @@
 //   L(c, k) = Lsun(c, k) + (sum_w X(c, w)) q_lamb_k c_k            ground c (Lambertian)
 //   X(i, w) = rho_i sum_{slots e of row i arriving along w} P_e L(src_e, dir_e)
 //
-// with Q_j the species mixture of the HG quadrature by arrival direction,
-// c the routing weight normalised with Q_j(w -> .), and Lsun the first-order
-// leaving power (e1 times the sun weights of the assembly).  The series of
-// Eq. fs_sum is iterated until the relative change of X is below the
-// requested tolerance.
+// with Q_j = sum_sp w_sp(j) Q_sp the species mixture of the HG quadrature by
+// arrival direction, c the routing weight of the coupling normalised with
+// Q_j(w -> .), and Lsun the first-order leaving power (e1 times the sun
+// weights of the assembly).
+//
+// The routing weight factors: c_j(u | w) = C(j, u) zf(j, w) with
+// zf = sum_u' Q_j(w, u') / sum_u' Q_j(w, u') C(j, u') over the directions u'
+// that have a receiver, wherever the routing applies at j (coupling on and
+// some receiver with C > 0: Q_j > 0 everywhere, so that decision does not
+// depend on w), and c = 1 elsewhere.  With
+//   A(j, (w, sp)) = w_sp(j) zf(j, w) X(j, w),   B((w, sp), u) = Q_sp(w -> u)
+// every term's leaving power is one dense contraction per node tile,
+//   L(j, u) = Lsun(j, u) + Cf(j, u) [A B](j, u),   Cf = C or 1,
+// for the directions that have a receiver.  A direction without one (it
+// leaves through the top; its light still crosses the source's own cell,
+// whose self slot reads L) has c = 1; those L come from a second, small
+// contraction over the top layers with A = w_sp X.  The denominators of zf
+// are one more contraction, per assembly:
+//   sqc(j, w) = [A' B'](j, w),  A'(j, (u, sp)) = w_sp(j) C(j, u),  B'((u, sp), w) = Q_sp(w -> u).
+// FP32 scenes run the per-term contraction on the tensor cores (tcgen05,
+// TF32 operands split in a high and a low part, three products, FP32
+// accumulation in tensor memory: a few 1e-6 relative); the per-assembly
+// one, whose zf is part of the operator that the FP64 residual refines
+// against, and every contraction of FP64 scenes and of the CUDA-core
+// variant, run as register-blocked loops on the CUDA cores.  The transport pass is a gather: each arrival direction of a row is
+// summed by one warp over the template's slots of that direction, in a fixed
+// order, so every term is deterministic.
+//
+// The series of Eq. fs_sum is iterated until the relative change of X is at
+// most the tolerance; the stopping test runs on the device and the host
+// reads it every few terms.  FP32 scenes then refine: the residual
+// r = F(X) - X of the fixed point X = F(X) is evaluated with X in FP64 and
+// every product accumulated in double-single (FP32 pairs), and the FP32
+// series solves e = r + (F(e) - F(0)) for the correction, X += e in FP64.
 #pragma once
 
 #include "kern.h"
 
 namespace tk {
 
+// tiles of the dense contractions: 128 nodes (the tensor-core M) by all
+// outputs; the K dimension runs in chunks of kAniRows rows of X (or of C)
+// times the species
+constexpr int kAniTileM = 128;
+constexpr int kAniRows = 8;
+
 template <typename T>
 struct AniP {
-    T *Q;          // [S][nin][nd] HG quadrature by arrival direction (rows sum to 1)
-    double *Qraw;  // [S][nin][nd] cell sums before normalisation
-    T *C;          // [n_nodes][nd] coupling of each chain's first receiver (-1: none)
-    T *Lsun;       // [n_nodes][nd] first-order leaving power along each direction
-    T *Wg;         // [n_ground][ngd] weights q_lamb c of the ground sources
-    T *Lh;         // [nd][npad] leaving power, haloed planes (read at source-relative positions)
-    double *acc;   // [2] sum of squared changes and of squares of X
+    T *Q;           // [S][nin][nd] HG quadrature by arrival direction (rows sum to 1)
+    double *Qraw;   // [S][nin][nd] cell sums before normalisation
+    T *SQ;          // [nz][S][nin] sum of Q_sp(w -> u) over the u that have a receiver from layer z
+    T *CT;          // [nd][n_atm] coupling of each chain's first receiver (0: none)
+    T *on;          // [n_atm] 1 where the routing applies, else 0
+    T *zf;          // [nin][n_atm] the routing factor zf (1 where the routing does not apply)
+    T *LsT;         // [nd][n_nodes] first-order leaving power (ground nodes: their ngd directions)
+    T *Wg;          // [n_ground][ngd] weights q_lamb c of the ground sources
+    T *Lh;          // [nd][npad] leaving power, haloed planes (read at source-relative positions)
+    const int *tperm;  // per layer template: its slots in order of arrival direction (template-local)
+    const int *tseg;   // [nz + 1][nin + 1] start of each arrival direction's run in tperm
+    double *part;   // [transport blocks][2] partial sums of the change of a term
+    double *acc;    // [3] sum of squared changes, of squares, relative change of the last checked term
+    int *ctl;       // [2] converged flag, terms taken when it was set
+    float *Bl;      // tensor-core operand of the leave contraction (FP32 scenes), split high / low
+    int mma;        // 1: contractions on the tensor cores (FP32 scenes)
 };
+
+// Operand tables in the tensor cores' layout: chunk c of K holds kAniRows
+// rows of X (or C) times S species, kc = kAniRows S values per output row;
+// per chunk, the high parts then the low parts, each np x kc values in
+// 8 x 4 core matrices (row groups of 8 outputs, 4 K values per 16 bytes).
+// The tile widths np (the MMA's N) the tensor-core kernel is built for
+// (N = nd <= 128); S >= 3 species use the widest.
+__host__ __device__ constexpr int ani_leave_np(int N, int S) {
+    return S >= 3 ? 128 : N <= 32 ? 32 : N <= 64 ? 64 : N <= 112 ? 112 : 128;
+}
+__host__ __device__ constexpr int ani_chunks(int rows) { return (rows + kAniRows - 1) / kAniRows; }
+// floats of a packed operand of `rows` K rows, tile width np
+inline size_t ani_btab_floats(int rows, int np, int S) {
+    return (size_t)ani_chunks(rows) * 2 * np * kAniRows * S;
+}
 
 // Per assembly: the edge kernel writes the raw deposit fraction P of every
 // slot into val (instead of K); then couplings, first-order leaving power,
-// ground weights and the quadrature tables.
+// ground weights, the quadrature tables, the routing factors zf and the
+// tensor-core operands.
 template <typename T>
 void launch_assemble_rows_p(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
                             const ViewC &vc, long long *launches);
@@ -43,16 +103,35 @@ template <typename T>
 void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                        const ViewP &vp, const AniP<T> &a, long long *launches);
 
-// One term of the series: X -> L (haloed planes) -> Xn = rho T L (Xn zeroed
-// here), and the change |Xn - X|^2, |Xn|^2 accumulated into a.acc (zeroed here).
+// One term of the series, X -> L (haloed planes) -> Xn = radd + rho T L,
+// where L carries Lsun when `sun` is set and radd may be null; then the
+// change |Xn - X|^2, |Xn|^2 and the stopping test: the first term whose
+// relative change is at most tol sets a.ctl = {1, term}; every kernel of a
+// later term returns at once.  a.ctl must be zeroed before the first term.
 template <typename T>
-void launch_aniso_step(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                       const AniP<T> &a, const T *X, T *Xn, long long *launches);
+void launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                       const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
+                       long long *launches);
+
+// FP32 refinement.  The residual r = F(X64) - X64 (F with Lsun) with every
+// product accumulated in double-single, L64 the haloed FP64 planes
+// [nd][npad]; r is stored in FP32 and a.acc gets |r|^2, |X64|^2.
+void launch_aniso_resid(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
+                        const ViewC &vc, const AniP<float> &a, const double *X64, double *L64, float *r,
+                        long long *launches);
+// X64 += e (init: X64 = e)
+void launch_aniso_update(cudaStream_t st, long long n, const float *e, double *X64, bool init);
 
 // x (total scattered power, FP64 haloed, for the ground term of the pixels)
-// and the emission toward the instrument from X.
-template <typename T>
-void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const T *X, double *x64, T *emis,
+// and the emission toward the instrument from X (type X of the unknowns).
+template <typename T, typename XT>
+void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, double *x64, T *emis,
                          long long *launches);
+
+// The two contractions alone, for the tests: out(j, n) for the atmospheric
+// nodes j of the current tables, n < N ([N][n_atm]); which: 0 leave (X in
+// [nin][n_nodes]), 1 sqc; mma: the tensor-core kernel, else the CUDA-core one.
+void launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
+                                const AniP<float> &a, const float *X, float *out, int which, bool mma);
 
 }  // namespace tk

@@ -165,9 +165,14 @@ struct tursca_scene {
     // anisotropic multiple scattering (edge unknowns): option, state, buffers
     int aniso = 0;
     bool aniso_asm = false, ani_ready = false;
-    void *ani_Q = nullptr, *ani_C = nullptr, *ani_Ls = nullptr, *ani_Wg = nullptr, *ani_Lh = nullptr,
-         *ani_X = nullptr, *ani_Xn = nullptr;
-    double *ani_Qraw = nullptr, *ani_acc = nullptr;
+    void *ani_Q = nullptr, *ani_SQ = nullptr, *ani_CT = nullptr, *ani_on = nullptr, *ani_zf = nullptr,
+         *ani_LsT = nullptr, *ani_Wg = nullptr, *ani_Lh = nullptr, *ani_X = nullptr, *ani_Xn = nullptr;
+    double *ani_Qraw = nullptr, *ani_acc = nullptr, *ani_part = nullptr;
+    int *ani_ctl = nullptr;
+    int *ani_tperm = nullptr, *ani_tseg = nullptr;  // slots of each layer by arrival direction (graph build)
+    float *ani_Bl = nullptr;                          // tensor-core operand (FP32 scenes)
+    double *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X in FP64, FP64 leaving power
+    float *ani_r = nullptr, *ani_E = nullptr;         // FP32 refinement: residual, correction
     bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
@@ -1324,17 +1329,43 @@ tursca_status ensure_aniso(tursca_scene *sc) {
     if (sc->ani_ready) return TURSCA_OK;
     const tk::GridC g = grid_c(sc);
     const size_t es = sc->es, nin = (size_t)g.nd + g.ngd, S = (size_t)g.S;
+    const size_t nblk = (size_t)(g.nz + 1) * g.gpl;
     CK(dalloc(sc->allocs, sc->ani_Q, S * nin * g.nd * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Qraw, S * nin * g.nd * sizeof(double)), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_C, (size_t)g.n_nodes * g.nd * es), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_Ls, (size_t)g.n_nodes * g.nd * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_SQ, (size_t)g.nz * S * nin * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_CT, (size_t)g.nd * g.n_atm * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_on, (size_t)g.n_atm * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_zf, nin * g.n_atm * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_LsT, (size_t)g.nd * g.n_nodes * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Wg, (size_t)std::max(1, g.n_ground) * std::max(1, g.ngd) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Lh, (size_t)g.nd * g.npad * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_X, nin * g.n_nodes * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Xn, nin * g.n_nodes * es), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_acc, 2 * sizeof(double)), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_acc, 3 * sizeof(double)), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_part, 2 * nblk * sizeof(double)), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_ctl, 2 * sizeof(int)), "alloc aniso");
+    if (sc->d.precision != TURSCA_FP64) {
+        // packed for the tile width the tensor-core launches use
+        CK(dalloc(sc->allocs, sc->ani_Bl,
+                  tk::ani_btab_floats((int)nin, tk::ani_leave_np(g.nd, g.S), g.S) * sizeof(float)),
+           "alloc aniso");
+
+    }
     CK(cudaMemsetAsync(sc->ani_Lh, 0, (size_t)g.nd * g.npad * es, sc->st), "memset aniso");
     sc->ani_ready = true;
+    return TURSCA_OK;
+}
+
+// The FP32 refinement's buffers, allocated by the first refinement.
+tursca_status ensure_aniso_refine(tursca_scene *sc) {
+    if (sc->ani_X64) return TURSCA_OK;
+    const tk::GridC g = grid_c(sc);
+    const size_t nx = ((size_t)g.nd + g.ngd) * g.n_nodes;
+    CK(dalloc(sc->allocs, sc->ani_X64, nx * sizeof(double)), "alloc aniso refinement");
+    CK(dalloc(sc->allocs, sc->ani_L64, (size_t)g.nd * g.npad * sizeof(double)), "alloc aniso refinement");
+    CK(dalloc(sc->allocs, sc->ani_r, nx * sizeof(float)), "alloc aniso refinement");
+    CK(dalloc(sc->allocs, sc->ani_E, nx * sizeof(float)), "alloc aniso refinement");
+    CK(cudaMemsetAsync(sc->ani_L64, 0, (size_t)g.nd * g.npad * sizeof(double), sc->st), "memset aniso");
     return TURSCA_OK;
 }
 
@@ -1343,51 +1374,128 @@ tk::AniP<T> ani_p(tursca_scene *sc) {
     tk::AniP<T> a;
     a.Q = (T *)sc->ani_Q;
     a.Qraw = sc->ani_Qraw;
-    a.C = (T *)sc->ani_C;
-    a.Lsun = (T *)sc->ani_Ls;
+    a.SQ = (T *)sc->ani_SQ;
+    a.CT = (T *)sc->ani_CT;
+    a.on = (T *)sc->ani_on;
+    a.zf = (T *)sc->ani_zf;
+    a.LsT = (T *)sc->ani_LsT;
     a.Wg = (T *)sc->ani_Wg;
     a.Lh = (T *)sc->ani_Lh;
+    a.tperm = sc->ani_tperm;
+    a.tseg = sc->ani_tseg;
+    a.part = sc->ani_part;
     a.acc = sc->ani_acc;
+    a.ctl = sc->ani_ctl;
+    a.Bl = sc->ani_Bl;
+    a.mma = sizeof(T) == 4 && sc->aniso == 1;
     return a;
 }
 
-// The series of Eq. fs_sum over the edge unknowns until the relative change
-// of X is at most the tolerance (FP32 scenes: at least 1e-6, about the
-// rounding floor of an FP32 iterate), then x and the emission from X.
+// Terms of the series X <- radd + rho T L(X) (L with Lsun when `sun`) from
+// the content of X (buffer 0) until the relative change is at most tol or
+// max_terms terms: the stopping test runs on the device after every term and
+// the host reads it every kAniCheck terms.  Returns the buffer holding the
+// last term in *xi (0: X, 1: Xn), the terms in *terms, the last change in *rel.
+constexpr int kAniCheck = 8;
 template <typename T>
-tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun, double tol, int max_terms,
+                         int *xi, int *terms, double *rel) {
     const tk::GridC g = grid_c(sc);
     const tk::GraphP gp = graph_p(sc);
     const tk::FieldP<T> f = field_p<T>(sc);
     const tk::ViewC vc = view_c(sc);
     const tk::AniP<T> a = ani_p<T>(sc);
-    const double tol = sizeof(T) == 8 ? rtol : std::max(rtol, 1e-6);
+    T *buf[2] = {X, Xn};
+    CK(cudaMemsetAsync(a.ctl, 0, 2 * sizeof(int), sc->st), "memset ctl");
+    int k = 0, h[2] = {0, 0};
+    double acc[3] = {0.0, 0.0, 1.0};
+    while (k < max_terms) {
+        const int n = std::min(kAniCheck, max_terms - k);
+        for (int i = 0; i < n; ++i, ++k)
+            tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol, k + 1,
+                                     &sc->launches);
+        CK(cudaGetLastError(), "aniso launch");
+        CK(cudaMemcpyAsync(h, a.ctl, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read ctl");
+        CK(cudaMemcpyAsync(acc, a.acc, sizeof acc, cudaMemcpyDeviceToHost, sc->st), "read change");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        if (h[0]) break;
+    }
+    const int taken = h[0] ? h[1] : k;
+    *xi = taken & 1;
+    *terms = taken;
+    *rel = acc[2];
+    return TURSCA_OK;
+}
+
+// The series of Eq. fs_sum over the edge unknowns, then x and the emission
+// from X.  FP64 scenes: until the relative change of X is at most rtol.
+// FP32 scenes: the FP32 series to a change of max(rtol, 1e-6) (about the
+// rounding floor of an FP32 iterate), then while the FP64 residual
+// |F(X) - X| / |X| is above rtol, the correction series and X += e in FP64.
+constexpr int kAniMaxRefine = 8;
+template <typename T>
+tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
+    const tk::GridC g = grid_c(sc);
+    const tk::FieldP<T> f = field_p<T>(sc);
     const size_t nx = ((size_t)g.nd + g.ngd) * g.n_nodes;
     T *X = (T *)sc->ani_X, *Xn = (T *)sc->ani_Xn;
     CK(cudaMemsetAsync(X, 0, nx * sizeof(T), sc->st), "memset X");
+    const double tol = sizeof(T) == 8 ? rtol : std::max(rtol, 1e-6);
+    int xi = 0, terms = 0, total = 0, refinements = 0;
     double rel = 1.0;
-    int it = 0;
-    while (it < max_iter) {
-        tk::launch_aniso_step<T>(sc->st, g, gp, f, vc, a, X, Xn, &sc->launches);
-        double h[2] = {0.0, 0.0};
-        CK(cudaMemcpyAsync(h, a.acc, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read change");
-        CK(cudaStreamSynchronize(sc->st), "sync");
-        std::swap(X, Xn);
-        ++it;
-        rel = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : 0.0;
-        if (rel <= tol) break;
+    tursca_status e = ani_series<T>(sc, X, Xn, nullptr, true, tol, max_iter, &xi, &terms, &rel);
+    if (e) return e;
+    total = terms;
+    bool converged = rel <= tol;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 refinement with the FP64 residual
+        e = ensure_aniso_refine(sc);
+        if (e) return e;
+        const tk::GridC gg = grid_c(sc);
+        const tk::GraphP gp = graph_p(sc);
+        const tk::ViewC vc = view_c(sc);
+        const tk::AniP<float> a = ani_p<float>(sc);
+        tk::launch_aniso_update(sc->st, (long long)nx, xi ? Xn : X, sc->ani_X64, true);
+        converged = false;
+        while (refinements < kAniMaxRefine) {
+            tk::launch_aniso_resid(sc->st, gg, gp, f, vc, a, sc->ani_X64, sc->ani_L64, sc->ani_r, &sc->launches);
+            sc->launches++;
+            double acc[3];
+            CK(cudaGetLastError(), "aniso residual launch");
+            CK(cudaMemcpyAsync(acc, a.acc, sizeof acc, cudaMemcpyDeviceToHost, sc->st), "read residual");
+            CK(cudaStreamSynchronize(sc->st), "sync");
+            ++refinements;
+            rel = acc[2];
+            if (rel <= rtol) {
+                converged = true;
+                break;
+            }
+            if (total >= max_iter) break;
+            // e = r + (F(e) - F(0)), from e = r
+            const double tol_e = std::min(0.5, std::max(1e-6, 0.3 * rtol / rel));
+            CK(cudaMemcpyAsync(sc->ani_E, sc->ani_r, nx * sizeof(float), cudaMemcpyDeviceToDevice, sc->st),
+               "copy residual");
+            int ei = 0, et = 0;
+            double erel = 1.0;
+            e = ani_series<float>(sc, sc->ani_E, (float *)Xn, sc->ani_r, false, tol_e, max_iter - total, &ei, &et,
+                                  &erel);
+            if (e) return e;
+            total += et;
+            tk::launch_aniso_update(sc->st, (long long)nx, ei ? (float *)Xn : sc->ani_E, sc->ani_X64, false);
+        }
+        tk::launch_aniso_finish<float, double>(sc->st, gg, f, sc->ani_X64, sc->x64, (float *)sc->emis,
+                                               &sc->launches);
+    } else {
+        tk::launch_aniso_finish<T, T>(sc->st, g, f, xi ? Xn : X, sc->x64, (T *)sc->emis, &sc->launches);
     }
-    sc->ani_X = X;
-    sc->ani_Xn = Xn;
-    tk::launch_aniso_finish<T>(sc->st, g, f, X, sc->x64, (T *)sc->emis, &sc->launches);
     CK(cudaGetLastError(), "aniso launch");
     if (solver == TURSCA_SOLVER_AUTO)
         solver = sc->d.precision == TURSCA_FP64 ? TURSCA_SOLVER_GMRES : TURSCA_SOLVER_CHEBYSHEV;
-    if (info) *info = tursca_solve_info{it, 0, rel, 0.0, solver};
-    tursca_status e = sync_check(sc, "solve");
+    if (info) *info = tursca_solve_info{total, refinements, rel, 0.0, solver};
+    e = sync_check(sc, "solve");
     if (e) return e;
     sc->solved = true;
-    if (rel > tol) return fail(sc, TURSCA_E_NOT_CONVERGED, "series stopped above the tolerance");
+    if (!converged) return fail(sc, TURSCA_E_NOT_CONVERGED, "series stopped above the tolerance");
     return TURSCA_OK;
 }
 
@@ -1637,6 +1745,33 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
             d.splitd = e.split;
         }
         CK(upload(sc, sc->allocs, sc->aslot, as.data(), as.size() * sizeof(tk::ASlot)), "upload slots");
+        // the edge form's transport order: each layer's template slots
+        // grouped by arrival direction (atmospheric direction, or nd + the
+        // ground direction of a ground source), in template order inside a
+        // direction
+        {
+            const int ndh = (int)G.uhat.size(), nin = ndh + (int)G.gdirs.size();
+            std::vector<int> perm(as.size()), segs((size_t)(sc->d.nz + 1) * (nin + 1));
+            for (int z = 0; z <= sc->d.nz; ++z) {
+                const int t0 = G.tmpl_start[z], nt = G.tmpl_start[z + 1] - t0;
+                std::vector<int> cnt(nin + 1, 0);
+                for (int t = 0; t < nt; ++t) {
+                    const tk::ASlot &d = as[t0 + t];
+                    const int din = ((d.bits >> 11) & 1) ? ndh + d.dir : d.dir;
+                    if (din < 0 || din >= nin) return fail(sc, TURSCA_E_INVALID, "internal error: arrival direction");
+                    cnt[din + 1]++;
+                }
+                for (int w = 0; w < nin; ++w) cnt[w + 1] += cnt[w];
+                for (int w = 0; w <= nin; ++w) segs[(size_t)z * (nin + 1) + w] = cnt[w];
+                for (int t = 0; t < nt; ++t) {
+                    const tk::ASlot &d = as[t0 + t];
+                    const int din = ((d.bits >> 11) & 1) ? ndh + d.dir : d.dir;
+                    perm[t0 + cnt[din]++] = t;
+                }
+            }
+            CK(upload(sc, sc->allocs, sc->ani_tperm, perm.data(), perm.size() * sizeof(int)), "upload order");
+            CK(upload(sc, sc->allocs, sc->ani_tseg, segs.data(), segs.size() * sizeof(int)), "upload order");
+        }
         if (th.empty()) th.push_back(0);
         CK(upload(sc, sc->allocs, sc->tap_h, th.data(), th.size() * sizeof(int)), "upload taps");
         CK(upload(sc, sc->allocs, sc->dir_h, dh.data(), dh.size() * sizeof(int)), "upload dirs");
@@ -2162,7 +2297,8 @@ tursca_status tursca_set_option(tursca_scene *sc, int option, double value) {
             }
             return TURSCA_OK;
         case TURSCA_OPT_ANISO:
-            if (value != 0.0 && value != 1.0) return fail(sc, TURSCA_E_INVALID, "anisotropic mode must be 0 or 1");
+            if (value != 0.0 && value != 1.0 && value != 2.0)
+                return fail(sc, TURSCA_E_INVALID, "anisotropic mode must be 0, 1 or 2");
             if ((int)value != sc->aniso) {
                 sc->aniso = (int)value;
                 sc->assembled = sc->solved = sc->rendered = false;
@@ -2237,6 +2373,25 @@ tursca_status tursca_selftest_barrier(void *cuda_stream, int blocks, int arrive)
     const int r = tk::batch_barrier_selftest((cudaStream_t)cuda_stream, blocks, arrive);
     if (r < 0) return fail(nullptr, TURSCA_E_CUDA, "barrier self-test: CUDA error");
     return r ? TURSCA_E_TIMEOUT : TURSCA_OK;
+}
+
+tursca_status tursca_selftest_aniso_contract(tursca_scene *sc, int which, int tensor_cores, const void *X,
+                                            void *out) {
+    if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");
+    if (which != 0 && which != 1) return fail(sc, TURSCA_E_INVALID, "which must be 0 or 1");
+    if (!out || (which == 0 && !X)) return fail(sc, TURSCA_E_INVALID, "null buffer");
+    if (sc->d.precision == TURSCA_FP64) return fail(sc, TURSCA_E_UNSUPPORTED, "FP32 scenes only");
+    if (!sc->assembled || !sc->aniso_asm) return fail(sc, TURSCA_E_STATE, "no anisotropic assembly");
+    if (tensor_cores && which == 1)
+        return fail(sc, TURSCA_E_UNSUPPORTED, "the routing denominators run on the CUDA cores only");
+    if (tensor_cores && (!sc->ani_Bl || sc->aniso != 1))
+        return fail(sc, TURSCA_E_STATE, "no tensor-core operands");
+    tk::AniP<float> a = ani_p<float>(sc);
+    a.mma = tensor_cores ? 1 : 0;
+    tk::launch_aniso_contract_test(sc->st, grid_c(sc), graph_p(sc), field_p<float>(sc), a, (const float *)X,
+                                   (float *)out, which, tensor_cores != 0);
+    CK(cudaGetLastError(), "contraction launch");
+    return sync_check(sc, "contraction");
 }
 
 tursca_status tursca_selection_info(const tursca_scene *sc, double *threshold, long long *n_couplings,

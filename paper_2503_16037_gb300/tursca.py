@@ -110,6 +110,7 @@ def lib() -> C.CDLL:
             "tursca_server_stats_get": (st, [_vp, C.POINTER(tursca_server_stats)]),
             "tursca_server_configure": (st, [_vp, C.c_int, C.c_double]),
             "tursca_selftest_barrier": (st, [_vp, C.c_int, C.c_int]),
+            "tursca_selftest_aniso_contract": (st, [_vp, C.c_int, C.c_int, _vp, _vp]),
             "tursca_server_destroy": (st, [_vp]),
             "tursca_graph_info": (st, [C.POINTER(tursca_grid_desc), C.POINTER(tursca_graph_stats)]),
             "tursca_graph_structure": (st, [C.POINTER(tursca_grid_desc), _vp, _vp, _vp, _vp]),
@@ -225,6 +226,14 @@ def tursca_set_option(scene, option: int, value: float):
 def tursca_selftest_barrier(blocks: int, arrive: bool, stream: int = 0) -> int:
     """Status of the batched refinements' barrier self-test (OK or E_TIMEOUT)."""
     return int(lib().tursca_selftest_barrier(C.c_void_p(stream), int(blocks), 1 if arrive else 0))
+
+
+def tursca_selftest_aniso_contract(scene, which: int, tensor_cores: bool, X, out):
+    """Raw dense contraction of the anisotropic mode (0: leave, 1: routing
+    denominators) into the device tensor ``out`` ([N][n_atm], float32)."""
+    xp = None if X is None else C.c_void_p(X.data_ptr())
+    _check(scene, lib().tursca_selftest_aniso_contract(scene, int(which), 1 if tensor_cores else 0, xp,
+                                                       C.c_void_p(out.data_ptr())))
 
 
 def tursca_selection_info(scene) -> dict:

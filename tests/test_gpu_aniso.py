@@ -2,7 +2,9 @@
 TURSCA_OPT_ANISO) against the FP64 oracle's edge form.
 
 Tolerances as for the node form: FP64 1e-10 relative on every radiance,
-FP32 (series in FP32 to a relative change of 1e-6) 1e-4.
+FP32 (FP32 series, then refinement with the FP64 residual; the dense
+per-node contraction on the tensor cores, or with TURSCA_OPT_ANISO = 2 on
+the CUDA cores) 1e-4.
 """
 import numpy as np
 import pytest
@@ -43,20 +45,67 @@ CASES = {
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_cuda_cores"])
 def test_aniso_parity(name, prec):
     sc = CASES[name]()
     r = O.run(sc, flags=O.ANISO)
-    rn, rad = run_aniso(sc, T.FP64 if prec == "fp64" else T.FP32_REFINE)
+    rn, rad = run_aniso(sc, T.FP64 if prec == "fp64" else T.FP32_REFINE, aniso=2 if prec == "fp32_cuda_cores" else 1)
     tol = 1e-10 if prec == "fp64" else 1e-4
     st = rn.stats
     x = rn.get(T.F_X, st.n_nodes, torch.float64)
     assert np.abs(x - r["x"]).max() <= tol * np.abs(r["x"]).max()
     err = (np.abs(rad - r["rad"]) / np.abs(r["rad"])).max()
     node = O.run(sc)["rad"]
-    print("%s %s: %d terms, radiance max rel err %.2e (edge vs node form differ by %.2e)"
-          % (name, prec, rn.info.iters, err, (np.abs(r["rad"] - node) / node).max()))
+    print("%s %s: %d terms, %d residuals (%.1e), radiance max rel err %.2e (edge vs node form differ by %.2e)"
+          % (name, prec, rn.info.iters, rn.info.refinements, rn.info.rel_resid64, err,
+             (np.abs(r["rad"] - node) / node).max()))
     assert err < tol
+    if prec != "fp64":
+        assert rn.info.refinements >= 1 and rn.info.rel_resid64 <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["random_R2_2species", "random_R1_3species"])
+def test_aniso_contractions_tensor_cores_match_cuda_cores(name):
+    """The tcgen05 kernel (TF32 high/low split, FP32 accumulation in tensor
+    memory) against the CUDA-core FP32 kernel on the same tables, every
+    output of the per-term contraction; the per-assembly one runs on the
+    CUDA cores only."""
+    sc = CASES[name]()
+    rn = T.Runner(sc, T.FP32_REFINE)
+    T.tursca_set_option(rn.handle, T.OPT_ANISO, 1)
+    mu_a, mu_s = rn.fields("cuda")
+    rn.set_medium(mu_a, mu_s)
+    rn.assemble()
+    st = rn.stats
+    nin = st.n_dirs + st.n_gdirs
+    g = torch.Generator(device="cpu").manual_seed(7)
+    X = torch.rand((nin, st.n_nodes), generator=g, dtype=torch.float32).cuda()
+    out = torch.zeros((nin, st.n_atm), dtype=torch.float32, device="cuda")
+    with pytest.raises(T.TurscaError) as e:
+        T.tursca_selftest_aniso_contract(rn.handle, 1, True, X, out)
+    assert e.value.status == T.E_UNSUPPORTED
+    for which, N in ((0, st.n_dirs),):
+        outs = []
+        for mma in (True, False):
+            out = torch.full((N, st.n_atm), float("nan"), dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            T.tursca_selftest_aniso_contract(rn.handle, which, mma, X, out)
+            outs.append(out.double().cpu().numpy())
+        a, b = outs
+        assert np.isfinite(a).all() and np.isfinite(b).all()
+        scale = np.abs(b).max(axis=0, keepdims=True) + 1e-30
+        err = (np.abs(a - b) / scale).max()
+        print("%s contraction %d: max rel err %.2e" % (name, which, err))
+        # hi*hi + hi*lo + lo*hi leaves 2^-22 of each product; the tensor
+        # memory's FP32 accumulation over the 3 K / 8 MMAs adds a few 1e-6
+        assert err < 2e-5
+
+
+def test_aniso_terms_are_deterministic():
+    sc = CASES["plume_12x12x6"]()
+    _, a = run_aniso(sc, T.FP32_REFINE)
+    _, b = run_aniso(sc, T.FP32_REFINE)
+    assert np.array_equal(a, b)
 
 
 def test_aniso_isotropic_phase_equals_node_form_on_gpu():
