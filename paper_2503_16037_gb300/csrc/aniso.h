@@ -16,6 +16,14 @@
 // Q_j(w -> .), and Lsun the first-order leaving power (e1 times the sun
 // weights of the assembly).
 //
+// The series itself runs on G = [A B] (and, on the top layers, its zf-free
+// form for the directions without a receiver; on the ground x_t q_lamb c):
+// per assembly Cf is folded into the deposit fractions, P' = P Cf(src, dir),
+// and the first-order term b = rho T Lsun is formed once, so that a term is
+//   X' = b + rho sum_slots P' G(src, dir)
+// and the contraction's epilogue only stores G.  The FP64 residual keeps
+// the unfolded form L = Lsun + Cf G with the plain P.
+//
 // The routing weight factors: c_j(u | w) = C(j, u) zf(j, w) with
 // zf = sum_u' Q_j(w, u') / sum_u' Q_j(w, u') C(j, u') over the directions u'
 // that have a receiver, wherever the routing applies at j (coupling on and
@@ -64,12 +72,21 @@ struct AniP {
     T *SQ;          // [nz][S][nin] sum of Q_sp(w -> u) over the u that have a receiver from layer z
     T *CT;          // [nd][n_atm] coupling of each chain's first receiver (0: none)
     T *on;          // [n_atm] 1 where the routing applies, else 0
-    T *zf;          // [nin][n_atm] the routing factor zf (1 where the routing does not apply)
+    T *zf;          // [nin][ldz] the routing factor zf (1 where the routing does not apply)
     T *LsT;         // [nd][n_nodes] first-order leaving power (ground nodes: their ngd directions)
     T *Wg;          // [n_ground][ngd] weights q_lamb c of the ground sources
     T *Lh;          // [nd][npad] leaving power, haloed planes (read at source-relative positions)
-    const int *tperm;  // per layer template: its slots in order of arrival direction (template-local)
-    const int *tseg;   // [nz + 1][nin + 1] start of each arrival direction's run in tperm
+    T *CfH;         // [nd][npad] routing coupling Cf of every chain (C where the routing applies, else 1;
+                    // ground sources 1), haloed planes
+    T *Pc;          // per slot (K's value layout) the deposit fraction times its chain's Cf: P Cf(src, dir)
+    T *b;           // [nin][ldx] first-order term rho T Lsun (the series' source)
+    const int4 *tslot; // per layer template: its slots in order of arrival direction, {t, src, dir, 0}
+                       // (t: template-local index, src and dir as in the slot descriptor)
+    const int *tseg;   // [nz + 1][nin + 1] start of each arrival direction's run in tslot
+    int max_nt;        // slots of the largest layer template
+    int ldx;           // row stride of the [nin][.] node arrays (X, Xn, corrections, residual, X in FP64):
+                       // n_nodes rounded up to 32, so that every row starts on 128 bytes
+    int ldz;           // row stride of zf: n_atm rounded up to 32
     double *part;   // [transport blocks][2] partial sums of the change of a term
     double *acc;    // [3] sum of squared changes, of squares, relative change of the last checked term
     int *ctl;       // [2] converged flag, terms taken when it was set
@@ -103,15 +120,18 @@ template <typename T>
 void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                        const ViewP &vp, const AniP<T> &a, long long *launches);
 
+// X, Xn and radd below are [nin][ldx].
 // One term of the series, X -> L (haloed planes) -> Xn = radd + rho T L,
 // where L carries Lsun when `sun` is set and radd may be null; then the
 // change |Xn - X|^2, |Xn|^2 and the stopping test: the first term whose
 // relative change is at most tol sets a.ctl = {1, term}; every kernel of a
 // later term returns at once.  a.ctl must be zeroed before the first term.
+// cudaErrorInvalidValue when the tensor-core kernel's tensor maps cannot be
+// made (nothing launched then).
 template <typename T>
-void launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                       const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
-                       long long *launches);
+cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                              const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
+                              long long *launches);
 
 // FP32 refinement.  The residual r = F(X64) - X64 (F with Lsun) with every
 // product accumulated in double-single, L64 the haloed FP64 planes
@@ -121,17 +141,16 @@ void launch_aniso_resid(cudaStream_t st, const GridC &g, const GraphP &gp, const
                         long long *launches);
 // X64 += e (init: X64 = e)
 void launch_aniso_update(cudaStream_t st, long long n, const float *e, double *X64, bool init);
-
 // x (total scattered power, FP64 haloed, for the ground term of the pixels)
 // and the emission toward the instrument from X (type X of the unknowns).
 template <typename T, typename XT>
-void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, double *x64, T *emis,
-                         long long *launches);
+void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, int ldx, double *x64,
+                         T *emis, long long *launches);
 
 // The two contractions alone, for the tests: out(j, n) for the atmospheric
 // nodes j of the current tables, n < N ([N][n_atm]); which: 0 leave (X in
-// [nin][n_nodes]), 1 sqc; mma: the tensor-core kernel, else the CUDA-core one.
-void launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
-                                const AniP<float> &a, const float *X, float *out, int which, bool mma);
+// [nin][ldx]), 1 sqc; mma: the tensor-core kernel, else the CUDA-core one.
+cudaError_t launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
+                                       const AniP<float> &a, const float *X, float *out, int which, bool mma);
 
 }  // namespace tk

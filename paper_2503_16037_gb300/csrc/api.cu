@@ -169,8 +169,11 @@ struct tursca_scene {
          *ani_LsT = nullptr, *ani_Wg = nullptr, *ani_Lh = nullptr, *ani_X = nullptr, *ani_Xn = nullptr;
     double *ani_Qraw = nullptr, *ani_acc = nullptr, *ani_part = nullptr;
     int *ani_ctl = nullptr;
-    int *ani_tperm = nullptr, *ani_tseg = nullptr;  // slots of each layer by arrival direction (graph build)
+    int4 *ani_tslot = nullptr;  // slots of each layer by arrival direction (graph build): {t, src, dir, 0}
+    int *ani_tseg = nullptr;    // start of each arrival direction's run
+    int ani_max_nt = 0;         // slots of the largest layer template
     float *ani_Bl = nullptr;                          // tensor-core operand (FP32 scenes)
+    void *ani_CfH = nullptr, *ani_Pc = nullptr, *ani_b = nullptr;  // the series' folded form
     double *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X in FP64, FP64 leaving power
     float *ani_r = nullptr, *ani_E = nullptr;         // FP32 refinement: residual, correction
     bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
@@ -1324,6 +1327,11 @@ tursca_status ensure_select(tursca_scene *sc) {
     return TURSCA_OK;
 }
 
+// Row strides of the anisotropic mode's [nin][.] arrays: every row starts
+// on 128 bytes (the tensor maps of the tensor-core kernel want 16).
+inline int ani_ldx(const tk::GridC &g) { return (g.n_nodes + 31) / 32 * 32; }
+inline int ani_ldz(const tk::GridC &g) { return (g.n_atm + 31) / 32 * 32; }
+
 // Buffers of the anisotropic mode, allocated by its first assembly.
 tursca_status ensure_aniso(tursca_scene *sc) {
     if (sc->ani_ready) return TURSCA_OK;
@@ -1335,12 +1343,16 @@ tursca_status ensure_aniso(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->ani_SQ, (size_t)g.nz * S * nin * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_CT, (size_t)g.nd * g.n_atm * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_on, (size_t)g.n_atm * es), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_zf, nin * g.n_atm * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_zf, nin * ani_ldz(g) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_LsT, (size_t)g.nd * g.n_nodes * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Wg, (size_t)std::max(1, g.n_ground) * std::max(1, g.ngd) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Lh, (size_t)g.nd * g.npad * es), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_X, nin * g.n_nodes * es), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_Xn, nin * g.n_nodes * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_CfH, (size_t)g.nd * g.npad * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Pc, (size_t)sc->G.nval * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_b, nin * ani_ldx(g) * es), "alloc aniso");
+    CK(cudaMemsetAsync(sc->ani_CfH, 0, (size_t)g.nd * g.npad * es, sc->st), "memset aniso");
+    CK(dalloc(sc->allocs, sc->ani_X, nin * ani_ldx(g) * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_Xn, nin * ani_ldx(g) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_acc, 3 * sizeof(double)), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_part, 2 * nblk * sizeof(double)), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_ctl, 2 * sizeof(int)), "alloc aniso");
@@ -1360,7 +1372,7 @@ tursca_status ensure_aniso(tursca_scene *sc) {
 tursca_status ensure_aniso_refine(tursca_scene *sc) {
     if (sc->ani_X64) return TURSCA_OK;
     const tk::GridC g = grid_c(sc);
-    const size_t nx = ((size_t)g.nd + g.ngd) * g.n_nodes;
+    const size_t nx = ((size_t)g.nd + g.ngd) * ani_ldx(g);
     CK(dalloc(sc->allocs, sc->ani_X64, nx * sizeof(double)), "alloc aniso refinement");
     CK(dalloc(sc->allocs, sc->ani_L64, (size_t)g.nd * g.npad * sizeof(double)), "alloc aniso refinement");
     CK(dalloc(sc->allocs, sc->ani_r, nx * sizeof(float)), "alloc aniso refinement");
@@ -1381,8 +1393,14 @@ tk::AniP<T> ani_p(tursca_scene *sc) {
     a.LsT = (T *)sc->ani_LsT;
     a.Wg = (T *)sc->ani_Wg;
     a.Lh = (T *)sc->ani_Lh;
-    a.tperm = sc->ani_tperm;
+    a.CfH = (T *)sc->ani_CfH;
+    a.Pc = (T *)sc->ani_Pc;
+    a.b = (T *)sc->ani_b;
+    a.tslot = sc->ani_tslot;
     a.tseg = sc->ani_tseg;
+    a.max_nt = sc->ani_max_nt;
+    a.ldx = ani_ldx(grid_c(sc));
+    a.ldz = ani_ldz(grid_c(sc));
     a.part = sc->ani_part;
     a.acc = sc->ani_acc;
     a.ctl = sc->ani_ctl;
@@ -1412,8 +1430,9 @@ tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun,
     while (k < max_terms) {
         const int n = std::min(kAniCheck, max_terms - k);
         for (int i = 0; i < n; ++i, ++k)
-            tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol, k + 1,
-                                     &sc->launches);
+            CK(tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol, k + 1,
+                                        &sc->launches),
+               "aniso term");
         CK(cudaGetLastError(), "aniso launch");
         CK(cudaMemcpyAsync(h, a.ctl, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read ctl");
         CK(cudaMemcpyAsync(acc, a.acc, sizeof acc, cudaMemcpyDeviceToHost, sc->st), "read change");
@@ -1431,13 +1450,19 @@ tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun,
 // from X.  FP64 scenes: until the relative change of X is at most rtol.
 // FP32 scenes: the FP32 series to a change of max(rtol, 1e-6) (about the
 // rounding floor of an FP32 iterate), then while the FP64 residual
-// |F(X) - X| / |X| is above rtol, the correction series and X += e in FP64.
+// |F(X) - X| / |X| (X in FP64, double-single sums) is above rtol, the
+// correction series e = r + (F(e) - F(0)) and X += e in FP64.  (Chebyshev
+// steps on a real interval, as the node form's refinements take, diverge
+// here: the arrival-direction memory gives A a spectrum well off the real
+// axis, and for a spectrum that fills a disk the plain series is the best
+// polynomial method.)
 constexpr int kAniMaxRefine = 8;
 template <typename T>
 tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_iter, tursca_solve_info *info) {
     const tk::GridC g = grid_c(sc);
     const tk::FieldP<T> f = field_p<T>(sc);
-    const size_t nx = ((size_t)g.nd + g.ngd) * g.n_nodes;
+    const int ldx = ani_ldx(g);
+    const size_t nx = ((size_t)g.nd + g.ngd) * ldx;
     T *X = (T *)sc->ani_X, *Xn = (T *)sc->ani_Xn;
     CK(cudaMemsetAsync(X, 0, nx * sizeof(T), sc->st), "memset X");
     const double tol = sizeof(T) == 8 ? rtol : std::max(rtol, 1e-6);
@@ -1448,17 +1473,15 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
     total = terms;
     bool converged = rel <= tol;
     if constexpr (sizeof(T) == 4) {
-        // FP32 refinement with the FP64 residual
         e = ensure_aniso_refine(sc);
         if (e) return e;
-        const tk::GridC gg = grid_c(sc);
         const tk::GraphP gp = graph_p(sc);
         const tk::ViewC vc = view_c(sc);
         const tk::AniP<float> a = ani_p<float>(sc);
         tk::launch_aniso_update(sc->st, (long long)nx, xi ? Xn : X, sc->ani_X64, true);
         converged = false;
         while (refinements < kAniMaxRefine) {
-            tk::launch_aniso_resid(sc->st, gg, gp, f, vc, a, sc->ani_X64, sc->ani_L64, sc->ani_r, &sc->launches);
+            tk::launch_aniso_resid(sc->st, g, gp, f, vc, a, sc->ani_X64, sc->ani_L64, sc->ani_r, &sc->launches);
             sc->launches++;
             double acc[3];
             CK(cudaGetLastError(), "aniso residual launch");
@@ -1483,10 +1506,10 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
             total += et;
             tk::launch_aniso_update(sc->st, (long long)nx, ei ? (float *)Xn : sc->ani_E, sc->ani_X64, false);
         }
-        tk::launch_aniso_finish<float, double>(sc->st, gg, f, sc->ani_X64, sc->x64, (float *)sc->emis,
+        tk::launch_aniso_finish<float, double>(sc->st, g, f, sc->ani_X64, ldx, sc->x64, (float *)sc->emis,
                                                &sc->launches);
     } else {
-        tk::launch_aniso_finish<T, T>(sc->st, g, f, xi ? Xn : X, sc->x64, (T *)sc->emis, &sc->launches);
+        tk::launch_aniso_finish<T, T>(sc->st, g, f, xi ? Xn : X, ldx, sc->x64, (T *)sc->emis, &sc->launches);
     }
     CK(cudaGetLastError(), "aniso launch");
     if (solver == TURSCA_SOLVER_AUTO)
@@ -1751,9 +1774,12 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
         // direction
         {
             const int ndh = (int)G.uhat.size(), nin = ndh + (int)G.gdirs.size();
-            std::vector<int> perm(as.size()), segs((size_t)(sc->d.nz + 1) * (nin + 1));
+            std::vector<int4> perm(as.size());
+            std::vector<int> segs((size_t)(sc->d.nz + 1) * (nin + 1));
+            sc->ani_max_nt = 0;
             for (int z = 0; z <= sc->d.nz; ++z) {
                 const int t0 = G.tmpl_start[z], nt = G.tmpl_start[z + 1] - t0;
+                sc->ani_max_nt = std::max(sc->ani_max_nt, nt);
                 std::vector<int> cnt(nin + 1, 0);
                 for (int t = 0; t < nt; ++t) {
                     const tk::ASlot &d = as[t0 + t];
@@ -1766,10 +1792,10 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
                 for (int t = 0; t < nt; ++t) {
                     const tk::ASlot &d = as[t0 + t];
                     const int din = ((d.bits >> 11) & 1) ? ndh + d.dir : d.dir;
-                    perm[t0 + cnt[din]++] = t;
+                    perm[t0 + cnt[din]++] = make_int4(t, d.src, d.dir, 0);
                 }
             }
-            CK(upload(sc, sc->allocs, sc->ani_tperm, perm.data(), perm.size() * sizeof(int)), "upload order");
+            CK(upload(sc, sc->allocs, sc->ani_tslot, perm.data(), perm.size() * sizeof(int4)), "upload order");
             CK(upload(sc, sc->allocs, sc->ani_tseg, segs.data(), segs.size() * sizeof(int)), "upload order");
         }
         if (th.empty()) th.push_back(0);
@@ -2388,8 +2414,17 @@ tursca_status tursca_selftest_aniso_contract(tursca_scene *sc, int which, int te
         return fail(sc, TURSCA_E_STATE, "no tensor-core operands");
     tk::AniP<float> a = ani_p<float>(sc);
     a.mma = tensor_cores ? 1 : 0;
-    tk::launch_aniso_contract_test(sc->st, grid_c(sc), graph_p(sc), field_p<float>(sc), a, (const float *)X,
-                                   (float *)out, which, tensor_cores != 0);
+    const tk::GridC g = grid_c(sc);
+    float *Xs = nullptr;
+    if (which == 0) {  // X with the internal row stride, in the scene's X buffer
+        Xs = (float *)sc->ani_X;
+        CK(cudaMemcpy2DAsync(Xs, (size_t)a.ldx * sizeof(float), X, (size_t)g.n_nodes * sizeof(float),
+                             (size_t)g.n_nodes * sizeof(float), (size_t)g.nd + g.ngd, cudaMemcpyDeviceToDevice, sc->st),
+           "copy X");
+    }
+    CK(tk::launch_aniso_contract_test(sc->st, g, graph_p(sc), field_p<float>(sc), a, Xs, (float *)out, which,
+                                      tensor_cores != 0),
+       "contraction");
     CK(cudaGetLastError(), "contraction launch");
     return sync_check(sc, "contraction");
 }

@@ -6,11 +6,14 @@
 // transport pass reads it at the source-relative positions of the slot
 // descriptors, and val holds the raw deposit fractions P in K's slot-major
 // layout.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "aniso.h"
 #include "aniso_contract.cuh"
@@ -148,17 +151,31 @@ __global__ void k_aniso_couple(GridC g, GraphP gp, FieldP<T> f, ViewC vc, AniP<T
 }
 
 // Leaving power of the ground (Lambertian) nodes: the total X times the
-// ground weights, plus Lsun where `sun` is set
+// ground weights (the G of the folded form; their Cf is 1), plus Lsun where
+// `sun` is set.  Block = 32 ground nodes x 8 warps: the warps sum
+// interleaved arrival directions, then write interleaved ground directions
+// (a warp's 32 nodes are adjacent).
 template <typename T, typename XT, typename LT>
-__global__ void k_ani_ground(GridC g, AniP<T> a, const XT *__restrict__ X, LT *Lh, int sun, const int *ctl) {
+__global__ void __launch_bounds__(256) k_ani_ground(GridC g, AniP<T> a, const XT *__restrict__ X, LT *Lh, int sun,
+                                                    const int *ctl) {
+    __shared__ XT part[8][33];
     if (ctl && *(volatile const int *)ctl) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.n_ground) return;
-    const int j = g.n_atm + c, y = c / g.nx, x = c - y * g.nx;
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool ok = c < g.n_ground;
+    const int j = g.n_atm + c;
     const int nin = g.nd + g.ngd;
+    XT s = XT(0);
+    if (ok)
+        for (int w = wv; w < nin; w += 8) s += X[(size_t)w * a.ldx + j];
+    part[wv][lane] = s;
+    __syncthreads();
+    if (!ok) return;
     XT xt = XT(0);
-    for (int w = 0; w < nin; ++w) xt += X[(size_t)w * g.n_nodes + j];
-    for (int k = 0; k < g.ngd; ++k) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xt += part[i][lane];
+    const int y = c / g.nx, x = c - y * g.nx;
+    for (int k = wv; k < g.ngd; k += 8) {
         LT l = (LT)xt * (LT)a.Wg[(size_t)c * g.ngd + k];
         if (sun) l += (LT)a.LsT[(size_t)k * g.n_nodes + j];
         store_halo(Lh + (size_t)k * g.npad, g, x, y, g.nz, l);
@@ -173,17 +190,28 @@ __global__ void k_ani_ground(GridC g, AniP<T> a, const XT *__restrict__ X, LT *L
 //   MODE 1: Xn = rho sum P L64 - X64 (FP64 sums, the residual stored in FP32)
 // Per-block sums of the squared change (residual) and of the squares of Xn
 // (X64) go to a.part.
-constexpr int kAniW = 4;
+// The layer's slot order and direction runs are staged in shared memory
+// first (dynamic: a.max_nt int4 then nin + 1 ints).
+constexpr int kAniW = 8;
+//   Pv: the deposit fractions (P' of the folded form, or P); bsrc, radd:
+//   added to Xn where not null; Xold null: no change sums (d2 = 0)
 template <typename T, int MODE, typename LT, typename XT>
 __global__ void __launch_bounds__(32 * kAniW) k_ani_transport(GridC g, GraphP gp, FieldP<T> f, ViewC vc, AniP<T> a,
-                                                              const LT *__restrict__ Lh,
+                                                              const T *__restrict__ Pv, const LT *__restrict__ Lh,
                                                               const XT *__restrict__ Xold, T *Xn,
-                                                              const T *__restrict__ radd) {
+                                                              const T *__restrict__ radd,
+                                                              const T *__restrict__ bsrc) {
     __shared__ double red[2][kAniW];
+    extern __shared__ int4 tsm[];
     if (MODE == 0 && *(volatile const int *)a.ctl) return;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nin = g.nd + g.ngd;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
+    int4 *slots = tsm;
+    int *seg = (int *)(tsm + a.max_nt);
+    for (int i = threadIdx.x; i < G.nt; i += blockDim.x) slots[i] = __ldg(a.tslot + G.t0 + i);
+    for (int i = threadIdx.x; i <= nin; i += blockDim.x) seg[i] = __ldg(a.tseg + (size_t)G.z * (nin + 1) + i);
+    __syncthreads();
     const bool ground_row = G.z == g.nz;
     T rho[4];
 #pragma unroll
@@ -197,20 +225,19 @@ __global__ void __launch_bounds__(32 * kAniW) k_ani_transport(GridC g, GraphP gp
             rho[k] = (T)vc.albedo;
         }
     }
-    const T *vrow = f.val + G.vb + 4 * lane;
-    const int *perm = a.tperm + G.t0;
-    const int *seg = a.tseg + (size_t)G.z * (nin + 1);
-    double d2 = 0.0, n2 = 0.0;
+    const T *vrow = Pv + G.vb + 4 * lane;
+    // the change sums: per thread in the accumulation type of the term (the
+    // stopping test needs no more; FP64 arithmetic is slow on this part)
+    using D = typename std::conditional<MODE == 0, T, double>::type;
+    D d2 = D(0), n2 = D(0);
     for (int d = w; d < nin; d += kAniW) {
-        const int e0 = __ldg(seg + d), e1 = __ldg(seg + d + 1);
+        const int e0 = seg[d], e1 = seg[d + 1];
         LT acc[4] = {LT(0), LT(0), LT(0), LT(0)};
         for (int e = e0; e < e1; ++e) {
-            const int t = __ldg(perm + e);
-            const ASlot &sd = gp.aslot[G.t0 + t];
-            const int src = __ldg(&sd.src), dir = __ldg(&sd.dir);
+            const int4 sl = slots[e];  // {t, src, dir, 0}
             T P[4];
-            ld_quad(vrow + (size_t)t * kGroup, P);
-            const LT *Ld = Lh + (size_t)dir * g.npad + src;
+            ld_quad(vrow + (size_t)sl.x * kGroup, P);
+            const LT *Ld = Lh + (size_t)sl.z * g.npad + sl.y;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (G.row[k] >= 0) acc[k] += (LT)P[k] * __ldg(Ld + G.rp[k]);
@@ -218,14 +245,15 @@ __global__ void __launch_bounds__(32 * kAniW) k_ani_transport(GridC g, GraphP gp
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (G.row[k] < 0) continue;
-            const size_t q = (size_t)d * g.n_nodes + G.row[k];
+            const size_t q = (size_t)d * a.ldx + G.row[k];
             if constexpr (MODE == 0) {
                 T xn = rho[k] * (T)acc[k];
                 if (radd) xn += radd[q];
-                const double dx = (double)xn - (double)Xold[q];
+                if (bsrc) xn += bsrc[q];
+                const T dx = Xold ? xn - Xold[q] : T(0);
                 Xn[q] = xn;
                 d2 += dx * dx;
-                n2 += (double)xn * (double)xn;
+                n2 += xn * xn;
             } else {
                 const double xo = (double)Xold[q];
                 const double r = (double)rho[k] * (double)acc[k] - xo;
@@ -235,13 +263,14 @@ __global__ void __launch_bounds__(32 * kAniW) k_ani_transport(GridC g, GraphP gp
             }
         }
     }
+    double d2d = (double)d2, n2d = (double)n2;
     for (int o = 16; o > 0; o >>= 1) {
-        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        d2d += __shfl_xor_sync(0xffffffffu, d2d, o);
+        n2d += __shfl_xor_sync(0xffffffffu, n2d, o);
     }
     if (lane == 0) {
-        red[0][w] = d2;
-        red[1][w] = n2;
+        red[0][w] = d2d;
+        red[1][w] = n2d;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -252,6 +281,74 @@ __global__ void __launch_bounds__(32 * kAniW) k_ani_transport(GridC g, GraphP gp
         }
         a.part[2 * (size_t)blockIdx.x] = s0;
         a.part[2 * (size_t)blockIdx.x + 1] = s1;
+    }
+}
+
+// Haloed planes of the routing coupling Cf (C where the routing applies and
+// the chain has a receiver, else 1; ground sources 1) and of Lsun.
+template <typename T>
+__global__ void k_ani_planes(GridC g, GraphP gp, AniP<T> a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_nodes) return;
+    const int z = j / g.nxy, r = j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    if (j < g.n_atm) {
+        const bool routed = a.on[j] > T(0);
+        for (int u = 0; u < g.nd; ++u) {
+            const bool has = z + gp.dirs[u].z < g.nz;
+            const T cf = (routed && has) ? a.CT[(size_t)u * g.n_atm + j] : T(1);
+            store_halo(a.CfH + (size_t)u * g.npad, g, x, y, z, cf);
+            store_halo(a.Lh + (size_t)u * g.npad, g, x, y, z, a.LsT[(size_t)u * g.n_nodes + j]);
+        }
+    } else {
+        for (int k = 0; k < g.ngd; ++k) {
+            store_halo(a.CfH + (size_t)k * g.npad, g, x, y, z, T(1));
+            store_halo(a.Lh + (size_t)k * g.npad, g, x, y, z, a.LsT[(size_t)k * g.n_nodes + j]);
+        }
+    }
+}
+
+// P' = P Cf(src, dir) for every slot, in K's value layout (block = one
+// group of 128 rows, as the transport walks them)
+template <typename T>
+__global__ void __launch_bounds__(128) k_ani_pc(GridC g, GraphP gp, FieldP<T> f, AniP<T> a) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const GroupRows G = group_rows(g, gp, blockIdx.x);
+    for (int t = w; t < G.nt; t += 4) {
+        const ASlot &sd = gp.aslot[G.t0 + t];
+        const int src = __ldg(&sd.src), dir = __ldg(&sd.dir);
+        const size_t v0 = (size_t)G.vb + (size_t)t * kGroup + 4 * lane;
+        const T *cf = a.CfH + (size_t)dir * g.npad + src;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a.Pc[v0 + k] = G.row[k] >= 0 ? f.val[v0 + k] * __ldg(cf + G.rp[k]) : T(0);
+    }
+}
+
+// The periodic halo of planes [nplanes][npad] on the atmospheric layers:
+// every border cell (width H in x and y) copies its interior cell.
+template <typename T>
+__global__ void k_ani_halo(GridC g, T *planes, int nplanes, const int *ctl) {
+    if (ctl && *(volatile const int *)ctl) return;
+    const int H = g.H, nxp = g.nxp;
+    const int per_layer = 2 * H * nxp + 2 * H * g.ny;
+    const long long total = (long long)nplanes * g.nz * per_layer;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % per_layer);
+        const long long pz = idx / per_layer;
+        const int z = (int)(pz % g.nz), pl = (int)(pz / g.nz);
+        int xh, yh;
+        if (c < 2 * H * nxp) {  // the H rows below and above the interior
+            const int r = c / nxp;
+            xh = c - r * nxp;
+            yh = r < H ? r : g.ny + r;
+        } else {  // the H columns left and right of the interior rows
+            const int c2 = c - 2 * H * nxp, r = c2 / (2 * H), k = c2 - r * 2 * H;
+            yh = H + r;
+            xh = k < H ? k : g.nx + k;
+        }
+        const int x = wrap_small(xh - H, g.nx), y = wrap_small(yh - H, g.ny);
+        T *p = planes + (size_t)pl * g.npad + (size_t)z * g.lp;
+        p[(size_t)yh * nxp + xh] = p[(size_t)(y + H) * nxp + x + H];
     }
 }
 
@@ -296,13 +393,13 @@ __global__ void k_ani_update(long long n, const float *e, double *X64, int init)
 // x = sum_w X(i, w) into the FP64 haloed vector, and the emission toward the
 // instrument E_i = e1_i Theta_i(s0 . v) + sum_w Theta_i(w . v) X(i, w)
 template <typename T, typename XT>
-__global__ void k_aniso_finish(GridC g, FieldP<T> f, const XT *__restrict__ X, double *x64, T *emis) {
+__global__ void k_aniso_finish(GridC g, FieldP<T> f, const XT *__restrict__ X, int ldx, double *x64, T *emis) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_nodes) return;
     const int nin = g.nd + g.ngd;
     const int z = i / g.nxy, r = i - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
     double xt = 0.0;
-    for (int wv = 0; wv < nin; ++wv) xt += (double)X[(size_t)wv * g.n_nodes + i];
+    for (int wv = 0; wv < nin; ++wv) xt += (double)X[(size_t)wv * ldx + i];
     store_halo(x64, g, x, y, z, xt);
     if (i >= g.n_atm) return;
     double w[MAX_SPECIES];
@@ -313,7 +410,7 @@ __global__ void k_aniso_finish(GridC g, FieldP<T> f, const XT *__restrict__ X, d
     }
     double e = 0;
     for (int wv = 0; wv < nin; ++wv) {
-        const double xw = (double)X[(size_t)wv * g.n_nodes + i];
+        const double xw = (double)X[(size_t)wv * ldx + i];
         if (xw == 0.0) continue;
         double th = 0;
         for (int sp = 0; sp < g.S; ++sp) th += w[sp] * (double)f.hgv[sp * nin + wv];
@@ -325,12 +422,46 @@ __global__ void k_aniso_finish(GridC g, FieldP<T> f, const XT *__restrict__ X, d
 // ---- launchers ----
 namespace {
 
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link to
+// the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// a [rows][ld] FP32 array as a 2-D tensor map of n_inner x rows, boxes of
+// 128 x kAniRows, zero beyond the array
+bool rows_map(CUtensorMap &m, const float *base, int n_inner, int ld, int rows) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (ld % 4) || ((uintptr_t)base % 16)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)n_inner, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kAniTileM, (cuuint32_t)kAniRows};
+    const cuuint32_t es[2] = {1, 1};
+    return enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // tensor-core launch of the leave contraction: N padded to one of a few
-// tile widths (N <= 128), S <= MAX_SPECIES
+// tile widths (N <= 128), S <= MAX_SPECIES.  cudaErrorInvalidValue when the
+// tensor maps of X and zf cannot be made.
 template <class Op>
-void mma_leave(cudaStream_t st, const Op &op, int S, int R, int N, const float *B, const int *ctl, int *status) {
+cudaError_t mma_leave(cudaStream_t st, const Op &op, int S, int R, int N, const float *B, const int *ctl,
+                      int *status) {
+    CUtensorMap mx, mz;
+    if (!rows_map(mx, op.X, op.g.n_atm, op.ldx, R) || !rows_map(mz, op.zf, op.g.n_atm, op.ldz, R))
+        return cudaErrorInvalidValue;
     const int np = ani_leave_np(N, S);
-#define TK_L(SS, NN) ani_mma_launch<SS, NN, Op>(st, op, R, N, B, ctl, status)
+#define TK_L(SS, NN) ani_mma_launch<SS, NN, Op>(st, op, R, N, B, mx, mz, ctl, status)
     if (S == 1) {
         if (np == 32) TK_L(1, 32); else if (np == 64) TK_L(1, 64); else if (np == 112) TK_L(1, 112); else TK_L(1, 128);
     } else if (S == 2) {
@@ -341,6 +472,7 @@ void mma_leave(cudaStream_t st, const Op &op, int S, int R, int N, const float *
         TK_L(4, 128);
     }
 #undef TK_L
+    return cudaSuccess;
 }
 
 // first node of the layers from which some direction has no receiver
@@ -348,12 +480,17 @@ void mma_leave(cudaStream_t st, const Op &op, int S, int R, int N, const float *
 inline int top_begin(const GridC &g) { return std::max(0, g.nz - g.R) * g.nxy; }
 
 template <typename T>
-LeaveOp<T, T, T> leave_op(const GridC &g, const GraphP &gp, const AniP<T> &a, const T *wsp, const T *X, int sun,
-                          int top) {
-    LeaveOp<T, T, T> op;
+size_t transport_smem(const GridC &g, const AniP<T> &a) {
+    return (size_t)a.max_nt * sizeof(int4) + (size_t)(g.nd + g.ngd + 1) * sizeof(int);
+}
+
+// the leave contraction; with_top adds the top layers' tiles
+template <typename T>
+LeaveOp<T, T, T, true> leave_op(const GridC &g, const GraphP &gp, const AniP<T> &a, const T *wsp, const T *X, int sun,
+                                bool with_top) {
+    LeaveOp<T, T, T, true> op;
     op.g = g;
-    op.jbeg = top ? top_begin(g) : 0;
-    op.top = top;
+    op.jtop = with_top ? top_begin(g) / kAniTileM * kAniTileM : g.n_atm;  // tiles start on 128 nodes
     op.dirs = gp.dirs;
     op.zf = a.zf;
     op.wsp = wsp;
@@ -364,30 +501,34 @@ LeaveOp<T, T, T> leave_op(const GridC &g, const GraphP &gp, const AniP<T> &a, co
     op.X = X;
     op.Lh = a.Lh;
     op.sun = sun;
+    op.ldx = a.ldx;
+    op.ldz = a.ldz;
     return op;
 }
 template <typename T>
 SqcOp<T> sqc_op(const GridC &g, const AniP<T> &a, const T *wsp) {
     SqcOp<T> op;
     op.g = g;
-    op.jbeg = 0;
+    op.jtop = g.n_atm;
     op.CT = a.CT;
     op.wsp = wsp;
     op.on = a.on;
     op.SQ = a.SQ;
     op.Q = a.Q;
     op.zf = a.zf;
+    op.ldz = a.ldz;
     return op;
 }
 
 // the contractions with their raw outputs out[n][n_atm] (tests)
 template <class Base>
 struct RawOp : Base {
+    static constexpr bool kBatched = false;
     float *raw;
     struct Pre {};
     __device__ __forceinline__ Pre pre(int) const { return Pre{}; }
     template <typename V>
-    __device__ __forceinline__ void out(const Pre &, int j, int n, V val) const {
+    __device__ __forceinline__ void out(const Pre &, int j, int n, V val, bool) const {
         raw[(size_t)n * this->g.n_atm + j] = (float)val;
     }
 };
@@ -406,10 +547,17 @@ void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const 
     // the routing denominators on the CUDA cores: zf is part of the operator
     // the FP64 residual refines against, so it keeps FP32 sums
     ani_simt_launch<T, 0>(st, sqc_op<T>(g, a, f.wsp), g.S, g.nd, nin, nullptr);
-    if (launches) *launches += 5;
+    // the folded form: Cf and Lsun planes, P' = P Cf, b = rho T Lsun
+    const int nblk = (g.nz + 1) * g.gpl;
+    cudaMemsetAsync(a.ctl, 0, 2 * sizeof(int), st);  // the transport below must not see a converged flag
+    k_ani_planes<T><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, gp, a);
+    k_ani_pc<T><<<nblk, 128, 0, st>>>(g, gp, f, a);
+    k_ani_transport<T, 0, T, T><<<nblk, 32 * kAniW, transport_smem(g, a), st>>>(g, gp, f, vc, a, f.val, a.Lh, nullptr,
+                                                                                  a.b, nullptr, nullptr);
+    if (launches) *launches += 8;
     if constexpr (sizeof(T) == 4) {
         if (a.mma) {
-            const LeaveOp<T, T, T> lop = leave_op<T>(g, gp, a, f.wsp, nullptr, 1, 0);
+            const LeaveOp<T, T, T, true> lop = leave_op<T>(g, gp, a, f.wsp, nullptr, 0, false);
             k_ani_pack<<<256, 256, 0, st>>>(lop, g.S, nin, g.nd, ani_leave_np(g.nd, g.S), a.Bl);
             if (launches) *launches += 1;
         }
@@ -417,40 +565,38 @@ void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const 
 }
 
 template <typename T>
-void launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                       const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
-                       long long *launches) {
+cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                              const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
+                              long long *launches) {
     const int nin = g.nd + g.ngd;
-    const LeaveOp<T, T, T> lop = leave_op<T>(g, gp, a, f.wsp, X, sun ? 1 : 0, 0);
-    const LeaveOp<T, T, T> top = leave_op<T>(g, gp, a, f.wsp, X, sun ? 1 : 0, 1);
+    const LeaveOp<T, T, T, true> lop = leave_op<T>(g, gp, a, f.wsp, X, 0, true);
     bool done = false;
     if constexpr (sizeof(T) == 4) {
         if (a.mma) {
-            mma_leave(st, lop, g.S, nin, g.nd, a.Bl, a.ctl, f.status);
-            mma_leave(st, top, g.S, nin, g.nd, a.Bl, a.ctl, f.status);
+            const cudaError_t e = mma_leave(st, lop, g.S, nin, g.nd, a.Bl, a.ctl, f.status);
+            if (e != cudaSuccess) return e;
             done = true;
         }
     }
-    if (!done) {
-        ani_simt_launch<T, 0>(st, lop, g.S, nin, g.nd, a.ctl);
-        ani_simt_launch<T, 0>(st, top, g.S, nin, g.nd, a.ctl);
-    }
+    if (!done) ani_simt_launch<T, 0>(st, lop, g.S, nin, g.nd, a.ctl);
+    k_ani_halo<T><<<1216, 256, 0, st>>>(g, a.Lh, g.nd, a.ctl);
     if (g.n_ground > 0)
-        k_ani_ground<T, T, T><<<(g.n_ground + 127) / 128, 128, 0, st>>>(g, a, X, a.Lh, sun ? 1 : 0, a.ctl);
+        k_ani_ground<T, T, T><<<(g.n_ground + 31) / 32, 256, 0, st>>>(g, a, X, a.Lh, 0, a.ctl);
     const int nblk = (g.nz + 1) * g.gpl;
-    k_ani_transport<T, 0, T, T><<<nblk, 32 * kAniW, 0, st>>>(g, gp, f, vc, a, a.Lh, X, Xn, radd);
+    k_ani_transport<T, 0, T, T><<<nblk, 32 * kAniW, transport_smem(g, a), st>>>(g, gp, f, vc, a, a.Pc, a.Lh, X, Xn, radd,
+                                                                                  sun ? a.b : nullptr);
     k_ani_check<<<1, 256, 0, st>>>(a.part, nblk, a.acc, a.ctl, tol, term, 1);
     if (launches) *launches += g.n_ground > 0 ? 5 : 4;
+    return cudaSuccess;
 }
 
 void launch_aniso_resid(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
                         const ViewC &vc, const AniP<float> &a, const double *X64, double *L64, float *r,
                         long long *launches) {
     const int nin = g.nd + g.ngd;
-    LeaveOp<float, double, double> op;
+    LeaveOp<float, double, double, false> op;
     op.g = g;
-    op.jbeg = 0;
-    op.top = 0;
+    op.jtop = top_begin(g) / kAniTileM * kAniTileM;
     op.dirs = gp.dirs;
     op.zf = a.zf;
     op.wsp = f.wsp;
@@ -461,16 +607,16 @@ void launch_aniso_resid(cudaStream_t st, const GridC &g, const GraphP &gp, const
     op.X = X64;
     op.Lh = L64;
     op.sun = 1;
-    ani_simt_launch<float, 1>(st, op, g.S, nin, g.nd, nullptr);
-    op.top = 1;
-    op.jbeg = top_begin(g);
+    op.ldx = a.ldx;
+    op.ldz = a.ldz;
     ani_simt_launch<float, 1>(st, op, g.S, nin, g.nd, nullptr);
     if (g.n_ground > 0)
-        k_ani_ground<float, double, double><<<(g.n_ground + 127) / 128, 128, 0, st>>>(g, a, X64, L64, 1, nullptr);
+        k_ani_ground<float, double, double><<<(g.n_ground + 31) / 32, 256, 0, st>>>(g, a, X64, L64, 1, nullptr);
     const int nblk = (g.nz + 1) * g.gpl;
-    k_ani_transport<float, 1, double, double><<<nblk, 32 * kAniW, 0, st>>>(g, gp, f, vc, a, L64, X64, r, nullptr);
+    k_ani_transport<float, 1, double, double><<<nblk, 32 * kAniW, transport_smem(g, a), st>>>(
+        g, gp, f, vc, a, f.val, L64, X64, r, nullptr, nullptr);
     k_ani_check<<<1, 256, 0, st>>>(a.part, nblk, a.acc, a.ctl, 0.0, 0, 0);
-    if (launches) *launches += g.n_ground > 0 ? 5 : 4;
+    if (launches) *launches += g.n_ground > 0 ? 4 : 3;
 }
 
 void launch_aniso_update(cudaStream_t st, long long n, const float *e, double *X64, bool init) {
@@ -478,41 +624,42 @@ void launch_aniso_update(cudaStream_t st, long long n, const float *e, double *X
 }
 
 template <typename T, typename XT>
-void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, double *x64, T *emis,
-                         long long *launches) {
-    k_aniso_finish<T, XT><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, f, X, x64, emis);
+void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, int ldx, double *x64,
+                         T *emis, long long *launches) {
+    k_aniso_finish<T, XT><<<(g.n_nodes + 127) / 128, 128, 0, st>>>(g, f, X, ldx, x64, emis);
     if (launches) *launches += 1;
 }
 
-void launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
-                                const AniP<float> &a, const float *X, float *out, int which, bool mma) {
+cudaError_t launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
+                                       const AniP<float> &a, const float *X, float *out, int which, bool mma) {
     const int nin = g.nd + g.ngd;
     if (which == 0) {
-        RawOp<LeaveOp<float, float, float>> op;
-        static_cast<LeaveOp<float, float, float> &>(op) = leave_op<float>(g, gp, a, f.wsp, X, 0, 0);
+        RawOp<LeaveOp<float, float, float, true>> op;
+        static_cast<LeaveOp<float, float, float, true> &>(op) = leave_op<float>(g, gp, a, f.wsp, X, 0, false);
         op.raw = out;
-        if (mma) mma_leave(st, op, g.S, nin, g.nd, a.Bl, nullptr, f.status);
-        else ani_simt_launch<float, 0>(st, op, g.S, nin, g.nd, nullptr);
+        if (mma) return mma_leave(st, op, g.S, nin, g.nd, a.Bl, nullptr, f.status);
+        ani_simt_launch<float, 0>(st, op, g.S, nin, g.nd, nullptr);
     } else {
         RawOp<SqcOp<float>> op;
         static_cast<SqcOp<float> &>(op) = sqc_op<float>(g, a, f.wsp);
         op.raw = out;
         ani_simt_launch<float, 0>(st, op, g.S, g.nd, nin, nullptr);
     }
+    return cudaSuccess;
 }
 
 #define INST(T)                                                                                                 \
     template void launch_aniso_prep<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
                                        const ViewC &, const ViewP &, const AniP<T> &, long long *);             \
-    template void launch_aniso_term<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
+    template cudaError_t launch_aniso_term<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,   \
                                        const ViewC &, const AniP<T> &, const T *, T *, const T *, bool, double, \
                                        int, long long *);                                                       \
-    template void launch_aniso_finish<T, T>(cudaStream_t, const GridC &, const FieldP<T> &, const T *,          \
+    template void launch_aniso_finish<T, T>(cudaStream_t, const GridC &, const FieldP<T> &, const T *, int,     \
                                             double *, T *, long long *);
 INST(float)
 INST(double)
 #undef INST
 template void launch_aniso_finish<float, double>(cudaStream_t, const GridC &, const FieldP<float> &,
-                                                 const double *, double *, float *, long long *);
+                                                 const double *, int, double *, float *, long long *);
 
 }  // namespace tk
