@@ -50,9 +50,9 @@
 // The series of Eq. fs_sum is iterated until the relative change of X is at
 // most the tolerance; the stopping test runs on the device and the host
 // reads it every few terms.  FP32 scenes then refine: the residual
-// r = F(X) - X of the fixed point X = F(X) is evaluated with X in FP64 and
-// every product accumulated in double-single (FP32 pairs), and the FP32
-// series solves e = r + (F(e) - F(0)) for the correction, X += e in FP64.
+// r = F(X) - X of the fixed point X = F(X) is evaluated with X and every
+// sum in double-single (FP32 pairs, about 48 bits), and the FP32 series
+// solves e = r + (F(e) - F(0)) for the correction, X += e in pairs.
 #pragma once
 
 #include "kern.h"
@@ -80,6 +80,8 @@ struct AniP {
                     // ground sources 1), haloed planes
     T *Pc;          // per slot (K's value layout) the deposit fraction times its chain's Cf: P Cf(src, dir)
     T *b;           // [nin][ldx] first-order term rho T Lsun (the series' source)
+    T *xtg;         // [n_ground] sum over the arrival directions of the current X (ground nodes)
+    T *xtb;         // [n_ground] the same for b (the series' first term)
     const int4 *tslot; // per layer template: its slots in order of arrival direction, {t, src, dir, 0}
                        // (t: template-local index, src and dir as in the slot descriptor)
     const int *tseg;   // [nz + 1][nin + 1] start of each arrival direction's run in tslot
@@ -89,8 +91,11 @@ struct AniP {
     int ldz;           // row stride of zf: n_atm rounded up to 32
     double *part;   // [transport blocks][2] partial sums of the change of a term
     double *acc;    // [3] sum of squared changes, of squares, relative change of the last checked term
-    int *ctl;       // [2] converged flag, terms taken when it was set
+    int *ctl;       // [3] converged flag, terms taken when it was set, blocks of the running transport done
     float *Bl;      // tensor-core operand of the leave contraction (FP32 scenes), split high / low
+    float2 *Ads;    // FP32 residual: A split in FP32 pairs, [ani_ds_kp][ldz]
+    float2 *Atop;   // the same for the top layers' tiles (A without zf), [ani_ds_kp][ani_ds_ldt]
+    float *Bds;     // FP32 residual: B padded to [ani_ds_kp][128]
     int mma;        // 1: contractions on the tensor cores (FP32 scenes)
 };
 
@@ -104,6 +109,10 @@ __host__ __device__ constexpr int ani_leave_np(int N, int S) {
     return S >= 3 ? 128 : N <= 32 ? 32 : N <= 64 ? 64 : N <= 112 ? 112 : 128;
 }
 __host__ __device__ constexpr int ani_chunks(int rows) { return (rows + kAniRows - 1) / kAniRows; }
+// the FP32 residual's contraction: K padded to 16, the top layers' row
+// stride (nodes from the first top tile, rounded up to 64)
+inline int ani_ds_kp(int nin, int S) { return (nin * S + 15) / 16 * 16; }
+inline int ani_ds_ldt(const GridC &g, int jtop) { return (g.n_atm - jtop + 63) / 64 * 64; }
 // floats of a packed operand of `rows` K rows, tile width np
 inline size_t ani_btab_floats(int rows, int np, int S) {
     return (size_t)ani_chunks(rows) * 2 * np * kAniRows * S;
@@ -111,21 +120,25 @@ inline size_t ani_btab_floats(int rows, int np, int S) {
 
 // Per assembly: the edge kernel writes the raw deposit fraction P of every
 // slot into val (instead of K); then couplings, first-order leaving power,
-// ground weights, the quadrature tables, the routing factors zf and the
-// tensor-core operands.
+// ground weights, the routing factors zf and the folded form; with `tables`
+// also the quadrature tables and the tensor-core operand (they depend on the
+// HG asymmetries and the graph only).
 template <typename T>
 void launch_assemble_rows_p(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
                             const ViewC &vc, long long *launches);
 template <typename T>
 void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                       const ViewP &vp, const AniP<T> &a, long long *launches);
+                       const ViewP &vp, const AniP<T> &a, bool tables, long long *launches);
 
-// X, Xn and radd below are [nin][ldx].
+// X, Xn and radd below are [nin][ldx].  a.xtg must hold the ground nodes'
+// sums of X over the arrival directions (zero for X = 0); the term leaves
+// those of Xn there (the residual pass those of r).
 // One term of the series, X -> L (haloed planes) -> Xn = radd + rho T L,
 // where L carries Lsun when `sun` is set and radd may be null; then the
 // change |Xn - X|^2, |Xn|^2 and the stopping test: the first term whose
 // relative change is at most tol sets a.ctl = {1, term}; every kernel of a
-// later term returns at once.  a.ctl must be zeroed before the first term.
+// later term returns at once.  a.ctl must be zeroed before the first term
+// (the transport's last block takes the test and resets its block count).
 // cudaErrorInvalidValue when the tensor-core kernel's tensor maps cannot be
 // made (nothing launched then).
 template <typename T>
@@ -133,14 +146,16 @@ cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp,
                               const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
                               long long *launches);
 
-// FP32 refinement.  The residual r = F(X64) - X64 (F with Lsun) with every
-// product accumulated in double-single, L64 the haloed FP64 planes
-// [nd][npad]; r is stored in FP32 and a.acc gets |r|^2, |X64|^2.
+// FP32 refinement, in double-single (FP32 pairs hi + lo, about 48 bits: the
+// arithmetic of FP64 on the FP32 units).  The residual r = F(X) - X (F with
+// Lsun) of X ([nin][ldx] pairs) with every product accumulated in pairs, L
+// the haloed planes [nd][npad] of pairs; r is stored rounded to FP32 and
+// a.acc gets |r|^2, |X|^2.
 void launch_aniso_resid(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
-                        const ViewC &vc, const AniP<float> &a, const double *X64, double *L64, float *r,
+                        const ViewC &vc, const AniP<float> &a, const float2 *X, float2 *L, float *r,
                         long long *launches);
-// X64 += e (init: X64 = e)
-void launch_aniso_update(cudaStream_t st, long long n, const float *e, double *X64, bool init);
+// X += e in pairs (init: X = e)
+void launch_aniso_update(cudaStream_t st, long long n, const float *e, float2 *X, bool init);
 // x (total scattered power, FP64 haloed, for the ground term of the pixels)
 // and the emission toward the instrument from X (type X of the unknowns).
 template <typename T, typename XT>

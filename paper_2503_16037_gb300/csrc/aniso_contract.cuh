@@ -26,8 +26,7 @@
 namespace tk {
 
 // L(u, j) = [Lsun(u, j)] + Cf(j, u) [A B](j, u) into the haloed planes, or
-// (BARE, the series' folded form) G(u, j) = [A B](j, u) at the interior
-// point.
+// (BARE, the series' folded form) G(u, j) = [A B](j, u).
 // With `top` set (a second pass over the layers from which some direction
 // has no receiver), A carries X without zf and only the directions without
 // a receiver are written, with the routing weight 1: their light still
@@ -79,8 +78,8 @@ struct LeaveOp {
         const bool has = p.z + __ldg(&dirs[n].z) < g.nz;
         if (top == has) return;
         LT l = (LT)val;
-        if constexpr (BARE) {  // the interior point only: a separate pass fills the halo
-            Lh[(size_t)n * g.npad + p.pos] = l;
+        if constexpr (BARE) {
+            store_halo(Lh + (size_t)n * g.npad, g, p.x, p.y, p.z, l);
         } else {
             const LT cf = (p.routed && has) ? (LT)__ldg(CT + (size_t)n * g.n_atm + j) : LT(1);
             l *= cf;
@@ -104,7 +103,7 @@ struct LeaveOp {
         if constexpr (BARE) {
 #pragma unroll
             for (int i = 0; i < K; ++i)
-                if (w[i]) Lh[(size_t)(n0 + i) * g.npad + p.pos] = (LT)val[i];
+                if (w[i]) store_halo(Lh + (size_t)(n0 + i) * g.npad, g, p.x, p.y, p.z, (LT)val[i]);
         } else {
             LT cf[K], ls[K];
 #pragma unroll
@@ -190,13 +189,16 @@ struct SqcOp {
 template <int S, int NP>
 struct MmaShape {
     static constexpr int KC = kAniRows * S;
-    static constexpr int NS = 2;  // A/B stages
     static constexpr int NR = 4;  // raw X / zf stages (tensor-map copies run this far ahead)
     static constexpr unsigned A_BYTES = 128u * KC * 4;
     static constexpr unsigned B_BYTES = (unsigned)NP * KC * 4;
     static constexpr unsigned STAGE = 2 * A_BYTES + 2 * B_BYTES;
     static constexpr unsigned RAW_HALF = kAniRows * 128u * 4;  // one box: kAniRows rows x 128 nodes
     static constexpr unsigned RAW = 2 * RAW_HALF;              // X, then zf
+    // A/B stages: as many as fit beside the raw ring in about 200 KB (up to
+    // 4), so that the MMAs' completion is rarely waited for
+    static constexpr int NS_FIT = (int)((200u * 1024u - NR * RAW) / STAGE);
+    static constexpr int NS = NS_FIT < 2 ? 2 : (NS_FIT > 4 ? 4 : NS_FIT);
     static constexpr unsigned RAW_OFF = NS * STAGE;
     static constexpr unsigned ACOLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : 256;
     static constexpr unsigned TCOLS = 2 * ACOLS;
@@ -257,28 +259,30 @@ __device__ __forceinline__ void bulk_copy(unsigned bar, unsigned dst, const void
 // Persistent, warp-specialised tensor-core contraction of the leave op (v =
 // zf X; top tiles: X).  Tiles of 128 nodes (the first ntop are the top
 // layers' tiles, from op.jtop, a multiple of 128) are dealt to the blocks
-// round robin.  Ten warps:
-//   9    its lane 0 copies each chunk's X and zf boxes (kAniRows rows x 128
+// round robin.  Fourteen warps (P = kMmaProducerWarps = 8):
+//   P+5  its lane 0 copies each chunk's X and zf boxes (kAniRows rows x 128
 //        nodes, tensor maps mx, mz; zero beyond the arrays) into the raw
 //        ring, up to NR chunks ahead
-//   0-3  producers: thread m owns row m of A; per K chunk it reads its raw
-//        values, releases the raw stage, waits for a free A/B stage, stores
-//        w v split in TF32 high and low parts in the core-matrix layout and
-//        arrives on the stage's full barrier (thread 0 first starts the copy
-//        of the chunk's packed B into the stage, counted in bytes on the
-//        same barrier)
-//   4-7  epilogue: drain one of the two tensor-memory accumulators (warp w
-//        reads lanes 32 (w % 4) ..) and write the outputs, then release it
-//   8    its lane 0 issues the 3 kc / 8 MMAs of each chunk once its stage is
+//   0..P-1  producers: threads m and m + 128 own row m of A, each half of
+//        the chunk's rows of v; per K chunk a thread reads its raw values,
+//        releases the raw stage, waits for a free A/B stage, stores w v split
+//        in TF32 high and low parts in the core-matrix layout and arrives on
+//        the stage's full barrier (thread 0 first starts the copy of the
+//        chunk's packed B into the stage, counted in bytes on the same
+//        barrier)
+//   P..P+3  epilogue: drain one of the two tensor-memory accumulators (warp
+//        w reads lanes 32 (w % 4) ..) and write the outputs, then release it
+//   P+4  its lane 0 issues the 3 kc / 8 MMAs of each chunk once its stage is
 //        full, commits them to the stage's empty barrier, and after a tile's
 //        last chunk to the accumulator's full barrier
 // Waits are bounded; after a timeout every wait that may return at once
 // does, no MMA is issued, every barrier still gets its arrivals, and the
 // block waits for its copies, frees its tensor memory and returns with
 // STATUS_TIMEOUT set.
-constexpr int kMmaThreads = 320;
+constexpr int kMmaProducerWarps = 8;  // two threads per row of A, each half of a chunk's rows of v
+constexpr int kMmaThreads = 32 * (kMmaProducerWarps + 6);
 template <int S, int NP, class Op>
-__global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N, int ntop, int ntiles,
+__global__ void __launch_bounds__(kMmaThreads, 1) k_ani_mma(Op op, int R, int N, int ntop, int ntiles,
                                                             const float *__restrict__ Btab,
                                                             const __grid_constant__ CUtensorMap mx,
                                                             const __grid_constant__ CUtensorMap mz, const int *ctl,
@@ -295,12 +299,12 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
     const int nch = ani_chunks(R);
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_addr(&full[s]), 128);
+            mbar_init(smem_addr(&full[s]), 32 * kMmaProducerWarps);
             mbar_init(smem_addr(&empty[s]), 1);
         }
         for (int s = 0; s < NR; ++s) {
             mbar_init(smem_addr(&rfull[s]), 1);
-            mbar_init(smem_addr(&rempty[s]), 128);
+            mbar_init(smem_addr(&rempty[s]), 32 * kMmaProducerWarps);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_addr(&accf[a]), 1);
@@ -320,12 +324,15 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
         top = t < ntop;
         return top ? op.jtop + t * kAniTileM : (t - ntop) * kAniTileM;
     };
-    if (warp < 4) {
-        // ---- producers ----
+    if (warp < kMmaProducerWarps) {
+        // ---- producers: thread (m, h) = (tid % 128, tid / 128) stages the
+        // K values of row m that come from rows h RH .. h RH + RH - 1 of v ----
+        constexpr int RH = kAniRows / 2, KH = RH * S;
+        const int m = tid & 127, h = tid >> 7;
         int q = 0;  // chunks staged by this block so far
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             bool top;
-            const int j = tile_j0(t, top) + tid;
+            const int j = tile_j0(t, top) + m;
             const bool valid = j < op.g.n_atm;
             float ws[S];
 #pragma unroll
@@ -333,10 +340,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
             for (int c = 0; c < nch; ++c, ++q) {
                 const int rs = q % NR, slot = q % NS;
                 spin_wait(smem_addr(&rfull[rs]), (unsigned)((q / NR) & 1), &abort_flag, status, true);
-                const float *rx = raw + rs * (Sh::RAW / 4), *rz = rx + Sh::RAW_HALF / 4;
-                float vc[kAniRows];
+                const float *rx = raw + rs * (Sh::RAW / 4) + h * RH * 128 + m, *rz = rx + Sh::RAW_HALF / 4;
+                float vc[RH];
 #pragma unroll
-                for (int i = 0; i < kAniRows; ++i) vc[i] = top ? rx[i * 128 + tid] : rz[i * 128 + tid] * rx[i * 128 + tid];
+                for (int i = 0; i < RH; ++i) vc[i] = top ? rx[i * 128] : rz[i * 128] * rx[i * 128];
                 mbar_arrive(smem_addr(&rempty[rs]));
                 const unsigned st = sbase + slot * Sh::STAGE;
                 spin_wait(smem_addr(&empty[slot]), (unsigned)(((q / NS) & 1) ^ 1), &abort_flag, status, true);
@@ -346,16 +353,16 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
                               2 * Sh::B_BYTES);
                 }
 #pragma unroll
-                for (int k4 = 0; k4 < KC / 4; ++k4) {
+                for (int k4 = 0; k4 < KH / 4; ++k4) {
                     float hi[4], lo[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int k = 4 * k4 + e;
+                        const int k = 4 * k4 + e;  // K index h KH + k of the chunk
                         const float a = ws[k % S] * vc[k / S];
                         hi[e] = tf32_rna(a);
                         lo[e] = tf32_rna(a - hi[e]);
                     }
-                    const unsigned off = cm_offset(tid, 4 * k4, KC);
+                    const unsigned off = op_offset<KC>(m, h * KH + 4 * k4);
                     st_shared_v4(st + off, hi[0], hi[1], hi[2], hi[3]);
                     st_shared_v4(st + Sh::A_BYTES + off, lo[0], lo[1], lo[2], lo[3]);
                 }
@@ -363,7 +370,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
                 mbar_arrive(smem_addr(&full[slot]));
             }
         }
-    } else if (warp < 8) {
+    } else if (warp < kMmaProducerWarps + 4) {
         // ---- epilogue ----
         const int quarter = warp & 3;
         int lt = 0;
@@ -386,10 +393,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
             tc_fence_before();
             mbar_arrive(smem_addr(&acce[acc]));
         }
-    } else if (warp == 8) {
+    } else if (warp == kMmaProducerWarps + 4) {
         // ---- MMA issue (the whole warp walks the loop, lane 0 acts) ----
         int q = 0, lt = 0;
-        constexpr unsigned kSbo = 32u * KC;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
             const int acc = lt & 1;
             // the epilogue has drained this accumulator (tile lt - 2)
@@ -405,13 +411,17 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
                 __syncwarp();
                 tc_fence_after();
                 if (lane == 0 && !*(volatile int *)&abort_flag) {
+                    // a K step of 8 is 32 bytes along the row (swizzled) or two core matrices
+                    constexpr unsigned kStep = sw_mode(KC) ? 32u : 256u;
 #pragma unroll
                     for (int ks = 0; ks < KC / 8; ++ks) {
-                        const unsigned ah = st + 256u * ks, al = ah + Sh::A_BYTES;
-                        const unsigned bh = st + 2 * Sh::A_BYTES + 256u * ks, bl = bh + Sh::B_BYTES;
-                        umma_tf32(d, umma_desc(ah, 128, kSbo), umma_desc(bh, 128, kSbo), kIdesc, (c | ks) != 0);
-                        umma_tf32(d, umma_desc(ah, 128, kSbo), umma_desc(bl, 128, kSbo), kIdesc, 1);
-                        umma_tf32(d, umma_desc(al, 128, kSbo), umma_desc(bh, 128, kSbo), kIdesc, 1);
+                        const unsigned ah = st + kStep * ks, al = ah + Sh::A_BYTES;
+                        const unsigned bh = st + 2 * Sh::A_BYTES + kStep * ks, bl = bh + Sh::B_BYTES;
+                        const uint64_t dah = op_desc<KC>(ah), dal = op_desc<KC>(al);
+                        const uint64_t dbh = op_desc<KC>(bh), dbl = op_desc<KC>(bl);
+                        umma_tf32(d, dah, dbh, kIdesc, (c | ks) != 0);
+                        umma_tf32(d, dah, dbl, kIdesc, 1);
+                        umma_tf32(d, dal, dbh, kIdesc, 1);
                     }
                 }
                 if (lane == 0) umma_commit(smem_addr(&empty[slot]));
@@ -451,10 +461,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2) k_ani_mma(Op op, int R, int N,
 }
 
 // packed B of the tensor-core kernel: per chunk, high then low parts, each
-// np x kc in the core-matrix layout (entries past R or N are 0)
-template <class Op>
-__global__ void k_ani_pack(Op op, int S, int R, int N, int np, float *Btab) {
-    const int kc = kAniRows * S;
+// np x kc in the operand layout of op_offset (entries past R or N are 0)
+template <class Op, int KC>
+__global__ void k_ani_pack(Op op, int R, int N, int np, float *Btab) {
+    constexpr int S = KC / kAniRows, kc = KC;
     const long long per = (long long)np * kc;
     const long long total = (long long)ani_chunks(R) * per;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -466,7 +476,7 @@ __global__ void k_ani_pack(Op op, int S, int R, int N, int np, float *Btab) {
         const float b = (r < R && n < N) ? (float)op.b(sp, r, n) : 0.f;
         const float h = tf32_rna(b), l = tf32_rna(b - h);
         float *base = Btab + (size_t)c * 2 * per;
-        const unsigned o = cm_offset(n, k, kc) >> 2;
+        const unsigned o = op_offset<KC>(n, k) >> 2;
         base[o] = h;
         base[per + o] = l;
     }
@@ -487,31 +497,28 @@ __device__ __forceinline__ void ds_fma(float &sh, float &sl, float ah, float al,
 
 // Tile of 64 nodes x 128 outputs (blockIdx.y: the column block), 256
 // threads: thread (tx, ty) = (tid % 16, tid / 16) accumulates nodes
-// 4 tx .. 4 tx + 3 times outputs 8 ty .. 8 ty + 7.  Per chunk the block
-// stages A (kc x 64) and B (kc x 128) in shared memory.  MODE 0: arithmetic
-// in T; MODE 1 (T = float): v in FP64, A split in FP32 pairs, products
-// accumulated in double-single.
+// 4 tx .. 4 tx + 3 times outputs 8 ty .. 8 ty + 7, in T.  Per chunk the
+// block loads every operand value first, then stages A (kc x 64) and B
+// (kc x 128) in shared memory.
 constexpr int kSimtM = 64, kSimtN = 128;
-template <typename T, int MODE, class Op>
+template <typename T, class Op>
 __global__ void __launch_bounds__(256) k_ani_simt(Op op, int S, int R, int N, int ntop, const int *ctl) {
-    using AT = typename std::conditional<MODE == 1, float2, T>::type;
     extern __shared__ __align__(16) unsigned char smem_s[];
     if (ctl && *(volatile const int *)ctl) return;
     const int kc = kAniRows * S;
-    AT *As = (AT *)smem_s;                                      // [kc][64]
-    T *Bs = (T *)(smem_s + (size_t)kc * kSimtM * sizeof(AT));   // [kc][128]
+    T *As = (T *)smem_s;                                     // [kc][64]
+    T *Bs = (T *)(smem_s + (size_t)kc * kSimtM * sizeof(T));  // [kc][128]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const bool top = (int)blockIdx.x < ntop;
     const int j0 = top ? op.jtop + (int)blockIdx.x * kSimtM : ((int)blockIdx.x - ntop) * kSimtM;
     const int n0 = blockIdx.y * kSimtN;
-    T acc[4][8], acl[4][8];
+    T acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = acl[a][b] = T(0);
+        for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
     const int nch = ani_chunks(R);
     for (int c = 0; c < nch; ++c) {
-        // every load of the chunk first, then the products and the stores
         constexpr int kLa = 2 * MAX_SPECIES, kLb = 4 * MAX_SPECIES;  // kc 64 / 256 and kc 128 / 256 at most
         typename Op::VRaw ra[kLa];
         T wa[kLa], rb[kLb];
@@ -531,72 +538,51 @@ __global__ void __launch_bounds__(256) k_ani_simt(Op op, int S, int R, int N, in
             const int r = c * kAniRows + k / S, sp = k % S;
             rb[it] = (it < 4 * S && r < R && n < N) ? op.b(sp, r, n) : T(0);
         }
-        __syncthreads();
+        __syncthreads();  // the previous chunk is read
 #pragma unroll
-        for (int it = 0; it < kLa; ++it) {
-            if (it < 2 * S) {
-                const int idx = tid + 256 * it;
-                if constexpr (MODE == 1) {
-                    const double a = (double)wa[it] * (double)Op::vmul(ra[it]);
-                    const float ah = (float)a;
-                    As[idx] = make_float2(ah, (float)(a - (double)ah));
-                } else {
-                    As[idx] = wa[it] * (T)Op::vmul(ra[it]);
-                }
-            }
-        }
+        for (int it = 0; it < kLa; ++it)
+            if (it < 2 * S) As[tid + 256 * it] = wa[it] * (T)Op::vmul(ra[it]);
 #pragma unroll
         for (int it = 0; it < kLb; ++it)
             if (it < 4 * S) Bs[tid + 256 * it] = rb[it];
         __syncthreads();
+        if (n0 + 8 * ty < N)  // column groups entirely past N have nothing to add
 #pragma unroll 2
-        for (int k = 0; k < kc; ++k) {
-            AT a[4];
-            T b[8];
+            for (int k = 0; k < kc; ++k) {
+                T a[4], b[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = As[k * kSimtM + 4 * tx + q];
+                for (int q = 0; q < 4; ++q) a[q] = As[k * kSimtM + 4 * tx + q];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) b[q] = Bs[k * kSimtN + 8 * ty + q];
+                for (int q = 0; q < 8; ++q) b[q] = Bs[k * kSimtN + 8 * ty + q];
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+                for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if constexpr (MODE == 1) ds_fma(acc[p][q], acl[p][q], a[p].x, a[p].y, b[q]);
-                    else acc[p][q] += a[p] * b[q];
-                }
-        }
+                    for (int q = 0; q < 8; ++q) acc[p][q] += a[p] * b[q];
+            }
     }
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
         const int j = j0 + 4 * tx + p;
         if (j >= op.g.n_atm) continue;
         const typename Op::Pre pr = op.pre(j);
-        if constexpr (MODE == 1) {
-            double v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = (double)acc[p][q] + (double)acl[p][q];
-            out_block(op, pr, j, n0 + 8 * ty, v, N, top);
-        } else {
-            out_block(op, pr, j, n0 + 8 * ty, acc[p], N, top);
-        }
+        out_block(op, pr, j, n0 + 8 * ty, acc[p], N, top);
     }
 }
 
-template <typename T, int MODE>
+template <typename T>
 inline size_t ani_simt_smem(int S) {
-    using AT = typename std::conditional<MODE == 1, float2, T>::type;
     const int kc = kAniRows * S;
-    return (size_t)kc * kSimtM * sizeof(AT) + (size_t)kc * kSimtN * sizeof(T);
+    return (size_t)kc * kSimtM * sizeof(T) + (size_t)kc * kSimtN * sizeof(T);
 }
 
 // the main tiles, preceded by the top layers' tiles when op.jtop < n_atm
-template <typename T, int MODE, class Op>
+template <typename T, class Op>
 inline void ani_simt_launch(cudaStream_t st, const Op &op, int S, int R, int N, const int *ctl) {
-    const size_t sm = ani_simt_smem<T, MODE>(S);
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ani_simt<T, MODE, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = ani_simt_smem<T>(S);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_ani_simt<T, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int ntop = op.jtop < op.g.n_atm ? (op.g.n_atm - op.jtop + kSimtM - 1) / kSimtM : 0;
     const dim3 grid(ntop + (op.g.n_atm + kSimtM - 1) / kSimtM, (N + kSimtN - 1) / kSimtN);
-    k_ani_simt<T, MODE, Op><<<grid, 256, sm, st>>>(op, S, R, N, ntop, ctl);
+    k_ani_simt<T, Op><<<grid, 256, sm, st>>>(op, S, R, N, ntop, ctl);
 }
 
 template <int S, int NP, class Op>

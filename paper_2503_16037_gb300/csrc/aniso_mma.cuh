@@ -100,4 +100,38 @@ __host__ __device__ __forceinline__ unsigned cm_offset(int row, int k, int kc) {
     return (unsigned)((((row >> 3) * (kc >> 2) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
 }
 
+// Swizzled K-major operands: a row of kc FP32 values is one row of the
+// swizzle atom (32, 64 or 128 bytes: kc = 8, 16 or 32), 8 rows per atom,
+// and the 16-byte chunk index within the row is XORed with bits of the row
+// index (the address bits 4.. with the bits 7..; atoms start on multiples of
+// their size).  Other kc use the layout without swizzle.
+__host__ __device__ constexpr int sw_mode(int kc) { return kc == 8 ? 1 : kc == 16 ? 2 : kc == 32 ? 3 : 0; }
+template <int KC>
+__host__ __device__ __forceinline__ unsigned op_offset(int row, int k) {
+    constexpr int mode = sw_mode(KC);
+    if constexpr (mode == 0) {
+        return cm_offset(row, k, KC);
+    } else {
+        constexpr int pitch = KC * 4;                       // bytes per row of the atom
+        constexpr int shift = mode == 1 ? 2 : mode == 2 ? 1 : 0;  // row bits that meet address bit 7
+        constexpr int mask = (1 << mode) - 1;               // chunk bits that are swizzled
+        const int r7 = row & 7;
+        const int chunk = (k >> 2) ^ ((r7 >> shift) & mask);
+        return (unsigned)((row >> 3) * 8 * pitch + r7 * pitch + (chunk << 4) + ((k & 3) << 2));
+    }
+}
+// descriptor of an operand with this layout, start at addr (a K step moves
+// it by 32 bytes): stride offset 8 rows, layout type 6 / 4 / 2 (32, 64, 128
+// byte swizzle) in bits 61-63; without swizzle the core-matrix offsets
+template <int KC>
+__device__ __forceinline__ uint64_t op_desc(unsigned addr) {
+    constexpr int mode = sw_mode(KC);
+    if constexpr (mode == 0) {
+        return umma_desc(addr, 128, 32u * KC);
+    } else {
+        constexpr uint64_t layout = mode == 1 ? 6ull : mode == 2 ? 4ull : 2ull;
+        return umma_desc(addr, 16, 8u * KC * 4) | (layout << 61);
+    }
+}
+
 }  // namespace tk

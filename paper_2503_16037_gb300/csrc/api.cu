@@ -174,8 +174,13 @@ struct tursca_scene {
     int ani_max_nt = 0;         // slots of the largest layer template
     float *ani_Bl = nullptr;                          // tensor-core operand (FP32 scenes)
     void *ani_CfH = nullptr, *ani_Pc = nullptr, *ani_b = nullptr;  // the series' folded form
-    double *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X in FP64, FP64 leaving power
+    void *ani_xtg = nullptr, *ani_xtb = nullptr;                   // ground nodes' sums of X and of b
+    bool ani_tables = false;                  // the quadrature tables hold ani_g's asymmetries
+    double ani_g[tk::MAX_SPECIES] = {0.0};
+    float2 *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X and the leaving power in FP32 pairs
     float *ani_r = nullptr, *ani_E = nullptr;         // FP32 refinement: residual, correction
+    float2 *ani_Ads = nullptr, *ani_Atop = nullptr;   // FP32 refinement: split operands of the residual
+    float *ani_Bds = nullptr;
     bool single_asm = false;  // the current assembly is first-order only (no K, s = 0, x = 0)
     int wq = 8;          // warps per 128-row group of the row-group passes
     bool wq_auto = true;  // wq chosen by the library (else set by the caller)
@@ -1350,12 +1355,16 @@ tursca_status ensure_aniso(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->ani_CfH, (size_t)g.nd * g.npad * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Pc, (size_t)sc->G.nval * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_b, nin * ani_ldx(g) * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_xtg, (size_t)std::max(1, g.n_ground) * es), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_xtb, (size_t)std::max(1, g.n_ground) * es), "alloc aniso");
+    sc->ani_tables = false;
     CK(cudaMemsetAsync(sc->ani_CfH, 0, (size_t)g.nd * g.npad * es, sc->st), "memset aniso");
     CK(dalloc(sc->allocs, sc->ani_X, nin * ani_ldx(g) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_Xn, nin * ani_ldx(g) * es), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_acc, 3 * sizeof(double)), "alloc aniso");
     CK(dalloc(sc->allocs, sc->ani_part, 2 * nblk * sizeof(double)), "alloc aniso");
-    CK(dalloc(sc->allocs, sc->ani_ctl, 2 * sizeof(int)), "alloc aniso");
+    CK(dalloc(sc->allocs, sc->ani_ctl, 4 * sizeof(int)), "alloc aniso");
+    CK(cudaMemsetAsync(sc->ani_ctl, 0, 4 * sizeof(int), sc->st), "memset aniso");
     if (sc->d.precision != TURSCA_FP64) {
         // packed for the tile width the tensor-core launches use
         CK(dalloc(sc->allocs, sc->ani_Bl,
@@ -1373,11 +1382,19 @@ tursca_status ensure_aniso_refine(tursca_scene *sc) {
     if (sc->ani_X64) return TURSCA_OK;
     const tk::GridC g = grid_c(sc);
     const size_t nx = ((size_t)g.nd + g.ngd) * ani_ldx(g);
-    CK(dalloc(sc->allocs, sc->ani_X64, nx * sizeof(double)), "alloc aniso refinement");
-    CK(dalloc(sc->allocs, sc->ani_L64, (size_t)g.nd * g.npad * sizeof(double)), "alloc aniso refinement");
+    CK(dalloc(sc->allocs, sc->ani_X64, nx * sizeof(float2)), "alloc aniso refinement");
+    CK(dalloc(sc->allocs, sc->ani_L64, (size_t)g.nd * g.npad * sizeof(float2)), "alloc aniso refinement");
     CK(dalloc(sc->allocs, sc->ani_r, nx * sizeof(float)), "alloc aniso refinement");
     CK(dalloc(sc->allocs, sc->ani_E, nx * sizeof(float)), "alloc aniso refinement");
-    CK(cudaMemsetAsync(sc->ani_L64, 0, (size_t)g.nd * g.npad * sizeof(double), sc->st), "memset aniso");
+    {
+        const int nin = g.nd + g.ngd, Kp = tk::ani_ds_kp(nin, g.S);
+        const int jtop = std::max(0, g.nz - g.R) * g.nxy / tk::kAniTileM * tk::kAniTileM;
+        CK(dalloc(sc->allocs, sc->ani_Ads, (size_t)Kp * ani_ldz(g) * sizeof(float2)), "alloc aniso refinement");
+        CK(dalloc(sc->allocs, sc->ani_Atop, (size_t)Kp * tk::ani_ds_ldt(g, jtop) * sizeof(float2)),
+           "alloc aniso refinement");
+        CK(dalloc(sc->allocs, sc->ani_Bds, (size_t)Kp * 128 * sizeof(float)), "alloc aniso refinement");
+    }
+    CK(cudaMemsetAsync(sc->ani_L64, 0, (size_t)g.nd * g.npad * sizeof(float2), sc->st), "memset aniso");
     return TURSCA_OK;
 }
 
@@ -1396,6 +1413,8 @@ tk::AniP<T> ani_p(tursca_scene *sc) {
     a.CfH = (T *)sc->ani_CfH;
     a.Pc = (T *)sc->ani_Pc;
     a.b = (T *)sc->ani_b;
+    a.xtg = (T *)sc->ani_xtg;
+    a.xtb = (T *)sc->ani_xtb;
     a.tslot = sc->ani_tslot;
     a.tseg = sc->ani_tseg;
     a.max_nt = sc->ani_max_nt;
@@ -1405,6 +1424,9 @@ tk::AniP<T> ani_p(tursca_scene *sc) {
     a.acc = sc->ani_acc;
     a.ctl = sc->ani_ctl;
     a.Bl = sc->ani_Bl;
+    a.Ads = sc->ani_Ads;
+    a.Atop = sc->ani_Atop;
+    a.Bds = sc->ani_Bds;
     a.mma = sizeof(T) == 4 && sc->aniso == 1;
     return a;
 }
@@ -1412,26 +1434,29 @@ tk::AniP<T> ani_p(tursca_scene *sc) {
 // Terms of the series X <- radd + rho T L(X) (L with Lsun when `sun`) from
 // the content of X (buffer 0) until the relative change is at most tol or
 // max_terms terms: the stopping test runs on the device after every term and
-// the host reads it every kAniCheck terms.  Returns the buffer holding the
+// the host reads it every kAniCheck terms (the terms launched past the one
+// that converged return at once).  Returns the buffer holding the
 // last term in *xi (0: X, 1: Xn), the terms in *terms, the last change in *rel.
-constexpr int kAniCheck = 8;
+constexpr int kAniCheck = 16;
 template <typename T>
 tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun, double tol, int max_terms,
-                         int *xi, int *terms, double *rel) {
+                         int *xi, int *terms, double *rel, int term0 = 0) {
     const tk::GridC g = grid_c(sc);
     const tk::GraphP gp = graph_p(sc);
     const tk::FieldP<T> f = field_p<T>(sc);
     const tk::ViewC vc = view_c(sc);
     const tk::AniP<T> a = ani_p<T>(sc);
     T *buf[2] = {X, Xn};
-    CK(cudaMemsetAsync(a.ctl, 0, 2 * sizeof(int), sc->st), "memset ctl");
+    CK(cudaMemsetAsync(a.ctl, 0, 3 * sizeof(int), sc->st), "memset ctl");
+    // terms term0 + 1, ...: term k reads buf[(k - 1 - term0) & 1]
     int k = 0, h[2] = {0, 0};
     double acc[3] = {0.0, 0.0, 1.0};
+    max_terms -= term0;
     while (k < max_terms) {
         const int n = std::min(kAniCheck, max_terms - k);
         for (int i = 0; i < n; ++i, ++k)
-            CK(tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol, k + 1,
-                                        &sc->launches),
+            CK(tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol,
+                                        term0 + k + 1, &sc->launches),
                "aniso term");
         CK(cudaGetLastError(), "aniso launch");
         CK(cudaMemcpyAsync(h, a.ctl, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read ctl");
@@ -1439,9 +1464,9 @@ tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun,
         CK(cudaStreamSynchronize(sc->st), "sync");
         if (h[0]) break;
     }
-    const int taken = h[0] ? h[1] : k;
+    const int taken = h[0] ? h[1] - term0 : k;
     *xi = taken & 1;
-    *terms = taken;
+    *terms = term0 + taken;
     *rel = acc[2];
     return TURSCA_OK;
 }
@@ -1449,9 +1474,9 @@ tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun,
 // The series of Eq. fs_sum over the edge unknowns, then x and the emission
 // from X.  FP64 scenes: until the relative change of X is at most rtol.
 // FP32 scenes: the FP32 series to a change of max(rtol, 1e-6) (about the
-// rounding floor of an FP32 iterate), then while the FP64 residual
-// |F(X) - X| / |X| (X in FP64, double-single sums) is above rtol, the
-// correction series e = r + (F(e) - F(0)) and X += e in FP64.  (Chebyshev
+// rounding floor of an FP32 iterate), then while the residual |F(X) - X| /
+// |X|, evaluated in double-single (X in FP32 pairs), is above rtol, the
+// correction series e = r + (F(e) - F(0)) and X += e in pairs.  (Chebyshev
 // steps on a real interval, as the node form's refinements take, diverge
 // here: the arrival-direction memory gives A a spectrum well off the real
 // axis, and for a spectrum that fills a disk the plain series is the best
@@ -1464,11 +1489,15 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
     const int ldx = ani_ldx(g);
     const size_t nx = ((size_t)g.nd + g.ngd) * ldx;
     T *X = (T *)sc->ani_X, *Xn = (T *)sc->ani_Xn;
-    CK(cudaMemsetAsync(X, 0, nx * sizeof(T), sc->st), "memset X");
+    // the first term from X = 0 is b, which the assembly formed (with the ground sums)
+    CK(cudaMemcpyAsync(X, sc->ani_b, nx * sizeof(T), cudaMemcpyDeviceToDevice, sc->st), "copy b");
+    CK(cudaMemcpyAsync(sc->ani_xtg, sc->ani_xtb, (size_t)std::max(1, g.n_ground) * sizeof(T),
+                       cudaMemcpyDeviceToDevice, sc->st),
+       "copy b");
     const double tol = sizeof(T) == 8 ? rtol : std::max(rtol, 1e-6);
     int xi = 0, terms = 0, total = 0, refinements = 0;
     double rel = 1.0;
-    tursca_status e = ani_series<T>(sc, X, Xn, nullptr, true, tol, max_iter, &xi, &terms, &rel);
+    tursca_status e = ani_series<T>(sc, X, Xn, nullptr, true, tol, max_iter, &xi, &terms, &rel, 1);
     if (e) return e;
     total = terms;
     bool converged = rel <= tol;
@@ -1506,7 +1535,7 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
             total += et;
             tk::launch_aniso_update(sc->st, (long long)nx, ei ? (float *)Xn : sc->ani_E, sc->ani_X64, false);
         }
-        tk::launch_aniso_finish<float, double>(sc->st, g, f, sc->ani_X64, ldx, sc->x64, (float *)sc->emis,
+        tk::launch_aniso_finish<float, float2>(sc->st, g, f, sc->ani_X64, ldx, sc->x64, (float *)sc->emis,
                                                &sc->launches);
     } else {
         tk::launch_aniso_finish<T, T>(sc->st, g, f, xi ? Xn : X, ldx, sc->x64, (T *)sc->emis, &sc->launches);
@@ -2107,15 +2136,20 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
         tursca_status e = ensure_aniso(sc);
         if (e) return e;
         int p1 = prof_begin(sc, P_ROWS);
+        // the quadrature tables depend on the HG asymmetries (and the graph) only
+        bool tables = !sc->ani_tables;
+        for (int sp = 0; sp < g.S; ++sp) tables = tables || vc.g[sp] != sc->ani_g[sp];
         if (sc->d.precision == TURSCA_FP64) {
             tk::launch_assemble_rows_p<double>(sc->st, g, gp, field_p<double>(sc), vc, &sc->launches);
-            tk::launch_aniso_prep<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, ani_p<double>(sc),
+            tk::launch_aniso_prep<double>(sc->st, g, gp, field_p<double>(sc), vc, vp, ani_p<double>(sc), tables,
                                           &sc->launches);
         } else {
             tk::launch_assemble_rows_p<float>(sc->st, g, gp, field_p<float>(sc), vc, &sc->launches);
-            tk::launch_aniso_prep<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, ani_p<float>(sc),
+            tk::launch_aniso_prep<float>(sc->st, g, gp, field_p<float>(sc), vc, vp, ani_p<float>(sc), tables,
                                          &sc->launches);
         }
+        sc->ani_tables = true;
+        for (int sp = 0; sp < g.S; ++sp) sc->ani_g[sp] = vc.g[sp];
         prof_end(sc, p1);
     } else {
         int p1 = prof_begin(sc, P_ROWS);
