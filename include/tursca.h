@@ -134,7 +134,9 @@ typedef enum {
     TURSCA_F_Q_ISO = 11,   /* double [n_dirs] */
     TURSCA_F_Q_LAMB = 12,  /* double [n_gdirs] */
     TURSCA_F_Q_SUN = 13,   /* real  [n_species][n_dirs] */
-    TURSCA_F_DIRS = 14     /* int32 [n_dirs][3] lattice directions, in the library's order */
+    TURSCA_F_DIRS = 14,    /* int32 [n_dirs][3] lattice directions, in the library's order */
+    TURSCA_F_ANISO_X = 15  /* double [n_dirs + n_gdirs][n_nodes] edge unknowns X(i, w) of the last
+                              TURSCA_OPT_ANISO solve (TURSCA_E_STATE before one) */
 } tursca_field;
 
 /* Create a scene for grid *desc whose work runs on cuda_stream (a

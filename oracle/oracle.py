@@ -119,6 +119,8 @@ def _load():
         lib.orc_partition.restype = C.c_int
         lib.orc_phase_quadrature.argtypes = [C.POINTER(OrcDesc), _dp, _dp, C.POINTER(C.c_int)]
         lib.orc_phase_quadrature.restype = C.c_int
+        lib.orc_aniso_rows.argtypes = [C.POINTER(OrcDesc), _dp, _dp, _dp, _dp, _ip, C.c_int, _dp]
+        lib.orc_aniso_rows.restype = C.c_int
         lib.orc_result_size.restype = C.c_int
         lib.orc_desc_size.restype = C.c_int
         assert lib.orc_result_size() == C.sizeof(OrcResult), "OrcResult layout mismatch"
@@ -147,6 +149,29 @@ def _arr(ptr, n, dtype=np.float64):
     if n == 0:
         return np.zeros(0, dtype=dtype)
     return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def aniso_rows(sc, X: np.ndarray, rows, threads: int = 0) -> np.ndarray:
+    """The edge form's fixed-point map F(X) (Eq. flux_system with the arrival
+    direction kept) at the receiver rows ``rows``: X is [n_nodes][n_dirs +
+    n_gdirs] in FP64 (the oracle's arrival-direction order); returns
+    [len(rows)][n_dirs + n_gdirs].  A solution of the series satisfies
+    F(X) = X."""
+    lib = _load()
+    d = _desc(sc, ANISO, threads, 1e-13)
+    mu_a = np.ascontiguousarray(sc.mu_a, dtype=np.float64).ravel()
+    mu_s = np.ascontiguousarray(sc.mu_s, dtype=np.float64).ravel()
+    g = np.ascontiguousarray(sc.g, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    nin = X.shape[1]
+    out = np.zeros((len(rows), nin), dtype=np.float64)
+    rc = lib.orc_aniso_rows(C.byref(d), mu_a.ctypes.data_as(_dp), mu_s.ctypes.data_as(_dp), g.ctypes.data_as(_dp),
+                            X.ctypes.data_as(_dp), rows.ctypes.data_as(_ip), C.c_int(len(rows)),
+                            out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise ValueError("oracle rejected the scene (code %d)" % rc)
+    return out
 
 
 def run(sc, flags: int = 0, threads: int = 0, gmres_tol: float = 1e-13) -> dict:

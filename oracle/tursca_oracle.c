@@ -1450,3 +1450,74 @@ void orc_fibonacci(int m, int M, double *s) { orc_fib_point(m, M, s); }
 
 int orc_result_size(void) { return (int)sizeof(orc_result); }
 int orc_desc_size(void) { return (int)sizeof(orc_desc); }
+
+/* The edge form's fixed-point map at chosen receiver rows (for checks of a
+ * solution X at sizes where the whole series does not fit): with X given for
+ * every node ([n_nodes][n_dirs + n_gdirs], the arrival directions as in
+ * orc_aniso), out[t][w] = F(X)(rows[t], w), where
+ *   F(X)(i, w) = rho_i sum_{slots e of row i arriving along w}
+ *                  (P_e L(src_e, dir_e) + depsun_e e1(src_e))
+ *   L(j, u)    = sum_w' X(j, w') Q_j(w' -> u) c_j(u | w')     atmospheric j
+ *   L(c, k)    = (sum_w' X(c, w')) q_lamb_k c_k                ground c
+ * the same definitions orc_aniso iterates (Eq. flux_system, Eq. F_term_phase),
+ * each source's leaving power built only when a chosen row needs it.
+ * Returns 0, or the code of orc_run. */
+int orc_aniso_rows(const orc_desc *d_in, const double *mu_a, const double *mu_s, const double *g, const double *X,
+                   const int *rows, int nrows, double *out) {
+    orc_desc dd = *d_in;
+    dd.flags |= ORC_ANISO | ORC_NO_SOLVE;
+    orc_result *r = NULL;
+    int rc = orc_run(&dd, mu_a, mu_s, g, &r);
+    if (rc != 0) return rc;
+    const int na = r->n_atm, nn = r->n_nodes, nd = r->n_dirs, ngd = r->n_gdirs, S = dd.S, nin = nd + ngd;
+    /* row ranges of the slots (sorted by row) */
+    long *start = calloc((size_t)nn + 1, sizeof(long));
+    for (long e = 0; e < r->n_slots; ++e) start[r->slot_row[e] + 1]++;
+    for (int i = 0; i < nn; ++i) start[i + 1] += start[i];
+    double *Q = malloc(sizeof(double) * (size_t)S * nin * nd);
+    orc_phase_quadrature_fill(&dd, r, g, Q);
+    double *mus = calloc((size_t)na, sizeof(double));
+    for (int j = 0; j < na; ++j)
+        for (int sp = 0; sp < S; ++sp) mus[j] += mu_s[(size_t)sp * na + j];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < nrows; ++t) {
+        const int i = rows[t];
+        double *o = out + (size_t)t * nin;
+        for (int w = 0; w < nin; ++w) o[w] = 0.0;
+        if (i < 0 || i >= nn) continue;
+        const double mue_i = i < na ? mu_a[i] + mus[i] : 0.0;
+        const double rho = i < na ? (mue_i > 0.0 ? mus[i] / mue_i : 0.0) : dd.albedo;
+        for (long e = start[i]; e < start[i + 1]; ++e) {
+            const int j = r->slot_col[e], din = r->slot_dir[e];
+            const int u = din < nd ? din : din - nd;
+            /* L(j, u) from the definitions (one source, one direction) */
+            double L = 0.0;
+            if (j < na) {
+                double q[ORC_MAXDIR], cw[ORC_MAXDIR], z, wsp[16];
+                for (int sp = 0; sp < S; ++sp) wsp[sp] = mus[j] > 0.0 ? mu_s[(size_t)sp * na + j] / mus[j] : 1.0 / S;
+                for (int w = 0; w < nin; ++w) {
+                    const double xw = X[(size_t)j * nin + w];
+                    if (xw == 0.0) continue;
+                    for (int v = 0; v < nd; ++v) {
+                        double acc = 0.0;
+                        for (int sp = 0; sp < S; ++sp) acc += wsp[sp] * Q[((size_t)sp * nin + w) * nd + v];
+                        q[v] = acc;
+                    }
+                    orc_route(&dd, &r->chain_C[(size_t)j * nd], q, nd, cw, &z);
+                    L += xw * q[u] * cw[u];
+                }
+            } else {
+                double cw[ORC_MAXGDIR], z, xt = 0.0;
+                orc_route(&dd, &r->chain_C[(size_t)j * nd], r->q_lamb, ngd, cw, &z);
+                for (int w = 0; w < nin; ++w) xt += X[(size_t)j * nin + w];
+                L = xt * r->q_lamb[u] * cw[u];
+            }
+            o[din] += rho * (r->slot_P[e] * L + r->slot_depsun[e] * r->e1[j]);
+        }
+    }
+    free(mus);
+    free(Q);
+    free(start);
+    orc_free(r);
+    return 0;
+}

@@ -162,6 +162,10 @@ template <typename T, typename XT>
 void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, const XT *X, int ldx, double *x64,
                          T *emis, long long *launches);
 
+// The solution X(i, w) as [nin][n_nodes] FP64 (from FP32 pairs or FP64).
+template <typename XT>
+void launch_aniso_export(cudaStream_t st, const GridC &g, const XT *X, int ldx, double *out);
+
 // The two contractions alone, for the tests: out(j, n) for the atmospheric
 // nodes j of the current tables, n < N ([N][n_atm]); which: 0 leave (X in
 // [nin][ldx]), 1 sqc; mma: the tensor-core kernel, else the CUDA-core one.

@@ -175,6 +175,7 @@ struct tursca_scene {
     float *ani_Bl = nullptr;                          // tensor-core operand (FP32 scenes)
     void *ani_CfH = nullptr, *ani_Pc = nullptr, *ani_b = nullptr;  // the series' folded form
     void *ani_xtg = nullptr, *ani_xtb = nullptr;                   // ground nodes' sums of X and of b
+    void *ani_Xsol = nullptr;  // the solved X: FP32 pairs (FP32 scenes) or FP64, [nin][ldx]; null before a solve
     bool ani_tables = false;                  // the quadrature tables hold ani_g's asymmetries
     double ani_g[tk::MAX_SPECIES] = {0.0};
     float2 *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X and the leaving power in FP32 pairs
@@ -1537,8 +1538,10 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
         }
         tk::launch_aniso_finish<float, float2>(sc->st, g, f, sc->ani_X64, ldx, sc->x64, (float *)sc->emis,
                                                &sc->launches);
+        sc->ani_Xsol = sc->ani_X64;
     } else {
         tk::launch_aniso_finish<T, T>(sc->st, g, f, xi ? Xn : X, ldx, sc->x64, (T *)sc->emis, &sc->launches);
+        sc->ani_Xsol = xi ? Xn : X;
     }
     CK(cudaGetLastError(), "aniso launch");
     if (solver == TURSCA_SOLVER_AUTO)
@@ -2288,6 +2291,27 @@ tursca_status tursca_get(tursca_scene *sc, tursca_field which, void *dst, size_t
         case TURSCA_F_Q_ISO: src = G.q_iso.data(); need = G.q_iso.size() * 8; host = true; break;
         case TURSCA_F_Q_LAMB: src = G.q_lamb.data(); need = G.q_lamb.size() * 8; host = true; break;
         case TURSCA_F_Q_SUN: src = sc->q_sun; need = (size_t)sc->d.n_species * G.dirs.size() * es; break;
+        case TURSCA_F_ANISO_X: {
+            // the edge unknowns of the last anisotropic solve, [nin][n_nodes] FP64
+            if (!sc->solved || !sc->aniso_asm || !sc->ani_Xsol)
+                return fail(sc, TURSCA_E_STATE, "no anisotropic solve");
+            const tk::GridC gc = grid_c(sc);
+            const size_t nx = ((size_t)gc.nd + gc.ngd) * gc.n_nodes;
+            if (bytes != nx * 8) return fail(sc, TURSCA_E_INVALID, "bytes does not match the field size");
+            void *dtmp = nullptr;
+            CK(cudaMalloc(&dtmp, nx * 8), "alloc");
+            if (sc->d.precision == TURSCA_FP64)
+                tk::launch_aniso_export<double>(sc->st, gc, (const double *)sc->ani_Xsol, ani_ldx(gc), (double *)dtmp);
+            else
+                tk::launch_aniso_export<float2>(sc->st, gc, (const float2 *)sc->ani_Xsol, ani_ldx(gc), (double *)dtmp);
+            sc->launches++;
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, dtmp, nx * 8, cudaMemcpyDefault, sc->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(sc->st);
+            cudaFree(dtmp);
+            if (e != cudaSuccess) return cuda_fail(sc, e, "get aniso X");
+            return TURSCA_OK;
+        }
         case TURSCA_F_DIRS:
             tmp32.resize(G.dirs.size() * 3);
             for (size_t u = 0; u < G.dirs.size(); ++u)

@@ -856,6 +856,22 @@ void launch_aniso_finish(cudaStream_t st, const GridC &g, const FieldP<T> &f, co
     if (launches) *launches += 1;
 }
 
+template <typename XT>
+__global__ void k_ani_export(GridC g, const XT *__restrict__ X, int ldx, double *out) {
+    const long long n = (long long)(g.nd + g.ngd) * g.n_nodes;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int w = (int)(idx / g.n_nodes), j = (int)(idx - (long long)w * g.n_nodes);
+        out[idx] = as_double(X[(size_t)w * ldx + j]);
+    }
+}
+template <typename XT>
+void launch_aniso_export(cudaStream_t st, const GridC &g, const XT *X, int ldx, double *out) {
+    k_ani_export<XT><<<1216, 256, 0, st>>>(g, X, ldx, out);
+}
+template void launch_aniso_export<float2>(cudaStream_t, const GridC &, const float2 *, int, double *);
+template void launch_aniso_export<double>(cudaStream_t, const GridC &, const double *, int, double *);
+
 cudaError_t launch_aniso_contract_test(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<float> &f,
                                        const AniP<float> &a, const float *X, float *out, int which, bool mma) {
     const int nin = g.nd + g.ngd;

@@ -26,7 +26,7 @@ SOLVER_AUTO, SOLVER_NEUMANN, SOLVER_GMRES, SOLVER_CHEBYSHEV = 0, 1, 2, 3
 OK, E_INVALID, E_NOMEM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_STATE, E_UNSUPPORTED = range(8)
 
 F_ROW_PTR, F_COL, F_VAL, F_SLOT_DIR, F_SLOT_K, F_TSUN, F_E1, F_S, F_X, F_EMIS, F_GSUN, F_Q_ISO, F_Q_LAMB, \
-    F_Q_SUN, F_DIRS = range(15)
+    F_Q_SUN, F_DIRS, F_ANISO_X = range(16)
 
 
 class TurscaError(RuntimeError):

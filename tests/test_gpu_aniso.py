@@ -137,3 +137,36 @@ def test_aniso_combinations_and_toggle():
     rn.run(mu_a, mu_s, rtol=1e-10)
     torch.cuda.synchronize()
     assert np.array_equal(rn.rad.cpu().numpy().astype(np.float64), full0)
+
+
+def _sample_rows(sc, n_per_layer=12, seed=3):
+    """Rows spread over the layers that differ: the bottom and top layers
+    (ground hits, directions without a receiver), the middle, and the ground."""
+    rng = np.random.default_rng(seed)
+    nxy = sc.nx * sc.ny
+    layers = sorted({0, 1, sc.nz // 2, sc.nz - 2, sc.nz - 1, sc.nz})  # nz: the ground nodes
+    rows = [z * nxy + int(c) for z in layers for c in rng.choice(nxy, n_per_layer, replace=False)]
+    return np.array(rows, dtype=np.int32)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_aniso_full_plume_is_a_fixed_point_of_the_oracle_map(prec):
+    """The full 64x64x32 plume (the bench's edge-form workload): the GPU's
+    solved X(i, w) satisfies the oracle's own edge-form map, F_oracle(X) = X,
+    at rows sampled over the layers that differ (the whole series does not
+    fit the oracle at this size).  FP64: to rounding.  FP32 + refinement: to
+    the FP32 rounding of the coefficients the GPU operator stores."""
+    sc = scenes.make_plume()
+    P = T.FP64 if prec == "fp64" else T.FP32_REFINE
+    rn, rad = run_aniso(sc, P)
+    st = rn.stats
+    nin = st.n_dirs + st.n_gdirs
+    X = rn.get(T.F_ANISO_X, nin * st.n_nodes, torch.float64).reshape(nin, st.n_nodes).T.copy()
+    rows = _sample_rows(sc)
+    F = O.aniso_rows(sc, X, rows)
+    scale = np.abs(X[rows]).max(axis=1) + 1e-300
+    err = (np.abs(F - X[rows]).max(axis=1) / scale).max()
+    print("plume 64x64x32 %s: %d terms, %d residuals (%.1e); max row-relative |F(X) - X| = %.2e over %d rows"
+          % (prec, rn.info.iters, rn.info.refinements, rn.info.rel_resid64, err, len(rows)))
+    assert np.isfinite(rad).all() and (rad > 0).all()
+    assert err < (1e-11 if prec == "fp64" else 5e-6)

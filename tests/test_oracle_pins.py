@@ -1064,3 +1064,29 @@ def test_ground_hit_columns_brute_force():
         assert got == expect
         vals = [v for _, v in hits]
         assert max(vals) - min(vals) <= 1e-15 * max(vals)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: scenes.make_random(7, 6, 5, seed=61, S=2, R=2, M=512),
+    lambda: scenes.make_random(8, 7, 4, seed=62, S=3, R=1, M=512, sza=20.0, vza=55.0),
+])
+def test_p12_rowwise_edge_map_fixes_the_oracle_edge_solution(make):
+    """The row-wise edge-form map (orc_aniso_rows, which builds each needed
+    source's leaving power on the fly) reproduces the converged series of
+    orc_aniso at every row: F(X) = X, and a change of X at one source moves
+    F at its receivers only through that source's chains."""
+    sc = make()
+    r = O.run(sc, flags=O.ANISO)
+    X = r["X"]
+    rng = np.random.default_rng(5)
+    rows = rng.choice(r["n_nodes"], 48, replace=False).astype(np.int32)
+    F = O.aniso_rows(sc, X, rows)
+    assert np.abs(F - X[rows]).max() <= 1e-12 * np.abs(X).max()
+    # doubling X at one source changes F exactly at the rows its slots reach
+    j = int(rows[0])
+    X2 = X.copy()
+    X2[j] *= 2.0
+    reach = set(r["slot_row"][r["slot_col"] == j].tolist())
+    F2 = O.aniso_rows(sc, X2, rows)
+    moved = {int(i) for i, a, b in zip(rows, F, F2) if np.abs(a - b).max() > 1e-14 * np.abs(X).max()}
+    assert moved and moved <= reach
