@@ -73,6 +73,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
+# nominal dense TF32 / BF16 tensor rate of this part (1.1 / 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak():
+    """TF32 tensor peak: the measured sustained BF16 GEMM rate (a kernel timed
+    inside a long step) times the nominal TF32 / BF16 ratio."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]) * TF32_PER_BF16, "measured bf16 sustained x nominal tf32/bf16"
+    except Exception:
+        return 1700.0 * TF32_PER_BF16, "fallback bf16 sustained x nominal tf32/bf16"
+
+
 # the sources each traffic record depends on
 TRAFFIC_SOURCES = {
     "k_tile_OpCheb": ("kernels_solve.cu", "stage.cuh", "kern.h"),
@@ -772,6 +787,38 @@ def main():
                 "traffic": traffic_record("k_tile_OpCheb") if not variant else None,
                 "algorithmic_bytes_per_launch": spmv_bytes,
                 "avg_launch_us": avg_s * 1e6}
+    # ---- the edge form's terms: the contraction (tcgen05, TF32 split in
+    # three products) against the TF32 peak, counting the useful FP32 flops
+    # 2 n_atm nd nin S; the transport against HBM, counting P' (4 nnz), the
+    # planes of G (4 nd N), b and the previous X read and the new X written
+    # (12 nin N).  Per working term: terms launched past convergence return
+    # at once and are not counted.
+    roof_edge = None
+    if args.aniso and prof.get("ani_leave", (0, 0.0))[0] and prof_steps:
+        nin = st.n_dirs + st.n_gdirs
+        n_terms = max(1, len(prof_steps) * (iters[prof_steps[0]][0] - 1))
+        t_leave = prof["ani_leave"][1] / n_terms / 1000.0
+        t_move = prof["ani_transport"][1] / n_terms / 1000.0
+        flops = 2.0 * st.n_atm * st.n_dirs * nin * sc.n_species
+        tpk, tpk_kind = tf32_peak()
+        mv_bytes = 4 * st.nnz + 4 * st.n_dirs * st.n_nodes + 12 * nin * st.n_nodes
+        roof_edge = {
+            "contraction": {"kernel": "k_ani_mma (tcgen05 kind::tf32, A and B split in high and low TF32 parts, "
+                                      "three products, persistent warp-specialised, TMA-fed)", "bound": "tensor",
+                            "achieved": flops / t_leave / 1e12, "peak": tpk, "unit": "TFLOP/s",
+                            "frac": flops / t_leave / 1e12 / tpk, "peak_kind": tpk_kind,
+                            "algorithmic_flops_per_term": flops, "tensor_flops_issued_per_term": 3 * flops,
+                            "avg_term_us": t_leave * 1e6},
+            "transport": {"kernel": "k_ani_transport (gather by arrival direction, P' = P Cf, first-order term b)",
+                          "bound": "hbm", "achieved": mv_bytes / t_move / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": mv_bytes / t_move / 1e9 / peak, "peak_kind": peak_kind + " (hbm_gbs, copy)",
+                          "algorithmic_bytes_per_term": mv_bytes, "avg_term_us": t_move * 1e6},
+            "terms_per_solve": iters[prof_steps[0]][0], "residuals_per_solve": iters[prof_steps[0]][1],
+            "residual_ms": prof.get("ani_residual", (1, 0.0))[1] / max(1, prof.get("ani_residual", (1, 0.0))[0]),
+        }
+        if roof is None:
+            roof = dict(roof_edge["contraction"])
+            roof["traffic"] = None
     # ---- roofline of the assembly (edge march and edge weights, with the
     # per-scene tables): algorithmic bytes per scene = fields read 4 N (2 + S)
     # + values written 4 nnz + s, e1, g^sun 12 N + tau_inf round trip
@@ -818,6 +865,7 @@ def main():
         "edges_per_s": value * st.nnz_edges,
         "roofline": roof,
         "roofline_assembly": roof_asm,
+        "roofline_edge_form": roof_edge,
         "kernels": kernels,
         "stage_shares": stages,
         "cpu_baseline": cpu,

@@ -351,7 +351,11 @@ typedef struct {
                            counted as a launch), "set_medium" (its copies), "solve" (a whole
                            solve, from its first to its last operation on the stream,
                            host round trips included; the solve's other categories lie
-                           inside it) */
+                           inside it), and of the anisotropic mode "ani_leave" (one term's
+                           contraction and ground leaving power), "ani_transport" (one
+                           term's transport and stopping test; terms launched past
+                           convergence return at once and count too), "ani_residual" (one
+                           residual evaluation of the FP32 refinement) */
     long long launches; /* launches since the last read */
     double total_ms;    /* summed event time of those launches */
 } tursca_kernel_stat;

@@ -139,12 +139,17 @@ void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const 
 // relative change is at most tol sets a.ctl = {1, term}; every kernel of a
 // later term returns at once.  a.ctl must be zeroed before the first term
 // (the transport's last block takes the test and resets its block count).
-// cudaErrorInvalidValue when the tensor-core kernel's tensor maps cannot be
-// made (nothing launched then).
+// A term is two launches: launch_aniso_leave (the contraction and the
+// ground's leaving power of X into a.Lh; cudaErrorInvalidValue, nothing
+// launched, when the tensor-core kernel's tensor maps cannot be made), then
+// launch_aniso_move (the transport and the stopping test).
 template <typename T>
-cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                              const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
-                              long long *launches);
+cudaError_t launch_aniso_leave(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                               const AniP<T> &a, const T *X, long long *launches);
+template <typename T>
+void launch_aniso_move(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                       const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
+                       long long *launches);
 
 // FP32 refinement, in double-single (FP32 pairs hi + lo, about 48 bits: the
 // arithmetic of FP64 on the FP32 units).  The residual r = F(X) - X (F with

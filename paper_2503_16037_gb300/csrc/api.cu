@@ -197,16 +197,20 @@ struct tursca_scene {
 };
 
 namespace {
-const char *const kProfNames[] = {"spmv",   "resid64",    "assemble_rows", "assemble_pre", "render", "cheb",
-                                  "gmres_orth", "select", "gmres_prod",   "set_medium",   "solve"};
-constexpr int kNProf = 11;
+const char *const kProfNames[] = {"spmv",   "resid64",    "assemble_rows", "assemble_pre",  "render",
+                                  "cheb",   "gmres_orth", "select",        "gmres_prod",    "set_medium",
+                                  "solve",  "ani_leave",  "ani_transport", "ani_residual"};
+constexpr int kNProf = 14;
 // P_GPROD: the passes over K of one Arnoldi step (preconditioner and product
 // with I - K), counted as launches; P_MEDIUM: the copies of set_medium;
 // P_SOLVE: a whole solve, from its first to its last operation on the stream
-// (the other categories of the solve lie inside it)
+// (the other categories of the solve lie inside it); P_ALEAVE, P_AMOVE: the
+// edge form's per-term leaving power (contraction and ground) and transport
+// (with its stopping test), terms past convergence included; P_ARESID: a
+// whole residual evaluation of its refinement
 enum {
     P_SPMV = 0, P_RESID = 1, P_ROWS = 2, P_PRE = 3, P_RENDER = 4, P_CHEB = 5, P_ORTH = 6, P_SEL = 7, P_GPROD = 8,
-    P_MEDIUM = 9, P_SOLVE = 10
+    P_MEDIUM = 9, P_SOLVE = 10, P_ALEAVE = 11, P_AMOVE = 12, P_ARESID = 13
 };
 
 // NVTX range around one call of the C ABI (a stage of the path), for
@@ -1455,10 +1459,15 @@ tursca_status ani_series(tursca_scene *sc, T *X, T *Xn, const T *radd, bool sun,
     max_terms -= term0;
     while (k < max_terms) {
         const int n = std::min(kAniCheck, max_terms - k);
-        for (int i = 0; i < n; ++i, ++k)
-            CK(tk::launch_aniso_term<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol,
-                                        term0 + k + 1, &sc->launches),
-               "aniso term");
+        for (int i = 0; i < n; ++i, ++k) {
+            const int p0 = prof_begin(sc, P_ALEAVE);
+            CK(tk::launch_aniso_leave<T>(sc->st, g, gp, f, a, buf[k & 1], &sc->launches), "aniso term");
+            prof_end(sc, p0);
+            const int p1 = prof_begin(sc, P_AMOVE);
+            tk::launch_aniso_move<T>(sc->st, g, gp, f, vc, a, buf[k & 1], buf[(k + 1) & 1], radd, sun, tol,
+                                     term0 + k + 1, &sc->launches);
+            prof_end(sc, p1);
+        }
         CK(cudaGetLastError(), "aniso launch");
         CK(cudaMemcpyAsync(h, a.ctl, sizeof h, cudaMemcpyDeviceToHost, sc->st), "read ctl");
         CK(cudaMemcpyAsync(acc, a.acc, sizeof acc, cudaMemcpyDeviceToHost, sc->st), "read change");
@@ -1511,7 +1520,9 @@ tursca_status do_solve_aniso(tursca_scene *sc, int solver, double rtol, int max_
         tk::launch_aniso_update(sc->st, (long long)nx, xi ? Xn : X, sc->ani_X64, true);
         converged = false;
         while (refinements < kAniMaxRefine) {
+            const int pr = prof_begin(sc, P_ARESID);
             tk::launch_aniso_resid(sc->st, g, gp, f, vc, a, sc->ani_X64, sc->ani_L64, sc->ani_r, &sc->launches);
+            prof_end(sc, pr);
             sc->launches++;
             double acc[3];
             CK(cudaGetLastError(), "aniso residual launch");
@@ -2191,14 +2202,15 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
         sc->solved = true;
         return TURSCA_OK;
     }
-    if (sc->aniso_asm) {
-        if (sc->d.precision == TURSCA_FP64) return do_solve_aniso<double>(sc, solver, rtol, max_iter, info);
-        return do_solve_aniso<float>(sc, solver, rtol, max_iter, info);
-    }
     const int ps = prof_begin(sc, P_SOLVE);
-    const tursca_status r = sc->d.precision == TURSCA_FP64
-                                ? do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc))
-                                : do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
+    tursca_status r;
+    if (sc->aniso_asm)
+        r = sc->d.precision == TURSCA_FP64 ? do_solve_aniso<double>(sc, solver, rtol, max_iter, info)
+                                           : do_solve_aniso<float>(sc, solver, rtol, max_iter, info);
+    else
+        r = sc->d.precision == TURSCA_FP64
+                ? do_solve<double>(sc, solver, rtol, max_iter, info, forward_io<double>(sc))
+                : do_solve<float>(sc, solver, rtol, max_iter, info, forward_io<float>(sc));
     prof_end(sc, ps);
     return r;
 }

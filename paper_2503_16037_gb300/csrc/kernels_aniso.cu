@@ -682,9 +682,8 @@ void launch_aniso_prep(cudaStream_t st, const GridC &g, const GraphP &gp, const 
 }
 
 template <typename T>
-cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
-                              const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
-                              long long *launches) {
+cudaError_t launch_aniso_leave(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                               const AniP<T> &a, const T *X, long long *launches) {
     const int nin = g.nd + g.ngd;
     const LeaveOp<T, T, T, true> lop = leave_op<T>(g, gp, a, f.wsp, X, 0, true);
     bool done = false;
@@ -698,11 +697,18 @@ cudaError_t launch_aniso_term(cudaStream_t st, const GridC &g, const GraphP &gp,
     if (!done) ani_simt_launch<T>(st, lop, g.S, nin, g.nd, a.ctl);
     if (g.n_ground > 0)
         k_ani_ground_x<T><<<(g.n_ground * g.ngd + 255) / 256, 256, 0, st>>>(g, a, a.Lh, a.ctl);
+    if (launches) *launches += g.n_ground > 0 ? 2 : 1;
+    return cudaSuccess;
+}
+
+template <typename T>
+void launch_aniso_move(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                       const AniP<T> &a, const T *X, T *Xn, const T *radd, bool sun, double tol, int term,
+                       long long *launches) {
     const int nblk = (g.nz + 1) * g.gpl;
     k_ani_transport<T, 0, T, T><<<nblk, 32 * kAniW, transport_smem(g, a), st>>>(g, gp, f, vc, a, a.Pc, a.Lh, X, Xn, radd,
                                                                                   sun ? a.b : nullptr, 1, tol, term);
-    if (launches) *launches += g.n_ground > 0 ? 3 : 2;
-    return cudaSuccess;
+    if (launches) *launches += 1;
 }
 
 // ---- the residual's contraction in double-single ----
@@ -893,7 +899,9 @@ cudaError_t launch_aniso_contract_test(cudaStream_t st, const GridC &g, const Gr
 #define INST(T)                                                                                                 \
     template void launch_aniso_prep<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
                                        const ViewC &, const ViewP &, const AniP<T> &, bool, long long *);       \
-    template cudaError_t launch_aniso_term<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,   \
+    template cudaError_t launch_aniso_leave<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,  \
+                                               const AniP<T> &, const T *, long long *);                        \
+    template void launch_aniso_move<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,          \
                                        const ViewC &, const AniP<T> &, const T *, T *, const T *, bool, double, \
                                        int, long long *);                                                       \
     template void launch_aniso_finish<T, T>(cudaStream_t, const GridC &, const FieldP<T> &, const T *, int,     \
