@@ -177,6 +177,11 @@ struct tursca_scene {
     void *ani_xtg = nullptr, *ani_xtb = nullptr;                   // ground nodes' sums of X and of b
     void *ani_Xsol = nullptr;  // the solved X: FP32 pairs (FP32 scenes) or FP64, [nin][ldx]; null before a solve
     bool ani_tables = false;                  // the quadrature tables hold ani_g's asymmetries
+    // the node form's quadrature tables (q^sun, HG weights toward the
+    // instrument) hold the view and asymmetries in qt_key (sun and view
+    // directions, then g per species)
+    bool qt_ok = false;
+    double qt_key[6 + tk::MAX_SPECIES] = {0.0};
     double ani_g[tk::MAX_SPECIES] = {0.0};
     float2 *ani_X64 = nullptr, *ani_L64 = nullptr;    // FP32 refinement: X and the leaving power in FP32 pairs
     float *ani_r = nullptr, *ani_E = nullptr;         // FP32 refinement: residual, correction
@@ -1890,6 +1895,7 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
     CK(dalloc(sc->allocs, sc->tinfg, (size_t)ngd * lph * es), "alloc tinfg");
     CK(cudaMemsetAsync(sc->tinfg, 0, (size_t)ngd * lph * es, sc->st), "memset tinfg");
     CK(dalloc(sc->allocs, sc->q_sun, (size_t)sc->d.n_species * nd * es), "alloc qsun");
+    sc->qt_ok = false;
     CK(dalloc(sc->allocs, sc->hgv, (size_t)sc->d.n_species * (nd + ngd) * es), "alloc hgv");
     CK(dalloc(sc->allocs, sc->hg0v, (size_t)sc->d.n_species * es), "alloc hg0v");
     CK(dalloc(sc->allocs, sc->cellsum, (size_t)sc->d.n_species * nd * sizeof(double)), "alloc cellsum");
@@ -2112,12 +2118,18 @@ tursca_status tursca_assemble_flux(tursca_scene *sc, const tursca_geometry *geom
     }
     int p0 = prof_begin(sc, P_PRE);
     const cudaStream_t streams[4] = {sc->st, sc->aux[0], sc->aux[1], sc->aux[2]};
+    double key[6 + tk::MAX_SPECIES] = {vc.s0[0], vc.s0[1], vc.s0[2], vc.v[0], vc.v[1], vc.v[2]};
+    for (int sp = 0; sp < tk::MAX_SPECIES; ++sp) key[6 + sp] = sp < g.S ? vc.g[sp] : 0.0;
+    bool tables = !sc->qt_ok;
+    for (int k = 0; k < 6 + tk::MAX_SPECIES; ++k) tables = tables || key[k] != sc->qt_key[k];
     if (sc->d.precision == TURSCA_FP64)
-        tk::launch_assemble_pre<double>(streams, sc->fork, g, gp, field_p<double>(sc), vc, vp, sc->segtab_d,
+        tk::launch_assemble_pre<double>(streams, sc->fork, g, gp, field_p<double>(sc), vc, vp, sc->segtab_d, tables,
                                         &sc->launches);
     else
-        tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, sc->segtab_f,
+        tk::launch_assemble_pre<float>(streams, sc->fork, g, gp, field_p<float>(sc), vc, vp, sc->segtab_f, tables,
                                        &sc->launches);
+    sc->qt_ok = true;
+    for (int k = 0; k < 6 + tk::MAX_SPECIES; ++k) sc->qt_key[k] = key[k];
     prof_end(sc, p0);
     sc->c_eff = sc->c_min;
     sc->n_couplings = sc->n_kept = -1;

@@ -297,7 +297,7 @@ __host__ __device__ __forceinline__ int slot_src(const GridC &g, int row, int x,
 // st[0]: scene stream; st[1..3]: auxiliary streams; ev: five events (no timing)
 template <typename T>
 void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], const GridC &g, const GraphP &gp,
-                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, const SegTab<T> &segtab,
+                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, const SegTab<T> &segtab, bool tables,
                          long long *launches);
 // the fused edge march + edge weights over all receiver rows
 template <typename T>

@@ -224,14 +224,13 @@ __device__ __forceinline__ T ray_tau_block(const GridC &g, const RTap *__restric
     return (a0 + a1) + (a2 + a3);
 }
 
-// grid (ceil(nxy / kRayBlock), nz + 1): blockIdx.y = node layer (nz: the ground)
+// The direct beam of node (x, y) of layer L (nz: the ground), r its index in
+// the layer (r >= nxy: a padding thread, which still takes part in the
+// block's tap staging): T_sun from the ray's optical depth, e1, and their
+// stores; returns e1 (0 for padding threads).
 template <typename T>
-__global__ void __launch_bounds__(kRayBlock) k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
-    __shared__ RayTap<T> stap[kRayChunk];
-    const int L = blockIdx.y;
-    const int r = blockIdx.x * kRayBlock + threadIdx.x;
-    const int rr = r < g.nxy ? r : 0;
-    const int y = rr / g.nx, x = rr - y * g.nx;
+__device__ __forceinline__ T sun_node(const GridC &g, const FieldP<T> &f, const ViewC &vc, const ViewP &vp, int L,
+                                      int r, int x, int y, RayTap<T> *stap) {
     const int Zs = L < g.nz ? L + 1 : 0;  // ray start: top face of layer L, or the ground point
     const T *len;
     if constexpr (sizeof(T) == 4)
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(kRayBlock) k_sun(GridC g, FieldP<T> f, ViewC v
         len = (const T *)vp.sun_len_d;
     const T tau = ray_tau_block<T>(g, vp.sun_rt, len, f.mu_x, __ldg(vp.sun_off + Zs), __ldg(vp.sun_n + Zs), x, y,
                                    stap);
-    if (r >= g.nxy) return;
+    if (r >= g.nxy) return T(0);
     const T Ts = dexp<T>(-tau);
     const T base = (T)(vc.f0 * vc.mu0 * g.hx * g.hy);
     if (L < g.nz) {
@@ -251,13 +250,24 @@ __global__ void __launch_bounds__(kRayBlock) k_sun(GridC g, FieldP<T> f, ViewC v
         const T e = om * base * Ts * (-dexpm1<T>(-me * (T)(g.hz / vc.mu0)));
         f.e1[i] = e;
         store_halo(f.e1_h, g, x, y, L, e);
-    } else {
-        const int i = g.n_atm + r;
-        f.tsun[i] = Ts;
-        const T e = (T)vc.albedo * base * Ts;
-        f.e1[i] = e;
-        store_halo(f.e1_h, g, x, y, g.nz, e);
+        return e;
     }
+    const int i = g.n_atm + r;
+    f.tsun[i] = Ts;
+    const T e = (T)vc.albedo * base * Ts;
+    f.e1[i] = e;
+    store_halo(f.e1_h, g, x, y, g.nz, e);
+    return e;
+}
+
+// grid (ceil(nxy / kRayBlock), nz + 1): blockIdx.y = node layer (nz: the ground)
+template <typename T>
+__global__ void __launch_bounds__(kRayBlock) k_sun(GridC g, FieldP<T> f, ViewC vc, ViewP vp) {
+    __shared__ RayTap<T> stap[kRayChunk];
+    const int r = blockIdx.x * kRayBlock + threadIdx.x;
+    const int rr = r < g.nxy ? r : 0;
+    const int y = rr / g.nx, x = rr - y * g.nx;
+    sun_node<T>(g, f, vc, vp, blockIdx.y, r, x, y, stap);
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +449,8 @@ constexpr int kZnBlock = 128;
 constexpr int kZnMaxDir = 128;
 
 template <typename T, int S>
-__global__ void __launch_bounds__(kZnBlock) k_znorm(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
+__global__ void __launch_bounds__(kZnBlock) k_sunz(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp) {
+    __shared__ RayTap<T> stap[kRayChunk];
     __shared__ int sdh[kZnMaxDir];
     __shared__ T sw[kZnMaxDir][1 + S];
     __shared__ T sq[kZnMaxDir][1 + S];   // q of the directions with a receiver (0: none)
@@ -448,6 +459,15 @@ __global__ void __launch_bounds__(kZnBlock) k_znorm(GridC g, GraphP gp, FieldP<T
     const int L = blockIdx.y;
     const bool ground = L == g.nz;
     const int ndir = ground ? g.ngd : g.nd;
+    // the direct beam of the block's nodes (the rays of k_sun), kept for the
+    // source records below
+    T e1;
+    {
+        const int r = blockIdx.x * kZnBlock + threadIdx.x;
+        const int rr = r < g.nxy ? r : 0;
+        const int y = rr / g.nx, x = rr - y * g.nx;
+        e1 = sun_node<T>(g, f, vc, vp, L, r, x, y, stap);
+    }
     const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     for (int u = threadIdx.x; u < ndir; u += blockDim.x) {
         T w[1 + S], qq[1 + S], gg[1 + S];
@@ -547,7 +567,6 @@ __global__ void __launch_bounds__(kZnBlock) k_znorm(GridC g, GraphP gp, FieldP<T
     // (negated when c^sun = 1; a ground source: e1 a_iso, negated when c = 1)
     constexpr int RS = srec_stride(S);
     T rec[RS];
-    const T e1 = f.e1[i];
     rec[0] = ai;
 #pragma unroll
     for (int k = 1; k < RS; ++k) {
@@ -750,7 +769,11 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM_MINB)
 // sqrt(mu_s(n1)) is the row's own value when the first receiver is the
 // receiver itself (bit 12 of the descriptor); only the optical depths the
 // slot's kind needs are read.  g^sun is accumulated per species (the species
-// weights of the receiver applied once at the end).
+// weights of the receiver applied once at the end).  The block first copies
+// its layer's template (the slot descriptors, with each slot's q^sun and HG
+// weight toward the instrument per species looked up once) into shared
+// memory, so a warp's step to its next slot costs a shared-memory read
+// instead of a dependent global round trip.
 template <typename T, int RS>
 struct Rec;
 template <>
@@ -839,20 +862,61 @@ __device__ __forceinline__ void slot_fast(const GridC &g, const FieldP<T> &f, co
     }
 }
 
-// blocks per SM the register budget of k_asm0 allows
+// Warps per group and register budget (blocks per SM) of k_asm0.
+#ifndef TK_ASM0_W
+#define TK_ASM0_W 8
+#endif
 #ifndef TK_ASM0_MINB
 #define TK_ASM0_MINB 3
 #endif
-template <typename T, int S>
-__global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
+// int4 words of a slot descriptor the kernel reads (FP32: the first 64 bytes)
+template <typename T>
+__host__ __device__ constexpr int asm0_words() { return sizeof(T) == 4 ? 4 : 6; }
+// dynamic shared memory of k_asm0: per slot of the group's template its
+// descriptor words and 2 S constants (q^sun and the HG weight toward the
+// instrument per species); after the slot loop the same space holds the
+// warps' partial sums of s and g^sun ([W][4 + 4 S][32])
+template <typename T, int W>
+inline size_t asm0_smem(const GridC &g) {
+    const size_t desc = (size_t)g.ntmax * (16 * asm0_words<T>() + 2 * g.S * sizeof(T));
+    const size_t red = (size_t)W * (4 + 4 * g.S) * 32 * sizeof(T);
+    return desc > red ? desc : red;
+}
+template <typename T, int S, int W, int MINB>
+__global__ void __launch_bounds__(32 * W, MINB)
     k_asm0(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
     constexpr int RS = srec_stride(S);
-    __shared__ T sh[kAsmW][4 + 4 * S][32];
+    constexpr int NW = asm0_words<T>();
+    extern __shared__ __align__(16) unsigned char asm0_dyn[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
     const bool ground_row = G.z == g.nz;
-    const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     const int ndir = g.nd + g.ngd;
+    int4 *sdesc = reinterpret_cast<int4 *>(asm0_dyn);
+    T *sconst = reinterpret_cast<T *>(sdesc + (size_t)NW * G.nt);
+    {
+        // the group's template: descriptors and the per-slot direction constants
+        for (int t = threadIdx.x; t < G.nt; t += 32 * W) {
+            const int4 *src = reinterpret_cast<const int4 *>(gp.aslot + G.t0 + t);
+            int4 d[NW];
+#pragma unroll
+            for (int e = 0; e < NW; ++e) d[e] = __ldg(src + e);
+#pragma unroll
+            for (int e = 0; e < NW; ++e) sdesc[(size_t)t * NW + e] = d[e];
+            const int bits = d[1].z, dir = d[1].w, hgdir = d[2].x;
+            const bool gsrc = (bits >> 11) & 1;
+            T q;
+            if constexpr (sizeof(T) == 4) q = __int_as_float(d[3].y);
+            else q = __longlong_as_double(((long long)d[4].y << 32) | (unsigned)d[4].x);
+#pragma unroll
+            for (int sp = 0; sp < S; ++sp) {
+                sconst[(size_t)t * 2 * S + sp] = !gsrc ? f.q_sun[sp * g.nd + dir] : (sp == 0 ? q : T(0));
+                sconst[(size_t)t * 2 * S + S + sp] = ground_row ? T(0) : f.hgv[sp * ndir + hgdir];
+            }
+        }
+        __syncthreads();
+    }
+    const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     T rho[4], rtr[4];
     int rowc[4];
 #pragma unroll
@@ -872,40 +936,45 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
 #pragma unroll
         for (int sp = 0; sp < S; ++sp) acc_g[k][sp] = T(0);
     T *vout = f.val + G.vb + 4 * lane;
-    for (int t = w; t < G.nt; t += kAsmW) {
-        const ASlot &d = gp.aslot[G.t0 + t];
-        const int4 a0 = __ldg(reinterpret_cast<const int4 *>(&d));
-        const int4 a1 = __ldg(reinterpret_cast<const int4 *>(&d) + 1);
-        const int4 a2 = __ldg(reinterpret_cast<const int4 *>(&d) + 2);
-        const int src = a0.x, pre = a0.y, seg = a0.z, n1 = a0.w;
-        const int aux = a1.x, tbase = a1.y, bits = a1.z, dir = a1.w;
-        const int hgdir = a2.x, taps = a2.y, pre_off = a2.z, seg_off = a2.w;
+    for (int t = w; t < G.nt; t += W) {
+        int4 a0, a1, a2;
         int hit_off;
         T q, dinv, split;
-        if constexpr (sizeof(T) == 4) {
-            const float4 a3 = __ldg(reinterpret_cast<const float4 *>(&d) + 3);
-            hit_off = __float_as_int(a3.x);
-            q = a3.y;
-            dinv = a3.z;
-            split = a3.w;
-        } else {
-            hit_off = __ldg(&d.hit_off);
-            q = aslot_q<T>(d);
-            dinv = aslot_dinv<T>(d);
-            split = aslot_split<T>(d);
+        T qsun[S], hv[S];
+        {
+            const int4 *d = sdesc + (size_t)t * NW;
+            a0 = d[0];
+            a1 = d[1];
+            a2 = d[2];
+            if constexpr (sizeof(T) == 4) {
+                const float4 a3 = reinterpret_cast<const float4 *>(d)[3];
+                hit_off = __float_as_int(a3.x);
+                q = a3.y;
+                dinv = a3.z;
+                split = a3.w;
+            } else {
+                hit_off = d[3].x;
+                const double2 b0 = reinterpret_cast<const double2 *>(d)[4];
+                const double2 b1 = reinterpret_cast<const double2 *>(d)[5];
+                q = b0.x;
+                dinv = b0.y;
+                split = b1.x;
+            }
+#pragma unroll
+            for (int sp = 0; sp < S; ++sp) {
+                qsun[sp] = sconst[(size_t)t * 2 * S + sp];
+                hv[sp] = sconst[(size_t)t * 2 * S + S + sp];
+            }
         }
+        const int src = a0.x, pre = a0.y, seg = a0.z, n1 = a0.w;
+        const int aux = a1.x, tbase = a1.y, bits = a1.z;
+        const int taps = a2.y, pre_off = a2.z, seg_off = a2.w;
         const int kind = bits & 15, bkind = (bits >> 4) & 15;
         const bool c_one = (bits >> 8) & 1, n1_ground = (bits >> 9) & 1, has_pre = (bits >> 10) & 1;
-        const bool gsrc = (bits >> 11) & 1, n1_row = (bits >> 12) & 1;
+        const bool n1_row = (bits >> 12) & 1;
         const int ft = (bits >> 13) & 3;
         const int pre_n = taps & 0xff, seg_n = (taps >> 8) & 0xff, hit_n = (taps >> 16) & 0xff;
         const T qd = q * dinv;
-        T qsun[S], hv[S];
-#pragma unroll
-        for (int sp = 0; sp < S; ++sp) {
-            qsun[sp] = !gsrc ? f.q_sun[sp * g.nd + dir] : (sp == 0 ? q : T(0));
-            hv[sp] = ground_row ? T(0) : f.hgv[sp * ndir + hgdir];
-        }
         T kv[4];
         if (ft == 1) {
             if (has_pre)
@@ -993,6 +1062,8 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
         }
         st_quad_cs(vout + (size_t)t * kGroup, kv);
     }
+    __syncthreads();  // every warp is done with the staged template
+    T(*sh)[4 + 4 * S][32] = reinterpret_cast<T(*)[4 + 4 * S][32]>(asm0_dyn);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         sh[w][k][lane] = acc_s[k];
@@ -1006,7 +1077,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
             if (G.row[k] < 0) continue;
             T a = T(0);
 #pragma unroll
-            for (int qq = 0; qq < kAsmW; ++qq) a += sh[qq][k][lane];
+            for (int qq = 0; qq < W; ++qq) a += sh[qq][k][lane];
             f.s[G.row[k]] = a;
             if (!ground_row) {
                 T b = T(0);
@@ -1014,7 +1085,7 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
                 for (int sp = 0; sp < S; ++sp) {
                     T c = T(0);
 #pragma unroll
-                    for (int qq = 0; qq < kAsmW; ++qq) c += sh[qq][4 + 4 * sp + k][lane];
+                    for (int qq = 0; qq < W; ++qq) c += sh[qq][4 + 4 * sp + k][lane];
                     b += f.wsp[(size_t)sp * g.n_atm + G.row[k]] * c;
                 }
                 f.gsun[G.row[k]] = b;
@@ -1023,32 +1094,39 @@ __global__ void __launch_bounds__(32 * kAsmW, TK_ASM0_MINB)
     }
 }
 
-// Per-scene tables.  Dependencies: prep -> {segtau -> tinf, tinfg, sun};
-// tables, sun -> znorm.  st[0] is the scene stream; st[1..3] are auxiliary
-// streams forked from it and joined back with events, so the independent
-// tables run concurrently.
+// Per-scene tables.  Dependencies: prep -> {segtau -> tinf, tinfg, sunz};
+// quadrature tables -> sunz (the direct beam, then the coupling normalisers
+// and the source records, in one pass).  st[0] is the scene stream; st[1..3]
+// are auxiliary streams forked from it and joined back with events, so the
+// independent tables run concurrently.  The quadrature tables (q^sun, the HG
+// weights toward the instrument) depend on the view and the asymmetries
+// only: `tables` false skips them when the caller knows they are current.
 template <typename T>
-void launch_znorm(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc) {
+void launch_sunz(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                 const ViewP &vp) {
+    static_assert(kZnBlock == kRayBlock, "the direct beam and the normalisers share the thread layout");
     const dim3 grid((g.nxy + kZnBlock - 1) / kZnBlock, g.nz + 1);
     switch (g.S) {
-        case 1: k_znorm<T, 1><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc); break;
-        case 2: k_znorm<T, 2><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc); break;
-        case 3: k_znorm<T, 3><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc); break;
-        default: k_znorm<T, 4><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc); break;
+        case 1: k_sunz<T, 1><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc, vp); break;
+        case 2: k_sunz<T, 2><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc, vp); break;
+        case 3: k_sunz<T, 3><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc, vp); break;
+        default: k_sunz<T, 4><<<grid, kZnBlock, 0, st>>>(g, gp, f, vc, vp); break;
     }
 }
 
 template <typename T>
 void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], const GridC &g, const GraphP &gp,
-                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, const SegTab<T> &segtab,
+                         const FieldP<T> &f, const ViewC &vc, const ViewP &vp, const SegTab<T> &segtab, bool tables,
                          long long *launches) {
     const int th = 256;
     // ev[0]: start (orders the aux streams after earlier work of the scene stream)
     cudaEventRecord(ev[0], st[0]);
-    cudaStreamWaitEvent(st[1], ev[0], 0);
-    k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st[1]>>>(g, f, vc, vp);
-    k_tables_norm<T><<<g.S, 128, 0, st[1]>>>(g, f, vc, vp);
-    cudaEventRecord(ev[2], st[1]);
+    if (tables) {
+        cudaStreamWaitEvent(st[1], ev[0], 0);
+        k_tables_cells<T><<<dim3(g.nd, g.S), 128, 0, st[1]>>>(g, f, vc, vp);
+        k_tables_norm<T><<<g.S, 128, 0, st[1]>>>(g, f, vc, vp);
+        cudaEventRecord(ev[2], st[1]);
+    }
     cudaMemsetAsync(f.mus_max_bits, 0, sizeof(unsigned long long), st[0]);
     k_prep<T><<<(g.n_atm + th - 1) / th, th, 0, st[0]>>>(g, f);
     cudaEventRecord(ev[1], st[0]);  // fields ready
@@ -1065,23 +1143,28 @@ void launch_assemble_pre(cudaStream_t const st[4], cudaEvent_t const ev[5], cons
     cudaStreamWaitEvent(st[3], ev[1], 0);
     k_tinfg<T><<<dim3((g.nxy + kRayBlock - 1) / kRayBlock, g.ngd), kRayBlock, 0, st[3]>>>(g, gp, f);
     cudaEventRecord(ev[4], st[3]);
-    k_sun<T><<<dim3((g.nxy + kRayBlock - 1) / kRayBlock, g.nz + 1), kRayBlock, 0, st[0]>>>(g, f, vc, vp);
-    cudaStreamWaitEvent(st[0], ev[2], 0);
-    launch_znorm<T>(st[0], g, gp, f, vc);
+    if (tables) cudaStreamWaitEvent(st[0], ev[2], 0);
+    launch_sunz<T>(st[0], g, gp, f, vc, vp);
     cudaStreamWaitEvent(st[0], ev[3], 0);
     cudaStreamWaitEvent(st[0], ev[4], 0);
-    if (launches) *launches += 8;
+    if (launches) *launches += tables ? 7 : 5;
 }
 
 template <typename T>
 void launch_assemble_rows(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                           long long *launches) {
     const int nb = (g.nz + 1) * g.gpl;
+    constexpr int W0 = TK_ASM0_W, B0 = TK_ASM0_MINB;
+    const size_t sm = asm0_smem<T, W0>(g);
+    auto go = [&](auto kern) {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<nb, 32 * W0, sm, st>>>(g, gp, f, vc);
+    };
     switch (g.S) {  // the species count as a compile-time constant
-        case 1: k_asm0<T, 1><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        case 2: k_asm0<T, 2><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        case 3: k_asm0<T, 3><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
-        default: k_asm0<T, 4><<<nb, 32 * kAsmW, 0, st>>>(g, gp, f, vc); break;
+        case 1: go(k_asm0<T, 1, W0, B0>); break;
+        case 2: go(k_asm0<T, 2, W0, B0>); break;
+        case 3: go(k_asm0<T, 3, W0, B0>); break;
+        default: go(k_asm0<T, 4, W0, B0>); break;
     }
     if (launches) *launches += 1;
 }
@@ -1135,7 +1218,7 @@ void launch_assemble_direct(cudaStream_t st, const GridC &g, const FieldP<T> &f,
                                             const ViewC &, long long *);                                          \
     template void launch_assemble_pre<T>(cudaStream_t const[4], cudaEvent_t const[5], const GridC &,              \
                                          const GraphP &, const FieldP<T> &, const ViewC &, const ViewP &,         \
-                                         const SegTab<T> &, long long *);                                         \
+                                         const SegTab<T> &, bool, long long *);                                   \
     template void launch_assemble_rows<T>(cudaStream_t, const GridC &, const GraphP &, const FieldP<T> &,         \
                                           const ViewC &, long long *);                                            \
     template void launch_export_csr<T>(cudaStream_t, const GridC &, const GraphP &, const T *, int32_t *,         \
