@@ -1319,6 +1319,17 @@ tursca_status ensure_select(tursca_scene *sc) {
        "alloc select");
     CK(dalloc(sc->allocs, q.musmax_bits, sizeof(unsigned long long)), "alloc select");
     q.dmax = std::max(nd, ngd);
+    {
+        const size_t nn = (size_t)sc->G.n_nodes;
+        int ht = 1;
+        while ((size_t)ht < 2 * nn) ht <<= 1;
+        q.ht = ht;
+        CK(dalloc(sc->allocs, q.mask, nn * sizeof(ulonglong2)), "alloc select");
+        CK(dalloc(sc->allocs, q.rep, nn * sizeof(int)), "alloc select");
+        CK(dalloc(sc->allocs, q.table, (size_t)ht * sizeof(int)), "alloc select");
+        CK(dalloc(sc->allocs, q.pcnt, nn * q.dmax * sizeof(int)), "alloc select");
+        CK(dalloc(sc->allocs, q.ph, nn * sc->d.n_species * q.dmax * sc->es), "alloc select");
+    }
     const size_t plane = (size_t)grid_c(sc).npad * sc->es;
     CK(dalloc(sc->allocs, sc->w_iso, q.dmax * plane), "alloc select weights");
     CK(dalloc(sc->allocs, sc->w_sun, q.dmax * plane), "alloc select weights");

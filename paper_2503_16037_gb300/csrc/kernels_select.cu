@@ -71,96 +71,193 @@ __global__ void k_sel_consts(GridC g, SelP sp, const double *cellsum, T *hgpt_t,
     }
 }
 
-// One warp per source node.  The values (weights, sums, normalisers) are in
-// the compute type T; the decisions (kept or not, which kept direction a
-// point joins) are exact.
+// The source of a selection warp and its total scattering coefficient: FP64
+// on FP64 scenes; FP32 scenes take the FP32 sum and the FP64 one only near
+// the threshold.
 template <typename T>
-__global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp,
-                                                          SelP sp, const T *hgpt, const T *cellsum, const T *htot_g,
-                                                          T *w_iso, T *w_sun) {
+struct SelSrc {
+    bool ground;
+    int j, x, y, z, nd;
+    double mus_lamb, mus_src64;
+    T mus_src;
+};
+template <typename T>
+__device__ __forceinline__ SelSrc<T> sel_src(const GridC &g, const FieldP<T> &f, const ViewC &vc, const SelP &sp,
+                                             int j) {
+    SelSrc<T> o;
+    o.j = j;
+    o.mus_lamb = vc.albedo * __longlong_as_double((long long)*sp.musmax_bits);
+    o.ground = j >= g.n_atm;
+    const int jj = o.ground ? j - g.n_atm : j;
+    o.z = o.ground ? g.nz : jj / g.nxy;
+    const int r = jj - (o.ground ? 0 : o.z * g.nxy);
+    o.y = r / g.nx;
+    o.x = r - o.y * g.nx;
+    o.nd = o.ground ? g.ngd : g.nd;
+    o.mus_src64 = (sizeof(T) == 8) ? (o.ground ? o.mus_lamb : mus64(g, f, j)) : 0.0;
+    o.mus_src = (sizeof(T) == 8) ? (T)o.mus_src64 : (o.ground ? (T)o.mus_lamb : f.mu_st[j]);
+    return o;
+}
+
+// The coupling C of chain u of the source (-1: the chain has no receiver) and
+// whether the chain is kept (always, without a receiver).
+template <typename T>
+__device__ __forceinline__ void sel_chain(const GridC &g, const GraphP &gp, const FieldP<T> &f, const SelP &sp,
+                                          const SelSrc<T> &src, int u, T &C, bool &keep) {
+    C = T(-1);
+    keep = true;
+    int nidx = -1;  // receiver voxel (-1: the ground)
+    bool recv = false;
+    T dist = T(1);
+    const int x = src.x, y = src.y, z = src.z;
+    if (!src.ground) {
+        const int4 d = gp.dirs[u];
+        const int rz = z + d.z;
+        if (rz < g.nz) {
+            recv = true;
+            if (rz >= 0) {
+                const int xn = wrap_small(x + d.x, g.nx), yn = wrap_small(y + d.y, g.ny);
+                nidx = (rz * g.ny + yn) * g.nx + xn;
+                dist = Cst<T>::dir_len(gp, u);
+            } else {  // the chain hits the ground before its first node
+                dist = ((T)z + T(0.5)) / (T)(-d.z) * Cst<T>::dir_len(gp, u);
+            }
+        }
+    } else {
+        const int4 m = gp.gmem1[u];
+        if ((double)m.z - 0.5 <= (double)g.nz) {
+            recv = true;
+            const int xn = wrap_small(x + m.x, g.nx), yn = wrap_small(y + m.y, g.ny);
+            nidx = ((m.z - 1) * g.ny + yn) * g.nx + xn;
+            dist = Cst<T>::gdist1(gp, u);
+        }
+    }
+    // the FP64 distance to the first receiver (the oracle's arithmetic)
+    auto dist64 = [&]() -> double {
+        if (src.ground) return gp.gdist1[u];
+        const int dz = gp.dirs[u].z;
+        return z + dz >= 0 ? gp.dir_len[u] : ((double)z + 0.5) / (double)(-dz) * gp.dir_len[u];
+    };
+    if (recv) {
+        if constexpr (sizeof(T) == 4) {
+            // FP32 value (relative error below 1e-6); the FP64 coupling
+            // decides only where the FP32 one is that close to c_min
+            const float mus_n = nidx >= 0 ? f.mu_st[nidx] : (float)src.mus_lamb;
+            const float c32 = sqrtf(src.mus_src * mus_n) / dist;
+            C = c32;
+            if (sp.c_min > 0.0) {
+                if (fabs((double)c32 - sp.c_min) > 1e-5 * sp.c_min) {
+                    keep = (double)c32 > sp.c_min;
+                } else {
+                    const double ms = src.ground ? src.mus_lamb : mus64(g, f, src.j);
+                    const double mn = nidx >= 0 ? mus64(g, f, nidx) : src.mus_lamb;
+                    keep = sqrt(ms * mn) / dist64() > sp.c_min;
+                }
+            }
+        } else {
+            const double mn = nidx >= 0 ? mus64(g, f, nidx) : src.mus_lamb;
+            C = sqrt(src.mus_src64 * mn) / dist64();
+            keep = !(sp.c_min > 0.0) || C > sp.c_min;
+        }
+    }
+}
+
+// Which directions a source keeps (bit u of its mask) fixes how its lattice
+// points are re-drawn: the re-partition is a function of the kept set (and of
+// whether the source is a ground node) alone, so it is computed once per
+// distinct kept set.  Pass 1 (one warp per source): the mask, and whether the
+// source has anything to re-draw (some direction dropped and some kept):
+// rep = -2 if so, else -1.
+template <typename T>
+__global__ void __launch_bounds__(32 * kSelWarps) k_sel_mask(GridC g, GraphP gp, FieldP<T> f, ViewC vc, SelP sp) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kSelWarps + w;
+    if (j >= g.n_nodes) return;  // whole warps leave together
+    const SelSrc<T> src = sel_src(g, f, vc, sp, j);
+    unsigned long long m0 = 0ull, m1 = 0ull;
+    int nl = 0, nk = 0;
+    for (int b = 0; b < kSelMaxDir / 32; ++b) {
+        const int u = b * 32 + lane;
+        bool keep = false;
+        if (u < src.nd) {
+            T C;
+            sel_chain(g, gp, f, sp, src, u, C, keep);
+        }
+        const unsigned mk = __ballot_sync(0xffffffffu, u < src.nd && keep);
+        const unsigned md = __ballot_sync(0xffffffffu, u < src.nd && !keep);
+        nk += __popc(mk);
+        nl += __popc(md);
+        if (b < 2) m0 |= (unsigned long long)mk << (32 * b);
+        else m1 |= (unsigned long long)mk << (32 * (b - 2));
+    }
+    if (lane == 0) {
+        sp.mask[j] = make_ulonglong2(m0, m1);
+        sp.rep[j] = (nl > 0 && nk > 0) ? -2 : -1;
+    }
+}
+
+__device__ __forceinline__ unsigned sel_hash(unsigned long long a, unsigned long long b, bool ground) {
+    unsigned long long h = a * 0x9E3779B97F4A7C15ull;
+    h ^= (b + 0x632BE59BD9B4E019ull) * 0xC2B2AE3D27D4EB4Full;
+    h ^= ground ? 0xD6E8FEB86659FD93ull : 0ull;
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 32;
+    return (unsigned)h;
+}
+
+// Pass 2 (one thread per source with something to re-draw): the first source
+// of each distinct (kept set, ground) to claim a slot of the open-addressing
+// table becomes its representative; every other source finds it by linear
+// probing.  Which source wins depends on timing, but the re-partition it
+// computes is the same function of the kept set, so the weights are too.
+// The table has at least twice as many slots as sources and is cleared
+// before the pass, so a free slot is always found.
+__global__ void k_sel_dedupe(int n, int n_atm, SelP sp) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n || sp.rep[j] != -2) return;
+    const ulonglong2 m = sp.mask[j];
+    const bool ground = j >= n_atm;
+    unsigned h = sel_hash(m.x, m.y, ground) & (unsigned)(sp.ht - 1);
+    for (int probe = 0; probe < sp.ht; ++probe) {
+        const int old = atomicCAS(sp.table + h, -1, j);
+        if (old == -1) {
+            sp.rep[j] = j;
+            return;
+        }
+        const ulonglong2 mo = sp.mask[old];
+        if (mo.x == m.x && mo.y == m.y && (old >= n_atm) == ground) {
+            sp.rep[j] = old;
+            return;
+        }
+        h = (h + 1) & (unsigned)(sp.ht - 1);
+    }
+}
+
+// Pass 3 (one warp per representative source): the points of every dropped
+// cell join their closest kept direction; the point counts and the HG sums of
+// every direction after the re-draw go to pcnt / ph of the representative.
+// The values (sums) are in the compute type T; the decisions (which kept
+// direction a point joins) are exact.
+template <typename T>
+__global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, SelP sp, const T *hgpt,
+                                                            const T *cellsum) {
     __shared__ int s_cnt[kSelWarps][kSelMaxDir];
     __shared__ T s_h[kSelWarps][MAX_SPECIES][kSelMaxDir];
-    __shared__ T s_c[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_kept[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_list[kSelWarps][kSelMaxDir];
     __shared__ unsigned char s_klist[kSelWarps][kSelMaxDir];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x * kSelWarps + w;
-    if (j >= g.n_nodes) return;  // whole warps leave together
+    if (j >= g.n_nodes || sp.rep[j] != j) return;  // whole warps leave together
     int *cnt = s_cnt[w];
-    T *cc = s_c[w];
     unsigned char *kept = s_kept[w];
-    const double mus_lamb = vc.albedo * __longlong_as_double((long long)*sp.musmax_bits);
     const bool ground = j >= g.n_atm;
-    const int jj = ground ? j - g.n_atm : j;
-    const int z = ground ? g.nz : jj / g.nxy, r = jj - (ground ? 0 : z * g.nxy), y = r / g.nx, x = r - y * g.nx;
     const int nd = ground ? g.ngd : g.nd;
-    // total scattering coefficient of the source: FP64 on FP64 scenes; FP32
-    // scenes take the FP32 sum and the FP64 one only near the threshold
-    const double mus_src64 = (sizeof(T) == 8) ? (ground ? mus_lamb : mus64(g, f, j)) : 0.0;
-    const T mus_src = (sizeof(T) == 8) ? (T)mus_src64 : (ground ? (T)mus_lamb : f.mu_st[j]);
-
-    // couplings of the chains and the kept set
-    int ndrop = 0;
+    const ulonglong2 mk = sp.mask[j];
     for (int u = lane; u < nd; u += 32) {
-        T C = T(-1);  // -1: the chain has no receiver
-        bool keep = true;
-        int nidx = -1;           // receiver voxel (-1: the ground)
-        bool recv = false;
-        T dist = T(1);
-        if (!ground) {
-            const int4 d = gp.dirs[u];
-            const int rz = z + d.z;
-            if (rz < g.nz) {
-                recv = true;
-                if (rz >= 0) {
-                    const int xn = wrap_small(x + d.x, g.nx), yn = wrap_small(y + d.y, g.ny);
-                    nidx = (rz * g.ny + yn) * g.nx + xn;
-                    dist = Cst<T>::dir_len(gp, u);
-                } else {  // the chain hits the ground before its first node
-                    dist = ((T)z + T(0.5)) / (T)(-d.z) * Cst<T>::dir_len(gp, u);
-                }
-            }
-        } else {
-            const int4 m = gp.gmem1[u];
-            if ((double)m.z - 0.5 <= (double)g.nz) {
-                recv = true;
-                const int xn = wrap_small(x + m.x, g.nx), yn = wrap_small(y + m.y, g.ny);
-                nidx = ((m.z - 1) * g.ny + yn) * g.nx + xn;
-                dist = Cst<T>::gdist1(gp, u);
-            }
-        }
-        // the FP64 distance to the first receiver (the oracle's arithmetic)
-        auto dist64 = [&]() -> double {
-            if (ground) return gp.gdist1[u];
-            const int dz = gp.dirs[u].z;
-            return z + dz >= 0 ? gp.dir_len[u] : ((double)z + 0.5) / (double)(-dz) * gp.dir_len[u];
-        };
-        if (recv) {
-            if constexpr (sizeof(T) == 4) {
-                // FP32 value (relative error below 1e-6); the FP64 coupling
-                // decides only where the FP32 one is that close to c_min
-                const float mus_n = nidx >= 0 ? f.mu_st[nidx] : (float)mus_lamb;
-                const float c32 = sqrtf(mus_src * mus_n) / dist;
-                C = c32;
-                if (sp.c_min > 0.0) {
-                    if (fabs((double)c32 - sp.c_min) > 1e-5 * sp.c_min) {
-                        keep = (double)c32 > sp.c_min;
-                    } else {
-                        const double ms = ground ? mus_lamb : mus64(g, f, j);
-                        const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
-                        keep = sqrt(ms * mn) / dist64() > sp.c_min;
-                    }
-                }
-            } else {
-                const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
-                C = sqrt(mus_src64 * mn) / dist64();
-                keep = !(sp.c_min > 0.0) || C > sp.c_min;
-            }
-        }
+        const bool keep = ((u < 64 ? mk.x >> u : mk.y >> (u - 64)) & 1ull) != 0ull;
         kept[u] = keep;
-        cc[u] = C;
-        ndrop += !keep;
         if (!ground) {
             cnt[u] = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
             for (int s = 0; s < g.S; ++s) s_h[w][s][u] = keep ? cellsum[s * g.nd + u] : T(0);
@@ -168,30 +265,27 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
             s_h[w][0][u] = keep ? (T)sp.gzsum[u] : T(0);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) ndrop += __shfl_xor_sync(0xffffffffu, ndrop, o);
     __syncwarp();
 
-    // the points of every dropped cell join their closest kept direction: a
-    // lane walks whole cells, whose points are ordered by their rankings, so
-    // the target changes rarely and the lane adds a run at a time.  With many
-    // kept directions a point's target is the first kept one in its ranking;
-    // with few, the largest FP32 cosine over the kept list picks it, and exact
-    // FP64 cosines (the ranking's arithmetic) decide near-ties.  A source
-    // that keeps nothing has nothing to re-assign.
+    // a lane walks whole cells, whose points are ordered by their rankings,
+    // so the target changes rarely and the lane adds a run at a time.  With
+    // many kept directions a point's target is the first kept one in its
+    // ranking; with few, the largest FP32 cosine over the kept list picks it,
+    // and exact FP64 cosines (the ranking's arithmetic) decide near-ties.
     unsigned char *list = s_list[w], *klist = s_klist[w];
     int nl = 0, nk = 0;
     for (int b = 0; b < nd; b += 32) {
         const int u = b + lane;
         const bool dr = u < nd && !kept[u], kp = u < nd && kept[u];
-        const unsigned m = __ballot_sync(0xffffffffu, dr), mk = __ballot_sync(0xffffffffu, kp);
+        const unsigned m = __ballot_sync(0xffffffffu, dr), mkb = __ballot_sync(0xffffffffu, kp);
         const unsigned below = (1u << lane) - 1u;
         if (dr) list[nl + __popc(m & below)] = (unsigned char)u;
-        if (kp) klist[nk + __popc(mk & below)] = (unsigned char)u;
+        if (kp) klist[nk + __popc(mkb & below)] = (unsigned char)u;
         nl += __popc(m);
-        nk += __popc(mk);
+        nk += __popc(mkb);
     }
     __syncwarp();
-    if (nl > 0 && nk > 0) {
+    {
         const unsigned char *rk = ground ? sp.grank : sp.rank;
         const int *cs = ground ? sp.gcell_start : vp.cell_start;
         const float4 *pf = ground ? sp.glatf : sp.latf;
@@ -267,14 +361,35 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
         }
     }
     __syncwarp();
+    T *ph = reinterpret_cast<T *>(sp.ph) + (size_t)j * g.S * sp.dmax;
+    for (int u = lane; u < nd; u += 32) {
+        sp.pcnt[(size_t)j * sp.dmax + u] = cnt[u];
+        for (int s = 0; s < (ground ? 1 : g.S); ++s) ph[(size_t)s * sp.dmax + u] = s_h[w][s][u];
+    }
+}
 
-    // weights and routing normalisers over the chains with a receiver
+// Pass 4 (one warp per source): the weights and routing normalisers over the
+// chains with a receiver, from the source's couplings and its kept set's
+// re-partition (the representative's, or the cells themselves when nothing
+// was re-drawn), into the haloed planes W = q' c.
+template <typename T>
+__global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp,
+                                                          SelP sp, const T *cellsum, const T *htot_g, T *w_iso,
+                                                          T *w_sun) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * kSelWarps + w;
+    if (j >= g.n_nodes) return;  // whole warps leave together
+    const SelSrc<T> src = sel_src(g, f, vc, sp, j);
+    const bool ground = src.ground;
+    const int nd = src.nd;
+    const int rep = sp.rep[j];
+    const T *ph = rep >= 0 ? reinterpret_cast<const T *>(sp.ph) + (size_t)rep * g.S * sp.dmax : nullptr;
     T wsp[MAX_SPECIES], rht[MAX_SPECIES];
     if (!ground) {
         for (int s = 0; s < g.S; ++s) {
             if constexpr (sizeof(T) == 8) {
                 const double ms = (double)f.mu_s[(size_t)s * g.n_atm + j];
-                wsp[s] = mus_src64 > 0.0 ? ms / mus_src64 : 1.0 / g.S;
+                wsp[s] = src.mus_src64 > 0.0 ? ms / src.mus_src64 : 1.0 / g.S;
             } else {
                 wsp[s] = f.wsp[(size_t)s * g.n_atm + j];
             }
@@ -283,28 +398,41 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     }
     const T rM = T(1) / (T)sp.M, rz = T(1) / (T)sp.gztot;
     T sq = 0, sqc = 0, sqs = 0, sqcs = 0;
-    T qiv[kSelMaxDir / 32], qsv[kSelMaxDir / 32];
+    T qiv[kSelMaxDir / 32], qsv[kSelMaxDir / 32], ccv[kSelMaxDir / 32];
 #pragma unroll
     for (int b = 0; b < kSelMaxDir / 32; ++b) {
         const int u = b * 32 + lane;
-        T qi = T(0), qs = T(0);
+        T qi = T(0), qs = T(0), C = T(-1);
         if (u < nd) {
+            bool keep;
+            sel_chain(g, gp, f, sp, src, u, C, keep);
             if (!ground) {
-                qi = (T)cnt[u] * rM;
-                for (int s = 0; s < g.S; ++s) qs += wsp[s] * (s_h[w][s][u] * rht[s]);
+                int cnt;
+                T h[MAX_SPECIES];
+                if (ph) {
+                    cnt = sp.pcnt[(size_t)rep * sp.dmax + u];
+                    for (int s = 0; s < g.S; ++s) h[s] = ph[(size_t)s * sp.dmax + u];
+                } else {
+                    cnt = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
+                    for (int s = 0; s < g.S; ++s) h[s] = keep ? cellsum[s * g.nd + u] : T(0);
+                }
+                qi = (T)cnt * rM;
+                for (int s = 0; s < g.S; ++s) qs += wsp[s] * (h[s] * rht[s]);
             } else {
-                qi = s_h[w][0][u] * rz;
+                const T h0 = ph ? ph[u] : (keep ? (T)sp.gzsum[u] : T(0));
+                qi = h0 * rz;
                 qs = qi;
             }
-            if (cc[u] >= T(0)) {
+            if (C >= T(0)) {
                 sq += qi;
-                sqc += qi * cc[u];
+                sqc += qi * C;
                 sqs += qs;
-                sqcs += qs * cc[u];
+                sqcs += qs * C;
             }
         }
         qiv[b] = qi;
         qsv[b] = qs;
+        ccv[b] = C;
     }
     for (int o = 16; o > 0; o >>= 1) {
         sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -318,11 +446,11 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     for (int b = 0; b < kSelMaxDir / 32; ++b) {
         const int u = b * 32 + lane;
         if (u >= nd) continue;
-        const T C = cc[u];
+        const T C = ccv[b];
         const T ci = (ci_on && C >= T(0)) ? C * fi : T(1);
         const T cs = (cs_on && C >= T(0)) ? C * fs : T(1);
-        store_halo(w_iso + (size_t)u * g.npad, g, x, y, z, qiv[b] * ci);
-        store_halo(w_sun + (size_t)u * g.npad, g, x, y, z, qsv[b] * cs);
+        store_halo(w_iso + (size_t)u * g.npad, g, src.x, src.y, src.z, qiv[b] * ci);
+        store_halo(w_sun + (size_t)u * g.npad, g, src.x, src.y, src.z, qsv[b] * cs);
     }
 }
 
@@ -338,9 +466,13 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
     k_sel_points<<<(sp.M + 127) / 128, 128, 0, st>>>(g, vc, sp.lat, sp.M, sp.hgpt);
     const int nc = std::max(g.S * sp.M, g.S * g.nd);
     k_sel_consts<T><<<(nc + 255) / 256, 256, 0, st>>>(g, sp, f.cellsum, hgpt_t, cellsum_t, htot_t);
-    k_select<T><<<(g.n_nodes + kSelWarps - 1) / kSelWarps, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, hgpt_t,
-                                                                                     cellsum_t, htot_t, w_iso, w_sun);
-    if (launches) *launches += 4;
+    const int nbw = (g.n_nodes + kSelWarps - 1) / kSelWarps;
+    k_sel_mask<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, sp);
+    cudaMemsetAsync(sp.table, 0xff, (size_t)sp.ht * sizeof(int), st);
+    k_sel_dedupe<<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g.n_nodes, g.n_atm, sp);
+    k_sel_part<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, vp, sp, hgpt_t, cellsum_t);
+    k_select<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, cellsum_t, htot_t, w_iso, w_sun);
+    if (launches) *launches += 7;
 }
 
 // ---------------------------------------------------------------------------

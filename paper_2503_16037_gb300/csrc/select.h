@@ -44,6 +44,13 @@ struct SelP {
     double *hgpt;                    // [S][M] HG toward each lattice point (order of the rankings), followed by
                                      // its compute-type copy, the cell sums [S][nd] and the totals [S] in it
     unsigned long long *musmax_bits; // max over voxels of the FP64 total scattering coefficient
+    // the re-partition once per distinct kept set
+    ulonglong2 *mask;                // [n_nodes] kept set of each source (bit u: direction u)
+    int *rep;                        // [n_nodes] source whose re-partition serves this one (-1: none needed)
+    int *table;                      // [ht] open-addressing table of kept sets (source index, -1: free)
+    int ht;                          // slots: a power of two, at least twice the sources
+    int *pcnt;                       // [n_nodes][dmax] point counts after the re-draw (representatives only)
+    void *ph;                        // [n_nodes][S][dmax] HG (ground: cosine) sums after the re-draw, compute type
 };
 
 // Weights W of every (source, direction) for the current fields and
