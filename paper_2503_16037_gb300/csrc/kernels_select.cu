@@ -267,11 +267,14 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
     }
     __syncwarp();
 
-    // a lane walks whole cells, whose points are ordered by their rankings,
-    // so the target changes rarely and the lane adds a run at a time.  With
-    // many kept directions a point's target is the first kept one in its
-    // ranking; with few, the largest FP32 cosine over the kept list picks it,
-    // and exact FP64 cosines (the ranking's arithmetic) decide near-ties.
+    // The points of the dropped cells, cell after cell, are dealt to the
+    // lanes round robin (lane l takes points l, l + 32, ... of that
+    // sequence), so every lane has work whatever the number of dropped cells.
+    // Inside a cell the points are ordered by their rankings, so a lane's
+    // target changes rarely and it adds a run at a time.  With many kept
+    // directions a point's target is the first kept one in its ranking; with
+    // few, the largest FP32 cosine over the kept list picks it, and exact
+    // FP64 cosines (the ranking's arithmetic) decide near-ties.
     unsigned char *list = s_list[w], *klist = s_klist[w];
     int nl = 0, nk = 0;
     for (int b = 0; b < nd; b += 32) {
@@ -293,11 +296,21 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
         const float4 *df = sp.dirf + (ground ? g.nd : 0);
         const double *dd = vp.dirhat + 3 * (ground ? g.nd : 0);
         const bool dots = nk <= kSelDots;
-        for (int i = lane; i < nl; i += 32) {
-            const int u = list[i];
-            int cur = -1, n = 0;
-            T a[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
-            for (int p = cs[u]; p < cs[u + 1]; ++p) {
+        int tot = 0;  // points of the dropped cells
+        for (int i = 0; i < nl; ++i) tot += cs[list[i] + 1] - cs[list[i]];
+        int ci = 0, off = lane;  // the lane's cell (index into list) and point offset inside it
+        int cur = -1, n = 0;
+        T a[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
+        for (int f0 = lane; f0 < tot; f0 += 32) {
+            int csz = cs[list[ci] + 1] - cs[list[ci]];
+            while (off >= csz) {
+                off -= csz;
+                ++ci;
+                csz = cs[list[ci] + 1] - cs[list[ci]];
+            }
+            const int p = cs[list[ci]] + off;
+            off += 32;
+            {
                 int v = -1;
                 if (dots) {
                     const float4 pt = pf[p];
@@ -354,10 +367,10 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
                     for (int s = 0; s < g.S; ++s) a[s] += hgpt[(size_t)s * sp.M + p];
                 }
             }
-            if (cur >= 0) {
-                if (!ground) atomicAdd(&cnt[cur], n);
-                for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
-            }
+        }
+        if (cur >= 0) {
+            if (!ground) atomicAdd(&cnt[cur], n);
+            for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
         }
     }
     __syncwarp();
