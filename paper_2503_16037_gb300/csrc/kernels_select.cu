@@ -165,35 +165,31 @@ __device__ __forceinline__ void sel_chain(const GridC &g, const GraphP &gp, cons
 // Which directions a source keeps (bit u of its mask) fixes how its lattice
 // points are re-drawn: the re-partition is a function of the kept set (and of
 // whether the source is a ground node) alone, so it is computed once per
-// distinct kept set.  Pass 1 (one warp per source): the mask, and whether the
-// source has anything to re-draw (some direction dropped and some kept):
-// rep = -2 if so, else -1.
+// distinct kept set.  Pass 1 (one thread per source, so that the threads of
+// a warp gather the first receivers of one direction from consecutive
+// voxels): the mask, and whether the source has anything to re-draw (some
+// direction dropped and some kept): rep = -2 if so, else -1.
 template <typename T>
-__global__ void __launch_bounds__(32 * kSelWarps) k_sel_mask(GridC g, GraphP gp, FieldP<T> f, ViewC vc, SelP sp) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * kSelWarps + w;
-    if (j >= g.n_nodes) return;  // whole warps leave together
+__global__ void k_sel_mask(GridC g, GraphP gp, FieldP<T> f, ViewC vc, SelP sp) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_nodes) return;
     const SelSrc<T> src = sel_src(g, f, vc, sp, j);
     unsigned long long m0 = 0ull, m1 = 0ull;
     int nl = 0, nk = 0;
-    for (int b = 0; b < kSelMaxDir / 32; ++b) {
-        const int u = b * 32 + lane;
-        bool keep = false;
-        if (u < src.nd) {
-            T C;
-            sel_chain(g, gp, f, sp, src, u, C, keep);
+    for (int u = 0; u < src.nd; ++u) {
+        T C;
+        bool keep;
+        sel_chain(g, gp, f, sp, src, u, C, keep);
+        if (keep) {
+            if (u < 64) m0 |= 1ull << u;
+            else m1 |= 1ull << (u - 64);
+            ++nk;
+        } else {
+            ++nl;
         }
-        const unsigned mk = __ballot_sync(0xffffffffu, u < src.nd && keep);
-        const unsigned md = __ballot_sync(0xffffffffu, u < src.nd && !keep);
-        nk += __popc(mk);
-        nl += __popc(md);
-        if (b < 2) m0 |= (unsigned long long)mk << (32 * b);
-        else m1 |= (unsigned long long)mk << (32 * (b - 2));
     }
-    if (lane == 0) {
-        sp.mask[j] = make_ulonglong2(m0, m1);
-        sp.rep[j] = (nl > 0 && nk > 0) ? -2 : -1;
-    }
+    sp.mask[j] = make_ulonglong2(m0, m1);
+    sp.rep[j] = (nl > 0 && nk > 0) ? -2 : -1;
 }
 
 __device__ __forceinline__ unsigned sel_hash(unsigned long long a, unsigned long long b, bool ground) {
@@ -381,24 +377,57 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
     }
 }
 
-// Pass 4 (one warp per source): the weights and routing normalisers over the
-// chains with a receiver, from the source's couplings and its kept set's
+// Pass 4 (one thread per source): the weights and routing normalisers over
+// the chains with a receiver, from the source's couplings and its kept set's
 // re-partition (the representative's, or the cells themselves when nothing
-// was re-drawn), into the haloed planes W = q' c.
+// was re-drawn), into the haloed planes W = q' c.  The first sweep over the
+// directions sums the normalisers, the second forms the weights again and
+// stores them (the threads of a warp store one direction's plane at
+// consecutive voxels).
 template <typename T>
-__global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp,
-                                                          SelP sp, const T *cellsum, const T *htot_g, T *w_iso,
-                                                          T *w_sun) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * kSelWarps + w;
-    if (j >= g.n_nodes) return;  // whole warps leave together
+struct SelQ {
+    T qi, qs, C;
+};
+template <typename T>
+__device__ __forceinline__ SelQ<T> sel_q(const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewP &vp,
+                                         const SelP &sp, const SelSrc<T> &src, int rep, const T *ph, const T *cellsum,
+                                         const T (&wsp)[MAX_SPECIES], const T (&rht)[MAX_SPECIES], T rM, T rz, int u) {
+    SelQ<T> o;
+    bool keep;
+    sel_chain(g, gp, f, sp, src, u, o.C, keep);
+    o.qi = T(0);
+    o.qs = T(0);
+    if (!src.ground) {
+        int cnt;
+        T h[MAX_SPECIES];
+        if (ph) {
+            cnt = sp.pcnt[(size_t)rep * sp.dmax + u];
+            for (int s = 0; s < g.S; ++s) h[s] = ph[(size_t)s * sp.dmax + u];
+        } else {
+            cnt = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
+            for (int s = 0; s < g.S; ++s) h[s] = keep ? cellsum[s * g.nd + u] : T(0);
+        }
+        o.qi = (T)cnt * rM;
+        for (int s = 0; s < g.S; ++s) o.qs += wsp[s] * (h[s] * rht[s]);
+    } else {
+        const T h0 = ph ? ph[u] : (keep ? (T)sp.gzsum[u] : T(0));
+        o.qi = h0 * rz;
+        o.qs = o.qi;
+    }
+    return o;
+}
+
+template <typename T>
+__global__ void k_select(GridC g, GraphP gp, FieldP<T> f, ViewC vc, ViewP vp, SelP sp, const T *cellsum,
+                         const T *htot_g, T *w_iso, T *w_sun) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.n_nodes) return;
     const SelSrc<T> src = sel_src(g, f, vc, sp, j);
-    const bool ground = src.ground;
     const int nd = src.nd;
     const int rep = sp.rep[j];
     const T *ph = rep >= 0 ? reinterpret_cast<const T *>(sp.ph) + (size_t)rep * g.S * sp.dmax : nullptr;
-    T wsp[MAX_SPECIES], rht[MAX_SPECIES];
-    if (!ground) {
+    T wsp[MAX_SPECIES] = {T(0), T(0), T(0), T(0)}, rht[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
+    if (!src.ground) {
         for (int s = 0; s < g.S; ++s) {
             if constexpr (sizeof(T) == 8) {
                 const double ms = (double)f.mu_s[(size_t)s * g.n_atm + j];
@@ -411,59 +440,23 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_select(GridC g, GraphP gp, F
     }
     const T rM = T(1) / (T)sp.M, rz = T(1) / (T)sp.gztot;
     T sq = 0, sqc = 0, sqs = 0, sqcs = 0;
-    T qiv[kSelMaxDir / 32], qsv[kSelMaxDir / 32], ccv[kSelMaxDir / 32];
-#pragma unroll
-    for (int b = 0; b < kSelMaxDir / 32; ++b) {
-        const int u = b * 32 + lane;
-        T qi = T(0), qs = T(0), C = T(-1);
-        if (u < nd) {
-            bool keep;
-            sel_chain(g, gp, f, sp, src, u, C, keep);
-            if (!ground) {
-                int cnt;
-                T h[MAX_SPECIES];
-                if (ph) {
-                    cnt = sp.pcnt[(size_t)rep * sp.dmax + u];
-                    for (int s = 0; s < g.S; ++s) h[s] = ph[(size_t)s * sp.dmax + u];
-                } else {
-                    cnt = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
-                    for (int s = 0; s < g.S; ++s) h[s] = keep ? cellsum[s * g.nd + u] : T(0);
-                }
-                qi = (T)cnt * rM;
-                for (int s = 0; s < g.S; ++s) qs += wsp[s] * (h[s] * rht[s]);
-            } else {
-                const T h0 = ph ? ph[u] : (keep ? (T)sp.gzsum[u] : T(0));
-                qi = h0 * rz;
-                qs = qi;
-            }
-            if (C >= T(0)) {
-                sq += qi;
-                sqc += qi * C;
-                sqs += qs;
-                sqcs += qs * C;
-            }
+    for (int u = 0; u < nd; ++u) {
+        const SelQ<T> o = sel_q(g, gp, f, vp, sp, src, rep, ph, cellsum, wsp, rht, rM, rz, u);
+        if (o.C >= T(0)) {
+            sq += o.qi;
+            sqc += o.qi * o.C;
+            sqs += o.qs;
+            sqcs += o.qs * o.C;
         }
-        qiv[b] = qi;
-        qsv[b] = qs;
-        ccv[b] = C;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        sqc += __shfl_xor_sync(0xffffffffu, sqc, o);
-        sqs += __shfl_xor_sync(0xffffffffu, sqs, o);
-        sqcs += __shfl_xor_sync(0xffffffffu, sqcs, o);
     }
     const bool ci_on = vc.coupling && sqc > T(0), cs_on = vc.coupling && sqcs > T(0);
     const T fi = ci_on ? sq / sqc : T(0), fs = cs_on ? sqs / sqcs : T(0);
-#pragma unroll
-    for (int b = 0; b < kSelMaxDir / 32; ++b) {
-        const int u = b * 32 + lane;
-        if (u >= nd) continue;
-        const T C = ccv[b];
-        const T ci = (ci_on && C >= T(0)) ? C * fi : T(1);
-        const T cs = (cs_on && C >= T(0)) ? C * fs : T(1);
-        store_halo(w_iso + (size_t)u * g.npad, g, src.x, src.y, src.z, qiv[b] * ci);
-        store_halo(w_sun + (size_t)u * g.npad, g, src.x, src.y, src.z, qsv[b] * cs);
+    for (int u = 0; u < nd; ++u) {
+        const SelQ<T> o = sel_q(g, gp, f, vp, sp, src, rep, ph, cellsum, wsp, rht, rM, rz, u);
+        const T ci = (ci_on && o.C >= T(0)) ? o.C * fi : T(1);
+        const T cs = (cs_on && o.C >= T(0)) ? o.C * fs : T(1);
+        store_halo(w_iso + (size_t)u * g.npad, g, src.x, src.y, src.z, o.qi * ci);
+        store_halo(w_sun + (size_t)u * g.npad, g, src.x, src.y, src.z, o.qs * cs);
     }
 }
 
@@ -479,12 +472,12 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
     k_sel_points<<<(sp.M + 127) / 128, 128, 0, st>>>(g, vc, sp.lat, sp.M, sp.hgpt);
     const int nc = std::max(g.S * sp.M, g.S * g.nd);
     k_sel_consts<T><<<(nc + 255) / 256, 256, 0, st>>>(g, sp, f.cellsum, hgpt_t, cellsum_t, htot_t);
-    const int nbw = (g.n_nodes + kSelWarps - 1) / kSelWarps;
-    k_sel_mask<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, sp);
+    const int nbw = (g.n_nodes + kSelWarps - 1) / kSelWarps, nbt = (g.n_nodes + 127) / 128;
+    k_sel_mask<T><<<nbt, 128, 0, st>>>(g, gp, f, vc, sp);
     cudaMemsetAsync(sp.table, 0xff, (size_t)sp.ht * sizeof(int), st);
     k_sel_dedupe<<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g.n_nodes, g.n_atm, sp);
     k_sel_part<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, vp, sp, hgpt_t, cellsum_t);
-    k_select<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, gp, f, vc, vp, sp, cellsum_t, htot_t, w_iso, w_sun);
+    k_select<T><<<nbt, 128, 0, st>>>(g, gp, f, vc, vp, sp, cellsum_t, htot_t, w_iso, w_sun);
     if (launches) *launches += 7;
 }
 
