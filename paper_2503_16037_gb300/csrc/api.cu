@@ -603,6 +603,9 @@ tursca_status read_red(tursca_scene *sc, int n) {
     int *hst = (int *)(sc->hred + 255);
     CK(cudaMemcpyAsync(hst, sc->status, sizeof(int), cudaMemcpyDeviceToHost, sc->st), "d2h");
     CK(cudaStreamSynchronize(sc->st), "sync");
+    // invalid field values flagged by the assembly (the node-form solve
+    // starts without waiting for it, so they are first seen here)
+    if (*hst & tk::STATUS_BAD_FIELD) return fail(sc, TURSCA_E_INVALID, "field values must be finite and non-negative");
     if (*hst & tk::STATUS_TIMEOUT) return fail(sc, TURSCA_E_TIMEOUT, "a bounded device wait gave up");
     return TURSCA_OK;
 }
@@ -2212,8 +2215,15 @@ tursca_status tursca_solve_with(tursca_scene *sc, int solver, double rtol, int m
     if (!(rtol > 0.0) || max_iter < 1) return fail(sc, TURSCA_E_INVALID, "rtol must be > 0 and max_iter >= 1");
     sc->rendered = false;
     if (solver < 0 || solver > 3) return fail(sc, TURSCA_E_INVALID, "unknown solver");
-    tursca_status e = sync_check(sc, "assemble");
-    if (e) return e;
+    // The node-form solve queues its first passes behind the assembly without
+    // waiting for it: the status word that reports invalid fields comes back
+    // with the solve's first residual norm.  The other forms check it now.
+    if (sc->single_asm || sc->aniso_asm) {
+        tursca_status e = sync_check(sc, "assemble");
+        if (e) return e;
+    } else {
+        CK(cudaGetLastError(), "assemble");
+    }
     if (sc->single_asm) {
         // s = 0: x = 0 solves the system exactly, with no products with K
         const size_t H = (size_t)sc->d.stencil_radius;

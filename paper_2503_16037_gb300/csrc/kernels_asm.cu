@@ -443,8 +443,9 @@ __global__ void __launch_bounds__(kRayBlock) k_tinfg(GridC g, GraphP gp, FieldP<
 // species, sun), and a thread sums them over sqrt(mu_s) of its source's first
 // receivers (a stencil sum over the haloed sqrt(mu_s)); ground receivers add
 // a per-layer constant.  The stored factors are premultiplied by sqrt(mu_s)
-// of the source: c = a sqrt(mu_s(n1)) / d.  The same pass writes the
-// per-source sun factors of the edge kernel (FieldP::gsrc), which need e1.
+// of the source: c = a sqrt(mu_s(n1)) / d.  The same pass writes the edge
+// kernel's source records (FieldP::srec), whose sun factors need e1, so it
+// first traces the direct beam of its nodes (k_sunz).
 constexpr int kZnBlock = 128;
 constexpr int kZnMaxDir = 128;
 
