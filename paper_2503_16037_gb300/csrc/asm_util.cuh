@@ -158,6 +158,74 @@ __device__ __forceinline__ T aslot_split(const ASlot &d) {
     else return d.splitd;
 }
 
+// The slot template of a layer staged in shared memory by the edge kernels:
+// per slot its descriptor words (FP32: the first 64 bytes of ASlot; FP64:
+// all 96) and 2 S constants, q^sun per species (a ground source: q in the
+// first) and the HG weight toward the instrument per species (0 on the
+// ground row).  Every thread of the block takes part; the caller
+// synchronises the block before reading.
+template <typename T>
+__host__ __device__ constexpr int aslot_words() { return sizeof(T) == 4 ? 4 : 6; }
+template <typename T>
+inline size_t template_smem(const GridC &g) {
+    return (size_t)g.ntmax * (16 * aslot_words<T>() + 2 * g.S * sizeof(T));
+}
+template <typename T, int S>
+__device__ __forceinline__ void stage_template(const GridC &g, const GraphP &gp, const FieldP<T> &f, int t0, int nt,
+                                               bool ground_row, int4 *sdesc, T *sconst) {
+    constexpr int NW = aslot_words<T>();
+    const int ndir = g.nd + g.ngd;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int4 *src = reinterpret_cast<const int4 *>(gp.aslot + t0 + t);
+        int4 d[NW];
+#pragma unroll
+        for (int e = 0; e < NW; ++e) d[e] = __ldg(src + e);
+#pragma unroll
+        for (int e = 0; e < NW; ++e) sdesc[(size_t)t * NW + e] = d[e];
+        const int bits = d[1].z, dir = d[1].w, hgdir = d[2].x;
+        const bool gsrc = (bits >> 11) & 1;
+        T q;
+        if constexpr (sizeof(T) == 4) q = __int_as_float(d[3].y);
+        else q = __longlong_as_double(((long long)d[4].y << 32) | (unsigned)d[4].x);
+#pragma unroll
+        for (int sp = 0; sp < S; ++sp) {
+            sconst[(size_t)t * 2 * S + sp] = !gsrc ? f.q_sun[sp * g.nd + dir] : (sp == 0 ? q : T(0));
+            sconst[(size_t)t * 2 * S + S + sp] = ground_row ? T(0) : f.hgv[sp * ndir + hgdir];
+        }
+    }
+}
+// descriptor fields of staged slot t: a0, a1, a2 and (hit_off, q, dinv, split)
+template <typename T>
+struct StagedSlot {
+    int4 a0, a1, a2;
+    int hit_off;
+    T q, dinv, split;
+};
+template <typename T>
+__device__ __forceinline__ StagedSlot<T> staged_slot(const int4 *sdesc, int t) {
+    constexpr int NW = aslot_words<T>();
+    const int4 *d = sdesc + (size_t)t * NW;
+    StagedSlot<T> o;
+    o.a0 = d[0];
+    o.a1 = d[1];
+    o.a2 = d[2];
+    if constexpr (sizeof(T) == 4) {
+        const float4 a3 = reinterpret_cast<const float4 *>(d)[3];
+        o.hit_off = __float_as_int(a3.x);
+        o.q = a3.y;
+        o.dinv = a3.z;
+        o.split = a3.w;
+    } else {
+        o.hit_off = d[3].x;
+        const double2 b0 = reinterpret_cast<const double2 *>(d)[4];
+        const double2 b1 = reinterpret_cast<const double2 *>(d)[5];
+        o.q = b0.x;
+        o.dinv = b0.y;
+        o.split = b1.x;
+    }
+    return o;
+}
+
 // optical depth of a tap list based at haloed position b
 template <typename T>
 __device__ __forceinline__ T tap_sum_h(const GraphP &gp, const T *__restrict__ mu_e_h, int off, int n, int b) {

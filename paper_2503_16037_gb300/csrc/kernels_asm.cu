@@ -870,16 +870,12 @@ __device__ __forceinline__ void slot_fast(const GridC &g, const FieldP<T> &f, co
 #ifndef TK_ASM0_MINB
 #define TK_ASM0_MINB 3
 #endif
-// int4 words of a slot descriptor the kernel reads (FP32: the first 64 bytes)
-template <typename T>
-__host__ __device__ constexpr int asm0_words() { return sizeof(T) == 4 ? 4 : 6; }
-// dynamic shared memory of k_asm0: per slot of the group's template its
-// descriptor words and 2 S constants (q^sun and the HG weight toward the
-// instrument per species); after the slot loop the same space holds the
-// warps' partial sums of s and g^sun ([W][4 + 4 S][32])
+// dynamic shared memory of k_asm0: the staged template (stage_template);
+// after the slot loop the same space holds the warps' partial sums of s and
+// g^sun ([W][4 + 4 S][32])
 template <typename T, int W>
 inline size_t asm0_smem(const GridC &g) {
-    const size_t desc = (size_t)g.ntmax * (16 * asm0_words<T>() + 2 * g.S * sizeof(T));
+    const size_t desc = template_smem<T>(g);
     const size_t red = (size_t)W * (4 + 4 * g.S) * 32 * sizeof(T);
     return desc > red ? desc : red;
 }
@@ -887,36 +883,16 @@ template <typename T, int S, int W, int MINB>
 __global__ void __launch_bounds__(32 * W, MINB)
     k_asm0(GridC g, GraphP gp, FieldP<T> f, ViewC vc) {
     constexpr int RS = srec_stride(S);
-    constexpr int NW = asm0_words<T>();
+    constexpr int NW = aslot_words<T>();
     extern __shared__ __align__(16) unsigned char asm0_dyn[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const GroupRows G = group_rows(g, gp, blockIdx.x);
     const bool ground_row = G.z == g.nz;
-    const int ndir = g.nd + g.ngd;
     int4 *sdesc = reinterpret_cast<int4 *>(asm0_dyn);
     T *sconst = reinterpret_cast<T *>(sdesc + (size_t)NW * G.nt);
-    {
-        // the group's template: descriptors and the per-slot direction constants
-        for (int t = threadIdx.x; t < G.nt; t += 32 * W) {
-            const int4 *src = reinterpret_cast<const int4 *>(gp.aslot + G.t0 + t);
-            int4 d[NW];
-#pragma unroll
-            for (int e = 0; e < NW; ++e) d[e] = __ldg(src + e);
-#pragma unroll
-            for (int e = 0; e < NW; ++e) sdesc[(size_t)t * NW + e] = d[e];
-            const int bits = d[1].z, dir = d[1].w, hgdir = d[2].x;
-            const bool gsrc = (bits >> 11) & 1;
-            T q;
-            if constexpr (sizeof(T) == 4) q = __int_as_float(d[3].y);
-            else q = __longlong_as_double(((long long)d[4].y << 32) | (unsigned)d[4].x);
-#pragma unroll
-            for (int sp = 0; sp < S; ++sp) {
-                sconst[(size_t)t * 2 * S + sp] = !gsrc ? f.q_sun[sp * g.nd + dir] : (sp == 0 ? q : T(0));
-                sconst[(size_t)t * 2 * S + S + sp] = ground_row ? T(0) : f.hgv[sp * ndir + hgdir];
-            }
-        }
-        __syncthreads();
-    }
+    // the group's template: descriptors and the per-slot direction constants
+    stage_template<T, S>(g, gp, f, G.t0, G.nt, ground_row, sdesc, sconst);
+    __syncthreads();
     const T rt_lamb = dsqrt<T>((T)(vc.albedo * __longlong_as_double((long long)*f.mus_max_bits)));
     T rho[4], rtr[4];
     int rowc[4];
@@ -943,24 +919,14 @@ __global__ void __launch_bounds__(32 * W, MINB)
         T q, dinv, split;
         T qsun[S], hv[S];
         {
-            const int4 *d = sdesc + (size_t)t * NW;
-            a0 = d[0];
-            a1 = d[1];
-            a2 = d[2];
-            if constexpr (sizeof(T) == 4) {
-                const float4 a3 = reinterpret_cast<const float4 *>(d)[3];
-                hit_off = __float_as_int(a3.x);
-                q = a3.y;
-                dinv = a3.z;
-                split = a3.w;
-            } else {
-                hit_off = d[3].x;
-                const double2 b0 = reinterpret_cast<const double2 *>(d)[4];
-                const double2 b1 = reinterpret_cast<const double2 *>(d)[5];
-                q = b0.x;
-                dinv = b0.y;
-                split = b1.x;
-            }
+            const StagedSlot<T> d = staged_slot<T>(sdesc, t);
+            a0 = d.a0;
+            a1 = d.a1;
+            a2 = d.a2;
+            hit_off = d.hit_off;
+            q = d.q;
+            dinv = d.dinv;
+            split = d.split;
 #pragma unroll
             for (int sp = 0; sp < S; ++sp) {
                 qsun[sp] = sconst[(size_t)t * 2 * S + sp];
