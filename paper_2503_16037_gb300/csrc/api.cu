@@ -1330,6 +1330,8 @@ tursca_status ensure_select(tursca_scene *sc) {
         CK(dalloc(sc->allocs, q.mask, nn * sizeof(ulonglong2)), "alloc select");
         CK(dalloc(sc->allocs, q.rep, nn * sizeof(int)), "alloc select");
         CK(dalloc(sc->allocs, q.table, (size_t)ht * sizeof(int)), "alloc select");
+        CK(dalloc(sc->allocs, q.rlist, nn * sizeof(int)), "alloc select");
+        CK(dalloc(sc->allocs, q.rcount, 2 * sizeof(int)), "alloc select");
         CK(dalloc(sc->allocs, q.pcnt, nn * q.dmax * sizeof(int)), "alloc select");
         CK(dalloc(sc->allocs, q.ph, nn * sc->d.n_species * q.dmax * sc->es), "alloc select");
     }

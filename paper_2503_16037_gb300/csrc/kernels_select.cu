@@ -219,6 +219,7 @@ __global__ void k_sel_dedupe(int n, int n_atm, SelP sp) {
         const int old = atomicCAS(sp.table + h, -1, j);
         if (old == -1) {
             sp.rep[j] = j;
+            sp.rlist[atomicAdd(sp.rcount, 1)] = j;
             return;
         }
         const ulonglong2 mo = sp.mask[old];
@@ -230,89 +231,105 @@ __global__ void k_sel_dedupe(int n, int n_atm, SelP sp) {
     }
 }
 
-// Pass 3 (one warp per representative source): the points of every dropped
-// cell join their closest kept direction; the point counts and the HG sums of
-// every direction after the re-draw go to pcnt / ph of the representative.
-// The values (sums) are in the compute type T; the decisions (which kept
-// direction a point joins) are exact.
+// Pass 3 (a block of kSelWarps warps per representative source; persistent
+// blocks take the representatives from the list one after another): the
+// points of every dropped cell join their closest kept direction; the point
+// counts and the HG sums of every direction after the re-draw go to pcnt /
+// ph of the representative.  The values (sums) are in the compute type T;
+// the decisions (which kept direction a point joins) are exact.
 template <typename T>
 __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, SelP sp, const T *hgpt,
                                                             const T *cellsum) {
     __shared__ int s_cnt[kSelWarps][kSelMaxDir];
     __shared__ T s_h[kSelWarps][MAX_SPECIES][kSelMaxDir];
-    __shared__ unsigned char s_kept[kSelWarps][kSelMaxDir];
-    __shared__ unsigned char s_list[kSelWarps][kSelMaxDir];
-    __shared__ unsigned char s_klist[kSelWarps][kSelMaxDir];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * kSelWarps + w;
-    if (j >= g.n_nodes || sp.rep[j] != j) return;  // whole warps leave together
-    int *cnt = s_cnt[w];
-    unsigned char *kept = s_kept[w];
-    const bool ground = j >= g.n_atm;
-    const int nd = ground ? g.ngd : g.nd;
-    const ulonglong2 mk = sp.mask[j];
-    for (int u = lane; u < nd; u += 32) {
-        const bool keep = ((u < 64 ? mk.x >> u : mk.y >> (u - 64)) & 1ull) != 0ull;
-        kept[u] = keep;
-        if (!ground) {
-            cnt[u] = keep ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
-            for (int s = 0; s < g.S; ++s) s_h[w][s][u] = keep ? cellsum[s * g.nd + u] : T(0);
-        } else {
-            s_h[w][0][u] = keep ? (T)sp.gzsum[u] : T(0);
-        }
-    }
-    __syncwarp();
-
-    // The points of the dropped cells, cell after cell, are dealt to the
-    // lanes round robin (lane l takes points l, l + 32, ... of that
-    // sequence), so every lane has work whatever the number of dropped cells.
-    // Inside a cell the points are ordered by their rankings, so a lane's
-    // target changes rarely and it adds a run at a time.  With many kept
-    // directions a point's target is the first kept one in its ranking; with
-    // few, the largest FP32 cosine over the kept list picks it, and exact
-    // FP64 cosines (the ranking's arithmetic) decide near-ties.
-    unsigned char *list = s_list[w], *klist = s_klist[w];
-    int nl = 0, nk = 0;
-    for (int b = 0; b < nd; b += 32) {
-        const int u = b + lane;
-        const bool dr = u < nd && !kept[u], kp = u < nd && kept[u];
-        const unsigned m = __ballot_sync(0xffffffffu, dr), mkb = __ballot_sync(0xffffffffu, kp);
-        const unsigned below = (1u << lane) - 1u;
-        if (dr) list[nl + __popc(m & below)] = (unsigned char)u;
-        if (kp) klist[nk + __popc(mkb & below)] = (unsigned char)u;
-        nl += __popc(m);
-        nk += __popc(mkb);
-    }
-    __syncwarp();
-    {
-        const unsigned char *rk = ground ? sp.grank : sp.rank;
-        const int *cs = ground ? sp.gcell_start : vp.cell_start;
-        const float4 *pf = ground ? sp.glatf : sp.latf;
-        const double *pd = ground ? sp.glat : sp.lat;
-        const float4 *df = sp.dirf + (ground ? g.nd : 0);
-        const double *dd = vp.dirhat + 3 * (ground ? g.nd : 0);
-        const bool dots = nk <= kSelDots;
-        int tot = 0;  // points of the dropped cells
-        for (int i = 0; i < nl; ++i) tot += cs[list[i] + 1] - cs[list[i]];
-        int ci = 0, off = lane;  // the lane's cell (index into list) and point offset inside it
-        int cur = -1, n = 0;
-        T a[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
-        for (int f0 = lane; f0 < tot; f0 += 32) {
-            int csz = cs[list[ci] + 1] - cs[list[ci]];
-            while (off >= csz) {
-                off -= csz;
-                ++ci;
-                csz = cs[list[ci] + 1] - cs[list[ci]];
+    __shared__ unsigned char s_kept[kSelMaxDir];
+    __shared__ unsigned char s_list[kSelMaxDir];
+    __shared__ unsigned char s_klist[kSelMaxDir];
+    __shared__ int s_r, s_nl, s_nk;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    constexpr int NT = 32 * kSelWarps;
+    const int nrep = sp.rcount[0];
+    for (;;) {
+        if (tid == 0) s_r = atomicAdd(sp.rcount + 1, 1);
+        __syncthreads();
+        const int ri = s_r;
+        if (ri >= nrep) break;
+        const int j = sp.rlist[ri];
+        const bool ground = j >= g.n_atm;
+        const int nd = ground ? g.ngd : g.nd;
+        const ulonglong2 mk = sp.mask[j];
+        // every warp's accumulators: the kept cells' own points in warp 0's
+        for (int u = tid; u < nd; u += NT) {
+            const bool keep = ((u < 64 ? mk.x >> u : mk.y >> (u - 64)) & 1ull) != 0ull;
+            s_kept[u] = keep;
+            for (int q = 0; q < kSelWarps; ++q) {
+                const bool own = q == 0 && keep;
+                s_cnt[q][u] = (!ground && own) ? vp.cell_start[u + 1] - vp.cell_start[u] : 0;
+                if (!ground) {
+                    for (int s = 0; s < g.S; ++s) s_h[q][s][u] = own ? cellsum[s * g.nd + u] : T(0);
+                } else {
+                    s_h[q][0][u] = own ? (T)sp.gzsum[u] : T(0);
+                }
             }
-            const int p = cs[list[ci]] + off;
-            off += 32;
-            {
+        }
+        __syncthreads();
+        if (w == 0) {  // the dropped and the kept directions, in order
+            int nl = 0, nk = 0;
+            for (int b = 0; b < nd; b += 32) {
+                const int u = b + lane;
+                const bool dr = u < nd && !s_kept[u], kp = u < nd && s_kept[u];
+                const unsigned m = __ballot_sync(0xffffffffu, dr), mkb = __ballot_sync(0xffffffffu, kp);
+                const unsigned below = (1u << lane) - 1u;
+                if (dr) s_list[nl + __popc(m & below)] = (unsigned char)u;
+                if (kp) s_klist[nk + __popc(mkb & below)] = (unsigned char)u;
+                nl += __popc(m);
+                nk += __popc(mkb);
+            }
+            if (lane == 0) {
+                s_nl = nl;
+                s_nk = nk;
+            }
+        }
+        __syncthreads();
+        const int nl = s_nl, nk = s_nk;
+        int *cnt = s_cnt[w];
+        // The points of the dropped cells, cell after cell, are dealt to the
+        // block's threads round robin (thread t takes points t, t + NT, ...
+        // of that sequence), so every thread has work whatever the number of
+        // dropped cells.  Inside a cell the points are ordered by their
+        // rankings, so a thread's target changes rarely and it adds a run at
+        // a time into its warp's accumulators.  With many kept directions a
+        // point's target is the first kept one in its ranking; with few, the
+        // largest FP32 cosine over the kept list picks it, and exact FP64
+        // cosines (the ranking's arithmetic) decide near-ties.
+        {
+            const unsigned char *rk = ground ? sp.grank : sp.rank;
+            const int *cs = ground ? sp.gcell_start : vp.cell_start;
+            const float4 *pf = ground ? sp.glatf : sp.latf;
+            const double *pd = ground ? sp.glat : sp.lat;
+            const float4 *df = sp.dirf + (ground ? g.nd : 0);
+            const double *dd = vp.dirhat + 3 * (ground ? g.nd : 0);
+            const bool dots = nk <= kSelDots;
+            int tot = 0;  // points of the dropped cells
+            for (int i = 0; i < nl; ++i) tot += cs[s_list[i] + 1] - cs[s_list[i]];
+            int ci = 0, off = tid;  // the thread's cell (index into the list) and point offset inside it
+            int cur = -1, n = 0;
+            T a[MAX_SPECIES] = {T(0), T(0), T(0), T(0)};
+            for (int f0 = tid; f0 < tot; f0 += NT) {
+                int csz = cs[s_list[ci] + 1] - cs[s_list[ci]];
+                while (off >= csz) {
+                    off -= csz;
+                    ++ci;
+                    csz = cs[s_list[ci] + 1] - cs[s_list[ci]];
+                }
+                const int p = cs[s_list[ci]] + off;
+                off += NT;
                 int v = -1;
                 if (dots) {
                     const float4 pt = pf[p];
                     float b1 = -3.f, b2 = -3.f;
                     for (int t = 0; t < nk; ++t) {
-                        const int c = klist[t];
+                        const int c = s_klist[t];
                         const float4 d = df[c];
                         const float co = d.x * pt.x + d.y * pt.y + d.z * pt.z;
                         if (co > b1) {
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
                         const double *q3 = pd + 3 * (size_t)p;
                         double best = -3.0;
                         for (int t = 0; t < nk; ++t) {
-                            const int c = klist[t];
+                            const int c = s_klist[t];
                             const double *h3 = dd + 3 * c;
                             const double co = __dadd_rn(__dadd_rn(__dmul_rn(h3[0], q3[0]), __dmul_rn(h3[1], q3[1])),
                                                         __dmul_rn(h3[2], q3[2]));
@@ -341,7 +358,7 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
                     const unsigned char *row = rk + (size_t)p * nd;
                     for (int q = 1; q < nd; ++q) {
                         const int c = row[q];
-                        if (kept[c]) {
+                        if (s_kept[c]) {
                             v = c;
                             break;
                         }
@@ -363,17 +380,25 @@ __global__ void __launch_bounds__(32 * kSelWarps) k_sel_part(GridC g, ViewP vp, 
                     for (int s = 0; s < g.S; ++s) a[s] += hgpt[(size_t)s * sp.M + p];
                 }
             }
+            if (cur >= 0) {
+                if (!ground) atomicAdd(&cnt[cur], n);
+                for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
+            }
         }
-        if (cur >= 0) {
-            if (!ground) atomicAdd(&cnt[cur], n);
-            for (int s = 0; s < (ground ? 1 : g.S); ++s) atomicAdd(&s_h[w][s][cur], a[s]);
+        __syncthreads();
+        // the warps' accumulators summed in a fixed order
+        T *ph = reinterpret_cast<T *>(sp.ph) + (size_t)j * g.S * sp.dmax;
+        for (int u = tid; u < nd; u += NT) {
+            int c = 0;
+            for (int q = 0; q < kSelWarps; ++q) c += s_cnt[q][u];
+            sp.pcnt[(size_t)j * sp.dmax + u] = c;
+            for (int s = 0; s < (ground ? 1 : g.S); ++s) {
+                T hsum = T(0);
+                for (int q = 0; q < kSelWarps; ++q) hsum += s_h[q][s][u];
+                ph[(size_t)s * sp.dmax + u] = hsum;
+            }
         }
-    }
-    __syncwarp();
-    T *ph = reinterpret_cast<T *>(sp.ph) + (size_t)j * g.S * sp.dmax;
-    for (int u = lane; u < nd; u += 32) {
-        sp.pcnt[(size_t)j * sp.dmax + u] = cnt[u];
-        for (int s = 0; s < (ground ? 1 : g.S); ++s) ph[(size_t)s * sp.dmax + u] = s_h[w][s][u];
+        __syncthreads();  // the shared arrays are reused for the next representative
     }
 }
 
@@ -475,8 +500,15 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
     const int nbw = (g.n_nodes + kSelWarps - 1) / kSelWarps, nbt = (g.n_nodes + 127) / 128;
     k_sel_mask<T><<<nbt, 128, 0, st>>>(g, gp, f, vc, sp);
     cudaMemsetAsync(sp.table, 0xff, (size_t)sp.ht * sizeof(int), st);
+    cudaMemsetAsync(sp.rcount, 0, 2 * sizeof(int), st);
     k_sel_dedupe<<<(g.n_nodes + 255) / 256, 256, 0, st>>>(g.n_nodes, g.n_atm, sp);
-    k_sel_part<T><<<nbw, 32 * kSelWarps, 0, st>>>(g, vp, sp, hgpt_t, cellsum_t);
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int nbp = std::max(1, std::min(nbw, 8 * std::max(1, sms)));
+        k_sel_part<T><<<nbp, 32 * kSelWarps, 0, st>>>(g, vp, sp, hgpt_t, cellsum_t);
+    }
     k_select<T><<<nbt, 128, 0, st>>>(g, gp, f, vc, vp, sp, cellsum_t, htot_t, w_iso, w_sun);
     if (launches) *launches += 7;
 }

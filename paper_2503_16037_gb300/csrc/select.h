@@ -49,6 +49,8 @@ struct SelP {
     int *rep;                        // [n_nodes] source whose re-partition serves this one (-1: none needed)
     int *table;                      // [ht] open-addressing table of kept sets (source index, -1: free)
     int ht;                          // slots: a power of two, at least twice the sources
+    int *rlist;                      // [n_nodes] the representative sources, in the order they claimed their slot
+    int *rcount;                     // [2] representatives listed, representatives handed out so far
     int *pcnt;                       // [n_nodes][dmax] point counts after the re-draw (representatives only)
     void *ph;                        // [n_nodes][S][dmax] HG (ground: cosine) sums after the re-draw, compute type
 };
