@@ -51,7 +51,7 @@ __device__ __forceinline__ double mus64(const GridC &g, const FieldP<T> &f, int 
     return s;
 }
 
-constexpr int kSelWarps = 4;
+constexpr int kSelWarps = 8;
 // kept directions up to which a point's target comes from cosines over the
 // kept list rather than from its ranking
 constexpr int kSelDots = 12;
