@@ -524,11 +524,8 @@ def main():
     mu_a, mu_s = rn.fields("cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    def step():
-        rn.set_medium(mu_a, mu_s)
-        rn.assemble()
-        rn.solve(rtol=RTOL, solver=args.solver)
-        rn.render()
+    def step():  # set_medium -> assemble -> solve -> render, one library call (tursca_run)
+        rn.run(mu_a, mu_s, rtol=RTOL, solver=args.solver)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -600,10 +597,8 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        T.tursca_set_medium(rn.handle, mu_a_h, mu_s_h, list(sc.g), sc.albedo)
-        T.tursca_assemble_flux(rn.handle, rn.geom)
-        T.tursca_solve_with(rn.handle, args.solver, RTOL, 5000)
-        T.tursca_render_radiance(rn.handle, rad_h, refl_h)  # synchronises
+        T.tursca_run(rn.handle, mu_a_h, mu_s_h, list(sc.g), sc.albedo, rn.geom, args.solver, RTOL, 5000, rad_h,
+                     refl_h)  # synchronises
         if k >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_t)

@@ -191,6 +191,17 @@ tursca_status tursca_solve_with(tursca_scene *scene, int solver, double rtol, in
  * NULL.  Requires solve.  Synchronises before returning. */
 tursca_status tursca_render_radiance(tursca_scene *scene, void *radiance, void *reflectance);
 
+/* The whole path for one medium in one call: tursca_set_medium,
+ * tursca_assemble_flux, tursca_solve_with and tursca_render_radiance in that
+ * order, with the arguments and the ownership rules of those calls (the
+ * steps of the method's data flow, Sec. 3: medium, graph weights, solve,
+ * detector).  Returns the first error (the later steps are then not run);
+ * info may be NULL.  Requires build_graph.  Synchronises before returning,
+ * as the render does; saves the caller's turnarounds between the four calls. */
+tursca_status tursca_run(tursca_scene *scene, const void *mu_abs, const void *mu_sca, const double *g, double albedo,
+                         const tursca_geometry *geom, int solver, double rtol, int max_iter, void *radiance,
+                         void *reflectance, tursca_solve_info *info);
+
 /* Gradient of a detector objective J with respect to the absorption
  * coefficient of every voxel, by the adjoint of the whole path (reverse-mode
  * differentiation written out by hand; the paper motivates the method with

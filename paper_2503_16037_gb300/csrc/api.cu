@@ -2262,6 +2262,19 @@ tursca_status tursca_render_radiance(tursca_scene *sc, void *radiance, void *ref
     return do_render<float>(sc, radiance, reflectance);
 }
 
+tursca_status tursca_run(tursca_scene *sc, const void *mu_abs, const void *mu_sca, const double *g, double albedo,
+                         const tursca_geometry *geom, int solver, double rtol, int max_iter, void *radiance,
+                         void *reflectance, tursca_solve_info *info) {
+    const NvtxRange nvtx("tursca_run");
+    tursca_status e = tursca_set_medium(sc, mu_abs, mu_sca, g, albedo);
+    if (e) return e;
+    e = tursca_assemble_flux(sc, geom);
+    if (e) return e;
+    e = tursca_solve_with(sc, solver, rtol, max_iter, info);
+    if (e) return e;
+    return tursca_render_radiance(sc, radiance, reflectance);
+}
+
 tursca_status tursca_adjoint(tursca_scene *sc, const void *dJ_dL, void *dJ_dmu_abs) {
     const NvtxRange nvtx("tursca_adjoint");
     if (!sc) return fail(nullptr, TURSCA_E_INVALID, "scene is null");

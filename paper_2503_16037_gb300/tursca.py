@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
             "tursca_solve": (st, [_vp, C.c_double, C.c_int, C.POINTER(tursca_solve_info)]),
             "tursca_solve_with": (st, [_vp, C.c_int, C.c_double, C.c_int, C.POINTER(tursca_solve_info)]),
             "tursca_render_radiance": (st, [_vp, _vp, _vp]),
+            "tursca_run": (st, [_vp, _vp, _vp, C.POINTER(C.c_double), C.c_double, C.POINTER(tursca_geometry), C.c_int,
+                                C.c_double, C.c_int, _vp, _vp, C.POINTER(tursca_solve_info)]),
             "tursca_adjoint": (st, [_vp, _vp, _vp]),
             "tursca_get": (st, [_vp, C.c_int, _vp, C.c_size_t]),
             "tursca_launch_count": (C.c_longlong, [_vp]),
@@ -193,6 +195,15 @@ def tursca_solve_with(scene, solver: int, rtol: float, max_iter: int) -> tursca_
 
 def tursca_render_radiance(scene, radiance, reflectance=None):
     _check(scene, lib().tursca_render_radiance(scene, _ptr(radiance), _ptr(reflectance)))
+
+
+def tursca_run(scene, mu_abs, mu_sca, g, albedo: float, geom: tursca_geometry, solver: int, rtol: float,
+               max_iter: int, radiance, reflectance=None) -> tursca_solve_info:
+    gg = (C.c_double * len(g))(*[float(v) for v in g])
+    info = tursca_solve_info()
+    _check(scene, lib().tursca_run(scene, _ptr(mu_abs), _ptr(mu_sca), gg, float(albedo), C.byref(geom), int(solver),
+                                   float(rtol), int(max_iter), _ptr(radiance), _ptr(reflectance), C.byref(info)))
+    return info
 
 
 def tursca_adjoint(scene, dJ_dL, dJ_dmu_abs):
@@ -371,10 +382,10 @@ class Runner:
         return rad, refl
 
     def run(self, mu_a, mu_s, rtol=1e-10, max_iter=5000, solver=SOLVER_AUTO):
-        self.set_medium(mu_a, mu_s)
-        self.assemble()
-        self.solve(rtol, max_iter, solver)
-        return self.render()
+        """set_medium -> assemble -> solve -> render in one library call."""
+        self.info = tursca_run(self.handle, mu_a, mu_s, list(self.sc.g), self.sc.albedo, self.geom, solver, rtol,
+                               max_iter, self.rad, self.refl)
+        return self.rad, self.refl
 
     def adjoint(self, dJ_dL):
         """dJ/dmu_abs (per voxel, C order (z, y, x), compute type) for the

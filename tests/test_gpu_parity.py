@@ -318,3 +318,38 @@ def test_repeated_runs_on_one_runner_identical(precision):
     for r in rads[1:]:
         assert np.array_equal(r[0], rads[0][0])
         assert np.array_equal(r[1], rads[0][1])
+
+
+@pytest.mark.parametrize("precision", [T.FP32_REFINE, T.FP64])
+def test_run_in_one_call_equals_the_four_calls(precision):
+    """tursca_run (set_medium, assemble_flux, solve, render in one call)
+    gives the bits of the four calls made one by one, with device and with
+    pinned host buffers, and reports the errors of its steps."""
+    sc = SMALL["random_R2_ragged"]()
+    rtol = 1e-10 if precision == T.FP32_REFINE else 1e-13
+    rn = T.Runner(sc, precision)
+    mu_a, mu_s = rn.fields("cuda")
+    rn.set_medium(mu_a, mu_s)
+    rn.assemble()
+    info1 = rn.solve(rtol=rtol)
+    rad1, refl1 = rn.render()
+    torch.cuda.synchronize()
+    ref = (rad1.cpu().numpy().copy(), refl1.cpu().numpy().copy())
+    rad2, refl2 = rn.run(mu_a, mu_s, rtol=rtol)
+    torch.cuda.synchronize()
+    assert np.array_equal(rad2.cpu().numpy(), ref[0]) and np.array_equal(refl2.cpu().numpy(), ref[1])
+    assert rn.info.iters == info1.iters and rn.info.refinements == info1.refinements
+    # pinned host buffers through the same call
+    dt = torch.float32 if precision == T.FP32_REFINE else torch.float64
+    rad_h = torch.empty((sc.npy, sc.npx), dtype=dt).pin_memory()
+    refl_h = torch.empty((sc.npy, sc.npx), dtype=dt).pin_memory()
+    T.tursca_run(rn.handle, mu_a.cpu().pin_memory(), mu_s.cpu().pin_memory(), list(sc.g), sc.albedo, rn.geom,
+                 T.SOLVER_AUTO, rtol, 5000, rad_h, refl_h)
+    assert np.array_equal(rad_h.numpy(), ref[0]) and np.array_equal(refl_h.numpy(), ref[1])
+    # an invalid field value is reported by the call
+    bad = mu_a.clone()
+    bad.view(-1)[0] = float("nan")
+    with pytest.raises(T.TurscaError) as ei:
+        rn.run(bad, mu_s, rtol=rtol)
+    assert ei.value.status == T.E_INVALID
+    rn.close()
