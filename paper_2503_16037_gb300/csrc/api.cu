@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "graph.h"
@@ -157,6 +158,7 @@ struct tursca_scene {
     cudaEvent_t bready = nullptr, bdone = nullptr;
     unsigned long long *topk_keys = nullptr;
     unsigned int *topk_hist = nullptr, *topk_hist_h = nullptr;
+    int *topk_band = nullptr, *topk_cnt = nullptr;  // chains in the FP32 band, [2] listed / above
     double c_eff = 0.0;
     long long n_couplings = -1, n_kept = -1;
     bool sel_ready = false, sel_asm = false;
@@ -1987,11 +1989,22 @@ tursca_status tursca_build_graph(tursca_scene *sc) {
 // that share the digits found so far, read back to pick the digit that
 // holds the wanted rank.  Needs the fields of set_medium (the keys are
 // formed from them before the rest of the assembly).
+// The (K + 1)-th largest coupling, exactly as the FP64 couplings order (the
+// oracle's arithmetic), in two steps.  A radix select on FP32 couplings
+// (relative error of a few 1e-7) finds the FP32 value t of that rank; every
+// coupling then differs from its FP32 value by far less than the band
+// [t (1 - 1e-5), t (1 + 1e-5)], so the FP64 threshold lies in the band, the
+// chains above it are all kept, and the threshold is the coupling of rank
+// K + 1 - (chains above the band) among the band's chains, whose exact FP64
+// keys are formed and ordered on the host.  Should that rank fall outside
+// the band, the radix select runs on the FP64 keys of every chain instead.
 tursca_status topk_threshold(tursca_scene *sc, const tk::GridC &g, const tk::GraphP &gp) {
     const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
     if (!sc->topk_keys) {
         CK(dalloc(sc->allocs, sc->topk_keys, (size_t)tot * sizeof(unsigned long long)), "alloc topk keys");
         CK(dalloc(sc->allocs, sc->topk_hist, sizeof(unsigned int) << tk::kTopkDigitBits), "alloc topk hist");
+        CK(dalloc(sc->allocs, sc->topk_band, (size_t)tot * sizeof(int)), "alloc topk band");
+        CK(dalloc(sc->allocs, sc->topk_cnt, 2 * sizeof(int)), "alloc topk band");
         cudaError_t e = cudaMallocHost((void **)&sc->topk_hist_h, sizeof(unsigned int) << tk::kTopkDigitBits);
         if (e != cudaSuccess) return cuda_fail(sc, e, "alloc pinned");
     }
@@ -1999,34 +2012,49 @@ tursca_status topk_threshold(tursca_scene *sc, const tk::GridC &g, const tk::Gra
         tursca_status e = ensure_select(sc);
         if (e) return e;
     }
-    if (sc->d.precision == TURSCA_FP64)
-        tk::launch_topk_keys<double>(sc->st, g, gp, field_p<double>(sc), view_c(sc), sc->selp.musmax_bits,
-                                     sc->topk_keys, &sc->launches);
-    else
-        tk::launch_topk_keys<float>(sc->st, g, gp, field_p<float>(sc), view_c(sc), sc->selp.musmax_bits,
-                                    sc->topk_keys, &sc->launches);
+    const bool fp64 = sc->d.precision == TURSCA_FP64;
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev), "device");
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "device");
     const int nb = std::max(1, nsm) * 8;
     const int nbins = 1 << tk::kTopkDigitBits;
-    unsigned long long prefix = 0ull;
-    int hi = 64;
-    long long rank = sc->max_couplings + 1;  // wanted rank from the top (1-based)
-    long long count = -1;
-    for (int pass = 0; hi > 0; ++pass) {
-        const int width = std::min(tk::kTopkDigitBits, hi), shift = hi - width;
-        tk::launch_topk_hist(sc->st, sc->topk_keys, tot, shift, width, hi, prefix, sc->topk_hist, nb);
+    const long long want = sc->max_couplings + 1;  // wanted rank from the top (1-based)
+    auto set_threshold = [&](unsigned long long key) {
+        double thr;
+        const unsigned long long bits = key - 1ull;
+        std::memcpy(&thr, &bits, sizeof(thr));
+        sc->c_eff = thr > 0.0 ? thr : 4.9406564584124654e-324;  // a zero coupling: keep C > 0
+    };
+    // one radix pass: the histogram of the next digit, read back
+    auto hist_pass = [&](auto launch) -> tursca_status {
+        launch();
         sc->launches += 1;
         CK(cudaMemcpyAsync(sc->topk_hist_h, sc->topk_hist, sizeof(unsigned int) * nbins, cudaMemcpyDeviceToHost,
                            sc->st), "d2h");
         CK(cudaStreamSynchronize(sc->st), "sync");
+        return TURSCA_OK;
+    };
+    // ---- FP32 couplings: radix select over 32-bit keys
+    unsigned int *keys32 = reinterpret_cast<unsigned int *>(sc->topk_keys);
+    if (fp64)
+        tk::launch_topk_keys32<double>(sc->st, g, gp, field_p<double>(sc), view_c(sc), sc->selp.musmax_bits, keys32,
+                                       &sc->launches);
+    else
+        tk::launch_topk_keys32<float>(sc->st, g, gp, field_p<float>(sc), view_c(sc), sc->selp.musmax_bits, keys32,
+                                      &sc->launches);
+    unsigned int prefix32 = 0u;
+    long long rank = want;
+    for (int hi = 32, pass = 0; hi > 0; ++pass) {
+        const int width = std::min(tk::kTopkDigitBits, hi), shift = hi - width;
+        tursca_status e = hist_pass([&] {
+            tk::launch_topk_hist32(sc->st, keys32, tot, shift, width, hi, prefix32, sc->topk_hist, nb);
+        });
+        if (e) return e;
         const unsigned int *h = sc->topk_hist_h;
         if (pass == 0) {
-            count = 0;
+            long long count = 0;
             for (int b = 0; b < nbins; ++b) count += h[b];
             sc->n_couplings = count;
-            sc->n_kept = 0;
             if (sc->max_couplings >= count) {
                 sc->c_eff = 0.0;
                 sc->n_kept = count;
@@ -2044,14 +2072,74 @@ tursca_status topk_threshold(tursca_scene *sc, const tk::GridC &g, const tk::Gra
         }
         if (pick < 0) return fail(sc, TURSCA_E_INVALID, "internal error: coupling rank not found");
         rank -= acc;
-        sc->n_kept += acc;  // keys in higher bins: couplings above the threshold
-        prefix = (prefix << width) | (unsigned long long)pick;
+        prefix32 = (prefix32 << width) | (unsigned int)pick;
         hi = shift;
     }
-    double thr;
-    const unsigned long long bits = prefix - 1ull;
-    std::memcpy(&thr, &bits, sizeof(thr));
-    sc->c_eff = thr > 0.0 ? thr : 4.9406564584124654e-324;  // a zero coupling: keep C > 0
+    float t32;
+    {
+        const unsigned int bits = prefix32 - 1u;
+        std::memcpy(&t32, &bits, sizeof(t32));
+    }
+    // ---- the band around it: exact keys of its chains, ordered on the host
+    const double lo = (double)t32 * (1.0 - 1e-5), hi = (double)t32 * (1.0 + 1e-5);
+    tk::launch_topk_band(sc->st, keys32, tot, lo, hi, sc->topk_band, sc->topk_cnt, nb);
+    int cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, sc->topk_cnt, sizeof cnt, cudaMemcpyDeviceToHost, sc->st), "d2h");
+    CK(cudaStreamSynchronize(sc->st), "sync");
+    const long long nband = cnt[0], above = cnt[1], rb = want - above;
+    if (rb >= 1 && rb <= nband) {
+        if (fp64)
+            tk::launch_topk_band_keys<double>(sc->st, g, gp, field_p<double>(sc), view_c(sc), sc->selp.musmax_bits,
+                                              sc->topk_band, (int)nband, sc->topk_keys);
+        else
+            tk::launch_topk_band_keys<float>(sc->st, g, gp, field_p<float>(sc), view_c(sc), sc->selp.musmax_bits,
+                                             sc->topk_band, (int)nband, sc->topk_keys);
+        sc->launches += 2;
+        std::vector<unsigned long long> v((size_t)nband);
+        CK(cudaMemcpyAsync(v.data(), sc->topk_keys, (size_t)nband * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, sc->st), "d2h");
+        CK(cudaStreamSynchronize(sc->st), "sync");
+        std::nth_element(v.begin(), v.begin() + (rb - 1), v.end(), std::greater<unsigned long long>());
+        const unsigned long long key = v[(size_t)rb - 1];
+        long long above_key = 0;
+        for (unsigned long long k : v) above_key += k > key;
+        sc->n_kept = above + above_key;
+        set_threshold(key);
+        return TURSCA_OK;
+    }
+    // ---- otherwise: the radix select over the FP64 keys of every chain
+    if (fp64)
+        tk::launch_topk_keys<double>(sc->st, g, gp, field_p<double>(sc), view_c(sc), sc->selp.musmax_bits,
+                                     sc->topk_keys, &sc->launches);
+    else
+        tk::launch_topk_keys<float>(sc->st, g, gp, field_p<float>(sc), view_c(sc), sc->selp.musmax_bits,
+                                    sc->topk_keys, &sc->launches);
+    unsigned long long prefix = 0ull;
+    rank = want;
+    sc->n_kept = 0;
+    for (int hi64 = 64; hi64 > 0;) {
+        const int width = std::min(tk::kTopkDigitBits, hi64), shift = hi64 - width;
+        tursca_status e = hist_pass([&] {
+            tk::launch_topk_hist(sc->st, sc->topk_keys, tot, shift, width, hi64, prefix, sc->topk_hist, nb);
+        });
+        if (e) return e;
+        const unsigned int *h = sc->topk_hist_h;
+        long long acc = 0;
+        int pick = -1;
+        for (int b = (1 << width) - 1; b >= 0; --b) {
+            if (acc + (long long)h[b] >= rank) {
+                pick = b;
+                break;
+            }
+            acc += h[b];
+        }
+        if (pick < 0) return fail(sc, TURSCA_E_INVALID, "internal error: coupling rank not found");
+        rank -= acc;
+        sc->n_kept += acc;  // keys in higher bins: couplings above the threshold
+        prefix = (prefix << width) | (unsigned long long)pick;
+        hi64 = shift;
+    }
+    set_threshold(prefix);
     return TURSCA_OK;
 }
 

@@ -524,55 +524,117 @@ void launch_select(cudaStream_t st, const GridC &g, const GraphP &gp, const Fiel
 // passes of kTopkBits bits: every pass histograms, over the keys that share
 // the prefix found so far, the next digit; the host picks the digit that
 // holds the wanted rank.  Keys are [n_atm][nd] then [n_ground][ngd].
-template <typename T>
-__global__ void k_topk_keys(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const unsigned long long *musmax_bits,
-                            unsigned long long *keys) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// The receiver of chain e ([n_atm][nd], then [n_ground][ngd]) and its
+// source: whether it has one, the receiver voxel (-1: the ground) and the
+// FP64 distance to it.
+struct TopkChain {
+    int j, nidx;
+    bool ground, recv;
+    double dist;
+};
+__device__ __forceinline__ TopkChain topk_chain(const GridC &g, const GraphP &gp, long long e) {
+    TopkChain c;
     const long long na_ch = (long long)g.n_atm * g.nd;
-    const long long tot = na_ch + (long long)g.n_ground * g.ngd;
-    if (e >= tot) return;
-    const double mus_lamb = vc.albedo * __longlong_as_double((long long)*musmax_bits);
-    const bool ground = e >= na_ch;
-    int j, u;
-    if (!ground) {
-        j = (int)(e / g.nd);
-        u = (int)(e - (long long)j * g.nd);
+    c.ground = e >= na_ch;
+    int u;
+    if (!c.ground) {
+        c.j = (int)(e / g.nd);
+        u = (int)(e - (long long)c.j * g.nd);
     } else {
         const long long q = e - na_ch;
-        j = (int)(q / g.ngd);
-        u = (int)(q - (long long)j * g.ngd);
+        c.j = (int)(q / g.ngd);
+        u = (int)(q - (long long)c.j * g.ngd);
     }
-    const int z = ground ? g.nz : j / g.nxy, r = ground ? j : j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
-    bool recv = false;
-    int nidx = -1;
-    double dist = 1.0;
-    if (!ground) {
+    const int z = c.ground ? g.nz : c.j / g.nxy, r = c.ground ? c.j : c.j - z * g.nxy, y = r / g.nx, x = r - y * g.nx;
+    c.recv = false;
+    c.nidx = -1;
+    c.dist = 1.0;
+    if (!c.ground) {
         const int4 d = gp.dirs[u];
         const int rz = z + d.z;
         if (rz < g.nz) {
-            recv = true;
+            c.recv = true;
             if (rz >= 0) {
-                nidx = (rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx);
-                dist = gp.dir_len[u];
+                c.nidx = (rz * g.ny + wrap_small(y + d.y, g.ny)) * g.nx + wrap_small(x + d.x, g.nx);
+                c.dist = gp.dir_len[u];
             } else {
-                dist = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
+                c.dist = ((double)z + 0.5) / (double)(-d.z) * gp.dir_len[u];
             }
         }
     } else {
         const int4 m = gp.gmem1[u];
         if ((double)m.z - 0.5 <= (double)g.nz) {
-            recv = true;
-            nidx = ((m.z - 1) * g.ny + wrap_small(y + m.y, g.ny)) * g.nx + wrap_small(x + m.x, g.nx);
-            dist = gp.gdist1[u];
+            c.recv = true;
+            c.nidx = ((m.z - 1) * g.ny + wrap_small(y + m.y, g.ny)) * g.nx + wrap_small(x + m.x, g.nx);
+            c.dist = gp.gdist1[u];
         }
     }
-    unsigned long long key = 0ull;
-    if (recv) {
-        const double ms = ground ? mus_lamb : mus64(g, f, j);
-        const double mn = nidx >= 0 ? mus64(g, f, nidx) : mus_lamb;
-        key = (unsigned long long)__double_as_longlong(sqrt(ms * mn) / dist) + 1ull;
+    return c;
+}
+
+// the exact key of chain e: 1 + the bits of its FP64 coupling (0: no receiver)
+template <typename T>
+__device__ __forceinline__ unsigned long long topk_key64(const GridC &g, const GraphP &gp, const FieldP<T> &f,
+                                                         double mus_lamb, long long e) {
+    const TopkChain c = topk_chain(g, gp, e);
+    if (!c.recv) return 0ull;
+    const double ms = c.ground ? mus_lamb : mus64(g, f, c.j);
+    const double mn = c.nidx >= 0 ? mus64(g, f, c.nidx) : mus_lamb;
+    return (unsigned long long)__double_as_longlong(sqrt(ms * mn) / c.dist) + 1ull;
+}
+
+template <typename T>
+__global__ void k_topk_keys(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const unsigned long long *musmax_bits,
+                            unsigned long long *keys) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
+    if (e >= tot) return;
+    const double mus_lamb = vc.albedo * __longlong_as_double((long long)*musmax_bits);
+    keys[e] = topk_key64(g, gp, f, mus_lamb, e);
+}
+
+// The same couplings in FP32 (relative error of a few 1e-7 against the FP64
+// ones): 1 + the bits of the FP32 value (0: no receiver).
+template <typename T>
+__global__ void k_topk_keys32(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const unsigned long long *musmax_bits,
+                              unsigned int *keys) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
+    if (e >= tot) return;
+    const float mus_lamb = (float)(vc.albedo * __longlong_as_double((long long)*musmax_bits));
+    const TopkChain c = topk_chain(g, gp, e);
+    unsigned int key = 0u;
+    if (c.recv) {
+        const float ms = c.ground ? mus_lamb : (float)f.mu_st[c.j];
+        const float mn = c.nidx >= 0 ? (float)f.mu_st[c.nidx] : mus_lamb;
+        key = (unsigned int)__float_as_int(sqrtf(ms * mn) / (float)c.dist) + 1u;
     }
     keys[e] = key;
+}
+
+// The chains whose FP32 coupling lies in [lo, hi] (their indices appended to
+// band in any order) and the number of chains above hi.
+__global__ void k_topk_band(const unsigned int *__restrict__ keys, long long n, double lo, double hi, int *band,
+                            int *counts) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned int k = keys[i];
+        if (k == 0u) continue;
+        const double c = (double)__int_as_float((int)(k - 1u));
+        if (c > hi)
+            atomicAdd(counts + 1, 1);
+        else if (c >= lo)
+            band[atomicAdd(counts, 1)] = (int)i;
+    }
+}
+
+// exact keys of the band's chains
+template <typename T>
+__global__ void k_topk_band_keys(GridC g, GraphP gp, FieldP<T> f, ViewC vc, const unsigned long long *musmax_bits,
+                                 const int *band, int nb, unsigned long long *keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const double mus_lamb = vc.albedo * __longlong_as_double((long long)*musmax_bits);
+    keys[i] = topk_key64(g, gp, f, mus_lamb, band[i]);
 }
 
 constexpr int kTopkBits = 11;
@@ -596,6 +658,53 @@ __global__ void k_topk_hist(const unsigned long long *__restrict__ keys, long lo
         if (h[b]) atomicAdd(hist + b, h[b]);
 }
 
+// the same histogram over 32-bit keys (the FP32 couplings)
+__global__ void k_topk_hist32(const unsigned int *__restrict__ keys, long long n, int shift, int width, int hi_shift,
+                              unsigned int prefix, unsigned int *hist) {
+    __shared__ unsigned int h[1 << kTopkBits];
+    for (int b = threadIdx.x; b < (1 << kTopkBits); b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    const unsigned int mask = (1u << width) - 1u;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned int k = keys[i];
+        if (k == 0u) continue;
+        if (hi_shift < 32 && (k >> hi_shift) != prefix) continue;
+        atomicAdd(&h[(k >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < (1 << kTopkBits); b += blockDim.x)
+        if (h[b]) atomicAdd(hist + b, h[b]);
+}
+
+template <typename T>
+void launch_topk_keys32(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                        unsigned long long *musmax_bits, unsigned int *keys, long long *launches) {
+    const long long tot = (long long)g.n_atm * g.nd + (long long)g.n_ground * g.ngd;
+    cudaMemsetAsync(musmax_bits, 0, sizeof(unsigned long long), st);
+    k_sel_musmax<T><<<(g.n_atm + 255) / 256, 256, 0, st>>>(g, f, musmax_bits);
+    k_topk_keys32<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, gp, f, vc, musmax_bits, keys);
+    if (launches) *launches += 2;
+}
+
+void launch_topk_hist32(cudaStream_t st, const unsigned int *keys, long long n, int shift, int width, int hi_shift,
+                        unsigned int prefix, unsigned int *hist, int nblocks) {
+    cudaMemsetAsync(hist, 0, sizeof(unsigned int) << kTopkBits, st);
+    k_topk_hist32<<<nblocks, 256, 0, st>>>(keys, n, shift, width < kTopkBits ? width : kTopkBits, hi_shift, prefix,
+                                           hist);
+}
+
+void launch_topk_band(cudaStream_t st, const unsigned int *keys, long long n, double lo, double hi, int *band,
+                      int *counts, int nblocks) {
+    cudaMemsetAsync(counts, 0, 2 * sizeof(int), st);
+    k_topk_band<<<nblocks, 256, 0, st>>>(keys, n, lo, hi, band, counts);
+}
+
+template <typename T>
+void launch_topk_band_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                           const unsigned long long *musmax_bits, const int *band, int nb, unsigned long long *keys) {
+    if (nb > 0) k_topk_band_keys<T><<<(nb + 255) / 256, 256, 0, st>>>(g, gp, f, vc, musmax_bits, band, nb, keys);
+}
+
 template <typename T>
 void launch_topk_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
                       unsigned long long *musmax_bits, unsigned long long *keys, long long *launches) {
@@ -615,6 +724,16 @@ void launch_topk_hist(cudaStream_t st, const unsigned long long *keys, long long
 
 template void launch_topk_keys<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
                                       const ViewC &, unsigned long long *, unsigned long long *, long long *);
+template void launch_topk_keys32<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
+                                        const ViewC &, unsigned long long *, unsigned int *, long long *);
+template void launch_topk_keys32<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,
+                                         const ViewC &, unsigned long long *, unsigned int *, long long *);
+template void launch_topk_band_keys<float>(cudaStream_t, const GridC &, const GraphP &, const FieldP<float> &,
+                                           const ViewC &, const unsigned long long *, const int *, int,
+                                           unsigned long long *);
+template void launch_topk_band_keys<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,
+                                            const ViewC &, const unsigned long long *, const int *, int,
+                                            unsigned long long *);
 template void launch_topk_keys<double>(cudaStream_t, const GridC &, const GraphP &, const FieldP<double> &,
                                        const ViewC &, unsigned long long *, unsigned long long *, long long *);
 

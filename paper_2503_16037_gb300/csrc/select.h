@@ -74,6 +74,22 @@ void launch_topk_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const F
 void launch_topk_hist(cudaStream_t st, const unsigned long long *keys, long long n, int shift, int width,
                       int hi_shift, unsigned long long prefix, unsigned int *hist, int nblocks);
 constexpr int kTopkDigitBits = 11;
+// The threshold in two steps: the radix select on FP32 keys (1 + the bits of
+// the FP32 coupling, relative error of a few 1e-7), then the exact FP64 keys
+// of the chains whose FP32 coupling lies within a relative band around the
+// FP32 threshold (launch_topk_band lists them and counts the chains above
+// it; launch_topk_band_keys forms their keys).  band: chain indices; counts:
+// [2] chains listed, chains above hi.
+template <typename T>
+void launch_topk_keys32(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                        unsigned long long *musmax_bits, unsigned int *keys, long long *launches);
+void launch_topk_hist32(cudaStream_t st, const unsigned int *keys, long long n, int shift, int width, int hi_shift,
+                        unsigned int prefix, unsigned int *hist, int nblocks);
+void launch_topk_band(cudaStream_t st, const unsigned int *keys, long long n, double lo, double hi, int *band,
+                      int *counts, int nblocks);
+template <typename T>
+void launch_topk_band_keys(cudaStream_t st, const GridC &g, const GraphP &gp, const FieldP<T> &f, const ViewC &vc,
+                           const unsigned long long *musmax_bits, const int *band, int nb, unsigned long long *keys);
 
 // The edge kernel with the weights read from w_iso / w_sun.
 template <typename T>
