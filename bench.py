@@ -244,6 +244,25 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x, dist=None):
+    """The largest x over all ranks (the slowest replica's time); x itself
+    when there is one rank.  The all-reduce runs on the GPU under NCCL and on
+    the host under gloo."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, slowest_s):
+    """Scenes per second of the whole job: every rank runs `steps` scenes of
+    its own replica, and the job ends with the slowest rank."""
+    return world * steps / slowest_s
+
+
 def cpu_baseline(sc, full=True):
     """The FP64 oracle as it stands, on all host cores, on one scene."""
     from oracle import oracle
@@ -580,12 +599,9 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = sum(step_ms)
     prof_ms = sum(step_ms[k] for k in prof_steps)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist)
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, args.steps, total_ms / 1000.0)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside
     mu_a_h = mu_a.cpu().pin_memory()
@@ -602,11 +618,8 @@ def main():
         if k >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * args.steps / e2e_total
+    e2e_total = max_over_ranks(e2e_total, dist)
+    e2e_value = whole_job_rate(world, args.steps, e2e_total)
     h2d = mu_a_h.numel() * 4 + mu_s_h.numel() * 4
     d2h = rad_h.numel() * 4 + refl_h.numel() * 4
 
