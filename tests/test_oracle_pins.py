@@ -6,6 +6,7 @@ Citations name the section / equation of Mikkonen et al. (scattering graph
 method) that the checked function implements.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -980,6 +981,76 @@ def test_p12_rejects_coupling_selection():
     sc = scenes.make_random(5, 5, 3, seed=1, S=1, R=1, M=512).replace(c_min=1.0)
     with pytest.raises(ValueError):
         O.run(sc, flags=O.ANISO)
+
+
+def read_flux_matrix_example():
+    """The worked example of Sec. 2 (four nodes, six edges, the printed
+    pattern of F), from tests/golden/flux_matrix_example.txt."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "flux_matrix_example.txt")
+    edges, pattern, in_pattern = {}, [], False
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if not line:
+            continue
+        if line[0] == "edge":
+            edges[int(line[1])] = (int(line[2]), int(line[3]))
+        elif line[0] == "pattern":
+            in_pattern = True
+        elif in_pattern:
+            pattern.append([int(v) for v in line])
+    return [edges[k] for k in sorted(edges)], np.array(pattern, dtype=np.int64)
+
+
+def test_p12_worked_example_pattern_is_head_to_tail():
+    """F_ab is nonzero exactly where edge a ends at the node where edge b
+    starts (light that arrives along a scatters there into b): that rule,
+    applied to the example's six edges, gives the pattern the paper prints,
+    and its transpose does not."""
+    edges, printed = read_flux_matrix_example()
+    assert printed.shape == (6, 6)
+    rule = np.array([[int(a[1] == b[0]) for b in edges] for a in edges])
+    assert (rule == printed).all()
+    assert (rule.T != printed).any()
+
+
+@pytest.mark.parametrize("make", [
+    lambda: scenes.make_random(5, 4, 3, seed=71, S=2, R=1, M=512, zero_frac=0.0),
+    lambda: scenes.make_random(6, 5, 3, seed=72, S=1, R=2, M=512, sza=35.0, albedo=0.4, zero_frac=0.0),
+])
+def test_p12_edge_form_couples_head_to_tail(make):
+    """The oracle's edge-form operator has the worked example's structure
+    (Sec. 2, the flux matrix example, with the edges arriving at a node along
+    one direction merged into one unknown): X(i, w) depends on X(j, w')
+    exactly when an edge from j reaches i along w, for every arrival
+    direction w' of j.  A seeded sample of the operator's columns is probed
+    with a single large entry at X = 0 (the map is affine, and a term with no
+    dependence adds exact zeros); a term that ran over the receiver's edges
+    instead of the source's, or kept the wrong arrival direction, moves the
+    pattern.  Every voxel of these scenes scatters (an element carries the
+    receiver's mu_s, so a voxel without scattering would zero the elements
+    of its edges)."""
+    sc = make()
+    r = O.run(sc, flags=O.ANISO)
+    nn, nin = r["n_nodes"], r["n_dirs"] + r["n_gdirs"]
+    rows = np.arange(nn, dtype=np.int32)
+    srow, scol, sdir = r["slot_row"], r["slot_col"], r["slot_dir"]
+    # the unknowns that are edges' heads: some edge arrives at i along w
+    arrives = np.zeros((nn, nin), dtype=bool)
+    arrives[srow, sdir] = True
+    feeds = {}  # source j -> the unknowns (i, w) of the edges that leave j
+    for i, j, w in zip(srow.tolist(), scol.tolist(), sdir.tolist()):
+        feeds.setdefault(j, set()).add((i, w))
+    X0 = np.zeros((nn, nin))
+    F0 = O.aniso_rows(sc, X0, rows)
+    cols = np.argwhere(arrives)
+    assert len(cols) > 0
+    if len(cols) > 500:  # a seeded sample of the columns keeps the R = 2 case to a few seconds
+        cols = cols[np.random.default_rng(9).choice(len(cols), 500, replace=False)]
+    for j, wp in cols.tolist():
+        X = X0.copy()
+        X[j, wp] = 1e10
+        d = O.aniso_rows(sc, X, rows) - F0
+        assert set(map(tuple, np.argwhere(d != 0).tolist())) == feeds.get(j, set()), (j, wp)
 
 
 # --------------------------------------------------------------------------
