@@ -4,8 +4,8 @@ Under torchrun every rank runs an independent replica of the scene path (the
 method has no exchange step between scenes), so the only cross-rank work is
 the timing: the job's time is the slowest rank's, and the whole-job rate
 counts every rank's scenes.  These tests run that reduction as two gloo
-ranks on the host, and check that the reference arm does no work on ranks
-other than 0.
+ranks on the host, check that the reference arm does no work on ranks
+other than 0, and check the JSON line the reference arm prints.
 """
 import os
 import socket
@@ -81,3 +81,28 @@ def test_reference_arm_runs_on_rank_0_only(capsys):
     args = types.SimpleNamespace(steps=1, warmup=0, gpus=2)
     bench.run_reference(args, rank=1)  # returns before any oracle work
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores
+    (one full plume scene per step) and prints one JSON line whose metric,
+    unit and direction are the GPU arm's, with its own CPU-baseline record
+    and an end-to-end record that moves no bytes to or from a device."""
+    import json
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT,
+                       env=dict(os.environ, CUDA_VISIBLE_DEVICES=""))
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "scenes/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["steps"] == 1 and d["warmup"] == 0 and d["dtype"] == "f64" and d["data"] == "synthetic"
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
